@@ -1,0 +1,156 @@
+/*
+ * qegb.h -- C ABI of libqegb: the plane-wave Kohn-Sham operator H|psi> and
+ * the block-Davidson eigensolver on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The paper ("Quantum ESPRESSO toward the exascale", Sec. 3.2.1) asks that
+ * the domain libraries exchange data only through plain APIs with minimal
+ * use of structured types; every entry point below takes plain pointers and
+ * sizes.  The one struct, qe_problem, is a flat descriptor of plain fields.
+ *
+ * Units: lengths in bohr, energies in Rydberg, k in Cartesian bohr^-1.
+ *
+ * Conventions shared by every entry point
+ *  - Complex arrays are interleaved (re, im) doubles.
+ *  - Plane-wave order: the order returned by qe_gsphere (ascending |k+G|^2,
+ *    ties by Miller index (m1, m2, m3) lexicographically).  psi, beta and
+ *    every per-plane-wave array use it.
+ *  - Bands are rows: a block of nbnd bands is [nbnd][npw][2] doubles.
+ *  - The real-space grid is [N3][N2][N1], x (the first lattice vector)
+ *    fastest; grid point r_j = sum_i (j_i / N_i) a_i.
+ *  - Memory: `mem` = QE_HOST means every array pointer of the call is host
+ *    memory (the library copies in and out); QE_DEVICE means every array
+ *    pointer is device memory on the context's GPU and the call is ordered on
+ *    `stream` (a cudaStream_t, or NULL for the legacy default stream).
+ *  - Ownership: the library never keeps a caller pointer after the call
+ *    returns (for QE_DEVICE, after the work queued on `stream` completes).
+ *  - Errors: every call returns a QE_* status and never aborts the process;
+ *    qe_last_error() gives a message for the calling thread's last failure.
+ *  - Thread safety: one qe_ctx per host thread.
+ */
+#ifndef QEGB_H
+#define QEGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  QE_OK = 0,        /* success */
+  QE_EINVAL = 1,    /* invalid argument (sizes, grid too small, null pointer) */
+  QE_ENOMEM = 2,    /* device or host allocation failed */
+  QE_ENOCONV = 3,   /* Davidson hit max_iter: the best bands are still returned */
+  QE_EAGAIN = 4,    /* serving queue full, retry later */
+  QE_PENDING = 5,   /* serving: request not finished yet */
+  QE_ETIMEOUT = 6,  /* a bounded device wait ran out */
+  QE_ECUDA = 7,     /* a CUDA runtime call failed (message in qe_last_error) */
+  QE_ECANCELED = 8  /* serving: request was cancelled */
+};
+
+enum { QE_FP64 = 0, QE_MIXED = 1 };   /* arithmetic of the GPU path */
+enum { QE_HOST = 0, QE_DEVICE = 1 };  /* where the caller's arrays live */
+
+typedef struct qe_ctx qe_ctx;
+
+/* Flat problem descriptor (caller-owned; read during the call only). */
+typedef struct {
+  double lat[9];          /* rows a1, a2, a3 (bohr) */
+  double k[3];            /* k-point, Cartesian (bohr^-1) */
+  double ecutwfc;         /* kinetic cut-off of the wavefunctions (Ry) */
+  int grid[3];            /* FFT grid N1, N2, N3; N_i >= 2 max|m_i| + 1 */
+  const double* vloc_r;   /* V_loc(r) samples [N3][N2][N1] (Ry), real */
+  int nproj;              /* number of projectors (0 allowed) */
+  const double* beta;     /* <k+G|beta_i>, complex [nproj][npw][2] */
+  const double* dmat;     /* D_ij (Ry), real symmetric [nproj][nproj] */
+  int nbnd;               /* bands in the block */
+  int mem;                /* QE_HOST or QE_DEVICE, for vloc_r, beta, dmat */
+} qe_problem;
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* qe_last_error(void);
+
+/* Create a context on CUDA device `device`.  Holds a plan cache (one plan per
+ * (lattice, k, cut-off, grid)) and the device workspaces.  QE_ECUDA if the
+ * device cannot be used. */
+int qe_ctx_create(int device, qe_ctx** out);
+void qe_ctx_destroy(qe_ctx* ctx);
+
+/* Per-kernel timing (the timing utilities of UtilXlib, Sec. 3.1).  enable=1
+ * resets the counters and records a pair of CUDA events around every kernel
+ * the context launches afterwards (on the launching stream); enable=0 stops
+ * recording.  Launches are counted whether or not timing is on. */
+int qe_profile(qe_ctx* ctx, int enable);
+
+/* Read entry `index` (0-based, in first-launch order): kernel name (copied
+ * into name[name_len]), number of timed launches and their summed device
+ * time in ms.  Waits for the recorded events.  `launches` (may be NULL)
+ * receives the number of kernels launched since the last reset.  index < 0
+ * only reports `launches`.  QE_EINVAL past the last entry. */
+int qe_profile_read(qe_ctx* ctx, int index, char* name, int name_len,
+                    long long* calls, double* ms, long long* launches);
+
+/* Plane-wave sphere (Sec. 3.2.2 item (vi): generation of plane waves and their
+ * mapping to FFT grids).  S_k = { m : |k + sum_i m_i b_i|^2 <= ecut (1 + 1e-12) },
+ * b_i = 2 pi (a_j x a_k) / (a_1 . (a_2 x a_3)).  The ordering value |k+G|^2 is
+ * the float64 expression ((qx*qx + qy*qy) + qz*qz) with
+ * q_c = ((k_c + m1*b1_c) + m2*b2_c) + m3*b3_c, each operation rounded.
+ * Host-only.  Call with miller == NULL to get the count in *npw; otherwise
+ * *npw is the capacity of miller ([*npw][3] ints) and kin (optional, may be
+ * NULL, [*npw] doubles |k+G|^2) and receives the count (QE_EINVAL if the
+ * capacity is too small).
+ * `grid` may be NULL; if given, QE_EINVAL when N_i < 2 max|m_i| + 1. */
+int qe_gsphere(const double lat[9], const double k[3], double ecut,
+               const int grid[3], int* npw, int* miller, double* kin);
+
+/* Gaussian local potential sampled on the grid (the synthetic stand-in for the
+ * pseudopotential's local part, Sec. 3.2.2 item (viii)):
+ * V(r_j) = amp * sum_I sum_{T in {-1,0,1}^3} exp(-|r_j - R_I - T.lat|^2 / (2 sigma^2)).
+ * tau: [natom][3] Cartesian positions (host).  vloc_out: [N3][N2][N1] doubles,
+ * host or device per `mem`; computed on the GPU. */
+int qe_vloc_gaussian(qe_ctx* ctx, const double lat[9], const int grid[3],
+                     int natom, const double* tau, double amp, double sigma,
+                     double* vloc_out, int mem, void* stream);
+
+/* Kleinman-Bylander projector coefficients (Sec. 3.2.2 item (viii)) of
+ * Gaussian-times-real-solid-harmonic projectors, unit L2 norm:
+ * beta_{I,n,l,m}(r) = N_{n,l} S_lm(r - R_I) exp(-|r - R_I|^2 / (2 w_n^2)),
+ * <k+G|beta> = Omega^-1/2 e^{-i q.R_I} N (-i)^l (2 pi)^{3/2} w^{2l+3} S_lm(q) e^{-w^2 q^2 / 2},
+ * q = k + G.  Order: atom-major, then per width w_n: [s, p_x, p_y, p_z], so
+ * nproj = 4 * nrad * natom.  tau [natom][3] and widths [nrad] are host arrays.
+ * beta_out: complex [nproj][npw][2], host or device per `mem`; GPU-computed. */
+int qe_beta_gaussian(qe_ctx* ctx, const double lat[9], const double k[3],
+                     double ecut, int natom, const double* tau, int nrad,
+                     const double* widths, double* beta_out, int mem,
+                     void* stream);
+
+/* H|psi> on a block of bands (Sec. 3.3: kinetic-energy, local-potential and
+ * pseudopotential contributions to the Hamiltonian):
+ *   (H c)_G = |k+G|^2 c_G + (1/N) sum_j e^{-iG.r_j} V(r_j) psi(r_j)
+ *             + sum_ij B_i(G) D_ij sum_G' conj(B_j(G')) c_G',
+ *   psi(r_j) = sum_G c_G e^{iG.r_j},  N = N1 N2 N3.
+ * psi, hpsi: complex [nbnd][npw][2], host or device per prob->mem (hpsi is
+ * overwritten).  precision: QE_FP64 (float64 throughout) or QE_MIXED (FP32
+ * FFTs and FP32 projector products, float64 in and out).
+ * Errors: QE_EINVAL for bad sizes or a grid smaller than the sphere needs. */
+int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
+            const double* psi, double* hpsi, void* stream);
+
+/* Block Davidson (Sec. 3.3, iterative solution of the Kohn-Sham Hamiltonian;
+ * Sec. 3.2.1, KS_Solvers and the dense eigensolver of LAXlib) for the nbnd
+ * lowest eigenpairs.  psi_inout: start bands in, Ritz vectors out
+ * (complex [nbnd][npw][2]); evals [nbnd] (Ry, ascending); resid [nbnd]
+ * residual 2-norms (may be NULL); iters (may be NULL) the number of basis
+ * expansions.  Converged when every ||H psi_n - e_n psi_n|| <= tol.
+ * max_dim: largest basis (0 selects 4 * nbnd).  Returns QE_ENOCONV (with the
+ * best bands filled in) after max_iter expansions.  Arrays per prob->mem;
+ * device work is ordered on `stream` and the call returns after it ends. */
+int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
+                int max_iter, int max_dim, double* psi_inout, double* evals,
+                double* resid, int* iters, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QEGB_H */

@@ -1,0 +1,251 @@
+"""Python binding of libqegb (plane-wave H|psi> and block Davidson on GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library behind the C ABI declared in include/qegb.h.  Host arrays are NumPy
+(complex128 or float64); device arrays are CUDA torch tensors (their
+``data_ptr()`` is passed through, with the tensor's current stream unless one
+is given).  There is no fallback: if the library is missing or fails to load,
+importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqegb.so")
+
+QE_OK, QE_EINVAL, QE_ENOMEM, QE_ENOCONV, QE_EAGAIN, QE_PENDING, QE_ETIMEOUT, QE_ECUDA, \
+    QE_ECANCELED = range(9)
+QE_FP64, QE_MIXED = 0, 1
+QE_HOST, QE_DEVICE = 0, 1
+
+SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
+           "qe_vloc_gaussian", "qe_beta_gaussian", "qe_hpsi", "qe_davidson", "qe_profile",
+           "qe_profile_read"]
+
+
+class QEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"QE error {code}: {msg}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libqegb.so not built ({LIB_PATH}); run "
+                          "`python -m paper_2104_10502_gb300.build`")
+    return ctypes.CDLL(LIB_PATH)
+
+
+_lib = _load()
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("lat", ctypes.c_double * 9), ("k", ctypes.c_double * 3),
+                ("ecutwfc", ctypes.c_double), ("grid", ctypes.c_int * 3),
+                ("vloc_r", _P), ("nproj", ctypes.c_int), ("beta", _P), ("dmat", _P),
+                ("nbnd", ctypes.c_int), ("mem", ctypes.c_int)]
+
+
+_lib.qe_last_error.restype = ctypes.c_char_p
+_lib.qe_ctx_create.argtypes = [ctypes.c_int, ctypes.POINTER(_P)]
+_lib.qe_ctx_destroy.argtypes = [_P]
+_lib.qe_ctx_destroy.restype = None
+_lib.qe_gsphere.argtypes = [_D, _D, ctypes.c_double, _I, _I, _I, _D]
+_lib.qe_vloc_gaussian.argtypes = [_P, _D, _I, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double,
+                                  _P, ctypes.c_int, _P]
+_lib.qe_beta_gaussian.argtypes = [_P, _D, _D, ctypes.c_double, ctypes.c_int, _D, ctypes.c_int, _D,
+                                  _P, ctypes.c_int, _P]
+_lib.qe_profile.argtypes = [_P, ctypes.c_int]
+_lib.qe_profile_read.argtypes = [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_longlong), _D,
+                                 ctypes.POINTER(ctypes.c_longlong)]
+_lib.qe_hpsi.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
+_lib.qe_davidson.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
+                             ctypes.c_int, ctypes.c_int, _P, _P, _P, _I, _P]
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(rc: int, allow=()):
+    if rc != QE_OK and rc not in allow:
+        raise QEError(rc, _lib.qe_last_error().decode())
+    return rc
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a, n=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, mem flag) of a host NumPy array or a CUDA torch tensor."""
+    if x is None:
+        return None, QE_HOST
+    if _is_torch(x):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("device arrays must be contiguous CUDA tensors")
+        return ctypes.c_void_p(x.data_ptr()), QE_DEVICE
+    if not (isinstance(x, np.ndarray) and x.flags.c_contiguous
+            and x.dtype in (np.float64, np.complex128)):
+        raise ValueError("host arrays must be C-contiguous float64/complex128 NumPy arrays")
+    return ctypes.c_void_p(x.ctypes.data), QE_HOST
+
+
+def _stream(stream, *tensors):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    for t in tensors:
+        if t is not None and _is_torch(t):
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def gsphere(lat, k, ecut: float, grid=None):
+    """Plane-wave sphere: (miller int32 (npw, 3), kin float64 (npw,))."""
+    lat = _f64(lat, 9)
+    k = _f64(k, 3)
+    g = None if grid is None else np.ascontiguousarray(grid, dtype=np.int32)
+    npw = ctypes.c_int(0)
+    gp = None if g is None else g.ctypes.data_as(_I)
+    _check(_lib.qe_gsphere(_dptr(lat), _dptr(k), float(ecut), gp, ctypes.byref(npw), None, None))
+    miller = np.zeros((npw.value, 3), dtype=np.int32)
+    kin = np.zeros(npw.value, dtype=np.float64)
+    _check(_lib.qe_gsphere(_dptr(lat), _dptr(k), float(ecut), gp, ctypes.byref(npw),
+                           miller.ctypes.data_as(_I), _dptr(kin)))
+    return miller, kin
+
+
+class Context:
+    """One CUDA device, its plan cache and workspaces (qe_ctx)."""
+
+    def __init__(self, device: int = 0):
+        h = _P()
+        _check(_lib.qe_ctx_create(int(device), ctypes.byref(h)))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.qe_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- per-kernel timing ---------------------------------------------------
+    def profile(self, enable: bool = True):
+        _check(_lib.qe_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """({kernel: (timed launches, total ms)}, kernels launched since reset)."""
+        out = {}
+        launches = ctypes.c_longlong(0)
+        _check(_lib.qe_profile_read(self._h, -1, None, 0, None, None, ctypes.byref(launches)))
+        i = 0
+        while True:
+            name = ctypes.create_string_buffer(64)
+            calls = ctypes.c_longlong(0)
+            ms = ctypes.c_double(0.0)
+            rc = _lib.qe_profile_read(self._h, i, name, 64, ctypes.byref(calls), ctypes.byref(ms),
+                                      None)
+            if rc == QE_EINVAL:
+                break
+            _check(rc)
+            out[name.value.decode()] = (calls.value, ms.value)
+            i += 1
+        return out, launches.value
+
+    # ---- builders ---------------------------------------------------------
+    def vloc_gaussian(self, lat, grid, tau, out, amp=-2.0, sigma=1.0, stream=None):
+        lat = _f64(lat, 9)
+        g = np.ascontiguousarray(grid, dtype=np.int32)
+        tau = _f64(tau)
+        p, mem = _ptr(out)
+        _check(_lib.qe_vloc_gaussian(self._h, _dptr(lat), g.ctypes.data_as(_I), tau.size // 3,
+                                     _dptr(tau), float(amp), float(sigma), p, mem,
+                                     _stream(stream, out)))
+        return out
+
+    def beta_gaussian(self, lat, k, ecut, tau, widths, out, stream=None):
+        lat = _f64(lat, 9)
+        k = _f64(k, 3)
+        tau = _f64(tau)
+        w = _f64(widths)
+        p, mem = _ptr(out)
+        _check(_lib.qe_beta_gaussian(self._h, _dptr(lat), _dptr(k), float(ecut), tau.size // 3,
+                                     _dptr(tau), w.size, _dptr(w), p, mem, _stream(stream, out)))
+        return out
+
+    # ---- operator and eigensolver -----------------------------------------
+    @staticmethod
+    def problem(lat, k, ecut, grid, vloc, beta, dmat, nbnd) -> Problem:
+        pr = Problem()
+        pr.lat[:] = list(_f64(lat, 9))
+        pr.k[:] = list(_f64(k, 3))
+        pr.ecutwfc = float(ecut)
+        pr.grid[:] = [int(x) for x in grid]
+        pv, mem = _ptr(vloc)
+        pr.vloc_r = pv
+        nproj = 0 if beta is None else int(beta.shape[0])
+        pr.nproj = nproj
+        if nproj:
+            pb, mb = _ptr(beta)
+            pd, md = _ptr(dmat)
+            if mb != mem or md != mem:
+                raise ValueError("vloc, beta and dmat must live in the same memory")
+            pr.beta, pr.dmat = pb, pd
+        pr.nbnd = int(nbnd)
+        pr.mem = mem
+        return pr
+
+    def hpsi(self, prob: Problem, psi, hpsi, precision=QE_FP64, stream=None):
+        pp, mp = _ptr(psi)
+        ph, mh = _ptr(hpsi)
+        if prob.nbnd > 0 and (mp != prob.mem or mh != prob.mem):
+            raise ValueError("psi/hpsi must live where the problem's arrays live")
+        _check(_lib.qe_hpsi(self._h, ctypes.byref(prob), int(precision), pp, ph,
+                            _stream(stream, psi)))
+        return hpsi
+
+    def davidson(self, prob: Problem, psi, evals, resid=None, precision=QE_FP64, tol=1e-8,
+                 max_iter=100, max_dim=0, stream=None):
+        """Returns (status, iters); status QE_OK or QE_ENOCONV."""
+        pp, mp = _ptr(psi)
+        pe, me = _ptr(evals)
+        pr_, mr = _ptr(resid)
+        if mp != prob.mem or me != prob.mem or (resid is not None and mr != prob.mem):
+            raise ValueError("psi/evals/resid must live where the problem's arrays live")
+        it = ctypes.c_int(0)
+        rc = _check(_lib.qe_davidson(self._h, ctypes.byref(prob), int(precision), float(tol),
+                                     int(max_iter), int(max_dim), pp, pe, pr_, ctypes.byref(it),
+                                     _stream(stream, psi)), allow=(QE_ENOCONV,))
+        return rc, it.value

@@ -1,0 +1,385 @@
+// C-ABI entry points: context, plan cache, builders and H|psi>.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "plan.h"
+#include "ctx.h"
+
+namespace qe {
+
+int build_vloc(const double lat[9], const int grid[3], int natom, const double* tau_h, double amp,
+               double sigma, double* v_dev, cudaStream_t st);
+int build_beta(const double lat[9], const double k[3], double ecut, int natom, const double* tau_h,
+               int nrad, const double* widths_h, double* beta_dev, int* npw_out, cudaStream_t st);
+
+void Prof::begin(const char* name, cudaStream_t st, cudaEvent_t* ev) {
+  ++launches;
+  *ev = nullptr;
+  if (!on) return;
+  if (cudaEventCreate(ev) != cudaSuccess) { cudaGetLastError(); *ev = nullptr; return; }
+  cudaEventRecord(*ev, st);
+}
+
+void Prof::end(const char* name, cudaStream_t st, cudaEvent_t ev) {
+  if (!on || !ev) return;
+  cudaEvent_t b;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaGetLastError(); cudaEventDestroy(ev); return; }
+  cudaEventRecord(b, st);
+  recs.push_back({name, ev, b});
+}
+
+int Prof::fold() {
+  int rc = QE_OK;
+  for (auto& r : recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      rc = QE_ECUDA;
+    }
+    size_t i = 0;
+    while (i < names.size() && names[i] != r.name) ++i;
+    if (i == names.size()) { names.push_back(r.name); calls.push_back(0); ms.push_back(0.0); }
+    calls[i] += 1;
+    ms[i] += t;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  recs.clear();
+  return rc;
+}
+
+void Prof::reset() {
+  fold();
+  names.clear();
+  calls.clear();
+  ms.clear();
+  launches = 0;
+}
+
+DevPlan::~DevPlan() {
+  if (block) cudaFree(block);
+}
+
+int DevBuf::ensure(size_t nbytes) {
+  if (nbytes <= bytes && p) return QE_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+  if (nbytes == 0) return QE_OK;
+  if (cudaMalloc(&p, nbytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed", nbytes);
+    p = nullptr;
+    return QE_ENOMEM;
+  }
+  bytes = nbytes;
+  return QE_OK;
+}
+DevBuf::~DevBuf() {
+  if (p) cudaFree(p);
+}
+
+static bool same_key(const DevPlan& P, const double lat[9], const double k[3], double ecut,
+                     const int grid[3]) {
+  return std::memcmp(P.lat, lat, sizeof(P.lat)) == 0 && std::memcmp(P.k, k, sizeof(P.k)) == 0 &&
+         P.ecut == ecut && P.grid[0] == grid[0] && P.grid[1] == grid[1] && P.grid[2] == grid[2];
+}
+
+int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, const int grid[3],
+             DevPlan** out) {
+  for (auto& p : ctx->plans)
+    if (same_key(*p, lat, k, ecut, grid)) { *out = p.get(); return QE_OK; }
+  auto P = std::make_unique<DevPlan>();
+  std::memcpy(P->lat, lat, sizeof(P->lat));
+  std::memcpy(P->k, k, sizeof(P->k));
+  P->ecut = ecut;
+  std::memcpy(P->grid, grid, sizeof(P->grid));
+  int rc = build_plan_host(lat, k, ecut, grid, P->h);
+  if (rc) return rc;
+  for (int c = 0; c < 3; ++c) make_radix(grid[c], P->rad[c]);
+  const PlanHost& h = P->h;
+  std::vector<int> perm[3];
+  std::vector<double> tw[3];
+  for (int c = 0; c < 3; ++c) { perm[c] = digit_reversal(P->rad[c]); tw[c] = twiddles(grid[c]); }
+  // one allocation: doubles first, then ints
+  size_t nd = h.npw;
+  for (int c = 0; c < 3; ++c) nd += 2 * (size_t)grid[c];
+  size_t ni = (h.nst + 1) + 3 * (size_t)h.npw + 2 * (size_t)h.nst + h.nax;
+  for (int c = 0; c < 3; ++c) ni += grid[c];
+  const size_t bytes = nd * sizeof(double) + ni * sizeof(int);
+  if (cudaMalloc(&P->block, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("plan: cudaMalloc of %zu bytes failed", bytes);
+    return QE_ENOMEM;
+  }
+  std::vector<char> host(bytes);
+  double* dp = reinterpret_cast<double*>(host.data());
+  size_t od = 0;
+  auto put_d = [&](const double* src, size_t n) { std::memcpy(dp + od, src, n * sizeof(double)); size_t o = od; od += n; return o; };
+  const size_t o_kin = put_d(h.kin.data(), h.npw);
+  size_t o_tw[3];
+  for (int c = 0; c < 3; ++c) o_tw[c] = put_d(tw[c].data(), tw[c].size());
+  int* ip = reinterpret_cast<int*>(host.data() + nd * sizeof(double));
+  size_t oi = 0;
+  auto put_i = [&](const int* src, size_t n) { std::memcpy(ip + oi, src, n * sizeof(int)); size_t o = oi; oi += n; return o; };
+  const size_t o_ptr = put_i(h.st_ptr.data(), h.nst + 1);
+  const size_t o_g = put_i(h.st_g.data(), h.npw);
+  const size_t o_z = put_i(h.st_z.data(), h.npw);
+  const size_t o_of = put_i(h.st_of.data(), h.npw);
+  const size_t o_x = put_i(h.st_x.data(), h.nst);
+  const size_t o_y = put_i(h.st_y.data(), h.nst);
+  const size_t o_ax = put_i(h.ax.data(), h.nax);
+  size_t o_perm[3];
+  for (int c = 0; c < 3; ++c) o_perm[c] = put_i(perm[c].data(), perm[c].size());
+  if (cudaMemcpy(P->block, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("plan: upload failed");
+    return QE_ECUDA;
+  }
+  double* dd = reinterpret_cast<double*>(P->block);
+  int* di = reinterpret_cast<int*>(reinterpret_cast<char*>(P->block) + nd * sizeof(double));
+  P->kin = dd + o_kin;
+  for (int c = 0; c < 3; ++c) { P->tw[c] = dd + o_tw[c]; P->perm[c] = di + o_perm[c]; }
+  P->st_ptr = di + o_ptr;
+  P->st_g = di + o_g;
+  P->st_z = di + o_z;
+  P->st_of = di + o_of;
+  P->st_x = di + o_x;
+  P->st_y = di + o_y;
+  P->ax = di + o_ax;
+  ctx->plans.push_back(std::move(P));
+  *out = ctx->plans.back().get();
+  return QE_OK;
+}
+
+int check_problem(const qe_problem* pr, const char* who) {
+  if (!pr) { set_error("%s: null problem", who); return QE_EINVAL; }
+  if (pr->mem != QE_HOST && pr->mem != QE_DEVICE) { set_error("%s: bad mem flag", who); return QE_EINVAL; }
+  if (pr->nbnd < 0 || pr->nproj < 0) { set_error("%s: negative size", who); return QE_EINVAL; }
+  for (int c = 0; c < 3; ++c)
+    if (pr->grid[c] < 1) { set_error("%s: grid must be positive", who); return QE_EINVAL; }
+  if (!pr->vloc_r) { set_error("%s: vloc_r is null", who); return QE_EINVAL; }
+  if (pr->nproj > 0 && (!pr->beta || !pr->dmat)) { set_error("%s: beta/dmat null with nproj > 0", who); return QE_EINVAL; }
+  return QE_OK;
+}
+
+#define QE_TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+#define QE_CU(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_error("%s: %s", #x, cudaGetErrorString(e_)); return QE_ECUDA; } } while (0)
+
+// Device views of the problem's operator arrays (copied in when they are host arrays).
+int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView& op,
+                     cudaStream_t st) {
+  const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
+  const size_t nbeta = (size_t)pr->nproj * P.h.npw * 2;
+  const size_t nd = (size_t)pr->nproj * pr->nproj;
+  op.nproj = pr->nproj;
+  if (pr->mem == QE_DEVICE) {
+    op.vloc = pr->vloc_r;
+    op.beta = pr->beta;
+    op.dmat = pr->dmat;
+    return QE_OK;
+  }
+  QE_TRY(ctx->h_v.ensure(ngrid * sizeof(double)));
+  QE_TRY(ctx->h_beta.ensure(nbeta * sizeof(double)));
+  QE_TRY(ctx->h_d.ensure(nd * sizeof(double)));
+  QE_CU(cudaMemcpyAsync(ctx->h_v.p, pr->vloc_r, ngrid * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (pr->nproj > 0) {
+    QE_CU(cudaMemcpyAsync(ctx->h_beta.p, pr->beta, nbeta * sizeof(double), cudaMemcpyHostToDevice, st));
+    QE_CU(cudaMemcpyAsync(ctx->h_d.p, pr->dmat, nd * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  op.vloc = (const double*)ctx->h_v.p;
+  op.beta = (const double*)ctx->h_beta.p;
+  op.dmat = (const double*)ctx->h_d.p;
+  return QE_OK;
+}
+
+template <typename T>
+static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const double* psi,
+                       double* hpsi, int nb, cudaStream_t st) {
+  const int npw = P.h.npw;
+  const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
+  QE_TRY(ctx->vp.ensure(ngrid * sizeof(T)));
+  QE_TRY(launch_vperm<T>(P, op.vloc, (T*)ctx->vp.p, st, &ctx->prof));
+  const size_t per_band = stick_bytes(P, 1, 2 * sizeof(T));
+  int nbc = (int)std::max<size_t>(1, ctx->stick_budget / std::max<size_t>(per_band, 1));
+  nbc = std::min(nbc, nb);
+  QE_TRY(ctx->sticks.ensure(stick_bytes(P, nbc, 2 * sizeof(T))));
+  for (int b0 = 0; b0 < nb; b0 += nbc) {
+    const int n = std::min(nbc, nb - b0);
+    QE_TRY(launch_local_kinetic<T>(P, psi, hpsi, (const T*)ctx->vp.p, ctx->sticks.p, b0, n, st,
+                                   &ctx->prof));
+  }
+  if (op.nproj > 0) {
+    const int np = op.nproj;
+    QE_TRY(ctx->proj.ensure((size_t)np * nb * 2 * sizeof(double)));
+    QE_TRY(ctx->projd.ensure((size_t)np * nb * 2 * sizeof(double)));
+    const size_t sb = gemm_inner_scratch(np, nb, npw, sizeof(T));
+    QE_TRY(ctx->part.ensure(sb));
+    QE_TRY(gemm_inner<T>(op.beta, npw, psi, npw, np, nb, npw, (double*)ctx->proj.p, nb,
+                         ctx->part.p, ctx->part.bytes, st, &ctx->prof));
+    QE_TRY(dmul(op.dmat, (const double*)ctx->proj.p, (double*)ctx->projd.p, np, nb, st, &ctx->prof));
+    QE_TRY(gemm_outer<T>(op.beta, npw, (const double*)ctx->projd.p, nb, npw, nb, np, hpsi, npw, 1, st,
+                         &ctx->prof));
+  }
+  return QE_OK;
+}
+
+int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, const double* psi,
+              double* hpsi, int nb, cudaStream_t st) {
+  if (nb == 0) return QE_OK;
+  if (precision == QE_FP64) return hpsi_device<double>(ctx, P, op, psi, hpsi, nb, st);
+  return hpsi_device<float>(ctx, P, op, psi, hpsi, nb, st);
+}
+
+}  // namespace qe
+
+using namespace qe;
+
+extern "C" {
+
+int qe_ctx_create(int device, qe_ctx** out) {
+  clear_error();
+  if (!out) { set_error("qe_ctx_create: null out"); return QE_EINVAL; }
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    set_error("qe_ctx_create: no CUDA device %d (%s)", device, cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  QE_CU(cudaSetDevice(device));
+  qe_ctx* c = new qe_ctx();
+  c->device = device;
+  *out = c;
+  return QE_OK;
+}
+
+void qe_ctx_destroy(qe_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  ctx->prof.reset();
+  delete ctx;
+}
+
+int qe_profile(qe_ctx* ctx, int enable) {
+  clear_error();
+  if (!ctx) { set_error("qe_profile: null context"); return QE_EINVAL; }
+  QE_CU(cudaSetDevice(ctx->device));
+  ctx->prof.reset();
+  ctx->prof.on = enable != 0;
+  return QE_OK;
+}
+
+int qe_profile_read(qe_ctx* ctx, int index, char* name, int name_len, long long* calls,
+                    double* ms, long long* launches) {
+  clear_error();
+  if (!ctx) { set_error("qe_profile_read: null context"); return QE_EINVAL; }
+  QE_CU(cudaSetDevice(ctx->device));
+  int rc = ctx->prof.fold();
+  if (launches) *launches = ctx->prof.launches;
+  if (index < 0) return rc;
+  if (index >= (int)ctx->prof.names.size()) { set_error("qe_profile_read: no entry %d", index); return QE_EINVAL; }
+  if (name && name_len > 0) {
+    std::strncpy(name, ctx->prof.names[index].c_str(), name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (calls) *calls = ctx->prof.calls[index];
+  if (ms) *ms = ctx->prof.ms[index];
+  return rc;
+}
+
+int qe_vloc_gaussian(qe_ctx* ctx, const double lat[9], const int grid[3], int natom,
+                     const double* tau, double amp, double sigma, double* vloc_out, int mem,
+                     void* stream) {
+  clear_error();
+  if (!ctx || !lat || !grid || !vloc_out || (natom > 0 && !tau) || natom < 0 || !(sigma > 0)) {
+    set_error("qe_vloc_gaussian: invalid argument");
+    return QE_EINVAL;
+  }
+  if (mem != QE_HOST && mem != QE_DEVICE) { set_error("qe_vloc_gaussian: bad mem flag"); return QE_EINVAL; }
+  QE_CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ng = (size_t)grid[0] * grid[1] * grid[2];
+  double* dst = vloc_out;
+  if (mem == QE_HOST) {
+    QE_TRY(ctx->h_v.ensure(ng * sizeof(double)));
+    dst = (double*)ctx->h_v.p;
+  }
+  QE_TRY(build_vloc(lat, grid, natom, tau, amp, sigma, dst, st));
+  if (mem == QE_HOST) {
+    QE_CU(cudaMemcpyAsync(vloc_out, dst, ng * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QE_CU(cudaStreamSynchronize(st));
+  }
+  return QE_OK;
+}
+
+int qe_beta_gaussian(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, int natom,
+                     const double* tau, int nrad, const double* widths, double* beta_out, int mem,
+                     void* stream) {
+  clear_error();
+  if (!ctx || !lat || !k || !beta_out || natom < 0 || nrad < 0 || (natom > 0 && !tau) ||
+      (nrad > 0 && !widths)) {
+    set_error("qe_beta_gaussian: invalid argument");
+    return QE_EINVAL;
+  }
+  for (int n = 0; n < nrad; ++n)
+    if (!(widths[n] > 0)) { set_error("qe_beta_gaussian: widths must be positive"); return QE_EINVAL; }
+  if (mem != QE_HOST && mem != QE_DEVICE) { set_error("qe_beta_gaussian: bad mem flag"); return QE_EINVAL; }
+  QE_CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Sphere S;
+  QE_TRY(build_sphere(lat, k, ecut, S));
+  const size_t n = (size_t)4 * nrad * natom * S.npw * 2;
+  double* dst = beta_out;
+  if (mem == QE_HOST) {
+    QE_TRY(ctx->h_beta.ensure(n * sizeof(double)));
+    dst = (double*)ctx->h_beta.p;
+  }
+  int npw = 0;
+  QE_TRY(build_beta(lat, k, ecut, natom, tau, nrad, widths, dst, &npw, st));
+  if (mem == QE_HOST && n > 0) {
+    QE_CU(cudaMemcpyAsync(beta_out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QE_CU(cudaStreamSynchronize(st));
+  }
+  return QE_OK;
+}
+
+int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* psi, double* hpsi,
+            void* stream) {
+  clear_error();
+  if (!ctx) { set_error("qe_hpsi: null context"); return QE_EINVAL; }
+  QE_TRY(check_problem(prob, "qe_hpsi"));
+  if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_hpsi: bad precision"); return QE_EINVAL; }
+  if (prob->nbnd > 0 && (!psi || !hpsi)) { set_error("qe_hpsi: null psi/hpsi"); return QE_EINVAL; }
+  QE_CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  DevPlan* P = nullptr;
+  QE_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
+  OpView op;
+  QE_TRY(resolve_operator(ctx, prob, *P, op, st));
+  const int nb = prob->nbnd;
+  const size_t nel = (size_t)nb * P->h.npw * 2;
+  const double* dpsi = psi;
+  double* dhpsi = hpsi;
+  if (prob->mem == QE_HOST && nb > 0) {
+    QE_TRY(ctx->h_psi.ensure(nel * sizeof(double)));
+    QE_TRY(ctx->h_hpsi.ensure(nel * sizeof(double)));
+    QE_CU(cudaMemcpyAsync(ctx->h_psi.p, psi, nel * sizeof(double), cudaMemcpyHostToDevice, st));
+    dpsi = (const double*)ctx->h_psi.p;
+    dhpsi = (double*)ctx->h_hpsi.p;
+  }
+  QE_TRY(hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st));
+  if (prob->mem == QE_HOST) {
+    if (nb > 0)
+      QE_CU(cudaMemcpyAsync(hpsi, dhpsi, nel * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QE_CU(cudaStreamSynchronize(st));
+  }
+  return QE_OK;
+}
+
+}  // extern "C"

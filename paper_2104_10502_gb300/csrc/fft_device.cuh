@@ -1,0 +1,174 @@
+// Device-side building blocks of the shared-memory 3D FFT.
+//
+// All transforms are in place, on lines held in shared memory, with every
+// thread of the block cooperating on every stage:
+//   * inverse transforms (G -> r, e^{+i}) run mixed-radix decimation in
+//     frequency (DIF): natural order in, digit-reversed order out;
+//   * forward transforms (r -> G, e^{-i}) run decimation in time (DIT):
+//     digit-reversed order in, natural order out.
+// A pointwise multiply placed between the two therefore needs no permutation
+// pass: it only indexes its operand through the digit-reversal table.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace qe {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.x * s, a.y * s}; }
+// i * s * a
+template <typename T>
+__device__ __forceinline__ cx<T> cimul(cx<T> a, T s) { return {-s * a.y, s * a.x}; }
+
+// ---- small DFTs: X_q = sum_r v_r exp(SIGN 2 pi i r q / R) --------------------
+template <typename T, int SIGN>
+__device__ __forceinline__ void dft2(cx<T>* v) {
+  const cx<T> a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <typename T, int SIGN>
+__device__ __forceinline__ void dft3(cx<T>* v) {
+  const T h = T(0.5);
+  const T s3 = T(SIGN) * T(0.866025403784438646763723170752936183);  // sin(2 pi / 3)
+  const cx<T> t1 = cadd(v[1], v[2]);
+  const cx<T> t2 = {v[0].x - h * t1.x, v[0].y - h * t1.y};
+  const cx<T> d = cimul(csub(v[1], v[2]), s3);
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(t2, d);
+  v[2] = csub(t2, d);
+}
+
+template <typename T, int SIGN>
+__device__ __forceinline__ void dft4(cx<T>* v) {
+  const cx<T> a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+  const cx<T> c = cadd(v[1], v[3]), d = cimul(csub(v[1], v[3]), T(SIGN));
+  v[0] = cadd(a, c);
+  v[2] = csub(a, c);
+  v[1] = cadd(b, d);
+  v[3] = csub(b, d);
+}
+
+template <typename T, int SIGN>
+__device__ __forceinline__ void dft5(cx<T>* v) {
+  // cos(2pi/5) = (sqrt5 - 1)/4, cos(4pi/5) = -(sqrt5 + 1)/4,
+  // sin(2pi/5) = sqrt((5 + sqrt5)/8), sin(4pi/5) = sqrt((5 - sqrt5)/8)
+  const T c1 = T(0.309016994374947424102293417182819059);
+  const T c2 = T(-0.809016994374947424102293417182819059);
+  const T s1 = T(SIGN) * T(0.951056516295153572116439333379382143);
+  const T s2 = T(SIGN) * T(0.587785252292473129168705954639072769);
+  const cx<T> a = v[0];
+  const cx<T> t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  const cx<T> t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  const cx<T> r1 = {a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y};
+  const cx<T> r2 = {a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y};
+  // i (s1 t3 + s2 t4) and i (s2 t3 - s1 t4)
+  const cx<T> i1 = {-(s1 * t3.y + s2 * t4.y), s1 * t3.x + s2 * t4.x};
+  const cx<T> i2 = {-(s2 * t3.y - s1 * t4.y), s2 * t3.x - s1 * t4.x};
+  v[0] = cadd(a, cadd(t1, t2));
+  v[1] = cadd(r1, i1);
+  v[4] = csub(r1, i1);
+  v[2] = cadd(r2, i2);
+  v[3] = csub(r2, i2);
+}
+
+template <typename T, int SIGN, int R>
+__device__ __forceinline__ void dftR(cx<T>* v) {
+  if constexpr (R == 2) dft2<T, SIGN>(v);
+  else if constexpr (R == 3) dft3<T, SIGN>(v);
+  else if constexpr (R == 4) dft4<T, SIGN>(v);
+  else dft5<T, SIGN>(v);
+}
+
+// Twiddle exp(SIGN 2 pi i t / n) from the table tw[t] = exp(-2 pi i t / n).
+template <typename T, int SIGN>
+__device__ __forceinline__ cx<T> twid(const cx<T>* tw, int t) {
+  const cx<T> w = tw[t];
+  return SIGN < 0 ? w : cx<T>{w.x, -w.y};
+}
+
+// One radix-R stage over `nlines` lines of length n.  Element e of line l sits
+// at base[lofs(l) + e * es], lofs(l) = lofs_tab ? lofs_tab[l] : l * ls.
+// line_fast selects which index varies fastest across consecutive threads
+// (pick the one that makes consecutive threads touch consecutive addresses).
+template <typename T, int SIGN, bool DIT, int R>
+__device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int* lofs_tab,
+                                          int nlines, bool line_fast, int n, int L,
+                                          const cx<T>* tw) {
+  const int M = L / R;
+  const int per_line = n / R;
+  const int nit = nlines * per_line;
+  const int tstep = n / L;
+  for (int it = threadIdx.x; it < nit; it += blockDim.x) {
+    int line, rest;
+    if (line_fast) { line = it % nlines; rest = it / nlines; }
+    else { line = it / per_line; rest = it - line * per_line; }
+    const int blk = rest / M;
+    const int j = rest - blk * M;
+    const int off = lofs_tab ? lofs_tab[line] : line * ls;
+    cx<T>* p = base + off + (blk * L + j) * es;
+    const int step = M * es;
+    cx<T> v[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[q] = p[q * step];
+    if (DIT) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
+      dftR<T, SIGN, R>(v);
+    } else {
+      dftR<T, SIGN, R>(v);
+#pragma unroll
+      for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) p[q * step] = v[q];
+  }
+}
+
+template <typename T, int SIGN, bool DIT>
+__device__ __forceinline__ void fft_stage_any(cx<T>* base, int es, int ls, const int* lofs,
+                                              int nlines, bool line_fast, int n, int R, int L,
+                                              const cx<T>* tw) {
+  switch (R) {
+    case 2: fft_stage<T, SIGN, DIT, 2>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
+    case 3: fft_stage<T, SIGN, DIT, 3>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
+    case 4: fft_stage<T, SIGN, DIT, 4>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
+    default: fft_stage<T, SIGN, DIT, 5>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
+  }
+}
+
+// Whole in-place transform of every line; ends with __syncthreads().
+// Must be called by every thread of the block.
+template <typename T, int SIGN, bool DIT>
+__device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlines,
+                          bool line_fast, const Radix& rp, const cx<T>* tw) {
+  if (!DIT) {
+    for (int s = 0; s < rp.nst; ++s) {
+      fft_stage_any<T, SIGN, false>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s], rp.L[s], tw);
+      __syncthreads();
+    }
+  } else {
+    for (int s = rp.nst - 1; s >= 0; --s) {
+      fft_stage_any<T, SIGN, true>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s], rp.L[s], tw);
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace qe

@@ -1,0 +1,266 @@
+// Complex matrix products of the nonlocal (pseudopotential) term and of the
+// Davidson subspace (Sec. 3.3: pseudopotential contribution to the
+// Hamiltonian; Sec. 3.2.1: LAXlib dense linear algebra):
+//
+//   gemm_inner  P[m][n] = sum_k conj(A[m][k]) B[n][k]   (projections <beta|psi>,
+//               overlap and Hamiltonian matrices of the subspace); K is the long
+//               plane-wave axis, so K is split over CTAs and the partial sums are
+//               added in a fixed order (deterministic, independent of timing);
+//   gemm_outer  C[n][m] (+)= sum_k A[k][m] B[k][n]    (beta (D P), rotations V X);
+//   dmul        Q = D P with a real D.
+// These are SIMT kernels: FP64 has no tcgen05 kind on sm_103a, and the FP32
+// variant serves the mixed-precision path.
+#include <algorithm>
+
+#include "fft_device.cuh"
+#include "plan.h"
+
+namespace qe {
+
+static int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+template <typename T>
+__device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) b
+template <typename T>
+__device__ __forceinline__ void cfma_conj(cx<T>& acc, cx<T> a, cx<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+constexpr int IBM = 32, IBN = 32, IBK = 16;
+
+// grid: (ceil(N/32), ceil(M/32), nsplit); block 256 = 16 x 16, 2 x 2 outputs each.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gemm_inner(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
+             int M, int N, int K, int kchunk, cx<T>* __restrict__ part) {
+  __shared__ cx<T> As[IBK][IBM + 1];
+  __shared__ cx<T> Bs[IBK][IBN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int n0 = blockIdx.x * IBN, m0 = blockIdx.y * IBM;
+  const int kb = blockIdx.z * kchunk;
+  const int ke = min(K, kb + kchunk);
+  cx<T> acc[2][2] = {};
+  for (int k0 = kb; k0 < ke; k0 += IBK) {
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+      const int idx = tid + rep * 256;
+      const int r = idx >> 4, kk = idx & 15;
+      const int gk = k0 + kk;
+      double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+      if (gk < ke) {
+        if (m0 + r < M) a = A[(size_t)(m0 + r) * lda + gk];
+        if (n0 + r < N) b = B[(size_t)(n0 + r) * ldb + gk];
+      }
+      As[kk][r] = {T(a.x), T(a.y)};
+      Bs[kk][r] = {T(b.x), T(b.y)};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < IBK; ++kk) {
+      const cx<T> a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      const cx<T> b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      cfma_conj(acc[0][0], a0, b0);
+      cfma_conj(acc[0][1], a0, b1);
+      cfma_conj(acc[1][0], a1, b0);
+      cfma_conj(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  cx<T>* out = part + (size_t)blockIdx.z * M * N;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int m = m0 + ty * 2 + i, n = n0 + tx * 2 + j;
+      if (m < M && n < N) out[(size_t)m * N + n] = acc[i][j];
+    }
+}
+
+template <typename T>
+__global__ void k_reduce_split(const cx<T>* __restrict__ part, int nsplit, int M, int N,
+                               double2* __restrict__ C, int ldc) {
+  const size_t total = (size_t)M * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < nsplit; ++s) {
+      const cx<T> p = part[(size_t)s * total + i];
+      sx += (double)p.x;
+      sy += (double)p.y;
+    }
+    const size_t m = i / N, n = i - m * N;
+    C[m * ldc + n] = make_double2(sx, sy);
+  }
+}
+
+static int inner_split(int M, int N, int K) {
+  const int tiles = ((M + IBM - 1) / IBM) * ((N + IBN - 1) / IBN);
+  int ns = (2 * 152 * 4 + tiles - 1) / tiles;  // aim for ~4 CTAs per SM
+  const int maxs = std::max(1, K / 256);        // at least 256 k per split
+  ns = std::max(1, std::min(ns, maxs));
+  return ns;
+}
+
+size_t gemm_inner_scratch(int M, int N, int K, size_t elem_bytes) {
+  return (size_t)inner_split(M, N, K) * M * N * 2 * elem_bytes;
+}
+
+template <typename T>
+int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
+               int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  const int ns = inner_split(M, N, K);
+  if ((size_t)ns * M * N * sizeof(cx<T>) > part_bytes) {
+    set_error("gemm_inner: scratch too small");
+    return QE_EINVAL;
+  }
+  int kchunk = (K + ns - 1) / ns;
+  kchunk = (kchunk + IBK - 1) / IBK * IBK;
+  const int nsplit = std::max(1, (K + kchunk - 1) / kchunk);
+  dim3 g((N + IBN - 1) / IBN, (M + IBM - 1) / IBM, nsplit);
+  int rc;
+  {
+  ProfScope ps(pf, "k_gemm_inner", st);
+  k_gemm_inner<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+                                      reinterpret_cast<const double2*>(B), ldb, M, N, K, kchunk,
+                                      reinterpret_cast<cx<T>*>(part));
+  rc = check_launch("k_gemm_inner");
+  }
+  if (rc) return rc;
+  ProfScope ps(pf, "k_reduce_split", st);
+  const size_t total = (size_t)M * N;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+  k_reduce_split<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<T>*>(part), nsplit, M, N,
+                                            reinterpret_cast<double2*>(C), ldc);
+  return check_launch("k_reduce_split");
+}
+
+constexpr int OBM = 64, OBN = 32, OBK = 16;
+
+// grid: (ceil(M/64), ceil(N/32)); block 256; thread (tm = tid % 16, tn = tid / 16)
+// owns m = m0 + tm + 16 i (i < 4) and n = n0 + 2 tn + j (j < 2).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
+             int M, int N, int K, double2* __restrict__ C, int ldc, int beta) {
+  __shared__ cx<T> As[OBK][OBM];
+  __shared__ cx<T> Bs[OBK][OBN + 1];
+  const int tid = threadIdx.x;
+  const int tm = tid & 15, tn = tid >> 4;
+  const int m0 = blockIdx.x * OBM, n0 = blockIdx.y * OBN;
+  cx<T> acc[4][2] = {};
+  for (int k0 = 0; k0 < K; k0 += OBK) {
+#pragma unroll
+    for (int rep = 0; rep < 4; ++rep) {
+      const int idx = tid + rep * 256;
+      const int kk = idx >> 6, mm = idx & 63;
+      double2 a = make_double2(0.0, 0.0);
+      if (k0 + kk < K && m0 + mm < M) a = A[(size_t)(k0 + kk) * lda + m0 + mm];
+      As[kk][mm] = {T(a.x), T(a.y)};
+    }
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+      const int idx = tid + rep * 256;
+      const int kk = idx >> 5, nn = idx & 31;
+      double2 b = make_double2(0.0, 0.0);
+      if (k0 + kk < K && n0 + nn < N) b = B[(size_t)(k0 + kk) * ldb + n0 + nn];
+      Bs[kk][nn] = {T(b.x), T(b.y)};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < OBK; ++kk) {
+      cx<T> a[4], b[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + 16 * i];
+      b[0] = Bs[kk][2 * tn];
+      b[1] = Bs[kk][2 * tn + 1];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        cfma(acc[i][0], a[i], b[0]);
+        cfma(acc[i][1], a[i], b[1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int n = n0 + 2 * tn + j;
+    if (n >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + tm + 16 * i;
+      if (m >= M) continue;
+      double2* c = C + (size_t)n * ldc + m;
+      double2 v = make_double2((double)acc[i][j].x, (double)acc[i][j].y);
+      if (beta) { const double2 o = *c; v.x += o.x; v.y += o.y; }
+      *c = v;
+    }
+  }
+}
+
+template <typename T>
+int gemm_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
+               int ldc, int beta, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  ProfScope ps(pf, "k_gemm_outer", st);
+  dim3 g((M + OBM - 1) / OBM, (N + OBN - 1) / OBN);
+  k_gemm_outer<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+                                      reinterpret_cast<const double2*>(B), ldb, M, N, K,
+                                      reinterpret_cast<double2*>(C), ldc, beta);
+  return check_launch("k_gemm_outer");
+}
+
+__global__ void k_dmul(const double* __restrict__ D, const double2* __restrict__ P,
+                       double2* __restrict__ Q, int np, int nb) {
+  const int i = blockIdx.y;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nb) return;
+  double sx = 0.0, sy = 0.0;
+  const double* d = D + (size_t)i * np;
+  for (int j = 0; j < np; ++j) {
+    const double dij = d[j];
+    if (dij != 0.0) {
+      const double2 p = P[(size_t)j * nb + n];
+      sx = fma(dij, p.x, sx);
+      sy = fma(dij, p.y, sy);
+    }
+  }
+  Q[(size_t)i * nb + n] = make_double2(sx, sy);
+}
+
+int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf) {
+  if (np <= 0 || nb <= 0) return QE_OK;
+  ProfScope ps(pf, "k_dmul", st);
+  dim3 g((nb + 127) / 128, np);
+  k_dmul<<<g, 128, 0, st>>>(D, reinterpret_cast<const double2*>(P), reinterpret_cast<double2*>(Q),
+                            np, nb);
+  return check_launch("k_dmul");
+}
+
+template int gemm_inner<double>(const double*, int, const double*, int, int, int, int, double*, int,
+                                void*, size_t, cudaStream_t, Prof*);
+template int gemm_inner<float>(const double*, int, const double*, int, int, int, int, double*, int,
+                               void*, size_t, cudaStream_t, Prof*);
+template int gemm_outer<double>(const double*, int, const double*, int, int, int, int, double*, int,
+                                int, cudaStream_t, Prof*);
+template int gemm_outer<float>(const double*, int, const double*, int, int, int, int, double*, int,
+                               int, cudaStream_t, Prof*);
+
+}  // namespace qe

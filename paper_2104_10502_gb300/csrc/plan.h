@@ -1,0 +1,95 @@
+// Device-resident plan of one (lattice, k, cut-off, grid) and the kernel
+// launchers that use it.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace qe {
+
+struct DevPlan {
+  double lat[9], k[3], ecut;
+  int grid[3];
+  PlanHost h;
+  Radix rad[3];
+  // device arrays (one allocation)
+  void* block = nullptr;
+  double* kin = nullptr;    // [npw]
+  int* st_ptr = nullptr;    // [nst+1]
+  int* st_g = nullptr;      // [npw]
+  int* st_z = nullptr;      // [npw]
+  int* st_of = nullptr;     // [npw]
+  int* st_x = nullptr;      // [nst]
+  int* st_y = nullptr;      // [nst]
+  int* ax = nullptr;        // [nax]
+  int* perm[3] = {nullptr, nullptr, nullptr};   // digit reversal per axis
+  double* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i t / N_axis), interleaved
+  ~DevPlan();
+};
+
+// Optional per-kernel timing: CUDA events recorded on the launching stream
+// around each kernel, folded into per-name totals on read.  Also counts
+// launches (always, even when timing is off).
+struct Prof {
+  bool on = false;
+  long long launches = 0;
+  struct Rec { const char* name; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<std::string> names;
+  std::vector<long long> calls;
+  std::vector<double> ms;
+  void begin(const char* name, cudaStream_t st, cudaEvent_t* ev);
+  void end(const char* name, cudaStream_t st, cudaEvent_t ev);
+  int fold();   // synchronises on the recorded events
+  void reset();
+};
+struct ProfScope {
+  Prof* p; const char* name; cudaStream_t st; cudaEvent_t a = nullptr;
+  ProfScope(Prof* p_, const char* n, cudaStream_t s) : p(p_), name(n), st(s) {
+    if (p) p->begin(name, st, &a);
+  }
+  ~ProfScope() { if (p) p->end(name, st, a); }
+};
+
+// Grow-only device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t nbytes);
+  ~DevBuf();
+};
+
+// ---- launchers (return QE_OK or QE_ECUDA with the error message set) -------
+// Vp[pz][py][px] = V[perm3[pz]][perm2[py]][perm1[px]] converted to T.
+template <typename T>
+int launch_vperm(const DevPlan& P, const double* vloc, T* vp, cudaStream_t st, Prof* pf);
+
+// hpsi[b] = |k+G|^2 psi[b] + V_loc psi[b] for bands b0 .. b0+nbc-1.
+// W: stick workspace of nbc * N3 * nst complex T.
+template <typename T>
+int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, const T* vp,
+                         void* W, int b0, int nbc, cudaStream_t st, Prof* pf);
+
+// Size in bytes of the stick workspace for nbc bands.
+size_t stick_bytes(const DevPlan& P, int nbc, size_t elem_bytes);
+
+// ---- complex GEMMs (all matrices complex, interleaved doubles in memory) -----
+// Split-K inner products: P[m][n] = sum_k conj(A[m][k]) B[n][k]; A [M][lda],
+// B [N][ldb]; result written to C (double complex, [M][ldc]).  `part` is a
+// scratch of gemm_inner_scratch(M, N, K) bytes.
+template <typename T>
+int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+               double* C, int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf);
+size_t gemm_inner_scratch(int M, int N, int K, size_t elem_bytes);
+
+// C[n][m] = beta * C[n][m] + sum_k A[k][m] B[k][n]; A [K][lda], B [K][ldb],
+// C [N][ldc]; beta in {0, 1}.
+template <typename T>
+int gemm_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+               double* C, int ldc, int beta, cudaStream_t st, Prof* pf);
+
+// Q[i][n] = sum_j D[i][j] P[j][n] (D real [np][np], P complex [np][nb]).
+int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf);
+
+}  // namespace qe
