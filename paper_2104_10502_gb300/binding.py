@@ -209,8 +209,8 @@ class Context:
     @staticmethod
     def problem(lat, k, ecut, grid, vloc, beta, dmat, nbnd) -> Problem:
         pr = Problem()
-        pr.lat[:] = list(_f64(lat, 9))
-        pr.k[:] = list(_f64(k, 3))
+        pr.lat[:] = [float(x) for x in _f64(lat, 9).ravel()]
+        pr.k[:] = [float(x) for x in _f64(k, 3).ravel()]
         pr.ecutwfc = float(ecut)
         pr.grid[:] = [int(x) for x in grid]
         pv, mem = _ptr(vloc)

@@ -1,0 +1,508 @@
+// FP64 complex dense linear algebra of the Rayleigh-Ritz step and of the
+// Cholesky orthonormalisation (Sec. 3.2.1 of the paper: LAXlib, parallel dense
+// linear algebra and diagonalisation; Sec. 3.3: generalized eigenproblems).
+//
+// Matrices are row-major complex (interleaved doubles), A[i][j] at i*lda + j.
+//   cholesky      right-looking, one launch per column, optional dropping of
+//                 columns whose remaining pivot is below a threshold (this is
+//                 Gram-Schmidt with dropping, expressed on the Gram matrix);
+//   trsm_lower    L X = B, column-parallel forward substitution;
+//   trsm_upper_h  L^+ X = B, column-parallel back substitution;
+//   heev_lowest   lowest eigenpairs of a Hermitian matrix: Householder
+//                 tridiagonalisation (real off-diagonal), Sturm bisection,
+//                 inverse iteration with re-orthogonalisation inside clusters
+//                 of (nearly) equal eigenvalues, back-transformation.
+// Every kernel is a plain data-parallel launch; there is no inter-CTA waiting.
+#include <algorithm>
+#include <cmath>
+
+#include "dense.h"
+#include "fft_device.cuh"
+
+namespace qe {
+
+using z = cx<double>;
+
+static int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+__device__ __forceinline__ z zconj(z a) { return {a.x, -a.y}; }
+__device__ __forceinline__ double zabs2(z a) { return a.x * a.x + a.y * a.y; }
+
+// Block-wide sum (blockDim.x a multiple of 32, <= 1024).  Every thread gets the result.
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// ---- Cholesky ------------------------------------------------------------------
+// Step j of the right-looking factorisation of the lower triangle.  Column j is
+// left unscaled; its pivot sqrt(d_j) goes to piv[j] (0 when dropped).
+__global__ void k_chol_step(z* A, int n, int lda, int j, double drop2, int allow_drop,
+                            double* piv, int* status) {
+  const double d = A[(size_t)j * lda + j].x;
+  const bool keep = allow_drop ? (d > drop2) : (d > 0.0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    piv[j] = keep ? sqrt(d) : 0.0;
+    if (!keep && !allow_drop) *status = 1 + j;
+  }
+  if (!keep) return;
+  const double inv = 1.0 / d;
+  const int m = n - j - 1;
+  const size_t total = (size_t)m * m;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = j + 1 + (int)(t / m), c = j + 1 + (int)(t % m);
+    if (c > r) continue;
+    const z arj = A[(size_t)r * lda + j], acj = A[(size_t)c * lda + j];
+    // A[r][c] -= a_rj conj(a_cj) / d
+    z& a = A[(size_t)r * lda + c];
+    a.x -= (arj.x * acj.x + arj.y * acj.y) * inv;
+    a.y -= (arj.y * acj.x - arj.x * acj.y) * inv;
+  }
+}
+
+// L[i][j] = A[i][j] / piv[j] for i >= j (0 for dropped columns); upper part zeroed.
+__global__ void k_chol_finish(z* A, int n, int lda, const double* piv) {
+  const size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    z& a = A[(size_t)i * lda + j];
+    if (j > i || piv[j] == 0.0) { a = {0.0, 0.0}; continue; }
+    if (i == j) { a = {piv[j], 0.0}; continue; }
+    const double s = 1.0 / piv[j];
+    a = {a.x * s, a.y * s};
+  }
+}
+
+int cholesky(z* A, int n, int lda, double drop2, bool allow_drop, double* piv, int* status,
+             cudaStream_t st) {
+  for (int j = 0; j < n; ++j) {
+    const size_t m = (size_t)(n - j - 1) * (n - j - 1);
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((m + 255) / 256, 152 * 4));
+    k_chol_step<<<blocks, 256, 0, st>>>(A, n, lda, j, drop2, allow_drop ? 1 : 0, piv, status);
+  }
+  const size_t total = (size_t)n * n;
+  k_chol_finish<<<(int)std::min<size_t>((total + 255) / 256, 152 * 4), 256, 0, st>>>(A, n, lda, piv);
+  return check_launch("cholesky");
+}
+
+// ---- triangular solves ---------------------------------------------------------
+constexpr int TCOLS = 8;
+
+// L X = B, L lower with real positive diagonal; B [n][ldb], columns c0.. of this CTA.
+__global__ void __launch_bounds__(256) k_trsm_lower(const z* L, int n, int ldl, z* B, int ldb,
+                                                    int ncols) {
+  const int c0 = blockIdx.x * TCOLS;
+  const int nc = min(TCOLS, ncols - c0);
+  for (int i = 0; i < n; ++i) {
+    if (threadIdx.x < nc) {
+      const double inv = 1.0 / L[(size_t)i * ldl + i].x;
+      z& b = B[(size_t)i * ldb + c0 + threadIdx.x];
+      b = {b.x * inv, b.y * inv};
+    }
+    __syncthreads();
+    const int rows = n - i - 1;
+    for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
+      const int r = i + 1 + t / nc, c = c0 + t % nc;
+      const z l = L[(size_t)r * ldl + i], x = B[(size_t)i * ldb + c];
+      z& b = B[(size_t)r * ldb + c];
+      b.x -= l.x * x.x - l.y * x.y;
+      b.y -= l.x * x.y + l.y * x.x;
+    }
+    __syncthreads();
+  }
+}
+
+// L^+ X = B (back substitution with the conjugate transpose of lower L).
+__global__ void __launch_bounds__(256) k_trsm_upper_h(const z* L, int n, int ldl, z* B, int ldb,
+                                                      int ncols) {
+  const int c0 = blockIdx.x * TCOLS;
+  const int nc = min(TCOLS, ncols - c0);
+  for (int i = n - 1; i >= 0; --i) {
+    if (threadIdx.x < nc) {
+      const double inv = 1.0 / L[(size_t)i * ldl + i].x;
+      z& b = B[(size_t)i * ldb + c0 + threadIdx.x];
+      b = {b.x * inv, b.y * inv};
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < i * nc; t += blockDim.x) {
+      const int r = t / nc, c = c0 + t % nc;
+      // (L^+)[r][i] = conj(L[i][r])
+      const z l = L[(size_t)i * ldl + r], x = B[(size_t)i * ldb + c];
+      z& b = B[(size_t)r * ldb + c];
+      b.x -= l.x * x.x + l.y * x.y;
+      b.y -= l.x * x.y - l.y * x.x;
+    }
+    __syncthreads();
+  }
+}
+
+int trsm_lower(const z* L, int n, int ldl, z* B, int ldb, int ncols, cudaStream_t st) {
+  if (n <= 0 || ncols <= 0) return QE_OK;
+  k_trsm_lower<<<(ncols + TCOLS - 1) / TCOLS, 256, 0, st>>>(L, n, ldl, B, ldb, ncols);
+  return check_launch("k_trsm_lower");
+}
+
+int trsm_upper_h(const z* L, int n, int ldl, z* B, int ldb, int ncols, cudaStream_t st) {
+  if (n <= 0 || ncols <= 0) return QE_OK;
+  k_trsm_upper_h<<<(ncols + TCOLS - 1) / TCOLS, 256, 0, st>>>(L, n, ldl, B, ldb, ncols);
+  return check_launch("k_trsm_upper_h");
+}
+
+// ---- element-wise helpers ------------------------------------------------------
+// dst[i][j] = conj(src[j][i])
+__global__ void k_conj_transpose(const z* src, int lds, z* dst, int ldd, int rows, int cols) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / cols), j = (int)(t % cols);   // dst row i, col j
+    dst[(size_t)i * ldd + j] = zconj(src[(size_t)j * lds + i]);
+  }
+}
+
+// A = (A + A^+) / 2 in place
+__global__ void k_hermitize(z* A, int n, int lda) {
+  const size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (j < i) continue;
+    const z a = A[(size_t)i * lda + j], b = A[(size_t)j * lda + i];
+    const z m = {0.5 * (a.x + b.x), 0.5 * (a.y - b.y)};
+    A[(size_t)i * lda + j] = m;
+    A[(size_t)j * lda + i] = zconj(m);
+  }
+}
+
+int conj_transpose(const z* src, int lds, z* dst, int ldd, int rows, int cols, cudaStream_t st) {
+  const size_t total = (size_t)rows * cols;
+  if (!total) return QE_OK;
+  k_conj_transpose<<<(int)std::min<size_t>((total + 255) / 256, 152 * 8), 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+  return check_launch("k_conj_transpose");
+}
+
+int hermitize(z* A, int n, int lda, cudaStream_t st) {
+  const size_t total = (size_t)n * n;
+  if (!total) return QE_OK;
+  k_hermitize<<<(int)std::min<size_t>((total + 255) / 256, 152 * 8), 256, 0, st>>>(A, n, lda);
+  return check_launch("k_hermitize");
+}
+
+// ---- Householder tridiagonalisation ------------------------------------------------
+// Reflector of step j from x = A[j+1 .. n-1][j]: H = I - tau v v^+, v_0 = 1, with
+// H^+ x = beta e_1, beta real.  v_1.. are stored in A[j+2 ..][j]; A[j+1][j] = beta.
+__global__ void k_house(z* A, int n, int lda, int j, z* tau, double* e) {
+  __shared__ double sh[33];
+  const int m = n - j - 1;
+  const z alpha = A[(size_t)(j + 1) * lda + j];
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += zabs2(A[(size_t)(j + 1 + i) * lda + j]);
+  const double sigma = block_sum(s, sh);
+  if (sigma == 0.0 && alpha.y == 0.0) {
+    if (threadIdx.x == 0) { tau[j] = {0.0, 0.0}; e[j] = alpha.x; }
+    return;
+  }
+  const double nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sigma);
+  const double beta = alpha.x >= 0.0 ? -nu : nu;
+  // scale = 1 / (alpha - beta)
+  const z am = {alpha.x - beta, alpha.y};
+  const double den = am.x * am.x + am.y * am.y;
+  const z sc = {am.x / den, -am.y / den};
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
+    z& x = A[(size_t)(j + 1 + i) * lda + j];
+    x = cmul(x, sc);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
+    e[j] = beta;
+    A[(size_t)(j + 1) * lda + j] = {beta, 0.0};
+  }
+}
+
+__device__ __forceinline__ z house_v(const z* A, int lda, int j, int r) {
+  // component r (absolute row index, r >= j+1) of the reflector of step j
+  return r == j + 1 ? z{1.0, 0.0} : A[(size_t)r * lda + j];
+}
+
+// p_r = tau * sum_c A[r][c] v_c over the trailing block; one warp per row.
+__global__ void k_tri_matvec(const z* A, int n, int lda, int j, const z* tau, z* p) {
+  const z t = tau[j];
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int r = j + 1 + warp;
+  if (r >= n) return;
+  z s = {0.0, 0.0};
+  if (t.x != 0.0 || t.y != 0.0) {
+    for (int c = j + 1 + lane; c < n; c += 32) s = cadd(s, cmul(A[(size_t)r * lda + c], house_v(A, lda, j, c)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  if (lane == 0) p[r] = cmul(t, s);
+}
+
+// w = p - (1/2) conj(tau) (v^+ p) v;  A -= v w^+ + w v^+ on the trailing block.
+__global__ void k_tri_update(z* A, int n, int lda, int j, const z* tau, const z* p) {
+  __shared__ double sh[33];
+  const z t = tau[j];
+  if (t.x == 0.0 && t.y == 0.0) return;
+  double sr = 0.0, si = 0.0;
+  for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
+    const z v = house_v(A, lda, j, r), pr = p[r];
+    sr += v.x * pr.x + v.y * pr.y;    // conj(v) p
+    si += v.x * pr.y - v.y * pr.x;
+  }
+  const double vpr = block_sum(sr, sh);
+  const double vpi = block_sum(si, sh);
+  // coef = 0.5 conj(tau) (v^+ p)
+  const z coef = {0.5 * (t.x * vpr + t.y * vpi), 0.5 * (t.x * vpi - t.y * vpr)};
+  const int m = n - j - 1;
+  const size_t total = (size_t)m * m;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int r = j + 1 + (int)(q / m), c = j + 1 + (int)(q % m);
+    const z vr = house_v(A, lda, j, r), vc = house_v(A, lda, j, c);
+    const z wr = csub(p[r], cmul(coef, vr)), wc = csub(p[c], cmul(coef, vc));
+    // A[r][c] -= vr conj(wc) + wr conj(vc)
+    const z d = cadd(cmul(vr, zconj(wc)), cmul(wr, zconj(vc)));
+    z& a = A[(size_t)r * lda + c];
+    a = csub(a, d);
+  }
+}
+
+__global__ void k_tri_diag(const z* A, int n, int lda, double* d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    d[i] = A[(size_t)i * lda + i].x;
+}
+
+// ---- tridiagonal eigenvalues: Sturm bisection, one thread per eigenvalue --------
+__device__ int sturm_count(const double* d, const double* e, int n, double x, double tiny) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (q == 0.0) q = -tiny;
+  if (q < 0.0) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (q == 0.0) q = -tiny;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_bisect(const double* d, const double* e, int n, int nev, double* w) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nev) return;
+  double lo = d[0], hi = d[0], nrm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+  }
+  nrm = fmax(fabs(lo), fabs(hi));
+  const double tiny = 1e-300 + 1e-30 * nrm;
+  lo -= 1e-14 * nrm + 1e-300;
+  hi += 1e-14 * nrm + 1e-300;
+  for (int it = 0; it < 256; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
+    if (sturm_count(d, e, n, mid, tiny) > k) hi = mid;
+    else lo = mid;
+  }
+  w[k] = 0.5 * (lo + hi);
+}
+
+// ---- tridiagonal eigenvectors: inverse iteration --------------------------------------
+// splitmix64 (Steele, Lea, Flood 2014) for deterministic start vectors
+__device__ __forceinline__ double start_component(unsigned long long k, unsigned long long i) {
+  unsigned long long x = k * 0x9E3779B97F4A7C15ull + i * 0xD1B54A32D192ED03ull + 0x632BE59BD9B4E019ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return ((double)(x >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+// One CTA per cluster of consecutive eigenvalues closer than ctol; the CTA whose
+// index starts a cluster handles all of it, the others return.  Vectors are rows
+// Y[k][0..n).  Shared memory: 6 arrays of n doubles (+ ints) for the factorisation.
+__global__ void __launch_bounds__(256) k_inviter(const double* d, const double* e, int n, int nev,
+                                                 const double* w, double ctol_rel, double* Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* u0 = reinterpret_cast<double*>(smem_raw);
+  double* u1 = u0 + n;
+  double* u2 = u1 + n;
+  double* ml = u2 + n;
+  double* y = ml + n;
+  int* sw = reinterpret_cast<int*>(y + n);
+  __shared__ double sh[33];
+  const int k0 = blockIdx.x;
+  if (k0 >= nev) return;
+  double nrm = 0.0;
+  for (int i = 0; i < n; ++i)
+    nrm = fmax(nrm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0));
+  const double ctol = ctol_rel * fmax(nrm, 1e-300);
+  if (k0 > 0 && w[k0] - w[k0 - 1] <= ctol) return;   // not a cluster start
+  int k1 = k0 + 1;
+  while (k1 < nev && w[k1] - w[k1 - 1] <= ctol) ++k1;
+  const double tiny = fmax(2.2e-16 * nrm, 1e-300);
+  for (int k = k0; k < k1; ++k) {
+    const double lam = w[k];
+    // LU with partial pivoting of T - lam I (thread 0)
+    if (threadIdx.x == 0) {
+      double c0 = d[0] - lam, c1 = n > 1 ? e[0] : 0.0, c2 = 0.0;
+      for (int i = 0; i < n - 1; ++i) {
+        double n0 = e[i], n1 = d[i + 1] - lam, n2 = (i + 2 < n) ? e[i + 1] : 0.0;
+        int s = 0;
+        if (fabs(n0) > fabs(c0)) {
+          double t;
+          t = c0; c0 = n0; n0 = t;
+          t = c1; c1 = n1; n1 = t;
+          t = c2; c2 = n2; n2 = t;
+          s = 1;
+        }
+        if (fabs(c0) < tiny) c0 = c0 < 0.0 ? -tiny : tiny;
+        const double mlt = n0 / c0;
+        u0[i] = c0; u1[i] = c1; u2[i] = c2; ml[i] = mlt; sw[i] = s;
+        c0 = n1 - mlt * c1;
+        c1 = n2 - mlt * c2;
+        c2 = 0.0;
+      }
+      if (fabs(c0) < tiny) c0 = c0 < 0.0 ? -tiny : tiny;
+      u0[n - 1] = c0; u1[n - 1] = 0.0; u2[n - 1] = 0.0;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = start_component(k, i);
+    __syncthreads();
+    for (int it = 0; it < 4; ++it) {
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < n - 1; ++i) {
+          if (sw[i]) { const double t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
+          y[i + 1] -= ml[i] * y[i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+          double s = y[i];
+          if (i + 1 < n) s -= u1[i] * y[i + 1];
+          if (i + 2 < n) s -= u2[i] * y[i + 2];
+          y[i] = s / u0[i];
+        }
+      }
+      __syncthreads();
+      // scale down first (the solve grows the vector by up to 1/tiny)
+      double mx = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(y[i]));
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double m2 = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m2 = fmax(m2, sh[q]);
+        sh[32] = m2 > 0.0 ? m2 : 1.0;
+      }
+      __syncthreads();
+      const double inv_mx = 1.0 / sh[32];
+      for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] *= inv_mx;
+      __syncthreads();
+      // orthogonalise against the finished vectors of this cluster (twice)
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int q = k0; q < k; ++q) {
+          const double* yq = Y + (size_t)q * n;
+          double s = 0.0;
+          for (int i = threadIdx.x; i < n; i += blockDim.x) s += yq[i] * y[i];
+          s = block_sum(s, sh);
+          for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] -= s * yq[i];
+          __syncthreads();
+        }
+      }
+      double s = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s += y[i] * y[i];
+      s = block_sum(s, sh);
+      const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] *= inv;
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Y[(size_t)k * n + i] = y[i];
+    __syncthreads();
+  }
+}
+
+// X[:, k] = H_0 H_1 ... H_{n-2} y_k, one CTA per eigenvector; X [n][ldx].
+__global__ void __launch_bounds__(256) k_backtransform(const z* A, int n, int lda, const z* tau,
+                                                       const double* Y, z* X, int ldx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  z* x = reinterpret_cast<z*>(smem_raw);
+  __shared__ double sh[33];
+  const int k = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = {Y[(size_t)k * n + i], 0.0};
+  __syncthreads();
+  for (int j = n - 2; j >= 0; --j) {
+    const z t = tau[j];
+    if (t.x == 0.0 && t.y == 0.0) continue;
+    double sr = 0.0, si = 0.0;
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
+      const z v = house_v(A, lda, j, r), xr = x[r];
+      sr += v.x * xr.x + v.y * xr.y;
+      si += v.x * xr.y - v.y * xr.x;
+    }
+    const double a = block_sum(sr, sh);
+    const double b = block_sum(si, sh);
+    const z f = cmul(t, z{a, b});     // tau (v^+ x)
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) x[r] = csub(x[r], cmul(f, house_v(A, lda, j, r)));
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)i * ldx + k] = x[i];
+}
+
+int heev_lowest(z* A, int n, int lda, int nev, double* w, z* X, int ldx, DenseWork& wk,
+                cudaStream_t st) {
+  if (n <= 0 || nev <= 0) return QE_OK;
+  if (nev > n || n > kMaxDense) {
+    set_error("heev_lowest: n = %d, nev = %d (max n %d)", n, nev, kMaxDense);
+    return QE_EINVAL;
+  }
+  for (int j = 0; j < n - 1; ++j) {
+    k_house<<<1, 256, 0, st>>>(A, n, lda, j, wk.tau, wk.e);
+    const int m = n - j - 1;
+    k_tri_matvec<<<(m * 32 + 255) / 256, 256, 0, st>>>(A, n, lda, j, wk.tau, wk.p);
+    const size_t mm = (size_t)m * m;
+    k_tri_update<<<(int)std::max<size_t>(1, std::min<size_t>((mm + 255) / 256, 152 * 4)), 256, 0, st>>>(
+        A, n, lda, j, wk.tau, wk.p);
+  }
+  k_tri_diag<<<(n + 255) / 256, 256, 0, st>>>(A, n, lda, wk.d);
+  int rc = check_launch("tridiagonalisation");
+  if (rc) return rc;
+  k_bisect<<<(nev + 127) / 128, 128, 0, st>>>(wk.d, wk.e, n, nev, w);
+  rc = check_launch("k_bisect");
+  if (rc) return rc;
+  const size_t ism = (size_t)n * (5 * sizeof(double) + sizeof(int));
+  cudaFuncSetAttribute(k_inviter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+  // eigenvalues within 1e-10 of each other (relative to the spread of T) share a cluster
+  k_inviter<<<nev, 256, ism, st>>>(wk.d, wk.e, n, nev, w, wk.ctol_rel, wk.y);
+  rc = check_launch("k_inviter");
+  if (rc) return rc;
+  const size_t bsm = (size_t)n * sizeof(z);
+  k_backtransform<<<nev, 256, bsm, st>>>(A, n, lda, wk.tau, wk.y, X, ldx);
+  return check_launch("k_backtransform");
+}
+
+}  // namespace qe

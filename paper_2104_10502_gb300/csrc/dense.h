@@ -1,0 +1,40 @@
+// FP64 dense linear algebra on the device (see dense.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft_device.cuh"
+
+namespace qe {
+
+constexpr int kMaxDense = 4096;   // largest reduced problem handled
+
+struct DenseWork {
+  cx<double>* tau = nullptr;   // [n] Householder scalars
+  cx<double>* p = nullptr;     // [n] tridiagonalisation work vector
+  double* d = nullptr;         // [n] diagonal of T
+  double* e = nullptr;         // [n] off-diagonal of T
+  double* y = nullptr;         // [nev][n] eigenvectors of T
+  double* piv = nullptr;       // [n] Cholesky pivots
+  int* status = nullptr;       // device status word (0 = ok)
+  double ctol_rel = 1e-10;     // cluster width relative to the spread of T
+};
+
+// Lower Cholesky in place (upper part zeroed).  allow_drop: a column whose
+// remaining pivot^2 is <= drop2 is dropped (zero column, piv = 0); otherwise a
+// non-positive pivot sets *status = 1 + column.
+int cholesky(cx<double>* A, int n, int lda, double drop2, bool allow_drop, double* piv,
+             int* status, cudaStream_t st);
+int trsm_lower(const cx<double>* L, int n, int ldl, cx<double>* B, int ldb, int ncols,
+               cudaStream_t st);
+int trsm_upper_h(const cx<double>* L, int n, int ldl, cx<double>* B, int ldb, int ncols,
+                 cudaStream_t st);
+int conj_transpose(const cx<double>* src, int lds, cx<double>* dst, int ldd, int rows, int cols,
+                   cudaStream_t st);
+int hermitize(cx<double>* A, int n, int lda, cudaStream_t st);
+// Lowest nev eigenpairs of Hermitian A (destroyed): w[nev] ascending, X [n][ldx]
+// with eigenvector k in column k.
+int heev_lowest(cx<double>* A, int n, int lda, int nev, double* w, cx<double>* X, int ldx,
+                DenseWork& wk, cudaStream_t st);
+
+}  // namespace qe
