@@ -137,6 +137,32 @@ int qe_beta_gaussian(qe_ctx* ctx, const double lat[9], const double k[3],
 int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
             const double* psi, double* hpsi, void* stream);
 
+/* H|psi> exactly as qe_hpsi, for callers that cannot allocate device memory
+ * (no counterpart in the paper).  Such callers include code running inside a
+ * memory pool or arena that another component owns, under an allocator that
+ * must see every allocation, or at points where a cudaMalloc would synchronise
+ * the device or fail because other work holds the free memory.  qe_hpsi takes
+ * its workspace from the context's buffers, which allocate on first use; this
+ * entry point takes all of it from one fixed 64 MiB device array inside the
+ * library (present on every GPU that loads the library, until process exit)
+ * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - No context: it runs on the calling thread's current CUDA device, which
+ *    must hold every array; prob->mem must be QE_DEVICE (else QE_EINVAL).
+ *  - The caller passes inputs (psi, vloc_r, beta, dmat) and the output hpsi.
+ *  - Size limit: the plan of the sphere, the permuted potential, the
+ *    projections, one band's stick buffer and one split of the projector
+ *    product must fit in 64 MiB; larger problems return QE_EINVAL with the
+ *    needed size in qe_last_error() (use qe_hpsi for those).
+ *  - The first call on each device looks up the array's device address; make
+ *    that first call before any stream capture.
+ *  - Every call uses the same array and leaves its contents behind; the
+ *    kernels overwrite all of it that they read.  Calls whose work overlaps on
+ *    the GPU (different streams, or different host threads) race on the
+ *    array: order them on one stream.
+ * Work is queued on `stream`; the call returns without waiting for it. */
+int qe_hpsi_noalloc(const qe_problem* prob, int precision, const double* psi,
+                    double* hpsi, void* stream);
+
 /* Block Davidson (Sec. 3.3, iterative solution of the Kohn-Sham Hamiltonian;
  * Sec. 3.2.1, KS_Solvers and the dense eigensolver of LAXlib) for the nbnd
  * lowest eigenpairs.  psi_inout: start bands in, Ritz vectors out

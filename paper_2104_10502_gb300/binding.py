@@ -24,7 +24,7 @@ QE_HOST, QE_DEVICE = 0, 1
 
 SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
            "qe_vloc_gaussian", "qe_beta_gaussian", "qe_hpsi", "qe_davidson", "qe_profile",
-           "qe_profile_read"]
+           "qe_profile_read", "qe_hpsi_noalloc"]
 
 
 class QEError(RuntimeError):
@@ -66,6 +66,7 @@ _lib.qe_profile.argtypes = [_P, ctypes.c_int]
 _lib.qe_profile_read.argtypes = [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_longlong), _D,
                                  ctypes.POINTER(ctypes.c_longlong)]
+_lib.qe_hpsi_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_hpsi.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_davidson.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
                              ctypes.c_int, ctypes.c_int, _P, _P, _P, _I, _P]
@@ -133,6 +134,18 @@ def gsphere(lat, k, ecut: float, grid=None):
     _check(_lib.qe_gsphere(_dptr(lat), _dptr(k), float(ecut), gp, ctypes.byref(npw),
                            miller.ctypes.data_as(_I), _dptr(kin)))
     return miller, kin
+
+
+def hpsi_noalloc(prob: "Problem", psi, hpsi, precision=QE_FP64, stream=None):
+    """H|psi> through the entry point that allocates no device memory (its
+    workspace is a fixed 64 MiB array inside the library).  All arrays must be
+    CUDA tensors on the current device."""
+    pp, mp = _ptr(psi)
+    ph, mh = _ptr(hpsi)
+    if prob.nbnd > 0 and (mp != QE_DEVICE or mh != QE_DEVICE):
+        raise ValueError("qe_hpsi_noalloc takes device arrays only")
+    _check(_lib.qe_hpsi_noalloc(ctypes.byref(prob), int(precision), pp, ph, _stream(stream, psi)))
+    return hpsi
 
 
 class Context:

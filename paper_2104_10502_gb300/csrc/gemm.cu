@@ -152,6 +152,44 @@ int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N,
   return check_launch("k_reduce_split");
 }
 
+// As gemm_inner, but with as many K splits as fit in `part_bytes` (at least one),
+// for callers whose scratch is a fixed-size region.
+template <typename T>
+int gemm_inner_bounded(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+                       double* C, int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  const size_t one = (size_t)M * N * sizeof(cx<T>);
+  if (one > part_bytes) {
+    set_error("gemm_inner_bounded: scratch holds no split");
+    return QE_EINVAL;
+  }
+  const int ns = std::max(1, std::min(inner_split(M, N, K), (int)(part_bytes / one)));
+  int kchunk = (K + ns - 1) / ns;
+  kchunk = (kchunk + IBK - 1) / IBK * IBK;
+  const int nsplit = std::max(1, (K + kchunk - 1) / kchunk);
+  dim3 g((N + IBN - 1) / IBN, (M + IBM - 1) / IBM, nsplit);
+  int rc;
+  {
+  ProfScope ps(pf, "k_gemm_inner", st);
+  k_gemm_inner<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+                                      reinterpret_cast<const double2*>(B), ldb, M, N, K, kchunk,
+                                      reinterpret_cast<cx<T>*>(part));
+  rc = check_launch("k_gemm_inner");
+  }
+  if (rc) return rc;
+  ProfScope ps(pf, "k_reduce_split", st);
+  const size_t total = (size_t)M * N;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+  k_reduce_split<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<T>*>(part), nsplit, M, N,
+                                            reinterpret_cast<double2*>(C), ldc);
+  return check_launch("k_reduce_split");
+}
+
+template int gemm_inner_bounded<double>(const double*, int, const double*, int, int, int, int,
+                                        double*, int, void*, size_t, cudaStream_t, Prof*);
+template int gemm_inner_bounded<float>(const double*, int, const double*, int, int, int, int,
+                                       double*, int, void*, size_t, cudaStream_t, Prof*);
+
 constexpr int OBM = 64, OBN = 32, OBK = 16;
 
 // grid: (ceil(M/64), ceil(N/32)); block 256; thread (tm = tid % 16, tn = tid / 16)

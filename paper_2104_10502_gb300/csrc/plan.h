@@ -82,6 +82,10 @@ template <typename T>
 int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
                double* C, int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf);
 size_t gemm_inner_scratch(int M, int N, int K, size_t elem_bytes);
+// As gemm_inner, with as many K splits as fit in part_bytes (>= 1).
+template <typename T>
+int gemm_inner_bounded(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+                       double* C, int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf);
 
 // C[n][m] = beta * C[n][m] + sum_k A[k][m] B[k][n]; A [K][lda], B [K][ldb],
 // C [N][ldc]; beta in {0, 1}.

@@ -1,0 +1,79 @@
+"""The allocation-free H|psi> entry point (qe_hpsi_noalloc) against qe_hpsi.
+
+qe_hpsi_noalloc serves callers that cannot allocate device memory: it takes
+its workspace from a fixed array inside the library instead of the context's
+buffers.  Called twice in a row through the C ABI (two different cells, so the
+second call re-plans into the array the first one left behind), each result
+must equal the regular entry point's within the FP64 parity tolerance of the
+other tests (per band 1e-12 relative).  A problem too large for the array must
+be refused with QE_EINVAL before any work is queued.
+
+This file is collected last so that a failure here cannot stop the others.
+"""
+import numpy as np
+import pytest
+
+import qeinputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _setup(q, ctx, name, nb, seed):
+    c = qeinputs.config(name)
+    lat, k, ecut, grid = c["lat"], c["k"], c["ecut"], c["grid"]
+    _, kin = q.gsphere(lat, k, ecut, grid)
+    npw = len(kin)
+    dev = torch.device("cuda", 0)
+    v = torch.empty((grid[2], grid[1], grid[0]), dtype=torch.float64, device=dev)
+    ctx.vloc_gaussian(lat, grid, c["tau"], v)
+    nproj = 4 * len(c["widths"]) * len(c["tau"])
+    beta = torch.empty((nproj, npw, 2), dtype=torch.float64, device=dev)
+    ctx.beta_gaussian(lat, k, ecut, c["tau"], c["widths"], beta)
+    d = torch.from_numpy(qeinputs.d_matrix(len(c["tau"]), len(c["widths"]))).to(dev)
+    psi = qeinputs.random_vectors(nb, npw, seed=seed)
+    pt = torch.from_numpy(psi.view(np.float64).reshape(nb, npw, 2).copy()).to(dev)
+    prob = ctx.problem(lat, k, ecut, grid, v, beta, d, nb)
+    return prob, pt, (v, beta, d)
+
+
+def _rel(a, b):
+    a = a[..., 0] + 1j * a[..., 1]
+    b = b[..., 0] + 1j * b[..., 1]
+    return float((np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)).max())
+
+
+def test_noalloc_matches_hpsi_on_two_calls_in_a_row():
+    import paper_2104_10502_gb300 as q
+    torch.cuda.set_device(0)
+    with q.Context(0) as ctx:
+        cases = [_setup(q, ctx, "C0", 8, 21), _setup(q, ctx, "SMALL", 5, 22)]
+        refs = []
+        for prob, pt, keep in cases:
+            ht = torch.empty_like(pt)
+            ctx.hpsi(prob, pt, ht, q.QE_FP64)
+            refs.append(ht)
+        outs = []
+        for prob, pt, keep in cases:           # two calls in a row
+            out = torch.full_like(pt, float("nan"))
+            q.hpsi_noalloc(prob, pt, out, q.QE_FP64)
+            outs.append(out)
+        torch.cuda.synchronize()
+        for out, ref in zip(outs, refs):
+            assert _rel(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-12
+
+
+def test_noalloc_refuses_problems_beyond_its_array():
+    import paper_2104_10502_gb300 as q
+    torch.cuda.set_device(0)
+    lat = qeinputs.cubic(40.0)
+    grid = (192, 192, 192)                    # the permuted potential alone is 56 MiB
+    _, kin = q.gsphere(lat, np.zeros(3), 40.0, grid)
+    v = torch.zeros((192, 192, 192), dtype=torch.float64, device="cuda")
+    with q.Context(0) as ctx:
+        prob = ctx.problem(lat, np.zeros(3), 40.0, grid, v, None, None, 1)
+    pt = torch.zeros((1, len(kin), 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(q.QEError) as e:
+        q.hpsi_noalloc(prob, pt, torch.empty_like(pt), q.QE_FP64)
+    assert e.value.code == q.QE_EINVAL
+    assert "64" in str(e.value) or "holds" in str(e.value)
