@@ -1,10 +1,461 @@
-// Block Davidson on the device (Sec. 3.3 of the paper: Davidson iterative
-// diagonalisation of the Kohn-Sham Hamiltonian).
+// Block Davidson on the device (Sec. 3.3 of the paper: iterative solution of
+// the Kohn-Sham Hamiltonian with the Davidson method; Sec. 3.2.1: KS_Solvers,
+// which call the Hamiltonian builder as an external routine, and LAXlib's dense
+// generalized eigensolver).
+//
+// The host drives the iteration; every step runs in device kernels:
+//   H products            hpsi_core (FFT local + kinetic, projector GEMMs)
+//   reduced matrices      gemm_inner, updated column block by column block
+//   Rayleigh-Ritz (FP64)  Cholesky of S_r, L^-1 H_r L^-+, tridiagonal eigensolver,
+//                         back substitution (dense.cu)
+//   Ritz vectors          gemm_outer (Psi = V X, H Psi = (HV) X)
+//   residuals (FP64)      k_resid: r_n = H psi_n - e_n psi_n and ||r_n||
+//   corrections           k_precond: r_n / sqrt((h_G - e_n)^2 + pmin^2), normalised
+//   orthonormalisation    two passes of projection against V, each followed by
+//                         a Cholesky orthonormalisation of the block that drops
+//                         corrections left without a new direction
+// Per iteration the host reads nb eigenvalues, nb residual norms, the Cholesky
+// status word and the kept-correction flags (a few KB).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "ctx.h"
+#include "dense.h"
+#include "fft_device.cuh"
+
+namespace qe {
+
+using z = cx<double>;
+
+static int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+#define DV_TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+#define DV_CU(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_error("%s: %s", #x, cudaGetErrorString(e_)); return QE_ECUDA; } } while (0)
+
+__device__ double dv_block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// r_b = hpsi_b - e_b psi_b ; rn[b] = ||r_b||_2 (FP64, fixed reduction order)
+__global__ void __launch_bounds__(256) k_resid(const z* psi, const z* hpsi, const double* e, int npw,
+                                               z* r, double* rn) {
+  __shared__ double sh[33];
+  const int b = blockIdx.x;
+  const double eb = e[b];
+  const z* p = psi + (size_t)b * npw;
+  const z* hp = hpsi + (size_t)b * npw;
+  z* rr = r + (size_t)b * npw;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const z a = hp[g], c = p[g];
+    const z v = {a.x - eb * c.x, a.y - eb * c.y};
+    rr[g] = v;
+    s += v.x * v.x + v.y * v.y;
+  }
+  s = dv_block_sum(s, sh);
+  if (threadIdx.x == 0) rn[b] = sqrt(s);
+}
+
+// d_j = r_{idx[j]} / sqrt((h_G - e)^2 + pmin^2), normalised to unit norm
+__global__ void __launch_bounds__(256) k_precond(const z* r, const int* idx, const double* e,
+                                                 const double* hd, int npw, double pmin2, z* d) {
+  __shared__ double sh[33];
+  const int j = blockIdx.x;
+  const int b = idx[j];
+  const double eb = e[b];
+  const z* rr = r + (size_t)b * npw;
+  z* dd = d + (size_t)j * npw;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double x = hd[g] - eb;
+    const double inv = 1.0 / sqrt(x * x + pmin2);
+    const z v = {rr[g].x * inv, rr[g].y * inv};
+    dd[g] = v;
+    s += v.x * v.x + v.y * v.y;
+  }
+  s = dv_block_sum(s, sh);
+  const double sc = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    dd[g].x *= sc;
+    dd[g].y *= sc;
+  }
+}
+
+// h_G = |k+G|^2 + vmean + sum_i D_ii |B_i(G)|^2
+__global__ void k_hdiag(const double* kin, const double* vmean, const z* beta, const double* D,
+                        int np, int npw, double* hd) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= npw) return;
+  double h = kin[g] + *vmean;
+  for (int i = 0; i < np; ++i) {
+    const double dii = D[(size_t)i * np + i];
+    if (dii != 0.0) {
+      const z b = beta[(size_t)i * npw + g];
+      h += dii * (b.x * b.x + b.y * b.y);
+    }
+  }
+  hd[g] = h;
+}
+
+__global__ void __launch_bounds__(1024) k_mean(const double* v, size_t n, double* out) {
+  __shared__ double sh[33];
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+  s = dv_block_sum(s, sh);
+  if (threadIdx.x == 0) *out = s / (double)n;
+}
+
+// H[n0 + j][i] = conj(H[i][n0 + j]) for i < n0 <= n0 + j < n1
+__global__ void k_mirror(z* H, int ld, int n0, int n1) {
+  const int m = n1 - n0;
+  const size_t total = (size_t)m * n0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int j = n0 + (int)(t / n0), i = (int)(t % n0);
+    const z a = H[(size_t)i * ld + j];
+    H[(size_t)j * ld + i] = {a.x, -a.y};
+  }
+}
+
+// dst[a][b] = src[keep[a]][keep[b]]
+__global__ void k_gather_sub(const z* src, int lds, const int* keep, int nk, z* dst, int ldd) {
+  const size_t total = (size_t)nk * nk;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / nk), b = (int)(t % nk);
+    dst[(size_t)a * ldd + b] = src[(size_t)keep[a] * lds + keep[b]];
+  }
+}
+
+// identity nk x nk (ld ldd)
+__global__ void k_identity(z* dst, int nk, int ldd) {
+  const size_t total = (size_t)nk * nk;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / nk), b = (int)(t % nk);
+    dst[(size_t)a * ldd + b] = {a == b ? 1.0 : 0.0, 0.0};
+  }
+}
+
+// full[keep[a]][c] = M[a][c]; full is [nrow][nk], zeroed beforehand
+__global__ void k_place_rows(const z* M, int ldm, const int* keep, int nk, z* full) {
+  const size_t total = (size_t)nk * nk;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(t / nk), c = (int)(t % nk);
+    full[(size_t)keep[a] * nk + c] = M[(size_t)a * ldm + c];
+  }
+}
+
+static int grid_for(size_t total) {
+  return (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 152 * 8));
+}
+
+struct DvState {
+  int npw = 0, nb = 0, max_dim = 0, np = 0;
+  z *V = nullptr, *HV = nullptr, *Psi = nullptr, *HPsi = nullptr, *R = nullptr, *D = nullptr,
+    *D2 = nullptr;
+  z *Hr = nullptr, *Sr = nullptr, *Lw = nullptr, *Zw = nullptr, *Aw = nullptr, *X = nullptr,
+    *C = nullptr, *G = nullptr, *Mf = nullptr, *Mk = nullptr, *Lk = nullptr;
+  double *e = nullptr, *rn = nullptr, *hd = nullptr, *vmean = nullptr;
+  int* idx = nullptr;
+  DenseWork dw;
+  void* part = nullptr;
+  size_t part_bytes = 0;
+};
+
+static int dv_alloc(qe_ctx* ctx, DvState& S) {
+  const size_t npw = S.npw, nb = S.nb, md = S.max_dim;
+  const size_t zb = sizeof(z);
+  // big: V, HV [md][npw]; Psi, HPsi, R, D, D2 [nb][npw]
+  const size_t big = (2 * md + 5 * nb) * npw * zb;
+  // small complex: Hr, Sr, Lw, Zw, Aw [md][md]; X [md][nb]; C [md][nb]; G, Mf, Mk, Lk [nb][nb]
+  const size_t smallz = (5 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
+  // doubles: e, rn [nb]; hd [npw]; vmean; dense work: d, e, piv [md], y [nb][md]
+  const size_t dbl = (2 * nb + npw + 1 + 3 * md + nb * md) * sizeof(double);
+  // dense work complex: tau, p [md]
+  const size_t dwz = 2 * md * zb;
+  const size_t ints = (nb + 16) * sizeof(int);
+  const size_t total = big + smallz + dbl + dwz + ints + 48 * 256;   // + alignment of 31 pieces
+  DV_TRY(ctx->dv_basis.ensure(total));
+  char* p = (char*)ctx->dv_basis.p;
+  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
+  S.V = (z*)take(md * npw * zb);
+  S.HV = (z*)take(md * npw * zb);
+  S.Psi = (z*)take(nb * npw * zb);
+  S.HPsi = (z*)take(nb * npw * zb);
+  S.R = (z*)take(nb * npw * zb);
+  S.D = (z*)take(nb * npw * zb);
+  S.D2 = (z*)take(nb * npw * zb);
+  S.Hr = (z*)take(md * md * zb);
+  S.Sr = (z*)take(md * md * zb);
+  S.Lw = (z*)take(md * md * zb);
+  S.Zw = (z*)take(md * md * zb);
+  S.Aw = (z*)take(md * md * zb);
+  S.X = (z*)take(md * nb * zb);
+  S.C = (z*)take(md * nb * zb);
+  S.G = (z*)take(nb * nb * zb);
+  S.Mf = (z*)take(nb * nb * zb);
+  S.Mk = (z*)take(nb * nb * zb);
+  S.Lk = (z*)take(nb * nb * zb);
+  S.e = (double*)take(nb * sizeof(double));
+  S.rn = (double*)take(nb * sizeof(double));
+  S.hd = (double*)take(npw * sizeof(double));
+  S.vmean = (double*)take(sizeof(double));
+  S.dw.d = (double*)take(md * sizeof(double));
+  S.dw.e = (double*)take(md * sizeof(double));
+  S.dw.piv = (double*)take(md * sizeof(double));
+  S.dw.y = (double*)take(nb * md * sizeof(double));
+  S.dw.tau = (z*)take(md * zb);
+  S.dw.p = (z*)take(md * zb);
+  S.idx = (int*)take(nb * sizeof(int));
+  S.dw.status = (int*)take(16 * sizeof(int));
+  if ((size_t)(p - (char*)ctx->dv_basis.p) > ctx->dv_basis.bytes) {
+    set_error("davidson: workspace layout overflow");
+    return QE_EINVAL;
+  }
+  // split-K partials: at most (splits for ~4 CTAs/SM + tiles) 32x32 tiles of FP64 complex
+  const size_t tiles = (size_t)((md + 31) / 32) * ((md + 31) / 32);
+  const size_t sb = (2 * 152 * 4 + tiles + 1) * 32 * 32 * zb;
+  DV_TRY(ctx->dv_red.ensure(sb));
+  S.part = ctx->dv_red.p;
+  S.part_bytes = sb;
+  return QE_OK;
+}
+
+template <typename T>
+static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
+                cudaStream_t st, Prof* pf) {
+  return gemm_inner<T>((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C,
+                       ldc, S.part, S.part_bytes, st, pf);
+}
+
+// Reduced matrices: columns [n0, n1) for rows [0, n1), then the mirrored rows.
+template <typename T>
+static int update_reduced(const DvState& S, int n0, int n1, cudaStream_t st, Prof* pf) {
+  const int md = S.max_dim;
+  DV_TRY(gram<T>(S, S.V, n1, S.HV + (size_t)n0 * S.npw, n1 - n0, S.Hr + n0, md, st, pf));
+  DV_TRY(gram<T>(S, S.V, n1, S.V + (size_t)n0 * S.npw, n1 - n0, S.Sr + n0, md, st, pf));
+  if (n0 > 0) {
+    const size_t t = (size_t)(n1 - n0) * n0;
+    k_mirror<<<grid_for(t), 256, 0, st>>>(S.Hr, md, n0, n1);
+    k_mirror<<<grid_for(t), 256, 0, st>>>(S.Sr, md, n0, n1);
+  }
+  return check_launch("k_mirror");
+}
+
+// Rayleigh-Ritz on span(V[0:n]): eigenvalues e[0:nb], X [n][nb] (ld nb).
+static int rayleigh_ritz(DvState& S, int n, cudaStream_t st) {
+  const int md = S.max_dim, nb = S.nb;
+  const size_t zb = sizeof(z);
+  DV_CU(cudaMemcpy2DAsync(S.Lw, n * zb, S.Sr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
+  DV_CU(cudaMemcpy2DAsync(S.Zw, n * zb, S.Hr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
+  DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, st));
+  DV_TRY(trsm_lower(S.Lw, n, n, S.Zw, n, n, st));                 // Z = L^-1 H
+  DV_TRY(conj_transpose(S.Zw, n, S.Aw, n, n, n, st));             // Z^+ = H L^-+
+  DV_TRY(trsm_lower(S.Lw, n, n, S.Aw, n, n, st));                 // A = L^-1 H L^-+
+  DV_TRY(hermitize(S.Aw, n, n, st));
+  DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st));
+  DV_TRY(trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st));              // X = L^-+ Y
+  return QE_OK;
+}
+
+// Orthonormalise the nd rows of `in` against V[0:n] and among themselves; the
+// kept vectors are written to `out` (rows).  Returns the number kept in *nk.
+template <typename T>
+static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out, double drop,
+                          cudaStream_t st, Prof* pf) {
+  const int npw = S.npw;
+  z* cur = in;
+  int ncur = nd;
+  for (int pass = 0; pass < 2 && ncur > 0; ++pass) {
+    // cur -= V (V^+ cur)
+    DV_TRY(gram<T>(S, S.V, n, cur, ncur, S.C, ncur, st, pf));
+    DV_TRY(gemm_outer_ab<T>((const double*)S.V, npw, (const double*)S.C, ncur, npw, ncur, n,
+                            (double*)cur, npw, 1, 1, st, pf));
+    // Cholesky of the block's Gram matrix with dropping
+    DV_TRY(gram<T>(S, cur, ncur, cur, ncur, S.G, ncur, st, pf));
+    DV_TRY(hermitize(S.G, ncur, ncur, st));
+    DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
+    DV_TRY(cholesky(S.G, ncur, ncur, drop * drop, true, S.dw.piv, S.dw.status, st));
+    std::vector<double> piv(ncur);
+    DV_CU(cudaMemcpyAsync(piv.data(), S.dw.piv, ncur * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DV_CU(cudaStreamSynchronize(st));
+    std::vector<int> keep;
+    for (int j = 0; j < ncur; ++j)
+      if (piv[j] > 0.0) keep.push_back(j);
+    const int nk = (int)keep.size();
+    if (nk == 0) { *nk_out = 0; return QE_OK; }
+    DV_CU(cudaMemcpyAsync(S.idx, keep.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st));
+    // Mk = Lk^-+ with Lk the kept sub-factor; Mf = rows of Mk at the kept positions
+    k_gather_sub<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.G, ncur, S.idx, nk, S.Lk, nk);
+    k_identity<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.Mk, nk, nk);
+    DV_TRY(check_launch("orthonormalise"));
+    DV_TRY(trsm_upper_h(S.Lk, nk, nk, S.Mk, nk, nk, st));
+    DV_CU(cudaMemsetAsync(S.Mf, 0, (size_t)ncur * nk * sizeof(z), st));
+    k_place_rows<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.Mk, nk, S.idx, nk, S.Mf);
+    DV_TRY(check_launch("k_place_rows"));
+    z* dst = (pass == 0) ? S.D2 : out;
+    DV_TRY(gemm_outer_ab<T>((const double*)cur, npw, (const double*)S.Mf, nk, npw, nk, ncur,
+                            (double*)dst, npw, 0, 0, st, pf));
+    cur = dst;
+    ncur = nk;
+    *nk_out = nk;
+  }
+  return QE_OK;
+}
+
+template <typename T>
+static int davidson_run(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, double tol,
+                        int max_iter, DvState& S, int* iters, bool* converged, cudaStream_t st) {
+  Prof* pf = &ctx->prof;
+  const int npw = S.npw, nb = S.nb, md = S.max_dim;
+  const size_t zb = sizeof(z);
+  const double pmin = 0.1;
+  const double drop = 1e-6;
+  // preconditioner diagonal
+  const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
+  k_mean<<<1, 1024, 0, st>>>(op.vloc, ngrid, S.vmean);
+  k_hdiag<<<(npw + 255) / 256, 256, 0, st>>>(P.kin, S.vmean, (const z*)op.beta, op.dmat, op.nproj,
+                                              npw, S.hd);
+  DV_TRY(check_launch("k_hdiag"));
+  // start block
+  DV_TRY(hpsi_core(ctx, P, op, precision, (const double*)S.V, (double*)S.HV, nb, st));
+  int n = nb;
+  DV_TRY(update_reduced<T>(S, 0, n, st, pf));
+  int it = 0;
+  bool first = true;
+  std::vector<double> e(nb), rn(nb);
+  *converged = false;
+  while (true) {
+    DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
+    DV_TRY(rayleigh_ritz(S, n, st));
+    DV_TRY(gemm_outer_ab<T>((const double*)S.V, npw, (const double*)S.X, nb, npw, nb, n,
+                            (double*)S.Psi, npw, 0, 0, st, pf));
+    DV_TRY(gemm_outer_ab<T>((const double*)S.HV, npw, (const double*)S.X, nb, npw, nb, n,
+                            (double*)S.HPsi, npw, 0, 0, st, pf));
+    if (first) {
+      // the Ritz vectors of the start block become the (orthonormal) basis
+      DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+      DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+      n = nb;
+      DV_TRY(update_reduced<T>(S, 0, n, st, pf));
+      first = false;
+    }
+    k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
+    DV_TRY(check_launch("k_resid"));
+    int status = 0;
+    DV_CU(cudaMemcpyAsync(e.data(), S.e, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DV_CU(cudaMemcpyAsync(rn.data(), S.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DV_CU(cudaMemcpyAsync(&status, S.dw.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DV_CU(cudaStreamSynchronize(st));
+    if (status != 0) {
+      set_error("davidson: reduced overlap matrix not positive definite (column %d)", status - 1);
+      *iters = it;
+      return QE_ENOCONV;
+    }
+    std::vector<int> unc;
+    for (int b = 0; b < nb; ++b)
+      if (!(rn[b] <= tol)) unc.push_back(b);
+    if (unc.empty()) { *converged = true; break; }
+    if (it >= max_iter) break;
+    ++it;
+    const int nu = (int)unc.size();
+    DV_CU(cudaMemcpyAsync(S.idx, unc.data(), nu * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_precond<<<nu, 256, 0, st>>>(S.R, S.idx, S.e, S.hd, npw, pmin * pmin, S.D);
+    DV_TRY(check_launch("k_precond"));
+    if (n + nu > md) {
+      DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+      DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+      n = nb;
+      DV_TRY(update_reduced<T>(S, 0, n, st, pf));
+    }
+    int nk = 0;
+    DV_TRY(orthonormalise<T>(S, n, S.D, nu, S.V + (size_t)n * npw, &nk, drop, st, pf));
+    if (nk == 0) break;
+    DV_TRY(hpsi_core(ctx, P, op, precision, (const double*)(S.V + (size_t)n * npw),
+                     (double*)(S.HV + (size_t)n * npw), nk, st));
+    DV_TRY(update_reduced<T>(S, n, n + nk, st, pf));
+    n += nk;
+  }
+  *iters = it;
+  return QE_OK;
+}
+
+}  // namespace qe
+
+using namespace qe;
 
 extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
                            int max_iter, int max_dim, double* psi_inout, double* evals,
                            double* resid, int* iters, void* stream) {
-  qe::set_error("qe_davidson: not available in this build");
-  return QE_EINVAL;
+  clear_error();
+  if (!ctx) { set_error("qe_davidson: null context"); return QE_EINVAL; }
+  DV_TRY(check_problem(prob, "qe_davidson"));
+  if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_davidson: bad precision"); return QE_EINVAL; }
+  if (!(tol > 0.0) || max_iter < 0) { set_error("qe_davidson: tol must be > 0, max_iter >= 0"); return QE_EINVAL; }
+  const int nb = prob->nbnd;
+  if (iters) *iters = 0;
+  if (nb == 0) return QE_OK;
+  if (!psi_inout || !evals) { set_error("qe_davidson: null psi/evals"); return QE_EINVAL; }
+  DV_CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  DevPlan* P = nullptr;
+  DV_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
+  const int npw = P->h.npw;
+  if (nb > npw) { set_error("qe_davidson: %d bands > %d plane waves", nb, npw); return QE_EINVAL; }
+  int md = max_dim > 0 ? max_dim : 4 * nb;
+  if (md < 2 * nb) { set_error("qe_davidson: max_dim %d < 2 nbnd", md); return QE_EINVAL; }
+  md = std::min(md, std::max(2 * nb, npw));
+  if (md > kMaxDense) { set_error("qe_davidson: max_dim %d above %d", md, kMaxDense); return QE_EINVAL; }
+  OpView op;
+  DV_TRY(resolve_operator(ctx, prob, *P, op, st));
+  DvState S;
+  S.npw = npw;
+  S.nb = nb;
+  S.max_dim = md;
+  S.np = prob->nproj;
+  DV_TRY(dv_alloc(ctx, S));
+  const size_t bytes = (size_t)nb * npw * sizeof(z);
+  const cudaMemcpyKind in_kind = prob->mem == QE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind out_kind = prob->mem == QE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  DV_CU(cudaMemcpyAsync(S.V, psi_inout, bytes, in_kind, st));
+  int it = 0;
+  bool conv = false;
+  int rc = precision == QE_FP64
+               ? davidson_run<double>(ctx, *P, op, precision, tol, max_iter, S, &it, &conv, st)
+               : davidson_run<float>(ctx, *P, op, precision, tol, max_iter, S, &it, &conv, st);
+  if (iters) *iters = it;
+  if (rc && rc != QE_ENOCONV) return rc;
+  DV_CU(cudaMemcpyAsync(psi_inout, S.Psi, bytes, out_kind, st));
+  DV_CU(cudaMemcpyAsync(evals, S.e, nb * sizeof(double), out_kind, st));
+  if (resid) DV_CU(cudaMemcpyAsync(resid, S.rn, nb * sizeof(double), out_kind, st));
+  DV_CU(cudaStreamSynchronize(st));
+  if (rc == QE_ENOCONV) return rc;
+  if (!conv) {
+    set_error("qe_davidson: not converged after %d iterations", it);
+    return QE_ENOCONV;
+  }
+  return QE_OK;
 }

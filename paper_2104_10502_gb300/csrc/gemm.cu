@@ -197,7 +197,7 @@ constexpr int OBM = 64, OBN = 32, OBK = 16;
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
-             int M, int N, int K, double2* __restrict__ C, int ldc, int beta) {
+             int M, int N, int K, double2* __restrict__ C, int ldc, int alpha_neg, int beta) {
   __shared__ cx<T> As[OBK][OBM];
   __shared__ cx<T> Bs[OBK][OBN + 1];
   const int tid = threadIdx.x;
@@ -247,6 +247,7 @@ k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__
       if (m >= M) continue;
       double2* c = C + (size_t)n * ldc + m;
       double2 v = make_double2((double)acc[i][j].x, (double)acc[i][j].y);
+      if (alpha_neg) { v.x = -v.x; v.y = -v.y; }
       if (beta) { const double2 o = *c; v.x += o.x; v.y += o.y; }
       *c = v;
     }
@@ -254,15 +255,25 @@ k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__
 }
 
 template <typename T>
-int gemm_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
-               int ldc, int beta, cudaStream_t st, Prof* pf) {
+int gemm_outer_ab(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+                  double* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf) {
   if (M <= 0 || N <= 0) return QE_OK;
+  if (K <= 0) {
+    set_error("gemm_outer: K must be positive");
+    return QE_EINVAL;
+  }
   ProfScope ps(pf, "k_gemm_outer", st);
   dim3 g((M + OBM - 1) / OBM, (N + OBN - 1) / OBN);
   k_gemm_outer<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
                                       reinterpret_cast<const double2*>(B), ldb, M, N, K,
-                                      reinterpret_cast<double2*>(C), ldc, beta);
+                                      reinterpret_cast<double2*>(C), ldc, alpha_neg, beta);
   return check_launch("k_gemm_outer");
+}
+
+template <typename T>
+int gemm_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
+               int ldc, int beta, cudaStream_t st, Prof* pf) {
+  return gemm_outer_ab<T>(A, lda, B, ldb, M, N, K, C, ldc, 0, beta, st, pf);
 }
 
 __global__ void k_dmul(const double* __restrict__ D, const double2* __restrict__ P,
@@ -296,6 +307,10 @@ template int gemm_inner<double>(const double*, int, const double*, int, int, int
                                 void*, size_t, cudaStream_t, Prof*);
 template int gemm_inner<float>(const double*, int, const double*, int, int, int, int, double*, int,
                                void*, size_t, cudaStream_t, Prof*);
+template int gemm_outer_ab<double>(const double*, int, const double*, int, int, int, int, double*,
+                                   int, int, int, cudaStream_t, Prof*);
+template int gemm_outer_ab<float>(const double*, int, const double*, int, int, int, int, double*,
+                                  int, int, int, cudaStream_t, Prof*);
 template int gemm_outer<double>(const double*, int, const double*, int, int, int, int, double*, int,
                                 int, cudaStream_t, Prof*);
 template int gemm_outer<float>(const double*, int, const double*, int, int, int, int, double*, int,

@@ -93,6 +93,11 @@ template <typename T>
 int gemm_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
                double* C, int ldc, int beta, cudaStream_t st, Prof* pf);
 
+// C[n][m] = beta * C[n][m] + (alpha_neg ? -1 : 1) * sum_k A[k][m] B[k][n]
+template <typename T>
+int gemm_outer_ab(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+                  double* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf);
+
 // Q[i][n] = sum_j D[i][j] P[j][n] (D real [np][np], P complex [np][nb]).
 int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf);
 
