@@ -176,6 +176,54 @@ int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
                 int max_iter, int max_dim, double* psi_inout, double* evals,
                 double* resid, int* iters, void* stream);
 
+/* ---- Serving: continuous batching of Davidson solves ------------------------
+ * The paper's outlook (Sec. 4) names memory per card as the bound on system size
+ * and ensembles of independent runs as the way to fill large machines; Sec. 3.3
+ * notes that over-subscribing one GPU with several small runs pays off.  A
+ * server runs requests of different cells, cut-offs and band counts as they
+ * arrive: a request is admitted, in arrival order, when one of max_slots slots
+ * is idle and its estimated device footprint fits in what hbm_budget_bytes has
+ * left; each slot has its own context and stream, so admitted solves overlap
+ * on the GPU; a finished solve returns its workspace and the next request is
+ * admitted.  Results do not depend on what else runs (kernels are
+ * deterministic and each solve owns its buffers). */
+typedef struct qe_srv qe_srv;
+
+enum { QE_SERVE_FAKE_SOLVER = 1 };   /* test hook: no GPU; a solve sleeps max_iter ms */
+
+/* max_queue: requests allowed to wait for admission (QE_EAGAIN beyond).
+ * flags: 0, or QE_SERVE_FAKE_SOLVER (host-only test mode). */
+int qe_serve_create(int device, size_t hbm_budget_bytes, int max_slots, int max_queue,
+                    int flags, qe_srv** out);
+
+/* Queue a Davidson solve (as qe_davidson with max_dim = 4 nbnd).  Every array of
+ * prob and psi0 must be host memory (prob->mem = QE_HOST); they are copied
+ * before the call returns.  *ticket identifies the request.  QE_EAGAIN when the
+ * queue is full; QE_EINVAL when the request alone exceeds the budget. */
+int qe_serve_submit(qe_srv* srv, const qe_problem* prob, int precision, double tol,
+                    int max_iter, const double* psi0, uint64_t* ticket);
+
+/* Wait up to timeout_ms (0: do not wait, < 0: wait until done) for a request.
+ * QE_PENDING while it is queued or running.  When done, copies the Ritz vectors
+ * (psi_out [nbnd][npw][2]), eigenvalues, residual norms, iteration count and the
+ * latency from submit to completion (seconds) into the non-NULL outputs, frees
+ * the request, and returns its status (QE_OK, QE_ENOCONV, QE_ECANCELED, or the
+ * solve's error).  Unknown tickets: QE_EINVAL. */
+int qe_serve_poll(qe_srv* srv, uint64_t ticket, int timeout_ms, double* psi_out,
+                  double* evals, double* resid, int* iters, double* latency_s);
+
+/* Cancel a request: a queued one is dropped at once, a running one finishes
+ * but reports QE_ECANCELED.  QE_EINVAL for unknown tickets. */
+int qe_serve_cancel(qe_srv* srv, uint64_t ticket);
+
+/* Counters: requests submitted, completed; running now; waiting; budget bytes
+ * held by running requests.  Any pointer may be NULL. */
+int qe_serve_stats(qe_srv* srv, long long* submitted, long long* completed, int* running,
+                   int* queued, size_t* bytes_in_use);
+
+/* Stop: queued requests are cancelled, running ones finish, then everything is freed. */
+void qe_serve_destroy(qe_srv* srv);
+
 #ifdef __cplusplus
 }
 #endif

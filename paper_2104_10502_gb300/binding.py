@@ -24,7 +24,9 @@ QE_HOST, QE_DEVICE = 0, 1
 
 SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
            "qe_vloc_gaussian", "qe_beta_gaussian", "qe_hpsi", "qe_davidson", "qe_profile",
-           "qe_profile_read", "qe_hpsi_noalloc"]
+           "qe_profile_read", "qe_hpsi_noalloc", "qe_serve_create", "qe_serve_submit",
+           "qe_serve_poll", "qe_serve_cancel", "qe_serve_stats", "qe_serve_destroy"]
+QE_SERVE_FAKE_SOLVER = 1
 
 
 class QEError(RuntimeError):
@@ -66,6 +68,17 @@ _lib.qe_profile.argtypes = [_P, ctypes.c_int]
 _lib.qe_profile_read.argtypes = [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_longlong), _D,
                                  ctypes.POINTER(ctypes.c_longlong)]
+_lib.qe_serve_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.POINTER(_P)]
+_lib.qe_serve_submit.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
+                                 ctypes.c_int, _P, ctypes.POINTER(ctypes.c_uint64)]
+_lib.qe_serve_poll.argtypes = [_P, ctypes.c_uint64, ctypes.c_int, _P, _P, _P, _I,
+                               ctypes.POINTER(ctypes.c_double)]
+_lib.qe_serve_cancel.argtypes = [_P, ctypes.c_uint64]
+_lib.qe_serve_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                _I, _I, ctypes.POINTER(ctypes.c_size_t)]
+_lib.qe_serve_destroy.argtypes = [_P]
+_lib.qe_serve_destroy.restype = None
 _lib.qe_hpsi_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_hpsi.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_davidson.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
@@ -262,3 +275,81 @@ class Context:
                                      int(max_iter), int(max_dim), pp, pe, pr_, ctypes.byref(it),
                                      _stream(stream, psi)), allow=(QE_ENOCONV,))
         return rc, it.value
+
+
+def problem(lat, k, ecut, grid, vloc, beta, dmat, nbnd) -> Problem:
+    """Flat problem descriptor (see Context.problem)."""
+    return Context.problem(lat, k, ecut, grid, vloc, beta, dmat, nbnd)
+
+
+class Server:
+    """Continuous-batching Davidson server (qe_serve_*).  Inputs are host
+    arrays, copied at submit; results come back from poll()."""
+
+    def __init__(self, device=0, budget_bytes=8 << 30, max_slots=4, max_queue=256, fake=False):
+        h = _P()
+        _check(_lib.qe_serve_create(int(device), int(budget_bytes), int(max_slots), int(max_queue),
+                                    QE_SERVE_FAKE_SOLVER if fake else 0, ctypes.byref(h)))
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, prob: Problem, psi0: np.ndarray, precision=QE_FP64, tol=1e-8, max_iter=100):
+        psi0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+        t = ctypes.c_uint64(0)
+        rc = _lib.qe_serve_submit(self._h, ctypes.byref(prob), int(precision), float(tol),
+                                  int(max_iter), ctypes.c_void_p(psi0.ctypes.data), ctypes.byref(t))
+        if rc == QE_EAGAIN:
+            return None
+        _check(rc)
+        self._shapes[t.value] = psi0.shape
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1):
+        """None while pending; else a dict with status, psi, evals, resid, iters, latency_s."""
+        if ticket not in self._shapes:
+            _check(_lib.qe_serve_poll(self._h, ctypes.c_uint64(ticket), 0, None, None, None, None,
+                                      None))
+        nb, npw = self._shapes[ticket]
+        psi = np.zeros((nb, npw), dtype=np.complex128)
+        ev = np.zeros(nb)
+        rs = np.zeros(nb)
+        it = ctypes.c_int(0)
+        lat = ctypes.c_double(0.0)
+        rc = _lib.qe_serve_poll(self._h, ctypes.c_uint64(ticket), int(timeout_ms),
+                                ctypes.c_void_p(psi.ctypes.data), ctypes.c_void_p(ev.ctypes.data),
+                                ctypes.c_void_p(rs.ctypes.data), ctypes.byref(it), ctypes.byref(lat))
+        if rc == QE_PENDING:
+            return None
+        if rc not in (QE_OK, QE_ENOCONV, QE_ECANCELED):
+            _check(rc)
+        del self._shapes[ticket]
+        return dict(status=rc, psi=psi, evals=ev, resid=rs, iters=it.value, latency_s=lat.value)
+
+    def cancel(self, ticket):
+        _check(_lib.qe_serve_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def stats(self):
+        sub, comp = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        run, que = ctypes.c_int(0), ctypes.c_int(0)
+        used = ctypes.c_size_t(0)
+        _check(_lib.qe_serve_stats(self._h, ctypes.byref(sub), ctypes.byref(comp), ctypes.byref(run),
+                                   ctypes.byref(que), ctypes.byref(used)))
+        return dict(submitted=sub.value, completed=comp.value, running=run.value, queued=que.value,
+                    bytes_in_use=used.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.qe_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

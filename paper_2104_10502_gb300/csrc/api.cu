@@ -59,27 +59,56 @@ void Prof::reset() {
   launches = 0;
 }
 
-DevPlan::~DevPlan() {
-  if (block) cudaFree(block);
-}
-
 int DevBuf::ensure(size_t nbytes) {
   if (nbytes <= bytes && p) return QE_OK;
-  if (p) cudaFree(p);
-  p = nullptr;
-  bytes = 0;
+  const cudaStream_t st = sp ? *sp : nullptr;
+  release();
   if (nbytes == 0) return QE_OK;
-  if (cudaMalloc(&p, nbytes) != cudaSuccess) {
+  if (cudaMallocAsync(&p, nbytes, st) != cudaSuccess) {
     cudaGetLastError();
-    set_error("cudaMalloc of %zu bytes failed", nbytes);
+    set_error("cudaMallocAsync of %zu bytes failed", nbytes);
     p = nullptr;
     return QE_ENOMEM;
   }
   bytes = nbytes;
   return QE_OK;
 }
-DevBuf::~DevBuf() {
-  if (p) cudaFree(p);
+
+void DevBuf::release() {
+  if (p) cudaFreeAsync(p, sp ? *sp : nullptr);
+  p = nullptr;
+  bytes = 0;
+}
+
+int ctx_trim_public(qe_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  return ctx_trim(ctx);
+}
+
+int ctx_begin(qe_ctx* ctx, cudaStream_t st) {
+  if (ctx->has_cur && ctx->cur != st) {
+    cudaError_t e = cudaStreamSynchronize(ctx->cur);
+    if (e != cudaSuccess) {
+      set_error("previous stream: %s", cudaGetErrorString(e));
+      return QE_ECUDA;
+    }
+  }
+  ctx->cur = st;
+  ctx->has_cur = true;
+  return QE_OK;
+}
+
+int ctx_trim(qe_ctx* ctx) {
+  for (DevBuf* b : ctx->bufs()) b->release();
+  for (auto& p : ctx->plans)
+    if (p->block) cudaFreeAsync(p->block, ctx->cur);
+  ctx->plans.clear();
+  cudaError_t e = cudaStreamSynchronize(ctx->cur);
+  if (e != cudaSuccess) {
+    set_error("ctx_trim: %s", cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
 }
 
 static bool same_key(const DevPlan& P, const double lat[9], const double k[3], double ecut,
@@ -110,9 +139,9 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
   size_t ni = (h.nst + 1) + 3 * (size_t)h.npw + 2 * (size_t)h.nst + h.nax;
   for (int c = 0; c < 3; ++c) ni += grid[c];
   const size_t bytes = nd * sizeof(double) + ni * sizeof(int);
-  if (cudaMalloc(&P->block, bytes) != cudaSuccess) {
+  if (cudaMallocAsync(&P->block, bytes, ctx->cur) != cudaSuccess) {
     cudaGetLastError();
-    set_error("plan: cudaMalloc of %zu bytes failed", bytes);
+    set_error("plan: cudaMallocAsync of %zu bytes failed", bytes);
     return QE_ENOMEM;
   }
   std::vector<char> host(bytes);
@@ -134,8 +163,10 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
   const size_t o_ax = put_i(h.ax.data(), h.nax);
   size_t o_perm[3];
   for (int c = 0; c < 3; ++c) o_perm[c] = put_i(perm[c].data(), perm[c].size());
-  if (cudaMemcpy(P->block, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemcpyAsync(P->block, host.data(), bytes, cudaMemcpyHostToDevice, ctx->cur) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->cur) != cudaSuccess) {
     cudaGetLastError();
+    cudaFreeAsync(P->block, ctx->cur);
     set_error("plan: upload failed");
     return QE_ECUDA;
   }
@@ -261,8 +292,9 @@ int qe_ctx_create(int device, qe_ctx** out) {
 void qe_ctx_destroy(qe_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  cudaDeviceSynchronize();
+  if (ctx->has_cur) cudaStreamSynchronize(ctx->cur);
   ctx->prof.reset();
+  ctx_trim(ctx);
   delete ctx;
 }
 
@@ -304,6 +336,7 @@ int qe_vloc_gaussian(qe_ctx* ctx, const double lat[9], const int grid[3], int na
   if (mem != QE_HOST && mem != QE_DEVICE) { set_error("qe_vloc_gaussian: bad mem flag"); return QE_EINVAL; }
   QE_CU(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
+  QE_TRY(ctx_begin(ctx, st));
   const size_t ng = (size_t)grid[0] * grid[1] * grid[2];
   double* dst = vloc_out;
   if (mem == QE_HOST) {
@@ -332,6 +365,7 @@ int qe_beta_gaussian(qe_ctx* ctx, const double lat[9], const double k[3], double
   if (mem != QE_HOST && mem != QE_DEVICE) { set_error("qe_beta_gaussian: bad mem flag"); return QE_EINVAL; }
   QE_CU(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
+  QE_TRY(ctx_begin(ctx, st));
   Sphere S;
   QE_TRY(build_sphere(lat, k, ecut, S));
   const size_t n = (size_t)4 * nrad * natom * S.npw * 2;
@@ -358,6 +392,7 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
   if (prob->nbnd > 0 && (!psi || !hpsi)) { set_error("qe_hpsi: null psi/hpsi"); return QE_EINVAL; }
   QE_CU(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
+  QE_TRY(ctx_begin(ctx, st));
   DevPlan* P = nullptr;
   QE_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
   OpView op;

@@ -85,8 +85,9 @@ int build_vloc(const double lat[9], const int grid[3], int natom, const double* 
                double sigma, double* v_dev, cudaStream_t st) {
   double* tau_d = nullptr;
   if (natom > 0) {
-    if (cudaMalloc(&tau_d, sizeof(double) * 3 * natom) != cudaSuccess) {
-      set_error("qe_vloc_gaussian: cudaMalloc failed");
+    if (cudaMallocAsync(&tau_d, sizeof(double) * 3 * natom, st) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("qe_vloc_gaussian: cudaMallocAsync failed");
       return QE_ENOMEM;
     }
     cudaMemcpyAsync(tau_d, tau_h, sizeof(double) * 3 * natom, cudaMemcpyHostToDevice, st);
@@ -99,7 +100,7 @@ int build_vloc(const double lat[9], const int grid[3], int natom, const double* 
                                  1.0 / (2.0 * sigma * sigma), v_dev);
   int rc = check_launch("k_vloc");
   cudaStreamSynchronize(st);
-  if (tau_d) cudaFree(tau_d);
+  if (tau_d) cudaFreeAsync(tau_d, st);
   return rc;
 }
 
@@ -120,8 +121,9 @@ int build_beta(const double lat[9], const double k[3], double ecut, int natom, c
   double *q_d = nullptr, *tau_d = nullptr, *w_d = nullptr;
   const size_t nb = sizeof(double) * (q.size() + 3 * (size_t)natom + nrad);
   void* blk = nullptr;
-  if (cudaMalloc(&blk, nb) != cudaSuccess) {
-    set_error("qe_beta_gaussian: cudaMalloc failed");
+  if (cudaMallocAsync(&blk, nb, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("qe_beta_gaussian: cudaMallocAsync failed");
     return QE_ENOMEM;
   }
   q_d = (double*)blk;
@@ -135,7 +137,7 @@ int build_beta(const double lat[9], const double k[3], double ecut, int natom, c
   k_beta<<<g, 128, 0, st>>>(q_d, S.npw, tau_d, natom, w_d, nrad, pref, beta_dev);
   rc = check_launch("k_beta");
   cudaStreamSynchronize(st);
-  cudaFree(blk);
+  cudaFreeAsync(blk, st);
   return rc;
 }
 

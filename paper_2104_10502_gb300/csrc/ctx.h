@@ -8,6 +8,10 @@
 
 struct qe_ctx {
   int device = 0;
+  // The stream of the current call.  A context's buffers are shared by its
+  // calls, so a call on a different stream first waits for the previous one.
+  cudaStream_t cur = nullptr;
+  bool has_cur = false;
   qe::Prof prof;
   std::vector<std::unique_ptr<qe::DevPlan>> plans;
   // H|psi> workspaces
@@ -16,7 +20,13 @@ struct qe_ctx {
   // device copies of host arrays
   qe::DevBuf h_v, h_beta, h_d, h_psi, h_hpsi;
   // Davidson workspaces
-  qe::DevBuf dv_basis, dv_hbasis, dv_red, dv_small, dv_vec;
+  qe::DevBuf dv_basis, dv_red;
+  qe_ctx() {
+    for (qe::DevBuf* b : bufs()) b->sp = &cur;
+  }
+  std::vector<qe::DevBuf*> bufs() {
+    return {&sticks, &vp, &part, &proj, &projd, &h_v, &h_beta, &h_d, &h_psi, &h_hpsi, &dv_basis, &dv_red};
+  }
 };
 
 namespace qe {
@@ -27,6 +37,12 @@ struct OpView {
   const double* beta = nullptr;
   const double* dmat = nullptr;
 };
+
+// Start of an API call on stream st (see qe_ctx::cur).
+int ctx_begin(qe_ctx* ctx, cudaStream_t st);
+// Return every buffer and plan of the context to the pool (stream-ordered on
+// the current stream, which is then synchronised).
+int ctx_trim(qe_ctx* ctx);
 
 int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, const int grid[3],
              DevPlan** out);

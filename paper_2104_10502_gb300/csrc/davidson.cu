@@ -185,6 +185,39 @@ struct DvState {
   size_t part_bytes = 0;
 };
 
+static size_t dv_bytes(size_t npw, size_t nb, size_t md) {
+  const size_t zb = sizeof(z);
+  const size_t big = (2 * md + 5 * nb) * npw * zb;
+  const size_t smallz = (5 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
+  const size_t dbl = (2 * nb + npw + 1 + 3 * md + nb * md) * sizeof(double);
+  const size_t dwz = 2 * md * zb;
+  const size_t ints = (nb + 16) * sizeof(int);
+  return big + smallz + dbl + dwz + ints + 48 * 256;
+}
+
+static size_t dv_red_bytes(size_t md) {
+  const size_t tiles = (size_t)((md + 31) / 32) * ((md + 31) / 32);
+  return (2 * 152 * 4 + tiles + 1) * 32 * 32 * sizeof(z);
+}
+
+// Upper bound of the device memory one qe_davidson call holds (FP64 path; the
+// mixed path needs less): Davidson state, H|psi> workspaces, operator copies of
+// host inputs and the plan.
+size_t davidson_footprint(int npw, int nb, int max_dim, int nproj, const int grid[3], int nst) {
+  const size_t md = std::max(max_dim, 2 * nb);
+  const size_t ngrid = (size_t)grid[0] * grid[1] * grid[2];
+  const size_t per_band = (size_t)grid[2] * nst * sizeof(z);
+  const size_t nbc = std::max<size_t>(1, std::min<size_t>(nb, ((size_t)64 << 20) / std::max<size_t>(per_band, 1)));
+  size_t b = dv_bytes(npw, nb, md) + dv_red_bytes(md);
+  b += ngrid * sizeof(double) * 2;                                  // V copy + permuted V
+  b += nbc * per_band;                                              // stick buffer
+  b += gemm_inner_scratch(nproj, nb, npw, sizeof(double));          // split-K partials
+  b += 2 * (size_t)nproj * nb * sizeof(z);                          // projections
+  b += (size_t)nproj * npw * sizeof(z) + (size_t)nproj * nproj * sizeof(double);   // beta, D
+  b += (size_t)npw * 24 + 16 * (size_t)npw + 64 * (size_t)(grid[0] + grid[1] + grid[2]);   // plan
+  return b + ((size_t)1 << 20);
+}
+
 static int dv_alloc(qe_ctx* ctx, DvState& S) {
   const size_t npw = S.npw, nb = S.nb, md = S.max_dim;
   const size_t zb = sizeof(z);
@@ -198,6 +231,10 @@ static int dv_alloc(qe_ctx* ctx, DvState& S) {
   const size_t dwz = 2 * md * zb;
   const size_t ints = (nb + 16) * sizeof(int);
   const size_t total = big + smallz + dbl + dwz + ints + 48 * 256;   // + alignment of 31 pieces
+  if (total != dv_bytes(npw, nb, md)) {
+    set_error("davidson: workspace size mismatch");
+    return QE_EINVAL;
+  }
   DV_TRY(ctx->dv_basis.ensure(total));
   char* p = (char*)ctx->dv_basis.p;
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
@@ -236,8 +273,7 @@ static int dv_alloc(qe_ctx* ctx, DvState& S) {
     return QE_EINVAL;
   }
   // split-K partials: at most (splits for ~4 CTAs/SM + tiles) 32x32 tiles of FP64 complex
-  const size_t tiles = (size_t)((md + 31) / 32) * ((md + 31) / 32);
-  const size_t sb = (2 * 152 * 4 + tiles + 1) * 32 * 32 * zb;
+  const size_t sb = dv_red_bytes(md);
   DV_TRY(ctx->dv_red.ensure(sb));
   S.part = ctx->dv_red.p;
   S.part_bytes = sb;
@@ -266,18 +302,33 @@ static int update_reduced(const DvState& S, int n0, int n1, cudaStream_t st, Pro
 }
 
 // Rayleigh-Ritz on span(V[0:n]): eigenvalues e[0:nb], X [n][nb] (ld nb).
-static int rayleigh_ritz(DvState& S, int n, cudaStream_t st) {
+static int rayleigh_ritz(DvState& S, int n, cudaStream_t st, Prof* pf) {
   const int md = S.max_dim, nb = S.nb;
   const size_t zb = sizeof(z);
   DV_CU(cudaMemcpy2DAsync(S.Lw, n * zb, S.Sr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
   DV_CU(cudaMemcpy2DAsync(S.Zw, n * zb, S.Hr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
-  DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, st));
-  DV_TRY(trsm_lower(S.Lw, n, n, S.Zw, n, n, st));                 // Z = L^-1 H
-  DV_TRY(conj_transpose(S.Zw, n, S.Aw, n, n, n, st));             // Z^+ = H L^-+
-  DV_TRY(trsm_lower(S.Lw, n, n, S.Aw, n, n, st));                 // A = L^-1 H L^-+
-  DV_TRY(hermitize(S.Aw, n, n, st));
-  DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st));
-  DV_TRY(trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st));              // X = L^-+ Y
+  {
+    ProfScope ps(pf, "rr_cholesky", st);
+    DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, st));
+    pf->launches += n;                                            // n + 1 kernels in the scope
+  }
+  {
+    ProfScope ps(pf, "rr_reduce", st);
+    DV_TRY(trsm_lower(S.Lw, n, n, S.Zw, n, n, st));               // Z = L^-1 H
+    DV_TRY(conj_transpose(S.Zw, n, S.Aw, n, n, n, st));           // Z^+ = H L^-+
+    DV_TRY(trsm_lower(S.Lw, n, n, S.Aw, n, n, st));               // A = L^-1 H L^-+
+    DV_TRY(hermitize(S.Aw, n, n, st));
+    pf->launches += 3;
+  }
+  {
+    ProfScope ps(pf, "rr_heev", st);
+    DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st));
+    pf->launches += 3 * (n - 1) + 3;
+  }
+  {
+    ProfScope ps(pf, "rr_backsub", st);
+    DV_TRY(trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st));            // X = L^-+ Y
+  }
   return QE_OK;
 }
 
@@ -303,10 +354,14 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
     DV_CU(cudaMemcpyAsync(piv.data(), S.dw.piv, ncur * sizeof(double), cudaMemcpyDeviceToHost, st));
     DV_CU(cudaStreamSynchronize(st));
     std::vector<int> keep;
+    double pmin_kept = 1.0;
     for (int j = 0; j < ncur; ++j)
-      if (piv[j] > 0.0) keep.push_back(j);
+      if (piv[j] > 0.0) { keep.push_back(j); pmin_kept = std::min(pmin_kept, piv[j]); }
     const int nk = (int)keep.size();
     if (nk == 0) { *nk_out = 0; return QE_OK; }
+    // "twice is enough": a second pass is needed only when this one removed most
+    // of some vector (its remaining norm fell below 1/2 of the unit input)
+    const bool last = pass == 1 || pmin_kept > 0.5;
     DV_CU(cudaMemcpyAsync(S.idx, keep.data(), nk * sizeof(int), cudaMemcpyHostToDevice, st));
     // Mk = Lk^-+ with Lk the kept sub-factor; Mf = rows of Mk at the kept positions
     k_gather_sub<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.G, ncur, S.idx, nk, S.Lk, nk);
@@ -316,12 +371,13 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
     DV_CU(cudaMemsetAsync(S.Mf, 0, (size_t)ncur * nk * sizeof(z), st));
     k_place_rows<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.Mk, nk, S.idx, nk, S.Mf);
     DV_TRY(check_launch("k_place_rows"));
-    z* dst = (pass == 0) ? S.D2 : out;
+    z* dst = last ? out : S.D2;
     DV_TRY(gemm_outer_ab<T>((const double*)cur, npw, (const double*)S.Mf, nk, npw, nk, ncur,
                             (double*)dst, npw, 0, 0, st, pf));
     cur = dst;
     ncur = nk;
     *nk_out = nk;
+    if (last) break;
   }
   return QE_OK;
 }
@@ -350,7 +406,7 @@ static int davidson_run(qe_ctx* ctx, const DevPlan& P, const OpView& op, int pre
   *converged = false;
   while (true) {
     DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
-    DV_TRY(rayleigh_ritz(S, n, st));
+    DV_TRY(rayleigh_ritz(S, n, st, pf));
     DV_TRY(gemm_outer_ab<T>((const double*)S.V, npw, (const double*)S.X, nb, npw, nb, n,
                             (double*)S.Psi, npw, 0, 0, st, pf));
     DV_TRY(gemm_outer_ab<T>((const double*)S.HV, npw, (const double*)S.X, nb, npw, nb, n,
@@ -421,6 +477,7 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   if (!psi_inout || !evals) { set_error("qe_davidson: null psi/evals"); return QE_EINVAL; }
   DV_CU(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
+  DV_TRY(ctx_begin(ctx, st));
   DevPlan* P = nullptr;
   DV_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
   const int npw = P->h.npw;

@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "dense.h"
+#include "plan.h"
 #include "fft_device.cuh"
 
 namespace qe {
@@ -495,7 +496,9 @@ int heev_lowest(z* A, int n, int lda, int nev, double* w, z* X, int ldx, DenseWo
   rc = check_launch("k_bisect");
   if (rc) return rc;
   const size_t ism = (size_t)n * (5 * sizeof(double) + sizeof(int));
-  cudaFuncSetAttribute(k_inviter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+  // same (largest) cap for every caller: the attribute is shared process-wide
+  set_max_dynamic_smem(k_inviter);
+  set_max_dynamic_smem(k_backtransform);
   // eigenvalues within 1e-10 of each other (relative to the spread of T) share a cluster
   k_inviter<<<nev, 256, ism, st>>>(wk.d, wk.e, n, nev, w, wk.ctol_rel, wk.y);
   rc = check_launch("k_inviter");

@@ -174,9 +174,12 @@ int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, cons
     set_error("FFT plane %d x %d does not fit in shared memory at this precision", n1, n2);
     return QE_EINVAL;
   }
-  cudaFuncSetAttribute(k_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
-  cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm);
-  cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsm);
+  // The cap is a per-function device attribute shared by every thread of the
+  // process: always set the same (largest) value so that concurrent callers
+  // with different plane sizes cannot lower it under each other's launch.
+  set_max_dynamic_smem(k_plane<T>);
+  set_max_dynamic_smem(k_zinv<T>);
+  set_max_dynamic_smem(k_zfwd<T>);
   dim3 gz((nst + spb - 1) / spb, nbc);
   int rc;
   {

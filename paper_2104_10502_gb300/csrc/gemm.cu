@@ -113,7 +113,7 @@ __global__ void k_reduce_split(const cx<T>* __restrict__ part, int nsplit, int M
 static int inner_split(int M, int N, int K) {
   const int tiles = ((M + IBM - 1) / IBM) * ((N + IBN - 1) / IBN);
   int ns = (2 * 152 * 4 + tiles - 1) / tiles;  // aim for ~4 CTAs per SM
-  const int maxs = std::max(1, K / 256);        // at least 256 k per split
+  const int maxs = std::max(1, K / 32);         // at least 32 k per split
   ns = std::max(1, std::min(ns, maxs));
   return ns;
 }

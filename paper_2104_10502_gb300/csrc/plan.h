@@ -25,8 +25,22 @@ struct DevPlan {
   int* ax = nullptr;        // [nax]
   int* perm[3] = {nullptr, nullptr, nullptr};   // digit reversal per axis
   double* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i t / N_axis), interleaved
-  ~DevPlan();
 };
+
+// Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum
+// minus its static shared memory.  Always the same value for a kernel, so
+// concurrent host threads never lower it under each other's launch.
+template <typename F>
+inline void set_max_dynamic_smem(F* f) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes a;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(f)) != cudaSuccess)
+    return;
+  cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       optin - (int)a.sharedSizeBytes);
+}
 
 // Optional per-kernel timing: CUDA events recorded on the launching stream
 // around each kernel, folded into per-name totals on read.  Also counts
@@ -52,12 +66,15 @@ struct ProfScope {
   ~ProfScope() { if (p) p->end(name, st, a); }
 };
 
-// Grow-only device buffer.
+// Grow-only device buffer, allocated and freed stream-ordered (cudaMallocAsync /
+// cudaFreeAsync) on the owning context's current stream, so that growing or
+// releasing it never synchronises the whole device.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  const cudaStream_t* sp = nullptr;   // owner's current stream
   int ensure(size_t nbytes);
-  ~DevBuf();
+  void release();
 };
 
 // ---- launchers (return QE_OK or QE_ECUDA with the error message set) -------

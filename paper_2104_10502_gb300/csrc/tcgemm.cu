@@ -1,0 +1,549 @@
+// Split-precision real GEMM on the 5th-generation tensor cores (tcgen05,
+// kind::tf32) and the operand packing of the complex products of the
+// nonlocal term (Sec. 3.3 of the paper: pseudopotential contribution to the
+// Hamiltonian) for the mixed-precision path.  See tcgemm.cuh.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.h"
+#include "plan.h"
+#include "tcgemm.cuh"
+
+namespace qe {
+
+// ---- PTX wrappers ------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Wait for the phase of parity `parity` to complete; gives up after `limit_ns`.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  const uint32_t addr = smem_u32(bar);
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                    // leading-dimension offset (unused when swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride-dimension offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major,
+// N = TC_BN, M = TC_BM.
+__host__ __device__ constexpr uint32_t tf32_idesc() {
+  return (1u << 4)                       // D format F32
+         | (2u << 7)                     // A format TF32
+         | (2u << 10)                    // B format TF32
+         | ((uint32_t)(TC_BN >> 3) << 17)
+         | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---- the GEMM kernel ------------------------------------------------------------
+// grid (Mp/128, Np/128, nsplit), block 128 (warp 0 lane 0: TMA producer; warp 1
+// lane 0: MMA issuer; all four warps: epilogue).  CTA z handles K blocks
+// [z*kb_per_split, min(nkb_total, (z+1)*kb_per_split)) and writes its partial
+// tile to C + z*split_stride (row-major, leading dimension ldc).
+__global__ void __launch_bounds__(128, 1)
+k_tc_gemm_tf32x3(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                 const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                 int nkb_total, int kb_per_split, float* __restrict__ C, int ldc,
+                 long long split_stride, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* tiles =
+      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* accb = empty + TC_STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+  __shared__ int s_err;
+  __shared__ int s_issued;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int nkb = min(kb_per_split, nkb_total - kb0);
+  const uint64_t limit = 2000000000ull;   // 2 s per wait
+
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_issued = 0;
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  if (nkb > 0 && warp == 0 && lane == 0) {
+    // producer: fill the stages with TMA loads
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % TC_STAGES;
+      const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+      if (i >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u, limit)) {
+        atomicExch(&s_err, TC_TIMEOUT_EMPTY);
+        break;
+      }
+      if (*(volatile int*)&s_err) break;
+      mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+      unsigned char* stg = tiles + s * TC_STAGE_BYTES;
+      const int kx = (kb0 + i) * TC_BK;
+      tma_load_2d(stg, &mAhi, &full[s], kx, m0);
+      tma_load_2d(stg + TC_TILE_BYTES, &mAlo, &full[s], kx, m0);
+      tma_load_2d(stg + 2 * TC_TILE_BYTES, &mBhi, &full[s], kx, n0);
+      tma_load_2d(stg + 3 * TC_TILE_BYTES, &mBlo, &full[s], kx, n0);
+      s_issued = i + 1;
+    }
+  } else if (nkb > 0 && warp == 1 && lane == 0) {
+    // MMA issuer: three split products per K step of 8
+    const uint32_t idesc = tf32_idesc();
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % TC_STAGES;
+      const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph, limit)) {
+        atomicExch(&s_err, TC_TIMEOUT_FULL);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(tiles + s * TC_STAGE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+        const uint32_t off = kk * 32;
+        const uint64_t ahi = sw128_desc(sa + off);
+        const uint64_t alo = sw128_desc(sa + TC_TILE_BYTES + off);
+        const uint64_t bhi = sw128_desc(sa + 2 * TC_TILE_BYTES + off);
+        const uint64_t blo = sw128_desc(sa + 3 * TC_TILE_BYTES + off);
+        mma_tf32(tmem, ahi, bhi, idesc, (i | kk) != 0 ? 1u : 0u);
+        mma_tf32(tmem, ahi, blo, idesc, 1u);
+        mma_tf32(tmem, alo, bhi, idesc, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    if (ok) mma_commit(accb);
+  }
+  __syncwarp();
+  // epilogue: each warp drains its 32 TMEM lanes (= 32 rows of the tile)
+  bool have = false;
+  if (nkb > 0) have = mbar_wait(accb, 0, limit) && *(volatile int*)&s_err == 0;
+  if (nkb > 0 && !have && threadIdx.x == 0) atomicCAS(&s_err, 0, TC_TIMEOUT_ACC);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncwarp();
+  float* crow = C + (size_t)blockIdx.z * split_stride + (size_t)(m0 + warp * 32 + lane) * ldc + n0;
+  if (have) {
+    for (int c = 0; c < TC_BN; c += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+      float4* dst = reinterpret_cast<float4*>(crow + c);
+      dst[0] = make_float4(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]), __uint_as_float(r[3]));
+      dst[1] = make_float4(__uint_as_float(r[4]), __uint_as_float(r[5]), __uint_as_float(r[6]), __uint_as_float(r[7]));
+      dst[2] = make_float4(__uint_as_float(r[8]), __uint_as_float(r[9]), __uint_as_float(r[10]), __uint_as_float(r[11]));
+      dst[3] = make_float4(__uint_as_float(r[12]), __uint_as_float(r[13]), __uint_as_float(r[14]), __uint_as_float(r[15]));
+    }
+  } else if (nkb <= 0) {
+    for (int c = 0; c < TC_BN; c += 4)
+      *reinterpret_cast<float4*>(crow + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_err != 0 && threadIdx.x == 0) {
+    // drain: wait (bounded) for the copies this CTA issued before releasing smem
+    const int issued = s_issued;
+    for (int i = max(0, issued - TC_STAGES); i < issued; ++i)
+      mbar_wait(&full[i % TC_STAGES], (uint32_t)(i / TC_STAGES) & 1u, limit);
+    atomicMax(status, s_err);
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN)
+                 : "memory");
+}
+
+// ---- host side ----------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static int get_encode() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+// rows x kp FP32 matrix, K-major, box 128 rows x 32 columns, 128-byte swizzle.
+static int make_map(CUtensorMap* m, const float* ptr, int rows, int kp) {
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+int tc_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int Mp,
+                   int Np, int Kp, int nsplit, float* C, int* status, cudaStream_t st, Prof* pf) {
+  if (Mp % TC_BM || Np % TC_BN || Kp % TC_BK || Mp <= 0 || Np <= 0 || Kp <= 0 || nsplit < 1) {
+    set_error("tc_gemm: bad padded sizes %d %d %d", Mp, Np, Kp);
+    return QE_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(Ahi) | reinterpret_cast<uintptr_t>(Alo) |
+       reinterpret_cast<uintptr_t>(Bhi) | reinterpret_cast<uintptr_t>(Blo)) & 15) {
+    set_error("tc_gemm: operands must be 16-byte aligned");
+    return QE_EINVAL;
+  }
+  int rc = get_encode();
+  if (rc) return rc;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  if ((rc = make_map(&mAhi, Ahi, Mp, Kp)) || (rc = make_map(&mAlo, Alo, Mp, Kp)) ||
+      (rc = make_map(&mBhi, Bhi, Np, Kp)) || (rc = make_map(&mBlo, Blo, Np, Kp)))
+    return rc;
+  const int nkb = Kp / TC_BK;
+  nsplit = std::min(nsplit, nkb);
+  const int per = (nkb + nsplit - 1) / nsplit;
+  nsplit = (nkb + per - 1) / per;   // every split non-empty
+  set_max_dynamic_smem(k_tc_gemm_tf32x3);
+  ProfScope ps(pf, "k_tc_gemm_tf32x3", st);
+  dim3 g(Mp / TC_BM, Np / TC_BN, nsplit);
+  k_tc_gemm_tf32x3<<<g, 128, TC_SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, nkb, per, C, Np,
+                                                  (long long)Mp * Np, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("k_tc_gemm_tf32x3: %s", cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+int tc_gemm_splits(int Mp, int Np, int Kp) {
+  const int tiles = (Mp / TC_BM) * (Np / TC_BN);
+  const int nkb = Kp / TC_BK;
+  int ns = std::max(1, (152 + tiles - 1) / tiles);
+  ns = std::min(ns, std::max(1, nkb / 4));   // at least 4 K blocks per CTA
+  const int per = (nkb + ns - 1) / ns;
+  return (nkb + per - 1) / per;
+}
+
+
+// ---- operand packing of the complex products ---------------------------------
+// Complex products are evaluated as real GEMMs over the concatenated (re, im)
+// K axis, with the signs placed in the packed B operand:
+//   P = conj(beta) psi^T      A[i] = [Re b_i | Im b_i],  B[n] = [Re psi_n | Im psi_n],
+//                             B[nb+n] = [Im psi_n | -Re psi_n]  ->  C[i][n] = Re P, C[i][nb+n] = Im P
+//   HPsi += beta^T Q          A[g] = [Re b_.(g) | Im b_.(g)],  B[n] = [Re Q_.n | -Im Q_.n],
+//                             B[nb+n] = [Im Q_.n | Re Q_.n]  ->  C[g][n] = Re, C[g][nb+n] = Im
+// Every value x is stored as hi = tf32(x), lo = tf32(x - hi) (round to nearest).
+
+namespace {
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void split_store(float x, float* hi, float* lo, size_t i) {
+  const float h = tf32_rn(x);
+  hi[i] = h;
+  lo[i] = tf32_rn(x - h);
+}
+
+// A[i][k], k < 2 npw: [Re | Im] of row i of a complex [rows][npw] matrix; zero padding.
+__global__ void k_pack_rows(const double2* __restrict__ src, int rows, int npw, int Mp, int Kp,
+                            float* __restrict__ hi, float* __restrict__ lo) {
+  const size_t total = (size_t)Mp * Kp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / Kp), k = (int)(t % Kp);
+    float x = 0.f;
+    if (r < rows) {
+      if (k < npw) x = (float)src[(size_t)r * npw + k].x;
+      else if (k < 2 * npw) x = (float)src[(size_t)r * npw + (k - npw)].y;
+    }
+    split_store(x, hi, lo, t);
+  }
+}
+
+// B rows n < nb: [Re psi_n | Im psi_n]; rows nb + n: [Im psi_n | -Re psi_n].
+__global__ void k_pack_psi(const double2* __restrict__ psi, int nb, int npw, int Np, int Kp,
+                           float* __restrict__ hi, float* __restrict__ lo) {
+  const size_t total = (size_t)Np * Kp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / Kp), k = (int)(t % Kp);
+    float x = 0.f;
+    if (r < 2 * nb && k < 2 * npw) {
+      const int n = r < nb ? r : r - nb;
+      const double2 v = psi[(size_t)n * npw + (k < npw ? k : k - npw)];
+      if (r < nb) x = (float)(k < npw ? v.x : v.y);
+      else x = (float)(k < npw ? v.y : -v.x);
+    }
+    split_store(x, hi, lo, t);
+  }
+}
+
+// Transposed beta: A[g][k], k < 2 np: [Re b_k(g) | Im b_k(g)]; tiles through shared memory.
+__global__ void k_pack_beta_t(const double2* __restrict__ beta, int np, int npw, int Mp, int Kp,
+                              float* __restrict__ hi, float* __restrict__ lo) {
+  __shared__ double2 tile[32][33];
+  const int g0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  // load beta[i0 .. i0+31][g0 .. g0+31] (coalesced along g)
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, g = g0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < np && g < npw) ? beta[(size_t)i * npw + g] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  // write rows g (coalesced along k): re part at k = i, im part at k = np + i
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int g = g0 + r, i = i0 + threadIdx.x;
+    if (g >= Mp || i >= np) continue;
+    const double2 v = tile[threadIdx.x][r];
+    split_store((float)v.x, hi, lo, (size_t)g * Kp + i);
+    split_store((float)v.y, hi, lo, (size_t)g * Kp + np + i);
+  }
+}
+
+// zero the K padding (k >= 2 np) of the transposed beta rows and padding rows
+__global__ void k_pack_pad(int Mp, int Kp, int rows, int kvalid, float* __restrict__ hi,
+                           float* __restrict__ lo) {
+  const size_t total = (size_t)Mp * Kp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / Kp), k = (int)(t % Kp);
+    if (r >= rows || k >= kvalid) { hi[t] = 0.f; lo[t] = 0.f; }
+  }
+}
+
+// B rows n < nb: [Re Q_.n | -Im Q_.n]; rows nb + n: [Im Q_.n | Re Q_.n]; Q is [np][nb].
+__global__ void k_pack_q(const double2* __restrict__ Q, int np, int nb, int Np, int Kp,
+                         float* __restrict__ hi, float* __restrict__ lo) {
+  const size_t total = (size_t)Np * Kp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / Kp), k = (int)(t % Kp);
+    float x = 0.f;
+    if (r < 2 * nb && k < 2 * np) {
+      const int n = r < nb ? r : r - nb;
+      const double2 q = Q[(size_t)(k < np ? k : k - np) * nb + n];
+      if (r < nb) x = (float)(k < np ? q.x : -q.y);
+      else x = (float)(k < np ? q.y : q.x);
+    }
+    split_store(x, hi, lo, t);
+  }
+}
+
+// P[i][n] = (sum_s C[s][i][n], sum_s C[s][i][nb + n]) in FP64
+__global__ void k_combine_p(const float* __restrict__ C, int ns, int Mp, int Np, int np, int nb,
+                            double2* __restrict__ P) {
+  const size_t total = (size_t)np * nb;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / nb), n = (int)(t % nb);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      const float* c = C + (size_t)s * Mp * Np + (size_t)i * Np;
+      re += (double)c[n];
+      im += (double)c[nb + n];
+    }
+    P[t] = make_double2(re, im);
+  }
+}
+
+// hpsi[n][g] += (sum_s C[s][g][n], sum_s C[s][g][nb + n]); consecutive threads take consecutive g
+__global__ void k_combine_h(const float* __restrict__ C, int ns, int Mp, int Np, int npw, int nb,
+                            double2* __restrict__ hpsi) {
+  const size_t total = (size_t)nb * npw;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(t / npw), g = (int)(t % npw);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      const float* c = C + (size_t)s * Mp * Np + (size_t)g * Np;
+      re += (double)c[n];
+      im += (double)c[nb + n];
+    }
+    double2 h = hpsi[t];
+    h.x += re;
+    h.y += im;
+    hpsi[t] = h;
+  }
+}
+
+int grid_of(size_t total) {
+  return (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 152 * 16));
+}
+
+}  // namespace
+
+static inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+size_t nonlocal_tc_bytes(int np, int nb, int npw) {
+  const size_t Mp = pad_to(np, TC_BM), Kp = pad_to(2 * npw, TC_BK), Np = pad_to(2 * nb, TC_BN);
+  const size_t Mp2 = pad_to(npw, TC_BM), Kp2 = pad_to(2 * np, TC_BK);
+  const size_t ns1 = tc_gemm_splits((int)Mp, (int)Np, (int)Kp), ns2 = tc_gemm_splits((int)Mp2, (int)Np, (int)Kp2);
+  size_t b = 0;
+  b += 2 * Mp * Kp * 4 + 2 * Np * Kp * 4 + ns1 * Mp * Np * 4;        // inner product
+  b += 2 * Mp2 * Kp2 * 4 + 2 * Np * Kp2 * 4 + ns2 * Mp2 * Np * 4;    // outer product
+  b += 2 * (size_t)np * nb * 16 + 64 * 256;                          // P, Q, status, alignment
+  return b;
+}
+
+// Nonlocal term on the tensor cores: hpsi += beta^T D (conj(beta) psi^T).
+int nonlocal_tc(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
+                int nb, int npw, void* work, size_t work_bytes, int* status, cudaStream_t st,
+                Prof* pf) {
+  if (np <= 0 || nb <= 0) return QE_OK;
+  if (nonlocal_tc_bytes(np, nb, npw) > work_bytes) {
+    set_error("nonlocal_tc: workspace too small");
+    return QE_EINVAL;
+  }
+  const int Mp = pad_to(np, TC_BM), Kp = pad_to(2 * npw, TC_BK), Np = pad_to(2 * nb, TC_BN);
+  const int Mp2 = pad_to(npw, TC_BM), Kp2 = pad_to(2 * np, TC_BK);
+  const int ns1 = tc_gemm_splits(Mp, Np, Kp), ns2 = tc_gemm_splits(Mp2, Np, Kp2);
+  char* p = static_cast<char*>(work);
+  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
+  float* ahi = (float*)take((size_t)Mp * Kp * 4);
+  float* alo = (float*)take((size_t)Mp * Kp * 4);
+  float* bhi = (float*)take((size_t)Np * Kp * 4);
+  float* blo = (float*)take((size_t)Np * Kp * 4);
+  float* c1 = (float*)take((size_t)ns1 * Mp * Np * 4);
+  float* a2hi = (float*)take((size_t)Mp2 * Kp2 * 4);
+  float* a2lo = (float*)take((size_t)Mp2 * Kp2 * 4);
+  float* b2hi = (float*)take((size_t)Np * Kp2 * 4);
+  float* b2lo = (float*)take((size_t)Np * Kp2 * 4);
+  float* c2 = (float*)take((size_t)ns2 * Mp2 * Np * 4);
+  double2* P = (double2*)take((size_t)np * nb * 16);
+  double2* Q = (double2*)take((size_t)np * nb * 16);
+  {
+    ProfScope ps(pf, "k_pack", st);
+    k_pack_rows<<<grid_of((size_t)Mp * Kp), 256, 0, st>>>((const double2*)beta, np, npw, Mp, Kp, ahi, alo);
+    k_pack_psi<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)psi, nb, npw, Np, Kp, bhi, blo);
+    k_pack_pad<<<grid_of((size_t)Mp2 * Kp2), 256, 0, st>>>(Mp2, Kp2, npw, 2 * np, a2hi, a2lo);
+    dim3 gt((Mp2 + 31) / 32, (np + 31) / 32);
+    k_pack_beta_t<<<gt, dim3(32, 8), 0, st>>>((const double2*)beta, np, npw, Mp2, Kp2, a2hi, a2lo);
+    if (pf) pf->launches += 3;
+  }
+  int rc = tc_gemm_tf32x3(ahi, alo, bhi, blo, Mp, Np, Kp, ns1, c1, status, st, pf);
+  if (rc) return rc;
+  {
+    ProfScope ps(pf, "k_combine_p", st);
+    k_combine_p<<<grid_of((size_t)np * nb), 256, 0, st>>>(c1, ns1, Mp, Np, np, nb, P);
+  }
+  rc = dmul(dmat, (const double*)P, (double*)Q, np, nb, st, pf);
+  if (rc) return rc;
+  {
+    ProfScope ps(pf, "k_pack_q", st);
+    k_pack_q<<<grid_of((size_t)Np * Kp2), 256, 0, st>>>(Q, np, nb, Np, Kp2, b2hi, b2lo);
+  }
+  rc = tc_gemm_tf32x3(a2hi, a2lo, b2hi, b2lo, Mp2, Np, Kp2, ns2, c2, status, st, pf);
+  if (rc) return rc;
+  {
+    ProfScope ps(pf, "k_combine_h", st);
+    k_combine_h<<<grid_of((size_t)nb * npw), 256, 0, st>>>(c2, ns2, Mp2, Np, npw, nb, (double2*)hpsi);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("nonlocal_tc: %s", cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+}  // namespace qe
