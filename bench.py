@@ -327,6 +327,9 @@ def run_gpu(args, rank, world, local_rank):
         e2e = {"value": world * nb * esteps / dt, "unit": "bands/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(oh.nbytes), "steps": esteps}
 
+    dav = run_davidson_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
+    srv = run_serve_bench(q, ctx, dev, local_rank) if (rank == 0 and not args.no_solvers) else None
+
     line = None
     if rank == 0:
         cpu = None
@@ -346,11 +349,154 @@ def run_gpu(args, rank, world, local_rank):
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roof,
                 "cpu_baseline": cpu,
                 "mixed": {"value": mixed_value, "unit": "bands/s", "ms_per_step": ms_mixed / args.steps,
-                          "dtype": "fp32 FFT + fp32 SIMT products", "kernels": kernels_mixed},
-                "kernels": kernels, "peaks": pk_kind}
+                          "dtype": "fp32 FFT + TF32x3 tensor-core projector products",
+                          "kernels": kernels_mixed},
+                "kernels": kernels, "peaks": pk_kind, "davidson": dav, "serve": srv}
         print(json.dumps(line), flush=True)
     ctx.close()
     return line
+
+
+def smooth_at_least(n):
+    """Smallest integer >= n whose only prime factors are 2, 3 and 5."""
+    m = max(1, int(n))
+    while True:
+        k = m
+        for f in (2, 3, 5):
+            while k % f == 0:
+                k //= f
+        if k == 1:
+            return m
+        m += 1
+
+
+def min_grid(a, ecut):
+    """N >= 2 floor(2 sqrt(ecut) a / 2 pi) + 1 (the grid holds G up to 2 G_max), 2,3,5-smooth."""
+    return smooth_at_least(2 * int(math.floor(2 * math.sqrt(ecut) * a / (2 * math.pi))) + 1)
+
+
+def device_problem(q, ctx, lat, k, ecut, grid, tau, widths, nb, seed, dev):
+    import torch
+    _, kin = q.gsphere(lat, k, ecut, grid)
+    npw = len(kin)
+    v = torch.empty((grid[2], grid[1], grid[0]), dtype=torch.float64, device=dev)
+    ctx.vloc_gaussian(lat, grid, tau, v)
+    nproj = 4 * len(widths) * len(tau)
+    beta = torch.empty((nproj, npw, 2), dtype=torch.float64, device=dev)
+    ctx.beta_gaussian(lat, k, ecut, tau, widths, beta)
+    d = torch.from_numpy(qeinputs.d_matrix(len(tau), len(widths))).to(dev)
+    psi0 = qeinputs.start_bands(kin, nb, seed)
+    pt = torch.from_numpy(psi0.view(np.float64).reshape(nb, npw, 2).copy()).to(dev)
+    return ctx.problem(lat, k, ecut, grid, v, beta, d, nb), pt, (v, beta, d)
+
+
+def golden(name):
+    p = os.path.join(ROOT, "tests", "golden", name)
+    try:
+        return np.loadtxt(p)
+    except Exception:
+        return None
+
+
+def run_davidson_bench(q, ctx, dev):
+    """Davidson solves/s: C0 (FP64 tol 1e-8, mixed tol 1e-5) and C2 (FP64 tol 1e-6,
+    mixed tol 1e-4), eigenvalue errors against the oracle's stored references."""
+    import torch
+    out = {}
+    specs = [("C0", q.QE_FP64, 1e-8, 5, "c0_dense_eigs.txt"), ("C0", q.QE_MIXED, 1e-5, 5, "c0_dense_eigs.txt"),
+             ("C2", q.QE_FP64, 1e-6, 1, "c2_davidson_eigs.txt"), ("C2", q.QE_MIXED, 1e-4, 1, "c2_davidson_eigs.txt")]
+    for name, prec, tol, reps, gold in specs:
+        c = qeinputs.config(name)
+        prob, pt0, keep = device_problem(q, ctx, c["lat"], c["k"], c["ecut"], c["grid"], c["tau"],
+                                         c["widths"], c["nbnd"], c["psi_seed"], dev)
+        ev = torch.zeros(c["nbnd"], dtype=torch.float64, device=dev)
+        times, iters = [], []
+        for _ in range(reps):
+            pt = pt0.clone()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rc, it = ctx.davidson(prob, pt, ev, None, precision=prec, tol=tol, max_iter=200)
+            torch.cuda.synchronize(dev)
+            times.append(time.perf_counter() - t0)
+            iters.append(it)
+        ref = golden(gold)
+        err = None
+        if ref is not None and len(ref) >= c["nbnd"]:
+            err = float(np.abs(ev.cpu().numpy() - ref[:c["nbnd"]]).max())
+        key = f"{name}_{'fp64' if prec == q.QE_FP64 else 'mixed'}"
+        out[key] = {"solves_per_s": 1.0 / float(np.median(times)), "seconds": float(np.median(times)),
+                    "iters": int(np.median(iters)), "tol": tol, "status": int(rc),
+                    "max_abs_eig_err_ry": err, "nbnd": c["nbnd"]}
+        del prob, pt0, keep
+    for name in ("C0", "C2"):
+        f, m = out.get(f"{name}_fp64"), out.get(f"{name}_mixed")
+        if f and m:
+            out[f"{name}_mixed_speedup"] = m["solves_per_s"] / f["solves_per_s"]
+    return out
+
+
+def serve_requests(q, ctx, n, seed, dev):
+    """Requests drawn like the serving workload, shrunk so that a stream ends in
+    seconds: cubic a in U[10,14] bohr, ecut in U[20,30] Ry, nb in U{8..32},
+    2..16 random atoms, one projector width (4 projectors/atom), minimum
+    2,3,5-smooth grid."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        a = float(rng.uniform(10.0, 14.0))
+        ecut = float(rng.uniform(20.0, 30.0))
+        nb = int(rng.integers(8, 33))
+        natom = int(rng.integers(2, 17))
+        lat = qeinputs.cubic(a)
+        tau = qeinputs.random_atoms(lat, natom, 2.0, seed=1000 + seed * 100 + i)
+        g = min_grid(a, ecut)
+        grid = (g, g, g)
+        prob_d, pt, keep = device_problem(q, ctx, lat, np.zeros(3), ecut, grid, tau, (1.0,), nb, i, dev)
+        v, beta, d = keep
+        vh, bh, dh = v.cpu().numpy().copy(), beta.cpu().numpy().copy(), d.cpu().numpy().copy()
+        ph = pt.cpu().numpy().copy()
+        psi0 = ph[..., 0] + 1j * ph[..., 1]
+        prob = q.problem(lat, np.zeros(3), ecut, grid, vh, bh, dh, nb)
+        reqs.append((prob, psi0, (vh, bh, dh)))
+    return reqs
+
+
+def run_serve_bench(q, ctx, dev, device_index):
+    """Serving: the same request list as a burst (capacity) and as a Poisson
+    stream at 70 % of capacity; latency = submit -> completion."""
+    out = {}
+    reqs = serve_requests(q, ctx, 24, 6, dev)
+    for prec, tol, tag in ((q.QE_FP64, 1e-8, "fp64"), (q.QE_MIXED, 1e-5, "mixed")):
+        with q.Server(device=device_index, budget_bytes=32 << 30, max_slots=4) as s:
+            t0 = time.perf_counter()
+            ts = [s.submit(p, x, precision=prec, tol=tol) for p, x, _ in reqs]
+            res = [s.poll(t) for t in ts]
+            burst = time.perf_counter() - t0
+        cap = len(reqs) / burst
+        rate = 0.7 * cap
+        rng = np.random.default_rng(7)
+        gaps = rng.exponential(1.0 / rate, len(reqs))
+        lat = []
+        with q.Server(device=device_index, budget_bytes=32 << 30, max_slots=4) as s:
+            t0 = time.perf_counter()
+            tickets = []
+            t_next = 0.0
+            for (p, x, _), gap in zip(reqs, gaps):
+                t_next += gap
+                while time.perf_counter() - t0 < t_next:
+                    time.sleep(0.0005)
+                tickets.append(s.submit(p, x, precision=prec, tol=tol))
+            res2 = [s.poll(t) for t in tickets]
+            wall = time.perf_counter() - t0
+        lat = np.array([r["latency_s"] for r in res2]) * 1e3
+        ok = sum(r["status"] == q.QE_OK for r in res2)
+        out[tag] = {"burst_solves_per_s": cap, "stream_rate_per_s": rate,
+                    "stream_solves_per_s": len(reqs) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99)), "converged": ok, "requests": len(reqs),
+                    "slots": 4}
+    out["workload"] = ("24 requests: cubic a~U[10,14] bohr, ecut~U[20,30] Ry, nb~U{8..32}, "
+                       "2-16 atoms, 4 projectors/atom; Poisson arrivals at 0.7 x burst capacity")
+    return out
 
 
 def stick_counts(c):
@@ -369,6 +515,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solvers", action="store_true",
+                    help="skip the Davidson and serving measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

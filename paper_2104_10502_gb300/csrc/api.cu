@@ -243,7 +243,17 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(launch_local_kinetic<T>(P, psi, hpsi, (const T*)ctx->vp.p, ctx->sticks.p, b0, n, st,
                                    &ctx->prof));
   }
-  if (op.nproj > 0) {
+  if (op.nproj > 0 && sizeof(T) == sizeof(float)) {
+    // mixed precision: projector products on the tensor cores (TF32x3 split)
+    const int np = op.nproj;
+    QE_TRY(ctx->tc_work.ensure(nonlocal_tc_bytes(np, nb, npw)));
+    if (!ctx->tc_status.p) {
+      QE_TRY(ctx->tc_status.ensure(256));
+      QE_CU(cudaMemsetAsync(ctx->tc_status.p, 0, 256, st));
+    }
+    QE_TRY(nonlocal_tc(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->tc_work.p, ctx->tc_work.bytes,
+                       (int*)ctx->tc_status.p, st, &ctx->prof));
+  } else if (op.nproj > 0) {
     const int np = op.nproj;
     QE_TRY(ctx->proj.ensure((size_t)np * nb * 2 * sizeof(double)));
     QE_TRY(ctx->projd.ensure((size_t)np * nb * 2 * sizeof(double)));
@@ -254,6 +264,19 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(dmul(op.dmat, (const double*)ctx->proj.p, (double*)ctx->projd.p, np, nb, st, &ctx->prof));
     QE_TRY(gemm_outer<T>(op.beta, npw, (const double*)ctx->projd.p, nb, npw, nb, np, hpsi, npw, 1, st,
                          &ctx->prof));
+  }
+  return QE_OK;
+}
+
+int tc_check(qe_ctx* ctx, cudaStream_t st) {
+  if (!ctx->tc_status.p) return QE_OK;
+  int v = 0;
+  QE_CU(cudaMemcpyAsync(&v, ctx->tc_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  QE_CU(cudaStreamSynchronize(st));
+  if (v != 0) {
+    QE_CU(cudaMemsetAsync(ctx->tc_status.p, 0, sizeof(int), st));
+    set_error("a tensor-core GEMM wait timed out (code %d); its products are invalid", v);
+    return QE_ETIMEOUT;
   }
   return QE_OK;
 }
@@ -413,6 +436,7 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
     if (nb > 0)
       QE_CU(cudaMemcpyAsync(hpsi, dhpsi, nel * sizeof(double), cudaMemcpyDeviceToHost, st));
     QE_CU(cudaStreamSynchronize(st));
+    QE_TRY(tc_check(ctx, st));
   }
   return QE_OK;
 }

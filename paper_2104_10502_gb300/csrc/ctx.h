@@ -21,11 +21,15 @@ struct qe_ctx {
   qe::DevBuf h_v, h_beta, h_d, h_psi, h_hpsi;
   // Davidson workspaces
   qe::DevBuf dv_basis, dv_red;
+  // tensor-core path: packed operands and the kernel's status word (a bounded
+  // wait that ran out writes a non-zero code; read at the next synchronising point)
+  qe::DevBuf tc_work, tc_status;
   qe_ctx() {
     for (qe::DevBuf* b : bufs()) b->sp = &cur;
   }
   std::vector<qe::DevBuf*> bufs() {
-    return {&sticks, &vp, &part, &proj, &projd, &h_v, &h_beta, &h_d, &h_psi, &h_hpsi, &dv_basis, &dv_red};
+    return {&sticks, &vp,       &part,     &proj,   &projd,   &h_v,     &h_beta,
+            &h_d,    &h_psi,    &h_hpsi,   &dv_basis, &dv_red, &tc_work, &tc_status};
   }
 };
 
@@ -52,5 +56,8 @@ int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView
 // H psi for nb bands already on the device.
 int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, const double* psi,
               double* hpsi, int nb, cudaStream_t st);
+// Status word of the tensor-core kernels since the last check (synchronises on
+// `st`); QE_ETIMEOUT with a message if a bounded wait ran out, then resets it.
+int tc_check(qe_ctx* ctx, cudaStream_t st);
 
 }  // namespace qe

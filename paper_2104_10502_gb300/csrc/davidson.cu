@@ -190,7 +190,7 @@ static size_t dv_bytes(size_t npw, size_t nb, size_t md) {
   const size_t big = (2 * md + 5 * nb) * npw * zb;
   const size_t smallz = (5 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
   const size_t dbl = (2 * nb + npw + 1 + 3 * md + nb * md) * sizeof(double);
-  const size_t dwz = 2 * md * zb;
+  const size_t dwz = 3 * md * zb;
   const size_t ints = (nb + 16) * sizeof(int);
   return big + smallz + dbl + dwz + ints + 48 * 256;
 }
@@ -227,8 +227,8 @@ static int dv_alloc(qe_ctx* ctx, DvState& S) {
   const size_t smallz = (5 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
   // doubles: e, rn [nb]; hd [npw]; vmean; dense work: d, e, piv [md], y [nb][md]
   const size_t dbl = (2 * nb + npw + 1 + 3 * md + nb * md) * sizeof(double);
-  // dense work complex: tau, p [md]
-  const size_t dwz = 2 * md * zb;
+  // dense work complex: tau, p, vbuf [md]
+  const size_t dwz = 3 * md * zb;
   const size_t ints = (nb + 16) * sizeof(int);
   const size_t total = big + smallz + dbl + dwz + ints + 48 * 256;   // + alignment of 31 pieces
   if (total != dv_bytes(npw, nb, md)) {
@@ -266,8 +266,12 @@ static int dv_alloc(qe_ctx* ctx, DvState& S) {
   S.dw.y = (double*)take(nb * md * sizeof(double));
   S.dw.tau = (z*)take(md * zb);
   S.dw.p = (z*)take(md * zb);
+  S.dw.vbuf = (z*)take(md * zb);
   S.idx = (int*)take(nb * sizeof(int));
   S.dw.status = (int*)take(16 * sizeof(int));
+  S.dw.bar.count = reinterpret_cast<unsigned int*>(S.dw.status + 4);
+  S.dw.bar.gen = S.dw.bar.count + 1;
+  S.dw.bar.err = S.dw.status + 8;
   if ((size_t)(p - (char*)ctx->dv_basis.p) > ctx->dv_basis.bytes) {
     set_error("davidson: workspace layout overflow");
     return QE_EINVAL;
@@ -309,8 +313,8 @@ static int rayleigh_ritz(DvState& S, int n, cudaStream_t st, Prof* pf) {
   DV_CU(cudaMemcpy2DAsync(S.Zw, n * zb, S.Hr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
   {
     ProfScope ps(pf, "rr_cholesky", st);
-    DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, st));
-    pf->launches += n;                                            // n + 1 kernels in the scope
+    DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, S.dw.bar, st));
+
   }
   {
     ProfScope ps(pf, "rr_reduce", st);
@@ -320,11 +324,7 @@ static int rayleigh_ritz(DvState& S, int n, cudaStream_t st, Prof* pf) {
     DV_TRY(hermitize(S.Aw, n, n, st));
     pf->launches += 3;
   }
-  {
-    ProfScope ps(pf, "rr_heev", st);
-    DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st));
-    pf->launches += 3 * (n - 1) + 3;
-  }
+  DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf));
   {
     ProfScope ps(pf, "rr_backsub", st);
     DV_TRY(trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st));            // X = L^-+ Y
@@ -349,7 +349,7 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
     DV_TRY(gram<T>(S, cur, ncur, cur, ncur, S.G, ncur, st, pf));
     DV_TRY(hermitize(S.G, ncur, ncur, st));
     DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
-    DV_TRY(cholesky(S.G, ncur, ncur, drop * drop, true, S.dw.piv, S.dw.status, st));
+    DV_TRY(cholesky(S.G, ncur, ncur, drop * drop, true, S.dw.piv, S.dw.status, S.dw.bar, st));
     std::vector<double> piv(ncur);
     DV_CU(cudaMemcpyAsync(piv.data(), S.dw.piv, ncur * sizeof(double), cudaMemcpyDeviceToHost, st));
     DV_CU(cudaStreamSynchronize(st));
@@ -382,6 +382,30 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
   return QE_OK;
 }
 
+// Mixed-precision defect correction: one FP64 H|psi> of the Ritz vectors and a
+// FP64 Rayleigh-Ritz on their span.  The FP32 accumulation of the reduced
+// matrices over ~1e4-1e5 plane waves leaves ~1e-5 relative noise in H_r; this
+// last step brings the eigenvalue error down to O(residual^2 / gap) and reports
+// FP64 residual norms of the returned vectors.
+static int refine_fp64(qe_ctx* ctx, const DevPlan& P, const OpView& op, DvState& S, cudaStream_t st) {
+  Prof* pf = &ctx->prof;
+  const int npw = S.npw, nb = S.nb, md = S.max_dim;
+  const size_t zb = sizeof(z);
+  DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+  DV_TRY(hpsi_core(ctx, P, op, QE_FP64, (const double*)S.V, (double*)S.HV, nb, st));
+  DV_TRY(update_reduced<double>(S, 0, nb, st, pf));
+  DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
+  DV_TRY(rayleigh_ritz(S, nb, st, pf));
+  DV_TRY(gemm_outer_ab<double>((const double*)S.V, npw, (const double*)S.X, nb, npw, nb, nb,
+                               (double*)S.Psi, npw, 0, 0, st, pf));
+  DV_TRY(gemm_outer_ab<double>((const double*)S.HV, npw, (const double*)S.X, nb, npw, nb, nb,
+                               (double*)S.HPsi, npw, 0, 0, st, pf));
+  k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
+  DV_TRY(check_launch("k_resid"));
+  (void)md;
+  return QE_OK;
+}
+
 template <typename T>
 static int davidson_run(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, double tol,
                         int max_iter, DvState& S, int* iters, bool* converged, cudaStream_t st) {
@@ -396,6 +420,7 @@ static int davidson_run(qe_ctx* ctx, const DevPlan& P, const OpView& op, int pre
   k_hdiag<<<(npw + 255) / 256, 256, 0, st>>>(P.kin, S.vmean, (const z*)op.beta, op.dmat, op.nproj,
                                               npw, S.hd);
   DV_TRY(check_launch("k_hdiag"));
+  DV_CU(cudaMemsetAsync(S.dw.status, 0, 16 * sizeof(int), st));
   // start block
   DV_TRY(hpsi_core(ctx, P, op, precision, (const double*)S.V, (double*)S.HV, nb, st));
   int n = nb;
@@ -405,7 +430,7 @@ static int davidson_run(qe_ctx* ctx, const DevPlan& P, const OpView& op, int pre
   std::vector<double> e(nb), rn(nb);
   *converged = false;
   while (true) {
-    DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
+    DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));   // keeps the barrier error word
     DV_TRY(rayleigh_ritz(S, n, st, pf));
     DV_TRY(gemm_outer_ab<T>((const double*)S.V, npw, (const double*)S.X, nb, npw, nb, n,
                             (double*)S.Psi, npw, 0, 0, st, pf));
@@ -421,13 +446,19 @@ static int davidson_run(qe_ctx* ctx, const DevPlan& P, const OpView& op, int pre
     }
     k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
     DV_TRY(check_launch("k_resid"));
-    int status = 0;
+    int status[16];
     DV_CU(cudaMemcpyAsync(e.data(), S.e, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     DV_CU(cudaMemcpyAsync(rn.data(), S.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-    DV_CU(cudaMemcpyAsync(&status, S.dw.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DV_CU(cudaMemcpyAsync(status, S.dw.status, sizeof(status), cudaMemcpyDeviceToHost, st));
     DV_CU(cudaStreamSynchronize(st));
-    if (status != 0) {
-      set_error("davidson: reduced overlap matrix not positive definite (column %d)", status - 1);
+    DV_TRY(tc_check(ctx, st));
+    if (status[8] != 0) {
+      set_error("davidson: a grid barrier of the dense eigensolver timed out");
+      *iters = it;
+      return QE_ETIMEOUT;
+    }
+    if (status[0] != 0) {
+      set_error("davidson: reduced overlap matrix not positive definite (column %d)", status[0] - 1);
       *iters = it;
       return QE_ENOCONV;
     }
@@ -456,6 +487,7 @@ static int davidson_run(qe_ctx* ctx, const DevPlan& P, const OpView& op, int pre
     n += nk;
   }
   *iters = it;
+  if (precision != QE_FP64) DV_TRY(refine_fp64(ctx, P, op, S, st));
   return QE_OK;
 }
 
@@ -508,7 +540,12 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   DV_CU(cudaMemcpyAsync(psi_inout, S.Psi, bytes, out_kind, st));
   DV_CU(cudaMemcpyAsync(evals, S.e, nb * sizeof(double), out_kind, st));
   if (resid) DV_CU(cudaMemcpyAsync(resid, S.rn, nb * sizeof(double), out_kind, st));
+  int fin[16];
+  DV_CU(cudaMemcpyAsync(fin, S.dw.status, sizeof(fin), cudaMemcpyDeviceToHost, st));
   DV_CU(cudaStreamSynchronize(st));
+  if (fin[8] != 0) { set_error("qe_davidson: a grid barrier of the dense eigensolver timed out"); return QE_ETIMEOUT; }
+  if (fin[0] != 0) { set_error("qe_davidson: final overlap matrix not positive definite"); return QE_ENOCONV; }
+  DV_TRY(tc_check(ctx, st));
   if (rc == QE_ENOCONV) return rc;
   if (!conv) {
     set_error("qe_davidson: not converged after %d iterations", it);

@@ -54,61 +54,123 @@ __device__ double block_sum(double v, double* sh) {
   return sh[32];
 }
 
-// ---- Cholesky ------------------------------------------------------------------
-// Step j of the right-looking factorisation of the lower triangle.  Column j is
-// left unscaled; its pivot sqrt(d_j) goes to piv[j] (0 when dropped).
-__global__ void k_chol_step(z* A, int n, int lda, int j, double drop2, int allow_drop,
-                            double* piv, int* status) {
-  const double d = A[(size_t)j * lda + j].x;
-  const bool keep = allow_drop ? (d > drop2) : (d > 0.0);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    piv[j] = keep ? sqrt(d) : 0.0;
-    if (!keep && !allow_drop) *status = 1 + j;
+// ---- persistent (cooperative) kernels -------------------------------------------
+// Loads of data that other CTAs wrote earlier in the same kernel go through L2
+// (ld.global.cg): L1 is not coherent across SMs.
+__device__ __forceinline__ z ldz(const z* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned long long gtime_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every wait
+// is bounded (2 s); on time-out the error word is set, every later barrier
+// returns false at once and the kernel leaves.
+__device__ bool grid_sync(const GridBar& b) {
+  __syncthreads();
+  if (threadIdx.x == 0 && *(volatile int*)b.err == 0) {
+    const unsigned int g = *(volatile unsigned int*)b.gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      const unsigned long long t0 = gtime_ns();
+      while (*(volatile unsigned int*)b.gen == g) {
+        if (*(volatile int*)b.err) break;
+        if (gtime_ns() - t0 > 2000000000ull) { atomicExch(b.err, 1); break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
   }
-  if (!keep) return;
-  const double inv = 1.0 / d;
-  const int m = n - j - 1;
-  const size_t total = (size_t)m * m;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int r = j + 1 + (int)(t / m), c = j + 1 + (int)(t % m);
-    if (c > r) continue;
-    const z arj = A[(size_t)r * lda + j], acj = A[(size_t)c * lda + j];
-    // A[r][c] -= a_rj conj(a_cj) / d
-    z& a = A[(size_t)r * lda + c];
-    a.x -= (arj.x * acj.x + arj.y * acj.y) * inv;
-    a.y -= (arj.y * acj.x - arj.x * acj.y) * inv;
+  __syncthreads();
+  return *(volatile int*)b.err == 0;
+}
+
+// Cholesky of the lower triangle, all columns in one launch (one barrier per column).
+__global__ void __launch_bounds__(256) k_chol_coop(z* A, int n, int lda, double drop2, int allow_drop,
+                                                   double* piv, int* status, GridBar bar) {
+  const size_t nthr = (size_t)gridDim.x * blockDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int j = 0; j < n; ++j) {
+    const double d = ldz(&A[(size_t)j * lda + j]).x;
+    const bool keep = allow_drop ? (d > drop2) : (d > 0.0);
+    if (gtid == 0) {
+      piv[j] = keep ? sqrt(d) : 0.0;
+      if (!keep && !allow_drop) *status = 1 + j;
+    }
+    if (keep) {
+      const double inv = 1.0 / d;
+      const int m = n - j - 1;
+      const size_t total = (size_t)m * m;
+      for (size_t t = gtid; t < total; t += nthr) {
+        const int r = j + 1 + (int)(t / m), c = j + 1 + (int)(t % m);
+        if (c > r) continue;
+        const z arj = ldz(&A[(size_t)r * lda + j]), acj = ldz(&A[(size_t)c * lda + j]);
+        z& a = A[(size_t)r * lda + c];
+        const z av = ldz(&a);
+        a = {av.x - (arj.x * acj.x + arj.y * acj.y) * inv, av.y - (arj.y * acj.x - arj.x * acj.y) * inv};
+      }
+    }
+    if (!grid_sync(bar)) return;
+  }
+  const size_t total = (size_t)n * n;
+  for (size_t t = gtid; t < total; t += nthr) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    z& a = A[(size_t)i * lda + j];
+    const double pj = ldd(&piv[j]);
+    if (j > i || pj == 0.0) { a = {0.0, 0.0}; continue; }
+    if (i == j) { a = {pj, 0.0}; continue; }
+    const z av = ldz(&a);
+    a = {av.x / pj, av.y / pj};
   }
 }
 
-// L[i][j] = A[i][j] / piv[j] for i >= j (0 for dropped columns); upper part zeroed.
-__global__ void k_chol_finish(z* A, int n, int lda, const double* piv) {
-  const size_t total = (size_t)n * n;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / n), j = (int)(t % n);
-    z& a = A[(size_t)i * lda + j];
-    if (j > i || piv[j] == 0.0) { a = {0.0, 0.0}; continue; }
-    if (i == j) { a = {piv[j], 0.0}; continue; }
-    const double s = 1.0 / piv[j];
-    a = {a.x * s, a.y * s};
+// ---- Cholesky ------------------------------------------------------------------
+static int coop_blocks(const void* f, size_t work_items, size_t smem = 0) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, 256, smem);
+  const int cap = std::max(1, nsm * std::max(1, std::min(occ, 2)));
+  const int want = (int)std::max<size_t>(1, (work_items + 4095) / 4096);
+  return std::min(cap, want);
+}
+
+static int launch_coop(const void* f, int blocks, void** args, cudaStream_t st, const char* what,
+                       size_t smem = 0) {
+  cudaError_t e = cudaLaunchCooperativeKernel(f, dim3(blocks), dim3(256), args, smem, st);
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return QE_ECUDA;
   }
+  return QE_OK;
 }
 
 int cholesky(z* A, int n, int lda, double drop2, bool allow_drop, double* piv, int* status,
-             cudaStream_t st) {
-  for (int j = 0; j < n; ++j) {
-    const size_t m = (size_t)(n - j - 1) * (n - j - 1);
-    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((m + 255) / 256, 152 * 4));
-    k_chol_step<<<blocks, 256, 0, st>>>(A, n, lda, j, drop2, allow_drop ? 1 : 0, piv, status);
+             GridBar bar, cudaStream_t st) {
+  if (n <= 0) return QE_OK;
+  if (cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
+    set_error("cholesky: memset failed");
+    return QE_ECUDA;
   }
-  const size_t total = (size_t)n * n;
-  k_chol_finish<<<(int)std::min<size_t>((total + 255) / 256, 152 * 4), 256, 0, st>>>(A, n, lda, piv);
-  return check_launch("cholesky");
+  int allow = allow_drop ? 1 : 0;
+  void* args[] = {&A, &n, &lda, &drop2, &allow, &piv, &status, &bar};
+  const int blocks = coop_blocks((const void*)k_chol_coop, (size_t)n * n / 2);
+  return launch_coop((const void*)k_chol_coop, blocks, args, st, "k_chol_coop");
 }
 
 // ---- triangular solves ---------------------------------------------------------
-constexpr int TCOLS = 8;
+constexpr int TCOLS = 4;
 
 // L X = B, L lower with real positive diagonal; B [n][ldb], columns c0.. of this CTA.
 __global__ void __launch_bounds__(256) k_trsm_lower(const z* L, int n, int ldl, z* B, int ldb,
@@ -209,92 +271,103 @@ int hermitize(z* A, int n, int lda, cudaStream_t st) {
   return check_launch("k_hermitize");
 }
 
-// ---- Householder tridiagonalisation ------------------------------------------------
-// Reflector of step j from x = A[j+1 .. n-1][j]: H = I - tau v v^+, v_0 = 1, with
-// H^+ x = beta e_1, beta real.  v_1.. are stored in A[j+2 ..][j]; A[j+1][j] = beta.
-__global__ void k_house(z* A, int n, int lda, int j, z* tau, double* e) {
-  __shared__ double sh[33];
-  const int m = n - j - 1;
-  const z alpha = A[(size_t)(j + 1) * lda + j];
-  double s = 0.0;
-  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += zabs2(A[(size_t)(j + 1 + i) * lda + j]);
-  const double sigma = block_sum(s, sh);
-  if (sigma == 0.0 && alpha.y == 0.0) {
-    if (threadIdx.x == 0) { tau[j] = {0.0, 0.0}; e[j] = alpha.x; }
-    return;
-  }
-  const double nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sigma);
-  const double beta = alpha.x >= 0.0 ? -nu : nu;
-  // scale = 1 / (alpha - beta)
-  const z am = {alpha.x - beta, alpha.y};
-  const double den = am.x * am.x + am.y * am.y;
-  const z sc = {am.x / den, -am.y / den};
-  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
-    z& x = A[(size_t)(j + 1 + i) * lda + j];
-    x = cmul(x, sc);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
-    e[j] = beta;
-    A[(size_t)(j + 1) * lda + j] = {beta, 0.0};
-  }
-}
-
+// ---- Householder reflectors ----------------------------------------------------------
+// Step j: H = I - tau v v^+, v_0 = 1, H^+ x = beta e_1 with beta real, where x is
+// column j below the diagonal; v_1.. are stored in A[j+2 ..][j], A[j+1][j] = beta.
 __device__ __forceinline__ z house_v(const z* A, int lda, int j, int r) {
   // component r (absolute row index, r >= j+1) of the reflector of step j
   return r == j + 1 ? z{1.0, 0.0} : A[(size_t)r * lda + j];
 }
 
-// p_r = tau * sum_c A[r][c] v_c over the trailing block; one warp per row.
-__global__ void k_tri_matvec(const z* A, int n, int lda, int j, const z* tau, z* p) {
-  const z t = tau[j];
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int r = j + 1 + warp;
-  if (r >= n) return;
-  z s = {0.0, 0.0};
-  if (t.x != 0.0 || t.y != 0.0) {
-    for (int c = j + 1 + lane; c < n; c += 32) s = cadd(s, cmul(A[(size_t)r * lda + c], house_v(A, lda, j, c)));
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-  }
-  if (lane == 0) p[r] = cmul(t, s);
-}
-
-// w = p - (1/2) conj(tau) (v^+ p) v;  A -= v w^+ + w v^+ on the trailing block.
-__global__ void k_tri_update(z* A, int n, int lda, int j, const z* tau, const z* p) {
+// Householder tridiagonalisation, all steps in one launch (three barriers per
+// step).  The reflector v of step j is also written contiguously to vbuf; every
+// CTA stages v (and w) of the step in shared memory, so the matvec and the
+// rank-2 update stream only the trailing block of A.
+// Dynamic shared memory: 2 n complex.
+__global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* tau, double* e, z* p,
+                                                      double* dg, z* vbuf, GridBar bar) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  z* sv = reinterpret_cast<z*>(smem_raw);
+  z* sw = sv + n;
   __shared__ double sh[33];
-  const z t = tau[j];
-  if (t.x == 0.0 && t.y == 0.0) return;
-  double sr = 0.0, si = 0.0;
-  for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
-    const z v = house_v(A, lda, j, r), pr = p[r];
-    sr += v.x * pr.x + v.y * pr.y;    // conj(v) p
-    si += v.x * pr.y - v.y * pr.x;
+  const size_t nthr = (size_t)gridDim.x * blockDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nwarp = (int)(nthr >> 5), gwarp = (int)(gtid >> 5), lane = threadIdx.x & 31;
+  for (int j = 0; j < n - 1; ++j) {
+    const int m = n - j - 1;
+    // reflector of column j (one CTA)
+    if (blockIdx.x == 0) {
+      const z alpha = ldz(&A[(size_t)(j + 1) * lda + j]);
+      double s = 0.0;
+      for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += zabs2(ldz(&A[(size_t)(j + 1 + i) * lda + j]));
+      const double sigma = block_sum(s, sh);
+      if (sigma == 0.0 && alpha.y == 0.0) {
+        if (threadIdx.x == 0) { tau[j] = {0.0, 0.0}; e[j] = alpha.x; }
+      } else {
+        const double nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sigma);
+        const double beta = alpha.x >= 0.0 ? -nu : nu;
+        const z am = {alpha.x - beta, alpha.y};
+        const double den = am.x * am.x + am.y * am.y;
+        const z sc = {am.x / den, -am.y / den};
+        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
+          z* x = &A[(size_t)(j + 1 + i) * lda + j];
+          const z v = cmul(ldz(x), sc);
+          *x = v;
+          vbuf[i] = v;
+        }
+        if (threadIdx.x == 0) {
+          tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
+          e[j] = beta;
+          A[(size_t)(j + 1) * lda + j] = {beta, 0.0};
+          vbuf[0] = {1.0, 0.0};
+        }
+      }
+    }
+    if (!grid_sync(bar)) return;
+    const z t = ldz(&tau[j]);
+    const bool active = t.x != 0.0 || t.y != 0.0;
+    if (active) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = ldz(&vbuf[i]);
+      __syncthreads();
+      // p = tau A v over the trailing block (one warp per row)
+      for (int w = gwarp; w < m; w += nwarp) {
+        const z* row = A + (size_t)(j + 1 + w) * lda + (j + 1);
+        z acc = {0.0, 0.0};
+        for (int c = lane; c < m; c += 32) acc = cadd(acc, cmul(ldz(row + c), sv[c]));
+        for (int o = 16; o > 0; o >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) p[j + 1 + w] = cmul(t, acc);
+      }
+    }
+    if (!grid_sync(bar)) return;
+    // A -= v w^+ + w v^+, w = p - (1/2) conj(tau) (v^+ p) v
+    if (active) {
+      double sr = 0.0, si = 0.0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const z v = sv[i], pr = ldz(&p[j + 1 + i]);
+        sw[i] = pr;
+        sr += v.x * pr.x + v.y * pr.y;
+        si += v.x * pr.y - v.y * pr.x;
+      }
+      const double vpr = block_sum(sr, sh);
+      const double vpi = block_sum(si, sh);
+      const z coef = {0.5 * (t.x * vpr + t.y * vpi), 0.5 * (t.x * vpi - t.y * vpr)};
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = csub(sw[i], cmul(coef, sv[i]));
+      __syncthreads();
+      const size_t total = (size_t)m * m;
+      for (size_t q = gtid; q < total; q += nthr) {
+        const int r = (int)(q / m), c = (int)(q % m);
+        const z vr = sv[r], vc = sv[c], wr = sw[r], wc = sw[c];
+        const z dlt = cadd(cmul(vr, zconj(wc)), cmul(wr, zconj(vc)));
+        z* a = &A[(size_t)(j + 1 + r) * lda + (j + 1 + c)];
+        *a = csub(ldz(a), dlt);
+      }
+    }
+    if (!grid_sync(bar)) return;
   }
-  const double vpr = block_sum(sr, sh);
-  const double vpi = block_sum(si, sh);
-  // coef = 0.5 conj(tau) (v^+ p)
-  const z coef = {0.5 * (t.x * vpr + t.y * vpi), 0.5 * (t.x * vpi - t.y * vpr)};
-  const int m = n - j - 1;
-  const size_t total = (size_t)m * m;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
-       q += (size_t)gridDim.x * blockDim.x) {
-    const int r = j + 1 + (int)(q / m), c = j + 1 + (int)(q % m);
-    const z vr = house_v(A, lda, j, r), vc = house_v(A, lda, j, c);
-    const z wr = csub(p[r], cmul(coef, vr)), wc = csub(p[c], cmul(coef, vc));
-    // A[r][c] -= vr conj(wc) + wr conj(vc)
-    const z d = cadd(cmul(vr, zconj(wc)), cmul(wr, zconj(vc)));
-    z& a = A[(size_t)r * lda + c];
-    a = csub(a, d);
-  }
-}
-
-__global__ void k_tri_diag(const z* A, int n, int lda, double* d) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    d[i] = A[(size_t)i * lda + i].x;
+  for (size_t i = gtid; i < (size_t)n; i += nthr) dg[i] = ldz(&A[i * lda + i]).x;
 }
 
 // ---- tridiagonal eigenvalues: Sturm bisection, one thread per eigenvalue --------
@@ -311,27 +384,49 @@ __device__ int sturm_count(const double* d, const double* e, int n, double x, do
   return cnt;
 }
 
-__global__ void k_bisect(const double* d, const double* e, int n, int nev, double* w) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per eigenvalue: multisection.  Each round the 32 lanes evaluate the
+// Sturm count at 32 interior points of the current bracket and the bracket
+// shrinks to the sub-interval holding the (k+1)-th eigenvalue (a factor 33 per
+// round instead of 2 for bisection).
+__global__ void __launch_bounds__(64) k_bisect(const double* d, const double* e, int n, int nev,
+                                                double* w) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (k >= nev) return;
-  double lo = d[0], hi = d[0], nrm = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
-    lo = fmin(lo, d[i] - r);
-    hi = fmax(hi, d[i] + r);
+  double lo = 0.0, hi = 0.0;
+  {
+    double l = 1e300, h = -1e300;
+    for (int i = lane; i < n; i += 32) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+      l = fmin(l, d[i] - r);
+      h = fmax(h, d[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
+      h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+    }
+    lo = l;
+    hi = h;
   }
-  nrm = fmax(fabs(lo), fabs(hi));
+  const double nrm = fmax(fabs(lo), fabs(hi));
   const double tiny = 1e-300 + 1e-30 * nrm;
   lo -= 1e-14 * nrm + 1e-300;
   hi += 1e-14 * nrm + 1e-300;
-  for (int it = 0; it < 256; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
+  for (int it = 0; it < 64; ++it) {
     if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
-    if (sturm_count(d, e, n, mid, tiny) > k) hi = mid;
-    else lo = mid;
+    const double step = (hi - lo) / 33.0;
+    const double x = lo + step * (lane + 1);
+    const int c = (x > lo && x < hi) ? sturm_count(d, e, n, x, tiny) : (x <= lo ? 0 : n);
+    // lanes whose point has more than k eigenvalues below it bound from above
+    const unsigned above = __ballot_sync(0xffffffffu, c > k);
+    const int first = above ? __ffs(above) - 1 : 32;    // first lane with count > k
+    const double nlo = first == 0 ? lo : lo + step * first;
+    const double nhi = first == 32 ? hi : lo + step * (first + 1);
+    if (!(nhi < hi || nlo > lo)) break;                 // no progress at this resolution
+    lo = nlo;
+    hi = nhi;
   }
-  w[k] = 0.5 * (lo + hi);
+  if (lane == 0) w[k] = 0.5 * (lo + hi);
 }
 
 // ---- tridiagonal eigenvectors: inverse iteration --------------------------------------
@@ -475,24 +570,32 @@ __global__ void __launch_bounds__(256) k_backtransform(const z* A, int n, int ld
 }
 
 int heev_lowest(z* A, int n, int lda, int nev, double* w, z* X, int ldx, DenseWork& wk,
-                cudaStream_t st) {
+                cudaStream_t st, Prof* pf) {
   if (n <= 0 || nev <= 0) return QE_OK;
   if (nev > n || n > kMaxDense) {
     set_error("heev_lowest: n = %d, nev = %d (max n %d)", n, nev, kMaxDense);
     return QE_EINVAL;
   }
-  for (int j = 0; j < n - 1; ++j) {
-    k_house<<<1, 256, 0, st>>>(A, n, lda, j, wk.tau, wk.e);
-    const int m = n - j - 1;
-    k_tri_matvec<<<(m * 32 + 255) / 256, 256, 0, st>>>(A, n, lda, j, wk.tau, wk.p);
-    const size_t mm = (size_t)m * m;
-    k_tri_update<<<(int)std::max<size_t>(1, std::min<size_t>((mm + 255) / 256, 152 * 4)), 256, 0, st>>>(
-        A, n, lda, j, wk.tau, wk.p);
+  if (cudaMemsetAsync(wk.bar.count, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
+    set_error("heev_lowest: memset failed");
+    return QE_ECUDA;
   }
-  k_tri_diag<<<(n + 255) / 256, 256, 0, st>>>(A, n, lda, wk.d);
-  int rc = check_launch("tridiagonalisation");
-  if (rc) return rc;
-  k_bisect<<<(nev + 127) / 128, 128, 0, st>>>(wk.d, wk.e, n, nev, w);
+  {
+    GridBar bar = wk.bar;
+    void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.p, &wk.d, &wk.vbuf, &bar};
+    const size_t tsm = 2 * (size_t)n * sizeof(z);
+    set_max_dynamic_smem(k_tridiag_coop);
+    const int blocks = coop_blocks((const void*)k_tridiag_coop, (size_t)n * n, tsm);
+    ProfScope ps(pf, "heev_tridiag", st);
+    int rc0 = launch_coop((const void*)k_tridiag_coop, blocks, args, st, "k_tridiag_coop", tsm);
+    if (rc0) return rc0;
+  }
+  int rc = QE_OK;
+  {
+    ProfScope ps(pf, "heev_bisect", st);
+    // two warps per block: the Sturm counts are FP64-bound, so spread them over the SMs
+    k_bisect<<<(nev * 32 + 63) / 64, 64, 0, st>>>(wk.d, wk.e, n, nev, w);
+  }
   rc = check_launch("k_bisect");
   if (rc) return rc;
   const size_t ism = (size_t)n * (5 * sizeof(double) + sizeof(int));
@@ -500,11 +603,17 @@ int heev_lowest(z* A, int n, int lda, int nev, double* w, z* X, int ldx, DenseWo
   set_max_dynamic_smem(k_inviter);
   set_max_dynamic_smem(k_backtransform);
   // eigenvalues within 1e-10 of each other (relative to the spread of T) share a cluster
-  k_inviter<<<nev, 256, ism, st>>>(wk.d, wk.e, n, nev, w, wk.ctol_rel, wk.y);
+  {
+    ProfScope ps(pf, "heev_inviter", st);
+    k_inviter<<<nev, 256, ism, st>>>(wk.d, wk.e, n, nev, w, wk.ctol_rel, wk.y);
+  }
   rc = check_launch("k_inviter");
   if (rc) return rc;
   const size_t bsm = (size_t)n * sizeof(z);
-  k_backtransform<<<nev, 256, bsm, st>>>(A, n, lda, wk.tau, wk.y, X, ldx);
+  {
+    ProfScope ps(pf, "heev_backtransform", st);
+    k_backtransform<<<nev, 256, bsm, st>>>(A, n, lda, wk.tau, wk.y, X, ldx);
+  }
   return check_launch("k_backtransform");
 }
 

@@ -115,6 +115,17 @@ template <typename T>
 int gemm_outer_ab(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
                   double* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf);
 
+// ---- tensor-core (tcgen05, TF32x3) path of the mixed-precision nonlocal term ----
+// Real split-precision GEMM on padded K-major operands (tcgemm.cu).
+int tc_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int Mp,
+                   int Np, int Kp, int nsplit, float* C, int* status, cudaStream_t st, Prof* pf);
+int tc_gemm_splits(int Mp, int Np, int Kp);
+// hpsi += beta^T D (conj(beta) psi^T) on the tensor cores; work of nonlocal_tc_bytes().
+size_t nonlocal_tc_bytes(int np, int nb, int npw);
+int nonlocal_tc(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
+                int nb, int npw, void* work, size_t work_bytes, int* status, cudaStream_t st,
+                Prof* pf);
+
 // Q[i][n] = sum_j D[i][j] P[j][n] (D real [np][np], P complex [np][nb]).
 int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf);
 

@@ -154,3 +154,18 @@ def test_rejects_small_basis(q, ctx):
     with pytest.raises(q.QEError) as e:
         ctx.davidson(prob, pt, ev, None, tol=1e-8, max_dim=c["nbnd"] + 1)
     assert e.value.code == q.QE_EINVAL
+
+
+def test_c2_full_size_fp64_and_mixed_against_oracle(q, ctx):
+    """The C2 workload (C1 cell, 256 bands, 34 265 plane waves): FP64 within
+    1e-10 Ry and mixed precision within 1e-6 Ry of the oracle's Davidson."""
+    c, prob, pt0, keep = _setup(q, ctx, "C2")
+    ref = _golden("c2_davidson_eigs.txt")
+    pt = pt0.clone()
+    rc, it, ev, rs = _solve(q, ctx, prob, pt, 1e-4, precision=q.QE_MIXED, max_iter=200)
+    assert rc == q.QE_OK
+    assert np.abs(ev - ref).max() <= 1e-6
+    pt = pt0.clone()
+    rc, it, ev, rs = _solve(q, ctx, prob, pt, 1e-6, max_iter=200)
+    assert rc == q.QE_OK
+    assert np.abs(ev - ref).max() <= 1e-10
