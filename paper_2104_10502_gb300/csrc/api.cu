@@ -100,6 +100,7 @@ int ctx_begin(qe_ctx* ctx, cudaStream_t st) {
 
 int ctx_trim(qe_ctx* ctx) {
   for (DevBuf* b : ctx->bufs()) b->release();
+  ctx->tc_beta_tag = 0;
   for (auto& p : ctx->plans)
     if (p->block) cudaFreeAsync(p->block, ctx->cur);
   ctx->plans.clear();
@@ -207,6 +208,7 @@ int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView
   const size_t nbeta = (size_t)pr->nproj * P.h.npw * 2;
   const size_t nd = (size_t)pr->nproj * pr->nproj;
   op.nproj = pr->nproj;
+  op.tag = ++ctx->op_tag;
   if (pr->mem == QE_DEVICE) {
     op.vloc = pr->vloc_r;
     op.beta = pr->beta;
@@ -251,8 +253,14 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
       QE_TRY(ctx->tc_status.ensure(256));
       QE_CU(cudaMemsetAsync(ctx->tc_status.p, 0, 256, st));
     }
-    QE_TRY(nonlocal_tc(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->tc_work.p, ctx->tc_work.bytes,
-                       (int*)ctx->tc_status.p, st, &ctx->prof));
+    const void* before = ctx->tc_beta.p;
+    const size_t before_bytes = ctx->tc_beta.bytes;
+    QE_TRY(ctx->tc_beta.ensure(nonlocal_tc_beta_bytes(np, npw)));
+    if (ctx->tc_beta.p != before || ctx->tc_beta.bytes != before_bytes) ctx->tc_beta_tag = 0;
+    const bool pack = ctx->tc_beta_tag == 0 || ctx->tc_beta_tag != op.tag;
+    QE_TRY(nonlocal_tc(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->tc_beta.p, pack,
+                       ctx->tc_work.p, ctx->tc_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof));
+    ctx->tc_beta_tag = op.tag;
   } else if (op.nproj > 0) {
     const int np = op.nproj;
     QE_TRY(ctx->proj.ensure((size_t)np * nb * 2 * sizeof(double)));

@@ -23,19 +23,23 @@ struct qe_ctx {
   qe::DevBuf dv_basis, dv_red;
   // tensor-core path: packed operands and the kernel's status word (a bounded
   // wait that ran out writes a non-zero code; read at the next synchronising point)
-  qe::DevBuf tc_work, tc_status;
+  qe::DevBuf tc_work, tc_status, tc_beta;
+  // the packed beta in tc_beta belongs to the operator with this tag (0: none);
+  // every API call that takes an operator gets a fresh tag
+  unsigned long long tc_beta_tag = 0, op_tag = 0;
   qe_ctx() {
     for (qe::DevBuf* b : bufs()) b->sp = &cur;
   }
   std::vector<qe::DevBuf*> bufs() {
     return {&sticks, &vp,       &part,     &proj,   &projd,   &h_v,     &h_beta,
-            &h_d,    &h_psi,    &h_hpsi,   &dv_basis, &dv_red, &tc_work, &tc_status};
+            &h_d,    &h_psi,    &h_hpsi,   &dv_basis, &dv_red, &tc_work, &tc_status, &tc_beta};
   }
 };
 
 namespace qe {
 
 struct OpView {
+  unsigned long long tag = 0;   // identifies the operator within one API call
   int nproj = 0;
   const double* vloc = nullptr;
   const double* beta = nullptr;

@@ -141,7 +141,8 @@ static int coop_blocks(const void* f, size_t work_items, size_t smem = 0) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, 256, smem);
-  const int cap = std::max(1, nsm * std::max(1, std::min(occ, 2)));
+  // one CTA per SM at most: fewer arrivals per grid barrier
+  const int cap = std::max(1, nsm * std::max(1, std::min(occ, 1)));
   const int want = (int)std::max<size_t>(1, (work_items + 4095) / 4096);
   return std::min(cap, want);
 }
@@ -279,10 +280,42 @@ __device__ __forceinline__ z house_v(const z* A, int lda, int j, int r) {
   return r == j + 1 ? z{1.0, 0.0} : A[(size_t)r * lda + j];
 }
 
-// Householder tridiagonalisation, all steps in one launch (three barriers per
-// step).  The reflector v of step j is also written contiguously to vbuf; every
-// CTA stages v (and w) of the step in shared memory, so the matvec and the
-// rank-2 update stream only the trailing block of A.
+// Reflector of step j from the updated column j (rows j+1 ..), computed by one
+// CTA: v_1.. to A[j+2 ..][j] and vbuf[1 ..], beta to A[j+1][j] and e[j], tau[j].
+__device__ void house_step(z* A, int n, int lda, int j, z* tau, double* e, z* vbuf, double* sh) {
+  const int m = n - j - 1;
+  const z alpha = ldz(&A[(size_t)(j + 1) * lda + j]);
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += zabs2(ldz(&A[(size_t)(j + 1 + i) * lda + j]));
+  const double sigma = block_sum(s, sh);
+  if (sigma == 0.0 && alpha.y == 0.0) {
+    if (threadIdx.x == 0) { tau[j] = {0.0, 0.0}; e[j] = alpha.x; }
+    return;
+  }
+  const double nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sigma);
+  const double beta = alpha.x >= 0.0 ? -nu : nu;
+  const z am = {alpha.x - beta, alpha.y};
+  const double den = am.x * am.x + am.y * am.y;
+  const z sc = {am.x / den, -am.y / den};
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
+    z* x = &A[(size_t)(j + 1 + i) * lda + j];
+    const z v = cmul(ldz(x), sc);
+    *x = v;
+    vbuf[i] = v;
+  }
+  if (threadIdx.x == 0) {
+    tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
+    e[j] = beta;
+    A[(size_t)(j + 1) * lda + j] = {beta, 0.0};
+    vbuf[0] = {1.0, 0.0};
+  }
+}
+
+// Householder tridiagonalisation, all steps in one launch, two barriers per
+// step: (matvec p = tau A v) | (rank-2 update A -= v w^+ + w v^+, and, in CTA 0,
+// the update of the next column followed by the next reflector).  The
+// reflector is also kept contiguous in vbuf; every CTA stages v and w of the
+// step in shared memory, so the two phases stream only the trailing block of A.
 // Dynamic shared memory: 2 n complex.
 __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* tau, double* e, z* p,
                                                       double* dg, z* vbuf, GridBar bar) {
@@ -293,37 +326,10 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* t
   const size_t nthr = (size_t)gridDim.x * blockDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int nwarp = (int)(nthr >> 5), gwarp = (int)(gtid >> 5), lane = threadIdx.x & 31;
+  if (n >= 2 && blockIdx.x == 0) house_step(A, n, lda, 0, tau, e, vbuf, sh);
+  if (!grid_sync(bar)) return;
   for (int j = 0; j < n - 1; ++j) {
     const int m = n - j - 1;
-    // reflector of column j (one CTA)
-    if (blockIdx.x == 0) {
-      const z alpha = ldz(&A[(size_t)(j + 1) * lda + j]);
-      double s = 0.0;
-      for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += zabs2(ldz(&A[(size_t)(j + 1 + i) * lda + j]));
-      const double sigma = block_sum(s, sh);
-      if (sigma == 0.0 && alpha.y == 0.0) {
-        if (threadIdx.x == 0) { tau[j] = {0.0, 0.0}; e[j] = alpha.x; }
-      } else {
-        const double nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sigma);
-        const double beta = alpha.x >= 0.0 ? -nu : nu;
-        const z am = {alpha.x - beta, alpha.y};
-        const double den = am.x * am.x + am.y * am.y;
-        const z sc = {am.x / den, -am.y / den};
-        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
-          z* x = &A[(size_t)(j + 1 + i) * lda + j];
-          const z v = cmul(ldz(x), sc);
-          *x = v;
-          vbuf[i] = v;
-        }
-        if (threadIdx.x == 0) {
-          tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
-          e[j] = beta;
-          A[(size_t)(j + 1) * lda + j] = {beta, 0.0};
-          vbuf[0] = {1.0, 0.0};
-        }
-      }
-    }
-    if (!grid_sync(bar)) return;
     const z t = ldz(&tau[j]);
     const bool active = t.x != 0.0 || t.y != 0.0;
     if (active) {
@@ -342,8 +348,8 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* t
       }
     }
     if (!grid_sync(bar)) return;
-    // A -= v w^+ + w v^+, w = p - (1/2) conj(tau) (v^+ p) v
     if (active) {
+      // w = p - (1/2) conj(tau) (v^+ p) v
       double sr = 0.0, si = 0.0;
       for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const z v = sv[i], pr = ldz(&p[j + 1 + i]);
@@ -356,12 +362,32 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* t
       const z coef = {0.5 * (t.x * vpr + t.y * vpi), 0.5 * (t.x * vpi - t.y * vpr)};
       for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = csub(sw[i], cmul(coef, sv[i]));
       __syncthreads();
-      const size_t total = (size_t)m * m;
-      for (size_t q = gtid; q < total; q += nthr) {
-        const int r = (int)(q / m), c = (int)(q % m);
-        const z vr = sv[r], vc = sv[c], wr = sw[r], wc = sw[c];
-        const z dlt = cadd(cmul(vr, zconj(wc)), cmul(wr, zconj(vc)));
-        z* a = &A[(size_t)(j + 1 + r) * lda + (j + 1 + c)];
+      // all columns but the first of the trailing block (CTA 0 owns that one)
+      if (m > 1) {
+        const size_t total = (size_t)m * (m - 1);
+        for (size_t q = gtid; q < total; q += nthr) {
+          const int r = (int)(q / (m - 1)), c = 1 + (int)(q % (m - 1));
+          const z dlt = cadd(cmul(sv[r], zconj(sw[c])), cmul(sw[r], zconj(sv[c])));
+          z* a = &A[(size_t)(j + 1 + r) * lda + (j + 1 + c)];
+          *a = csub(ldz(a), dlt);
+        }
+      }
+    }
+    if (blockIdx.x == 0 && j + 1 < n - 1) {
+      if (active) {
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+          const z dlt = cadd(cmul(sv[r], zconj(sw[0])), cmul(sw[r], zconj(sv[0])));
+          z* a = &A[(size_t)(j + 1 + r) * lda + (j + 1)];
+          *a = csub(ldz(a), dlt);
+        }
+        __syncthreads();
+      }
+      house_step(A, n, lda, j + 1, tau, e, vbuf, sh);
+    } else if (blockIdx.x == 0 && active) {
+      // last step: only the 1 x 1 trailing element remains
+      for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        const z dlt = cadd(cmul(sv[r], zconj(sw[0])), cmul(sw[r], zconj(sv[0])));
+        z* a = &A[(size_t)(j + 1 + r) * lda + (j + 1)];
         *a = csub(ldz(a), dlt);
       }
     }

@@ -8,8 +8,9 @@
 //               added in a fixed order (deterministic, independent of timing);
 //   gemm_outer  C[n][m] (+)= sum_k A[k][m] B[k][n]    (beta (D P), rotations V X);
 //   dmul        Q = D P with a real D.
-// These are SIMT kernels: FP64 has no tcgen05 kind on sm_103a, and the FP32
-// variant serves the mixed-precision path.
+// These are SIMT kernels: FP64 has no tcgen05 kind on sm_103a (and DMMA runs
+// no faster than DFMA on GB300), so the FP64 path is ALU-bound and uses the
+// three-multiplication complex product to cut its FMAs by a quarter.
 #include <algorithm>
 
 #include "fft_device.cuh"
@@ -26,37 +27,24 @@ static int check_launch(const char* what) {
   return QE_OK;
 }
 
-template <typename T>
-__device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b) {
-  acc.x = fma(a.x, b.x, acc.x);
-  acc.x = fma(-a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y);
-  acc.y = fma(a.y, b.x, acc.y);
-}
-// acc += conj(a) b
-template <typename T>
-__device__ __forceinline__ void cfma_conj(cx<T>& acc, cx<T> a, cx<T> b) {
-  acc.x = fma(a.x, b.x, acc.x);
-  acc.x = fma(a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y);
-  acc.y = fma(-a.y, b.x, acc.y);
-}
-
 constexpr int IBM = 32, IBN = 32, IBK = 16;
 
 // grid: (ceil(N/32), ceil(M/32), nsplit); block 256 = 16 x 16, 2 x 2 outputs each.
+// Complex products by the three-multiplication form (3 real FMAs per complex
+// multiply-add instead of 4): for conj(a) b,
+//   t1 = ar br, t2 = ai bi, t3 = (ar - ai)(br + bi);  Re = t1 + t2, Im = t3 - t1 + t2.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gemm_inner(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
              int M, int N, int K, int kchunk, cx<T>* __restrict__ part) {
-  __shared__ cx<T> As[IBK][IBM + 1];
-  __shared__ cx<T> Bs[IBK][IBN + 1];
+  __shared__ T Ar[IBK][IBM + 1], Ai[IBK][IBM + 1], As[IBK][IBM + 1];
+  __shared__ T Br[IBK][IBN + 1], Bi[IBK][IBN + 1], Bs[IBK][IBN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int n0 = blockIdx.x * IBN, m0 = blockIdx.y * IBM;
   const int kb = blockIdx.z * kchunk;
   const int ke = min(K, kb + kchunk);
-  cx<T> acc[2][2] = {};
+  T t1[2][2] = {}, t2[2][2] = {}, t3[2][2] = {};
   for (int k0 = kb; k0 < ke; k0 += IBK) {
 #pragma unroll
     for (int rep = 0; rep < 2; ++rep) {
@@ -68,18 +56,30 @@ k_gemm_inner(const double2* __restrict__ A, int lda, const double2* __restrict__
         if (m0 + r < M) a = A[(size_t)(m0 + r) * lda + gk];
         if (n0 + r < N) b = B[(size_t)(n0 + r) * ldb + gk];
       }
-      As[kk][r] = {T(a.x), T(a.y)};
-      Bs[kk][r] = {T(b.x), T(b.y)};
+      Ar[kk][r] = T(a.x);
+      Ai[kk][r] = T(a.y);
+      As[kk][r] = T(a.x) - T(a.y);
+      Br[kk][r] = T(b.x);
+      Bi[kk][r] = T(b.y);
+      Bs[kk][r] = T(b.x) + T(b.y);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < IBK; ++kk) {
-      const cx<T> a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-      const cx<T> b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      cfma_conj(acc[0][0], a0, b0);
-      cfma_conj(acc[0][1], a0, b1);
-      cfma_conj(acc[1][0], a1, b0);
-      cfma_conj(acc[1][1], a1, b1);
+      T ar[2], ai[2], as[2], br[2], bi[2], bs[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        ar[i] = Ar[kk][ty * 2 + i]; ai[i] = Ai[kk][ty * 2 + i]; as[i] = As[kk][ty * 2 + i];
+        br[i] = Br[kk][tx * 2 + i]; bi[i] = Bi[kk][tx * 2 + i]; bs[i] = Bs[kk][tx * 2 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          t1[i][j] = fma(ar[i], br[j], t1[i][j]);
+          t2[i][j] = fma(ai[i], bi[j], t2[i][j]);
+          t3[i][j] = fma(as[i], bs[j], t3[i][j]);
+        }
     }
     __syncthreads();
   }
@@ -89,7 +89,7 @@ k_gemm_inner(const double2* __restrict__ A, int lda, const double2* __restrict__
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int m = m0 + ty * 2 + i, n = n0 + tx * 2 + j;
-      if (m < M && n < N) out[(size_t)m * N + n] = acc[i][j];
+      if (m < M && n < N) out[(size_t)m * N + n] = {t1[i][j] + t2[i][j], t3[i][j] - t1[i][j] + t2[i][j]};
     }
 }
 
@@ -193,17 +193,19 @@ template int gemm_inner_bounded<float>(const double*, int, const double*, int, i
 constexpr int OBM = 64, OBN = 32, OBK = 16;
 
 // grid: (ceil(M/64), ceil(N/32)); block 256; thread (tm = tid % 16, tn = tid / 16)
-// owns m = m0 + tm + 16 i (i < 4) and n = n0 + 2 tn + j (j < 2).
+// owns m = m0 + tm + 16 i (i < 4) and n = n0 + 2 tn + j (j < 2).  Three-
+// multiplication complex products: t1 = ar br, t2 = ai bi,
+// t3 = (ar + ai)(br + bi);  Re = t1 - t2, Im = t3 - t1 - t2.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
              int M, int N, int K, double2* __restrict__ C, int ldc, int alpha_neg, int beta) {
-  __shared__ cx<T> As[OBK][OBM];
-  __shared__ cx<T> Bs[OBK][OBN + 1];
+  __shared__ T Ar[OBK][OBM], Ai[OBK][OBM], As[OBK][OBM];
+  __shared__ T Br[OBK][OBN + 1], Bi[OBK][OBN + 1], Bs[OBK][OBN + 1];
   const int tid = threadIdx.x;
   const int tm = tid & 15, tn = tid >> 4;
   const int m0 = blockIdx.x * OBM, n0 = blockIdx.y * OBN;
-  cx<T> acc[4][2] = {};
+  T t1[4][2] = {}, t2[4][2] = {}, t3[4][2] = {};
   for (int k0 = 0; k0 < K; k0 += OBK) {
 #pragma unroll
     for (int rep = 0; rep < 4; ++rep) {
@@ -211,7 +213,9 @@ k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__
       const int kk = idx >> 6, mm = idx & 63;
       double2 a = make_double2(0.0, 0.0);
       if (k0 + kk < K && m0 + mm < M) a = A[(size_t)(k0 + kk) * lda + m0 + mm];
-      As[kk][mm] = {T(a.x), T(a.y)};
+      Ar[kk][mm] = T(a.x);
+      Ai[kk][mm] = T(a.y);
+      As[kk][mm] = T(a.x) + T(a.y);
     }
 #pragma unroll
     for (int rep = 0; rep < 2; ++rep) {
@@ -219,21 +223,30 @@ k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__
       const int kk = idx >> 5, nn = idx & 31;
       double2 b = make_double2(0.0, 0.0);
       if (k0 + kk < K && n0 + nn < N) b = B[(size_t)(k0 + kk) * ldb + n0 + nn];
-      Bs[kk][nn] = {T(b.x), T(b.y)};
+      Br[kk][nn] = T(b.x);
+      Bi[kk][nn] = T(b.y);
+      Bs[kk][nn] = T(b.x) + T(b.y);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < OBK; ++kk) {
-      cx<T> a[4], b[2];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + 16 * i];
-      b[0] = Bs[kk][2 * tn];
-      b[1] = Bs[kk][2 * tn + 1];
+      T ar[4], ai[4], as[4], br[2], bi[2], bs[2];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        cfma(acc[i][0], a[i], b[0]);
-        cfma(acc[i][1], a[i], b[1]);
+        ar[i] = Ar[kk][tm + 16 * i]; ai[i] = Ai[kk][tm + 16 * i]; as[i] = As[kk][tm + 16 * i];
       }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        br[j] = Br[kk][2 * tn + j]; bi[j] = Bi[kk][2 * tn + j]; bs[j] = Bs[kk][2 * tn + j];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          t1[i][j] = fma(ar[i], br[j], t1[i][j]);
+          t2[i][j] = fma(ai[i], bi[j], t2[i][j]);
+          t3[i][j] = fma(as[i], bs[j], t3[i][j]);
+        }
     }
     __syncthreads();
   }
@@ -246,7 +259,7 @@ k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__
       const int m = m0 + tm + 16 * i;
       if (m >= M) continue;
       double2* c = C + (size_t)n * ldc + m;
-      double2 v = make_double2((double)acc[i][j].x, (double)acc[i][j].y);
+      double2 v = make_double2((double)(t1[i][j] - t2[i][j]), (double)(t3[i][j] - t1[i][j] - t2[i][j]));
       if (alpha_neg) { v.x = -v.x; v.y = -v.y; }
       if (beta) { const double2 o = *c; v.x += o.x; v.y += o.y; }
       *c = v;
@@ -276,30 +289,59 @@ int gemm_outer(const double* A, int lda, const double* B, int ldb, int M, int N,
   return gemm_outer_ab<T>(A, lda, B, ldb, M, N, K, C, ldc, 0, beta, st, pf);
 }
 
-__global__ void k_dmul(const double* __restrict__ D, const double2* __restrict__ P,
-                       double2* __restrict__ Q, int np, int nb) {
-  const int i = blockIdx.y;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nb) return;
-  double sx = 0.0, sy = 0.0;
+// One CTA per row i of D: the nonzero entries of the row are compacted in
+// shared memory in column order (a block-wide scan, so the summation order is
+// fixed), then each thread sums them for its columns n of P.
+__global__ void __launch_bounds__(128) k_dmul(const double* __restrict__ D,
+                                              const double2* __restrict__ P,
+                                              double2* __restrict__ Q, int np, int nb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* val = reinterpret_cast<double*>(smem_raw);
+  int* col = reinterpret_cast<int*>(val + np);
+  __shared__ int wcount[4];
+  __shared__ int base;
+  const int i = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
   const double* d = D + (size_t)i * np;
-  for (int j = 0; j < np; ++j) {
-    const double dij = d[j];
-    if (dij != 0.0) {
-      const double2 p = P[(size_t)j * nb + n];
-      sx = fma(dij, p.x, sx);
-      sy = fma(dij, p.y, sy);
+  for (int j0 = 0; j0 < np; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    const double v = j < np ? d[j] : 0.0;
+    const bool nz = v != 0.0;
+    const unsigned bal = __ballot_sync(0xffffffffu, nz);
+    if (lane == 0) wcount[warp] = __popc(bal);
+    __syncthreads();
+    int off = base;
+    for (int w = 0; w < warp; ++w) off += wcount[w];
+    if (nz) {
+      const int pos = off + __popc(bal & ((1u << lane) - 1u));
+      val[pos] = v;
+      col[pos] = j;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) base += wcount[0] + wcount[1] + wcount[2] + wcount[3];
+    __syncthreads();
   }
-  Q[(size_t)i * nb + n] = make_double2(sx, sy);
+  const int cnt = base;
+  for (int n = threadIdx.x; n < nb; n += blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int q = 0; q < cnt; ++q) {
+      const double2 pv = P[(size_t)col[q] * nb + n];
+      sx = fma(val[q], pv.x, sx);
+      sy = fma(val[q], pv.y, sy);
+    }
+    Q[(size_t)i * nb + n] = make_double2(sx, sy);
+  }
 }
 
 int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf) {
   if (np <= 0 || nb <= 0) return QE_OK;
   ProfScope ps(pf, "k_dmul", st);
-  dim3 g((nb + 127) / 128, np);
-  k_dmul<<<g, 128, 0, st>>>(D, reinterpret_cast<const double2*>(P), reinterpret_cast<double2*>(Q),
-                            np, nb);
+  const size_t sm = (size_t)np * (sizeof(double) + sizeof(int));
+  set_max_dynamic_smem(k_dmul);
+  k_dmul<<<np, 128, sm, st>>>(D, reinterpret_cast<const double2*>(P), reinterpret_cast<double2*>(Q),
+                              np, nb);
   return check_launch("k_dmul");
 }
 

@@ -122,9 +122,10 @@ int tc_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const f
 int tc_gemm_splits(int Mp, int Np, int Kp);
 // hpsi += beta^T D (conj(beta) psi^T) on the tensor cores; work of nonlocal_tc_bytes().
 size_t nonlocal_tc_bytes(int np, int nb, int npw);
+size_t nonlocal_tc_beta_bytes(int np, int npw);
 int nonlocal_tc(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
-                int nb, int npw, void* work, size_t work_bytes, int* status, cudaStream_t st,
-                Prof* pf);
+                int nb, int npw, void* bpack, bool pack_beta, void* work, size_t work_bytes,
+                int* status, cudaStream_t st, Prof* pf);
 
 // Q[i][n] = sum_j D[i][j] P[j][n] (D real [np][np], P complex [np][nb]).
 int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf);

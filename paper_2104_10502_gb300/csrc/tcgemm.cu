@@ -474,21 +474,31 @@ int grid_of(size_t total) {
 
 static inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
 
+// Packed beta operands (both GEMMs); they depend only on beta, np and npw, so a
+// caller that applies the same operator repeatedly packs them once.
+size_t nonlocal_tc_beta_bytes(int np, int npw) {
+  const size_t Mp = pad_to(np, TC_BM), Kp = pad_to(2 * npw, TC_BK);
+  const size_t Mp2 = pad_to(npw, TC_BM), Kp2 = pad_to(2 * np, TC_BK);
+  return 2 * Mp * Kp * 4 + 2 * Mp2 * Kp2 * 4 + 4 * 256;
+}
+
 size_t nonlocal_tc_bytes(int np, int nb, int npw) {
   const size_t Mp = pad_to(np, TC_BM), Kp = pad_to(2 * npw, TC_BK), Np = pad_to(2 * nb, TC_BN);
   const size_t Mp2 = pad_to(npw, TC_BM), Kp2 = pad_to(2 * np, TC_BK);
   const size_t ns1 = tc_gemm_splits((int)Mp, (int)Np, (int)Kp), ns2 = tc_gemm_splits((int)Mp2, (int)Np, (int)Kp2);
   size_t b = 0;
-  b += 2 * Mp * Kp * 4 + 2 * Np * Kp * 4 + ns1 * Mp * Np * 4;        // inner product
-  b += 2 * Mp2 * Kp2 * 4 + 2 * Np * Kp2 * 4 + ns2 * Mp2 * Np * 4;    // outer product
-  b += 2 * (size_t)np * nb * 16 + 64 * 256;                          // P, Q, status, alignment
+  b += 2 * Np * Kp * 4 + ns1 * Mp * Np * 4;                          // inner product
+  b += 2 * Np * Kp2 * 4 + ns2 * Mp2 * Np * 4;                        // outer product
+  b += 2 * (size_t)np * nb * 16 + 64 * 256;                          // P, Q, alignment
   return b;
 }
 
 // Nonlocal term on the tensor cores: hpsi += beta^T D (conj(beta) psi^T).
+// bpack (nonlocal_tc_beta_bytes) holds the packed beta operands; they are
+// (re)written when pack_beta is true.
 int nonlocal_tc(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
-                int nb, int npw, void* work, size_t work_bytes, int* status, cudaStream_t st,
-                Prof* pf) {
+                int nb, int npw, void* bpack, bool pack_beta, void* work, size_t work_bytes,
+                int* status, cudaStream_t st, Prof* pf) {
   if (np <= 0 || nb <= 0) return QE_OK;
   if (nonlocal_tc_bytes(np, nb, npw) > work_bytes) {
     set_error("nonlocal_tc: workspace too small");
@@ -497,28 +507,32 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
   const int Mp = pad_to(np, TC_BM), Kp = pad_to(2 * npw, TC_BK), Np = pad_to(2 * nb, TC_BN);
   const int Mp2 = pad_to(npw, TC_BM), Kp2 = pad_to(2 * np, TC_BK);
   const int ns1 = tc_gemm_splits(Mp, Np, Kp), ns2 = tc_gemm_splits(Mp2, Np, Kp2);
-  char* p = static_cast<char*>(work);
+  char* p = static_cast<char*>(bpack);
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
   float* ahi = (float*)take((size_t)Mp * Kp * 4);
   float* alo = (float*)take((size_t)Mp * Kp * 4);
+  float* a2hi = (float*)take((size_t)Mp2 * Kp2 * 4);
+  float* a2lo = (float*)take((size_t)Mp2 * Kp2 * 4);
+  p = static_cast<char*>(work);
   float* bhi = (float*)take((size_t)Np * Kp * 4);
   float* blo = (float*)take((size_t)Np * Kp * 4);
   float* c1 = (float*)take((size_t)ns1 * Mp * Np * 4);
-  float* a2hi = (float*)take((size_t)Mp2 * Kp2 * 4);
-  float* a2lo = (float*)take((size_t)Mp2 * Kp2 * 4);
   float* b2hi = (float*)take((size_t)Np * Kp2 * 4);
   float* b2lo = (float*)take((size_t)Np * Kp2 * 4);
   float* c2 = (float*)take((size_t)ns2 * Mp2 * Np * 4);
   double2* P = (double2*)take((size_t)np * nb * 16);
   double2* Q = (double2*)take((size_t)np * nb * 16);
-  {
-    ProfScope ps(pf, "k_pack", st);
+  if (pack_beta) {
+    ProfScope ps(pf, "k_pack_beta", st);
     k_pack_rows<<<grid_of((size_t)Mp * Kp), 256, 0, st>>>((const double2*)beta, np, npw, Mp, Kp, ahi, alo);
-    k_pack_psi<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)psi, nb, npw, Np, Kp, bhi, blo);
     k_pack_pad<<<grid_of((size_t)Mp2 * Kp2), 256, 0, st>>>(Mp2, Kp2, npw, 2 * np, a2hi, a2lo);
     dim3 gt((Mp2 + 31) / 32, (np + 31) / 32);
     k_pack_beta_t<<<gt, dim3(32, 8), 0, st>>>((const double2*)beta, np, npw, Mp2, Kp2, a2hi, a2lo);
-    if (pf) pf->launches += 3;
+    if (pf) pf->launches += 2;
+  }
+  {
+    ProfScope ps(pf, "k_pack_psi", st);
+    k_pack_psi<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)psi, nb, npw, Np, Kp, bhi, blo);
   }
   int rc = tc_gemm_tf32x3(ahi, alo, bhi, blo, Mp, Np, Kp, ns1, c1, status, st, pf);
   if (rc) return rc;
