@@ -176,6 +176,41 @@ int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
                 int max_iter, int max_dim, double* psi_inout, double* evals,
                 double* resid, int* iters, void* stream);
 
+/* ---- Batches: many problems per launch --------------------------------------
+ * The paper's benchmarks parallelise over k points (pools, Sec. 3.3) and note
+ * that several small runs sharing one GPU pay off.  A batch applies H to the
+ * bands of many problems (k points of one cell, independent cells; different
+ * grids, plane-wave counts and band counts) with each FFT stage as ONE
+ * persistent launch whose CTAs pull (problem, band, tile) work items from a
+ * counter.  Results are bit-identical to qe_hpsi on each problem alone. */
+
+/* H|psi> for nprob problems.  Every array of every problem (and psi[p],
+ * hpsi[p], complex [probs[p].nbnd][npw_p][2]) must be device memory
+ * (mem = QE_DEVICE, else QE_EINVAL).  Device work is ordered on `stream`. */
+int qe_hpsi_batch(qe_ctx* ctx, int nprob, const qe_problem* probs, int precision,
+                  const double* const* psi, double* const* hpsi, void* stream);
+
+/* A batch recorded once into a CUDA graph and replayed: qe_batch_create runs
+ * the batch once (sizing and owning its own workspace), then captures its
+ * launches; qe_batch_run replays them on `stream` for the SAME arrays (update
+ * their contents between runs, not their addresses).  The problem descriptors
+ * and the arrays they point to must stay valid while the batch exists; the
+ * context must outlive it. */
+typedef struct qe_batch qe_batch;
+int qe_batch_create(qe_ctx* ctx, int nprob, const qe_problem* probs, int precision,
+                    const double* const* psi, double* const* hpsi, void* stream,
+                    qe_batch** out);
+int qe_batch_run(qe_batch* batch, void* stream);
+void qe_batch_destroy(qe_batch* batch);
+
+/* Autotuner of the FFT launch shapes (sticks per CTA and threads per CTA of
+ * the z and plane stages) for prob's grid at this precision: times candidate
+ * shapes on the problem and keeps the fastest for every later call with that
+ * grid (process-wide; also written to the file named by the environment
+ * variable QE_AUTOTUNE_CACHE, read back at the next start).  Any shape gives
+ * bit-identical results. */
+int qe_autotune(qe_ctx* ctx, const qe_problem* prob, int precision, void* stream);
+
 /* ---- Serving: continuous batching of Davidson solves ------------------------
  * The paper's outlook (Sec. 4) names memory per card as the bound on system size
  * and ensembles of independent runs as the way to fill large machines; Sec. 3.3

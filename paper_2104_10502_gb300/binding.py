@@ -25,7 +25,8 @@ QE_HOST, QE_DEVICE = 0, 1
 SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
            "qe_vloc_gaussian", "qe_beta_gaussian", "qe_hpsi", "qe_davidson", "qe_profile",
            "qe_profile_read", "qe_hpsi_noalloc", "qe_serve_create", "qe_serve_submit",
-           "qe_serve_poll", "qe_serve_cancel", "qe_serve_stats", "qe_serve_destroy"]
+           "qe_serve_poll", "qe_serve_cancel", "qe_serve_stats", "qe_serve_destroy",
+           "qe_hpsi_batch", "qe_batch_create", "qe_batch_run", "qe_batch_destroy", "qe_autotune"]
 QE_SERVE_FAKE_SOLVER = 1
 
 
@@ -79,6 +80,14 @@ _lib.qe_serve_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.PO
                                 _I, _I, ctypes.POINTER(ctypes.c_size_t)]
 _lib.qe_serve_destroy.argtypes = [_P]
 _lib.qe_serve_destroy.restype = None
+_lib.qe_hpsi_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
+                               ctypes.POINTER(_P), ctypes.POINTER(_P), _P]
+_lib.qe_batch_create.argtypes = [_P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
+                                 ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]
+_lib.qe_batch_run.argtypes = [_P, _P]
+_lib.qe_batch_destroy.argtypes = [_P]
+_lib.qe_batch_destroy.restype = None
+_lib.qe_autotune.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P]
 _lib.qe_hpsi_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_hpsi.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_davidson.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
@@ -262,6 +271,30 @@ class Context:
                             _stream(stream, psi)))
         return hpsi
 
+    # ---- batches ------------------------------------------------------------------
+    @staticmethod
+    def _batch_args(probs, psis, hpsis):
+        n = len(probs)
+        arr = (Problem * n)(*probs)
+        pp = (_P * n)(*[_ptr(x)[0] for x in psis])
+        hp = (_P * n)(*[_ptr(x)[0] for x in hpsis])
+        return n, arr, pp, hp
+
+    def hpsi_batch(self, probs, psis, hpsis, precision=QE_FP64, stream=None):
+        """H|psi> for a list of device-resident problems in one set of launches."""
+        n, arr, pp, hp = self._batch_args(probs, psis, hpsis)
+        _check(_lib.qe_hpsi_batch(self._h, n, arr, int(precision), pp, hp,
+                                  _stream(stream, *psis)))
+        return hpsis
+
+    def batch_create(self, probs, psis, hpsis, precision=QE_FP64, stream=None):
+        """Record the batch into a CUDA graph (see Batch)."""
+        return Batch(self, probs, psis, hpsis, precision, stream)
+
+    def autotune(self, prob: Problem, precision=QE_FP64, stream=None):
+        _check(_lib.qe_autotune(self._h, ctypes.byref(prob), int(precision),
+                                _stream(stream) if stream is not None else ctypes.c_void_p(0)))
+
     def davidson(self, prob: Problem, psi, evals, resid=None, precision=QE_FP64, tol=1e-8,
                  max_iter=100, max_dim=0, stream=None):
         """Returns (status, iters); status QE_OK or QE_ENOCONV."""
@@ -275,6 +308,64 @@ class Context:
                                      int(max_iter), int(max_dim), pp, pe, pr_, ctypes.byref(it),
                                      _stream(stream, psi)), allow=(QE_ENOCONV,))
         return rc, it.value
+
+
+class Batch:
+    """A batched H|psi> captured in a CUDA graph (qe_batch_*).  Keeps references
+    to the problems and arrays: replay with run() after updating psi in place."""
+
+    def __init__(self, ctx, probs, psis, hpsis, precision, stream):
+        self._keep = (list(probs), list(psis), list(hpsis))
+        n, arr, pp, hp = Context._batch_args(probs, psis, hpsis)
+        self._keep += (arr, pp, hp)
+        h = _P()
+        self._stream = _stream(stream, *psis)
+        _check(_lib.qe_batch_create(ctx._h, n, arr, int(precision), pp, hp, self._stream,
+                                    ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(_lib.qe_batch_run(self._h, self._stream if stream is None else _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.qe_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A batched H|psi> captured in a CUDA graph (qe_batch_*).  Keeps references
+    to the problems and arrays: replay with run() after updating psi in place."""
+
+    def __init__(self, ctx, probs, psis, hpsis, precision, stream):
+        self._keep = (list(probs), list(psis), list(hpsis))
+        n, arr, pp, hp = Context._batch_args(probs, psis, hpsis)
+        self._keep += (arr, pp, hp)
+        h = _P()
+        self._stream = _stream(stream, *psis)
+        _check(_lib.qe_batch_create(ctx._h, n, arr, int(precision), pp, hp, self._stream,
+                                    ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(_lib.qe_batch_run(self._h, self._stream if stream is None else _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.qe_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def problem(lat, k, ecut, grid, vloc, beta, dmat, nbnd) -> Problem:

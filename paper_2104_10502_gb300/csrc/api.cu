@@ -100,6 +100,7 @@ int ctx_begin(qe_ctx* ctx, cudaStream_t st) {
 
 int ctx_trim(qe_ctx* ctx) {
   for (DevBuf* b : ctx->bufs()) b->release();
+  ctx_batch_release(ctx);
   ctx->tc_beta_tag = 0;
   for (auto& p : ctx->plans)
     if (p->block) cudaFreeAsync(p->block, ctx->cur);

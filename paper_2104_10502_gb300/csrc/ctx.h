@@ -27,6 +27,8 @@ struct qe_ctx {
   // the packed beta in tc_beta belongs to the operator with this tag (0: none);
   // every API call that takes an operator gets a fresh tag
   unsigned long long tc_beta_tag = 0, op_tag = 0;
+  // batched H|psi> workspaces (created on first use; type private to batch.cu)
+  std::shared_ptr<void> batch;
   qe_ctx() {
     for (qe::DevBuf* b : bufs()) b->sp = &cur;
   }
@@ -63,5 +65,9 @@ int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, co
 // Status word of the tensor-core kernels since the last check (synchronises on
 // `st`); QE_ETIMEOUT with a message if a bounded wait ran out, then resets it.
 int tc_check(qe_ctx* ctx, cudaStream_t st);
+// Batched H|psi> of device-resident problems on stream st (batch.cu).
+int hpsi_batch_core(qe_ctx* ctx, int nprob, const qe_problem* probs, int precision,
+                    const double* const* psi, double* const* hpsi, cudaStream_t st);
+void ctx_batch_release(qe_ctx* ctx);
 
 }  // namespace qe

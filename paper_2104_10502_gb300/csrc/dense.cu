@@ -611,7 +611,8 @@ int heev_lowest(z* A, int n, int lda, int nev, double* w, z* X, int ldx, DenseWo
     void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.p, &wk.d, &wk.vbuf, &bar};
     const size_t tsm = 2 * (size_t)n * sizeof(z);
     set_max_dynamic_smem(k_tridiag_coop);
-    const int blocks = coop_blocks((const void*)k_tridiag_coop, (size_t)n * n, tsm);
+    // all SMs once the trailing block is large: the FP64 work is spread
+    const int blocks = coop_blocks((const void*)k_tridiag_coop, (size_t)n * n * 4, tsm);
     ProfScope ps(pf, "heev_tridiag", st);
     int rc0 = launch_coop((const void*)k_tridiag_coop, blocks, args, st, "k_tridiag_coop", tsm);
     if (rc0) return rc0;

@@ -3,19 +3,27 @@
 //
 //   psi(r_j) = sum_G c_G e^{iG.r_j},   (H c)_G = |k+G|^2 c_G + (1/N) sum_j e^{-iG.r_j} V(r_j) psi(r_j)
 //
-// as a pruned 3D FFT in three kernels per block of bands:
-//   k_zinv   scatter the sphere onto its sticks (x, y columns) and run the
-//            inverse z transform of each stick (DIF, z left digit-reversed);
-//   k_plane  one CTA per (z plane, band): scatter the sticks into the plane,
-//            inverse y transform of the columns that hold sticks, inverse x
-//            transform of every row, multiply by V (read through the digit
-//            reversal), forward x and y transforms (DIT), gather the sticks;
-//   k_zfwd   forward z transform of each stick (DIT, natural order out),
-//            gather onto the sphere, scale by 1/N and add |k+G|^2 c_G.
+// as a pruned 3D FFT in three stages per block of bands:
+//   zinv   scatter the sphere onto its sticks (x, y columns) and run the
+//          inverse z transform of each stick (DIF, z left digit-reversed);
+//   plane  one CTA per (z plane, band): scatter the sticks into the plane,
+//          inverse y transform of the columns that hold sticks, inverse x
+//          transform of every row, multiply by V (read through the digit
+//          reversal), forward x and y transforms (DIT), gather the sticks;
+//   zfwd   forward z transform of each stick (DIT, natural order out),
+//          gather onto the sphere, scale by 1/N and add |k+G|^2 c_G.
 // Sticks live in a workspace laid out [band][z][stick] so that every kernel
 // reads and writes it with consecutive threads on consecutive sticks.
+//
+// Each stage is a device "tile" function driven by a job descriptor (one
+// problem: plan, operands, band range).  A single problem launches the tiles
+// as a grid; a batch of problems with different cells, grids, plane-wave
+// counts and band counts runs each stage as ONE persistent launch whose CTAs
+// pull (problem, band, tile) items from an atomic work counter.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "fft_device.cuh"
 #include "plan.h"
@@ -45,30 +53,26 @@ __global__ void k_vperm(const double* __restrict__ v, T* __restrict__ vp, int n1
   }
 }
 
+// ---- tiles ----------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_zinv(const double* __restrict__ psi, int npw, int b0, const int* __restrict__ st_ptr,
-       const int* __restrict__ st_g, const int* __restrict__ st_z, const int* __restrict__ st_of,
-       int nst, Radix r3, const double* __restrict__ tw3, cx<T>* __restrict__ W, int spb) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* line = reinterpret_cast<cx<T>*>(smem_raw);
-  const int n3 = r3.n;
+__device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* smem) {
+  cx<T>* line = reinterpret_cast<cx<T>*>(smem);
+  const int n3 = J.r3.n, spb = J.spb, nst = J.nst;
   cx<T>* tw = line + (size_t)n3 * spb;
-  const int s0 = blockIdx.x * spb;
+  const int s0 = sblk * spb;
   const int ns = min(spb, nst - s0);
-  const int b = blockIdx.y;
   for (int i = threadIdx.x; i < n3 * spb; i += blockDim.x) line[i] = {T(0), T(0)};
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(tw3[2 * i]), T(tw3[2 * i + 1])};
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(J.tw3[2 * i]), T(J.tw3[2 * i + 1])};
   __syncthreads();
-  const double2* ps = reinterpret_cast<const double2*>(psi) + (size_t)(b0 + b) * npw;
-  const int e0 = st_ptr[s0], e1 = st_ptr[s0 + ns];
+  const double2* ps = reinterpret_cast<const double2*>(J.psi) + (size_t)(J.b0 + b) * J.npw;
+  const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const double2 c = ps[st_g[e]];
-    line[st_z[e] * spb + (st_of[e] - s0)] = {T(c.x), T(c.y)};
+    const double2 c = ps[J.st_g[e]];
+    line[J.st_z[e] * spb + (J.st_of[e] - s0)] = {T(c.x), T(c.y)};
   }
   __syncthreads();
-  fft_lines<T, +1, false>(line, spb, 1, nullptr, ns, true, r3, tw);
-  cx<T>* Wb = W + (size_t)b * n3 * nst;
+  fft_lines<T, +1, false>(line, spb, 1, nullptr, ns, true, J.r3, tw);
+  cx<T>* Wb = J.W + (size_t)b * n3 * nst;
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
     const int pz = i / ns, l = i - pz * ns;
     Wb[(size_t)pz * nst + s0 + l] = line[pz * spb + l];
@@ -76,79 +80,172 @@ k_zinv(const double* __restrict__ psi, int npw, int b0, const int* __restrict__ 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_plane(cx<T>* __restrict__ W, int nst, const int* __restrict__ st_x, const int* __restrict__ st_y,
-        const int* __restrict__ ax_g, int nax, Radix r1, Radix r2, const double* __restrict__ tw1g,
-        const double* __restrict__ tw2g, const T* __restrict__ vp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n1 = r1.n, n2 = r2.n, n3 = gridDim.x;
-  cx<T>* plane = reinterpret_cast<cx<T>*>(smem_raw);
+__device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* smem) {
+  const int n1 = J.r1.n, n2 = J.r2.n, n3 = J.r3.n, nst = J.nst, nax = J.nax;
+  cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
   cx<T>* tw1 = plane + (size_t)n1 * n2;
   cx<T>* tw2 = tw1 + n1;
   int* ax = reinterpret_cast<int*>(tw2 + n2);
-  const int pz = blockIdx.x, b = blockIdx.y;
   for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) plane[i] = {T(0), T(0)};
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = {T(tw1g[2 * i]), T(tw1g[2 * i + 1])};
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = {T(tw2g[2 * i]), T(tw2g[2 * i + 1])};
-  for (int i = threadIdx.x; i < nax; i += blockDim.x) ax[i] = ax_g[i];
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = {T(J.tw1[2 * i]), T(J.tw1[2 * i + 1])};
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = {T(J.tw2[2 * i]), T(J.tw2[2 * i + 1])};
+  for (int i = threadIdx.x; i < nax; i += blockDim.x) ax[i] = J.ax[i];
   __syncthreads();
-  cx<T>* Wp = W + ((size_t)b * n3 + pz) * nst;
-  for (int s = threadIdx.x; s < nst; s += blockDim.x) plane[st_y[s] * n1 + st_x[s]] = Wp[s];
+  cx<T>* Wp = J.W + ((size_t)b * n3 + pz) * nst;
+  for (int s = threadIdx.x; s < nst; s += blockDim.x) plane[J.st_y[s] * n1 + J.st_x[s]] = Wp[s];
   __syncthreads();
-  fft_lines<T, +1, false>(plane, n1, 0, ax, nax, true, r2, tw2);        // y, active columns
-  fft_lines<T, +1, false>(plane, 1, n1, nullptr, n2, false, r1, tw1);   // x, every row
-  const T* v = vp + (size_t)pz * n1 * n2;
+  fft_lines<T, +1, false>(plane, n1, 0, ax, nax, true, J.r2, tw2);        // y, active columns
+  fft_lines<T, +1, false>(plane, 1, n1, nullptr, n2, false, J.r1, tw1);   // x, every row
+  const T* v = J.vp + (size_t)pz * n1 * n2;
   for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) plane[i] = cscale(plane[i], v[i]);
   __syncthreads();
-  fft_lines<T, -1, true>(plane, 1, n1, nullptr, n2, false, r1, tw1);
-  fft_lines<T, -1, true>(plane, n1, 0, ax, nax, true, r2, tw2);
-  for (int s = threadIdx.x; s < nst; s += blockDim.x) Wp[s] = plane[st_y[s] * n1 + st_x[s]];
+  fft_lines<T, -1, true>(plane, 1, n1, nullptr, n2, false, J.r1, tw1);
+  fft_lines<T, -1, true>(plane, n1, 0, ax, nax, true, J.r2, tw2);
+  for (int s = threadIdx.x; s < nst; s += blockDim.x) Wp[s] = plane[J.st_y[s] * n1 + J.st_x[s]];
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256)
-k_zfwd(const cx<T>* __restrict__ W, int nst, const int* __restrict__ st_ptr,
-       const int* __restrict__ st_g, const int* __restrict__ st_z, const int* __restrict__ st_of,
-       Radix r3, const double* __restrict__ tw3, const double* __restrict__ psi,
-       const double* __restrict__ kin, double* __restrict__ hpsi, int npw, int b0, double inv_n,
-       int spb) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* line = reinterpret_cast<cx<T>*>(smem_raw);
-  const int n3 = r3.n;
+__device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* smem) {
+  cx<T>* line = reinterpret_cast<cx<T>*>(smem);
+  const int n3 = J.r3.n, spb = J.spb, nst = J.nst;
   cx<T>* tw = line + (size_t)n3 * spb;
-  const int s0 = blockIdx.x * spb;
+  const int s0 = sblk * spb;
   const int ns = min(spb, nst - s0);
-  const int b = blockIdx.y;
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(tw3[2 * i]), T(tw3[2 * i + 1])};
-  const cx<T>* Wb = W + (size_t)b * n3 * nst;
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(J.tw3[2 * i]), T(J.tw3[2 * i + 1])};
+  const cx<T>* Wb = J.W + (size_t)b * n3 * nst;
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
     const int pz = i / ns, l = i - pz * ns;
     line[pz * spb + l] = Wb[(size_t)pz * nst + s0 + l];
   }
   __syncthreads();
-  fft_lines<T, -1, true>(line, spb, 1, nullptr, ns, true, r3, tw);
-  const double2* ps = reinterpret_cast<const double2*>(psi) + (size_t)(b0 + b) * npw;
-  double2* hp = reinterpret_cast<double2*>(hpsi) + (size_t)(b0 + b) * npw;
-  const int e0 = st_ptr[s0], e1 = st_ptr[s0 + ns];
+  fft_lines<T, -1, true>(line, spb, 1, nullptr, ns, true, J.r3, tw);
+  const double2* ps = reinterpret_cast<const double2*>(J.psi) + (size_t)(J.b0 + b) * J.npw;
+  double2* hp = reinterpret_cast<double2*>(J.hpsi) + (size_t)(J.b0 + b) * J.npw;
+  const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const int g = st_g[e];
-    const cx<T> c = line[st_z[e] * spb + (st_of[e] - s0)];
+    const int g = J.st_g[e];
+    const cx<T> c = line[J.st_z[e] * spb + (J.st_of[e] - s0)];
     const double2 p = ps[g];
-    const double kg = kin[g];
-    hp[g] = make_double2((double)c.x * inv_n + kg * p.x, (double)c.y * inv_n + kg * p.y);
+    const double kg = J.kin[g];
+    hp[g] = make_double2((double)c.x * J.inv_n + kg * p.x, (double)c.y * J.inv_n + kg * p.y);
   }
 }
 
+// ---- one problem: tiles mapped on the grid ----------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512) k_zinv(const FftJob<T> J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  zinv_tile<T>(J, blockIdx.y, blockIdx.x, smem_raw);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_plane(const FftJob<T> J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  plane_tile<T>(J, blockIdx.y, blockIdx.x, smem_raw);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_zfwd(const FftJob<T> J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  zfwd_tile<T>(J, blockIdx.y, blockIdx.x, smem_raw);
+}
+
+// ---- a batch of problems: persistent CTAs over a work queue ------------------------
+// Items of job j are [prefix[j], prefix[j+1]); item i of a job maps to
+// (band, tile) = (i / tiles, i % tiles).  counter must be zero at launch.
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(512) k_fft_batch(const FftJob<T>* __restrict__ jobs,
+                                                   const int* __restrict__ prefix, int njobs,
+                                                   int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ FftJob<T> sJ;
+  __shared__ int item, cur;
+  if (threadIdx.x == 0) cur = -1;
+  const int total = prefix[njobs];
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = item;
+    if (it >= total) break;
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (prefix[mid] <= it) lo = mid;
+      else hi = mid;
+    }
+    if (lo != cur) {   // stage the job descriptor in shared memory
+      const int* src = reinterpret_cast<const int*>(&jobs[lo]);
+      int* dst = reinterpret_cast<int*>(&sJ);
+      for (int w = threadIdx.x; w < (int)(sizeof(FftJob<T>) / sizeof(int)); w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x == 0) cur = lo;
+    }
+    const int local = it - prefix[lo];
+    const int tiles = STAGE == 1 ? sJ.r3.n : sJ.nsb;
+    const int b = local / tiles, t = local - b * tiles;
+    if (STAGE == 0) zinv_tile<T>(sJ, b, t, smem_raw);
+    else if (STAGE == 1) plane_tile<T>(sJ, b, t, smem_raw);
+    else zfwd_tile<T>(sJ, b, t, smem_raw);
+  }
+}
+
+// ---- host side ---------------------------------------------------------------------
 size_t stick_bytes(const DevPlan& P, int nbc, size_t elem_bytes) {
   return (size_t)nbc * P.grid[2] * P.h.nst * elem_bytes;
 }
 
 template <typename T>
-static int sticks_per_block(int n3) {
+int default_spb(int n3) {
   int spb = (int)(49152 / ((size_t)n3 * sizeof(cx<T>)));
   if (spb > 32) spb = 32;
   if (spb < 1) spb = 1;
   return spb;
+}
+
+template <typename T>
+size_t zsm_bytes(int n3, int spb) {
+  return ((size_t)n3 * spb + n3) * sizeof(cx<T>);
+}
+
+template <typename T>
+size_t psm_bytes(const DevPlan& P) {
+  return ((size_t)P.grid[0] * P.grid[1] + P.grid[0] + P.grid[1]) * sizeof(cx<T>) +
+         (size_t)P.h.nax * sizeof(int);
+}
+
+template <typename T>
+FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* vp, void* W, int b0,
+                   int nb, const FftShape& sh) {
+  FftJob<T> J;
+  std::memset(&J, 0, sizeof(J));
+  J.r1 = P.rad[0];
+  J.r2 = P.rad[1];
+  J.r3 = P.rad[2];
+  J.st_ptr = P.st_ptr;
+  J.st_g = P.st_g;
+  J.st_z = P.st_z;
+  J.st_of = P.st_of;
+  J.st_x = P.st_x;
+  J.st_y = P.st_y;
+  J.ax = P.ax;
+  J.tw1 = P.tw[0];
+  J.tw2 = P.tw[1];
+  J.tw3 = P.tw[2];
+  J.kin = P.kin;
+  J.psi = psi;
+  J.hpsi = hpsi;
+  J.vp = vp;
+  J.W = reinterpret_cast<cx<T>*>(W);
+  J.nst = P.h.nst;
+  J.nax = P.h.nax;
+  J.npw = P.h.npw;
+  J.nb = nb;
+  J.b0 = b0;
+  J.spb = sh.spb > 0 ? sh.spb : default_spb<T>(P.grid[2]);
+  J.nsb = (J.nst + J.spb - 1) / J.spb;
+  J.inv_n = 1.0 / ((double)P.grid[0] * P.grid[1] * P.grid[2]);
+  return J;
 }
 
 template <typename T>
@@ -162,16 +259,15 @@ int launch_vperm(const DevPlan& P, const double* vloc, T* vp, cudaStream_t st, P
 }
 
 template <typename T>
-int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, const T* vp, void* Wv,
-                         int b0, int nbc, cudaStream_t st, Prof* pf) {
-  cx<T>* W = reinterpret_cast<cx<T>*>(Wv);
-  const int n1 = P.grid[0], n2 = P.grid[1], n3 = P.grid[2];
-  const int nst = P.h.nst;
-  const int spb = sticks_per_block<T>(n3);
-  const size_t zsm = ((size_t)n3 * spb + n3) * sizeof(cx<T>);
-  const size_t psm = ((size_t)n1 * n2 + n1 + n2) * sizeof(cx<T>) + (size_t)P.h.nax * sizeof(int);
+int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi, const T* vp,
+                               void* Wv, int b0, int nbc, const FftShape& sh, cudaStream_t st,
+                               Prof* pf) {
+  const FftJob<T> J = make_job<T>(P, psi, hpsi, vp, Wv, b0, nbc, sh);
+  const size_t zsm = zsm_bytes<T>(P.grid[2], J.spb);
+  const size_t psm = psm_bytes<T>(P);
   if (psm > 227 * 1024) {
-    set_error("FFT plane %d x %d does not fit in shared memory at this precision", n1, n2);
+    set_error("FFT plane %d x %d does not fit in shared memory at this precision", P.grid[0],
+              P.grid[1]);
     return QE_EINVAL;
   }
   // The cap is a per-function device attribute shared by every thread of the
@@ -180,28 +276,75 @@ int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, cons
   set_max_dynamic_smem(k_plane<T>);
   set_max_dynamic_smem(k_zinv<T>);
   set_max_dynamic_smem(k_zfwd<T>);
-  dim3 gz((nst + spb - 1) / spb, nbc);
+  const int zt = sh.zthreads > 0 ? sh.zthreads : 256, pt = sh.pthreads > 0 ? sh.pthreads : 256;
+  dim3 gz(J.nsb, nbc);
   int rc;
   {
-  ProfScope ps(pf, "k_zinv", st);
-  k_zinv<T><<<gz, 256, zsm, st>>>(psi, P.h.npw, b0, P.st_ptr, P.st_g, P.st_z, P.st_of, nst,
-                                  P.rad[2], P.tw[2], W, spb);
-  rc = check_launch("k_zinv");
+    ProfScope ps(pf, "k_zinv", st);
+    k_zinv<T><<<gz, zt, zsm, st>>>(J);
+    rc = check_launch("k_zinv");
   }
   if (rc) return rc;
-  dim3 gp(n3, nbc);
   {
-  ProfScope ps(pf, "k_plane", st);
-  k_plane<T><<<gp, 256, psm, st>>>(W, nst, P.st_x, P.st_y, P.ax, P.h.nax, P.rad[0], P.rad[1],
-                                   P.tw[0], P.tw[1], vp);
-  rc = check_launch("k_plane");
+    ProfScope ps(pf, "k_plane", st);
+    k_plane<T><<<dim3(P.grid[2], nbc), pt, psm, st>>>(J);
+    rc = check_launch("k_plane");
   }
   if (rc) return rc;
   ProfScope ps(pf, "k_zfwd", st);
-  const double inv_n = 1.0 / ((double)n1 * n2 * n3);
-  k_zfwd<T><<<gz, 256, zsm, st>>>(W, nst, P.st_ptr, P.st_g, P.st_z, P.st_of, P.rad[2], P.tw[2],
-                                  psi, P.kin, hpsi, P.h.npw, b0, inv_n, spb);
+  k_zfwd<T><<<gz, zt, zsm, st>>>(J);
   return check_launch("k_zfwd");
+}
+
+template <typename T>
+int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, const T* vp, void* Wv,
+                         int b0, int nbc, cudaStream_t st, Prof* pf) {
+  return launch_local_kinetic_shape<T>(P, psi, hpsi, vp, Wv, b0, nbc, tuned_shape(P, sizeof(T)),
+                                       st, pf);
+}
+
+// Batched local + kinetic: every stage is one persistent launch over all jobs.
+// prefix_dev holds two prefix arrays of njobs + 1 items (stick-block items, then
+// plane items); counters (3 ints) are zeroed here; smem_* are the largest
+// per-item needs over the jobs.
+template <typename T>
+int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev, int njobs,
+                               int* counters, size_t smem_z, size_t smem_p, int threads,
+                               cudaStream_t st, Prof* pf) {
+  if (smem_p > 227 * 1024) {
+    set_error("batched FFT: a plane does not fit in shared memory at this precision");
+    return QE_EINVAL;
+  }
+  set_max_dynamic_smem(k_fft_batch<T, 0>);
+  set_max_dynamic_smem(k_fft_batch<T, 1>);
+  set_max_dynamic_smem(k_fft_batch<T, 2>);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMemsetAsync(counters, 0, 3 * sizeof(int), st) != cudaSuccess) {
+    set_error("batched FFT: memset failed");
+    return QE_ECUDA;
+  }
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_batch<T, 0>, threads, smem_z);
+  {
+    ProfScope ps(pf, "k_zinv_batch", st);
+    k_fft_batch<T, 0><<<nsm * std::max(1, occ), threads, smem_z, st>>>(jobs_dev, prefix_dev, njobs,
+                                                                       counters);
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_batch<T, 1>, threads, smem_p);
+  {
+    ProfScope ps(pf, "k_plane_batch", st);
+    k_fft_batch<T, 1><<<nsm * std::max(1, occ), threads, smem_p, st>>>(
+        jobs_dev, prefix_dev + (njobs + 1), njobs, counters + 1);
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_batch<T, 2>, threads, smem_z);
+  {
+    ProfScope ps(pf, "k_zfwd_batch", st);
+    k_fft_batch<T, 2><<<nsm * std::max(1, occ), threads, smem_z, st>>>(jobs_dev, prefix_dev, njobs,
+                                                                       counters + 2);
+  }
+  return check_launch("batched FFT");
 }
 
 template int launch_vperm<double>(const DevPlan&, const double*, double*, cudaStream_t, Prof*);
@@ -210,5 +353,23 @@ template int launch_local_kinetic<double>(const DevPlan&, const double*, double*
                                           void*, int, int, cudaStream_t, Prof*);
 template int launch_local_kinetic<float>(const DevPlan&, const double*, double*, const float*,
                                          void*, int, int, cudaStream_t, Prof*);
+template int launch_local_kinetic_shape<double>(const DevPlan&, const double*, double*,
+                                                const double*, void*, int, int, const FftShape&,
+                                                cudaStream_t, Prof*);
+template int launch_local_kinetic_shape<float>(const DevPlan&, const double*, double*, const float*,
+                                               void*, int, int, const FftShape&, cudaStream_t,
+                                               Prof*);
+template int launch_local_kinetic_batch<double>(const FftJob<double>*, const int*, int, int*, size_t,
+                                                size_t, int, cudaStream_t, Prof*);
+template int launch_local_kinetic_batch<float>(const FftJob<float>*, const int*, int, int*, size_t,
+                                               size_t, int, cudaStream_t, Prof*);
+template FftJob<double> make_job<double>(const DevPlan&, const double*, double*, const double*,
+                                         void*, int, int, const FftShape&);
+template FftJob<float> make_job<float>(const DevPlan&, const double*, double*, const float*, void*,
+                                       int, int, const FftShape&);
+template size_t zsm_bytes<double>(int, int);
+template size_t zsm_bytes<float>(int, int);
+template size_t psm_bytes<double>(const DevPlan&);
+template size_t psm_bytes<float>(const DevPlan&);
 
 }  // namespace qe

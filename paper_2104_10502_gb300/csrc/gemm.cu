@@ -111,6 +111,7 @@ __global__ void k_reduce_split(const cx<T>* __restrict__ part, int nsplit, int M
 }
 
 static int inner_split(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 1;
   const int tiles = ((M + IBM - 1) / IBM) * ((N + IBN - 1) / IBN);
   int ns = (2 * 152 * 4 + tiles - 1) / tiles;  // aim for ~4 CTAs per SM
   const int maxs = std::max(1, K / 32);         // at least 32 k per split
@@ -119,6 +120,7 @@ static int inner_split(int M, int N, int K) {
 }
 
 size_t gemm_inner_scratch(int M, int N, int K, size_t elem_bytes) {
+  if (M <= 0 || N <= 0) return 0;
   return (size_t)inner_split(M, N, K) * M * N * 2 * elem_bytes;
 }
 

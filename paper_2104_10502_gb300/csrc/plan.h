@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "common.h"
+#include "fft_device.cuh"
 
 namespace qe {
 
@@ -77,6 +78,38 @@ struct DevBuf {
   void release();
 };
 
+// ---- FFT stage descriptors ---------------------------------------------------------
+// Launch shape of the FFT kernels for one grid: sticks per CTA of the z stages
+// and threads per CTA of the z and plane stages (0 = default).  Any shape gives
+// bit-identical results; the autotuner only picks the fastest.
+struct FftShape {
+  int spb = 0, zthreads = 0, pthreads = 0;
+};
+// Tuned shape for this plan's grid at this element size (defaults if untuned).
+FftShape tuned_shape(const DevPlan& P, size_t elem_bytes);
+
+// One problem's share of the local + kinetic stages: plan, operands, bands.
+template <typename T>
+struct FftJob {
+  Radix r1, r2, r3;
+  const int *st_ptr, *st_g, *st_z, *st_of, *st_x, *st_y, *ax;
+  const double *tw1, *tw2, *tw3, *kin;
+  const double* psi;
+  double* hpsi;
+  const T* vp;
+  cx<T>* W;
+  int nst, nax, npw, nb, b0, spb, nsb, pad;
+  double inv_n;
+};
+
+template <typename T>
+FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* vp, void* W, int b0,
+                   int nb, const FftShape& sh);
+template <typename T>
+size_t zsm_bytes(int n3, int spb);
+template <typename T>
+size_t psm_bytes(const DevPlan& P);
+
 // ---- launchers (return QE_OK or QE_ECUDA with the error message set) -------
 // Vp[pz][py][px] = V[perm3[pz]][perm2[py]][perm1[px]] converted to T.
 template <typename T>
@@ -87,6 +120,15 @@ int launch_vperm(const DevPlan& P, const double* vloc, T* vp, cudaStream_t st, P
 template <typename T>
 int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, const T* vp,
                          void* W, int b0, int nbc, cudaStream_t st, Prof* pf);
+
+template <typename T>
+int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi, const T* vp,
+                               void* W, int b0, int nbc, const FftShape& sh, cudaStream_t st,
+                               Prof* pf);
+template <typename T>
+int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev, int njobs,
+                               int* counters, size_t smem_z, size_t smem_p, int threads,
+                               cudaStream_t st, Prof* pf);
 
 // Size in bytes of the stick workspace for nbc bands.
 size_t stick_bytes(const DevPlan& P, int nbc, size_t elem_bytes);

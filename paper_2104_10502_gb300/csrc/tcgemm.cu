@@ -109,7 +109,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
 }
 
 // ---- the GEMM kernel ------------------------------------------------------------
-// grid (Mp/128, Np/128, nsplit), block 128 (warp 0 lane 0: TMA producer; warp 1
+// grid (Np/128, Mp/128, nsplit), block 128 (warp 0 lane 0: TMA producer; warp 1
 // lane 0: MMA issuer; all four warps: epilogue).  CTA z handles K blocks
 // [z*kb_per_split, min(nkb_total, (z+1)*kb_per_split)) and writes its partial
 // tile to C + z*split_stride (row-major, leading dimension ldc).
@@ -129,7 +129,9 @@ k_tc_gemm_tf32x3(const __grid_constant__ CUtensorMap mAhi, const __grid_constant
   __shared__ int s_issued;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  // N tiles vary fastest across consecutive CTAs, so the CTAs that share an A
+  // tile run together and read it from L2 rather than from DRAM again
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
   const int kb0 = blockIdx.z * kb_per_split;
   const int nkb = min(kb_per_split, nkb_total - kb0);
   const uint64_t limit = 2000000000ull;   // 2 s per wait
@@ -301,7 +303,7 @@ int tc_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const f
   nsplit = (nkb + per - 1) / per;   // every split non-empty
   set_max_dynamic_smem(k_tc_gemm_tf32x3);
   ProfScope ps(pf, "k_tc_gemm_tf32x3", st);
-  dim3 g(Mp / TC_BM, Np / TC_BN, nsplit);
+  dim3 g(Np / TC_BN, Mp / TC_BM, nsplit);
   k_tc_gemm_tf32x3<<<g, 128, TC_SMEM_BYTES, st>>>(mAhi, mAlo, mBhi, mBlo, nkb, per, C, Np,
                                                   (long long)Mp * Np, status);
   cudaError_t e = cudaGetLastError();
