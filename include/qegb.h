@@ -190,6 +190,22 @@ int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
 int qe_hpsi_batch(qe_ctx* ctx, int nprob, const qe_problem* probs, int precision,
                   const double* const* psi, double* const* hpsi, void* stream);
 
+/* Block Davidson for nprob problems advanced in lockstep (k points of one
+ * cell, Sec. 3.3 pools, or independent cells): every iteration applies H to
+ * the new basis vectors of all unfinished solves in one batched H|psi> as
+ * above.  Arguments per problem as qe_davidson (same tol, max_iter, max_dim,
+ * precision for all); every array must be device memory (else QE_EINVAL).
+ * status[p] (may be NULL): QE_OK, QE_ENOCONV (best bands filled in) or the
+ * error of that solve; iters[p] (may be NULL) its basis expansions.  Returns
+ * QE_OK when all converged, QE_ENOCONV when some did not, else the first
+ * other error.  Each problem's result equals qe_davidson on it alone bit for
+ * bit.  Each solve owns a workspace of the context (kept for later calls).
+ * Device work is ordered on `stream`; the call returns after it ends. */
+int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs, int precision,
+                      double tol, int max_iter, int max_dim, double* const* psi_inout,
+                      double* const* evals, double* const* resid, int* iters, int* status,
+                      void* stream);
+
 /* A batch recorded once into a CUDA graph and replayed: qe_batch_create runs
  * the batch once (sizing and owning its own workspace), then captures its
  * launches; qe_batch_run replays them on `stream` for the SAME arrays (update

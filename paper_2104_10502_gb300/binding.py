@@ -26,7 +26,8 @@ SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
            "qe_vloc_gaussian", "qe_beta_gaussian", "qe_hpsi", "qe_davidson", "qe_profile",
            "qe_profile_read", "qe_hpsi_noalloc", "qe_serve_create", "qe_serve_submit",
            "qe_serve_poll", "qe_serve_cancel", "qe_serve_stats", "qe_serve_destroy",
-           "qe_hpsi_batch", "qe_batch_create", "qe_batch_run", "qe_batch_destroy", "qe_autotune"]
+           "qe_hpsi_batch", "qe_batch_create", "qe_batch_run", "qe_batch_destroy", "qe_autotune",
+           "qe_davidson_batch"]
 QE_SERVE_FAKE_SOLVER = 1
 
 
@@ -92,6 +93,9 @@ _lib.qe_hpsi_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, _P, _P, 
 _lib.qe_hpsi.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_davidson.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
                              ctypes.c_int, ctypes.c_int, _P, _P, _P, _I, _P]
+_lib.qe_davidson_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P),
+                                   ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I, _P]
 
 
 def lib() -> ctypes.CDLL:
@@ -260,6 +264,8 @@ class Context:
             pr.beta, pr.dmat = pb, pd
         pr.nbnd = int(nbnd)
         pr.mem = mem
+        # the descriptor holds raw pointers: keep the arrays alive with it
+        pr._keep = (vloc, beta, dmat)
         return pr
 
     def hpsi(self, prob: Problem, psi, hpsi, precision=QE_FP64, stream=None):
@@ -308,6 +314,22 @@ class Context:
                                      int(max_iter), int(max_dim), pp, pe, pr_, ctypes.byref(it),
                                      _stream(stream, psi)), allow=(QE_ENOCONV,))
         return rc, it.value
+
+    def davidson_batch(self, probs, psis, evals, resids=None, precision=QE_FP64, tol=1e-8,
+                       max_iter=100, max_dim=0, stream=None):
+        """Lockstep Davidson over device-resident problems.  Returns (rc, status
+        list, iters list); rc QE_OK, or QE_ENOCONV if some solve did not converge."""
+        n = len(probs)
+        arr = (Problem * n)(*probs)
+        pp = (_P * n)(*[_ptr(x)[0] for x in psis])
+        pe = (_P * n)(*[_ptr(x)[0] for x in evals])
+        pr_ = (_P * n)(*[_ptr(x)[0] for x in resids]) if resids is not None else None
+        its = (ctypes.c_int * max(n, 1))()
+        sts = (ctypes.c_int * max(n, 1))()
+        rc = _check(_lib.qe_davidson_batch(self._h, n, arr, int(precision), float(tol),
+                                           int(max_iter), int(max_dim), pp, pe, pr_, its, sts,
+                                           _stream(stream, *psis)), allow=(QE_ENOCONV,))
+        return rc, list(sts)[:n], list(its)[:n]
 
 
 class Batch:

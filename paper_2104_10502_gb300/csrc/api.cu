@@ -100,6 +100,10 @@ int ctx_begin(qe_ctx* ctx, cudaStream_t st) {
 
 int ctx_trim(qe_ctx* ctx) {
   for (DevBuf* b : ctx->bufs()) b->release();
+  for (auto& b : ctx->dvb_basis) b->release();
+  for (auto& b : ctx->dvb_red) b->release();
+  ctx->dvb_basis.clear();
+  ctx->dvb_red.clear();
   ctx_batch_release(ctx);
   ctx->tc_beta_tag = 0;
   for (auto& p : ctx->plans)

@@ -29,6 +29,8 @@ struct qe_ctx {
   unsigned long long tc_beta_tag = 0, op_tag = 0;
   // batched H|psi> workspaces (created on first use; type private to batch.cu)
   std::shared_ptr<void> batch;
+  // per-solve Davidson workspaces of a batched solve (basis, reduced matrices)
+  std::vector<std::unique_ptr<qe::DevBuf>> dvb_basis, dvb_red;
   qe_ctx() {
     for (qe::DevBuf* b : bufs()) b->sp = &cur;
   }

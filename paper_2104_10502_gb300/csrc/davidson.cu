@@ -218,7 +218,7 @@ size_t davidson_footprint(int npw, int nb, int max_dim, int nproj, const int gri
   return b + ((size_t)1 << 20);
 }
 
-static int dv_alloc(qe_ctx* ctx, DvState& S) {
+static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S) {
   const size_t npw = S.npw, nb = S.nb, md = S.max_dim;
   const size_t zb = sizeof(z);
   // big: V, HV [md][npw]; Psi, HPsi, R, D, D2 [nb][npw]
@@ -235,8 +235,8 @@ static int dv_alloc(qe_ctx* ctx, DvState& S) {
     set_error("davidson: workspace size mismatch");
     return QE_EINVAL;
   }
-  DV_TRY(ctx->dv_basis.ensure(total));
-  char* p = (char*)ctx->dv_basis.p;
+  DV_TRY(basis.ensure(total));
+  char* p = (char*)basis.p;
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
   S.V = (z*)take(md * npw * zb);
   S.HV = (z*)take(md * npw * zb);
@@ -272,14 +272,14 @@ static int dv_alloc(qe_ctx* ctx, DvState& S) {
   S.dw.bar.count = reinterpret_cast<unsigned int*>(S.dw.status + 4);
   S.dw.bar.gen = S.dw.bar.count + 1;
   S.dw.bar.err = S.dw.status + 8;
-  if ((size_t)(p - (char*)ctx->dv_basis.p) > ctx->dv_basis.bytes) {
+  if ((size_t)(p - (char*)basis.p) > basis.bytes) {
     set_error("davidson: workspace layout overflow");
     return QE_EINVAL;
   }
   // split-K partials: at most (splits for ~4 CTAs/SM + tiles) 32x32 tiles of FP64 complex
   const size_t sb = dv_red_bytes(md);
-  DV_TRY(ctx->dv_red.ensure(sb));
-  S.part = ctx->dv_red.p;
+  DV_TRY(red.ensure(sb));
+  S.part = red.p;
   S.part_bytes = sb;
   return QE_OK;
 }
@@ -387,12 +387,16 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
 // matrices over ~1e4-1e5 plane waves leaves ~1e-5 relative noise in H_r; this
 // last step brings the eigenvalue error down to O(residual^2 / gap) and reports
 // FP64 residual norms of the returned vectors.
-static int refine_fp64(qe_ctx* ctx, const DevPlan& P, const OpView& op, DvState& S, cudaStream_t st) {
-  Prof* pf = &ctx->prof;
-  const int npw = S.npw, nb = S.nb, md = S.max_dim;
-  const size_t zb = sizeof(z);
-  DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
-  DV_TRY(hpsi_core(ctx, P, op, QE_FP64, (const double*)S.V, (double*)S.HV, nb, st));
+// Split in two around the H product so that a batch can apply it to all its
+// solves at once: refine_pre copies the Ritz vectors into V[0:nb], the caller
+// applies FP64 H to them into HV[0:nb], refine_post does the Rayleigh-Ritz.
+static int refine_pre(DvState& S, cudaStream_t st) {
+  DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)S.nb * S.npw * sizeof(z), cudaMemcpyDeviceToDevice, st));
+  return QE_OK;
+}
+
+static int refine_post(DvState& S, cudaStream_t st, Prof* pf) {
+  const int npw = S.npw, nb = S.nb;
   DV_TRY(update_reduced<double>(S, 0, nb, st, pf));
   DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
   DV_TRY(rayleigh_ritz(S, nb, st, pf));
@@ -401,99 +405,264 @@ static int refine_fp64(qe_ctx* ctx, const DevPlan& P, const OpView& op, DvState&
   DV_TRY(gemm_outer_ab<double>((const double*)S.HV, npw, (const double*)S.X, nb, npw, nb, nb,
                                (double*)S.HPsi, npw, 0, 0, st, pf));
   k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
-  DV_TRY(check_launch("k_resid"));
-  (void)md;
+  return check_launch("k_resid");
+}
+
+// One Davidson solve as a state machine, so that a batch can advance many
+// solves in lockstep and apply H to all their new vectors in one batched call:
+//   begin -> [H on V[0:nb]] -> after_first_h -> { step -> [H on the new rows] -> after_h }*
+struct DvSolve {
+  const DevPlan* P = nullptr;
+  OpView op;
+  int precision = QE_FP64;
+  double tol = 0.0;
+  int max_iter = 0;
+  DvState S;
+  int n = 0, it = 0, nk = 0;
+  bool first = true, done = false, conv = false;
+  std::vector<double> e, rn;
+  // pending H product: rows [h_row, h_row + h_rows) of V into the same rows of HV
+  int h_row = 0, h_rows = 0;
+};
+
+static int dv_begin(DvSolve& v, cudaStream_t st) {
+  DvState& S = v.S;
+  const DevPlan& P = *v.P;
+  const int npw = S.npw, nb = S.nb;
+  const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
+  k_mean<<<1, 1024, 0, st>>>(v.op.vloc, ngrid, S.vmean);
+  k_hdiag<<<(npw + 255) / 256, 256, 0, st>>>(P.kin, S.vmean, (const z*)v.op.beta, v.op.dmat,
+                                              v.op.nproj, npw, S.hd);
+  DV_TRY(check_launch("k_hdiag"));
+  DV_CU(cudaMemsetAsync(S.dw.status, 0, 16 * sizeof(int), st));
+  v.e.assign(nb, 0.0);
+  v.rn.assign(nb, 0.0);
+  v.n = nb;
+  v.h_row = 0;
+  v.h_rows = nb;
   return QE_OK;
 }
 
 template <typename T>
-static int davidson_run(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, double tol,
-                        int max_iter, DvState& S, int* iters, bool* converged, cudaStream_t st) {
-  Prof* pf = &ctx->prof;
+static int dv_after_first_h(DvSolve& v, cudaStream_t st, Prof* pf) {
+  v.h_rows = 0;
+  return update_reduced<T>(v.S, 0, v.n, st, pf);
+}
+
+// Rayleigh-Ritz and residuals, launched without waiting (a batch queues every
+// solve's before the first wait) ...
+template <typename T>
+static int dv_step_launch(DvSolve& v, cudaStream_t st, Prof* pf) {
+  DvState& S = v.S;
+  const int npw = S.npw, nb = S.nb;
+  const size_t zb = sizeof(z);
+  DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));   // keeps the barrier error word
+  DV_TRY(rayleigh_ritz(S, v.n, st, pf));
+  DV_TRY(gemm_outer_ab<T>((const double*)S.V, npw, (const double*)S.X, nb, npw, nb, v.n,
+                          (double*)S.Psi, npw, 0, 0, st, pf));
+  DV_TRY(gemm_outer_ab<T>((const double*)S.HV, npw, (const double*)S.X, nb, npw, nb, v.n,
+                          (double*)S.HPsi, npw, 0, 0, st, pf));
+  if (v.first) {
+    // the Ritz vectors of the start block become the (orthonormal) basis
+    DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+    DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+    v.n = nb;
+    DV_TRY(update_reduced<T>(S, 0, v.n, st, pf));
+    v.first = false;
+  }
+  k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
+  return check_launch("k_resid");
+}
+
+// ... then the convergence test on the host; either done, or the corrections
+// are appended to V and their H product is left pending.
+template <typename T>
+static int dv_step_finish(qe_ctx* ctx, DvSolve& v, cudaStream_t st, Prof* pf) {
+  DvState& S = v.S;
   const int npw = S.npw, nb = S.nb, md = S.max_dim;
   const size_t zb = sizeof(z);
   const double pmin = 0.1;
   const double drop = 1e-6;
-  // preconditioner diagonal
-  const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
-  k_mean<<<1, 1024, 0, st>>>(op.vloc, ngrid, S.vmean);
-  k_hdiag<<<(npw + 255) / 256, 256, 0, st>>>(P.kin, S.vmean, (const z*)op.beta, op.dmat, op.nproj,
-                                              npw, S.hd);
-  DV_TRY(check_launch("k_hdiag"));
-  DV_CU(cudaMemsetAsync(S.dw.status, 0, 16 * sizeof(int), st));
-  // start block
-  DV_TRY(hpsi_core(ctx, P, op, precision, (const double*)S.V, (double*)S.HV, nb, st));
-  int n = nb;
-  DV_TRY(update_reduced<T>(S, 0, n, st, pf));
-  int it = 0;
-  bool first = true;
-  std::vector<double> e(nb), rn(nb);
-  *converged = false;
-  while (true) {
-    DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));   // keeps the barrier error word
-    DV_TRY(rayleigh_ritz(S, n, st, pf));
-    DV_TRY(gemm_outer_ab<T>((const double*)S.V, npw, (const double*)S.X, nb, npw, nb, n,
-                            (double*)S.Psi, npw, 0, 0, st, pf));
-    DV_TRY(gemm_outer_ab<T>((const double*)S.HV, npw, (const double*)S.X, nb, npw, nb, n,
-                            (double*)S.HPsi, npw, 0, 0, st, pf));
-    if (first) {
-      // the Ritz vectors of the start block become the (orthonormal) basis
-      DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
-      DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
-      n = nb;
-      DV_TRY(update_reduced<T>(S, 0, n, st, pf));
-      first = false;
-    }
-    k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
-    DV_TRY(check_launch("k_resid"));
-    int status[16];
-    DV_CU(cudaMemcpyAsync(e.data(), S.e, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-    DV_CU(cudaMemcpyAsync(rn.data(), S.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-    DV_CU(cudaMemcpyAsync(status, S.dw.status, sizeof(status), cudaMemcpyDeviceToHost, st));
-    DV_CU(cudaStreamSynchronize(st));
-    DV_TRY(tc_check(ctx, st));
-    if (status[8] != 0) {
-      set_error("davidson: a grid barrier of the dense eigensolver timed out");
-      *iters = it;
-      return QE_ETIMEOUT;
-    }
-    if (status[0] != 0) {
-      set_error("davidson: reduced overlap matrix not positive definite (column %d)", status[0] - 1);
-      *iters = it;
-      return QE_ENOCONV;
-    }
-    std::vector<int> unc;
-    for (int b = 0; b < nb; ++b)
-      if (!(rn[b] <= tol)) unc.push_back(b);
-    if (unc.empty()) { *converged = true; break; }
-    if (it >= max_iter) break;
-    ++it;
-    const int nu = (int)unc.size();
-    DV_CU(cudaMemcpyAsync(S.idx, unc.data(), nu * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_precond<<<nu, 256, 0, st>>>(S.R, S.idx, S.e, S.hd, npw, pmin * pmin, S.D);
-    DV_TRY(check_launch("k_precond"));
-    if (n + nu > md) {
-      DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
-      DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
-      n = nb;
-      DV_TRY(update_reduced<T>(S, 0, n, st, pf));
-    }
-    int nk = 0;
-    DV_TRY(orthonormalise<T>(S, n, S.D, nu, S.V + (size_t)n * npw, &nk, drop, st, pf));
-    if (nk == 0) break;
-    DV_TRY(hpsi_core(ctx, P, op, precision, (const double*)(S.V + (size_t)n * npw),
-                     (double*)(S.HV + (size_t)n * npw), nk, st));
-    DV_TRY(update_reduced<T>(S, n, n + nk, st, pf));
-    n += nk;
+  int status[16];
+  DV_CU(cudaMemcpyAsync(v.e.data(), S.e, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DV_CU(cudaMemcpyAsync(v.rn.data(), S.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DV_CU(cudaMemcpyAsync(status, S.dw.status, sizeof(status), cudaMemcpyDeviceToHost, st));
+  DV_CU(cudaStreamSynchronize(st));
+  DV_TRY(tc_check(ctx, st));
+  if (status[8] != 0) {
+    set_error("davidson: a grid barrier of the dense eigensolver timed out");
+    return QE_ETIMEOUT;
   }
-  *iters = it;
-  if (precision != QE_FP64) DV_TRY(refine_fp64(ctx, P, op, S, st));
+  if (status[0] != 0) {
+    set_error("davidson: reduced overlap matrix not positive definite (column %d)", status[0] - 1);
+    return QE_ENOCONV;
+  }
+  std::vector<int> unc;
+  for (int b = 0; b < nb; ++b)
+    if (!(v.rn[b] <= v.tol)) unc.push_back(b);
+  if (unc.empty()) { v.conv = true; v.done = true; return QE_OK; }
+  if (v.it >= v.max_iter) { v.done = true; return QE_OK; }
+  ++v.it;
+  const int nu = (int)unc.size();
+  DV_CU(cudaMemcpyAsync(S.idx, unc.data(), nu * sizeof(int), cudaMemcpyHostToDevice, st));
+  k_precond<<<nu, 256, 0, st>>>(S.R, S.idx, S.e, S.hd, npw, pmin * pmin, S.D);
+  DV_TRY(check_launch("k_precond"));
+  if (v.n + nu > md) {
+    DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+    DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+    v.n = nb;
+    DV_TRY(update_reduced<T>(S, 0, v.n, st, pf));
+  }
+  int nk = 0;
+  DV_TRY(orthonormalise<T>(S, v.n, S.D, nu, S.V + (size_t)v.n * npw, &nk, drop, st, pf));
+  if (nk == 0) { v.done = true; return QE_OK; }
+  v.nk = nk;
+  v.h_row = v.n;
+  v.h_rows = nk;
+  return QE_OK;
+}
+
+template <typename T>
+static int dv_after_h(DvSolve& v, cudaStream_t st, Prof* pf) {
+  DV_TRY(update_reduced<T>(v.S, v.n, v.n + v.nk, st, pf));
+  v.n += v.nk;
+  v.h_rows = 0;
+  return QE_OK;
+}
+
+static int dv_apply_h(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
+  const size_t off = (size_t)v.h_row * v.S.npw;
+  return hpsi_core(ctx, *v.P, v.op, v.precision, (const double*)(v.S.V + off),
+                   (double*)(v.S.HV + off), v.h_rows, st);
+}
+
+template <typename T>
+static int davidson_run(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
+  Prof* pf = &ctx->prof;
+  DV_TRY(dv_begin(v, st));
+  DV_TRY(dv_apply_h(ctx, v, st));
+  DV_TRY(dv_after_first_h<T>(v, st, pf));
+  while (true) {
+    DV_TRY(dv_step_launch<T>(v, st, pf));
+    DV_TRY(dv_step_finish<T>(ctx, v, st, pf));
+    if (v.done) break;
+    DV_TRY(dv_apply_h(ctx, v, st));
+    DV_TRY(dv_after_h<T>(v, st, pf));
+  }
+  if (v.precision != QE_FP64) {
+    DV_TRY(refine_pre(v.S, st));
+    DV_TRY(hpsi_core(ctx, *v.P, v.op, QE_FP64, (const double*)v.S.V, (double*)v.S.HV, v.S.nb, st));
+    DV_TRY(refine_post(v.S, st, pf));
+  }
+  return QE_OK;
+}
+
+// Lockstep over a batch of solves: each H product of an iteration, for every
+// solve still running, goes through one batched H|psi> (batch.cu).
+template <typename T>
+static int davidson_batch_run(qe_ctx* ctx, std::vector<DvSolve>& vs,
+                              const std::vector<qe_problem>& probs, cudaStream_t st,
+                              std::vector<int>& rcs) {
+  Prof* pf = &ctx->prof;
+  const int np = (int)vs.size();
+  auto apply_pending = [&](int precision) -> int {
+    std::vector<qe_problem> pr;
+    std::vector<const double*> in;
+    std::vector<double*> out;
+    for (int p = 0; p < np; ++p) {
+      DvSolve& v = vs[p];
+      if (rcs[p] != QE_OK || v.h_rows == 0) continue;
+      qe_problem q = probs[p];
+      q.nbnd = v.h_rows;
+      pr.push_back(q);
+      const size_t off = (size_t)v.h_row * v.S.npw;
+      in.push_back((const double*)(v.S.V + off));
+      out.push_back((double*)(v.S.HV + off));
+    }
+    if (pr.empty()) return QE_OK;
+    return hpsi_batch_core(ctx, (int)pr.size(), pr.data(), precision, in.data(), out.data(), st);
+  };
+  for (int p = 0; p < np; ++p) rcs[p] = dv_begin(vs[p], st);
+  DV_TRY(apply_pending(vs[0].precision));
+  for (int p = 0; p < np; ++p)
+    if (rcs[p] == QE_OK) rcs[p] = dv_after_first_h<T>(vs[p], st, pf);
+  while (true) {
+    bool any = false;
+    for (int p = 0; p < np; ++p)
+      if (rcs[p] == QE_OK && !vs[p].done) rcs[p] = dv_step_launch<T>(vs[p], st, pf);
+    for (int p = 0; p < np; ++p) {
+      DvSolve& v = vs[p];
+      if (rcs[p] != QE_OK || v.done) continue;
+      rcs[p] = dv_step_finish<T>(ctx, v, st, pf);
+      if (rcs[p] == QE_OK && !v.done) any = true;
+    }
+    if (!any) break;
+    DV_TRY(apply_pending(vs[0].precision));
+    for (int p = 0; p < np; ++p) {
+      DvSolve& v = vs[p];
+      if (rcs[p] == QE_OK && !v.done && v.h_rows > 0) rcs[p] = dv_after_h<T>(v, st, pf);
+    }
+  }
+  if (vs[0].precision != QE_FP64) {
+    for (int p = 0; p < np; ++p) {
+      DvSolve& v = vs[p];
+      v.h_rows = 0;
+      if (rcs[p] != QE_OK) continue;
+      rcs[p] = refine_pre(v.S, st);
+      v.h_row = 0;
+      v.h_rows = v.S.nb;
+    }
+    DV_TRY(apply_pending(QE_FP64));
+    for (int p = 0; p < np; ++p)
+      if (rcs[p] == QE_OK) rcs[p] = refine_post(vs[p].S, st, pf);
+  }
   return QE_OK;
 }
 
 }  // namespace qe
 
 using namespace qe;
+
+namespace {
+
+// Checks of one problem's arguments, its plan and operator, and the layout of
+// its Davidson workspace in `basis` / `red`.
+int dv_setup(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int max_iter,
+             int max_dim, DevBuf& basis, DevBuf& red, DvSolve& v, cudaStream_t st, const char* who) {
+  DV_TRY(check_problem(prob, who));
+  const int nb = prob->nbnd;
+  DevPlan* P = nullptr;
+  DV_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
+  const int npw = P->h.npw;
+  if (nb > npw) { set_error("%s: %d bands > %d plane waves", who, nb, npw); return QE_EINVAL; }
+  int md = max_dim > 0 ? max_dim : 4 * nb;
+  if (md < 2 * nb) { set_error("%s: max_dim %d < 2 nbnd", who, md); return QE_EINVAL; }
+  md = std::min(md, std::max(2 * nb, npw));
+  if (md > kMaxDense) { set_error("%s: max_dim %d above %d", who, md, kMaxDense); return QE_EINVAL; }
+  v.P = P;
+  DV_TRY(resolve_operator(ctx, prob, *P, v.op, st));
+  v.precision = precision;
+  v.tol = tol;
+  v.max_iter = max_iter;
+  DvState& S = v.S;
+  S.npw = npw;
+  S.nb = nb;
+  S.max_dim = md;
+  S.np = prob->nproj;
+  return dv_alloc(basis, red, S);
+}
+
+// Final status of a solve: barrier and overlap checks of the last Rayleigh-Ritz.
+int dv_final_status(DvSolve& v, cudaStream_t st, const char* who) {
+  int fin[16];
+  DV_CU(cudaMemcpyAsync(fin, v.S.dw.status, sizeof(fin), cudaMemcpyDeviceToHost, st));
+  DV_CU(cudaStreamSynchronize(st));
+  if (fin[8] != 0) { set_error("%s: a grid barrier of the dense eigensolver timed out", who); return QE_ETIMEOUT; }
+  if (fin[0] != 0) { set_error("%s: final overlap matrix not positive definite", who); return QE_ENOCONV; }
+  return QE_OK;
+}
+
+}  // namespace
 
 extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
                            int max_iter, int max_dim, double* psi_inout, double* evals,
@@ -510,46 +679,104 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   DV_CU(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   DV_TRY(ctx_begin(ctx, st));
-  DevPlan* P = nullptr;
-  DV_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
-  const int npw = P->h.npw;
-  if (nb > npw) { set_error("qe_davidson: %d bands > %d plane waves", nb, npw); return QE_EINVAL; }
-  int md = max_dim > 0 ? max_dim : 4 * nb;
-  if (md < 2 * nb) { set_error("qe_davidson: max_dim %d < 2 nbnd", md); return QE_EINVAL; }
-  md = std::min(md, std::max(2 * nb, npw));
-  if (md > kMaxDense) { set_error("qe_davidson: max_dim %d above %d", md, kMaxDense); return QE_EINVAL; }
-  OpView op;
-  DV_TRY(resolve_operator(ctx, prob, *P, op, st));
-  DvState S;
-  S.npw = npw;
-  S.nb = nb;
-  S.max_dim = md;
-  S.np = prob->nproj;
-  DV_TRY(dv_alloc(ctx, S));
-  const size_t bytes = (size_t)nb * npw * sizeof(z);
+  DvSolve v;
+  DV_TRY(dv_setup(ctx, prob, precision, tol, max_iter, max_dim, ctx->dv_basis, ctx->dv_red, v, st,
+                  "qe_davidson"));
+  DvState& S = v.S;
+  const size_t bytes = (size_t)nb * S.npw * sizeof(z);
   const cudaMemcpyKind in_kind = prob->mem == QE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const cudaMemcpyKind out_kind = prob->mem == QE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   DV_CU(cudaMemcpyAsync(S.V, psi_inout, bytes, in_kind, st));
-  int it = 0;
-  bool conv = false;
-  int rc = precision == QE_FP64
-               ? davidson_run<double>(ctx, *P, op, precision, tol, max_iter, S, &it, &conv, st)
-               : davidson_run<float>(ctx, *P, op, precision, tol, max_iter, S, &it, &conv, st);
-  if (iters) *iters = it;
+  int rc = precision == QE_FP64 ? davidson_run<double>(ctx, v, st) : davidson_run<float>(ctx, v, st);
+  if (iters) *iters = v.it;
   if (rc && rc != QE_ENOCONV) return rc;
   DV_CU(cudaMemcpyAsync(psi_inout, S.Psi, bytes, out_kind, st));
   DV_CU(cudaMemcpyAsync(evals, S.e, nb * sizeof(double), out_kind, st));
   if (resid) DV_CU(cudaMemcpyAsync(resid, S.rn, nb * sizeof(double), out_kind, st));
-  int fin[16];
-  DV_CU(cudaMemcpyAsync(fin, S.dw.status, sizeof(fin), cudaMemcpyDeviceToHost, st));
-  DV_CU(cudaStreamSynchronize(st));
-  if (fin[8] != 0) { set_error("qe_davidson: a grid barrier of the dense eigensolver timed out"); return QE_ETIMEOUT; }
-  if (fin[0] != 0) { set_error("qe_davidson: final overlap matrix not positive definite"); return QE_ENOCONV; }
+  DV_TRY(dv_final_status(v, st, "qe_davidson"));
   DV_TRY(tc_check(ctx, st));
   if (rc == QE_ENOCONV) return rc;
-  if (!conv) {
-    set_error("qe_davidson: not converged after %d iterations", it);
+  if (!v.conv) {
+    set_error("qe_davidson: not converged after %d iterations", v.it);
     return QE_ENOCONV;
   }
   return QE_OK;
+}
+
+extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs, int precision,
+                                 double tol, int max_iter, int max_dim, double* const* psi_inout,
+                                 double* const* evals, double* const* resid, int* iters,
+                                 int* status, void* stream) {
+  clear_error();
+  if (!ctx) { set_error("qe_davidson_batch: null context"); return QE_EINVAL; }
+  if (nprob < 0 || (nprob > 0 && (!probs || !psi_inout || !evals))) {
+    set_error("qe_davidson_batch: bad problem list");
+    return QE_EINVAL;
+  }
+  if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_davidson_batch: bad precision"); return QE_EINVAL; }
+  if (!(tol > 0.0) || max_iter < 0) { set_error("qe_davidson_batch: tol must be > 0, max_iter >= 0"); return QE_EINVAL; }
+  for (int p = 0; p < nprob; ++p) {
+    DV_TRY(check_problem(&probs[p], "qe_davidson_batch"));
+    if (probs[p].mem != QE_DEVICE) {
+      set_error("qe_davidson_batch: problem %d: arrays must be device memory", p);
+      return QE_EINVAL;
+    }
+    if (probs[p].nbnd > 0 && (!psi_inout[p] || !evals[p])) {
+      set_error("qe_davidson_batch: problem %d: null psi/evals", p);
+      return QE_EINVAL;
+    }
+    if (iters) iters[p] = 0;
+    if (status) status[p] = QE_OK;
+  }
+  if (nprob == 0) return QE_OK;
+  DV_CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  DV_TRY(ctx_begin(ctx, st));
+  // the solves with bands, each with its own workspace
+  std::vector<int> ids;
+  for (int p = 0; p < nprob; ++p)
+    if (probs[p].nbnd > 0) ids.push_back(p);
+  const int ns = (int)ids.size();
+  while ((int)ctx->dvb_basis.size() < ns) {
+    ctx->dvb_basis.push_back(std::make_unique<DevBuf>());
+    ctx->dvb_red.push_back(std::make_unique<DevBuf>());
+    ctx->dvb_basis.back()->sp = &ctx->cur;
+    ctx->dvb_red.back()->sp = &ctx->cur;
+  }
+  std::vector<DvSolve> vs(ns);
+  std::vector<qe_problem> sub(ns);
+  for (int i = 0; i < ns; ++i) {
+    const int p = ids[i];
+    sub[i] = probs[p];
+    DV_TRY(dv_setup(ctx, &probs[p], precision, tol, max_iter, max_dim, *ctx->dvb_basis[i],
+                    *ctx->dvb_red[i], vs[i], st, "qe_davidson_batch"));
+    DV_CU(cudaMemcpyAsync(vs[i].S.V, psi_inout[p], (size_t)vs[i].S.nb * vs[i].S.npw * sizeof(z),
+                          cudaMemcpyDeviceToDevice, st));
+  }
+  std::vector<int> rcs(ns, QE_OK);
+  DV_TRY(precision == QE_FP64 ? davidson_batch_run<double>(ctx, vs, sub, st, rcs)
+                              : davidson_batch_run<float>(ctx, vs, sub, st, rcs));
+  int worst = QE_OK;
+  for (int i = 0; i < ns; ++i) {
+    const int p = ids[i];
+    DvSolve& v = vs[i];
+    int rc = rcs[i];
+    if (iters) iters[p] = v.it;
+    if (rc == QE_OK || rc == QE_ENOCONV) {
+      const int nb = v.S.nb;
+      DV_CU(cudaMemcpyAsync(psi_inout[p], v.S.Psi, (size_t)nb * v.S.npw * sizeof(z),
+                            cudaMemcpyDeviceToDevice, st));
+      DV_CU(cudaMemcpyAsync(evals[p], v.S.e, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      if (resid && resid[p])
+        DV_CU(cudaMemcpyAsync(resid[p], v.S.rn, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      const int frc = dv_final_status(v, st, "qe_davidson_batch");
+      if (frc) rc = frc;
+      else if (rc == QE_OK && !v.conv) rc = QE_ENOCONV;
+    }
+    if (status) status[p] = rc;
+    if (rc != QE_OK && (worst == QE_OK || worst == QE_ENOCONV)) worst = rc;
+  }
+  DV_TRY(tc_check(ctx, st));
+  if (worst == QE_ENOCONV) set_error("qe_davidson_batch: some problems did not converge");
+  return worst;
 }

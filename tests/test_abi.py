@@ -100,3 +100,24 @@ def test_context_without_gpu_fails_cleanly(q):
     with pytest.raises(q.QEError) as e:
         q.Context(0)
     assert e.value.code == q.QE_ECUDA
+
+
+def test_problem_keeps_its_arrays_alive(q):
+    """A problem descriptor holds raw pointers; the binding must keep the arrays
+    it was built from alive for as long as the descriptor lives (temporaries
+    passed straight into problem() included)."""
+    import gc
+    import weakref
+    c = qeinputs.config("SMALL")
+    v = np.zeros((c["grid"][2], c["grid"][1], c["grid"][0]))
+    beta = np.zeros((2, 10, 2))
+    d = np.eye(2)
+    refs = [weakref.ref(a) for a in (v, beta, d)]
+    pr = q.problem(c["lat"], c["k"], c["ecut"], c["grid"], v, beta, d, 1)
+    del v, beta, d
+    gc.collect()
+    assert all(r() is not None for r in refs)
+    assert pr.vloc_r == refs[0]().ctypes.data
+    del pr
+    gc.collect()
+    assert all(r() is None for r in refs)
