@@ -329,6 +329,7 @@ def run_gpu(args, rank, world, local_rank):
 
     dav = run_davidson_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
     srv = run_serve_bench(q, ctx, dev, local_rank) if (rank == 0 and not args.no_solvers) else None
+    bat = run_batch_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
 
     line = None
     if rank == 0:
@@ -351,7 +352,7 @@ def run_gpu(args, rank, world, local_rank):
                 "mixed": {"value": mixed_value, "unit": "bands/s", "ms_per_step": ms_mixed / args.steps,
                           "dtype": "fp32 FFT + TF32x3 tensor-core projector products",
                           "kernels": kernels_mixed},
-                "kernels": kernels, "peaks": pk_kind, "davidson": dav, "serve": srv}
+                "kernels": kernels, "peaks": pk_kind, "davidson": dav, "serve": srv, "batch": bat}
         print(json.dumps(line), flush=True)
     ctx.close()
     return line
@@ -432,6 +433,76 @@ def run_davidson_bench(q, ctx, dev):
         f, m = out.get(f"{name}_fp64"), out.get(f"{name}_mixed")
         if f and m:
             out[f"{name}_mixed_speedup"] = m["solves_per_s"] / f["solves_per_s"]
+    return out
+
+
+def run_batch_bench(q, ctx, dev):
+    """The batched workload (C3: 16 k points of the tetragonal cell + 32 cubic
+    cells, 48 problems of different grids and band counts): batched H|psi>
+    (eager and CUDA-graph replay) against one qe_hpsi per problem, and the
+    lockstep batched Davidson against one qe_davidson per problem, FP64 and
+    mixed.  Batched and sequential results must agree bit for bit."""
+    import torch
+    specs = qeinputs.c3_problems()
+    items = [device_problem(q, ctx, p["lat"], p["k"], p["ecut"], p["grid"], p["tau"], p["widths"],
+                            p["nbnd"], p["psi_seed"], dev) for p in specs]
+    probs = [it[0] for it in items]
+    psis = [it[1] for it in items]
+    nbands = sum(p.nbnd for p in probs)
+    tol = specs[0]["tol"]
+    out = {"problems": len(probs), "bands": nbands, "tol": tol,
+           "workload": "C3: tetragonal 12x12x24 bohr, 24 atoms, 30 Ry, grid 48x48x96, 16 k points, "
+                       "64 bands; + 32 cubic cells a in U{8..16}, 2-24 atoms, nb in U{16..96}, 30 Ry"}
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize(dev)
+            ts.append(time.perf_counter() - t0)
+        return float(np.median(ts))
+
+    for prec, tag in ((q.QE_FP64, "fp64"), (q.QE_MIXED, "mixed")):
+        hs = [torch.empty_like(x) for x in psis]
+        hb = [torch.empty_like(x) for x in psis]
+        t_seq = timed(lambda: [ctx.hpsi(p, x, h, prec) for p, x, h in zip(probs, psis, hs)])
+        t_bat = timed(lambda: ctx.hpsi_batch(probs, psis, hb, prec))
+        g = ctx.batch_create(probs, psis, hb, prec)
+        t_gr = timed(lambda: g.run())
+        g.close()
+        same = all(torch.equal(a, b) for a, b in zip(hs, hb))
+        r = {"hpsi_bands_per_s_sequential": nbands / t_seq, "hpsi_bands_per_s_batched": nbands / t_bat,
+             "hpsi_bands_per_s_graph": nbands / t_gr, "hpsi_identical": bool(same)}
+        # Davidson: one pass each way (solves are long enough to time singly)
+        tol_p = tol if prec == q.QE_FP64 else 1e-5
+        seq_ev, seq_it = [], []
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for p, x in zip(probs, psis):
+            pt = x.clone()
+            ev = torch.zeros(p.nbnd, dtype=torch.float64, device=dev)
+            rc, it = ctx.davidson(p, pt, ev, None, precision=prec, tol=tol_p, max_iter=200)
+            seq_ev.append(ev)
+            seq_it.append(it)
+        torch.cuda.synchronize(dev)
+        t_dseq = time.perf_counter() - t0
+        bpsi = [x.clone() for x in psis]
+        bev = [torch.zeros(p.nbnd, dtype=torch.float64, device=dev) for p in probs]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, sts, its = ctx.davidson_batch(probs, bpsi, bev, precision=prec, tol=tol_p, max_iter=200)
+        torch.cuda.synchronize(dev)
+        t_dbat = time.perf_counter() - t0
+        r.update({"davidson_tol": tol_p, "solves_per_s_sequential": len(probs) / t_dseq,
+                  "solves_per_s_batched": len(probs) / t_dbat, "batched_speedup": t_dseq / t_dbat,
+                  "converged": int(sum(s == q.QE_OK for s in sts)),
+                  "eigs_identical": bool(all(torch.equal(a, b) for a, b in zip(seq_ev, bev))),
+                  "iters_identical": bool(seq_it == its), "max_iters": int(max(its))})
+        out[tag] = r
+    del items
     return out
 
 

@@ -133,3 +133,50 @@ def config(name: str) -> dict:
                     grid=(24, 27, 30), tau=tau, widths=(1.0, 0.7), nbnd=7,
                     tol=1e-8, psi_seed=11)
     raise KeyError(name)
+
+
+def smooth235(n: int) -> int:
+    """Smallest integer >= n whose only prime factors are 2, 3 and 5."""
+    m = max(1, int(n))
+    while True:
+        r = m
+        for f in (2, 3, 5):
+            while r % f == 0:
+                r //= f
+        if r == 1:
+            return m
+        m += 1
+
+
+def c3_problems() -> list:
+    """The batched workload: the C3T cell at its 16 Gamma-centred k points
+    (k = (i/4) b1 + (j/4) b2, i, j = 0..3), then 32 cubic cells with
+    a in U{8..16} bohr, 2..24 atoms (fewer in the smallest cells, so that
+    rejection sampling at 2.5 bohr separation stays quick: at most a^3/24),
+    nb in U{16..96}, 30 Ry, 4 projectors per atom (w = 1 bohr) and each grid
+    dimension the smallest 2,3,5-smooth N >= 2 floor(a sqrt(ecut) / 2 pi) + 1
+    (the no-wrap bound on a cubic cell at Gamma).  Draws from
+    default_rng(5); start-band seeds 100 + index."""
+    t = config("C3T")
+    lat = t["lat"]
+    if np.count_nonzero(lat - np.diag(np.diag(lat))):
+        raise ValueError("c3_problems: orthogonal cell expected")
+    bdiag = 2.0 * np.pi / np.diag(lat)          # b_i of an orthogonal cell
+    out = []
+    for i, kf in enumerate(t["kfrac"]):
+        out.append(dict(lat=lat, k=kf * bdiag, ecut=t["ecut"], grid=t["grid"], tau=t["tau"],
+                        widths=t["widths"], nbnd=t["nbnd"], psi_seed=100 + i, tol=t["tol"]))
+    rng = np.random.default_rng(5)
+    for j in range(32):
+        a = int(rng.integers(8, 17))
+        natom = int(rng.integers(2, 25))
+        natom = max(2, min(natom, (a ** 3) // 24))
+        nb = int(rng.integers(16, 97))
+        aseed = int(rng.integers(0, 2 ** 31))
+        lat_c = cubic(float(a))
+        mmax = int(np.floor(a * np.sqrt(30.0) / (2.0 * np.pi)))
+        n = smooth235(2 * mmax + 1)
+        out.append(dict(lat=lat_c, k=np.zeros(3), ecut=30.0, grid=(n, n, n),
+                        tau=random_atoms(lat_c, natom, 2.5, seed=aseed), widths=(1.0,),
+                        nbnd=nb, psi_seed=100 + len(out), tol=t["tol"]))
+    return out

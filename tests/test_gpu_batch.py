@@ -227,3 +227,34 @@ def test_davidson_batch_reports_nonconvergence_per_problem():
         assert rc == q.QE_ENOCONV
         assert sts == [q.QE_ENOCONV] * 3 and its == [1, 1, 1]
         assert all(torch.isfinite(e).all() for e in evs)
+
+
+def test_c3_cubes_batched_davidson_against_oracle():
+    """The 32 cubic cells of the batched workload (grids 15^3..27^3, 16..96
+    bands) solved as one lockstep batch; the cells small enough for the
+    oracle's dense diagonalisation (a <= 9 bohr) within 1e-10 Ry."""
+    import paper_2104_10502_gb300 as q
+    specs = qeinputs.c3_problems()[16:]
+    with q.Context(0) as ctx:
+        items = [_prob(q, ctx, p["lat"], p["k"], p["ecut"], p["grid"], p["tau"], p["widths"],
+                       p["nbnd"], 0) for p in specs]
+        for it, p in zip(items, specs):
+            _, kin = q.gsphere(p["lat"], p["k"], p["ecut"], p["grid"])
+            psi0 = qeinputs.start_bands(kin, p["nbnd"], p["psi_seed"])
+            it["psi"] = torch.from_numpy(psi0.view(np.float64).reshape(p["nbnd"], len(kin), 2).copy()).to(0)
+        evs = [torch.zeros(p["nbnd"], dtype=torch.float64, device="cuda") for p in specs]
+        rc, sts, its = ctx.davidson_batch([it["prob"] for it in items], [it["psi"] for it in items],
+                                          evs, tol=1e-8, max_iter=300)
+        assert rc == q.QE_OK, (sts, its)
+        checked = 0
+        for p, e in zip(specs, evs):
+            if p["lat"][0, 0] > 9.0:
+                continue
+            v = oracle.vloc_gaussian(p["lat"], p["grid"], p["tau"])
+            beta = oracle.beta_gaussian(p["lat"], p["k"], p["ecut"], p["tau"], p["widths"])
+            d = qeinputs.d_matrix(len(p["tau"]), len(p["widths"]))
+            h = oracle.dense_h(p["lat"], p["k"], p["ecut"], p["grid"], v, beta, d)
+            ref = np.linalg.eigvalsh(h)[:p["nbnd"]]
+            assert np.abs(e.cpu().numpy() - ref).max() <= 1e-10
+            checked += 1
+        assert checked >= 4
