@@ -73,8 +73,9 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   __syncthreads();
   fft_lines<T, +1, false>(line, spb, 1, nullptr, ns, true, J.r3, tw);
   cx<T>* Wb = J.W + (size_t)b * n3 * nst;
+  const FastDiv fns(ns);
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
-    const int pz = i / ns, l = i - pz * ns;
+    const int pz = fns.div(i), l = i - pz * ns;
     Wb[(size_t)pz * nst + s0 + l] = line[pz * spb + l];
   }
 }
@@ -113,8 +114,9 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   const int ns = min(spb, nst - s0);
   for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(J.tw3[2 * i]), T(J.tw3[2 * i + 1])};
   const cx<T>* Wb = J.W + (size_t)b * n3 * nst;
+  const FastDiv fns(ns);
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
-    const int pz = i / ns, l = i - pz * ns;
+    const int pz = fns.div(i), l = i - pz * ns;
     line[pz * spb + l] = Wb[(size_t)pz * nst + s0 + l];
   }
   __syncthreads();

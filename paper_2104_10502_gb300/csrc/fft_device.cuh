@@ -103,6 +103,22 @@ __device__ __forceinline__ cx<T> twid(const cx<T>* tw, int t) {
   return SIGN < 0 ? w : cx<T>{w.x, -w.y};
 }
 
+// Division by a divisor fixed for a whole stage: q = hi32(x * ceil(2^32 / d)),
+// exact for x, d < 2^16 (x d < 2^32 bounds the rounding of the multiplier
+// below the gap 1/d between x/d and the next integer).  Replaces the runtime
+// integer divisions in the butterfly index arithmetic.  Every index it divides
+// counts elements of one shared-memory tile (at most 227 KB / 8 B < 2^15), and
+// every divisor is a line count or length within that tile.
+struct FastDiv {
+  unsigned d, m;
+  __device__ __forceinline__ explicit FastDiv(int dv) : d((unsigned)dv) {
+    m = d <= 1 ? 0u : (unsigned)(0xFFFFFFFFu / d) + 1u;
+  }
+  __device__ __forceinline__ int div(int x) const {
+    return d <= 1 ? x : (int)__umulhi((unsigned)x, m);
+  }
+};
+
 // One radix-R stage over `nlines` lines of length n.  Element e of line l sits
 // at base[lofs(l) + e * es], lofs(l) = lofs_tab ? lofs_tab[l] : l * ls.
 // line_fast selects which index varies fastest across consecutive threads
@@ -115,11 +131,12 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
   const int per_line = n / R;
   const int nit = nlines * per_line;
   const int tstep = n / L;
+  const FastDiv fd_lines(nlines), fd_per(per_line), fd_m(M);
   for (int it = threadIdx.x; it < nit; it += blockDim.x) {
     int line, rest;
-    if (line_fast) { line = it % nlines; rest = it / nlines; }
-    else { line = it / per_line; rest = it - line * per_line; }
-    const int blk = rest / M;
+    if (line_fast) { rest = fd_lines.div(it); line = it - rest * nlines; }
+    else { line = fd_per.div(it); rest = it - line * per_line; }
+    const int blk = fd_m.div(rest);
     const int j = rest - blk * M;
     const int off = lofs_tab ? lofs_tab[line] : line * ls;
     cx<T>* p = base + off + (blk * L + j) * es;
