@@ -80,6 +80,18 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   }
 }
 
+// The plane stage fuses radix stages in pairs in single precision (its FP32
+// butterflies are issue-bound); in FP64 the extra registers cost more than the
+// saved shared-memory passes.
+template <typename T>
+constexpr bool kFusePlane = sizeof(T) == 4;
+
+// Launch bounds of the plane stage.  FP32: two CTAs of 256 threads per SM and
+// up to 128 registers for the fused stage pairs (capping registers for a third
+// CTA makes the fused butterflies spill).
+template <typename T> struct PlaneLB { static constexpr int threads = 512, minb = 1; };
+template <> struct PlaneLB<float> { static constexpr int threads = 256, minb = 2; };
+
 template <typename T>
 __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* smem) {
   const int n1 = J.r1.n, n2 = J.r2.n, n3 = J.r3.n, nst = J.nst, nax = J.nax;
@@ -95,13 +107,13 @@ __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* sme
   cx<T>* Wp = J.W + ((size_t)b * n3 + pz) * nst;
   for (int s = threadIdx.x; s < nst; s += blockDim.x) plane[J.st_y[s] * n1 + J.st_x[s]] = Wp[s];
   __syncthreads();
-  fft_lines<T, +1, false>(plane, n1, 0, ax, nax, true, J.r2, tw2);        // y, active columns
-  fft_lines<T, +1, false>(plane, 1, n1, nullptr, n2, false, J.r1, tw1);   // x, every row
+  fft_lines<T, +1, false, kFusePlane<T>>(plane, n1, 0, ax, nax, true, J.r2, tw2);        // y, active columns
+  fft_lines<T, +1, false, kFusePlane<T>>(plane, 1, n1, nullptr, n2, false, J.r1, tw1);   // x, every row
   const T* v = J.vp + (size_t)pz * n1 * n2;
   for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) plane[i] = cscale(plane[i], v[i]);
   __syncthreads();
-  fft_lines<T, -1, true>(plane, 1, n1, nullptr, n2, false, J.r1, tw1);
-  fft_lines<T, -1, true>(plane, n1, 0, ax, nax, true, J.r2, tw2);
+  fft_lines<T, -1, true, kFusePlane<T>>(plane, 1, n1, nullptr, n2, false, J.r1, tw1);
+  fft_lines<T, -1, true, kFusePlane<T>>(plane, n1, 0, ax, nax, true, J.r2, tw2);
   for (int s = threadIdx.x; s < nst; s += blockDim.x) Wp[s] = plane[J.st_y[s] * n1 + J.st_x[s]];
 }
 
@@ -141,7 +153,7 @@ __global__ void __launch_bounds__(512) k_zinv(const FftJob<T> J) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_plane(const FftJob<T> J) {
+__global__ void __launch_bounds__(PlaneLB<T>::threads, PlaneLB<T>::minb) k_plane(const FftJob<T> J) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   plane_tile<T>(J, blockIdx.y, blockIdx.x, smem_raw);
 }
@@ -156,7 +168,13 @@ __global__ void __launch_bounds__(512) k_zfwd(const FftJob<T> J) {
 // Items of job j are [prefix[j], prefix[j+1]); item i of a job maps to
 // (band, tile) = (i / tiles, i % tiles).  counter must be zero at launch.
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(512) k_fft_batch(const FftJob<T>* __restrict__ jobs,
+struct BatchLB {
+  static constexpr int threads = STAGE == 1 ? PlaneLB<T>::threads : 512;
+  static constexpr int minb = STAGE == 1 ? PlaneLB<T>::minb : 1;
+};
+
+template <typename T, int STAGE>
+__global__ void __launch_bounds__(BatchLB<T, STAGE>::threads, BatchLB<T, STAGE>::minb) k_fft_batch(const FftJob<T>* __restrict__ jobs,
                                                    const int* __restrict__ prefix, int njobs,
                                                    int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -278,7 +296,8 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
   set_max_dynamic_smem(k_plane<T>);
   set_max_dynamic_smem(k_zinv<T>);
   set_max_dynamic_smem(k_zfwd<T>);
-  const int zt = sh.zthreads > 0 ? sh.zthreads : 256, pt = sh.pthreads > 0 ? sh.pthreads : 256;
+  const int zt = sh.zthreads > 0 ? sh.zthreads : 256;
+  const int pt = std::min(sh.pthreads > 0 ? sh.pthreads : 256, PlaneLB<T>::threads);
   dim3 gz(J.nsb, nbc);
   int rc;
   {

@@ -170,19 +170,145 @@ __device__ __forceinline__ void fft_stage_any(cx<T>* base, int es, int ls, const
   }
 }
 
-// Whole in-place transform of every line; ends with __syncthreads().
-// Must be called by every thread of the block.
+// Two consecutive stages fused in registers: stage a (radix RA over spans of
+// length L) and stage b (radix RB over the spans of length L / RA it leaves).
+// A work item holds the RA x RB elements blk L + jb + qb Mb + qa Ma (Ma = L/RA,
+// Mb = Ma/RB, qa < RA, qb < RB): exactly the elements that the RB stage-a
+// butterflies j = jb + qb Mb produce and the RA stage-b butterflies j = jb
+// consume.  Every element sees the same operations in the same order as in
+// two separate stages (bit-identical results), with one shared-memory round
+// trip and one barrier instead of two.  DIF applies a then b, DIT b then a.
+template <typename T, int SIGN, bool DIT, int RA, int RB>
+__device__ __forceinline__ void fft_stage2(cx<T>* base, int es, int ls, const int* lofs_tab,
+                                           int nlines, bool line_fast, int n, int L,
+                                           const cx<T>* tw) {
+  const int Ma = L / RA, Mb = Ma / RB;
+  const int per_line = n / (RA * RB);
+  const int nit = nlines * per_line;
+  const int tsa = n / L, tsb = n / Ma;
+  const FastDiv fd_lines(nlines), fd_per(per_line), fd_mb(Mb);
+  for (int it = threadIdx.x; it < nit; it += blockDim.x) {
+    int line, rest;
+    if (line_fast) { rest = fd_lines.div(it); line = it - rest * nlines; }
+    else { line = fd_per.div(it); rest = it - line * per_line; }
+    const int blk = fd_mb.div(rest);
+    const int jb = rest - blk * Mb;
+    const int off = lofs_tab ? lofs_tab[line] : line * ls;
+    cx<T>* p = base + off + (blk * L + jb) * es;
+    const int sa = Ma * es, sb = Mb * es;
+    cx<T> v[RA][RB];
+#pragma unroll
+    for (int qa = 0; qa < RA; ++qa)
+#pragma unroll
+      for (int qb = 0; qb < RB; ++qb) v[qa][qb] = p[qa * sa + qb * sb];
+    if (!DIT) {
+#pragma unroll
+      for (int qb = 0; qb < RB; ++qb) {
+        cx<T> u[RA];
+#pragma unroll
+        for (int qa = 0; qa < RA; ++qa) u[qa] = v[qa][qb];
+        dftR<T, SIGN, RA>(u);
+        const int ja = jb + qb * Mb;
+#pragma unroll
+        for (int qa = 1; qa < RA; ++qa) u[qa] = cmul(u[qa], twid<T, SIGN>(tw, ja * qa * tsa));
+#pragma unroll
+        for (int qa = 0; qa < RA; ++qa) v[qa][qb] = u[qa];
+      }
+#pragma unroll
+      for (int qa = 0; qa < RA; ++qa) {
+        dftR<T, SIGN, RB>(v[qa]);
+#pragma unroll
+        for (int qb = 1; qb < RB; ++qb) v[qa][qb] = cmul(v[qa][qb], twid<T, SIGN>(tw, jb * qb * tsb));
+      }
+    } else {
+#pragma unroll
+      for (int qa = 0; qa < RA; ++qa) {
+#pragma unroll
+        for (int qb = 1; qb < RB; ++qb) v[qa][qb] = cmul(v[qa][qb], twid<T, SIGN>(tw, jb * qb * tsb));
+        dftR<T, SIGN, RB>(v[qa]);
+      }
+#pragma unroll
+      for (int qb = 0; qb < RB; ++qb) {
+        cx<T> u[RA];
+#pragma unroll
+        for (int qa = 0; qa < RA; ++qa) u[qa] = v[qa][qb];
+        const int ja = jb + qb * Mb;
+#pragma unroll
+        for (int qa = 1; qa < RA; ++qa) u[qa] = cmul(u[qa], twid<T, SIGN>(tw, ja * qa * tsa));
+        dftR<T, SIGN, RA>(u);
+#pragma unroll
+        for (int qa = 0; qa < RA; ++qa) v[qa][qb] = u[qa];
+      }
+    }
+#pragma unroll
+    for (int qa = 0; qa < RA; ++qa)
+#pragma unroll
+      for (int qb = 0; qb < RB; ++qb) p[qa * sa + qb * sb] = v[qa][qb];
+  }
+}
+
+// Largest register tile of a fused pair (complex elements per work item).
+template <typename T>
+__host__ __device__ constexpr int fuse_limit() { return sizeof(T) == 8 ? 16 : 20; }
+
+template <typename T, int SIGN, bool DIT, int RA>
+__device__ __forceinline__ void fft_stage2_b(cx<T>* base, int es, int ls, const int* lofs,
+                                             int nlines, bool line_fast, int n, int RB, int L,
+                                             const cx<T>* tw) {
+  switch (RB) {
+    case 2: fft_stage2<T, SIGN, DIT, RA, 2>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
+    case 3: fft_stage2<T, SIGN, DIT, RA, 3>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
+    case 4: fft_stage2<T, SIGN, DIT, RA, 4>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
+    default:
+      if constexpr (RA * 5 <= fuse_limit<T>())
+        fft_stage2<T, SIGN, DIT, RA, 5>(base, es, ls, lofs, nlines, line_fast, n, L, tw);
+      break;
+  }
+}
+
 template <typename T, int SIGN, bool DIT>
+__device__ __forceinline__ void fft_stage2_any(cx<T>* base, int es, int ls, const int* lofs,
+                                               int nlines, bool line_fast, int n, int RA, int RB,
+                                               int L, const cx<T>* tw) {
+  switch (RA) {
+    case 2: fft_stage2_b<T, SIGN, DIT, 2>(base, es, ls, lofs, nlines, line_fast, n, RB, L, tw); break;
+    case 3: fft_stage2_b<T, SIGN, DIT, 3>(base, es, ls, lofs, nlines, line_fast, n, RB, L, tw); break;
+    case 4: fft_stage2_b<T, SIGN, DIT, 4>(base, es, ls, lofs, nlines, line_fast, n, RB, L, tw); break;
+    default: fft_stage2_b<T, SIGN, DIT, 5>(base, es, ls, lofs, nlines, line_fast, n, RB, L, tw); break;
+  }
+}
+
+// Whole in-place transform of every line; ends with __syncthreads().
+// Must be called by every thread of the block.  With FUSE, consecutive stages
+// are fused in pairs while the pair's register tile stays within fuse_limit
+// (same results; fewer shared-memory passes for more registers per thread).
+template <typename T, int SIGN, bool DIT, bool FUSE = false>
 __device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlines,
                           bool line_fast, const Radix& rp, const cx<T>* tw) {
   if (!DIT) {
-    for (int s = 0; s < rp.nst; ++s) {
-      fft_stage_any<T, SIGN, false>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s], rp.L[s], tw);
+    int s = 0;
+    while (s < rp.nst) {
+      if (FUSE && s + 1 < rp.nst && rp.r[s] * rp.r[s + 1] <= fuse_limit<T>()) {
+        fft_stage2_any<T, SIGN, false>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
+                                       rp.r[s + 1], rp.L[s], tw);
+        s += 2;
+      } else {
+        fft_stage_any<T, SIGN, false>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s], rp.L[s], tw);
+        s += 1;
+      }
       __syncthreads();
     }
   } else {
-    for (int s = rp.nst - 1; s >= 0; --s) {
-      fft_stage_any<T, SIGN, true>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s], rp.L[s], tw);
+    int s = rp.nst - 1;
+    while (s >= 0) {
+      if (FUSE && s >= 1 && rp.r[s - 1] * rp.r[s] <= fuse_limit<T>()) {
+        fft_stage2_any<T, SIGN, true>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s - 1],
+                                      rp.r[s], rp.L[s - 1], tw);
+        s -= 2;
+      } else {
+        fft_stage_any<T, SIGN, true>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s], rp.L[s], tw);
+        s -= 1;
+      }
       __syncthreads();
     }
   }
