@@ -143,18 +143,21 @@ KERNEL_SOURCES = {"k_plane": ("fft.cu", "fft_device.cuh"), "k_zinv": ("fft.cu", 
 
 
 def traffic_for(kernel, tag):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    sources are unchanged since the capture (else None)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch (read + write, one ncu capture of this bench's own
+    launches) from the table in profiles/traffic_c1.md, if the kernel's sources
+    are unchanged since the capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic_c1.md")
     try:
         with open(p) as f:
-            d = json.load(f)
-        e = d[f"{kernel}:{tag}"]
-        if e.get("src") != src_hash(*KERNEL_SOURCES[kernel]):
-            return None
-        return e["bytes_per_launch"]
+            for line in f:
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) >= 5 and cells[0] == kernel and cells[1] == tag:
+                    if cells[4] != src_hash(*KERNEL_SOURCES[kernel]):
+                        return None
+                    return float(cells[2])
     except Exception:
         return None
+    return None
 
 
 def c1_cpu_inputs(c):

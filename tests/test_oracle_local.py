@@ -143,3 +143,15 @@ def test_dense_matrix_agrees_with_operator():
     x = qeinputs.random_vectors(3, h.shape[0], seed=4)
     np.testing.assert_allclose(oracle.hpsi(lat, k, ecut, grid, v, beta, d, x), x @ h.T,
                                rtol=0, atol=1e-12)
+
+
+def test_preconditioner_diagonal_is_the_exact_diagonal_for_diagonal_d():
+    """h_G = |k+G|^2 + mean V + sum_i D_ii |B_i(G)|^2 is the exact diagonal of H
+    when D is diagonal: the local term's diagonal is V~(0) = mean V and the
+    nonlocal one is sum_ij B_i D_ij conj(B_j) at G = G'."""
+    lat, k, ecut, grid, v, beta, d = _small_problem()
+    assert np.count_nonzero(d - np.diag(np.diag(d))) == 0
+    _, kin, _ = oracle.gsphere(lat, k, ecut)
+    h = oracle.dense_h(lat, k, ecut, grid, v, beta, d)
+    np.testing.assert_allclose(oracle.h_diag(kin, v, beta, d), np.real(np.diag(h)), rtol=0,
+                               atol=1e-13 * np.abs(h).max())
