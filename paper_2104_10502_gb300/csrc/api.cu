@@ -106,6 +106,7 @@ int ctx_trim(qe_ctx* ctx) {
   ctx->dvb_red.clear();
   ctx_batch_release(ctx);
   ctx->tc_beta_tag = 0;
+  ctx->oz_beta_tag = 0;
   for (auto& p : ctx->plans)
     if (p->block) cudaFreeAsync(p->block, ctx->cur);
   ctx->plans.clear();
@@ -266,6 +267,22 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(nonlocal_tc(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->tc_beta.p, pack,
                        ctx->tc_work.p, ctx->tc_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof));
     ctx->tc_beta_tag = op.tag;
+  } else if (op.nproj > 0 && fp64_gemm_on_tensor_cores()) {
+    // FP64: FP64-accurate projector products on the BF16 tensor cores (Ozaki slices)
+    const int np = op.nproj;
+    QE_TRY(ctx->oz_work.ensure(nonlocal_oz_bytes(np, nb, npw)));
+    if (!ctx->tc_status.p) {
+      QE_TRY(ctx->tc_status.ensure(256));
+      QE_CU(cudaMemsetAsync(ctx->tc_status.p, 0, 256, st));
+    }
+    const void* before = ctx->oz_beta.p;
+    const size_t before_bytes = ctx->oz_beta.bytes;
+    QE_TRY(ctx->oz_beta.ensure(nonlocal_oz_beta_bytes(np, npw)));
+    if (ctx->oz_beta.p != before || ctx->oz_beta.bytes != before_bytes) ctx->oz_beta_tag = 0;
+    const bool slice = ctx->oz_beta_tag == 0 || ctx->oz_beta_tag != op.tag;
+    QE_TRY(nonlocal_oz(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->oz_beta.p, slice,
+                       ctx->oz_work.p, ctx->oz_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof));
+    ctx->oz_beta_tag = op.tag;
   } else if (op.nproj > 0) {
     const int np = op.nproj;
     QE_TRY(ctx->proj.ensure((size_t)np * nb * 2 * sizeof(double)));

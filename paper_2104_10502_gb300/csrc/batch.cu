@@ -27,12 +27,14 @@ static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 // batch (qe_batch) owns its own, because the graph keeps their addresses.
 struct BatchWork {
   cudaStream_t cur = nullptr;
-  DevBuf ws, part, proj, projd, tc_work, tc_beta, tc_status;
+  DevBuf ws, part, proj, projd, tc_work, tc_beta, tc_status, oz_work, oz_beta;
   BatchWork() {
-    for (DevBuf* b : {&ws, &part, &proj, &projd, &tc_work, &tc_beta, &tc_status}) b->sp = &cur;
+    for (DevBuf* b : {&ws, &part, &proj, &projd, &tc_work, &tc_beta, &tc_status, &oz_work, &oz_beta})
+      b->sp = &cur;
   }
   void release() {
-    for (DevBuf* b : {&ws, &part, &proj, &projd, &tc_work, &tc_beta, &tc_status}) b->release();
+    for (DevBuf* b : {&ws, &part, &proj, &projd, &tc_work, &tc_beta, &tc_status, &oz_work, &oz_beta})
+      b->release();
   }
 };
 
@@ -45,6 +47,7 @@ struct BatchLayout {
   size_t smem_z = 0, smem_p = 0;
   size_t np_max_part = 0, np_max_proj = 0;   // nonlocal workspaces (largest problem)
   size_t tc_work = 0, tc_beta = 0;
+  size_t oz_work = 0, oz_beta = 0;
 };
 
 template <typename T>
@@ -85,6 +88,8 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
       L.np_max_proj = std::max(L.np_max_proj, (size_t)op.nproj * pr->nbnd * 2 * sizeof(double));
       L.tc_work = std::max(L.tc_work, nonlocal_tc_bytes(op.nproj, pr->nbnd, P->h.npw));
       L.tc_beta = std::max(L.tc_beta, nonlocal_tc_beta_bytes(op.nproj, P->h.npw));
+      L.oz_work = std::max(L.oz_work, nonlocal_oz_bytes(op.nproj, pr->nbnd, P->h.npw));
+      L.oz_beta = std::max(L.oz_beta, nonlocal_oz_beta_bytes(op.nproj, P->h.npw));
     }
   }
   L.jobs_off = off;
@@ -102,10 +107,13 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
     if (sizeof(T) == sizeof(float)) {
       BT_TRY(W.tc_work.ensure(L.tc_work));
       BT_TRY(W.tc_beta.ensure(L.tc_beta));
-      if (!W.tc_status.p) {
-        BT_TRY(W.tc_status.ensure(256));
-        BT_CU(cudaMemsetAsync(W.tc_status.p, 0, 256, st));
-      }
+    } else if (fp64_gemm_on_tensor_cores()) {
+      BT_TRY(W.oz_work.ensure(L.oz_work));
+      BT_TRY(W.oz_beta.ensure(L.oz_beta));
+    }
+    if (!W.tc_status.p) {
+      BT_TRY(W.tc_status.ensure(256));
+      BT_CU(cudaMemsetAsync(W.tc_status.p, 0, 256, st));
     }
   }
   // job descriptors and the two prefix arrays (stick-block items, plane items)
@@ -143,6 +151,9 @@ static int batch_launch(BatchWork& W, int nprob, const qe_problem* probs, const 
     if (sizeof(T) == sizeof(float)) {
       BT_TRY(nonlocal_tc(op.beta, op.dmat, psi[p], hpsi[p], np, nb, npw, W.tc_beta.p, true,
                          W.tc_work.p, W.tc_work.bytes, (int*)W.tc_status.p, st, pf));
+    } else if (fp64_gemm_on_tensor_cores()) {
+      BT_TRY(nonlocal_oz(op.beta, op.dmat, psi[p], hpsi[p], np, nb, npw, W.oz_beta.p, true,
+                         W.oz_work.p, W.oz_work.bytes, (int*)W.tc_status.p, st, pf));
     } else {
       BT_TRY(gemm_inner<T>(op.beta, npw, psi[p], npw, np, nb, npw, (double*)W.proj.p, nb,
                            W.part.p, W.part.bytes, st, pf));
@@ -164,7 +175,7 @@ static int hpsi_batch_t(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem* 
   BT_CU(cudaMemcpyAsync(base + L.jobs_off, tables.data(), tables.size(), cudaMemcpyHostToDevice, st));
   BT_CU(cudaStreamSynchronize(st));   // the host tables are freed on return
   BT_TRY(batch_launch<T>(W, nprob, probs, psi, hpsi, L, st, &ctx->prof));
-  if (sizeof(T) == sizeof(float) && W.tc_status.p) {
+  if (W.tc_status.p) {
     int v = 0;
     BT_CU(cudaMemcpyAsync(&v, W.tc_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     BT_CU(cudaStreamSynchronize(st));

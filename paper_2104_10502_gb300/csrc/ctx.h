@@ -24,6 +24,9 @@ struct qe_ctx {
   // tensor-core path: packed operands and the kernel's status word (a bounded
   // wait that ran out writes a non-zero code; read at the next synchronising point)
   qe::DevBuf tc_work, tc_status, tc_beta;
+  // FP64 path on the tensor cores: beta slices (tagged like tc_beta) and work
+  qe::DevBuf oz_beta, oz_work;
+  unsigned long long oz_beta_tag = 0;
   // the packed beta in tc_beta belongs to the operator with this tag (0: none);
   // every API call that takes an operator gets a fresh tag
   unsigned long long tc_beta_tag = 0, op_tag = 0;
@@ -36,7 +39,8 @@ struct qe_ctx {
   }
   std::vector<qe::DevBuf*> bufs() {
     return {&sticks, &vp,       &part,     &proj,   &projd,   &h_v,     &h_beta,
-            &h_d,    &h_psi,    &h_hpsi,   &dv_basis, &dv_red, &tc_work, &tc_status, &tc_beta};
+            &h_d,    &h_psi,    &h_hpsi,   &dv_basis, &dv_red, &tc_work, &tc_status, &tc_beta,
+            &oz_beta, &oz_work};
   }
 };
 

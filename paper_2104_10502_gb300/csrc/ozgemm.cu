@@ -1,0 +1,637 @@
+// FP64-accurate complex matrix products on the BF16 tensor cores (tcgen05,
+// kind::f16) by exact operand splitting — the Ozaki scheme (Ozaki, Ogita,
+// Oishi & Rump, Numer. Algorithms 59, 2012) — for the FP64 path's projector
+// products of the nonlocal term (Sec. 3.3 of the paper: pseudopotential
+// contribution to the Hamiltonian).
+//
+// GB300 runs FP64 at ~1.2 TFLOP/s on either the vector or the DMMA pipe, and
+// BF16 at ~1.9 PFLOP/s.  Every row r of an operand is scaled by 2^-e_r (e_r the
+// exponent bound of its largest entry) and written as S = 8 slices of 7 bits:
+//   round(x 2^(56-e_r)) 2^-56 = sum_t q_t 2^-7(t+1),  q_t integer,
+//   |q_1| <= 128, |q_t>1| <= 64 (balanced digits), each q_t exact in BF16
+// (the rounding to 2^-56 of the row maximum is below the dropped terms).  A product of slices t and u is an integer below
+// 2^14; the tensor cores sum such products exactly in FP32 as long as the sum
+// stays below 2^24, which holds for the pairs of one "diagonal" t + u = d over
+// a K chunk of 384 (at most 10 * 2^12 per K step on the longest diagonal).  The
+// pairs with t + u <= S - 1 (0-based; 36 of 64) are kept: the dropped ones
+// weigh below 2^-55 of |row max| * |column max| per term.  Each diagonal has its
+// own FP32 accumulator in TMEM (8 x 64 columns = all 512); after every chunk the
+// epilogue warps add them, scaled by 2^-7(d+2), into FP64 registers.
+//
+// Complex products are real GEMMs on interleaved (re, im) K axes:
+//   inner  P = conj(A) B^T:  A'[m] = (ar, ai)_k,  B'[2n] = (br, bi)_k,  B'[2n+1] = (bi, -br)_k
+//   outer  C = A^T B:        A'[m] = (ar, ai)_k,  B'[2n] = (br, -bi)_k, B'[2n+1] = (bi, br)_k
+// so that column 2n of the real product is Re and 2n+1 is Im of complex column n.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+
+#include "common.h"
+#include "plan.h"
+#include "tc_ptx.cuh"
+
+namespace qe {
+
+constexpr int OZ_S = 8;                 // slices per operand
+constexpr int OZ_BM = 128;              // rows of A per CTA (TMEM lanes)
+constexpr int OZ_BN = 64;               // rows of B per CTA (columns of one accumulator)
+constexpr int OZ_BK = 64;               // K per step: one 128-byte swizzle row of BF16
+constexpr int OZ_KPC = 6;               // K steps per exact FP32 chunk (384)
+constexpr int OZ_ASTAGES = 4;
+constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;            // 16 KiB: one A slice tile
+constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;            // 8 KiB: one B slice tile
+constexpr int OZ_BSTAGE_BYTES = OZ_S * OZ_B_BYTES;       // all B slices of one K step
+constexpr int OZ_SMEM_BYTES = OZ_ASTAGES * OZ_A_BYTES + 2 * OZ_BSTAGE_BYTES + 1024 + 256;
+constexpr int OZ_THREADS = 192;         // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
+enum { OZ_OK = 0, OZ_TIMEOUT = 4 };
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major,
+// N = OZ_BN, M = OZ_BM.
+__host__ __device__ constexpr uint32_t oz_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
+         ((uint32_t)(OZ_BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+// 2^e as a double for the exponent range of normal numbers.
+__device__ __forceinline__ double pow2(int e) {
+  e = max(-1022, min(1023, e));
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// ---- the GEMM kernel ----------------------------------------------------------
+// C'[m][j] = sum_k A'[m][k] B'[j][k] for one 128 x 64 tile and one K range.
+// A slices: rows t * Mp + m of mapA; B slices: rows t * Np + j of mapB.
+// Output: complex pairs (C'[m][2n], C'[m][2n+1]) to out[z * zstride + n * ldo + m]
+// for m < M, n < N (n = j / 2), negated if alpha_neg, added to the old value if
+// beta.  grid (Np / 64, Mp / 128, nsplit); CTA z takes K steps
+// [z * ks_per_split, min(nks, (z + 1) * ks_per_split)).
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+          int Mp, int Np, int nks, int ks_per_split, const int* __restrict__ eA,
+          const int* __restrict__ eB, double2* __restrict__ out, int ldo, long long zstride, int M,
+          int N, int alpha_neg, int beta, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;                                   // OZ_ASTAGES x 16 KiB
+  unsigned char* sB = base + OZ_ASTAGES * OZ_A_BYTES;          // 2 x 64 KiB
+  uint64_t* afull = reinterpret_cast<uint64_t*>(sB + 2 * OZ_BSTAGE_BYTES);
+  uint64_t* aempty = afull + OZ_ASTAGES;
+  uint64_t* bfull = aempty + OZ_ASTAGES;
+  uint64_t* bempty = bfull + 2;
+  uint64_t* accfull = bempty + 2;
+  uint64_t* accempty = accfull + 1;
+  uint64_t* mmadone = accempty + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mmadone + 1);
+  __shared__ int s_err, s_issued_a, s_issued_b;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * OZ_BM;
+  const int ks0 = blockIdx.z * ks_per_split;
+  const int nk = max(0, min(ks_per_split, nks - ks0));
+  const int nchunks = (nk + OZ_KPC - 1) / OZ_KPC;
+  const uint64_t limit = 2000000000ull;   // 2 s per wait
+
+  if (threadIdx.x == 0) {
+    s_err = 0;
+    s_issued_a = 0;
+    s_issued_b = 0;
+    for (int s = 0; s < OZ_ASTAGES; ++s) {
+      mbar_init(&afull[s], 1);
+      mbar_init(&aempty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&bfull[s], 1);
+      mbar_init(&bempty[s], 1);
+    }
+    mbar_init(accfull, 1);
+    mbar_init(accempty, 4);
+    mbar_init(mmadone, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  if (warp == 4 && lane == 0 && nk > 0) {
+    // producer: per K step, all B slices (one stage of the B ring), then the
+    // A slices one per stage of the A ring
+    int j = 0;
+    for (int i = 0; i < nk && !*(volatile int*)&s_err; ++i) {
+      const int sb = i & 1;
+      if (i >= 2 && !mbar_wait(&bempty[sb], ((uint32_t)(i >> 1) & 1u) ^ 1u, limit)) {
+        atomicExch(&s_err, OZ_TIMEOUT);
+        break;
+      }
+      const int kx = (ks0 + i) * OZ_BK;
+      mbar_expect_tx(&bfull[sb], OZ_BSTAGE_BYTES);
+      for (int t = 0; t < OZ_S; ++t)
+        tma_load_2d(sB + sb * OZ_BSTAGE_BYTES + t * OZ_B_BYTES, &mapB, &bfull[sb], kx, t * Np + n0);
+      s_issued_b = i + 1;
+      for (int t = 0; t < OZ_S; ++t, ++j) {
+        const int sa = j % OZ_ASTAGES;
+        if (j >= OZ_ASTAGES &&
+            !mbar_wait(&aempty[sa], ((uint32_t)(j / OZ_ASTAGES) & 1u) ^ 1u, limit)) {
+          atomicExch(&s_err, OZ_TIMEOUT);
+          break;
+        }
+        mbar_expect_tx(&afull[sa], OZ_A_BYTES);
+        tma_load_2d(sA + sa * OZ_A_BYTES, &mapA, &afull[sa], kx, t * Mp + m0);
+        s_issued_a = j + 1;
+      }
+    }
+  } else if (warp == 5 && lane == 0 && nk > 0) {
+    // MMA issuer: for every K step and A slice t, the pairs (t, u), u <= S-1-t,
+    // into the accumulator of diagonal d = t + u
+    const uint32_t idesc = oz_idesc();
+    int j = 0, c = 0;
+    bool ok = true;
+    for (int i = 0; i < nk && ok; ++i) {
+      const bool cstart = (i % OZ_KPC) == 0;
+      if (cstart && i > 0 && !mbar_wait(accempty, (uint32_t)(c - 1) & 1u, limit)) {
+        atomicExch(&s_err, OZ_TIMEOUT);
+        ok = false;
+        break;
+      }
+      const int sb = i & 1;
+      if (!mbar_wait(&bfull[sb], (uint32_t)(i >> 1) & 1u, limit)) {
+        atomicExch(&s_err, OZ_TIMEOUT);
+        ok = false;
+        break;
+      }
+      const uint32_t bbase = smem_u32(sB + sb * OZ_BSTAGE_BYTES);
+      for (int t = 0; t < OZ_S; ++t, ++j) {
+        const int sa = j % OZ_ASTAGES;
+        if (!mbar_wait(&afull[sa], (uint32_t)(j / OZ_ASTAGES) & 1u, limit)) {
+          atomicExch(&s_err, OZ_TIMEOUT);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t abase = smem_u32(sA + sa * OZ_A_BYTES);
+        for (int u = 0; u < OZ_S - t; ++u) {
+          const uint32_t dt = tmem + (uint32_t)((t + u) * OZ_BN);
+#pragma unroll
+          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+            const uint64_t ad = sw128_desc(abase + kk * 32);
+            const uint64_t bd = sw128_desc(bbase + u * OZ_B_BYTES + kk * 32);
+            mma_bf16(dt, ad, bd, idesc, (cstart && t == 0 && kk == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(&aempty[sa]);
+      }
+      if (!ok) break;
+      mma_commit(&bempty[sb]);
+      if ((i % OZ_KPC) == OZ_KPC - 1 || i == nk - 1) {
+        mma_commit(accfull);
+        ++c;
+      }
+    }
+    // every MMA issued so far has completed once this barrier flips
+    mma_commit(mmadone);
+    mbar_wait(mmadone, 0, limit);
+  }
+  __syncwarp();
+
+  if (warp < 4) {
+    double acc[OZ_BN];
+#pragma unroll
+    for (int q = 0; q < OZ_BN; ++q) acc[q] = 0.0;
+    bool ok = true;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c = 0; c < nchunks; ++c) {
+      if (!mbar_wait(accfull, (uint32_t)c & 1u, limit) || *(volatile int*)&s_err) {
+        if (lane == 0) atomicCAS(&s_err, 0, OZ_TIMEOUT);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int d = 0; d < OZ_S; ++d) {
+        const double w = pow2(-7 * (d + 2));
+#pragma unroll
+        for (int h = 0; h < OZ_BN / 32; ++h) {
+          uint32_t r[32];
+          tmem_ld32(lane_base + (uint32_t)(d * OZ_BN + h * 32), r);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) acc[h * 32 + q] = fma((double)__uint_as_float(r[q]), w, acc[h * 32 + q]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accempty);
+    }
+    const int m = m0 + warp * 32 + lane;
+    if (ok && m < M) {
+      const int ea = eA[m];
+      double2* o = out + (size_t)blockIdx.z * zstride + m;
+#pragma unroll
+      for (int q = 0; q < OZ_BN / 2; ++q) {
+        const int n = (n0 >> 1) + q;
+        if (n >= N) break;
+        const double f = pow2(ea + eB[n]);
+        double2 v = make_double2(acc[2 * q] * f, acc[2 * q + 1] * f);
+        if (alpha_neg) { v.x = -v.x; v.y = -v.y; }
+        double2* p = o + (size_t)n * ldo;
+        if (beta) { const double2 old = *p; v.x += old.x; v.y += old.y; }
+        *p = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_err != 0 && threadIdx.x == 0) {
+    // drain: wait (bounded) for the copies this CTA issued before releasing smem
+    const int ia = s_issued_a, ib = s_issued_b;
+    for (int j = max(0, ia - OZ_ASTAGES); j < ia; ++j)
+      mbar_wait(&afull[j % OZ_ASTAGES], (uint32_t)(j / OZ_ASTAGES) & 1u, limit);
+    for (int i = max(0, ib - 2); i < ib; ++i) mbar_wait(&bfull[i & 1], (uint32_t)(i >> 1) & 1u, limit);
+    atomicMax(status, s_err);
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+}
+
+// ---- slicing ------------------------------------------------------------------
+// Exponent bound of a row: the smallest e with max |x| < 2^e (0 for a zero row).
+__device__ __forceinline__ int exp_bound(double mx) { return mx > 0.0 ? ilogb(mx) + 1 : 0; }
+
+// The S slices of x 2^-e: F = round(|x| 2^(56-e)) < 2^56 (sc56 = 2^(56-e)) in
+// balanced base-128 digits, least significant first (digits in [-64, 63], the
+// leading one in [0, 128]), with the sign of x.  Integer work only, so slicing
+// runs at memory speed rather than at GB300's FP64 rate.
+__device__ __forceinline__ void slices_of(double x, double sc56, __nv_bfloat16* q) {
+  unsigned long long F = __double2ull_rn(fabs(x) * sc56);
+  const float sg = x < 0.0 ? -1.f : 1.f;
+  int carry = 0;
+#pragma unroll
+  for (int t = OZ_S - 1; t >= 1; --t) {
+    int v = (int)(F & 127ull) + carry;
+    F >>= 7;
+    carry = v >= 64 ? 1 : 0;
+    v -= carry << 7;
+    q[t] = __float2bfloat16_rn(sg * (float)v);
+  }
+  q[0] = __float2bfloat16_rn(sg * (float)((int)F + carry));
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (threadIdx.x == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// Row slicing: input row r of a complex [rows][K] matrix (leading dimension ld,
+// complex units).  form 0: output row r = (x, y)_k; form 1: rows 2r = (x, y)_k
+// and 2r+1 = (y, -x)_k.  Q is [S][rows_out_p][Kp] BF16 (K padding zeroed), e[r]
+// the row's exponent.  One CTA per input row (padding rows included: zeros).
+__global__ void __launch_bounds__(256) k_oz_slice_rows(const double2* __restrict__ src, int ld,
+                                                       int rows, int K, int form, int rows_out_p,
+                                                       int Kp, __nv_bfloat16* __restrict__ Q,
+                                                       int* __restrict__ e) {
+  __shared__ double sh[33];
+  const int r = blockIdx.x;
+  const double2* row = src + (size_t)r * ld;
+  const bool valid = r < rows;
+  double mx = 0.0;
+  if (valid)
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const double2 v = row[k];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+  mx = block_max(mx, sh);
+  const int ex = exp_bound(mx);
+  if (threadIdx.x == 0 && valid) e[r] = ex;
+  const double sc = pow2(56 - ex);
+  const size_t slice = (size_t)rows_out_p * Kp;
+  const int orow = form == 0 ? r : 2 * r;
+  const int kh = Kp / 2;
+  for (int k = threadIdx.x; k < kh; k += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (valid && k < K) v = row[k];
+    __nv_bfloat16 qx[OZ_S], qy[OZ_S];
+    slices_of(v.x, sc, qx);
+    slices_of(v.y, sc, qy);
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) {
+      __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(Q + t * slice + (size_t)orow * Kp) + k;
+      *p0 = __halves2bfloat162(qx[t], qy[t]);
+      if (form == 1) {
+        __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(Q + t * slice + (size_t)(orow + 1) * Kp) + k;
+        *p1 = __halves2bfloat162(qy[t], __hneg(qx[t]));
+      }
+    }
+  }
+}
+
+// Column exponents of a complex [K][M] matrix (leading dimension ld): e[m] for
+// max over k of |x|, |y|; consecutive threads take consecutive m.
+__global__ void k_oz_colmax(const double2* __restrict__ src, int ld, int K, int M, int* __restrict__ e) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double mx = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double2 v = src[(size_t)k * ld + m];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  e[m] = exp_bound(mx);
+}
+
+// Transposed slicing of a complex [K][M] matrix: output rows from its columns.
+// form 0: row m = (x, y)_k; form 2: rows 2m = (x, -y)_k and 2m+1 = (y, x)_k.
+// 32 x 32 tiles through shared memory (reads coalesced along m, writes along k).
+// grid (ceil(cols_p / 32), Kp / 64) with cols_p = the padded column count.
+__global__ void k_oz_slice_cols(const double2* __restrict__ src, int ld, int K, int M, int form,
+                                const int* __restrict__ e, int rows_out_p, int Kp,
+                                __nv_bfloat16* __restrict__ Q) {
+  __shared__ double2 tile[32][33];
+  const int m0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, m = m0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < K && m < M) ? src[(size_t)k * ld + m] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const size_t slice = (size_t)rows_out_p * Kp;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int m = m0 + r, k = k0 + threadIdx.x;
+    const int orow = form == 0 ? m : 2 * m;
+    if (orow >= rows_out_p || 2 * k >= Kp) continue;
+    const double2 v = tile[threadIdx.x][r];
+    const double sc = pow2(56 - (m < M ? e[m] : 0));
+    __nv_bfloat16 qx[OZ_S], qy[OZ_S];
+    slices_of(v.x, sc, qx);
+    slices_of(v.y, sc, qy);
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) {
+      __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(Q + t * slice + (size_t)orow * Kp) + k;
+      if (form == 0) {
+        *p0 = __halves2bfloat162(qx[t], qy[t]);
+      } else {
+        *p0 = __halves2bfloat162(qx[t], __hneg(qy[t]));
+        __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(Q + t * slice + (size_t)(orow + 1) * Kp) + k;
+        *p1 = __halves2bfloat162(qy[t], qx[t]);
+      }
+    }
+  }
+}
+
+// P[m][n] = sum_z part[z][n][m] (fixed order), into C with leading dimension ldc.
+__global__ void k_oz_reduce(const double2* __restrict__ part, int nsplit, long long zstride,
+                            int Mp, int M, int N, double2* __restrict__ C, int ldc) {
+  const size_t total = (size_t)M * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i / N), n = (int)(i % N);
+    double sx = 0.0, sy = 0.0;
+    for (int z = 0; z < nsplit; ++z) {
+      const double2 v = part[(size_t)z * zstride + (size_t)n * Mp + m];
+      sx += v.x;
+      sy += v.y;
+    }
+    C[(size_t)m * ldc + n] = make_double2(sx, sy);
+  }
+}
+
+// ---- host side ----------------------------------------------------------------
+static inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+static inline size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static int oz_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+// rows x Kp BF16 matrix, K-major, box `box_rows` rows x 64 columns, 128-byte swizzle.
+static int oz_map(CUtensorMap* m, const __nv_bfloat16* ptr, int rows, int Kp, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  int rc = tc_get_encode(&enc);
+  if (rc) return rc;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)ptr, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (BF16) failed (%d)", (int)r);
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+// Sliced operand: S slices of a [rows_p][Kp] BF16 matrix and its row exponents.
+struct OzOperand {
+  __nv_bfloat16* q = nullptr;
+  int* e = nullptr;
+  int rows_p = 0, Kp = 0;
+};
+
+size_t oz_operand_bytes(int rows_out, int K) {
+  const size_t rp = pad_to(std::max(rows_out, 1), OZ_BM), kp = pad_to(2 * std::max(K, 1), OZ_BK);
+  return up256((size_t)OZ_S * rp * kp * 2) + up256(rp * sizeof(int)) + 256;
+}
+
+static OzOperand oz_carve(void* mem, int rows_out, int K) {
+  OzOperand o;
+  o.rows_p = pad_to(std::max(rows_out, 1), OZ_BM);
+  o.Kp = pad_to(2 * std::max(K, 1), OZ_BK);
+  char* p = reinterpret_cast<char*>(((uintptr_t)mem + 255) & ~(uintptr_t)255);
+  o.q = reinterpret_cast<__nv_bfloat16*>(p);
+  o.e = reinterpret_cast<int*>(p + up256((size_t)OZ_S * o.rows_p * o.Kp * 2));
+  return o;
+}
+
+// Slices of the rows of a complex [rows][K] matrix (form 0: one output row per
+// input row; form 1: the inner product's B pair).  Returns the carved operand.
+int oz_slice_rows(const double* src, int ld, int rows, int K, int form, void* mem, OzOperand* out,
+                  cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, "k_oz_slice", st);
+  const int rows_out = form == 0 ? rows : 2 * rows;
+  *out = oz_carve(mem, rows_out, K);
+  const int in_rows_p = form == 0 ? out->rows_p : out->rows_p / 2;
+  k_oz_slice_rows<<<in_rows_p, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, rows, K,
+                                             form, out->rows_p, out->Kp, out->q, out->e);
+  return oz_check("k_oz_slice_rows");
+}
+
+// Slices of the columns of a complex [K][cols] matrix (form 0: one output row
+// per column; form 2: the outer product's B pair).
+int oz_slice_cols(const double* src, int ld, int K, int cols, int form, void* mem, OzOperand* out,
+                  cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, "k_oz_slice", st);
+  const int rows_out = form == 0 ? cols : 2 * cols;
+  *out = oz_carve(mem, rows_out, K);
+  k_oz_colmax<<<(cols + 255) / 256, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols,
+                                                  out->e);
+  int rc = oz_check("k_oz_colmax");
+  if (rc) return rc;
+  if (pf) pf->launches += 1;
+  const int cols_p = form == 0 ? out->rows_p : out->rows_p / 2;
+  dim3 g((cols_p + 31) / 32, out->Kp / 64);
+  k_oz_slice_cols<<<g, dim3(32, 8), 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols,
+                                             form, out->e, out->rows_p, out->Kp, out->q);
+  return oz_check("k_oz_slice_cols");
+}
+
+static int oz_splits(int tiles, int nks) {
+  int ns = std::max(1, (152 + tiles - 1) / tiles);
+  ns = std::min(ns, std::max(1, nks / OZ_KPC));   // at least one full chunk per CTA
+  const int per = (nks + ns - 1) / ns;
+  return (nks + per - 1) / per;
+}
+
+size_t oz_partial_bytes(int M, int N, int K) {
+  const int Mp = pad_to(std::max(M, 1), OZ_BM), Np = pad_to(2 * std::max(N, 1), OZ_BM);
+  const int nks = pad_to(2 * std::max(K, 1), OZ_BK) / OZ_BK;
+  const int ns = oz_splits((Mp / OZ_BM) * (Np / OZ_BN), nks);
+  return up256((size_t)ns * (Np / 2) * Mp * 16);
+}
+
+static int oz_launch(const OzOperand& A, const OzOperand& B, int M, int N, double2* out, int ldo,
+                     long long zstride, int nsplit, int alpha_neg, int beta, int* status,
+                     cudaStream_t st, Prof* pf) {
+  if (A.Kp != B.Kp) {
+    set_error("oz_gemm: K padding mismatch");
+    return QE_EINVAL;
+  }
+  CUtensorMap mA, mB;
+  int rc;
+  if ((rc = oz_map(&mA, A.q, OZ_S * A.rows_p, A.Kp, OZ_BM)) ||
+      (rc = oz_map(&mB, B.q, OZ_S * B.rows_p, B.Kp, OZ_BN)))
+    return rc;
+  const int nks = A.Kp / OZ_BK;
+  const int per = (nks + nsplit - 1) / nsplit;
+  set_max_dynamic_smem(k_oz_gemm);
+  ProfScope ps(pf, "k_oz_gemm", st);
+  dim3 g(B.rows_p / OZ_BN, A.rows_p / OZ_BM, nsplit);
+  k_oz_gemm<<<g, OZ_THREADS, OZ_SMEM_BYTES, st>>>(mA, mB, A.rows_p, B.rows_p, nks, per, A.e, B.e,
+                                                   out, ldo, zstride, M, N, alpha_neg, beta, status);
+  return oz_check("k_oz_gemm");
+}
+
+// C[m][n] = sum_k conj(A[m][k]) B[n][k] with A sliced by oz_slice_rows (form 0)
+// and B by oz_slice_rows (form 1); split K, fixed-order reduction.
+int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* C, int ldc,
+                  void* part, size_t part_bytes, int* status, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  const int nks = A.Kp / OZ_BK;
+  const int ns = oz_splits((A.rows_p / OZ_BM) * (B.rows_p / OZ_BN), nks);
+  const long long zstride = (long long)(B.rows_p / 2) * A.rows_p;
+  if ((size_t)ns * zstride * 16 > part_bytes) {
+    set_error("oz_gemm_inner: partial buffer too small");
+    return QE_EINVAL;
+  }
+  int rc = oz_launch(A, B, M, N, reinterpret_cast<double2*>(part), A.rows_p, zstride, ns, 0, 0,
+                     status, st, pf);
+  if (rc) return rc;
+  const int per = (nks + ns - 1) / ns;
+  const int nsplit = (nks + per - 1) / per;
+  ProfScope ps(pf, "k_oz_reduce", st);
+  const size_t total = (size_t)M * N;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+  k_oz_reduce<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(part), nsplit, zstride,
+                                      A.rows_p, M, N, reinterpret_cast<double2*>(C), ldc);
+  return oz_check("k_oz_reduce");
+}
+
+// C[n][m] (+)= (-) sum_k A[k][m] B[k][n] with A sliced by oz_slice_cols (form 0)
+// and B by oz_slice_cols (form 2).
+int oz_gemm_outer(const OzOperand& A, const OzOperand& B, int M, int N, double* C, int ldc,
+                  int alpha_neg, int beta, int* status, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  return oz_launch(A, B, M, N, reinterpret_cast<double2*>(C), ldc, 0, 1, alpha_neg, beta, status,
+                   st, pf);
+}
+
+bool fp64_gemm_on_tensor_cores() {
+  static const bool on = [] {
+    const char* v = std::getenv("QE_FP64_GEMM");
+    return !(v && std::strcmp(v, "simt") == 0);
+  }();
+  return on;
+}
+
+// ---- the nonlocal term -----------------------------------------------------------
+size_t nonlocal_oz_beta_bytes(int np, int npw) {
+  return oz_operand_bytes(np, npw) + oz_operand_bytes(npw, np);
+}
+
+size_t nonlocal_oz_bytes(int np, int nb, int npw) {
+  return oz_operand_bytes(2 * nb, npw) + oz_partial_bytes(np, nb, npw) +
+         oz_operand_bytes(2 * nb, np) + 2 * up256((size_t)np * nb * 16) + 1024;
+}
+
+// hpsi += beta^T D (conj(beta) psi^T) with FP64-accurate products on the BF16
+// tensor cores.  bslices (nonlocal_oz_beta_bytes) holds the two slicings of
+// beta (rows for the inner product, columns for the outer one); they are
+// (re)computed when slice_beta is true.
+int nonlocal_oz(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
+                int nb, int npw, void* bslices, bool slice_beta, void* work, size_t work_bytes,
+                int* status, cudaStream_t st, Prof* pf) {
+  if (np <= 0 || nb <= 0) return QE_OK;
+  if (nonlocal_oz_bytes(np, nb, npw) > work_bytes) {
+    set_error("nonlocal_oz: workspace too small");
+    return QE_EINVAL;
+  }
+  char* bs = static_cast<char*>(bslices);
+  OzOperand A1, A2, B1, B2;
+  int rc;
+  if (slice_beta) {
+    if ((rc = oz_slice_rows(beta, npw, np, npw, 0, bs, &A1, st, pf))) return rc;
+    if ((rc = oz_slice_cols(beta, npw, np, npw, 0, bs + oz_operand_bytes(np, npw), &A2, st, pf)))
+      return rc;
+  } else {
+    A1 = oz_carve(bs, np, npw);
+    A2 = oz_carve(bs + oz_operand_bytes(np, npw), npw, np);
+  }
+  char* w = static_cast<char*>(work);
+  char* wb1 = w;
+  char* part = wb1 + oz_operand_bytes(2 * nb, npw);
+  char* wb2 = part + oz_partial_bytes(np, nb, npw);
+  double* P = reinterpret_cast<double*>(wb2 + oz_operand_bytes(2 * nb, np));
+  P = reinterpret_cast<double*>(((uintptr_t)P + 255) & ~(uintptr_t)255);
+  double* Q = reinterpret_cast<double*>(reinterpret_cast<char*>(P) + up256((size_t)np * nb * 16));
+  if ((rc = oz_slice_rows(psi, npw, nb, npw, 1, wb1, &B1, st, pf))) return rc;
+  if ((rc = oz_gemm_inner(A1, B1, np, nb, P, nb, part, oz_partial_bytes(np, nb, npw), status, st, pf)))
+    return rc;
+  if ((rc = dmul(dmat, P, Q, np, nb, st, pf))) return rc;
+  if ((rc = oz_slice_cols(Q, nb, np, nb, 2, wb2, &B2, st, pf))) return rc;
+  return oz_gemm_outer(A2, B2, npw, nb, hpsi, npw, 0, 1, status, st, pf);
+}
+
+}  // namespace qe

@@ -172,4 +172,16 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
 // Q[i][n] = sum_j D[i][j] P[j][n] (D real [np][np], P complex [np][nb]).
 int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf);
 
+// hpsi += beta^T D (conj(beta) psi^T) with FP64-accurate products on the BF16
+// tensor cores (ozgemm.cu); beta slices in bslices (nonlocal_oz_beta_bytes),
+// work of nonlocal_oz_bytes().
+size_t nonlocal_oz_bytes(int np, int nb, int npw);
+size_t nonlocal_oz_beta_bytes(int np, int npw);
+int nonlocal_oz(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
+                int nb, int npw, void* bslices, bool slice_beta, void* work, size_t work_bytes,
+                int* status, cudaStream_t st, Prof* pf);
+// FP64 projector products on the tensor cores (default) or on the DFMA pipe
+// (environment QE_FP64_GEMM=simt).
+bool fp64_gemm_on_tensor_cores();
+
 }  // namespace qe
