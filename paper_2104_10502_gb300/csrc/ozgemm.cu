@@ -44,7 +44,8 @@ constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;            // 16 KiB: one A slice 
 constexpr int OZ_B_BYTES = OZ_BN * OZ_BK * 2;            // 8 KiB: one B slice tile
 constexpr int OZ_BSTAGE_BYTES = OZ_S * OZ_B_BYTES;       // all B slices of one K step
 constexpr int OZ_SMEM_BYTES = OZ_ASTAGES * OZ_A_BYTES + 2 * OZ_BSTAGE_BYTES + 1024 + 256;
-constexpr int OZ_THREADS = 192;         // warps 0-3 epilogue, 4 TMA producer, 5 MMA issuer
+constexpr int OZ_THREADS = 320;         // warps 0-7 epilogue, 8 TMA producer, 9 MMA issuer
+constexpr int OZ_ECOLS = OZ_BN / 2;     // accumulator columns per epilogue warp
 enum { OZ_OK = 0, OZ_TIMEOUT = 4 };
 
 // Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major,
@@ -116,7 +117,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       mbar_init(&bempty[s], 1);
     }
     mbar_init(accfull, 1);
-    mbar_init(accempty, 4);
+    mbar_init(accempty, 8);
     mbar_init(mmadone, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -133,7 +134,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  if (warp == 4 && lane == 0 && nk > 0) {
+  if (warp == 8 && lane == 0 && nk > 0) {
     // producer: per K step, all B slices (one stage of the B ring), then the
     // A slices one per stage of the A ring
     int j = 0;
@@ -160,7 +161,7 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         s_issued_a = j + 1;
       }
     }
-  } else if (warp == 5 && lane == 0 && nk > 0) {
+  } else if (warp == 9 && lane == 0 && nk > 0) {
     // MMA issuer: for every K step and A slice t, the pairs (t, u), u <= S-1-t,
     // into the accumulator of diagonal d = t + u
     const uint32_t idesc = oz_idesc();
@@ -213,12 +214,14 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   }
   __syncwarp();
 
-  if (warp < 4) {
-    double acc[OZ_BN];
+  if (warp < 8) {
+    // epilogue warp: TMEM lanes of quarter (warp % 4), columns [c0, c0 + 32)
+    const int quarter = warp & 3, c0 = (warp >> 2) * OZ_ECOLS;
+    double acc[OZ_ECOLS];
 #pragma unroll
-    for (int q = 0; q < OZ_BN; ++q) acc[q] = 0.0;
+    for (int q = 0; q < OZ_ECOLS; ++q) acc[q] = 0.0;
     bool ok = true;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
     for (int c = 0; c < nchunks; ++c) {
       if (!mbar_wait(accfull, (uint32_t)c & 1u, limit) || *(volatile int*)&s_err) {
         if (lane == 0) atomicCAS(&s_err, 0, OZ_TIMEOUT);
@@ -226,28 +229,40 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // Combine the exact integer sums of four diagonals in int64,
+      //   T = ((S_d0 128 + S_d0+1) 128 + S_d0+2) 128 + S_d0+3  (|T| < 2^46),
+      // so that each column costs 2 conversions and 2 FP64 FMAs per chunk
+      // instead of 8 each (GB300's FP64 pipe also runs the conversions).
 #pragma unroll
-      for (int d = 0; d < OZ_S; ++d) {
-        const double w = pow2(-7 * (d + 2));
+      for (int cb = 0; cb < OZ_ECOLS / 8; ++cb) {
 #pragma unroll
-        for (int h = 0; h < OZ_BN / 32; ++h) {
-          uint32_t r[32];
-          tmem_ld32(lane_base + (uint32_t)(d * OZ_BN + h * 32), r);
+        for (int g = 0; g < 2; ++g) {
+          uint32_t r[4][8];
 #pragma unroll
-          for (int q = 0; q < 32; ++q) acc[h * 32 + q] = fma((double)__uint_as_float(r[q]), w, acc[h * 32 + q]);
+          for (int dd = 0; dd < 4; ++dd)
+            tmem_ld8_nowait(lane_base + (uint32_t)((4 * g + dd) * OZ_BN + cb * 8), r[dd]);
+          tmem_wait_ld();
+          const double w = pow2(-7 * (4 * g + 3 + 2));
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            long long T = __float2int_rn(__uint_as_float(r[0][q]));
+#pragma unroll
+            for (int dd = 1; dd < 4; ++dd) T = T * 128 + __float2int_rn(__uint_as_float(r[dd][q]));
+            acc[cb * 8 + q] = fma(__ll2double_rn(T), w, acc[cb * 8 + q]);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(accempty);
     }
-    const int m = m0 + warp * 32 + lane;
+    const int m = m0 + quarter * 32 + lane;
     if (ok && m < M) {
       const int ea = eA[m];
       double2* o = out + (size_t)blockIdx.z * zstride + m;
 #pragma unroll
-      for (int q = 0; q < OZ_BN / 2; ++q) {
-        const int n = (n0 >> 1) + q;
+      for (int q = 0; q < OZ_ECOLS / 2; ++q) {
+        const int n = ((n0 + c0) >> 1) + q;
         if (n >= N) break;
         const double f = pow2(ea + eB[n]);
         double2 v = make_double2(acc[2 * q] * f, acc[2 * q + 1] * f);
@@ -508,8 +523,10 @@ int oz_slice_cols(const double* src, int ld, int K, int cols, int form, void* me
   return oz_check("k_oz_slice_cols");
 }
 
+// K splits: as many CTAs as fit in ONE wave (one CTA per SM: the kernel holds
+// all of TMEM and ~195 KB of shared memory), at least one chunk each.
 static int oz_splits(int tiles, int nks) {
-  int ns = std::max(1, (152 + tiles - 1) / tiles);
+  int ns = std::max(1, 152 / std::max(1, tiles));
   ns = std::min(ns, std::max(1, nks / OZ_KPC));   // at least one full chunk per CTA
   const int per = (nks + ns - 1) / ns;
   return (nks + per - 1) / per;

@@ -245,7 +245,8 @@ int tc_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const f
 int tc_gemm_splits(int Mp, int Np, int Kp) {
   const int tiles = (Mp / TC_BM) * (Np / TC_BN);
   const int nkb = Kp / TC_BK;
-  int ns = std::max(1, (152 + tiles - 1) / tiles);
+  // one wave: a CTA per SM (the kernel's shared memory allows no second one)
+  int ns = std::max(1, 152 / std::max(1, tiles));
   ns = std::min(ns, std::max(1, nkb / 4));   // at least 4 K blocks per CTA
   const int per = (nkb + ns - 1) / ns;
   return (nkb + per - 1) / per;
