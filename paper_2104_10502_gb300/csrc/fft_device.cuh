@@ -144,14 +144,19 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
     cx<T> v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = p[q * step];
+    // M == 1 (last DIF / first DIT stage): every twiddle is 1, skip the products
     if (DIT) {
+      if (M > 1) {
 #pragma unroll
-      for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
+        for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
+      }
       dftR<T, SIGN, R>(v);
     } else {
       dftR<T, SIGN, R>(v);
+      if (M > 1) {
 #pragma unroll
-      for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
+        for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
+      }
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) p[q * step] = v[q];
@@ -217,14 +222,18 @@ __device__ __forceinline__ void fft_stage2(cx<T>* base, int es, int ls, const in
 #pragma unroll
       for (int qa = 0; qa < RA; ++qa) {
         dftR<T, SIGN, RB>(v[qa]);
+        if (Mb > 1) {
 #pragma unroll
-        for (int qb = 1; qb < RB; ++qb) v[qa][qb] = cmul(v[qa][qb], twid<T, SIGN>(tw, jb * qb * tsb));
+          for (int qb = 1; qb < RB; ++qb) v[qa][qb] = cmul(v[qa][qb], twid<T, SIGN>(tw, jb * qb * tsb));
+        }
       }
     } else {
 #pragma unroll
       for (int qa = 0; qa < RA; ++qa) {
+        if (Mb > 1) {
 #pragma unroll
-        for (int qb = 1; qb < RB; ++qb) v[qa][qb] = cmul(v[qa][qb], twid<T, SIGN>(tw, jb * qb * tsb));
+          for (int qb = 1; qb < RB; ++qb) v[qa][qb] = cmul(v[qa][qb], twid<T, SIGN>(tw, jb * qb * tsb));
+        }
         dftR<T, SIGN, RB>(v[qa]);
       }
 #pragma unroll

@@ -70,6 +70,9 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+// A row exponent; 0x80808080 marks an all-zero column of a transposed slicing.
+__device__ __forceinline__ int oz_exp(int e) { return e == (int)0x80808080 ? 0 : e; }
+
 // ---- the GEMM kernel ----------------------------------------------------------
 // C'[m][j] = sum_k A'[m][k] B'[j][k] for one 128 x 64 tile and one K range.
 // A slices: rows t * Mp + m of mapA; B slices: rows t * Np + j of mapB.
@@ -258,13 +261,13 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
     const int m = m0 + quarter * 32 + lane;
     if (ok && m < M) {
-      const int ea = eA[m];
+      const int ea = oz_exp(eA[m]);
       double2* o = out + (size_t)blockIdx.z * zstride + m;
 #pragma unroll
       for (int q = 0; q < OZ_ECOLS / 2; ++q) {
         const int n = ((n0 + c0) >> 1) + q;
         if (n >= N) break;
-        const double f = pow2(ea + eB[n]);
+        const double f = pow2(ea + oz_exp(eB[n]));
         double2 v = make_double2(acc[2 * q] * f, acc[2 * q + 1] * f);
         if (alpha_neg) { v.x = -v.x; v.y = -v.y; }
         double2* p = o + (size_t)n * ldo;
@@ -290,36 +293,80 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 }
 
 // ---- slicing ------------------------------------------------------------------
-// Exponent bound of a row: the smallest e with max |x| < 2^e (0 for a zero row).
-__device__ __forceinline__ int exp_bound(double mx) { return mx > 0.0 ? ilogb(mx) + 1 : 0; }
+// All integer: GB300's FP64 pipe (which also runs FP64 min/max and conversions)
+// would otherwise bound the slicing instead of memory.
 
-// The S slices of x 2^-e: F = round(|x| 2^(56-e)) < 2^56 (sc56 = 2^(56-e)) in
-// balanced base-128 digits, least significant first (digits in [-64, 63], the
-// leading one in [0, 128]), with the sign of x.  Integer work only, so slicing
-// runs at memory speed rather than at GB300's FP64 rate.
-__device__ __forceinline__ void slices_of(double x, double sc56, __nv_bfloat16* q) {
-  unsigned long long F = __double2ull_rn(fabs(x) * sc56);
-  const float sg = x < 0.0 ? -1.f : 1.f;
+// |x| as an ordered integer key (the IEEE magnitude bits).
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Exponent bound from magnitude bits: the smallest e with |x| < 2^e (0 for 0).
+__device__ __forceinline__ int exp_bound_bits(unsigned long long b) {
+  if (b == 0) return 0;
+  const int E = (int)(b >> 52);
+  if (E > 0) return E - 1022;                  // 2^(E-1023) <= |x| < 2^(E-1022)
+  return -1074 + (64 - __clzll((long long)b));   // subnormal
+}
+
+__device__ __forceinline__ int exp_bound(double mx) { return exp_bound_bits(mag_bits(mx)); }
+
+// BF16 bits of an integer v, |v| <= 128: its float has at most 8 significant
+// bits, so the upper half of the float's bits is exactly the BF16 value.
+__device__ __forceinline__ unsigned short bf16_of_int(int v) {
+  return (unsigned short)(__float_as_uint(__int2float_rn(v)) >> 16);
+}
+
+// The S slices of x 2^-e: F = round(|x| 2^(56-e)) < 2^56 in balanced base-128
+// digits, least significant first (digits in [-64, 63], the leading one in
+// [0, 128]), with the sign of x; q[t] are BF16 bit patterns.  F is handled as
+// two 28-bit halves (four digits each) in 32-bit arithmetic.
+__device__ __forceinline__ void slices_of(double x, int e, unsigned short* q) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  int Ee = E;
+  if (E > 0) m |= 1ull << 52;
+  else Ee = 1;
+  // |x| = m 2^(Ee-1075);  F = m 2^(Ee-1075+56-e) rounded
+  const int s = 1019 - Ee + e;
+  unsigned long long F;
+  if (s <= 0) F = m << (-s);
+  else if (s >= 64) F = 0;
+  else F = (m + (1ull << (s - 1))) >> s;
+  const int sg = (b >> 63) ? -1 : 1;
+  unsigned lo = (unsigned)(F & 0xFFFFFFFull), hi = (unsigned)(F >> 28);
   int carry = 0;
 #pragma unroll
   for (int t = OZ_S - 1; t >= 1; --t) {
-    int v = (int)(F & 127ull) + carry;
-    F >>= 7;
+    unsigned& w = t >= 4 ? lo : hi;
+    int v = (int)(w & 127u) + carry;
+    w >>= 7;
     carry = v >= 64 ? 1 : 0;
     v -= carry << 7;
-    q[t] = __float2bfloat16_rn(sg * (float)v);
+    q[t] = bf16_of_int(sg * v);
   }
-  q[0] = __float2bfloat16_rn(sg * (float)((int)F + carry));
+  q[0] = bf16_of_int(sg * ((int)hi + carry));
 }
 
-__device__ __forceinline__ double block_max(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+__device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) {
+  return (unsigned)lo | ((unsigned)hi << 16);
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
   __syncthreads();
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    unsigned long long t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, t, o);
+      t = w > t ? w : t;
+    }
     if (threadIdx.x == 0) sh[32] = t;
   }
   __syncthreads();
@@ -330,56 +377,78 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 // complex units).  form 0: output row r = (x, y)_k; form 1: rows 2r = (x, y)_k
 // and 2r+1 = (y, -x)_k.  Q is [S][rows_out_p][Kp] BF16 (K padding zeroed), e[r]
 // the row's exponent.  One CTA per input row (padding rows included: zeros).
+constexpr int OZ_ROW_CHUNK = 2048;   // complex elements of a row per CTA
+
+// Row exponents of a complex [rows][K] matrix: grid (rows, ceil(K / 2048)); the
+// CTAs of a row merge their exponent bounds with atomicMax (monotonic in the
+// maximum) into e, which holds 0x80808080 beforehand (kept by all-zero rows).
+__global__ void __launch_bounds__(256) k_oz_rowmax(const double2* __restrict__ src, int ld, int K,
+                                                   int* __restrict__ e) {
+  __shared__ unsigned long long sh[33];
+  const int r = blockIdx.x;
+  const double2* row = src + (size_t)r * ld;
+  const int k0 = blockIdx.y * OZ_ROW_CHUNK, k1 = min(K, k0 + OZ_ROW_CHUNK);
+  unsigned long long mx = 0;
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const double2 v = row[k];
+    const unsigned long long a = mag_bits(v.x), c = mag_bits(v.y);
+    const unsigned long long h = a > c ? a : c;
+    mx = h > mx ? h : mx;
+  }
+  mx = block_max_u64(mx, sh);
+  if (threadIdx.x == 0 && mx != 0) atomicMax(&e[r], exp_bound_bits(mx));
+}
+
+// Row slicing: input row r of a complex [rows][K] matrix (leading dimension ld,
+// complex units).  form 0: output row r = (x, y)_k; form 1: rows 2r = (x, y)_k
+// and 2r+1 = (y, -x)_k.  Q is [S][rows_out_p][Kp] BF16 (padding zeroed), e the
+// row exponents (k_oz_rowmax).  grid (input rows incl. padding, ceil(Kp/2 / 2048)).
 __global__ void __launch_bounds__(256) k_oz_slice_rows(const double2* __restrict__ src, int ld,
                                                        int rows, int K, int form, int rows_out_p,
-                                                       int Kp, __nv_bfloat16* __restrict__ Q,
-                                                       int* __restrict__ e) {
-  __shared__ double sh[33];
+                                                       int Kp, const int* __restrict__ e,
+                                                       __nv_bfloat16* __restrict__ Q) {
   const int r = blockIdx.x;
   const double2* row = src + (size_t)r * ld;
   const bool valid = r < rows;
-  double mx = 0.0;
-  if (valid)
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      const double2 v = row[k];
-      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-    }
-  mx = block_max(mx, sh);
-  const int ex = exp_bound(mx);
-  if (threadIdx.x == 0 && valid) e[r] = ex;
-  const double sc = pow2(56 - ex);
-  const size_t slice = (size_t)rows_out_p * Kp;
+  const int ex = valid ? oz_exp(e[r]) : 0;
+  const size_t slice2 = (size_t)rows_out_p * Kp / 2;     // one slice, in BF16 pairs
   const int orow = form == 0 ? r : 2 * r;
-  const int kh = Kp / 2;
-  for (int k = threadIdx.x; k < kh; k += blockDim.x) {
+  unsigned* base0 = reinterpret_cast<unsigned*>(Q + (size_t)orow * Kp);
+  unsigned* base1 = reinterpret_cast<unsigned*>(Q + (size_t)(orow + 1) * Kp);
+  const int k0 = blockIdx.y * OZ_ROW_CHUNK, k1 = min(Kp / 2, k0 + OZ_ROW_CHUNK);
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     double2 v = make_double2(0.0, 0.0);
     if (valid && k < K) v = row[k];
-    __nv_bfloat16 qx[OZ_S], qy[OZ_S];
-    slices_of(v.x, sc, qx);
-    slices_of(v.y, sc, qy);
+    unsigned short qx[OZ_S], qy[OZ_S];
+    slices_of(v.x, ex, qx);
+    slices_of(v.y, ex, qy);
 #pragma unroll
     for (int t = 0; t < OZ_S; ++t) {
-      __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(Q + t * slice + (size_t)orow * Kp) + k;
-      *p0 = __halves2bfloat162(qx[t], qy[t]);
-      if (form == 1) {
-        __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(Q + t * slice + (size_t)(orow + 1) * Kp) + k;
-        *p1 = __halves2bfloat162(qy[t], __hneg(qx[t]));
-      }
+      base0[t * slice2 + k] = pack2(qx[t], qy[t]);
+      if (form == 1) base1[t * slice2 + k] = pack2(qy[t], (unsigned short)(qx[t] ^ 0x8000u));
     }
   }
 }
 
 // Column exponents of a complex [K][M] matrix (leading dimension ld): e[m] for
-// max over k of |x|, |y|; consecutive threads take consecutive m.
+// max over k of |x|, |y|.  grid (ceil(M / 256), ceil(K / 64)): each thread
+// scans 64 rows of its column (consecutive threads, consecutive m) and merges
+// its exponent bound with atomicMax (the bound is monotonic in the maximum);
+// e must hold 0x80808080 (below every exponent) beforehand, and an all-zero
+// column keeps it.
 __global__ void k_oz_colmax(const double2* __restrict__ src, int ld, int K, int M, int* __restrict__ e) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
-  double mx = 0.0;
-  for (int k = 0; k < K; ++k) {
+  const int k0 = blockIdx.y * 64, k1 = min(K, k0 + 64);
+  unsigned long long mx = 0;
+#pragma unroll 8
+  for (int k = k0; k < k1; ++k) {
     const double2 v = src[(size_t)k * ld + m];
-    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    const unsigned long long a = mag_bits(v.x), c = mag_bits(v.y);
+    const unsigned long long h = a > c ? a : c;
+    mx = h > mx ? h : mx;
   }
-  e[m] = exp_bound(mx);
+  if (mx != 0) atomicMax(&e[m], exp_bound_bits(mx));
 }
 
 // Transposed slicing of a complex [K][M] matrix: output rows from its columns.
@@ -402,19 +471,19 @@ __global__ void k_oz_slice_cols(const double2* __restrict__ src, int ld, int K, 
     const int orow = form == 0 ? m : 2 * m;
     if (orow >= rows_out_p || 2 * k >= Kp) continue;
     const double2 v = tile[threadIdx.x][r];
-    const double sc = pow2(56 - (m < M ? e[m] : 0));
-    __nv_bfloat16 qx[OZ_S], qy[OZ_S];
-    slices_of(v.x, sc, qx);
-    slices_of(v.y, sc, qy);
+    const int ex = m < M ? oz_exp(e[m]) : 0;
+    unsigned short qx[OZ_S], qy[OZ_S];
+    slices_of(v.x, ex, qx);
+    slices_of(v.y, ex, qy);
+    unsigned* p0 = reinterpret_cast<unsigned*>(Q + (size_t)orow * Kp) + k;
+    unsigned* p1 = reinterpret_cast<unsigned*>(Q + (size_t)(orow + 1) * Kp) + k;
 #pragma unroll
     for (int t = 0; t < OZ_S; ++t) {
-      __nv_bfloat162* p0 = reinterpret_cast<__nv_bfloat162*>(Q + t * slice + (size_t)orow * Kp) + k;
       if (form == 0) {
-        *p0 = __halves2bfloat162(qx[t], qy[t]);
+        p0[t * slice / 2] = pack2(qx[t], qy[t]);
       } else {
-        *p0 = __halves2bfloat162(qx[t], __hneg(qy[t]));
-        __nv_bfloat162* p1 = reinterpret_cast<__nv_bfloat162*>(Q + t * slice + (size_t)(orow + 1) * Kp) + k;
-        *p1 = __halves2bfloat162(qy[t], qx[t]);
+        p0[t * slice / 2] = pack2(qx[t], (unsigned short)(qy[t] ^ 0x8000u));
+        p1[t * slice / 2] = pack2(qy[t], qx[t]);
       }
     }
   }
@@ -495,12 +564,24 @@ static OzOperand oz_carve(void* mem, int rows_out, int K) {
 // input row; form 1: the inner product's B pair).  Returns the carved operand.
 int oz_slice_rows(const double* src, int ld, int rows, int K, int form, void* mem, OzOperand* out,
                   cudaStream_t st, Prof* pf) {
-  ProfScope ps(pf, "k_oz_slice", st);
   const int rows_out = form == 0 ? rows : 2 * rows;
   *out = oz_carve(mem, rows_out, K);
+  if (rows > 0) {
+    ProfScope ps(pf, "k_oz_rowmax", st);
+    if (cudaMemsetAsync(out->e, 0x80, (size_t)rows * sizeof(int), st) != cudaSuccess) {
+      set_error("oz_slice_rows: memset failed");
+      return QE_ECUDA;
+    }
+    dim3 gm(rows, (K + OZ_ROW_CHUNK - 1) / OZ_ROW_CHUNK);
+    k_oz_rowmax<<<gm, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, out->e);
+    int rc = oz_check("k_oz_rowmax");
+    if (rc) return rc;
+  }
+  ProfScope ps(pf, "k_oz_slice_rows", st);
   const int in_rows_p = form == 0 ? out->rows_p : out->rows_p / 2;
-  k_oz_slice_rows<<<in_rows_p, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, rows, K,
-                                             form, out->rows_p, out->Kp, out->q, out->e);
+  dim3 g(in_rows_p, (out->Kp / 2 + OZ_ROW_CHUNK - 1) / OZ_ROW_CHUNK);
+  k_oz_slice_rows<<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, rows, K, form,
+                                     out->rows_p, out->Kp, out->e, out->q);
   return oz_check("k_oz_slice_rows");
 }
 
@@ -508,14 +589,20 @@ int oz_slice_rows(const double* src, int ld, int rows, int K, int form, void* me
 // per column; form 2: the outer product's B pair).
 int oz_slice_cols(const double* src, int ld, int K, int cols, int form, void* mem, OzOperand* out,
                   cudaStream_t st, Prof* pf) {
-  ProfScope ps(pf, "k_oz_slice", st);
   const int rows_out = form == 0 ? cols : 2 * cols;
   *out = oz_carve(mem, rows_out, K);
-  k_oz_colmax<<<(cols + 255) / 256, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols,
-                                                  out->e);
-  int rc = oz_check("k_oz_colmax");
-  if (rc) return rc;
-  if (pf) pf->launches += 1;
+  {
+    ProfScope ps(pf, "k_oz_colmax", st);
+    if (cudaMemsetAsync(out->e, 0x80, (size_t)cols * sizeof(int), st) != cudaSuccess) {
+      set_error("oz_slice_cols: memset failed");
+      return QE_ECUDA;
+    }
+    dim3 gm((cols + 255) / 256, (K + 63) / 64);
+    k_oz_colmax<<<gm, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols, out->e);
+    int rc = oz_check("k_oz_colmax");
+    if (rc) return rc;
+  }
+  ProfScope ps(pf, "k_oz_slice_cols", st);
   const int cols_p = form == 0 ? out->rows_p : out->rows_p / 2;
   dim3 g((cols_p + 31) / 32, out->Kp / 64);
   k_oz_slice_cols<<<g, dim3(32, 8), 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols,
