@@ -267,7 +267,7 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(nonlocal_tc(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->tc_beta.p, pack,
                        ctx->tc_work.p, ctx->tc_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof));
     ctx->tc_beta_tag = op.tag;
-  } else if (op.nproj > 0 && fp64_gemm_on_tensor_cores()) {
+  } else if (op.nproj > 0 && oz_worth(op.nproj, nb, npw)) {
     // FP64: FP64-accurate projector products on the BF16 tensor cores (Ozaki slices)
     const int np = op.nproj;
     QE_TRY(ctx->oz_work.ensure(nonlocal_oz_bytes(np, nb, npw)));

@@ -151,7 +151,7 @@ static int batch_launch(BatchWork& W, int nprob, const qe_problem* probs, const 
     if (sizeof(T) == sizeof(float)) {
       BT_TRY(nonlocal_tc(op.beta, op.dmat, psi[p], hpsi[p], np, nb, npw, W.tc_beta.p, true,
                          W.tc_work.p, W.tc_work.bytes, (int*)W.tc_status.p, st, pf));
-    } else if (fp64_gemm_on_tensor_cores()) {
+    } else if (oz_worth(np, nb, npw)) {
       BT_TRY(nonlocal_oz(op.beta, op.dmat, psi[p], hpsi[p], np, nb, npw, W.oz_beta.p, true,
                          W.oz_work.p, W.oz_work.bytes, (int*)W.tc_status.p, st, pf));
     } else {

@@ -183,7 +183,21 @@ struct DvState {
   DenseWork dw;
   void* part = nullptr;
   size_t part_bytes = 0;
+  // FP64 subspace products on the tensor cores: operand slices + partials
+  void* oz = nullptr;
+  size_t oz_bytes = 0;
 };
+
+// Scratch of the FP64 tensor-core subspace products: the largest inner product
+// (basis x new block over the plane waves) and outer product (rotation of the
+// basis) of a solve.
+// The mixed path uses it only for its final FP64 Rayleigh-Ritz on the nb Ritz vectors.
+static size_t dv_oz_bytes(size_t npw, size_t nb, size_t md, bool fp64) {
+  if (!fp64_gemm_on_tensor_cores()) return 0;
+  const size_t n = fp64 ? md : nb;
+  return std::max(oz_inner_scratch((int)n, (int)nb, (int)npw),
+                  oz_outer_scratch((int)npw, (int)nb, (int)n)) + 256;
+}
 
 static size_t dv_bytes(size_t npw, size_t nb, size_t md) {
   const size_t zb = sizeof(z);
@@ -208,17 +222,19 @@ size_t davidson_footprint(int npw, int nb, int max_dim, int nproj, const int gri
   const size_t ngrid = (size_t)grid[0] * grid[1] * grid[2];
   const size_t per_band = (size_t)grid[2] * nst * sizeof(z);
   const size_t nbc = std::max<size_t>(1, std::min<size_t>(nb, ((size_t)64 << 20) / std::max<size_t>(per_band, 1)));
-  size_t b = dv_bytes(npw, nb, md) + dv_red_bytes(md);
+  size_t b = dv_bytes(npw, nb, md) + dv_red_bytes(md) + dv_oz_bytes(npw, nb, md, true);
   b += ngrid * sizeof(double) * 2;                                  // V copy + permuted V
   b += nbc * per_band;                                              // stick buffer
   b += gemm_inner_scratch(nproj, nb, npw, sizeof(double));          // split-K partials
+  if (nproj > 0 && fp64_gemm_on_tensor_cores())                     // beta slices + work
+    b += nonlocal_oz_bytes(nproj, nb, npw) + nonlocal_oz_beta_bytes(nproj, npw);
   b += 2 * (size_t)nproj * nb * sizeof(z);                          // projections
   b += (size_t)nproj * npw * sizeof(z) + (size_t)nproj * nproj * sizeof(double);   // beta, D
   b += (size_t)npw * 24 + 16 * (size_t)npw + 64 * (size_t)(grid[0] + grid[1] + grid[2]);   // plan
   return b + ((size_t)1 << 20);
 }
 
-static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S) {
+static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
   const size_t npw = S.npw, nb = S.nb, md = S.max_dim;
   const size_t zb = sizeof(z);
   // big: V, HV [md][npw]; Psi, HPsi, R, D, D2 [nb][npw]
@@ -278,17 +294,38 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S) {
   }
   // split-K partials: at most (splits for ~4 CTAs/SM + tiles) 32x32 tiles of FP64 complex
   const size_t sb = dv_red_bytes(md);
-  DV_TRY(red.ensure(sb));
+  const size_t ob = dv_oz_bytes(npw, nb, md, fp64);
+  DV_TRY(red.ensure(sb + ob));
   S.part = red.p;
   S.part_bytes = sb;
+  S.oz = ob ? static_cast<char*>(red.p) + sb : nullptr;
+  S.oz_bytes = ob;
   return QE_OK;
 }
+
+// The status word of the tensor-core products of a solve (a bounded wait that
+// ran out); read with the other status words at every convergence test.
+static int* dv_tc_status(const DvState& S) { return S.dw.status + 12; }
 
 template <typename T>
 static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
                 cudaStream_t st, Prof* pf) {
+  if (sizeof(T) == sizeof(double) && S.oz && oz_worth(m, n, S.npw))
+    return oz_inner((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C, ldc,
+                    S.oz, S.oz_bytes, dv_tc_status(S), st, pf);
   return gemm_inner<T>((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C,
                        ldc, S.part, S.part_bytes, st, pf);
+}
+
+// C[n][m] (+)= (-) sum_k A[k][m] B[k][n]: rotations and projections out of the basis
+template <typename T>
+static int outer(const DvState& S, const z* A, int lda, const z* B, int ldb, int M, int N, int K,
+                 z* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf) {
+  if (sizeof(T) == sizeof(double) && S.oz && oz_worth(M, N, K))
+    return oz_outer((const double*)A, lda, (const double*)B, ldb, M, N, K, (double*)C, ldc,
+                    alpha_neg, beta, S.oz, S.oz_bytes, dv_tc_status(S), st, pf);
+  return gemm_outer_ab<T>((const double*)A, lda, (const double*)B, ldb, M, N, K, (double*)C, ldc,
+                          alpha_neg, beta, st, pf);
 }
 
 // Reduced matrices: columns [n0, n1) for rows [0, n1), then the mirrored rows.
@@ -343,8 +380,7 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
   for (int pass = 0; pass < 2 && ncur > 0; ++pass) {
     // cur -= V (V^+ cur)
     DV_TRY(gram<T>(S, S.V, n, cur, ncur, S.C, ncur, st, pf));
-    DV_TRY(gemm_outer_ab<T>((const double*)S.V, npw, (const double*)S.C, ncur, npw, ncur, n,
-                            (double*)cur, npw, 1, 1, st, pf));
+    DV_TRY(outer<T>(S, S.V, npw, S.C, ncur, npw, ncur, n, cur, npw, 1, 1, st, pf));
     // Cholesky of the block's Gram matrix with dropping
     DV_TRY(gram<T>(S, cur, ncur, cur, ncur, S.G, ncur, st, pf));
     DV_TRY(hermitize(S.G, ncur, ncur, st));
@@ -372,8 +408,7 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
     k_place_rows<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.Mk, nk, S.idx, nk, S.Mf);
     DV_TRY(check_launch("k_place_rows"));
     z* dst = last ? out : S.D2;
-    DV_TRY(gemm_outer_ab<T>((const double*)cur, npw, (const double*)S.Mf, nk, npw, nk, ncur,
-                            (double*)dst, npw, 0, 0, st, pf));
+    DV_TRY(outer<T>(S, cur, npw, S.Mf, nk, npw, nk, ncur, dst, npw, 0, 0, st, pf));
     cur = dst;
     ncur = nk;
     *nk_out = nk;
@@ -400,10 +435,8 @@ static int refine_post(DvState& S, cudaStream_t st, Prof* pf) {
   DV_TRY(update_reduced<double>(S, 0, nb, st, pf));
   DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
   DV_TRY(rayleigh_ritz(S, nb, st, pf));
-  DV_TRY(gemm_outer_ab<double>((const double*)S.V, npw, (const double*)S.X, nb, npw, nb, nb,
-                               (double*)S.Psi, npw, 0, 0, st, pf));
-  DV_TRY(gemm_outer_ab<double>((const double*)S.HV, npw, (const double*)S.X, nb, npw, nb, nb,
-                               (double*)S.HPsi, npw, 0, 0, st, pf));
+  DV_TRY(outer<double>(S, S.V, npw, S.X, nb, npw, nb, nb, S.Psi, npw, 0, 0, st, pf));
+  DV_TRY(outer<double>(S, S.HV, npw, S.X, nb, npw, nb, nb, S.HPsi, npw, 0, 0, st, pf));
   k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
   return check_launch("k_resid");
 }
@@ -458,10 +491,8 @@ static int dv_step_launch(DvSolve& v, cudaStream_t st, Prof* pf) {
   const size_t zb = sizeof(z);
   DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));   // keeps the barrier error word
   DV_TRY(rayleigh_ritz(S, v.n, st, pf));
-  DV_TRY(gemm_outer_ab<T>((const double*)S.V, npw, (const double*)S.X, nb, npw, nb, v.n,
-                          (double*)S.Psi, npw, 0, 0, st, pf));
-  DV_TRY(gemm_outer_ab<T>((const double*)S.HV, npw, (const double*)S.X, nb, npw, nb, v.n,
-                          (double*)S.HPsi, npw, 0, 0, st, pf));
+  DV_TRY(outer<T>(S, S.V, npw, S.X, nb, npw, nb, v.n, S.Psi, npw, 0, 0, st, pf));
+  DV_TRY(outer<T>(S, S.HV, npw, S.X, nb, npw, nb, v.n, S.HPsi, npw, 0, 0, st, pf));
   if (v.first) {
     // the Ritz vectors of the start block become the (orthonormal) basis
     DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
@@ -491,6 +522,10 @@ static int dv_step_finish(qe_ctx* ctx, DvSolve& v, cudaStream_t st, Prof* pf) {
   DV_TRY(tc_check(ctx, st));
   if (status[8] != 0) {
     set_error("davidson: a grid barrier of the dense eigensolver timed out");
+    return QE_ETIMEOUT;
+  }
+  if (status[12] != 0) {
+    set_error("davidson: a tensor-core product wait timed out (code %d)", status[12]);
     return QE_ETIMEOUT;
   }
   if (status[0] != 0) {
@@ -649,7 +684,7 @@ int dv_setup(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int
   S.nb = nb;
   S.max_dim = md;
   S.np = prob->nproj;
-  return dv_alloc(basis, red, S);
+  return dv_alloc(basis, red, S, precision == QE_FP64);
 }
 
 // Final status of a solve: barrier and overlap checks of the last Rayleigh-Ritz.
@@ -658,6 +693,7 @@ int dv_final_status(DvSolve& v, cudaStream_t st, const char* who) {
   DV_CU(cudaMemcpyAsync(fin, v.S.dw.status, sizeof(fin), cudaMemcpyDeviceToHost, st));
   DV_CU(cudaStreamSynchronize(st));
   if (fin[8] != 0) { set_error("%s: a grid barrier of the dense eigensolver timed out", who); return QE_ETIMEOUT; }
+  if (fin[12] != 0) { set_error("%s: a tensor-core product wait timed out", who); return QE_ETIMEOUT; }
   if (fin[0] != 0) { set_error("%s: final overlap matrix not positive definite", who); return QE_ENOCONV; }
   return QE_OK;
 }

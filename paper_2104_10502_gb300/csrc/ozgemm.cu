@@ -690,6 +690,62 @@ bool fp64_gemm_on_tensor_cores() {
   return on;
 }
 
+// Whether an FP64 complex product of this size goes to the tensor cores: the
+// slicing launches and the one-wave split cost ~30 us, which the DFMA kernels
+// recover below ~4 M complex multiply-adds.
+bool oz_worth(long long M, long long N, long long K) {
+  return fp64_gemm_on_tensor_cores() && M > 0 && N > 0 && M * N * K >= (1ll << 22);
+}
+
+// ---- general complex products from FP64 operands ------------------------------------
+size_t oz_inner_scratch(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 0;
+  return oz_operand_bytes(M, K) + oz_operand_bytes(2 * N, K) + oz_partial_bytes(M, N, K);
+}
+
+size_t oz_outer_scratch(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 0;
+  return oz_operand_bytes(M, K) + oz_operand_bytes(2 * N, K);
+}
+
+// C[m][n] = sum_k conj(A[m][k]) B[n][k] (rows of A and B contiguous in k,
+// leading dimensions in complex units), FP64-accurate on the tensor cores.
+int oz_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
+             int ldc, void* scratch, size_t scratch_bytes, int* status, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  if (oz_inner_scratch(M, N, K) > scratch_bytes) {
+    set_error("oz_inner: scratch too small");
+    return QE_EINVAL;
+  }
+  char* p = static_cast<char*>(scratch);
+  OzOperand a, b;
+  int rc;
+  if ((rc = oz_slice_rows(A, lda, M, K, 0, p, &a, st, pf))) return rc;
+  p += oz_operand_bytes(M, K);
+  if ((rc = oz_slice_rows(B, ldb, N, K, 1, p, &b, st, pf))) return rc;
+  p += oz_operand_bytes(2 * N, K);
+  return oz_gemm_inner(a, b, M, N, C, ldc, p, oz_partial_bytes(M, N, K), status, st, pf);
+}
+
+// C[n][m] (+)= (-) sum_k A[k][m] B[k][n] (rows of A and B indexed by k),
+// FP64-accurate on the tensor cores.
+int oz_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
+             int ldc, int alpha_neg, int beta, void* scratch, size_t scratch_bytes, int* status,
+             cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  if (oz_outer_scratch(M, N, K) > scratch_bytes) {
+    set_error("oz_outer: scratch too small");
+    return QE_EINVAL;
+  }
+  char* p = static_cast<char*>(scratch);
+  OzOperand a, b;
+  int rc;
+  if ((rc = oz_slice_cols(A, lda, K, M, 0, p, &a, st, pf))) return rc;
+  p += oz_operand_bytes(M, K);
+  if ((rc = oz_slice_cols(B, ldb, K, N, 2, p, &b, st, pf))) return rc;
+  return oz_gemm_outer(a, b, M, N, C, ldc, alpha_neg, beta, status, st, pf);
+}
+
 // ---- the nonlocal term -----------------------------------------------------------
 size_t nonlocal_oz_beta_bytes(int np, int npw) {
   return oz_operand_bytes(np, npw) + oz_operand_bytes(npw, np);

@@ -180,8 +180,20 @@ size_t nonlocal_oz_beta_bytes(int np, int npw);
 int nonlocal_oz(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
                 int nb, int npw, void* bslices, bool slice_beta, void* work, size_t work_bytes,
                 int* status, cudaStream_t st, Prof* pf);
-// FP64 projector products on the tensor cores (default) or on the DFMA pipe
+// FP64 complex products on the tensor cores (default) or on the DFMA pipe
 // (environment QE_FP64_GEMM=simt).
 bool fp64_gemm_on_tensor_cores();
+// ... and large enough for them to pay (M N K >= 2^22 complex multiply-adds).
+bool oz_worth(long long M, long long N, long long K);
+// General FP64-accurate complex products on the tensor cores (ozgemm.cu), with
+// the semantics of gemm_inner / gemm_outer_ab; scratch of oz_*_scratch bytes;
+// a bounded wait that ran out writes a non-zero code to *status.
+size_t oz_inner_scratch(int M, int N, int K);
+size_t oz_outer_scratch(int M, int N, int K);
+int oz_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
+             int ldc, void* scratch, size_t scratch_bytes, int* status, cudaStream_t st, Prof* pf);
+int oz_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
+             int ldc, int alpha_neg, int beta, void* scratch, size_t scratch_bytes, int* status,
+             cudaStream_t st, Prof* pf);
 
 }  // namespace qe
