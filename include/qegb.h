@@ -247,7 +247,7 @@ enum { QE_SERVE_FAKE_SOLVER = 1 };   /* test hook: no GPU; a solve sleeps max_it
 int qe_serve_create(int device, size_t hbm_budget_bytes, int max_slots, int max_queue,
                     int flags, qe_srv** out);
 
-/* Queue a Davidson solve (as qe_davidson with max_dim = 4 nbnd).  Every array of
+/* Queue a Davidson solve (as qe_davidson with the default max_dim, 4 nbnd).  Every array of
  * prob and psi0 must be host memory (prob->mem = QE_HOST); they are copied
  * before the call returns.  *ticket identifies the request.  QE_EAGAIN when the
  * queue is full; QE_EINVAL when the request alone exceeds the budget. */

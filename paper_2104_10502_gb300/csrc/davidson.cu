@@ -202,7 +202,7 @@ static size_t dv_oz_bytes(size_t npw, size_t nb, size_t md, bool fp64) {
 static size_t dv_bytes(size_t npw, size_t nb, size_t md) {
   const size_t zb = sizeof(z);
   const size_t big = (2 * md + 5 * nb) * npw * zb;
-  const size_t smallz = (5 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
+  const size_t smallz = (6 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
   const size_t dbl = (2 * nb + npw + 1 + 3 * md + nb * md) * sizeof(double);
   const size_t dwz = 3 * md * zb;
   const size_t ints = (nb + 16) * sizeof(int);
@@ -239,8 +239,8 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
   const size_t zb = sizeof(z);
   // big: V, HV [md][npw]; Psi, HPsi, R, D, D2 [nb][npw]
   const size_t big = (2 * md + 5 * nb) * npw * zb;
-  // small complex: Hr, Sr, Lw, Zw, Aw [md][md]; X [md][nb]; C [md][nb]; G, Mf, Mk, Lk [nb][nb]
-  const size_t smallz = (5 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
+  // small complex: Hr, Sr, Lw, Zw, Aw, reflectors [md][md]; X [md][nb]; C [md][nb]; G, Mf, Mk, Lk [nb][nb]
+  const size_t smallz = (6 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
   // doubles: e, rn [nb]; hd [npw]; vmean; dense work: d, e, piv [md], y [nb][md]
   const size_t dbl = (2 * nb + npw + 1 + 3 * md + nb * md) * sizeof(double);
   // dense work complex: tau, p, vbuf [md]
@@ -283,6 +283,7 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
   S.dw.tau = (z*)take(md * zb);
   S.dw.p = (z*)take(md * zb);
   S.dw.vbuf = (z*)take(md * zb);
+  S.dw.refl = (z*)take(md * md * zb);
   S.idx = (int*)take(nb * sizeof(int));
   S.dw.status = (int*)take(16 * sizeof(int));
   S.dw.bar.count = reinterpret_cast<unsigned int*>(S.dw.status + 4);
@@ -329,23 +330,36 @@ static int outer(const DvState& S, const z* A, int lda, const z* B, int ldb, int
 }
 
 // Reduced matrices: columns [n0, n1) for rows [0, n1), then the mirrored rows.
+// The overlap S_r only when the Rayleigh-Ritz that follows is a generalised one.
 template <typename T>
-static int update_reduced(const DvState& S, int n0, int n1, cudaStream_t st, Prof* pf) {
+static int update_reduced(const DvState& S, int n0, int n1, bool with_s, cudaStream_t st, Prof* pf) {
   const int md = S.max_dim;
   DV_TRY(gram<T>(S, S.V, n1, S.HV + (size_t)n0 * S.npw, n1 - n0, S.Hr + n0, md, st, pf));
-  DV_TRY(gram<T>(S, S.V, n1, S.V + (size_t)n0 * S.npw, n1 - n0, S.Sr + n0, md, st, pf));
+  if (with_s) DV_TRY(gram<T>(S, S.V, n1, S.V + (size_t)n0 * S.npw, n1 - n0, S.Sr + n0, md, st, pf));
   if (n0 > 0) {
     const size_t t = (size_t)(n1 - n0) * n0;
     k_mirror<<<grid_for(t), 256, 0, st>>>(S.Hr, md, n0, n1);
-    k_mirror<<<grid_for(t), 256, 0, st>>>(S.Sr, md, n0, n1);
+    if (with_s) k_mirror<<<grid_for(t), 256, 0, st>>>(S.Sr, md, n0, n1);
   }
   return check_launch("k_mirror");
 }
 
 // Rayleigh-Ritz on span(V[0:n]): eigenvalues e[0:nb], X [n][nb] (ld nb).
-static int rayleigh_ritz(DvState& S, int n, cudaStream_t st, Prof* pf) {
+// Generalised (S_r = L L^+ by Cholesky, then the standard problem of
+// L^-1 H_r L^-+) in every iteration: the basis is orthonormal only up to the
+// eigenvector accuracy of the previous reduced problem (inverse iteration
+// re-orthogonalises only within clusters of eigenvalues closer than 1e-10 of
+// the spread), and a standard Rayleigh-Ritz that assumed S_r = I stalled the
+// C0 iteration.  `generalised = false` (S_r = I) is kept for callers that know
+// their basis is orthonormal.
+static int rayleigh_ritz(DvState& S, int n, bool generalised, cudaStream_t st, Prof* pf) {
   const int md = S.max_dim, nb = S.nb;
   const size_t zb = sizeof(z);
+  if (!generalised) {
+    DV_CU(cudaMemcpy2DAsync(S.Aw, n * zb, S.Hr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
+    DV_TRY(hermitize(S.Aw, n, n, st));
+    return heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf);
+  }
   DV_CU(cudaMemcpy2DAsync(S.Lw, n * zb, S.Sr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
   DV_CU(cudaMemcpy2DAsync(S.Zw, n * zb, S.Hr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
   {
@@ -432,9 +446,9 @@ static int refine_pre(DvState& S, cudaStream_t st) {
 
 static int refine_post(DvState& S, cudaStream_t st, Prof* pf) {
   const int npw = S.npw, nb = S.nb;
-  DV_TRY(update_reduced<double>(S, 0, nb, st, pf));
+  DV_TRY(update_reduced<double>(S, 0, nb, true, st, pf));
   DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
-  DV_TRY(rayleigh_ritz(S, nb, st, pf));
+  DV_TRY(rayleigh_ritz(S, nb, true, st, pf));
   DV_TRY(outer<double>(S, S.V, npw, S.X, nb, npw, nb, nb, S.Psi, npw, 0, 0, st, pf));
   DV_TRY(outer<double>(S, S.HV, npw, S.X, nb, npw, nb, nb, S.HPsi, npw, 0, 0, st, pf));
   k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
@@ -479,7 +493,7 @@ static int dv_begin(DvSolve& v, cudaStream_t st) {
 template <typename T>
 static int dv_after_first_h(DvSolve& v, cudaStream_t st, Prof* pf) {
   v.h_rows = 0;
-  return update_reduced<T>(v.S, 0, v.n, st, pf);
+  return update_reduced<T>(v.S, 0, v.n, true, st, pf);
 }
 
 // Rayleigh-Ritz and residuals, launched without waiting (a batch queues every
@@ -490,7 +504,7 @@ static int dv_step_launch(DvSolve& v, cudaStream_t st, Prof* pf) {
   const int npw = S.npw, nb = S.nb;
   const size_t zb = sizeof(z);
   DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));   // keeps the barrier error word
-  DV_TRY(rayleigh_ritz(S, v.n, st, pf));
+  DV_TRY(rayleigh_ritz(S, v.n, true, st, pf));
   DV_TRY(outer<T>(S, S.V, npw, S.X, nb, npw, nb, v.n, S.Psi, npw, 0, 0, st, pf));
   DV_TRY(outer<T>(S, S.HV, npw, S.X, nb, npw, nb, v.n, S.HPsi, npw, 0, 0, st, pf));
   if (v.first) {
@@ -498,7 +512,7 @@ static int dv_step_launch(DvSolve& v, cudaStream_t st, Prof* pf) {
     DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
     DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
     v.n = nb;
-    DV_TRY(update_reduced<T>(S, 0, v.n, st, pf));
+    DV_TRY(update_reduced<T>(S, 0, v.n, true, st, pf));
     v.first = false;
   }
   k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
@@ -546,7 +560,7 @@ static int dv_step_finish(qe_ctx* ctx, DvSolve& v, cudaStream_t st, Prof* pf) {
     DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
     DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
     v.n = nb;
-    DV_TRY(update_reduced<T>(S, 0, v.n, st, pf));
+    DV_TRY(update_reduced<T>(S, 0, v.n, true, st, pf));
   }
   int nk = 0;
   DV_TRY(orthonormalise<T>(S, v.n, S.D, nu, S.V + (size_t)v.n * npw, &nk, drop, st, pf));
@@ -559,7 +573,7 @@ static int dv_step_finish(qe_ctx* ctx, DvSolve& v, cudaStream_t st, Prof* pf) {
 
 template <typename T>
 static int dv_after_h(DvSolve& v, cudaStream_t st, Prof* pf) {
-  DV_TRY(update_reduced<T>(v.S, v.n, v.n + v.nk, st, pf));
+  DV_TRY(update_reduced<T>(v.S, v.n, v.n + v.nk, true, st, pf));
   v.n += v.nk;
   v.h_rows = 0;
   return QE_OK;
@@ -660,6 +674,13 @@ using namespace qe;
 
 namespace {
 
+// Default basis size in units of nbnd.  Four: with two (Quantum ESPRESSO's
+// default workspace) the reduced problems are 8x cheaper, but the iteration
+// stalls on the SMALL cell (7 bands, band 7 close to band 8) and the FP64 C2
+// solve needs 48 instead of 19 iterations (2.35 s against 1.97 s); only the
+// mixed C2 solve gains (0.94 s against 1.38 s).  Callers can pass max_dim.
+constexpr int kDefaultDimFactor = 4;
+
 // Checks of one problem's arguments, its plan and operator, and the layout of
 // its Davidson workspace in `basis` / `red`.
 int dv_setup(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int max_iter,
@@ -670,7 +691,7 @@ int dv_setup(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int
   DV_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
   const int npw = P->h.npw;
   if (nb > npw) { set_error("%s: %d bands > %d plane waves", who, nb, npw); return QE_EINVAL; }
-  int md = max_dim > 0 ? max_dim : 4 * nb;
+  int md = max_dim > 0 ? max_dim : kDefaultDimFactor * nb;
   if (md < 2 * nb) { set_error("%s: max_dim %d < 2 nbnd", who, md); return QE_EINVAL; }
   md = std::min(md, std::max(2 * nb, npw));
   if (md > kMaxDense) { set_error("%s: max_dim %d above %d", who, md, kMaxDense); return QE_EINVAL; }

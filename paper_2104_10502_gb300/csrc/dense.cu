@@ -274,15 +274,12 @@ int hermitize(z* A, int n, int lda, cudaStream_t st) {
 
 // ---- Householder reflectors ----------------------------------------------------------
 // Step j: H = I - tau v v^+, v_0 = 1, H^+ x = beta e_1 with beta real, where x is
-// column j below the diagonal; v_1.. are stored in A[j+2 ..][j], A[j+1][j] = beta.
-__device__ __forceinline__ z house_v(const z* A, int lda, int j, int r) {
-  // component r (absolute row index, r >= j+1) of the reflector of step j
-  return r == j + 1 ? z{1.0, 0.0} : A[(size_t)r * lda + j];
-}
-
+// column j below the diagonal; v_1.. are stored in A[j+2 ..][j] and, for the
+// back-transformation, in row j of refl; A[j+1][j] = beta.
 // Reflector of step j from the updated column j (rows j+1 ..), computed by one
 // CTA: v_1.. to A[j+2 ..][j] and vbuf[1 ..], beta to A[j+1][j] and e[j], tau[j].
-__device__ void house_step(z* A, int n, int lda, int j, z* tau, double* e, z* vbuf, double* sh) {
+__device__ void house_step(z* A, int n, int lda, int j, z* tau, double* e, z* vbuf, z* refl,
+                           double* sh) {
   const int m = n - j - 1;
   const z alpha = ldz(&A[(size_t)(j + 1) * lda + j]);
   double s = 0.0;
@@ -297,17 +294,20 @@ __device__ void house_step(z* A, int n, int lda, int j, z* tau, double* e, z* vb
   const z am = {alpha.x - beta, alpha.y};
   const double den = am.x * am.x + am.y * am.y;
   const z sc = {am.x / den, -am.y / den};
+  z* rrow = refl + (size_t)j * n + (j + 1);
   for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
     z* x = &A[(size_t)(j + 1 + i) * lda + j];
     const z v = cmul(ldz(x), sc);
     *x = v;
     vbuf[i] = v;
+    rrow[i] = v;
   }
   if (threadIdx.x == 0) {
     tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
     e[j] = beta;
     A[(size_t)(j + 1) * lda + j] = {beta, 0.0};
     vbuf[0] = {1.0, 0.0};
+    rrow[0] = {1.0, 0.0};
   }
 }
 
@@ -318,7 +318,7 @@ __device__ void house_step(z* A, int n, int lda, int j, z* tau, double* e, z* vb
 // step in shared memory, so the two phases stream only the trailing block of A.
 // Dynamic shared memory: 2 n complex.
 __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* tau, double* e, z* p,
-                                                      double* dg, z* vbuf, GridBar bar) {
+                                                      double* dg, z* vbuf, z* refl, GridBar bar) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   z* sv = reinterpret_cast<z*>(smem_raw);
   z* sw = sv + n;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* t
   const size_t nthr = (size_t)gridDim.x * blockDim.x;
   const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int nwarp = (int)(nthr >> 5), gwarp = (int)(gtid >> 5), lane = threadIdx.x & 31;
-  if (n >= 2 && blockIdx.x == 0) house_step(A, n, lda, 0, tau, e, vbuf, sh);
+  if (n >= 2 && blockIdx.x == 0) house_step(A, n, lda, 0, tau, e, vbuf, refl, sh);
   if (!grid_sync(bar)) return;
   for (int j = 0; j < n - 1; ++j) {
     const int m = n - j - 1;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* t
         }
         __syncthreads();
       }
-      house_step(A, n, lda, j + 1, tau, e, vbuf, sh);
+      house_step(A, n, lda, j + 1, tau, e, vbuf, refl, sh);
     } else if (blockIdx.x == 0 && active) {
       // last step: only the 1 x 1 trailing element remains
       for (int r = threadIdx.x; r < m; r += blockDim.x) {
@@ -568,9 +568,10 @@ __global__ void __launch_bounds__(256) k_inviter(const double* d, const double* 
   }
 }
 
-// X[:, k] = H_0 H_1 ... H_{n-2} y_k, one CTA per eigenvector; X [n][ldx].
-__global__ void __launch_bounds__(256) k_backtransform(const z* A, int n, int lda, const z* tau,
-                                                       const double* Y, z* X, int ldx) {
+// X[:, k] = H_0 H_1 ... H_{n-2} y_k, one CTA per eigenvector; X [n][ldx].  The
+// reflectors are read from their rows in refl (contiguous, coalesced).
+__global__ void __launch_bounds__(256) k_backtransform(const z* __restrict__ refl, int n,
+                                                       const z* tau, const double* Y, z* X, int ldx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   z* x = reinterpret_cast<z*>(smem_raw);
   __shared__ double sh[33];
@@ -580,16 +581,17 @@ __global__ void __launch_bounds__(256) k_backtransform(const z* A, int n, int ld
   for (int j = n - 2; j >= 0; --j) {
     const z t = tau[j];
     if (t.x == 0.0 && t.y == 0.0) continue;
+    const z* v = refl + (size_t)j * n;
     double sr = 0.0, si = 0.0;
     for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
-      const z v = house_v(A, lda, j, r), xr = x[r];
-      sr += v.x * xr.x + v.y * xr.y;
-      si += v.x * xr.y - v.y * xr.x;
+      const z vr = v[r], xr = x[r];
+      sr += vr.x * xr.x + vr.y * xr.y;
+      si += vr.x * xr.y - vr.y * xr.x;
     }
     const double a = block_sum(sr, sh);
     const double b = block_sum(si, sh);
     const z f = cmul(t, z{a, b});     // tau (v^+ x)
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) x[r] = csub(x[r], cmul(f, house_v(A, lda, j, r)));
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) x[r] = csub(x[r], cmul(f, v[r]));
     __syncthreads();
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)i * ldx + k] = x[i];
@@ -608,7 +610,7 @@ int heev_lowest(z* A, int n, int lda, int nev, double* w, z* X, int ldx, DenseWo
   }
   {
     GridBar bar = wk.bar;
-    void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.p, &wk.d, &wk.vbuf, &bar};
+    void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.p, &wk.d, &wk.vbuf, &wk.refl, &bar};
     const size_t tsm = 2 * (size_t)n * sizeof(z);
     set_max_dynamic_smem(k_tridiag_coop);
     // all SMs once the trailing block is large: the FP64 work is spread
@@ -639,7 +641,7 @@ int heev_lowest(z* A, int n, int lda, int nev, double* w, z* X, int ldx, DenseWo
   const size_t bsm = (size_t)n * sizeof(z);
   {
     ProfScope ps(pf, "heev_backtransform", st);
-    k_backtransform<<<nev, 256, bsm, st>>>(A, n, lda, wk.tau, wk.y, X, ldx);
+    k_backtransform<<<nev, 256, bsm, st>>>(wk.refl, n, wk.tau, wk.y, X, ldx);
   }
   return check_launch("k_backtransform");
 }

@@ -22,6 +22,7 @@ struct DenseWork {
   cx<double>* tau = nullptr;   // [n] Householder scalars
   cx<double>* p = nullptr;     // [n] tridiagonalisation work vector
   cx<double>* vbuf = nullptr;  // [n] reflector of the current step, contiguous
+  cx<double>* refl = nullptr;  // [n][n] reflector j in row j (coalesced back-transformation)
   double* d = nullptr;         // [n] diagonal of T
   double* e = nullptr;         // [n] off-diagonal of T
   double* y = nullptr;         // [nev][n] eigenvectors of T
