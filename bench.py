@@ -71,7 +71,15 @@ def kernel_flops(name, c, npw, nst, nax, nb, nproj):
         return 8.0 * nproj * nb * npw
     if name == "k_dmul":
         return 4.0 * nproj * nproj * nb
+    if name == "k_oz_gemm":
+        # BF16 tensor flops of the two launches (inner and outer product) of a
+        # call, per launch: 36 slice pairs x 2 flops x M N K of the real products
+        # (inner: nproj x 2nb x 2npw, outer: npw x 2nb x 2nproj)
+        return 36 * 2.0 * (nproj * 2 * nb * 2 * npw + npw * 2 * nb * 2 * nproj) / 2
     return 0.0
+
+
+TENSOR_KERNELS = {"k_oz_gemm"}
 
 
 class ClockSampler:
@@ -137,7 +145,7 @@ def src_hash(*names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"k_plane": ("fft.cu", "fft_device.cuh"), "k_zinv": ("fft.cu", "fft_device.cuh"),
+KERNEL_SOURCES = {"k_oz_gemm": ("ozgemm.cu", "tc_ptx.cuh"), "k_plane": ("fft.cu", "fft_device.cuh"), "k_zinv": ("fft.cu", "fft_device.cuh"),
                   "k_zfwd": ("fft.cu", "fft_device.cuh"), "k_gemm_inner": ("gemm.cu",),
                   "k_gemm_outer": ("gemm.cu",), "k_dmul": ("gemm.cu",)}
 
@@ -287,13 +295,22 @@ def run_gpu(args, rank, world, local_rank):
     dom = max(kern, key=lambda n: kern[n][1])
     calls, tot = kern[dom]
     avg_ms = tot / calls
-    fl_step = kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
+    fl_launch = kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
+    if dom in TENSOR_KERNELS:
+        # per launch already; the measured BF16 burst peak of the GB300s
+        fl_step = fl_launch * calls / args.steps
+        bound, peak = "tensor", pk["bf16_tflops"]
+        psrc = f"measured BF16 burst ({pk_kind}) of MEASURED_PEAKS.json"
+    else:
+        fl_step = fl_launch
+        bound, peak = "alu", FP64_NOMINAL_TFLOPS
+        psrc = "nominal FP64 of GB300 (recipe table); measured DFMA loop 1.17-1.19"
     fl = fl_step * args.steps / calls
     achieved = fl_step * args.steps / (tot / 1e3) / 1e12
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic_for(dom, "fp64"),
-            "peak_source": "nominal FP64 of GB300 (recipe table); measured DFMA loop 1.17-1.19",
+            "peak_source": psrc,
             "flops_per_launch": fl, "avg_launch_ms": avg_ms}
     kernels = {n: {"launches": kern[n][0], "ms": kern[n][1], "share": kern[n][1] / sum(x[1] for x in kern.values())}
                for n in kern}
@@ -509,6 +526,29 @@ def run_batch_bench(q, ctx, dev):
     return out
 
 
+def profile_davidson(name):
+    """One FP64 Davidson solve (after a warm-up solve) of a named workload: the
+    command that ncu captures of the dense eigensolver kernels run."""
+    import torch
+    import paper_2104_10502_gb300 as q
+    dev = torch.device("cuda", 0)
+    c = qeinputs.config(name)
+    with q.Context(0) as ctx:
+        prob, pt0, keep = device_problem(q, ctx, c["lat"], c["k"], c["ecut"], c["grid"], c["tau"],
+                                         c["widths"], c["nbnd"], c["psi_seed"], dev)
+        ev = torch.zeros(c["nbnd"], dtype=torch.float64, device=dev)
+        times = []
+        for _ in range(2):
+            pt = pt0.clone()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rc, it = ctx.davidson(prob, pt, ev, None, precision=q.QE_FP64, tol=1e-6, max_iter=200)
+            torch.cuda.synchronize(dev)
+            times.append(time.perf_counter() - t0)
+    print(json.dumps({"profile_davidson": name, "status": int(rc), "iters": int(it),
+                      "seconds": times[-1]}))
+
+
 def serve_requests(q, ctx, n, seed, dev):
     """Requests drawn like the serving workload, shrunk so that a stream ends in
     seconds: cubic a in U[10,14] bohr, ecut in U[20,30] Ry, nb in U{8..32},
@@ -591,7 +631,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solvers", action="store_true",
                     help="skip the Davidson and serving measurements")
+    ap.add_argument("--profile-davidson", default=None, metavar="CONFIG",
+                    help="profiling driver: one FP64 Davidson solve of C0, SMALL or C2 after one "
+                         "warm-up solve, a one-line JSON with its time, nothing else")
     args = ap.parse_args()
+    if args.profile_davidson:
+        profile_davidson(args.profile_davidson)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
