@@ -344,6 +344,84 @@ static int update_reduced(const DvState& S, int n0, int n1, bool with_s, cudaStr
   return check_launch("k_mirror");
 }
 
+// FP64 <-> FP32 copies of the reduced problem for the mixed path.
+__global__ void k_z_to_c(const z* __restrict__ src, int lds, cx<float>* __restrict__ dst, int ldd,
+                         int rows, int cols) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / cols), c = (int)(t % cols);
+    const z v = src[(size_t)r * lds + c];
+    dst[(size_t)r * ldd + c] = {(float)v.x, (float)v.y};
+  }
+}
+
+__global__ void k_c_to_z(const cx<float>* __restrict__ src, int lds, z* __restrict__ dst, int ldd,
+                         int rows, int cols, const float* __restrict__ ws, double* __restrict__ wd,
+                         int nw) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / cols), c = (int)(t % cols);
+    const cx<float> v = src[(size_t)r * lds + c];
+    dst[(size_t)r * ldd + c] = {(double)v.x, (double)v.y};
+    if (t < (size_t)nw) wd[t] = (double)ws[t];
+  }
+}
+
+// Rayleigh-Ritz of the mixed path's iterations in FP32: its reduced matrices
+// come from FP32 products (~1e-6 relative), so solving them in FP64 buys no
+// accuracy, and GB300 runs FP32 ~60x faster.  The final FP64 Rayleigh-Ritz of
+// the converged Ritz vectors (refine) restores FP64 eigenpairs.  The FP32
+// matrices live in the FP64 work buffers (half their size).
+static int rayleigh_ritz_f32(DvState& S, int n, cudaStream_t st, Prof* pf) {
+  using zf = cx<float>;
+  const int md = S.max_dim, nb = S.nb;
+  zf* H32 = reinterpret_cast<zf*>(S.Zw);
+  zf* L32 = reinterpret_cast<zf*>(S.Lw);
+  zf* A32 = reinterpret_cast<zf*>(S.Aw);
+  zf* X32 = reinterpret_cast<zf*>(S.C);
+  float* e32 = reinterpret_cast<float*>(S.rn);
+  DenseWorkT<float> w;
+  w.tau = reinterpret_cast<zf*>(S.dw.tau);
+  w.p = reinterpret_cast<zf*>(S.dw.p);
+  w.vbuf = reinterpret_cast<zf*>(S.dw.vbuf);
+  w.refl = reinterpret_cast<zf*>(S.dw.refl);
+  w.d = reinterpret_cast<float*>(S.dw.d);
+  w.e = reinterpret_cast<float*>(S.dw.e);
+  w.y = reinterpret_cast<float*>(S.dw.y);
+  w.piv = reinterpret_cast<float*>(S.dw.piv);
+  w.status = S.dw.status;
+  w.bar = S.dw.bar;
+  k_z_to_c<<<grid_for((size_t)n * n), 256, 0, st>>>(S.Hr, md, H32, n, n, n);
+  k_z_to_c<<<grid_for((size_t)n * n), 256, 0, st>>>(S.Sr, md, L32, n, n, n);
+  DV_TRY(check_launch("k_z_to_c"));
+  if (f32::rr_small_fits(n)) {
+    DV_TRY(f32::rr_small(H32, L32, n, n, nb, L32, e32, X32, nb, w, st, pf));
+  } else {
+    {
+      ProfScope ps(pf, "rr_cholesky", st);
+      DV_TRY(f32::cholesky(L32, n, n, 0.f, false, w.piv, w.status, w.bar, w.p, w.vbuf, st));
+    }
+    {
+      ProfScope ps(pf, "rr_reduce", st);
+      DV_TRY(f32::transpose(L32, n, w.refl, n, n, n, st));
+      DV_TRY(f32::trsm_lower_t(w.refl, n, n, H32, n, n, st));
+      DV_TRY(f32::conj_transpose(H32, n, A32, n, n, n, st));
+      DV_TRY(f32::trsm_lower_t(w.refl, n, n, A32, n, n, st));
+      DV_TRY(f32::hermitize(A32, n, n, st));
+      pf->launches += 4;
+    }
+    DV_TRY(f32::heev_lowest(A32, n, n, nb, e32, X32, nb, w, st, pf));
+  }
+  {
+    ProfScope ps(pf, "rr_backsub", st);
+    DV_TRY(f32::trsm_upper_h(L32, n, n, X32, nb, nb, st));
+  }
+  k_c_to_z<<<grid_for((size_t)n * nb), 256, 0, st>>>(X32, nb, S.X, nb, n, nb, e32, S.e, nb);
+  return check_launch("k_c_to_z");
+}
+
 // Rayleigh-Ritz on span(V[0:n]): eigenvalues e[0:nb], X [n][nb] (ld nb).
 // Generalised (S_r = L L^+ by Cholesky, then the standard problem of
 // L^-1 H_r L^-+) in every iteration: the basis is orthonormal only up to the
@@ -360,20 +438,27 @@ static int rayleigh_ritz(DvState& S, int n, bool generalised, cudaStream_t st, P
     DV_TRY(hermitize(S.Aw, n, n, st));
     return heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf);
   }
+  if (rr_small_fits(n)) {
+    // one CTA in shared memory: Cholesky, reduction, tridiagonalisation
+    DV_TRY(rr_small(S.Hr, S.Sr, md, n, nb, S.Lw, S.e, S.X, nb, S.dw, st, pf));
+    ProfScope ps(pf, "rr_backsub", st);
+    return trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st);            // X = L^-+ Y
+  }
   DV_CU(cudaMemcpy2DAsync(S.Lw, n * zb, S.Sr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
   DV_CU(cudaMemcpy2DAsync(S.Zw, n * zb, S.Hr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
   {
     ProfScope ps(pf, "rr_cholesky", st);
-    DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, S.dw.bar, st));
-
+    DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, S.dw.bar, S.dw.p, S.dw.vbuf, st));
   }
   {
+    // L^T in the reflector buffer (free until the eigensolver) for coalesced solves
     ProfScope ps(pf, "rr_reduce", st);
-    DV_TRY(trsm_lower(S.Lw, n, n, S.Zw, n, n, st));               // Z = L^-1 H
+    DV_TRY(transpose(S.Lw, n, S.dw.refl, n, n, n, st));
+    DV_TRY(trsm_lower_t(S.dw.refl, n, n, S.Zw, n, n, st));        // Z = L^-1 H
     DV_TRY(conj_transpose(S.Zw, n, S.Aw, n, n, n, st));           // Z^+ = H L^-+
-    DV_TRY(trsm_lower(S.Lw, n, n, S.Aw, n, n, st));               // A = L^-1 H L^-+
+    DV_TRY(trsm_lower_t(S.dw.refl, n, n, S.Aw, n, n, st));        // A = L^-1 H L^-+
     DV_TRY(hermitize(S.Aw, n, n, st));
-    pf->launches += 3;
+    pf->launches += 4;
   }
   DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf));
   {
@@ -399,7 +484,8 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
     DV_TRY(gram<T>(S, cur, ncur, cur, ncur, S.G, ncur, st, pf));
     DV_TRY(hermitize(S.G, ncur, ncur, st));
     DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
-    DV_TRY(cholesky(S.G, ncur, ncur, drop * drop, true, S.dw.piv, S.dw.status, S.dw.bar, st));
+    DV_TRY(cholesky(S.G, ncur, ncur, drop * drop, true, S.dw.piv, S.dw.status, S.dw.bar, S.dw.p,
+                    S.dw.vbuf, st));
     std::vector<double> piv(ncur);
     DV_CU(cudaMemcpyAsync(piv.data(), S.dw.piv, ncur * sizeof(double), cudaMemcpyDeviceToHost, st));
     DV_CU(cudaStreamSynchronize(st));
@@ -504,7 +590,8 @@ static int dv_step_launch(DvSolve& v, cudaStream_t st, Prof* pf) {
   const int npw = S.npw, nb = S.nb;
   const size_t zb = sizeof(z);
   DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));   // keeps the barrier error word
-  DV_TRY(rayleigh_ritz(S, v.n, true, st, pf));
+  if (sizeof(T) == sizeof(float)) DV_TRY(rayleigh_ritz_f32(S, v.n, st, pf));
+  else DV_TRY(rayleigh_ritz(S, v.n, true, st, pf));
   DV_TRY(outer<T>(S, S.V, npw, S.X, nb, npw, nb, v.n, S.Psi, npw, 0, 0, st, pf));
   DV_TRY(outer<T>(S, S.HV, npw, S.X, nb, npw, nb, v.n, S.HPsi, npw, 0, 0, st, pf));
   if (v.first) {

@@ -1,0 +1,931 @@
+// Implementation of the complex dense linear algebra for one real type R
+// (double: the FP64 kernels; float: the mixed path's reduced problems), included
+// by dense.cu with QE_DENSE_R = double and by dense_f32.cu with float.
+// Matrices are row-major complex (interleaved R), A[i][j] at i*lda + j.
+#include <algorithm>
+#include <cmath>
+
+#include "dense.h"
+#include "plan.h"
+#include "fft_device.cuh"
+
+namespace QE_DENSE_NS {
+
+using namespace ::qe;
+using R = QE_DENSE_R;
+using z = cx<R>;
+
+
+
+static int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+__device__ __forceinline__ z zconj(z a) { return {a.x, -a.y}; }
+__device__ __forceinline__ R zabs2(z a) { return a.x * a.x + a.y * a.y; }
+
+// Block-wide sum (blockDim.x a multiple of 32, <= 1024).  Every thread gets the result.
+__device__ R block_sum(R v, R* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  R t = R(0);
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < nw ? sh[threadIdx.x] : R(0);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// ---- persistent (cooperative) kernels -------------------------------------------
+// Loads of data that other CTAs wrote earlier in the same kernel go through L2
+// (ld.global.cg): L1 is not coherent across SMs.
+__device__ __forceinline__ z ldz(const z* p) {
+  const typename RealT<R>::vec2 v = __ldcg(reinterpret_cast<const typename RealT<R>::vec2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ R ldd(const R* p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned long long gtime_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every wait
+// is bounded (2 s); on time-out the error word is set, every later barrier
+// returns false at once and the kernel leaves.
+__device__ bool grid_sync(const GridBar& b) {
+  __shared__ int s_ok;
+  __syncthreads();
+  // one CTA: the block barrier above already orders its global accesses
+  if (gridDim.x == 1) return true;
+  if (threadIdx.x == 0) {
+    int ok = *(volatile int*)b.err == 0;
+    if (ok) {
+      const unsigned int g = *(volatile unsigned int*)b.gen;
+      __threadfence();
+      const unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
+      if (arrived == gridDim.x) {
+        atomicExch(b.count, 0u);
+        __threadfence();
+        atomicAdd(b.gen, 1u);
+      } else {
+        const unsigned long long t0 = gtime_ns();
+        while (*(volatile unsigned int*)b.gen == g) {
+          if (*(volatile int*)b.err) break;
+          if (gtime_ns() - t0 > 2000000000ull) { atomicExch(b.err, 1); break; }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+      ok = *(volatile int*)b.err == 0;
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Cholesky of the lower triangle, all columns in one launch (one barrier per
+// column).  The pivot column of step j is read from a contiguous copy (c0/c1,
+// n complex each, alternating): the warp that updates row r writes the new
+// A[r][j+1] there for step j+1, so no step reads a column of A with stride lda.
+__global__ void __launch_bounds__(256) k_chol_coop(z* A, int n, int lda, R drop2, int allow_drop,
+                                                   R* piv, int* status, GridBar bar, z* c0,
+                                                   z* c1) {
+  const size_t nthr = (size_t)gridDim.x * blockDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (size_t i = gtid; i < (size_t)n; i += nthr) c0[i] = ldz(&A[i * lda]);
+  if (!grid_sync(bar)) return;
+  for (int j = 0; j < n; ++j) {
+    z* cur = (j & 1) ? c1 : c0;
+    z* nxt = (j & 1) ? c0 : c1;
+    const R d = ldz(&cur[j]).x;
+    const bool keep = allow_drop ? (d > drop2) : (d > R(0));
+    if (gtid == 0) {
+      piv[j] = keep ? sqrt(d) : R(0);
+      if (!keep && !allow_drop) *status = 1 + j;
+    }
+    if (keep) {
+      // lower trailing block, consecutive threads on consecutive columns of a row
+      const R inv = R(1) / d;
+      const int m = n - j - 1;
+      const size_t total = (size_t)m * m;
+      for (size_t t = gtid; t < total; t += nthr) {
+        const int r = j + 1 + (int)(t / m), c = j + 1 + (int)(t % m);
+        if (c > r) continue;
+        const z arj = ldz(&cur[r]), acj = ldz(&cur[c]);
+        z* a = &A[(size_t)r * lda + c];
+        const z av = ldz(a);
+        const z nv = {av.x - (arj.x * acj.x + arj.y * acj.y) * inv,
+                      av.y - (arj.y * acj.x - arj.x * acj.y) * inv};
+        *a = nv;
+        if (c == j + 1) nxt[r] = nv;
+      }
+    } else {
+      // a dropped column changes nothing: the next pivot column as it stands
+      for (size_t r = j + 1 + gtid; r < (size_t)n; r += nthr) nxt[r] = ldz(&A[r * lda + j + 1]);
+    }
+    if (!grid_sync(bar)) return;
+  }
+  const size_t total = (size_t)n * n;
+  for (size_t t = gtid; t < total; t += nthr) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    z& a = A[(size_t)i * lda + j];
+    const R pj = ldd(&piv[j]);
+    if (j > i || pj == R(0)) { a = {R(0), R(0)}; continue; }
+    if (i == j) { a = {pj, R(0)}; continue; }
+    const z av = ldz(&a);
+    a = {av.x / pj, av.y / pj};
+  }
+}
+
+// ---- Cholesky ------------------------------------------------------------------
+static int coop_blocks(const void* f, size_t work_items, size_t smem = 0) {
+  int dev = 0, nsm = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, 256, smem);
+  // one CTA per SM at most: fewer arrivals per grid barrier
+  const int cap = std::max(1, nsm * std::max(1, std::min(occ, 1)));
+  const int want = (int)std::max<size_t>(1, (work_items + 4095) / 4096);
+  return std::min(cap, want);
+}
+
+static int launch_coop(const void* f, int blocks, void** args, cudaStream_t st, const char* what,
+                       size_t smem = 0) {
+  cudaError_t e = cudaLaunchCooperativeKernel(f, dim3(blocks), dim3(256), args, smem, st);
+  if (e != cudaSuccess) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  return QE_OK;
+}
+
+int cholesky(z* A, int n, int lda, R drop2, bool allow_drop, R* piv, int* status,
+             GridBar bar, z* c0, z* c1, cudaStream_t st) {
+  if (n <= 0) return QE_OK;
+  if (cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
+    set_error("cholesky: memset failed");
+    return QE_ECUDA;
+  }
+  int allow = allow_drop ? 1 : 0;
+  void* args[] = {&A, &n, &lda, &drop2, &allow, &piv, &status, &bar, &c0, &c1};
+  const int blocks = coop_blocks((const void*)k_chol_coop, (size_t)n * n / 2);
+  return launch_coop((const void*)k_chol_coop, blocks, args, st, "k_chol_coop");
+}
+
+// ---- triangular solves ---------------------------------------------------------
+constexpr int TCOLS = 4;
+
+// L X = B, L lower with real positive diagonal, given as its transpose LT
+// (LT[i][r] = L[r][i], so that column i of L is a contiguous row); B [n][ldb],
+// columns c0.. of this CTA.
+__global__ void __launch_bounds__(256) k_trsm_lower_t(const z* LT, int n, int ldt, z* B, int ldb,
+                                                      int ncols) {
+  const int c0 = blockIdx.x * TCOLS;
+  const int nc = min(TCOLS, ncols - c0);
+  for (int i = 0; i < n; ++i) {
+    const z* lcol = LT + (size_t)i * ldt;
+    if (threadIdx.x < nc) {
+      const R inv = R(1) / lcol[i].x;
+      z& b = B[(size_t)i * ldb + c0 + threadIdx.x];
+      b = {b.x * inv, b.y * inv};
+    }
+    __syncthreads();
+    const int rows = n - i - 1;
+    for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
+      const int r = i + 1 + t / nc, c = c0 + t % nc;
+      const z l = lcol[r], x = B[(size_t)i * ldb + c];
+      z& b = B[(size_t)r * ldb + c];
+      b.x -= l.x * x.x - l.y * x.y;
+      b.y -= l.x * x.y + l.y * x.x;
+    }
+    __syncthreads();
+  }
+}
+
+// L^+ X = B (back substitution with the conjugate transpose of lower L).
+__global__ void __launch_bounds__(256) k_trsm_upper_h(const z* L, int n, int ldl, z* B, int ldb,
+                                                      int ncols) {
+  const int c0 = blockIdx.x * TCOLS;
+  const int nc = min(TCOLS, ncols - c0);
+  for (int i = n - 1; i >= 0; --i) {
+    if (threadIdx.x < nc) {
+      const R inv = R(1) / L[(size_t)i * ldl + i].x;
+      z& b = B[(size_t)i * ldb + c0 + threadIdx.x];
+      b = {b.x * inv, b.y * inv};
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < i * nc; t += blockDim.x) {
+      const int r = t / nc, c = c0 + t % nc;
+      // (L^+)[r][i] = conj(L[i][r])
+      const z l = L[(size_t)i * ldl + r], x = B[(size_t)i * ldb + c];
+      z& b = B[(size_t)r * ldb + c];
+      b.x -= l.x * x.x + l.y * x.y;
+      b.y -= l.x * x.y - l.y * x.x;
+    }
+    __syncthreads();
+  }
+}
+
+int trsm_lower_t(const z* LT, int n, int ldt, z* B, int ldb, int ncols, cudaStream_t st) {
+  if (n <= 0 || ncols <= 0) return QE_OK;
+  k_trsm_lower_t<<<(ncols + TCOLS - 1) / TCOLS, 256, 0, st>>>(LT, n, ldt, B, ldb, ncols);
+  return check_launch("k_trsm_lower_t");
+}
+
+int trsm_upper_h(const z* L, int n, int ldl, z* B, int ldb, int ncols, cudaStream_t st) {
+  if (n <= 0 || ncols <= 0) return QE_OK;
+  k_trsm_upper_h<<<(ncols + TCOLS - 1) / TCOLS, 256, 0, st>>>(L, n, ldl, B, ldb, ncols);
+  return check_launch("k_trsm_upper_h");
+}
+
+// ---- element-wise helpers ------------------------------------------------------
+// dst[i][j] = src[j][i]
+__global__ void k_transpose(const z* src, int lds, z* dst, int ldd, int rows, int cols) {
+  __shared__ z tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = r0 + r, j = c0 + threadIdx.x;
+    if (i < rows && j < cols) tile[r][threadIdx.x] = src[(size_t)i * lds + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = c0 + r, i = r0 + threadIdx.x;
+    if (i < rows && j < cols) dst[(size_t)j * ldd + i] = tile[threadIdx.x][r];
+  }
+}
+
+int transpose(const z* src, int lds, z* dst, int ldd, int rows, int cols, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return QE_OK;
+  dim3 g((cols + 31) / 32, (rows + 31) / 32);
+  k_transpose<<<g, dim3(32, 8), 0, st>>>(src, lds, dst, ldd, rows, cols);
+  return check_launch("k_transpose");
+}
+
+// dst[i][j] = conj(src[j][i])
+__global__ void k_conj_transpose(const z* src, int lds, z* dst, int ldd, int rows, int cols) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / cols), j = (int)(t % cols);   // dst row i, col j
+    dst[(size_t)i * ldd + j] = zconj(src[(size_t)j * lds + i]);
+  }
+}
+
+// A = (A + A^+) / 2 in place
+__global__ void k_hermitize(z* A, int n, int lda) {
+  const size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (j < i) continue;
+    const z a = A[(size_t)i * lda + j], b = A[(size_t)j * lda + i];
+    const z m = {R(0.5) * (a.x + b.x), R(0.5) * (a.y - b.y)};
+    A[(size_t)i * lda + j] = m;
+    A[(size_t)j * lda + i] = zconj(m);
+  }
+}
+
+int conj_transpose(const z* src, int lds, z* dst, int ldd, int rows, int cols, cudaStream_t st) {
+  const size_t total = (size_t)rows * cols;
+  if (!total) return QE_OK;
+  k_conj_transpose<<<(int)std::min<size_t>((total + 255) / 256, 152 * 8), 256, 0, st>>>(src, lds, dst, ldd, rows, cols);
+  return check_launch("k_conj_transpose");
+}
+
+int hermitize(z* A, int n, int lda, cudaStream_t st) {
+  const size_t total = (size_t)n * n;
+  if (!total) return QE_OK;
+  k_hermitize<<<(int)std::min<size_t>((total + 255) / 256, 152 * 8), 256, 0, st>>>(A, n, lda);
+  return check_launch("k_hermitize");
+}
+
+// ---- Householder reflectors ----------------------------------------------------------
+// Step j: H = I - tau v v^+, v_0 = 1, H^+ x = beta e_1 with beta real, where x is
+// column j below the diagonal; v_1.. are stored in A[j+2 ..][j] and, for the
+// back-transformation, in row j of refl; A[j+1][j] = beta.
+// Reflector of step j from the updated column j (rows j+1 ..), computed by one
+// CTA: v_1.. to A[j+2 ..][j] and vbuf[1 ..], beta to A[j+1][j] and e[j], tau[j].
+__device__ void house_step(z* A, int n, int lda, int j, z* tau, R* e, z* vbuf, z* refl,
+                           R* sh) {
+  const int m = n - j - 1;
+  const z alpha = ldz(&A[(size_t)(j + 1) * lda + j]);
+  R s = R(0);
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += zabs2(ldz(&A[(size_t)(j + 1 + i) * lda + j]));
+  const R sigma = block_sum(s, sh);
+  if (sigma == R(0) && alpha.y == R(0)) {
+    if (threadIdx.x == 0) { tau[j] = {R(0), R(0)}; e[j] = alpha.x; }
+    return;
+  }
+  const R nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sigma);
+  const R beta = alpha.x >= R(0) ? -nu : nu;
+  const z am = {alpha.x - beta, alpha.y};
+  const R den = am.x * am.x + am.y * am.y;
+  const z sc = {am.x / den, -am.y / den};
+  z* rrow = refl + (size_t)j * n + (j + 1);
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
+    z* x = &A[(size_t)(j + 1 + i) * lda + j];
+    const z v = cmul(ldz(x), sc);
+    *x = v;
+    vbuf[i] = v;
+    rrow[i] = v;
+  }
+  if (threadIdx.x == 0) {
+    tau[j] = {(beta - alpha.x) / beta, -alpha.y / beta};
+    e[j] = beta;
+    A[(size_t)(j + 1) * lda + j] = {beta, R(0)};
+    vbuf[0] = {R(1), R(0)};
+    rrow[0] = {R(1), R(0)};
+  }
+}
+
+// Householder tridiagonalisation, all steps in one launch, two barriers per
+// step: (matvec p = tau A v) | (rank-2 update A -= v w^+ + w v^+, and, in CTA 0,
+// the update of the next column followed by the next reflector).  The
+// reflector is also kept contiguous in vbuf; every CTA stages v and w of the
+// step in shared memory, so the two phases stream only the trailing block of A.
+// Dynamic shared memory: 2 n complex.
+__global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* tau, R* e, z* p,
+                                                      R* dg, z* vbuf, z* refl, GridBar bar) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  z* sv = reinterpret_cast<z*>(smem_raw);
+  z* sw = sv + n;
+  __shared__ R sh[33];
+  const size_t nthr = (size_t)gridDim.x * blockDim.x;
+  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nwarp = (int)(nthr >> 5), gwarp = (int)(gtid >> 5), lane = threadIdx.x & 31;
+  if (n >= 2 && blockIdx.x == 0) house_step(A, n, lda, 0, tau, e, vbuf, refl, sh);
+  if (!grid_sync(bar)) return;
+  for (int j = 0; j < n - 1; ++j) {
+    const int m = n - j - 1;
+    const z t = ldz(&tau[j]);
+    const bool active = t.x != R(0) || t.y != R(0);
+    if (active) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = ldz(&vbuf[i]);
+      __syncthreads();
+      // p = tau A v over the trailing block (one warp per row; four loads in
+      // flight per lane: the row is read from L2, latency-bound otherwise)
+      for (int w = gwarp; w < m; w += nwarp) {
+        const z* row = A + (size_t)(j + 1 + w) * lda + (j + 1);
+        z acc = {R(0), R(0)}, acc1 = {R(0), R(0)};
+        int c = lane;
+        for (; c + 96 < m; c += 128) {
+          const z a0 = ldz(row + c), a1 = ldz(row + c + 32), a2 = ldz(row + c + 64), a3 = ldz(row + c + 96);
+          acc = cadd(acc, cmul(a0, sv[c]));
+          acc1 = cadd(acc1, cmul(a1, sv[c + 32]));
+          acc = cadd(acc, cmul(a2, sv[c + 64]));
+          acc1 = cadd(acc1, cmul(a3, sv[c + 96]));
+        }
+        for (; c < m; c += 32) acc = cadd(acc, cmul(ldz(row + c), sv[c]));
+        acc = cadd(acc, acc1);
+        for (int o = 16; o > 0; o >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) p[j + 1 + w] = cmul(t, acc);
+      }
+    }
+    if (!grid_sync(bar)) return;
+    if (active) {
+      // w = p - (1/2) conj(tau) (v^+ p) v
+      R sr = R(0), si = R(0);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const z v = sv[i], pr = ldz(&p[j + 1 + i]);
+        sw[i] = pr;
+        sr += v.x * pr.x + v.y * pr.y;
+        si += v.x * pr.y - v.y * pr.x;
+      }
+      const R vpr = block_sum(sr, sh);
+      const R vpi = block_sum(si, sh);
+      const z coef = {R(0.5) * (t.x * vpr + t.y * vpi), R(0.5) * (t.x * vpi - t.y * vpr)};
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = csub(sw[i], cmul(coef, sv[i]));
+      __syncthreads();
+      // all columns but the first of the trailing block, one warp per row, by the
+      // CTAs other than 0 (CTA 0 meanwhile updates that first column and builds
+      // the next reflector, the critical path of the step)
+      if (m > 1 && (gridDim.x == 1 || blockIdx.x > 0)) {
+        const int wpb = (int)(blockDim.x >> 5);
+        const int bw = gridDim.x == 1 ? gwarp : gwarp - wpb;
+        const int nbw = gridDim.x == 1 ? nwarp : nwarp - wpb;
+        for (int r = bw; r < m; r += nbw) {
+          const z vr = sv[r], wr = sw[r];
+          z* arow = A + (size_t)(j + 1 + r) * lda + (j + 1);
+          int c = 1 + lane;
+          for (; c + 32 < m; c += 64) {
+            const z a0 = ldz(arow + c), a1 = ldz(arow + c + 32);
+            const z d0 = cadd(cmul(vr, zconj(sw[c])), cmul(wr, zconj(sv[c])));
+            const z d1 = cadd(cmul(vr, zconj(sw[c + 32])), cmul(wr, zconj(sv[c + 32])));
+            arow[c] = csub(a0, d0);
+            arow[c + 32] = csub(a1, d1);
+          }
+          for (; c < m; c += 32) {
+            const z dlt = cadd(cmul(vr, zconj(sw[c])), cmul(wr, zconj(sv[c])));
+            arow[c] = csub(ldz(arow + c), dlt);
+          }
+        }
+      }
+    }
+    if (blockIdx.x == 0 && j + 1 < n - 1) {
+      if (active) {
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+          const z dlt = cadd(cmul(sv[r], zconj(sw[0])), cmul(sw[r], zconj(sv[0])));
+          z* a = &A[(size_t)(j + 1 + r) * lda + (j + 1)];
+          *a = csub(ldz(a), dlt);
+        }
+        __syncthreads();
+      }
+      house_step(A, n, lda, j + 1, tau, e, vbuf, refl, sh);
+    } else if (blockIdx.x == 0 && active) {
+      // last step: only the 1 x 1 trailing element remains
+      for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        const z dlt = cadd(cmul(sv[r], zconj(sw[0])), cmul(sw[r], zconj(sv[0])));
+        z* a = &A[(size_t)(j + 1 + r) * lda + (j + 1)];
+        *a = csub(ldz(a), dlt);
+      }
+    }
+    if (!grid_sync(bar)) return;
+  }
+  for (size_t i = gtid; i < (size_t)n; i += nthr) dg[i] = ldz(&A[i * lda + i]).x;
+}
+
+// ---- tridiagonal eigenvalues: Sturm bisection, one thread per eigenvalue --------
+__device__ int sturm_count(const R* d, const R* e, int n, R x, R tiny) {
+  int cnt = 0;
+  R q = d[0] - x;
+  if (q == R(0)) q = -tiny;
+  if (q < R(0)) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (q == R(0)) q = -tiny;
+    if (q < R(0)) ++cnt;
+  }
+  return cnt;
+}
+
+// One warp per eigenvalue: multisection.  Each round the 32 lanes evaluate the
+// Sturm count at 32 interior points of the current bracket and the bracket
+// shrinks to the sub-interval holding the (k+1)-th eigenvalue (a factor 33 per
+// round instead of 2 for bisection).
+__global__ void __launch_bounds__(64) k_bisect(const R* d, const R* e, int n, int nev,
+                                                R* w) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k >= nev) return;
+  R lo = R(0), hi = R(0);
+  {
+    R l = 1e300, h = -1e300;
+    for (int i = lane; i < n; i += 32) {
+      const R r = (i > 0 ? fabs(e[i - 1]) : R(0)) + (i < n - 1 ? fabs(e[i]) : R(0));
+      l = fmin(l, d[i] - r);
+      h = fmax(h, d[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
+      h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+    }
+    lo = l;
+    hi = h;
+  }
+  const R nrm = fmax(fabs(lo), fabs(hi));
+  const R tiny = RealT<R>::tiny + RealT<R>::tiny_rel * nrm;
+  lo -= RealT<R>::margin * nrm + RealT<R>::tiny;
+  hi += RealT<R>::margin * nrm + RealT<R>::tiny;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= RealT<R>::eps * fmax(fabs(lo), fabs(hi))) break;
+    const R step = (hi - lo) / R(33);
+    const R x = lo + step * (lane + 1);
+    const int c = (x > lo && x < hi) ? sturm_count(d, e, n, x, tiny) : (x <= lo ? 0 : n);
+    // lanes whose point has more than k eigenvalues below it bound from above
+    const unsigned above = __ballot_sync(0xffffffffu, c > k);
+    const int first = above ? __ffs(above) - 1 : 32;    // first lane with count > k
+    const R nlo = first == 0 ? lo : lo + step * first;
+    const R nhi = first == 32 ? hi : lo + step * (first + 1);
+    if (!(nhi < hi || nlo > lo)) break;                 // no progress at this resolution
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) w[k] = R(0.5) * (lo + hi);
+}
+
+// ---- tridiagonal eigenvectors: inverse iteration --------------------------------------
+// splitmix64 (Steele, Lea, Flood 2014) for deterministic start vectors
+__device__ __forceinline__ double start_component(unsigned long long k, unsigned long long i) {
+  unsigned long long x = k * 0x9E3779B97F4A7C15ull + i * 0xD1B54A32D192ED03ull + 0x632BE59BD9B4E019ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return ((double)(x >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+// One CTA per cluster of consecutive eigenvalues closer than ctol; the CTA whose
+// index starts a cluster handles all of it, the others return.  Vectors are rows
+// Y[k][0..n).  Shared memory: 6 arrays of n doubles (+ ints) for the factorisation.
+__global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, int nev,
+                                                 const R* w, R ctol_rel, R* Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* u0 = reinterpret_cast<R*>(smem_raw);
+  R* u1 = u0 + n;
+  R* u2 = u1 + n;
+  R* ml = u2 + n;
+  R* y = ml + n;
+  int* sw = reinterpret_cast<int*>(y + n);
+  __shared__ R sh[33];
+  const int k0 = blockIdx.x;
+  if (k0 >= nev) return;
+  R nrm = R(0);
+  for (int i = 0; i < n; ++i)
+    nrm = fmax(nrm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : R(0)) + (i < n - 1 ? fabs(e[i]) : R(0)));
+  const R ctol = ctol_rel * fmax(nrm, RealT<R>::tiny);
+  if (k0 > 0 && w[k0] - w[k0 - 1] <= ctol) return;   // not a cluster start
+  int k1 = k0 + 1;
+  while (k1 < nev && w[k1] - w[k1 - 1] <= ctol) ++k1;
+  const R tiny = fmax(RealT<R>::eps * nrm, RealT<R>::tiny);
+  for (int k = k0; k < k1; ++k) {
+    const R lam = w[k];
+    // LU with partial pivoting of T - lam I (thread 0)
+    if (threadIdx.x == 0) {
+      R c0 = d[0] - lam, c1 = n > 1 ? e[0] : R(0), c2 = R(0);
+      for (int i = 0; i < n - 1; ++i) {
+        R n0 = e[i], n1 = d[i + 1] - lam, n2 = (i + 2 < n) ? e[i + 1] : R(0);
+        int s = 0;
+        if (fabs(n0) > fabs(c0)) {
+          R t;
+          t = c0; c0 = n0; n0 = t;
+          t = c1; c1 = n1; n1 = t;
+          t = c2; c2 = n2; n2 = t;
+          s = 1;
+        }
+        if (fabs(c0) < tiny) c0 = c0 < R(0) ? -tiny : tiny;
+        const R mlt = n0 / c0;
+        u0[i] = c0; u1[i] = c1; u2[i] = c2; ml[i] = mlt; sw[i] = s;
+        c0 = n1 - mlt * c1;
+        c1 = n2 - mlt * c2;
+        c2 = R(0);
+      }
+      if (fabs(c0) < tiny) c0 = c0 < R(0) ? -tiny : tiny;
+      u0[n - 1] = c0; u1[n - 1] = R(0); u2[n - 1] = R(0);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = start_component(k, i);
+    __syncthreads();
+    for (int it = 0; it < 4; ++it) {
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < n - 1; ++i) {
+          if (sw[i]) { const R t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
+          y[i + 1] -= ml[i] * y[i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+          R s = y[i];
+          if (i + 1 < n) s -= u1[i] * y[i + 1];
+          if (i + 2 < n) s -= u2[i] * y[i + 2];
+          y[i] = s / u0[i];
+        }
+      }
+      __syncthreads();
+      // scale down first (the solve grows the vector by up to 1/tiny)
+      R mx = R(0);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fabs(y[i]));
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        R m2 = R(0);
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m2 = fmax(m2, sh[q]);
+        sh[32] = m2 > R(0) ? m2 : R(1);
+      }
+      __syncthreads();
+      const R inv_mx = R(1) / sh[32];
+      for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] *= inv_mx;
+      __syncthreads();
+      // orthogonalise against the finished vectors of this cluster (twice)
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int q = k0; q < k; ++q) {
+          const R* yq = Y + (size_t)q * n;
+          R s = R(0);
+          for (int i = threadIdx.x; i < n; i += blockDim.x) s += yq[i] * y[i];
+          s = block_sum(s, sh);
+          for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] -= s * yq[i];
+          __syncthreads();
+        }
+      }
+      R s = R(0);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s += y[i] * y[i];
+      s = block_sum(s, sh);
+      const R inv = s > R(0) ? R(1) / sqrt(s) : R(0);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] *= inv;
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Y[(size_t)k * n + i] = y[i];
+    __syncthreads();
+  }
+}
+
+// X[:, k] = H_0 H_1 ... H_{n-2} y_k, one CTA per eigenvector; X [n][ldx].  The
+// reflectors are read from their rows in refl (contiguous, coalesced).
+__global__ void __launch_bounds__(256) k_backtransform(const z* __restrict__ refl, int n,
+                                                       const z* tau, const R* Y, z* X, int ldx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  z* x = reinterpret_cast<z*>(smem_raw);
+  __shared__ R sh[33];
+  const int k = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = {Y[(size_t)k * n + i], R(0)};
+  __syncthreads();
+  for (int j = n - 2; j >= 0; --j) {
+    const z t = tau[j];
+    if (t.x == R(0) && t.y == R(0)) continue;
+    const z* v = refl + (size_t)j * n;
+    R sr = R(0), si = R(0);
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
+      const z vr = v[r], xr = x[r];
+      sr += vr.x * xr.x + vr.y * xr.y;
+      si += vr.x * xr.y - vr.y * xr.x;
+    }
+    const R a = block_sum(sr, sh);
+    const R b = block_sum(si, sh);
+    const z f = cmul(t, z{a, b});     // tau (v^+ x)
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) x[r] = csub(x[r], cmul(f, v[r]));
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)i * ldx + k] = x[i];
+}
+
+// Eigenvalues and eigenvectors of the tridiagonal T (wk.d, wk.e) and the
+// back-transformation through the reflectors (wk.tau, wk.refl) into X.
+static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, cudaStream_t st,
+                       Prof* pf) {
+  int rc = QE_OK;
+  {
+    ProfScope ps(pf, "heev_bisect", st);
+    // two warps per block: the Sturm counts are FP64-bound, so spread them over the SMs
+    k_bisect<<<(nev * 32 + 63) / 64, 64, 0, st>>>(wk.d, wk.e, n, nev, w);
+  }
+  rc = check_launch("k_bisect");
+  if (rc) return rc;
+  const size_t ism = (size_t)n * (5 * sizeof(R) + sizeof(int));
+  // same (largest) cap for every caller: the attribute is shared process-wide
+  set_max_dynamic_smem(k_inviter);
+  set_max_dynamic_smem(k_backtransform);
+  // eigenvalues within 1e-10 of each other (relative to the spread of T) share a cluster
+  {
+    ProfScope ps(pf, "heev_inviter", st);
+    k_inviter<<<nev, 256, ism, st>>>(wk.d, wk.e, n, nev, w, wk.ctol_rel, wk.y);
+  }
+  rc = check_launch("k_inviter");
+  if (rc) return rc;
+  const size_t bsm = (size_t)n * sizeof(z);
+  {
+    ProfScope ps(pf, "heev_backtransform", st);
+    k_backtransform<<<nev, 256, bsm, st>>>(wk.refl, n, wk.tau, wk.y, X, ldx);
+  }
+  return check_launch("k_backtransform");
+}
+
+int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk,
+                cudaStream_t st, Prof* pf) {
+  if (n <= 0 || nev <= 0) return QE_OK;
+  if (nev > n || n > kMaxDense) {
+    set_error("heev_lowest: n = %d, nev = %d (max n %d)", n, nev, kMaxDense);
+    return QE_EINVAL;
+  }
+  if (cudaMemsetAsync(wk.bar.count, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
+    set_error("heev_lowest: memset failed");
+    return QE_ECUDA;
+  }
+  {
+    GridBar bar = wk.bar;
+    void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.p, &wk.d, &wk.vbuf, &wk.refl, &bar};
+    const size_t tsm = 2 * (size_t)n * sizeof(z);
+    set_max_dynamic_smem(k_tridiag_coop);
+    // all SMs once the trailing block is large: the FP64 work is spread
+    const int blocks = coop_blocks((const void*)k_tridiag_coop, (size_t)n * n * 4, tsm);
+    ProfScope ps(pf, "heev_tridiag", st);
+    int rc0 = launch_coop((const void*)k_tridiag_coop, blocks, args, st, "k_tridiag_coop", tsm);
+    if (rc0) return rc0;
+  }
+  return heev_finish(n, nev, w, X, ldx, wk, st, pf);
+}
+
+// ---- small generalised problems in one CTA ---------------------------------------------
+// For n <= kSmallDense the whole reduction runs in one CTA on a shared-memory
+// copy of the matrix: the multi-CTA kernels above spend ~15 us per column on
+// L2 round trips and barriers even with one CTA, while one SM's FP64 rate
+// (1/152 of the GPU) is still enough for n^3 work at this size.
+//   S = L L^+ (L -> Lg, lower, upper zeroed; status = 1 + column on a
+//   non-positive pivot), A = L^-1 H L^-+, A = Q T Q^+ (T -> d, e; Q as
+//   reflectors -> tau, refl rows, as k_tridiag_coop).
+__device__ __forceinline__ R warp_sum(R v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(512) k_rr_small(const z* __restrict__ H, const z* __restrict__ S,
+                                                  int ld, int n, z* Lg, R* dgl, R* egl,
+                                                  z* taug, z* refl, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  z* A = reinterpret_cast<z*>(smem_raw);          // n x n: H, then the reduced matrix
+  z* L = A + (size_t)n * n;                        // n x n: S, then its Cholesky factor
+  z* sv = L + (size_t)n * n;                       // n
+  z* sw = sv + n;                                  // n
+  R* piv = reinterpret_cast<R*>(sw + n); // n
+  __shared__ R sred[4];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  if (tid == 0) s_fail = 0;
+  // 1. Cholesky of S in place (right-looking, lower triangle)
+  for (int t = tid; t < n * n; t += nt) {
+    L[t] = S[(size_t)(t / n) * ld + t % n];
+    A[t] = H[(size_t)(t / n) * ld + t % n];
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const R dj = L[(size_t)j * n + j].x;
+    if (!(dj > R(0))) {
+      if (tid == 0) { s_fail = 1; *status = 1 + j; }
+      break;
+    }
+    if (tid == 0) piv[j] = sqrt(dj);
+    const R inv = R(1) / dj;
+    const int m = n - j - 1;
+    for (int t = tid; t < m * m; t += nt) {
+      const int r = j + 1 + t / m, c = j + 1 + t % m;
+      if (c > r) continue;
+      const z arj = L[(size_t)r * n + j], acj = L[(size_t)c * n + j];
+      z& a = L[(size_t)r * n + c];
+      a = {a.x - (arj.x * acj.x + arj.y * acj.y) * inv, a.y - (arj.y * acj.x - arj.x * acj.y) * inv};
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (s_fail) {
+    for (int i = tid; i < n; i += nt) { dgl[i] = R(0); egl[i] = R(0); taug[i] = {R(0), R(0)}; }
+    return;
+  }
+  for (int t = tid; t < n * n; t += nt) {
+    const int r = t / n, c = t % n;
+    const z a = L[t];
+    const z l = c > r ? z{R(0), R(0)} : (c == r ? z{piv[c], R(0)} : z{a.x / piv[c], a.y / piv[c]});
+    L[t] = l;
+    Lg[t] = l;
+  }
+  __syncthreads();
+  // 2. A = L^-1 H L^-+: two forward substitutions (rows in order, columns in parallel)
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i < n; ++i) {
+      const z* li = L + (size_t)i * n;
+      const R inv = R(1) / li[i].x;
+      for (int c = tid; c < n; c += nt) {
+        z acc = A[(size_t)i * n + c];
+        for (int k = 0; k < i; ++k) {
+          const z l = li[k], x = A[(size_t)k * n + c];
+          acc.x -= l.x * x.x - l.y * x.y;
+          acc.y -= l.x * x.y + l.y * x.x;
+        }
+        A[(size_t)i * n + c] = {acc.x * inv, acc.y * inv};
+      }
+      __syncthreads();
+    }
+    if (pass == 0) {
+      // A <- A^+ (then the second substitution gives L^-1 (L^-1 H)^+ = L^-1 H L^-+)
+      for (int t = tid; t < n * n; t += nt) {
+        const int r = t / n, c = t % n;
+        if (c < r) continue;
+        const z a = A[t], b = A[(size_t)c * n + r];
+        A[t] = {b.x, -b.y};
+        A[(size_t)c * n + r] = {a.x, -a.y};
+      }
+      __syncthreads();
+    }
+  }
+  // Hermitian part
+  for (int t = tid; t < n * n; t += nt) {
+    const int r = t / n, c = t % n;
+    if (c < r) continue;
+    const z a = A[t], b = A[(size_t)c * n + r];
+    const z h = {R(0.5) * (a.x + b.x), R(0.5) * (a.y - b.y)};
+    A[t] = h;
+    A[(size_t)c * n + r] = {h.x, -h.y};
+  }
+  __syncthreads();
+  // 3. Householder tridiagonalisation in place
+  for (int j = 0; j < n - 1; ++j) {
+    const int m = n - j - 1;
+    // reflector of column j (warp 0)
+    if (warp == 0) {
+      const z alpha = A[(size_t)(j + 1) * n + j];
+      R sg = R(0);
+      for (int i = 1 + lane; i < m; i += 32) {
+        const z x = A[(size_t)(j + 1 + i) * n + j];
+        sg += x.x * x.x + x.y * x.y;
+      }
+      sg = warp_sum(sg);
+      if (sg == R(0) && alpha.y == R(0)) {
+        if (lane == 0) { taug[j] = {R(0), R(0)}; egl[j] = alpha.x; sred[0] = R(0); sred[1] = R(0); }
+      } else {
+        const R nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sg);
+        const R beta = alpha.x >= R(0) ? -nu : nu;
+        const z am = {alpha.x - beta, alpha.y};
+        const R den = am.x * am.x + am.y * am.y;
+        const z sc = {am.x / den, -am.y / den};
+        z* rrow = refl + (size_t)j * n + (j + 1);
+        for (int i = 1 + lane; i < m; i += 32) {
+          z* x = &A[(size_t)(j + 1 + i) * n + j];
+          const z v = cmul(*x, sc);
+          *x = v;
+          sv[i] = v;
+          rrow[i] = v;
+        }
+        if (lane == 0) {
+          const z t = {(beta - alpha.x) / beta, -alpha.y / beta};
+          taug[j] = t;
+          egl[j] = beta;
+          A[(size_t)(j + 1) * n + j] = {beta, R(0)};
+          sv[0] = {R(1), R(0)};
+          rrow[0] = {R(1), R(0)};
+          sred[0] = t.x;
+          sred[1] = t.y;
+        }
+      }
+    }
+    __syncthreads();
+    const z t = {sred[0], sred[1]};
+    if (t.x == R(0) && t.y == R(0)) {   // uniform: every thread read the same
+      __syncthreads();                // before warp 0 writes the next reflector's tau
+      continue;
+    }
+    // p = tau A_trail v (one warp per row)
+    for (int r = warp; r < m; r += nwarps) {
+      const z* row = A + (size_t)(j + 1 + r) * n + (j + 1);
+      R ax = R(0), ay = R(0);
+      for (int c = lane; c < m; c += 32) {
+        const z a = row[c], v = sv[c];
+        ax += a.x * v.x - a.y * v.y;
+        ay += a.x * v.y + a.y * v.x;
+      }
+      ax = warp_sum(ax);
+      ay = warp_sum(ay);
+      if (lane == 0) sw[r] = cmul(t, z{ax, ay});
+    }
+    __syncthreads();
+    // w = p - (1/2) conj(tau) (v^+ p) v
+    if (warp == 0) {
+      R sr = R(0), si = R(0);
+      for (int i = lane; i < m; i += 32) {
+        const z v = sv[i], pr = sw[i];
+        sr += v.x * pr.x + v.y * pr.y;
+        si += v.x * pr.y - v.y * pr.x;
+      }
+      sr = warp_sum(sr);
+      si = warp_sum(si);
+      if (lane == 0) { sred[2] = R(0.5) * (t.x * sr + t.y * si); sred[3] = R(0.5) * (t.x * si - t.y * sr); }
+    }
+    __syncthreads();
+    const z coef = {sred[2], sred[3]};
+    for (int i = tid; i < m; i += nt) sw[i] = csub(sw[i], cmul(coef, sv[i]));
+    __syncthreads();
+    // A_trail -= v w^+ + w v^+
+    for (int q = tid; q < m * m; q += nt) {
+      const int r = q / m, c = q % m;
+      const z dlt = cadd(cmul(sv[r], zconj(sw[c])), cmul(sw[r], zconj(sv[c])));
+      z& a = A[(size_t)(j + 1 + r) * n + (j + 1 + c)];
+      a = csub(a, dlt);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) dgl[i] = A[(size_t)i * n + i].x;
+}
+
+int rr_small_fits(int n) { return n > 0 && n <= kSmallDense; }
+
+int rr_small(const z* H, const z* S, int ld, int n, int nev, z* L, R* w, z* X, int ldx,
+             DenseWorkT<R>& wk, cudaStream_t st, Prof* pf) {
+  if (!rr_small_fits(n) || nev <= 0 || nev > n) {
+    set_error("rr_small: n = %d, nev = %d", n, nev);
+    return QE_EINVAL;
+  }
+  const size_t smem = 2 * (size_t)n * n * sizeof(z) + 2 * (size_t)n * sizeof(z) + (size_t)n * sizeof(R);
+  set_max_dynamic_smem(k_rr_small);
+  {
+    ProfScope ps(pf, "rr_small", st);
+    k_rr_small<<<1, 512, smem, st>>>(H, S, ld, n, L, wk.d, wk.e, wk.tau, wk.refl, wk.status);
+  }
+  const int rc = check_launch("k_rr_small");
+  if (rc) return rc;
+  return heev_finish(n, nev, w, X, ldx, wk, st, pf);
+}
+
+
+}  // namespace QE_DENSE_NS
