@@ -186,7 +186,22 @@ struct DvState {
   // FP64 subspace products on the tensor cores: operand slices + partials
   void* oz = nullptr;
   size_t oz_bytes = 0;
+  // the mixed path's subspace products on the tensor cores (TF32 x3)
+  void* tc = nullptr;
+  size_t tc_bytes = 0;
 };
+
+// Scratch of the mixed path's tensor-core subspace products (largest inner and
+// outer product of a solve).
+static size_t dv_tc_bytes(size_t npw, size_t nb, size_t md, bool fp64) {
+  if (fp64) return 0;
+  return std::max(tc_inner_bytes((int)md, (int)nb, (int)npw), tc_outer_bytes((int)npw, (int)nb, (int)md)) +
+         256;
+}
+
+// Products below ~4 M complex multiply-adds stay on the SIMT kernels (the
+// tensor-core path's packing launches cost more there).
+static bool tc_worth(long long M, long long N, long long K) { return M > 0 && N > 0 && M * N * K >= (1ll << 22); }
 
 // Scratch of the FP64 tensor-core subspace products: the largest inner product
 // (basis x new block over the plane waves) and outer product (rotation of the
@@ -296,11 +311,14 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
   // split-K partials: at most (splits for ~4 CTAs/SM + tiles) 32x32 tiles of FP64 complex
   const size_t sb = dv_red_bytes(md);
   const size_t ob = dv_oz_bytes(npw, nb, md, fp64);
-  DV_TRY(red.ensure(sb + ob));
+  const size_t tb = dv_tc_bytes(npw, nb, md, fp64);
+  DV_TRY(red.ensure(sb + ob + tb));
   S.part = red.p;
   S.part_bytes = sb;
   S.oz = ob ? static_cast<char*>(red.p) + sb : nullptr;
   S.oz_bytes = ob;
+  S.tc = tb ? static_cast<char*>(red.p) + sb + ob : nullptr;
+  S.tc_bytes = tb;
   return QE_OK;
 }
 
@@ -311,6 +329,9 @@ static int* dv_tc_status(const DvState& S) { return S.dw.status + 12; }
 template <typename T>
 static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
                 cudaStream_t st, Prof* pf) {
+  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(m, n, S.npw))
+    return tc_inner((const double*)A, (const double*)B, m, n, S.npw, (double*)C, ldc, S.tc,
+                    S.tc_bytes, dv_tc_status(S), st, pf);
   if (sizeof(T) == sizeof(double) && S.oz && oz_worth(m, n, S.npw))
     return oz_inner((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C, ldc,
                     S.oz, S.oz_bytes, dv_tc_status(S), st, pf);
@@ -322,6 +343,9 @@ static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, in
 template <typename T>
 static int outer(const DvState& S, const z* A, int lda, const z* B, int ldb, int M, int N, int K,
                  z* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf) {
+  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(M, N, K) && lda == M && ldb == N)
+    return tc_outer((const double*)A, (const double*)B, M, N, K, (double*)C, ldc, alpha_neg, beta,
+                    S.tc, S.tc_bytes, dv_tc_status(S), st, pf);
   if (sizeof(T) == sizeof(double) && S.oz && oz_worth(M, N, K))
     return oz_outer((const double*)A, lda, (const double*)B, ldb, M, N, K, (double*)C, ldc,
                     alpha_neg, beta, S.oz, S.oz_bytes, dv_tc_status(S), st, pf);

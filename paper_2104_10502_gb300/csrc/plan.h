@@ -162,6 +162,18 @@ int gemm_outer_ab(const double* A, int lda, const double* B, int ldb, int M, int
 int tc_gemm_tf32x3(const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int Mp,
                    int Np, int Kp, int nsplit, float* C, int* status, cudaStream_t st, Prof* pf);
 int tc_gemm_splits(int Mp, int Np, int Kp);
+// General complex products on the tensor cores, FP32-accurate (TF32 x3), for the
+// mixed path: inner C[m][n] = sum_k conj(A[m][k]) B[n][k] (A, B rows of length
+// K, contiguous); outer C[n][m] (+)= (-) sum_k A[k][m] B[k][n] (A [K][M], B
+// [K][N] dense).  Work of tc_*_bytes(); a bounded wait that ran out writes a
+// non-zero code to *status.
+size_t tc_inner_bytes(int M, int N, int K);
+size_t tc_outer_bytes(int M, int N, int K);
+int tc_inner(const double* A, const double* B, int M, int N, int K, double* C, int ldc, void* work,
+             size_t work_bytes, int* status, cudaStream_t st, Prof* pf);
+int tc_outer(const double* A, const double* B, int M, int N, int K, double* C, int ldc,
+             int alpha_neg, int beta, void* work, size_t work_bytes, int* status, cudaStream_t st,
+             Prof* pf);
 // hpsi += beta^T D (conj(beta) psi^T) on the tensor cores; work of nonlocal_tc_bytes().
 size_t nonlocal_tc_bytes(int np, int nb, int npw);
 size_t nonlocal_tc_beta_bytes(int np, int npw);

@@ -397,6 +397,43 @@ __global__ void k_combine_h(const float* __restrict__ C, int ns, int Mp, int Np,
   }
 }
 
+// C[m][n] = (sum_s C32[s][m][n], sum_s C32[s][m][N + n]) into ld ldc (inner products)
+__global__ void k_combine_inner(const float* __restrict__ C32, int ns, int Mp, int Np, int M, int N,
+                                double2* __restrict__ C, int ldc) {
+  const size_t total = (size_t)M * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(t / N), n = (int)(t % N);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      const float* c = C32 + (size_t)s * Mp * Np + (size_t)m * Np;
+      re += (double)c[n];
+      im += (double)c[N + n];
+    }
+    C[(size_t)m * ldc + n] = make_double2(re, im);
+  }
+}
+
+// C[n][m] (+)= (-) (sum_s C32[s][m][n], sum_s C32[s][m][N + n]) (outer products)
+__global__ void k_combine_outer(const float* __restrict__ C32, int ns, int Mp, int Np, int M, int N,
+                                double2* __restrict__ C, int ldc, int alpha_neg, int beta) {
+  const size_t total = (size_t)N * M;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(t / M), m = (int)(t % M);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      const float* c = C32 + (size_t)s * Mp * Np + (size_t)m * Np;
+      re += (double)c[n];
+      im += (double)c[N + n];
+    }
+    if (alpha_neg) { re = -re; im = -im; }
+    double2* p = C + (size_t)n * ldc + m;
+    if (beta) { const double2 o = *p; re += o.x; im += o.y; }
+    *p = make_double2(re, im);
+  }
+}
+
 int grid_of(size_t total) {
   return (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 152 * 16));
 }
@@ -488,6 +525,90 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
     set_error("nonlocal_tc: %s", cudaGetErrorString(e));
     return QE_ECUDA;
   }
+  return QE_OK;
+}
+
+// ---- general complex products (mixed path subspace products) -------------------------
+// inner: C[m][n] = sum_k conj(A[m][k]) B[n][k], rows of A and B contiguous in k
+// (leading dimension K); outer: C[n][m] (+)= (-) sum_k A[k][m] B[k][n] with A
+// [K][M] and B [K][N] dense.  FP32-accurate (TF32 x3) on the tensor cores.
+size_t tc_inner_bytes(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 0;
+  const size_t Mp = pad_to(M, TC_BM), Kp = pad_to(2 * K, TC_BK), Np = pad_to(2 * N, TC_BN);
+  const size_t ns = tc_gemm_splits((int)Mp, (int)Np, (int)Kp);
+  return 2 * Mp * Kp * 4 + 2 * Np * Kp * 4 + ns * Mp * Np * 4 + 8 * 256;
+}
+
+size_t tc_outer_bytes(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 0;
+  const size_t Mp = pad_to(M, TC_BM), Kp = pad_to(2 * K, TC_BK), Np = pad_to(2 * N, TC_BN);
+  const size_t ns = tc_gemm_splits((int)Mp, (int)Np, (int)Kp);
+  return 2 * Mp * Kp * 4 + 2 * Np * Kp * 4 + ns * Mp * Np * 4 + 8 * 256;
+}
+
+int tc_inner(const double* A, const double* B, int M, int N, int K, double* C, int ldc, void* work,
+             size_t work_bytes, int* status, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  if (tc_inner_bytes(M, N, K) > work_bytes) {
+    set_error("tc_inner: workspace too small");
+    return QE_EINVAL;
+  }
+  const int Mp = pad_to(M, TC_BM), Kp = pad_to(2 * K, TC_BK), Np = pad_to(2 * N, TC_BN);
+  const int ns = tc_gemm_splits(Mp, Np, Kp);
+  char* p = static_cast<char*>(work);
+  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
+  float* ahi = (float*)take((size_t)Mp * Kp * 4);
+  float* alo = (float*)take((size_t)Mp * Kp * 4);
+  float* bhi = (float*)take((size_t)Np * Kp * 4);
+  float* blo = (float*)take((size_t)Np * Kp * 4);
+  float* c = (float*)take((size_t)ns * Mp * Np * 4);
+  {
+    ProfScope ps(pf, "k_tc_pack", st);
+    k_pack_rows<<<grid_of((size_t)Mp * Kp), 256, 0, st>>>((const double2*)A, M, K, Mp, Kp, ahi, alo);
+    k_pack_psi<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)B, N, K, Np, Kp, bhi, blo);
+    if (pf) pf->launches += 1;
+  }
+  int rc = tc_gemm_tf32x3(ahi, alo, bhi, blo, Mp, Np, Kp, ns, c, status, st, pf);
+  if (rc) return rc;
+  ProfScope ps(pf, "k_tc_combine", st);
+  k_combine_inner<<<grid_of((size_t)M * N), 256, 0, st>>>(c, ns, Mp, Np, M, N, (double2*)C, ldc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error("tc_inner: %s", cudaGetErrorString(e)); return QE_ECUDA; }
+  return QE_OK;
+}
+
+int tc_outer(const double* A, const double* B, int M, int N, int K, double* C, int ldc,
+             int alpha_neg, int beta, void* work, size_t work_bytes, int* status, cudaStream_t st,
+             Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  if (tc_outer_bytes(M, N, K) > work_bytes) {
+    set_error("tc_outer: workspace too small");
+    return QE_EINVAL;
+  }
+  const int Mp = pad_to(M, TC_BM), Kp = pad_to(2 * K, TC_BK), Np = pad_to(2 * N, TC_BN);
+  const int ns = tc_gemm_splits(Mp, Np, Kp);
+  char* p = static_cast<char*>(work);
+  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
+  float* ahi = (float*)take((size_t)Mp * Kp * 4);
+  float* alo = (float*)take((size_t)Mp * Kp * 4);
+  float* bhi = (float*)take((size_t)Np * Kp * 4);
+  float* blo = (float*)take((size_t)Np * Kp * 4);
+  float* c = (float*)take((size_t)ns * Mp * Np * 4);
+  {
+    ProfScope ps(pf, "k_tc_pack", st);
+    k_pack_pad<<<grid_of((size_t)Mp * Kp), 256, 0, st>>>(Mp, Kp, M, 2 * K, ahi, alo);
+    dim3 gt((Mp + 31) / 32, (K + 31) / 32);
+    k_pack_beta_t<<<gt, dim3(32, 8), 0, st>>>((const double2*)A, K, M, Mp, Kp, ahi, alo);
+    k_pack_q<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)B, K, N, Np, Kp, bhi, blo);
+    if (pf) pf->launches += 2;
+  }
+  int rc = tc_gemm_tf32x3(ahi, alo, bhi, blo, Mp, Np, Kp, ns, c, status, st, pf);
+  if (rc) return rc;
+  ProfScope ps(pf, "k_tc_combine", st);
+  k_combine_outer<<<grid_of((size_t)M * N), 256, 0, st>>>(c, ns, Mp, Np, M, N, (double2*)C, ldc,
+                                                        alpha_neg, beta);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error("tc_outer: %s", cudaGetErrorString(e)); return QE_ECUDA; }
   return QE_OK;
 }
 
