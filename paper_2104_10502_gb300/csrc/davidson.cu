@@ -368,6 +368,99 @@ static int update_reduced(const DvState& S, int n0, int n1, bool with_s, cudaStr
   return check_launch("k_mirror");
 }
 
+// ---- Rayleigh-Ritz by Loewdin orthonormalisation ---------------------------------
+// After the first iteration the basis is orthonormal up to the previous
+// reduced problem's rounding: S_r = I + E with E tiny, and
+//   M = S_r^(-1/2) = I - E/2 + 3/8 E^2 + O(E^3)
+// makes A = M H_r M the standard problem whose eigenvectors Y give X = M Y
+// (X^+ S_r X = I to O(E^3)).  Four n x n (x nb) matrix products on the tensor
+// cores replace the Cholesky factorisation and the three triangular solves,
+// which take one grid-wide step per column.
+__global__ void k_lowdin_e(const z* __restrict__ Sr, int ld, int n, z* __restrict__ E) {
+  const size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    z v = Sr[(size_t)i * ld + j];
+    if (i == j) v.x -= 1.0;
+    E[t] = v;
+  }
+}
+
+// M = I - E/2 + 3/8 conj(F), F = conj(E E) (the inner product of E with itself)
+__global__ void k_lowdin_m(const z* __restrict__ E, const z* __restrict__ F, int n, z* __restrict__ M) {
+  const size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    const z e = E[t], f = F[t];
+    z m = {-0.5 * e.x + 0.375 * f.x, -0.5 * e.y - 0.375 * f.y};
+    if (i == j) m.x += 1.0;
+    M[t] = m;
+  }
+}
+
+__global__ void k_compact(const z* __restrict__ src, int lds, int n, z* __restrict__ dst) {
+  const size_t total = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x)
+    dst[t] = src[(t / n) * lds + t % n];
+}
+
+__global__ void k_conj(const z* __restrict__ src, z* __restrict__ dst, size_t count) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const z v = src[t];
+    dst[t] = {v.x, -v.y};
+  }
+}
+
+// C[m][n] = sum_k conj(A[m][k]) B[n][k] for compact operands (rows of length K),
+// on the tensor cores when the product is large enough and the scratch holds it.
+template <typename T>
+static int dense_inner(const DvState& S, const z* A, int M, const z* B, int N, int K, z* C, int ldc,
+                       cudaStream_t st, Prof* pf) {
+  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(M, N, K) && tc_inner_bytes(M, N, K) <= S.tc_bytes)
+    return tc_inner((const double*)A, (const double*)B, M, N, K, (double*)C, ldc, S.tc, S.tc_bytes,
+                    dv_tc_status(S), st, pf);
+  if (sizeof(T) == sizeof(double) && S.oz && oz_worth(M, N, K) && oz_inner_scratch(M, N, K) <= S.oz_bytes)
+    return oz_inner((const double*)A, K, (const double*)B, K, M, N, K, (double*)C, ldc, S.oz,
+                    S.oz_bytes, dv_tc_status(S), st, pf);
+  return gemm_inner<T>((const double*)A, K, (const double*)B, K, M, N, K, (double*)C, ldc, S.part,
+                       S.part_bytes, st, pf);
+}
+
+template <typename T>
+static int rayleigh_ritz_lowdin(DvState& S, int n, cudaStream_t st, Prof* pf) {
+  const int md = S.max_dim, nb = S.nb;
+  const size_t nn = (size_t)n * n;
+  ProfScope ps(pf, "rr_lowdin", st);
+  k_lowdin_e<<<grid_for(nn), 256, 0, st>>>(S.Sr, md, n, S.Lw);                     // E
+  DV_TRY(check_launch("k_lowdin_e"));
+  DV_TRY(dense_inner<T>(S, S.Lw, n, S.Lw, n, n, S.Zw, n, st, pf));                 // conj(E E)
+  k_lowdin_m<<<grid_for(nn), 256, 0, st>>>(S.Lw, S.Zw, n, S.Aw);                    // M
+  k_compact<<<grid_for(nn), 256, 0, st>>>(S.Hr, md, n, S.Lw);                       // H
+  DV_TRY(check_launch("k_lowdin_m"));
+  DV_TRY(dense_inner<T>(S, S.Aw, n, S.Lw, n, n, S.Zw, n, st, pf));                 // conj(M H)
+  k_conj<<<grid_for(nn), 256, 0, st>>>(S.Zw, S.Zw, nn);                             // M H
+  DV_TRY(dense_inner<T>(S, S.Zw, n, S.Aw, n, n, S.Lw, n, st, pf));                 // conj(M H M)
+  k_conj<<<grid_for(nn), 256, 0, st>>>(S.Lw, S.Lw, nn);
+  DV_TRY(check_launch("k_conj"));
+  DV_TRY(hermitize(S.Lw, n, n, st));
+  pf->launches += 4;
+  return QE_OK;
+}
+
+// X = M Y for the Loewdin Rayleigh-Ritz: Y [n][nb] in S.X, M in S.Aw.
+template <typename T>
+static int lowdin_back(DvState& S, int n, cudaStream_t st, Prof* pf) {
+  const int nb = S.nb;
+  k_conj<<<grid_for((size_t)n * n), 256, 0, st>>>(S.Aw, S.Zw, (size_t)n * n);        // conj(M)
+  DV_TRY(check_launch("k_conj"));
+  DV_TRY(transpose(S.X, nb, S.C, n, n, nb, st));                                    // Y^T
+  return dense_inner<T>(S, S.Zw, n, S.C, nb, n, S.X, nb, st, pf);                  // M Y
+}
+
 // FP64 <-> FP32 copies of the reduced problem for the mixed path.
 __global__ void k_z_to_c(const z* __restrict__ src, int lds, cx<float>* __restrict__ dst, int ldd,
                          int rows, int cols) {
@@ -442,6 +535,33 @@ static int rayleigh_ritz_f32(DvState& S, int n, cudaStream_t st, Prof* pf) {
     ProfScope ps(pf, "rr_backsub", st);
     DV_TRY(f32::trsm_upper_h(L32, n, n, X32, nb, nb, st));
   }
+  k_c_to_z<<<grid_for((size_t)n * nb), 256, 0, st>>>(X32, nb, S.X, nb, n, nb, e32, S.e, nb);
+  return check_launch("k_c_to_z");
+}
+
+// Lowest nb eigenpairs of the Hermitian n x n matrix in S.Lw (compact; destroyed)
+// into S.e, S.X (ld nb), in FP32 or FP64.
+static int rr_standard_eig(DvState& S, int n, bool fp32, cudaStream_t st, Prof* pf) {
+  const int nb = S.nb;
+  if (!fp32) return heev_lowest(S.Lw, n, n, nb, S.e, S.X, nb, S.dw, st, pf);
+  using zf = cx<float>;
+  zf* A32 = reinterpret_cast<zf*>(S.Zw);
+  zf* X32 = reinterpret_cast<zf*>(S.C);
+  float* e32 = reinterpret_cast<float*>(S.rn);
+  DenseWorkT<float> w;
+  w.tau = reinterpret_cast<zf*>(S.dw.tau);
+  w.p = reinterpret_cast<zf*>(S.dw.p);
+  w.vbuf = reinterpret_cast<zf*>(S.dw.vbuf);
+  w.refl = reinterpret_cast<zf*>(S.dw.refl);
+  w.d = reinterpret_cast<float*>(S.dw.d);
+  w.e = reinterpret_cast<float*>(S.dw.e);
+  w.y = reinterpret_cast<float*>(S.dw.y);
+  w.piv = reinterpret_cast<float*>(S.dw.piv);
+  w.status = S.dw.status;
+  w.bar = S.dw.bar;
+  k_z_to_c<<<grid_for((size_t)n * n), 256, 0, st>>>(S.Lw, n, A32, n, n, n);
+  DV_TRY(check_launch("k_z_to_c"));
+  DV_TRY(f32::heev_lowest(A32, n, n, nb, e32, X32, nb, w, st, pf));
   k_c_to_z<<<grid_for((size_t)n * nb), 256, 0, st>>>(X32, nb, S.X, nb, n, nb, e32, S.e, nb);
   return check_launch("k_c_to_z");
 }
@@ -629,8 +749,16 @@ static int dv_step_launch(DvSolve& v, cudaStream_t st, Prof* pf) {
   const size_t zb = sizeof(z);
   DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));   // keeps the barrier error word
   v.rr32 = rr_in_fp32(v);
-  if (v.rr32) DV_TRY(rayleigh_ritz_f32(S, v.n, st, pf));
-  else DV_TRY(rayleigh_ritz(S, v.n, true, st, pf));
+  if (!v.first && v.n > kSmallDense) {
+    // nearly orthonormal basis: Loewdin form on the tensor cores
+    DV_TRY(rayleigh_ritz_lowdin<T>(S, v.n, st, pf));
+    DV_TRY(rr_standard_eig(S, v.n, v.rr32, st, pf));
+    DV_TRY(lowdin_back<T>(S, v.n, st, pf));
+  } else if (v.rr32) {
+    DV_TRY(rayleigh_ritz_f32(S, v.n, st, pf));
+  } else {
+    DV_TRY(rayleigh_ritz(S, v.n, true, st, pf));
+  }
   DV_TRY(outer<T>(S, S.V, npw, S.X, nb, npw, nb, v.n, S.Psi, npw, 0, 0, st, pf));
   DV_TRY(outer<T>(S, S.HV, npw, S.X, nb, npw, nb, v.n, S.HPsi, npw, 0, 0, st, pf));
   if (v.first) {
