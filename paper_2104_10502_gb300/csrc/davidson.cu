@@ -206,10 +206,11 @@ static bool tc_worth(long long M, long long N, long long K) { return M > 0 && N 
 // Scratch of the FP64 tensor-core subspace products: the largest inner product
 // (basis x new block over the plane waves) and outer product (rotation of the
 // basis) of a solve.
-// The mixed path uses it only for its final FP64 Rayleigh-Ritz on the nb Ritz vectors.
+// The mixed path needs it for its final FP64 Rayleigh-Ritz and FP64 iterations.
 static size_t dv_oz_bytes(size_t npw, size_t nb, size_t md, bool fp64) {
+  (void)fp64;   // the mixed path may end with FP64 iterations over the whole basis
   if (!fp64_gemm_on_tensor_cores()) return 0;
-  const size_t n = fp64 ? md : nb;
+  const size_t n = md;
   return std::max(oz_inner_scratch((int)n, (int)nb, (int)npw),
                   oz_outer_scratch((int)npw, (int)nb, (int)n)) + 256;
 }
@@ -704,6 +705,9 @@ struct DvSolve {
   // the last iteration ran in FP32
   double rmax = HUGE_VAL;
   bool rr32 = false;
+  // mixed path: best largest residual so far and iterations without a 20 % gain
+  double best_rmax = HUGE_VAL;
+  int stall = 0;
 };
 
 // The FP64 path solves small reduced problems (n <= 64, the single-CTA path) in
@@ -802,11 +806,25 @@ static int dv_step_finish(qe_ctx* ctx, DvSolve& v, cudaStream_t st, Prof* pf) {
   }
   std::vector<int> unc;
   double rmax = 0.0;
+  // the mixed iteration stops at 1e-4 at the finest (its FP32 rounding floor on
+  // C2 is ~3e-5); dv_fp64_phase then meets the caller's tolerance
+  const double tol = v.precision != QE_FP64 ? std::max(v.tol, 1e-4) : v.tol;
   for (int b = 0; b < nb; ++b) {
-    if (!(v.rn[b] <= v.tol)) unc.push_back(b);
+    if (!(v.rn[b] <= tol)) unc.push_back(b);
     rmax = std::max(rmax, std::isfinite(v.rn[b]) ? v.rn[b] : HUGE_VAL);
   }
   v.rmax = rmax;
+  if (!unc.empty() && v.precision != QE_FP64) {
+    // an FP32 iteration that stalls above 1e-4 (five iterations without a 20 %
+    // gain) hands over to the FP64 refinement and iterations (dv_fp64_phase)
+    if (rmax < 0.8 * v.best_rmax) {
+      v.best_rmax = rmax;
+      v.stall = 0;
+    } else if (++v.stall >= 5 && rmax < 1e-3) {
+      v.done = true;
+      return QE_OK;
+    }
+  }
   if (unc.empty() && v.precision == QE_FP64 && v.rr32) {
     // converged on an FP32 Rayleigh-Ritz: redo it in FP64 before accepting
     v.rmax = 0.0;
@@ -850,11 +868,8 @@ static int dv_apply_h(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
 }
 
 template <typename T>
-static int davidson_run(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
+static int dv_loop(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
   Prof* pf = &ctx->prof;
-  DV_TRY(dv_begin(v, st));
-  DV_TRY(dv_apply_h(ctx, v, st));
-  DV_TRY(dv_after_first_h<T>(v, st, pf));
   while (true) {
     DV_TRY(dv_step_launch<T>(v, st, pf));
     DV_TRY(dv_step_finish<T>(ctx, v, st, pf));
@@ -863,10 +878,53 @@ static int davidson_run(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
     DV_TRY(dv_apply_h(ctx, v, st));
     DV_TRY(dv_after_h<T>(v, st, pf));
   }
+  return QE_OK;
+}
+
+// End of the mixed path, after the FP64 Rayleigh-Ritz of its Ritz vectors
+// (refine_pre/post): accept them if every FP64 residual is within tol, else go
+// on as an FP64 Davidson from them (they are an orthonormal basis to FP64
+// rounding) until tol or max_iter.  The mixed path thus meets the same
+// residual criterion as the FP64 one, with most iterations in FP32.
+static int dv_fp64_phase(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
+  DvState& S = v.S;
+  const int nb = S.nb, npw = S.npw;
+  DV_CU(cudaMemcpyAsync(v.rn.data(), S.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DV_CU(cudaStreamSynchronize(st));
+  double rmax = 0.0;
+  bool all = true;
+  for (int b = 0; b < nb; ++b) {
+    if (!(v.rn[b] <= v.tol)) all = false;
+    rmax = std::max(rmax, std::isfinite(v.rn[b]) ? v.rn[b] : HUGE_VAL);
+  }
+  v.conv = all;
+  if (all || v.it >= v.max_iter) return QE_OK;
+  const size_t bytes = (size_t)nb * npw * sizeof(z);
+  DV_CU(cudaMemcpyAsync(S.V, S.Psi, bytes, cudaMemcpyDeviceToDevice, st));
+  DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, bytes, cudaMemcpyDeviceToDevice, st));
+  v.n = nb;
+  DV_TRY(update_reduced<double>(S, 0, nb, true, st, &ctx->prof));
+  v.precision = QE_FP64;
+  v.first = false;
+  v.done = false;
+  v.conv = false;
+  v.rmax = rmax;
+  v.h_rows = 0;
+  return dv_loop<double>(ctx, v, st);
+}
+
+template <typename T>
+static int davidson_run(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
+  Prof* pf = &ctx->prof;
+  DV_TRY(dv_begin(v, st));
+  DV_TRY(dv_apply_h(ctx, v, st));
+  DV_TRY(dv_after_first_h<T>(v, st, pf));
+  DV_TRY(dv_loop<T>(ctx, v, st));
   if (v.precision != QE_FP64) {
     DV_TRY(refine_pre(v.S, st));
     DV_TRY(hpsi_core(ctx, *v.P, v.op, QE_FP64, (const double*)v.S.V, (double*)v.S.HV, v.S.nb, st));
     DV_TRY(refine_post(v.S, st, pf));
+    DV_TRY(dv_fp64_phase(ctx, v, st));
   }
   return QE_OK;
 }
@@ -929,6 +987,8 @@ static int davidson_batch_run(qe_ctx* ctx, std::vector<DvSolve>& vs,
     DV_TRY(apply_pending(QE_FP64));
     for (int p = 0; p < np; ++p)
       if (rcs[p] == QE_OK) rcs[p] = refine_post(vs[p].S, st, pf);
+    for (int p = 0; p < np; ++p)
+      if (rcs[p] == QE_OK) rcs[p] = dv_fp64_phase(ctx, vs[p], st);
   }
   return QE_OK;
 }
