@@ -62,34 +62,42 @@ __device__ __forceinline__ unsigned long long gtime_ns() {
   return t;
 }
 
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every wait
-// is bounded (2 s); on time-out the error word is set, every later barrier
-// returns false at once and the kernel leaves.
+// is bounded (2 s); on time-out the error word is set, the waiting CTAs see it
+// within 1024 polls, return false and leave the kernel.
 __device__ bool grid_sync(const GridBar& b) {
   __shared__ int s_ok;
   __syncthreads();
   // one CTA: the block barrier above already orders its global accesses
   if (gridDim.x == 1) return true;
   if (threadIdx.x == 0) {
-    int ok = *(volatile int*)b.err == 0;
-    if (ok) {
-      const unsigned int g = *(volatile unsigned int*)b.gen;
+    int ok = 1;
+    const unsigned int g = ld_acquire_gpu(b.gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(b.count, 0u);
       __threadfence();
-      const unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
-      if (arrived == gridDim.x) {
-        atomicExch(b.count, 0u);
-        __threadfence();
-        atomicAdd(b.gen, 1u);
-      } else {
-        const unsigned long long t0 = gtime_ns();
-        while (*(volatile unsigned int*)b.gen == g) {
-          if (*(volatile int*)b.err) break;
-          if (gtime_ns() - t0 > 2000000000ull) { atomicExch(b.err, 1); break; }
-          __nanosleep(32);
+      atomicAdd(b.gen, 1u);
+    } else {
+      // acquire-poll the generation word; the clock and the error word are read
+      // only every 1024 polls (each read is an L2 round trip on the critical path)
+      unsigned long long t0 = 0;
+      for (int it = 0;; ++it) {
+        if (ld_acquire_gpu(b.gen) != g) break;
+        if ((it & 1023) == 1023) {
+          const unsigned long long t = gtime_ns();
+          if (t0 == 0) t0 = t;
+          else if (t - t0 > 2000000000ull) { atomicExch(b.err, 1); ok = 0; break; }
+          if (*(volatile int*)b.err) { ok = 0; break; }
         }
       }
-      __threadfence();
-      ok = *(volatile int*)b.err == 0;
     }
     s_ok = ok;
   }
