@@ -28,6 +28,28 @@ static int check_launch(const char* what) {
 
 __device__ __forceinline__ z zconj(z a) { return {a.x, -a.y}; }
 __device__ __forceinline__ R zabs2(z a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmar(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// acc + a b and a - (x conj(y) + u conj(t)) as explicit FMA chains (4 and 8 FMAs;
+// left to contraction the products and sums take 6 and 12 FP64 instructions)
+__device__ __forceinline__ z zfma(z a, z b, z acc) {
+  acc.x = fmar(a.x, b.x, acc.x);
+  acc.x = fmar(-a.y, b.y, acc.x);
+  acc.y = fmar(a.x, b.y, acc.y);
+  acc.y = fmar(a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ z zrank2(z a, z x, z y, z u, z t) {
+  a.x = fmar(-x.x, y.x, a.x);
+  a.x = fmar(-x.y, y.y, a.x);
+  a.x = fmar(-u.x, t.x, a.x);
+  a.x = fmar(-u.y, t.y, a.x);
+  a.y = fmar(-x.y, y.x, a.y);
+  a.y = fmar(x.x, y.y, a.y);
+  a.y = fmar(-u.y, t.x, a.y);
+  a.y = fmar(u.x, t.y, a.y);
+  return a;
+}
 
 // Block-wide sum (blockDim.x a multiple of 32, <= 1024).  Every thread gets the result.
 __device__ R block_sum(R v, R* sh) {
@@ -469,6 +491,173 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* t
   for (size_t i = gtid; i < (size_t)n; i += nthr) dg[i] = ldz(&A[i * lda + i]).x;
 }
 
+// Householder tridiagonalisation (the same reflectors as k_tridiag_coop) with the
+// matrix held in the CTAs' shared memory: CTA c owns rows c, c + G, c + 2G, ...
+// (cyclic, so the shrinking trailing block stays evenly spread).  Every CTA
+// forms each reflector itself from the published column, so a step needs one
+// grid barrier: before it, the owners publish p_r = tau (A v)_r of their rows
+// and their entries of the next column; after it, every CTA reads both, forms
+// w = p - (1/2) conj(tau) (v^+ p) v, applies A -= v w^+ + w v^+ to its own rows
+// and to the next column, and builds the next reflector from that column.  All
+// CTAs reach bit-identical reflectors (same inputs, same reduction order).
+// Global A is read once at the start; its rows 0..3 then hold the exchange
+// vectors (p and the column, two parities).  Needs n >= 4 and at most
+// kTridRows rows per CTA.  Dynamic shared memory: (ceil(n / G) + 3) n complex.
+constexpr int kTridRows = 8;
+
+__device__ __forceinline__ void block_sum2(R& a, R& b, R* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { sh[w] = a; sh[16 + w] = b; }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (threadIdx.x < 32) {
+    R ta = threadIdx.x < nw ? sh[threadIdx.x] : R(0);
+    R tb = threadIdx.x < nw ? sh[16 + threadIdx.x] : R(0);
+    for (int o = 16; o > 0; o >>= 1) {
+      ta += __shfl_xor_sync(0xffffffffu, ta, o);
+      tb += __shfl_xor_sync(0xffffffffu, tb, o);
+    }
+    if (threadIdx.x == 0) { sh[32] = ta; sh[33] = tb; }
+  }
+  __syncthreads();
+  a = sh[32];
+  b = sh[33];
+}
+
+__global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* tau, R* e, R* dg,
+                                                      z* refl, GridBar bar) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  const int nrmax = (n + G - 1) / G;
+  const int nr = c < n ? (n - 1 - c) / G + 1 : 0;   // rows owned: c + q G, q < nr
+  z* rows = reinterpret_cast<z*>(smem_raw);          // nrmax x n
+  z* sv = rows + (size_t)nrmax * n;                  // reflector v (index i <-> row j+1+i)
+  z* sw = sv + n;                                    // p, then w
+  z* sx = sw + n;                                    // column to reduce (index i <-> row j+1+i)
+  __shared__ R sh[34];
+  __shared__ z spart[8][kTridRows];
+  for (int q = 0; q < nr; ++q) {
+    const z* src = A + (size_t)(c + q * G) * lda;
+    for (int k = tid; k < n; k += nt) rows[(size_t)q * n + k] = ldz(src + k);
+  }
+  for (int i = tid; i < n - 1; i += nt) sx[i] = ldz(&A[(size_t)(1 + i) * lda]);
+  if (c == 0 && tid == 0) dg[0] = ldz(&A[0]).x;
+  // every CTA has read A: its rows 0..3 become the exchange vectors
+  if (!grid_sync(bar)) return;
+  for (int j = 0; j < n - 1; ++j) {
+    const int m = n - 1 - j, par = j & 1;
+    z* xp = A + (size_t)(2 * par) * lda;       // p_r at [r]
+    z* xc = A + (size_t)(2 * par + 1) * lda;   // A[r][j+1] at [r], r >= j+2
+    // reflector of step j from sx[0..m)
+    const z alpha = sx[0];
+    R s = R(0);
+    for (int i = 1 + tid; i < m; i += nt) s = fmar(sx[i].x, sx[i].x, fmar(sx[i].y, sx[i].y, s));
+    const R sigma = block_sum(s, sh);
+    z t;
+    R beta;
+    if (sigma == R(0) && alpha.y == R(0)) {
+      t = {R(0), R(0)};
+      beta = alpha.x;
+      for (int i = tid; i < m; i += nt) sv[i] = {i == 0 ? R(1) : R(0), R(0)};
+    } else {
+      const R nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sigma);
+      beta = alpha.x >= R(0) ? -nu : nu;
+      const z am = {alpha.x - beta, alpha.y};
+      const R rden = R(1) / (am.x * am.x + am.y * am.y), rbeta = R(1) / beta;
+      const z sc = {am.x * rden, -am.y * rden};
+      t = {(beta - alpha.x) * rbeta, -alpha.y * rbeta};
+      for (int i = tid; i < m; i += nt) sv[i] = i == 0 ? z{R(1), R(0)} : cmul(sx[i], sc);
+    }
+    __syncthreads();
+    if (c == 0) {
+      z* rrow = refl + (size_t)j * n + (j + 1);
+      for (int i = tid; i < m; i += nt) rrow[i] = sv[i];
+      if (tid == 0) { tau[j] = t; e[j] = beta; }
+    }
+    // p = tau A v on the owned rows of the trailing block (r >= j+1): every warp
+    // takes 32-column chunks of all those rows, partial sums meet in spart
+    const int q0 = c >= j + 1 ? 0 : (j + 1 - c + G - 1) / G;
+    const int nq = nr - q0;
+    if (nq > 0) {
+      z acc[kTridRows];
+#pragma unroll
+      for (int q = 0; q < kTridRows; ++q) acc[q] = {R(0), R(0)};
+      for (int k = warp * 32 + lane; k < m; k += nwarp * 32) {
+        const z vk = sv[k];
+        const z* base = rows + (size_t)q0 * n + (j + 1) + k;
+#pragma unroll
+        for (int q = 0; q < kTridRows; ++q)
+          if (q < nq) acc[q] = zfma(base[(size_t)q * n], vk, acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kTridRows; ++q) {
+        if (q < nq) {
+          z a = acc[q];
+          for (int o = 16; o > 0; o >>= 1) {
+            a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+            a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+          }
+          if (lane == 0) spart[warp][q] = a;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < nq) {
+      z a = {R(0), R(0)};
+      for (int w = 0; w < nwarp; ++w) a = cadd(a, spart[w][tid]);
+      const int q = q0 + tid, r = c + q * G;
+      xp[r] = cmul(t, a);
+      if (r >= j + 2) xc[r] = rows[(size_t)q * n + (j + 1)];
+    }
+    if (!grid_sync(bar)) return;
+    // w = p - (1/2) conj(tau) (v^+ p) v; the next column (rows j+2 ..)
+    R sr = R(0), si = R(0);
+    for (int i = tid; i < m; i += nt) {
+      const z v = sv[i], pr = ldz(&xp[j + 1 + i]);
+      sw[i] = pr;
+      sr = fmar(v.x, pr.x, fmar(v.y, pr.y, sr));
+      si = fmar(v.x, pr.y, fmar(-v.y, pr.x, si));
+    }
+    for (int i = tid; i < m - 1; i += nt) sx[i] = ldz(&xc[j + 2 + i]);
+    block_sum2(sr, si, sh);
+    const z coef = {R(0.5) * (t.x * sr + t.y * si), R(0.5) * (t.x * si - t.y * sr)};
+    const z ncoef = {-coef.x, -coef.y};
+    for (int i = tid; i < m; i += nt) sw[i] = zfma(ncoef, sv[i], sw[i]);
+    __syncthreads();
+    // A -= v w^+ + w v^+ on the owned rows, and on the next column
+    for (int q = q0; q < nr; ++q) {
+      const int kr = c + q * G - (j + 1);
+      const z vr = sv[kr], wr = sw[kr];
+      z* arow = rows + (size_t)q * n + (j + 1);
+      for (int k = tid; k < m; k += nt) {
+        const z a = zrank2(arow[k], vr, sw[k], wr, sv[k]);
+        arow[k] = a;
+        if (kr == 0 && k == 0) dg[j + 1] = a.x;
+      }
+    }
+    {
+      // v_0 = 1: x_i - v_{i+1} conj(w_0) - w_{i+1}
+      const z w0 = sw[0];
+      for (int i = tid; i < m - 1; i += nt) {
+        const z v = sv[i + 1], w = sw[i + 1];
+        z x = {sx[i].x - w.x, sx[i].y - w.y};
+        x.x = fmar(-v.x, w0.x, x.x);
+        x.x = fmar(-v.y, w0.y, x.x);
+        x.y = fmar(-v.y, w0.x, x.y);
+        x.y = fmar(v.x, w0.y, x.y);
+        sx[i] = x;
+      }
+    }
+    __syncthreads();   // the next reflector reads all of sx
+  }
+}
+
 // ---- tridiagonal eigenvalues: Sturm bisection, one thread per eigenvalue --------
 __device__ int sturm_count(const R* d, const R* e, int n, R x, R tiny) {
   int cnt = 0;
@@ -701,6 +890,31 @@ static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, c
   return check_launch("k_backtransform");
 }
 
+// Grid of k_tridiag_rows for an n x n matrix (0: use k_tridiag_coop): one CTA per
+// SM (at most n), provided every CTA's rows and vectors fit in shared memory.
+static int tridiag_rows_grid(int n, size_t* smem) {
+  if (n < 16) return 0;
+  int dev = 0, nsm = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)k_tridiag_rows) != cudaSuccess) return 0;
+  const int g = std::min(nsm, n);
+  const int nrmax = (n + g - 1) / g;
+  if (nrmax > kTridRows) return 0;
+  const size_t sm = (size_t)(nrmax + 3) * n * sizeof(z);
+  if (sm + fa.sharedSizeBytes > (size_t)optin) return 0;
+  set_max_dynamic_smem(k_tridiag_rows);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_rows, 256, sm) != cudaSuccess ||
+      occ < 1)
+    return 0;
+  *smem = sm;
+  return g;
+}
+
 int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk,
                 cudaStream_t st, Prof* pf) {
   if (n <= 0 || nev <= 0) return QE_OK;
@@ -712,8 +926,15 @@ int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R
     set_error("heev_lowest: memset failed");
     return QE_ECUDA;
   }
-  {
-    GridBar bar = wk.bar;
+  GridBar bar = wk.bar;
+  size_t rsm = 0;
+  const int g = tridiag_rows_grid(n, &rsm);
+  if (g > 0) {
+    void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.d, &wk.refl, &bar};
+    ProfScope ps(pf, "heev_tridiag", st);
+    int rc0 = launch_coop((const void*)k_tridiag_rows, g, args, st, "k_tridiag_rows", rsm);
+    if (rc0) return rc0;
+  } else {
     void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.p, &wk.d, &wk.vbuf, &wk.refl, &bar};
     const size_t tsm = 2 * (size_t)n * sizeof(z);
     set_max_dynamic_smem(k_tridiag_coop);
