@@ -92,29 +92,41 @@ constexpr bool kFusePlane = sizeof(T) == 4;
 template <typename T> struct PlaneLB { static constexpr int threads = 512, minb = 1; };
 template <> struct PlaneLB<float> { static constexpr int threads = 256, minb = 2; };
 
+// Row stride of a plane in shared memory: odd, so that the lines of one pass that
+// consecutive threads take (rows in the x pass, columns in the y pass) fall in
+// different banks.
+__host__ __device__ inline int plane_ld(int n1) { return n1 | 1; }
+
 template <typename T>
 __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* smem) {
   const int n1 = J.r1.n, n2 = J.r2.n, n3 = J.r3.n, nst = J.nst, nax = J.nax;
+  const int ld = plane_ld(n1);
   cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
-  cx<T>* tw1 = plane + (size_t)n1 * n2;
+  cx<T>* tw1 = plane + (size_t)ld * n2;
   cx<T>* tw2 = tw1 + n1;
   int* ax = reinterpret_cast<int*>(tw2 + n2);
-  for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) plane[i] = {T(0), T(0)};
+  for (int i = threadIdx.x; i < ld * n2; i += blockDim.x) plane[i] = {T(0), T(0)};
   for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = {T(J.tw1[2 * i]), T(J.tw1[2 * i + 1])};
   for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = {T(J.tw2[2 * i]), T(J.tw2[2 * i + 1])};
   for (int i = threadIdx.x; i < nax; i += blockDim.x) ax[i] = J.ax[i];
   __syncthreads();
   cx<T>* Wp = J.W + ((size_t)b * n3 + pz) * nst;
-  for (int s = threadIdx.x; s < nst; s += blockDim.x) plane[J.st_y[s] * n1 + J.st_x[s]] = Wp[s];
+  for (int s = threadIdx.x; s < nst; s += blockDim.x) plane[J.st_y[s] * ld + J.st_x[s]] = Wp[s];
   __syncthreads();
-  fft_lines<T, +1, false, kFusePlane<T>>(plane, n1, 0, ax, nax, true, J.r2, tw2);        // y, active columns
-  fft_lines<T, +1, false, kFusePlane<T>>(plane, 1, n1, nullptr, n2, false, J.r1, tw1);   // x, every row
+  // y on the active columns, then x on every row; consecutive threads take
+  // consecutive lines in both passes
+  fft_lines<T, +1, false, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2);
+  fft_lines<T, +1, false, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1);
   const T* v = J.vp + (size_t)pz * n1 * n2;
-  for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) plane[i] = cscale(plane[i], v[i]);
+  const FastDiv fn1(n1);
+  for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) {
+    const int y = fn1.div(i), x = i - y * n1;
+    plane[y * ld + x] = cscale(plane[y * ld + x], v[i]);
+  }
   __syncthreads();
-  fft_lines<T, -1, true, kFusePlane<T>>(plane, 1, n1, nullptr, n2, false, J.r1, tw1);
-  fft_lines<T, -1, true, kFusePlane<T>>(plane, n1, 0, ax, nax, true, J.r2, tw2);
-  for (int s = threadIdx.x; s < nst; s += blockDim.x) Wp[s] = plane[J.st_y[s] * n1 + J.st_x[s]];
+  fft_lines<T, -1, true, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1);
+  fft_lines<T, -1, true, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2);
+  for (int s = threadIdx.x; s < nst; s += blockDim.x) Wp[s] = plane[J.st_y[s] * ld + J.st_x[s]];
 }
 
 template <typename T>
@@ -230,7 +242,7 @@ size_t zsm_bytes(int n3, int spb) {
 
 template <typename T>
 size_t psm_bytes(const DevPlan& P) {
-  return ((size_t)P.grid[0] * P.grid[1] + P.grid[0] + P.grid[1]) * sizeof(cx<T>) +
+  return ((size_t)plane_ld(P.grid[0]) * P.grid[1] + P.grid[0] + P.grid[1]) * sizeof(cx<T>) +
          (size_t)P.h.nax * sizeof(int);
 }
 

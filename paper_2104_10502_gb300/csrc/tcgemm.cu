@@ -276,37 +276,73 @@ __device__ __forceinline__ void split_store(float x, float* hi, float* lo, size_
   lo[i] = tf32_rn(x - h);
 }
 
-// A[i][k], k < 2 npw: [Re | Im] of row i of a complex [rows][npw] matrix; zero padding.
-__global__ void k_pack_rows(const double2* __restrict__ src, int rows, int npw, int Mp, int Kp,
+__device__ __forceinline__ void split_store4(const float (&x)[4], float* hi, float* lo, size_t i) {
+  float4 h, l;
+  h.x = tf32_rn(x[0]); l.x = tf32_rn(x[0] - h.x);
+  h.y = tf32_rn(x[1]); l.y = tf32_rn(x[1] - h.y);
+  h.z = tf32_rn(x[2]); l.z = tf32_rn(x[2] - h.z);
+  h.w = tf32_rn(x[3]); l.w = tf32_rn(x[3] - h.w);
+  *reinterpret_cast<float4*>(hi + i) = h;
+  *reinterpret_cast<float4*>(lo + i) = l;
+}
+
+// Inner-product operands: the K axis of a packed row is [Re | Im] with the
+// imaginary half at kh = pad4(K), so that every group of four floats lies in
+// one half (16-byte stores); zero beyond K in each half and beyond 2 kh.
+// One thread per four complex inputs of a row (both halves written from one
+// read); grid.y = packed row.
+
+// A[r] = [Re src_r | Im src_r], r < rows; zero rows up to Mp.
+__global__ void k_pack_rows(const double2* __restrict__ src, int rows, int K, int kh, int Kp,
                             float* __restrict__ hi, float* __restrict__ lo) {
-  const size_t total = (size_t)Mp * Kp;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / Kp), k = (int)(t % Kp);
-    float x = 0.f;
-    if (r < rows) {
-      if (k < npw) x = (float)src[(size_t)r * npw + k].x;
-      else if (k < 2 * npw) x = (float)src[(size_t)r * npw + (k - npw)].y;
+  const int r = blockIdx.y;
+  const int nq = kh >> 2, nz = (Kp - 2 * kh) >> 2;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq + nz; q += gridDim.x * blockDim.x) {
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    if (q >= nq) {   // tail beyond 2 kh
+      split_store4(re, hi, lo, (size_t)r * Kp + 2 * kh + 4 * (q - nq));
+      continue;
     }
-    split_store(x, hi, lo, t);
+    const int k = 4 * q;
+    if (r < rows) {
+      const double2* s = src + (size_t)r * K + k;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (k + j < K) { const double2 v = s[j]; re[j] = (float)v.x; im[j] = (float)v.y; }
+    }
+    split_store4(re, hi, lo, (size_t)r * Kp + k);
+    split_store4(im, hi, lo, (size_t)r * Kp + kh + k);
   }
 }
 
-// B rows n < nb: [Re psi_n | Im psi_n]; rows nb + n: [Im psi_n | -Re psi_n].
-__global__ void k_pack_psi(const double2* __restrict__ psi, int nb, int npw, int Np, int Kp,
+// B rows n < N: [Re psi_n | Im psi_n]; rows N + n: [Im psi_n | -Re psi_n]; zero rows
+// 2N .. Np.  grid.y = N + (Np - 2N): y < N writes the row pair of band y, the
+// rest the zero rows.
+__global__ void k_pack_psi(const double2* __restrict__ psi, int N, int K, int kh, int Kp,
                            float* __restrict__ hi, float* __restrict__ lo) {
-  const size_t total = (size_t)Np * Kp;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / Kp), k = (int)(t % Kp);
-    float x = 0.f;
-    if (r < 2 * nb && k < 2 * npw) {
-      const int n = r < nb ? r : r - nb;
-      const double2 v = psi[(size_t)n * npw + (k < npw ? k : k - npw)];
-      if (r < nb) x = (float)(k < npw ? v.x : v.y);
-      else x = (float)(k < npw ? v.y : -v.x);
+  const int y = blockIdx.y;
+  const int nq = kh >> 2, nz = (Kp - 2 * kh) >> 2;
+  const size_t r0 = y < N ? (size_t)y * Kp : (size_t)(N + y) * Kp;   // zero rows: 2N + (y - N)
+  const size_t r1 = (size_t)(N + y) * Kp;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq + nz; q += gridDim.x * blockDim.x) {
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    if (q >= nq || y >= N) {
+      const int k = q >= nq ? 2 * kh + 4 * (q - nq) : 4 * q;
+      split_store4(re, hi, lo, r0 + k);
+      if (q < nq) split_store4(re, hi, lo, r0 + kh + k);
+      if (y < N) split_store4(re, hi, lo, r1 + k);
+      continue;
     }
-    split_store(x, hi, lo, t);
+    const int k = 4 * q;
+    const double2* s = psi + (size_t)y * K + k;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (k + j < K) { const double2 v = s[j]; re[j] = (float)v.x; im[j] = (float)v.y; }
+    split_store4(re, hi, lo, r0 + k);
+    split_store4(im, hi, lo, r0 + kh + k);
+    split_store4(im, hi, lo, r1 + k);
+    float nre[4] = {-re[0], -re[1], -re[2], -re[3]};
+    split_store4(nre, hi, lo, r1 + kh + k);
   }
 }
 
@@ -331,14 +367,19 @@ __global__ void k_pack_beta_t(const double2* __restrict__ beta, int np, int npw,
   }
 }
 
-// zero the K padding (k >= 2 np) of the transposed beta rows and padding rows
+// zero the padding of a transposed-operand matrix: rows >= rows, and columns
+// k >= kvalid of the first rows
 __global__ void k_pack_pad(int Mp, int Kp, int rows, int kvalid, float* __restrict__ hi,
                            float* __restrict__ lo) {
-  const size_t total = (size_t)Mp * Kp;
+  const size_t tail = (size_t)(Mp - rows) * Kp;
+  const int kc = Kp - kvalid;
+  const size_t total = tail + (size_t)rows * kc;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / Kp), k = (int)(t % Kp);
-    if (r >= rows || k >= kvalid) { hi[t] = 0.f; lo[t] = 0.f; }
+    const size_t i = t < tail ? (size_t)rows * Kp + t
+                              : (size_t)((t - tail) / kc) * Kp + kvalid + (t - tail) % kc;
+    hi[i] = 0.f;
+    lo[i] = 0.f;
   }
 }
 
@@ -377,23 +418,36 @@ __global__ void k_combine_p(const float* __restrict__ C, int ns, int Mp, int Np,
   }
 }
 
-// hpsi[n][g] += (sum_s C[s][g][n], sum_s C[s][g][nb + n]); consecutive threads take consecutive g
+// hpsi[n][g] += (sum_s C[s][g][n], sum_s C[s][g][nb + n]): 32 x 32 tiles of (g, n)
+// through shared memory, so that both the C reads (along n) and the hpsi
+// updates (along g) are coalesced.  block (32, 8), grid (ceil(npw/32), ceil(nb/32)).
 __global__ void k_combine_h(const float* __restrict__ C, int ns, int Mp, int Np, int npw, int nb,
                             double2* __restrict__ hpsi) {
-  const size_t total = (size_t)nb * npw;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int n = (int)(t / npw), g = (int)(t % npw);
+  __shared__ double tre[32][33], tim[32][33];
+  const int g0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
+  const int tx = threadIdx.x;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int g = g0 + r, n = n0 + tx;
     double re = 0.0, im = 0.0;
-    for (int s = 0; s < ns; ++s) {
-      const float* c = C + (size_t)s * Mp * Np + (size_t)g * Np;
-      re += (double)c[n];
-      im += (double)c[nb + n];
+    if (g < npw && n < nb) {
+      for (int s = 0; s < ns; ++s) {
+        const float* c = C + (size_t)s * Mp * Np + (size_t)g * Np;
+        re += (double)c[n];
+        im += (double)c[nb + n];
+      }
     }
-    double2 h = hpsi[t];
-    h.x += re;
-    h.y += im;
-    hpsi[t] = h;
+    tre[r][tx] = re;
+    tim[r][tx] = im;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int n = n0 + r, g = g0 + tx;
+    if (n >= nb || g >= npw) continue;
+    double2* p = hpsi + (size_t)n * npw + g;
+    double2 h = *p;
+    h.x += tre[tx][r];
+    h.y += tim[tx][r];
+    *p = h;
   }
 }
 
@@ -441,17 +495,25 @@ int grid_of(size_t total) {
 }  // namespace
 
 static inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+// K layout of the inner-product operands: imaginary half at kh = pad4(K), rows of
+// Kp = pad(2 kh) floats
+static inline int kh_of(int K) { return pad_to(K, 4); }
+static inline int kcat(int K) { return pad_to(2 * kh_of(K), TC_BK); }
+static inline dim3 pack_grid(int Kp, int kh, int rows) {
+  const int items = (kh + (Kp - 2 * kh)) / 4;
+  return dim3((unsigned)std::max(1, std::min((items + 255) / 256, 64)), (unsigned)rows);
+}
 
 // Packed beta operands (both GEMMs); they depend only on beta, np and npw, so a
 // caller that applies the same operator repeatedly packs them once.
 size_t nonlocal_tc_beta_bytes(int np, int npw) {
-  const size_t Mp = pad_to(np, TC_BM), Kp = pad_to(2 * npw, TC_BK);
+  const size_t Mp = pad_to(np, TC_BM), Kp = kcat(npw);
   const size_t Mp2 = pad_to(npw, TC_BM), Kp2 = pad_to(2 * np, TC_BK);
   return 2 * Mp * Kp * 4 + 2 * Mp2 * Kp2 * 4 + 4 * 256;
 }
 
 size_t nonlocal_tc_bytes(int np, int nb, int npw) {
-  const size_t Mp = pad_to(np, TC_BM), Kp = pad_to(2 * npw, TC_BK), Np = pad_to(2 * nb, TC_BN);
+  const size_t Mp = pad_to(np, TC_BM), Kp = kcat(npw), Np = pad_to(2 * nb, TC_BN);
   const size_t Mp2 = pad_to(npw, TC_BM), Kp2 = pad_to(2 * np, TC_BK);
   const size_t ns1 = tc_gemm_splits((int)Mp, (int)Np, (int)Kp), ns2 = tc_gemm_splits((int)Mp2, (int)Np, (int)Kp2);
   size_t b = 0;
@@ -472,7 +534,7 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
     set_error("nonlocal_tc: workspace too small");
     return QE_EINVAL;
   }
-  const int Mp = pad_to(np, TC_BM), Kp = pad_to(2 * npw, TC_BK), Np = pad_to(2 * nb, TC_BN);
+  const int Mp = pad_to(np, TC_BM), Kp = kcat(npw), Np = pad_to(2 * nb, TC_BN), kh = kh_of(npw);
   const int Mp2 = pad_to(npw, TC_BM), Kp2 = pad_to(2 * np, TC_BK);
   const int ns1 = tc_gemm_splits(Mp, Np, Kp), ns2 = tc_gemm_splits(Mp2, Np, Kp2);
   char* p = static_cast<char*>(bpack);
@@ -492,15 +554,16 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
   double2* Q = (double2*)take((size_t)np * nb * 16);
   if (pack_beta) {
     ProfScope ps(pf, "k_pack_beta", st);
-    k_pack_rows<<<grid_of((size_t)Mp * Kp), 256, 0, st>>>((const double2*)beta, np, npw, Mp, Kp, ahi, alo);
-    k_pack_pad<<<grid_of((size_t)Mp2 * Kp2), 256, 0, st>>>(Mp2, Kp2, npw, 2 * np, a2hi, a2lo);
+    k_pack_rows<<<pack_grid(Kp, kh, Mp), 256, 0, st>>>((const double2*)beta, np, npw, kh, Kp, ahi, alo);
+    k_pack_pad<<<grid_of((size_t)(Mp2 - npw) * Kp2 + (size_t)npw * (Kp2 - 2 * np)), 256, 0, st>>>(
+        Mp2, Kp2, npw, 2 * np, a2hi, a2lo);
     dim3 gt((Mp2 + 31) / 32, (np + 31) / 32);
     k_pack_beta_t<<<gt, dim3(32, 8), 0, st>>>((const double2*)beta, np, npw, Mp2, Kp2, a2hi, a2lo);
     if (pf) pf->launches += 2;
   }
   {
     ProfScope ps(pf, "k_pack_psi", st);
-    k_pack_psi<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)psi, nb, npw, Np, Kp, bhi, blo);
+    k_pack_psi<<<pack_grid(Kp, kh, Np - nb), 256, 0, st>>>((const double2*)psi, nb, npw, kh, Kp, bhi, blo);
   }
   int rc = tc_gemm_tf32x3(ahi, alo, bhi, blo, Mp, Np, Kp, ns1, c1, status, st, pf);
   if (rc) return rc;
@@ -518,7 +581,8 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
   if (rc) return rc;
   {
     ProfScope ps(pf, "k_combine_h", st);
-    k_combine_h<<<grid_of((size_t)nb * npw), 256, 0, st>>>(c2, ns2, Mp2, Np, npw, nb, (double2*)hpsi);
+    k_combine_h<<<dim3((npw + 31) / 32, (nb + 31) / 32), dim3(32, 8), 0, st>>>(c2, ns2, Mp2, Np, npw,
+                                                                             nb, (double2*)hpsi);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -534,7 +598,7 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
 // [K][M] and B [K][N] dense.  FP32-accurate (TF32 x3) on the tensor cores.
 size_t tc_inner_bytes(int M, int N, int K) {
   if (M <= 0 || N <= 0) return 0;
-  const size_t Mp = pad_to(M, TC_BM), Kp = pad_to(2 * K, TC_BK), Np = pad_to(2 * N, TC_BN);
+  const size_t Mp = pad_to(M, TC_BM), Kp = kcat(K), Np = pad_to(2 * N, TC_BN);
   const size_t ns = tc_gemm_splits((int)Mp, (int)Np, (int)Kp);
   return 2 * Mp * Kp * 4 + 2 * Np * Kp * 4 + ns * Mp * Np * 4 + 8 * 256;
 }
@@ -553,7 +617,7 @@ int tc_inner(const double* A, const double* B, int M, int N, int K, double* C, i
     set_error("tc_inner: workspace too small");
     return QE_EINVAL;
   }
-  const int Mp = pad_to(M, TC_BM), Kp = pad_to(2 * K, TC_BK), Np = pad_to(2 * N, TC_BN);
+  const int Mp = pad_to(M, TC_BM), Kp = kcat(K), Np = pad_to(2 * N, TC_BN), kh = kh_of(K);
   const int ns = tc_gemm_splits(Mp, Np, Kp);
   char* p = static_cast<char*>(work);
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
@@ -564,8 +628,8 @@ int tc_inner(const double* A, const double* B, int M, int N, int K, double* C, i
   float* c = (float*)take((size_t)ns * Mp * Np * 4);
   {
     ProfScope ps(pf, "k_tc_pack", st);
-    k_pack_rows<<<grid_of((size_t)Mp * Kp), 256, 0, st>>>((const double2*)A, M, K, Mp, Kp, ahi, alo);
-    k_pack_psi<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)B, N, K, Np, Kp, bhi, blo);
+    k_pack_rows<<<pack_grid(Kp, kh, Mp), 256, 0, st>>>((const double2*)A, M, K, kh, Kp, ahi, alo);
+    k_pack_psi<<<pack_grid(Kp, kh, Np - N), 256, 0, st>>>((const double2*)B, N, K, kh, Kp, bhi, blo);
     if (pf) pf->launches += 1;
   }
   int rc = tc_gemm_tf32x3(ahi, alo, bhi, blo, Mp, Np, Kp, ns, c, status, st, pf);
@@ -596,7 +660,8 @@ int tc_outer(const double* A, const double* B, int M, int N, int K, double* C, i
   float* c = (float*)take((size_t)ns * Mp * Np * 4);
   {
     ProfScope ps(pf, "k_tc_pack", st);
-    k_pack_pad<<<grid_of((size_t)Mp * Kp), 256, 0, st>>>(Mp, Kp, M, 2 * K, ahi, alo);
+    k_pack_pad<<<grid_of((size_t)(Mp - M) * Kp + (size_t)M * (Kp - 2 * K)), 256, 0, st>>>(
+        Mp, Kp, M, 2 * K, ahi, alo);
     dim3 gt((Mp + 31) / 32, (K + 31) / 32);
     k_pack_beta_t<<<gt, dim3(32, 8), 0, st>>>((const double2*)A, K, M, Mp, Kp, ahi, alo);
     k_pack_q<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)B, K, N, Np, Kp, bhi, blo);
