@@ -127,6 +127,54 @@ __device__ bool grid_sync(const GridBar& b) {
   return s_ok != 0;
 }
 
+// Grid-wide barrier on a monotonic arrival counter (count zeroed by the host
+// before the launch; a launch uses either this or grid_sync): the k-th barrier
+// of the launch returns once count reaches k * gridDim.x.  Arrival is one
+// fence and one reduction without a return value, the wait one acquire poll
+// of the same word: fewer L2 round trips than the generation barrier.  Bounded
+// (2 s) like grid_sync.
+__device__ bool grid_sync_mono(const GridBar& b, unsigned k) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (gridDim.x == 1) return true;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(b.count, 1u);
+    const unsigned target = k * gridDim.x;
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
+      if (ld_acquire_gpu(b.count) >= target) break;
+      if ((it & 1023) == 1023) {
+        const unsigned long long t = gtime_ns();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > 2000000000ull) { atomicExch(b.err, 1); ok = 0; break; }
+        if (*(volatile int*)b.err) { ok = 0; break; }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Sums of two values over the block (at most 8 warps) with one barrier: warp
+// partials go to rb[par] and every thread adds them in the same order.  The
+// caller alternates par between consecutive calls, so a call never overwrites
+// partials that threads may still be reading from the previous one.
+__device__ __forceinline__ void block_sum2_1b(R& a, R& b, R (*rb)[2][8], int par) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) { rb[par][0][threadIdx.x >> 5] = a; rb[par][1][threadIdx.x >> 5] = b; }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  a = R(0);
+  b = R(0);
+  for (int w = 0; w < nw; ++w) { a += rb[par][0][w]; b += rb[par][1][w]; }
+}
+
 // Cholesky of the lower triangle, all columns in one launch (one barrier per
 // column).  The pivot column of step j is read from a contiguous copy (c0/c1,
 // n complex each, alternating): the warp that updates row r writes the new
@@ -505,30 +553,6 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* t
 // kTridRows rows per CTA.  Dynamic shared memory: (ceil(n / G) + 3) n complex.
 constexpr int kTridRows = 8;
 
-__device__ __forceinline__ void block_sum2(R& a, R& b, R* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) { sh[w] = a; sh[16 + w] = b; }
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  if (threadIdx.x < 32) {
-    R ta = threadIdx.x < nw ? sh[threadIdx.x] : R(0);
-    R tb = threadIdx.x < nw ? sh[16 + threadIdx.x] : R(0);
-    for (int o = 16; o > 0; o >>= 1) {
-      ta += __shfl_xor_sync(0xffffffffu, ta, o);
-      tb += __shfl_xor_sync(0xffffffffu, tb, o);
-    }
-    if (threadIdx.x == 0) { sh[32] = ta; sh[33] = tb; }
-  }
-  __syncthreads();
-  a = sh[32];
-  b = sh[33];
-}
-
 __global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* tau, R* e, R* dg,
                                                       z* refl, GridBar bar) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -540,7 +564,7 @@ __global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* t
   z* sv = rows + (size_t)nrmax * n;                  // reflector v (index i <-> row j+1+i)
   z* sw = sv + n;                                    // p, then w
   z* sx = sw + n;                                    // column to reduce (index i <-> row j+1+i)
-  __shared__ R sh[34];
+  __shared__ R rb[2][2][8];
   __shared__ z spart[8][kTridRows];
   for (int q = 0; q < nr; ++q) {
     const z* src = A + (size_t)(c + q * G) * lda;
@@ -549,7 +573,7 @@ __global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* t
   for (int i = tid; i < n - 1; i += nt) sx[i] = ldz(&A[(size_t)(1 + i) * lda]);
   if (c == 0 && tid == 0) dg[0] = ldz(&A[0]).x;
   // every CTA has read A: its rows 0..3 become the exchange vectors
-  if (!grid_sync(bar)) return;
+  if (!grid_sync_mono(bar, 1)) return;
   for (int j = 0; j < n - 1; ++j) {
     const int m = n - 1 - j, par = j & 1;
     z* xp = A + (size_t)(2 * par) * lda;       // p_r at [r]
@@ -558,7 +582,8 @@ __global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* t
     const z alpha = sx[0];
     R s = R(0);
     for (int i = 1 + tid; i < m; i += nt) s = fmar(sx[i].x, sx[i].x, fmar(sx[i].y, sx[i].y, s));
-    const R sigma = block_sum(s, sh);
+    R sigma = s, unused = R(0);
+    block_sum2_1b(sigma, unused, rb, 0);
     z t;
     R beta;
     if (sigma == R(0) && alpha.y == R(0)) {
@@ -615,7 +640,7 @@ __global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* t
       xp[r] = cmul(t, a);
       if (r >= j + 2) xc[r] = rows[(size_t)q * n + (j + 1)];
     }
-    if (!grid_sync(bar)) return;
+    if (!grid_sync_mono(bar, (unsigned)j + 2)) return;
     // w = p - (1/2) conj(tau) (v^+ p) v; the next column (rows j+2 ..)
     R sr = R(0), si = R(0);
     for (int i = tid; i < m; i += nt) {
@@ -625,7 +650,7 @@ __global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* t
       si = fmar(v.x, pr.y, fmar(-v.y, pr.x, si));
     }
     for (int i = tid; i < m - 1; i += nt) sx[i] = ldz(&xc[j + 2 + i]);
-    block_sum2(sr, si, sh);
+    block_sum2_1b(sr, si, rb, 1);
     const z coef = {R(0.5) * (t.x * sr + t.y * si), R(0.5) * (t.x * si - t.y * sr)};
     const z ncoef = {-coef.x, -coef.y};
     for (int i = tid; i < m; i += nt) sw[i] = zfma(ncoef, sv[i], sw[i]);
