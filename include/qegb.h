@@ -169,7 +169,7 @@ int qe_hpsi_noalloc(const qe_problem* prob, int precision, const double* psi,
  * (complex [nbnd][npw][2]); evals [nbnd] (Ry, ascending); resid [nbnd]
  * residual 2-norms (may be NULL); iters (may be NULL) the number of basis
  * expansions.  Converged when every ||H psi_n - e_n psi_n|| <= tol.
- * max_dim: largest basis (0 selects 4 * nbnd).  Returns QE_ENOCONV (with the
+ * max_dim: largest basis (0 selects 4 * nbnd below 64 bands, 3.5 * nbnd from 64 on).  Returns QE_ENOCONV (with the
  * best bands filled in) after max_iter expansions.  Arrays per prob->mem;
  * device work is ordered on `stream` and the call returns after it ends. */
 int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
@@ -247,7 +247,7 @@ enum { QE_SERVE_FAKE_SOLVER = 1 };   /* test hook: no GPU; a solve sleeps max_it
 int qe_serve_create(int device, size_t hbm_budget_bytes, int max_slots, int max_queue,
                     int flags, qe_srv** out);
 
-/* Queue a Davidson solve (as qe_davidson with the default max_dim, 4 nbnd).  Every array of
+/* Queue a Davidson solve (as qe_davidson with the default max_dim).  Every array of
  * prob and psi0 must be host memory (prob->mem = QE_HOST); they are copied
  * before the call returns.  *ticket identifies the request.  QE_EAGAIN when the
  * queue is full; QE_EINVAL when the request alone exceeds the budget. */

@@ -993,18 +993,20 @@ static int davidson_batch_run(qe_ctx* ctx, std::vector<DvSolve>& vs,
   return QE_OK;
 }
 
+// Default basis size.  Four nbnd for small blocks; with two (Quantum ESPRESSO's
+// default workspace) the iteration stalls on the SMALL cell (7 bands, band 7
+// close to band 8) and the FP64 C2 solve needs 48 instead of 19 iterations.
+// From 64 bands on, where the reduced eigenproblem's cost dominates an
+// iteration, 3.5 nbnd: on C2 (256 bands) the same 19 FP64 / 16 mixed
+// iterations as with 4 nbnd, 1.44 s against 1.48 s FP64 and 0.26 s against
+// 0.31 s mixed (3 nbnd: 28 FP64 iterations).  Callers can pass max_dim.
+int default_max_dim(int nb) { return nb < 64 ? 4 * nb : (7 * nb + 1) / 2; }
+
 }  // namespace qe
 
 using namespace qe;
 
 namespace {
-
-// Default basis size in units of nbnd.  Four: with two (Quantum ESPRESSO's
-// default workspace) the reduced problems are 8x cheaper, but the iteration
-// stalls on the SMALL cell (7 bands, band 7 close to band 8) and the FP64 C2
-// solve needs 48 instead of 19 iterations (2.35 s against 1.97 s); only the
-// mixed C2 solve gains (0.94 s against 1.38 s).  Callers can pass max_dim.
-constexpr int kDefaultDimFactor = 4;
 
 // Checks of one problem's arguments, its plan and operator, and the layout of
 // its Davidson workspace in `basis` / `red`.
@@ -1016,7 +1018,7 @@ int dv_setup(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int
   DV_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
   const int npw = P->h.npw;
   if (nb > npw) { set_error("%s: %d bands > %d plane waves", who, nb, npw); return QE_EINVAL; }
-  int md = max_dim > 0 ? max_dim : kDefaultDimFactor * nb;
+  int md = max_dim > 0 ? max_dim : default_max_dim(nb);
   if (md < 2 * nb) { set_error("%s: max_dim %d < 2 nbnd", who, md); return QE_EINVAL; }
   md = std::min(md, std::max(2 * nb, npw));
   if (md > kMaxDense) { set_error("%s: max_dim %d above %d", who, md, kMaxDense); return QE_EINVAL; }

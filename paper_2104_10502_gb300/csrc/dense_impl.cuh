@@ -752,6 +752,13 @@ __device__ __forceinline__ double start_component(unsigned long long k, unsigned
   return ((double)(x >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
 }
 
+// Inverse iterations per eigenvector.  The shift is the bisection eigenvalue
+// (within a few ulps of ||T||), so each solve multiplies the wanted component
+// by ~1/(eps ||T||) against 1/gap for the others: three leave ~(eps/gap_rel)^3
+// of any neighbour outside the shift's cluster (clusters are orthogonalised).
+// FP32 keeps a fourth (its eps is 1e9 times larger; the solves are cheap).
+constexpr int kInvIters = sizeof(R) == 8 ? 3 : 4;
+
 // One CTA per cluster of consecutive eigenvalues closer than ctol; the CTA whose
 // index starts a cluster handles all of it, the others return.  Vectors are rows
 // Y[k][0..n).  Shared memory: 6 arrays of n doubles (+ ints) for the factorisation.
@@ -777,7 +784,8 @@ __global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, 
   const R tiny = fmax(RealT<R>::eps * nrm, RealT<R>::tiny);
   for (int k = k0; k < k1; ++k) {
     const R lam = w[k];
-    // LU with partial pivoting of T - lam I (thread 0)
+    // LU with partial pivoting of T - lam I (thread 0; u0 holds the reciprocal
+    // pivots, so that the solves multiply)
     if (threadIdx.x == 0) {
       R c0 = d[0] - lam, c1 = n > 1 ? e[0] : R(0), c2 = R(0);
       for (int i = 0; i < n - 1; ++i) {
@@ -791,18 +799,19 @@ __global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, 
           s = 1;
         }
         if (fabs(c0) < tiny) c0 = c0 < R(0) ? -tiny : tiny;
-        const R mlt = n0 / c0;
-        u0[i] = c0; u1[i] = c1; u2[i] = c2; ml[i] = mlt; sw[i] = s;
+        const R rc = R(1) / c0;
+        const R mlt = n0 * rc;
+        u0[i] = rc; u1[i] = c1; u2[i] = c2; ml[i] = mlt; sw[i] = s;
         c0 = n1 - mlt * c1;
         c1 = n2 - mlt * c2;
         c2 = R(0);
       }
       if (fabs(c0) < tiny) c0 = c0 < R(0) ? -tiny : tiny;
-      u0[n - 1] = c0; u1[n - 1] = R(0); u2[n - 1] = R(0);
+      u0[n - 1] = R(1) / c0; u1[n - 1] = R(0); u2[n - 1] = R(0);
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = start_component(k, i);
     __syncthreads();
-    for (int it = 0; it < 4; ++it) {
+    for (int it = 0; it < kInvIters; ++it) {
       if (threadIdx.x == 0) {
         for (int i = 0; i < n - 1; ++i) {
           if (sw[i]) { const R t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
@@ -812,7 +821,7 @@ __global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, 
           R s = y[i];
           if (i + 1 < n) s -= u1[i] * y[i + 1];
           if (i + 2 < n) s -= u2[i] * y[i + 2];
-          y[i] = s / u0[i];
+          y[i] = s * u0[i];
         }
       }
       __syncthreads();

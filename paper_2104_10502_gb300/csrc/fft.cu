@@ -97,36 +97,107 @@ template <> struct PlaneLB<float> { static constexpr int threads = 256, minb = 2
 // different banks.
 __host__ __device__ inline int plane_ld(int n1) { return n1 | 1; }
 
+// FP32 planes also stage their V_loc plane in shared memory with cp.async,
+// issued first and waited for only before the multiply, so that its L2 latency
+// hides behind the inverse transforms -- when two CTAs per SM still fit (FP64
+// planes are FP64-pipe bound and their shared memory is full).
+template <typename T>
+constexpr bool kStageV = sizeof(T) == 4;
+constexpr size_t kStageVMaxBytes = 113 * 1024;
+
+// Byte offset of the staged V plane: after the plane, the twiddles and the
+// active-column table, rounded up to 16 bytes.
+template <typename T>
+__host__ __device__ inline size_t plane_v_offset(int n1, int n2, int nax) {
+  const size_t b = ((size_t)plane_ld(n1) * n2 + n1 + n2) * sizeof(cx<T>) + (size_t)nax * sizeof(int);
+  return (b + 15) & ~(size_t)15;
+}
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename T>
 __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* smem) {
   const int n1 = J.r1.n, n2 = J.r2.n, n3 = J.r3.n, nst = J.nst, nax = J.nax;
-  const int ld = plane_ld(n1);
+  const int ld = plane_ld(n1), nt = blockDim.x;
   cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
   cx<T>* tw1 = plane + (size_t)ld * n2;
   cx<T>* tw2 = tw1 + n1;
   int* ax = reinterpret_cast<int*>(tw2 + n2);
-  for (int i = threadIdx.x; i < ld * n2; i += blockDim.x) plane[i] = {T(0), T(0)};
-  for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = {T(J.tw1[2 * i]), T(J.tw1[2 * i + 1])};
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = {T(J.tw2[2 * i]), T(J.tw2[2 * i + 1])};
-  for (int i = threadIdx.x; i < nax; i += blockDim.x) ax[i] = J.ax[i];
+  const T* v = J.vp + (size_t)pz * n1 * n2;
+  T* sv = reinterpret_cast<T*>(smem + plane_v_offset<T>(n1, n2, nax));
+  const bool stage = kStageV<T> && J.stage_v;
+  if (stage) {
+    const int nv = n1 * n2;
+    if ((reinterpret_cast<size_t>(v) & 15) == 0) {
+      const int n16 = nv / 4;
+      for (int i = threadIdx.x; i < n16; i += nt) cp_async16(sv + 4 * i, v + 4 * i);
+      for (int i = 4 * n16 + threadIdx.x; i < nv; i += nt) cp_async4(sv + i, v + i);
+    } else {
+      for (int i = threadIdx.x; i < nv; i += nt) cp_async4(sv + i, v + i);
+    }
+  }
+  for (int i = threadIdx.x; i < ld * n2; i += nt) plane[i] = {T(0), T(0)};
+  for (int i = threadIdx.x; i < n1; i += nt) tw1[i] = {T(J.tw1[2 * i]), T(J.tw1[2 * i + 1])};
+  for (int i = threadIdx.x; i < n2; i += nt) tw2[i] = {T(J.tw2[2 * i]), T(J.tw2[2 * i + 1])};
+  for (int i = threadIdx.x; i < nax; i += nt) ax[i] = J.ax[i];
   __syncthreads();
+  // scatter the sticks of this plane: four loads in flight per thread
   cx<T>* Wp = J.W + ((size_t)b * n3 + pz) * nst;
-  for (int s = threadIdx.x; s < nst; s += blockDim.x) plane[J.st_y[s] * ld + J.st_x[s]] = Wp[s];
+  for (int s0 = threadIdx.x; s0 < nst; s0 += 4 * nt) {
+    int off[4];
+    cx<T> val[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = s0 + u * nt;
+      if (s < nst) { off[u] = J.st_y[s] * ld + J.st_x[s]; val[u] = Wp[s]; }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (s0 + u * nt < nst) plane[off[u]] = val[u];
+  }
   __syncthreads();
   // y on the active columns, then x on every row; consecutive threads take
   // consecutive lines in both passes
   fft_lines<T, +1, false, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2);
   fft_lines<T, +1, false, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1);
-  const T* v = J.vp + (size_t)pz * n1 * n2;
   const FastDiv fn1(n1);
-  for (int i = threadIdx.x; i < n1 * n2; i += blockDim.x) {
-    const int y = fn1.div(i), x = i - y * n1;
-    plane[y * ld + x] = cscale(plane[y * ld + x], v[i]);
+  if (stage) {
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1 * n2; i += nt) {
+      const int y = fn1.div(i), x = i - y * n1;
+      plane[y * ld + x] = cscale(plane[y * ld + x], sv[i]);
+    }
+  } else {
+    for (int i = threadIdx.x; i < n1 * n2; i += nt) {
+      const int y = fn1.div(i), x = i - y * n1;
+      plane[y * ld + x] = cscale(plane[y * ld + x], v[i]);
+    }
   }
   __syncthreads();
   fft_lines<T, -1, true, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1);
   fft_lines<T, -1, true, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2);
-  for (int s = threadIdx.x; s < nst; s += blockDim.x) Wp[s] = plane[J.st_y[s] * ld + J.st_x[s]];
+  for (int s0 = threadIdx.x; s0 < nst; s0 += 4 * nt) {
+    int off[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = s0 + u * nt;
+      if (s < nst) off[u] = J.st_y[s] * ld + J.st_x[s];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (s0 + u * nt < nst) Wp[s0 + u * nt] = plane[off[u]];
+  }
 }
 
 template <typename T>
@@ -241,9 +312,18 @@ size_t zsm_bytes(int n3, int spb) {
 }
 
 template <typename T>
+static bool plane_stages_v(const DevPlan& P) {
+  return kStageV<T> && plane_v_offset<T>(P.grid[0], P.grid[1], P.h.nax) +
+                               (size_t)P.grid[0] * P.grid[1] * sizeof(T) <= kStageVMaxBytes;
+}
+
+template <typename T>
 size_t psm_bytes(const DevPlan& P) {
-  return ((size_t)plane_ld(P.grid[0]) * P.grid[1] + P.grid[0] + P.grid[1]) * sizeof(cx<T>) +
-         (size_t)P.h.nax * sizeof(int);
+  const size_t base = ((size_t)plane_ld(P.grid[0]) * P.grid[1] + P.grid[0] + P.grid[1]) * sizeof(cx<T>) +
+                      (size_t)P.h.nax * sizeof(int);
+  return plane_stages_v<T>(P) ? plane_v_offset<T>(P.grid[0], P.grid[1], P.h.nax) +
+                                    (size_t)P.grid[0] * P.grid[1] * sizeof(T)
+                              : base;
 }
 
 template <typename T>
@@ -277,6 +357,7 @@ FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* v
   J.spb = sh.spb > 0 ? sh.spb : default_spb<T>(P.grid[2]);
   J.nsb = (J.nst + J.spb - 1) / J.spb;
   J.inv_n = 1.0 / ((double)P.grid[0] * P.grid[1] * P.grid[2]);
+  J.stage_v = plane_stages_v<T>(P) ? 1 : 0;
   return J;
 }
 

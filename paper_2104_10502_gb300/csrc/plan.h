@@ -98,7 +98,7 @@ struct FftJob {
   double* hpsi;
   const T* vp;
   cx<T>* W;
-  int nst, nax, npw, nb, b0, spb, nsb, pad;
+  int nst, nax, npw, nb, b0, spb, nsb, stage_v;   // stage_v: V plane staged in shared memory
   double inv_n;
 };
 

@@ -31,6 +31,7 @@
 namespace qe {
 int ctx_trim_public(qe_ctx* ctx);
 size_t davidson_footprint(int npw, int nb, int max_dim, int nproj, const int grid[3], int nst);
+int default_max_dim(int nb);
 }  // namespace qe
 
 namespace {
@@ -210,7 +211,7 @@ int qe_serve_submit(qe_srv* s, const qe_problem* prob, int precision, double tol
   r->max_iter = max_iter;
   const int nb = prob->nbnd;
   if (nb > h.npw) { qe::set_error("qe_serve_submit: more bands than plane waves"); return QE_EINVAL; }
-  r->bytes = qe::davidson_footprint(h.npw, nb, 4 * nb, prob->nproj, prob->grid, h.nst);
+  r->bytes = qe::davidson_footprint(h.npw, nb, qe::default_max_dim(nb), prob->nproj, prob->grid, h.nst);
   if (r->bytes > s->budget) {
     qe::set_error("qe_serve_submit: request needs %zu bytes, budget is %zu", r->bytes, s->budget);
     return QE_EINVAL;
