@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_precond(const z* r, const int* idx, con
   double s = 0.0;
   for (int g = threadIdx.x; g < npw; g += blockDim.x) {
     const double x = hd[g] - eb;
-    const double inv = 1.0 / sqrt(x * x + pmin2);
+    const double inv = rsqrt(x * x + pmin2);
     const z v = {rr[g].x * inv, rr[g].y * inv};
     dd[g] = v;
     s += v.x * v.x + v.y * v.y;

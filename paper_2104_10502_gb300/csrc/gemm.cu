@@ -93,30 +93,122 @@ k_gemm_inner(const double2* __restrict__ A, int lda, const double2* __restrict__
     }
 }
 
+// Narrow variant for N <= 8 (one new band block against the basis, a small
+// Gram matrix): tile 32 x 8, one output per thread (tm = tid % 32, tn = tid / 32),
+// same three-multiplication products and split-K partials as k_gemm_inner.
+// grid: (1, ceil(M/32), nsplit).
 template <typename T>
-__global__ void k_reduce_split(const cx<T>* __restrict__ part, int nsplit, int M, int N,
-                               double2* __restrict__ C, int ldc) {
-  const size_t total = (size_t)M * N;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    double sx = 0.0, sy = 0.0;
-    for (int s = 0; s < nsplit; ++s) {
-      const cx<T> p = part[(size_t)s * total + i];
-      sx += (double)p.x;
-      sy += (double)p.y;
+__global__ void __launch_bounds__(256)
+k_gemm_inner_n8(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
+                int M, int N, int K, int kchunk, cx<T>* __restrict__ part) {
+  __shared__ T Ar[IBK][IBM + 1], Ai[IBK][IBM + 1], As[IBK][IBM + 1];
+  __shared__ T Br[IBK][9], Bi[IBK][9], Bs[IBK][9];
+  const int tid = threadIdx.x;
+  const int tm = tid & 31, tn = tid >> 5;
+  const int m0 = blockIdx.y * IBM;
+  const int kb = blockIdx.z * kchunk;
+  const int ke = min(K, kb + kchunk);
+  T t1 = T(0), t2 = T(0), t3 = T(0);
+  for (int k0 = kb; k0 < ke; k0 += IBK) {
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+      const int idx = tid + rep * 256;
+      const int r = idx >> 4, kk = idx & 15;
+      const int gk = k0 + kk;
+      double2 a = make_double2(0.0, 0.0);
+      if (gk < ke && m0 + r < M) a = A[(size_t)(m0 + r) * lda + gk];
+      Ar[kk][r] = T(a.x);
+      Ai[kk][r] = T(a.y);
+      As[kk][r] = T(a.x) - T(a.y);
     }
-    const size_t m = i / N, n = i - m * N;
-    C[m * ldc + n] = make_double2(sx, sy);
+    if (tid < 8 * IBK) {
+      const int r = tid >> 4, kk = tid & 15;
+      const int gk = k0 + kk;
+      double2 b = make_double2(0.0, 0.0);
+      if (gk < ke && r < N) b = B[(size_t)r * ldb + gk];
+      Br[kk][r] = T(b.x);
+      Bi[kk][r] = T(b.y);
+      Bs[kk][r] = T(b.x) + T(b.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < IBK; ++kk) {
+      t1 = fma(Ar[kk][tm], Br[kk][tn], t1);
+      t2 = fma(Ai[kk][tm], Bi[kk][tn], t2);
+      t3 = fma(As[kk][tm], Bs[kk][tn], t3);
+    }
+    __syncthreads();
   }
+  const int m = m0 + tm, n = tn;
+  if (m < M && n < N)
+    part[(size_t)blockIdx.z * M * N + (size_t)m * N + n] = {t1 + t2, t3 - t1 + t2};
+}
+
+// C = sum over splits of the partials, in split order.  Eight threads per
+// output: thread q of an output adds splits q, q + 8, ... (two loads in
+// flight), then the eight sums are combined in lane order; the total is the
+// same for every launch (fixed order), independent of timing.
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduce_split(const cx<T>* __restrict__ part, int nsplit,
+                                                      int M, int N, double2* __restrict__ C,
+                                                      int ldc) {
+  const size_t total = (size_t)M * N;
+  const int q = threadIdx.x & 7;
+  const size_t o0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 3;
+  const size_t ostride = ((size_t)gridDim.x * blockDim.x) >> 3;
+  for (size_t i = o0; i < (total + ostride - 1) / ostride * ostride; i += ostride) {
+    const bool valid = i < total;
+    double sx = 0.0, sy = 0.0;
+    if (valid) {
+      int s = q;
+      for (; s + 8 < nsplit; s += 16) {
+        const cx<T> p0 = part[(size_t)s * total + i], p1 = part[(size_t)(s + 8) * total + i];
+        sx += (double)p0.x; sy += (double)p0.y;
+        sx += (double)p1.x; sy += (double)p1.y;
+      }
+      if (s < nsplit) {
+        const cx<T> p0 = part[(size_t)s * total + i];
+        sx += (double)p0.x; sy += (double)p0.y;
+      }
+    }
+    for (int o = 1; o < 8; o <<= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (valid && q == 0) {
+      const size_t m = i / N, n = i - m * N;
+      C[m * ldc + n] = make_double2(sx, sy);
+    }
+  }
+}
+
+static int reduce_blocks(size_t total) {
+  return (int)std::max<size_t>(1, std::min<size_t>((total * 8 + 255) / 256, 152 * 8));
 }
 
 static int inner_split(int M, int N, int K) {
   if (M <= 0 || N <= 0) return 1;
-  const int tiles = ((M + IBM - 1) / IBM) * ((N + IBN - 1) / IBN);
+  const int tiles = ((M + IBM - 1) / IBM) * (N <= 8 ? 1 : (N + IBN - 1) / IBN);
   int ns = (2 * 152 * 4 + tiles - 1) / tiles;  // aim for ~4 CTAs per SM
   const int maxs = std::max(1, K / 32);         // at least 32 k per split
   ns = std::max(1, std::min(ns, maxs));
   return ns;
+}
+
+template <typename T>
+static void launch_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+                         int kchunk, int nsplit, void* part, cudaStream_t st) {
+  if (N <= 8) {
+    dim3 g(1, (M + IBM - 1) / IBM, nsplit);
+    k_gemm_inner_n8<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+                                           reinterpret_cast<const double2*>(B), ldb, M, N, K, kchunk,
+                                           reinterpret_cast<cx<T>*>(part));
+  } else {
+    dim3 g((N + IBN - 1) / IBN, (M + IBM - 1) / IBM, nsplit);
+    k_gemm_inner<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+                                        reinterpret_cast<const double2*>(B), ldb, M, N, K, kchunk,
+                                        reinterpret_cast<cx<T>*>(part));
+  }
 }
 
 size_t gemm_inner_scratch(int M, int N, int K, size_t elem_bytes) {
@@ -136,19 +228,16 @@ int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N,
   int kchunk = (K + ns - 1) / ns;
   kchunk = (kchunk + IBK - 1) / IBK * IBK;
   const int nsplit = std::max(1, (K + kchunk - 1) / kchunk);
-  dim3 g((N + IBN - 1) / IBN, (M + IBM - 1) / IBM, nsplit);
   int rc;
   {
   ProfScope ps(pf, "k_gemm_inner", st);
-  k_gemm_inner<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
-                                      reinterpret_cast<const double2*>(B), ldb, M, N, K, kchunk,
-                                      reinterpret_cast<cx<T>*>(part));
+  launch_inner<T>(A, lda, B, ldb, M, N, K, kchunk, nsplit, part, st);
   rc = check_launch("k_gemm_inner");
   }
   if (rc) return rc;
   ProfScope ps(pf, "k_reduce_split", st);
   const size_t total = (size_t)M * N;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+  const int blocks = reduce_blocks(total);
   k_reduce_split<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<T>*>(part), nsplit, M, N,
                                             reinterpret_cast<double2*>(C), ldc);
   return check_launch("k_reduce_split");
@@ -169,19 +258,16 @@ int gemm_inner_bounded(const double* A, int lda, const double* B, int ldb, int M
   int kchunk = (K + ns - 1) / ns;
   kchunk = (kchunk + IBK - 1) / IBK * IBK;
   const int nsplit = std::max(1, (K + kchunk - 1) / kchunk);
-  dim3 g((N + IBN - 1) / IBN, (M + IBM - 1) / IBM, nsplit);
   int rc;
   {
   ProfScope ps(pf, "k_gemm_inner", st);
-  k_gemm_inner<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
-                                      reinterpret_cast<const double2*>(B), ldb, M, N, K, kchunk,
-                                      reinterpret_cast<cx<T>*>(part));
+  launch_inner<T>(A, lda, B, ldb, M, N, K, kchunk, nsplit, part, st);
   rc = check_launch("k_gemm_inner");
   }
   if (rc) return rc;
   ProfScope ps(pf, "k_reduce_split", st);
   const size_t total = (size_t)M * N;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+  const int blocks = reduce_blocks(total);
   k_reduce_split<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<T>*>(part), nsplit, M, N,
                                             reinterpret_cast<double2*>(C), ldc);
   return check_launch("k_reduce_split");
@@ -269,6 +355,56 @@ k_gemm_outer(const double2* __restrict__ A, int lda, const double2* __restrict__
   }
 }
 
+// Narrow variant for N <= 8: tile 32 x 8, one output per thread (tm = tid % 32,
+// tn = tid / 32), so that a band block of a small problem still spreads over
+// ceil(M/32) CTAs.  grid: (ceil(M/32), 1).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gemm_outer_n8(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
+                int M, int N, int K, double2* __restrict__ C, int ldc, int alpha_neg, int beta) {
+  __shared__ T Ar[OBK][32], Ai[OBK][32], As[OBK][32];
+  __shared__ T Br[OBK][9], Bi[OBK][9], Bs[OBK][9];
+  const int tid = threadIdx.x;
+  const int tm = tid & 31, tn = tid >> 5;
+  const int m0 = blockIdx.x * 32;
+  T t1 = T(0), t2 = T(0), t3 = T(0);
+  for (int k0 = 0; k0 < K; k0 += OBK) {
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+      const int idx = tid + rep * 256;
+      const int kk = idx >> 5, mm = idx & 31;
+      double2 a = make_double2(0.0, 0.0);
+      if (k0 + kk < K && m0 + mm < M) a = A[(size_t)(k0 + kk) * lda + m0 + mm];
+      Ar[kk][mm] = T(a.x);
+      Ai[kk][mm] = T(a.y);
+      As[kk][mm] = T(a.x) + T(a.y);
+    }
+    if (tid < OBK * 8) {
+      const int kk = tid >> 3, nn = tid & 7;
+      double2 b = make_double2(0.0, 0.0);
+      if (k0 + kk < K && nn < N) b = B[(size_t)(k0 + kk) * ldb + nn];
+      Br[kk][nn] = T(b.x);
+      Bi[kk][nn] = T(b.y);
+      Bs[kk][nn] = T(b.x) + T(b.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < OBK; ++kk) {
+      t1 = fma(Ar[kk][tm], Br[kk][tn], t1);
+      t2 = fma(Ai[kk][tm], Bi[kk][tn], t2);
+      t3 = fma(As[kk][tm], Bs[kk][tn], t3);
+    }
+    __syncthreads();
+  }
+  const int m = m0 + tm, n = tn;
+  if (m >= M || n >= N) return;
+  double2* c = C + (size_t)n * ldc + m;
+  double2 v = make_double2((double)(t1 - t2), (double)(t3 - t1 - t2));
+  if (alpha_neg) { v.x = -v.x; v.y = -v.y; }
+  if (beta) { const double2 o = *c; v.x += o.x; v.y += o.y; }
+  *c = v;
+}
+
 template <typename T>
 int gemm_outer_ab(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
                   double* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf) {
@@ -278,6 +414,13 @@ int gemm_outer_ab(const double* A, int lda, const double* B, int ldb, int M, int
     return QE_EINVAL;
   }
   ProfScope ps(pf, "k_gemm_outer", st);
+  if (N <= 8) {
+    k_gemm_outer_n8<T><<<(M + 31) / 32, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+                                                       reinterpret_cast<const double2*>(B), ldb, M, N,
+                                                       K, reinterpret_cast<double2*>(C), ldc,
+                                                       alpha_neg, beta);
+    return check_launch("k_gemm_outer");
+  }
   dim3 g((M + OBM - 1) / OBM, (N + OBN - 1) / OBN);
   k_gemm_outer<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
                                       reinterpret_cast<const double2*>(B), ldb, M, N, K,
