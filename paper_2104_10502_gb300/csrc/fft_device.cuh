@@ -144,16 +144,18 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
     cx<T> v[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = p[q * step];
-    // M == 1 (last DIF / first DIT stage): every twiddle is 1, skip the products
+    // j == 0 (every butterfly when M == 1): every twiddle is 1, skip the
+    // products; consecutive threads share j in the line-fast passes, so the
+    // branch is uniform across most warps
     if (DIT) {
-      if (M > 1) {
+      if (j != 0) {
 #pragma unroll
         for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
       }
       dftR<T, SIGN, R>(v);
     } else {
       dftR<T, SIGN, R>(v);
-      if (M > 1) {
+      if (j != 0) {
 #pragma unroll
         for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
       }
