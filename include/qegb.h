@@ -50,6 +50,20 @@ enum {
 };
 
 enum { QE_FP64 = 0, QE_MIXED = 1 };   /* arithmetic of the GPU path */
+/* Flags or-ed into `precision` (k = 0 only; Sec. 3.3 notes the Gamma-point
+ * trick of real wavefunctions, which halves the FFT work):
+ *  QE_GAMMA (qe_hpsi): every band is real in r, c(-G) = conj c(G); two bands
+ *    share each FFT and the projections are taken real.  The result is H
+ *    applied to that part of each band.  Ignored when k != 0.
+ *  With qe_davidson and qe_davidson_batch, a k = 0 solve whose projectors
+ *    are real in r (B_i(-G) = conj B_i(G) within 1e-12 of max |B|) can keep
+ *    every basis vector real in r: the start bands are replaced by their
+ *    larger real-in-r part, H runs as with QE_GAMMA, and the returned
+ *    eigenvectors are real in r (same eigenvalues).  This is the default for
+ *    QE_FP64; QE_MIXED solves use it only with QE_GAMMA (their FP32 phase
+ *    converges in fewer iterations on complex bands).
+ *  QE_NO_GAMMA (qe_davidson, qe_davidson_batch): never. */
+enum { QE_GAMMA = 0x100, QE_NO_GAMMA = 0x200 };
 enum { QE_HOST = 0, QE_DEVICE = 1 };  /* where the caller's arrays live */
 
 typedef struct qe_ctx qe_ctx;
@@ -132,7 +146,8 @@ int qe_beta_gaussian(qe_ctx* ctx, const double lat[9], const double k[3],
  *   psi(r_j) = sum_G c_G e^{iG.r_j},  N = N1 N2 N3.
  * psi, hpsi: complex [nbnd][npw][2], host or device per prob->mem (hpsi is
  * overwritten).  precision: QE_FP64 (float64 throughout) or QE_MIXED (FP32
- * FFTs and FP32 projector products, float64 in and out).
+ * FFTs and FP32 projector products, float64 in and out), optionally or-ed
+ * with QE_GAMMA (k = 0: bands real in r, two per FFT).
  * Errors: QE_EINVAL for bad sizes or a grid smaller than the sphere needs. */
 int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
             const double* psi, double* hpsi, void* stream);

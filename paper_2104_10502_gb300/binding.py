@@ -20,6 +20,9 @@ LIB_PATH = os.path.join(_PKG, "libqegb.so")
 QE_OK, QE_EINVAL, QE_ENOMEM, QE_ENOCONV, QE_EAGAIN, QE_PENDING, QE_ETIMEOUT, QE_ECUDA, \
     QE_ECANCELED = range(9)
 QE_FP64, QE_MIXED = 0, 1
+# flags or-ed into precision (k = 0): QE_GAMMA for hpsi (bands real in r, two per FFT),
+# QE_NO_GAMMA for davidson (keep complex bands)
+QE_GAMMA, QE_NO_GAMMA = 0x100, 0x200
 QE_HOST, QE_DEVICE = 0, 1
 
 SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",

@@ -143,7 +143,7 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
   // one allocation: doubles first, then ints
   size_t nd = h.npw;
   for (int c = 0; c < 3; ++c) nd += 2 * (size_t)grid[c];
-  size_t ni = (h.nst + 1) + 3 * (size_t)h.npw + 2 * (size_t)h.nst + h.nax;
+  size_t ni = (h.nst + 1) + 3 * (size_t)h.npw + 2 * (size_t)h.nst + h.nax + h.mg.size();
   for (int c = 0; c < 3; ++c) ni += grid[c];
   const size_t bytes = nd * sizeof(double) + ni * sizeof(int);
   if (cudaMallocAsync(&P->block, bytes, ctx->cur) != cudaSuccess) {
@@ -168,6 +168,7 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
   const size_t o_x = put_i(h.st_x.data(), h.nst);
   const size_t o_y = put_i(h.st_y.data(), h.nst);
   const size_t o_ax = put_i(h.ax.data(), h.nax);
+  const size_t o_mg = put_i(h.mg.data(), h.mg.size());
   size_t o_perm[3];
   for (int c = 0; c < 3; ++c) o_perm[c] = put_i(perm[c].data(), perm[c].size());
   if (cudaMemcpyAsync(P->block, host.data(), bytes, cudaMemcpyHostToDevice, ctx->cur) != cudaSuccess ||
@@ -188,6 +189,7 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
   P->st_x = di + o_x;
   P->st_y = di + o_y;
   P->ax = di + o_ax;
+  P->mg = h.gamma ? di + o_mg : nullptr;
   ctx->plans.push_back(std::move(P));
   *out = ctx->plans.back().get();
   return QE_OK;
@@ -235,21 +237,26 @@ int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView
   return QE_OK;
 }
 
+// pair: the bands are real in r (k = 0 plan); two share each FFT and the
+// projections are taken real.
 template <typename T>
 static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const double* psi,
-                       double* hpsi, int nb, cudaStream_t st) {
+                       double* hpsi, int nb, cudaStream_t st, bool pair) {
   const int npw = P.h.npw;
+  pair = pair && P.h.gamma;
   const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
   QE_TRY(ctx->vp.ensure(ngrid * sizeof(T)));
   QE_TRY(launch_vperm<T>(P, op.vloc, (T*)ctx->vp.p, st, &ctx->prof));
   const size_t per_band = stick_bytes(P, 1, 2 * sizeof(T));
-  int nbc = (int)std::max<size_t>(1, ctx->stick_budget / std::max<size_t>(per_band, 1));
-  nbc = std::min(nbc, nb);
-  QE_TRY(ctx->sticks.ensure(stick_bytes(P, nbc, 2 * sizeof(T))));
+  const int per_fft = pair ? 2 : 1;   // bands per FFT
+  int nfb = (int)std::max<size_t>(1, ctx->stick_budget / std::max<size_t>(per_band, 1));
+  nfb = std::min(nfb, (nb + per_fft - 1) / per_fft);
+  const int nbc = nfb * per_fft;
+  QE_TRY(ctx->sticks.ensure(stick_bytes(P, nfb, 2 * sizeof(T))));
   for (int b0 = 0; b0 < nb; b0 += nbc) {
     const int n = std::min(nbc, nb - b0);
     QE_TRY(launch_local_kinetic<T>(P, psi, hpsi, (const T*)ctx->vp.p, ctx->sticks.p, b0, n, st,
-                                   &ctx->prof));
+                                   &ctx->prof, pair ? 1 : 0));
   }
   if (op.nproj > 0 && sizeof(T) == sizeof(float)) {
     // mixed precision: projector products on the tensor cores (TF32x3 split)
@@ -265,7 +272,8 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     if (ctx->tc_beta.p != before || ctx->tc_beta.bytes != before_bytes) ctx->tc_beta_tag = 0;
     const bool pack = ctx->tc_beta_tag == 0 || ctx->tc_beta_tag != op.tag;
     QE_TRY(nonlocal_tc(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->tc_beta.p, pack,
-                       ctx->tc_work.p, ctx->tc_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof));
+                       ctx->tc_work.p, ctx->tc_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof,
+                       pair));
     ctx->tc_beta_tag = op.tag;
   } else if (op.nproj > 0 && oz_worth(op.nproj, nb, npw)) {
     // FP64: FP64-accurate projector products on the BF16 tensor cores (Ozaki slices)
@@ -281,7 +289,8 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     if (ctx->oz_beta.p != before || ctx->oz_beta.bytes != before_bytes) ctx->oz_beta_tag = 0;
     const bool slice = ctx->oz_beta_tag == 0 || ctx->oz_beta_tag != op.tag;
     QE_TRY(nonlocal_oz(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->oz_beta.p, slice,
-                       ctx->oz_work.p, ctx->oz_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof));
+                       ctx->oz_work.p, ctx->oz_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof,
+                       pair));
     ctx->oz_beta_tag = op.tag;
   } else if (op.nproj > 0) {
     const int np = op.nproj;
@@ -291,7 +300,8 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(ctx->part.ensure(sb));
     QE_TRY(gemm_inner<T>(op.beta, npw, psi, npw, np, nb, npw, (double*)ctx->proj.p, nb,
                          ctx->part.p, ctx->part.bytes, st, &ctx->prof));
-    QE_TRY(dmul(op.dmat, (const double*)ctx->proj.p, (double*)ctx->projd.p, np, nb, st, &ctx->prof));
+    QE_TRY(dmul(op.dmat, (const double*)ctx->proj.p, (double*)ctx->projd.p, np, nb, st, &ctx->prof,
+                pair));
     QE_TRY(gemm_outer<T>(op.beta, npw, (const double*)ctx->projd.p, nb, npw, nb, np, hpsi, npw, 1, st,
                          &ctx->prof));
   }
@@ -312,10 +322,10 @@ int tc_check(qe_ctx* ctx, cudaStream_t st) {
 }
 
 int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, const double* psi,
-              double* hpsi, int nb, cudaStream_t st) {
+              double* hpsi, int nb, cudaStream_t st, bool pair) {
   if (nb == 0) return QE_OK;
-  if (precision == QE_FP64) return hpsi_device<double>(ctx, P, op, psi, hpsi, nb, st);
-  return hpsi_device<float>(ctx, P, op, psi, hpsi, nb, st);
+  if (precision == QE_FP64) return hpsi_device<double>(ctx, P, op, psi, hpsi, nb, st, pair);
+  return hpsi_device<float>(ctx, P, op, psi, hpsi, nb, st, pair);
 }
 
 }  // namespace qe
@@ -441,6 +451,8 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
   clear_error();
   if (!ctx) { set_error("qe_hpsi: null context"); return QE_EINVAL; }
   QE_TRY(check_problem(prob, "qe_hpsi"));
+  const bool pair = (precision & QE_GAMMA) != 0;
+  precision &= ~QE_GAMMA;
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_hpsi: bad precision"); return QE_EINVAL; }
   if (prob->nbnd > 0 && (!psi || !hpsi)) { set_error("qe_hpsi: null psi/hpsi"); return QE_EINVAL; }
   QE_CU(cudaSetDevice(ctx->device));
@@ -461,7 +473,7 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
     dpsi = (const double*)ctx->h_psi.p;
     dhpsi = (double*)ctx->h_hpsi.p;
   }
-  QE_TRY(hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st));
+  QE_TRY(hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st, pair));
   if (prob->mem == QE_HOST) {
     if (nb > 0)
       QE_CU(cudaMemcpyAsync(hpsi, dhpsi, nel * sizeof(double), cudaMemcpyDeviceToHost, st));

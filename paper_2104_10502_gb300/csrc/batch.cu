@@ -48,12 +48,14 @@ struct BatchLayout {
   size_t np_max_part = 0, np_max_proj = 0;   // nonlocal workspaces (largest problem)
   size_t tc_work = 0, tc_beta = 0;
   size_t oz_work = 0, oz_beta = 0;
+  std::vector<char> pair;   // per problem: bands taken two per FFT (real in r, k = 0)
 };
 
 template <typename T>
 static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem* probs,
                          const double* const* psi, double* const* hpsi, BatchLayout& L,
-                         std::vector<char>& host_tables, cudaStream_t st) {
+                         std::vector<char>& host_tables, cudaStream_t st,
+                         const char* pair = nullptr) {
   W.cur = st;
   L = BatchLayout();
   size_t off = 0;
@@ -74,6 +76,7 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
     BT_TRY(resolve_operator(ctx, pr, *P, op, st));
     L.plans.push_back(P);
     L.ops.push_back(op);
+    L.pair.push_back(pair && pair[p] && P->h.gamma ? 1 : 0);
     const size_t ngrid = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
     L.vp_off.push_back(off);
     off += up256(ngrid * sizeof(T));
@@ -127,9 +130,9 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
     const DevPlan& P = *L.plans[p];
     const FftShape sh = tuned_shape(P, sizeof(T));
     jobs[p] = make_job<T>(P, psi[p], hpsi[p], reinterpret_cast<const T*>(base + L.vp_off[p]),
-                          base + L.w_off[p], 0, probs[p].nbnd, sh);
-    pre[p + 1] = pre[p] + probs[p].nbnd * jobs[p].nsb;
-    pre[nprob + 1 + p + 1] = pre[nprob + 1 + p] + probs[p].nbnd * P.grid[2];
+                          base + L.w_off[p], 0, probs[p].nbnd, sh, L.pair[p]);
+    pre[p + 1] = pre[p] + jobs[p].nb * jobs[p].nsb;   // FFT bands (band pairs with pair)
+    pre[nprob + 1 + p + 1] = pre[nprob + 1 + p] + jobs[p].nb * P.grid[2];
   }
   return QE_OK;
 }
@@ -148,16 +151,17 @@ static int batch_launch(BatchWork& W, int nprob, const qe_problem* probs, const 
     const OpView& op = L.ops[p];
     const int nb = probs[p].nbnd, np = op.nproj, npw = L.plans[p]->h.npw;
     if (np <= 0 || nb <= 0) continue;
+    const bool rp = L.pair[p] != 0;
     if (sizeof(T) == sizeof(float)) {
       BT_TRY(nonlocal_tc(op.beta, op.dmat, psi[p], hpsi[p], np, nb, npw, W.tc_beta.p, true,
-                         W.tc_work.p, W.tc_work.bytes, (int*)W.tc_status.p, st, pf));
+                         W.tc_work.p, W.tc_work.bytes, (int*)W.tc_status.p, st, pf, rp));
     } else if (oz_worth(np, nb, npw)) {
       BT_TRY(nonlocal_oz(op.beta, op.dmat, psi[p], hpsi[p], np, nb, npw, W.oz_beta.p, true,
-                         W.oz_work.p, W.oz_work.bytes, (int*)W.tc_status.p, st, pf));
+                         W.oz_work.p, W.oz_work.bytes, (int*)W.tc_status.p, st, pf, rp));
     } else {
       BT_TRY(gemm_inner<T>(op.beta, npw, psi[p], npw, np, nb, npw, (double*)W.proj.p, nb,
                            W.part.p, W.part.bytes, st, pf));
-      BT_TRY(dmul(op.dmat, (const double*)W.proj.p, (double*)W.projd.p, np, nb, st, pf));
+      BT_TRY(dmul(op.dmat, (const double*)W.proj.p, (double*)W.projd.p, np, nb, st, pf, rp));
       BT_TRY(gemm_outer<T>(op.beta, npw, (const double*)W.projd.p, nb, npw, nb, np, hpsi[p], npw, 1,
                            st, pf));
     }
@@ -167,10 +171,11 @@ static int batch_launch(BatchWork& W, int nprob, const qe_problem* probs, const 
 
 template <typename T>
 static int hpsi_batch_t(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem* probs,
-                        const double* const* psi, double* const* hpsi, cudaStream_t st) {
+                        const double* const* psi, double* const* hpsi, cudaStream_t st,
+                        const char* pair) {
   BatchLayout L;
   std::vector<char> tables;
-  BT_TRY(batch_prepare<T>(ctx, W, nprob, probs, psi, hpsi, L, tables, st));
+  BT_TRY(batch_prepare<T>(ctx, W, nprob, probs, psi, hpsi, L, tables, st, pair));
   char* base = static_cast<char*>(W.ws.p);
   BT_CU(cudaMemcpyAsync(base + L.jobs_off, tables.data(), tables.size(), cudaMemcpyHostToDevice, st));
   BT_CU(cudaStreamSynchronize(st));   // the host tables are freed on return
@@ -187,10 +192,11 @@ static int hpsi_batch_t(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem* 
 BatchWork& ctx_batch_work(qe_ctx* ctx);
 
 int hpsi_batch_core(qe_ctx* ctx, int nprob, const qe_problem* probs, int precision,
-                    const double* const* psi, double* const* hpsi, cudaStream_t st) {
+                    const double* const* psi, double* const* hpsi, cudaStream_t st,
+                    const char* pair) {
   BatchWork& W = ctx_batch_work(ctx);
-  if (precision == QE_FP64) return hpsi_batch_t<double>(ctx, W, nprob, probs, psi, hpsi, st);
-  return hpsi_batch_t<float>(ctx, W, nprob, probs, psi, hpsi, st);
+  if (precision == QE_FP64) return hpsi_batch_t<double>(ctx, W, nprob, probs, psi, hpsi, st, pair);
+  return hpsi_batch_t<float>(ctx, W, nprob, probs, psi, hpsi, st, pair);
 }
 
 // The context's batch workspace (created on first use, freed with the context).

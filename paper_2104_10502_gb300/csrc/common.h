@@ -53,6 +53,11 @@ struct PlanHost {
   std::vector<int> ax;            // [nax] x slots holding at least one stick
   std::vector<int> g_st;          // [npw] stick of plane wave g
   std::vector<int> g_z;           // [npw] natural z slot of plane wave g
+  // k = 0: the sphere is symmetric under G -> -G.  gamma = 1 when the sticks
+  // are ordered in mirror pairs (2i, 2i+1) = ((x, y), (-x, -y)) with the
+  // self-mirror stick (0, 0) last; mg[g] is the sphere index of -G.
+  int gamma = 0;
+  std::vector<int> mg;            // [npw] when gamma
 };
 int build_plan_host(const double lat[9], const double k[3], double ecut,
                     const int grid[3], PlanHost& out);

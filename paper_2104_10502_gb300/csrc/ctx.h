@@ -65,15 +65,19 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
 int check_problem(const qe_problem* pr, const char* who);
 int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView& op,
                      cudaStream_t st);
-// H psi for nb bands already on the device.
+// H psi for nb bands already on the device.  pair (k = 0 plans): the bands are
+// real in r, psi(-G) = conj psi(G); two share each FFT and the projections are
+// taken real, so the result is H applied to that part of each band.
 int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, const double* psi,
-              double* hpsi, int nb, cudaStream_t st);
+              double* hpsi, int nb, cudaStream_t st, bool pair = false);
 // Status word of the tensor-core kernels since the last check (synchronises on
 // `st`); QE_ETIMEOUT with a message if a bounded wait ran out, then resets it.
 int tc_check(qe_ctx* ctx, cudaStream_t st);
-// Batched H|psi> of device-resident problems on stream st (batch.cu).
+// Batched H|psi> of device-resident problems on stream st (batch.cu); pair
+// (per problem, may be null): as hpsi_core's.
 int hpsi_batch_core(qe_ctx* ctx, int nprob, const qe_problem* probs, int precision,
-                    const double* const* psi, double* const* hpsi, cudaStream_t st);
+                    const double* const* psi, double* const* hpsi, cudaStream_t st,
+                    const char* pair = nullptr);
 void ctx_batch_release(qe_ctx* ctx);
 
 }  // namespace qe

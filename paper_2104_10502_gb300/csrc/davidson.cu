@@ -172,6 +172,85 @@ static int grid_for(size_t total) {
   return (int)std::max<size_t>(1, std::min<size_t>((total + 255) / 256, 152 * 8));
 }
 
+// ---- k = 0: bands real in r ---------------------------------------------------
+// Row r of X becomes the larger of its two real-in-r parts,
+//   A = (X + conj X(-G)) / 2   and   B = (X - conj X(-G)) / 2i   (X = A + i B),
+// so that no start vector can vanish.  One CTA per row; every mirror pair
+// (g, -g) is read and written by one thread.
+__global__ void __launch_bounds__(256) k_gamma_start(z* X, int npw, const int* __restrict__ mg) {
+  __shared__ double sh[33];
+  z* x = X + (size_t)blockIdx.x * npw;
+  double na = 0.0, nbv = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const z a = x[g], b = x[mg[g]];
+    const double ax = 0.5 * (a.x + b.x), ay = 0.5 * (a.y - b.y);   // A_g
+    const double bx = 0.5 * (a.y + b.y), by = 0.5 * (b.x - a.x);   // B_g
+    na += ax * ax + ay * ay;
+    nbv += bx * bx + by * by;
+  }
+  na = dv_block_sum(na, sh);
+  nbv = dv_block_sum(nbv, sh);
+  const bool use_a = na >= nbv;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const int m = mg[g];
+    if (m < g) continue;
+    const z a = x[g], b = x[m];
+    z c = use_a ? z{0.5 * (a.x + b.x), 0.5 * (a.y - b.y)} : z{0.5 * (a.y + b.y), 0.5 * (b.x - a.x)};
+    if (m == g) c.y = 0.0;
+    x[g] = c;
+    x[m] = {c.x, -c.y};
+  }
+}
+
+// X <- (X + conj X(-G)) / 2 for rows [0, rows): the real-in-r part.
+__global__ void k_gamma_sym(z* X, int rows, int npw, const int* __restrict__ mg) {
+  const size_t total = (size_t)rows * npw;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / npw), g = (int)(t % npw);
+    const int m = mg[g];
+    if (m < g) continue;
+    z* x = X + (size_t)r * npw;
+    const z a = x[g], b = x[m];
+    z c = {0.5 * (a.x + b.x), 0.5 * (a.y - b.y)};
+    if (m == g) c.y = 0.0;
+    x[g] = c;
+    x[m] = {c.x, -c.y};
+  }
+}
+
+// Im C = 0 on a rows x cols block (inner products of vectors real in r are real).
+__global__ void k_real_part(z* C, int rows, int cols, int ldc) {
+  const size_t total = (size_t)rows * cols;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x)
+    C[(t / cols) * ldc + t % cols].y = 0.0;
+}
+
+// Largest |beta_i(-G) - conj beta_i(G)| and largest |beta_i(G)|, as the bit
+// patterns of non-negative doubles (ordered like the values) in out[0], out[1].
+__global__ void k_beta_mirror(const z* __restrict__ beta, int np, int npw, const int* __restrict__ mg,
+                              unsigned long long* out) {
+  double dmax = 0.0, bmax = 0.0;
+  const size_t total = (size_t)np * npw;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = t / npw;
+    const int g = (int)(t % npw);
+    const z a = beta[t], b = beta[i * npw + mg[g]];
+    dmax = fmax(dmax, fmax(fabs(b.x - a.x), fabs(b.y + a.y)));
+    bmax = fmax(bmax, fmax(fabs(a.x), fabs(a.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(dmax));
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(bmax));
+  }
+}
+
 struct DvState {
   int npw = 0, nb = 0, max_dim = 0, np = 0;
   z *V = nullptr, *HV = nullptr, *Psi = nullptr, *HPsi = nullptr, *R = nullptr, *D = nullptr,
@@ -189,6 +268,11 @@ struct DvState {
   // the mixed path's subspace products on the tensor cores (TF32 x3)
   void* tc = nullptr;
   size_t tc_bytes = 0;
+  // k = 0 with real projectors: every basis vector real in r (psi(-G) =
+  // conj psi(G), mg the sphere index of -G); two bands share each FFT and the
+  // reduced matrices are real
+  bool gamma = false;
+  const int* mg = nullptr;
 };
 
 // Scratch of the mixed path's tensor-core subspace products (largest inner and
@@ -328,8 +412,8 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
 static int* dv_tc_status(const DvState& S) { return S.dw.status + 12; }
 
 template <typename T>
-static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
-                cudaStream_t st, Prof* pf) {
+static int gram_any(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
+                    cudaStream_t st, Prof* pf) {
   if (sizeof(T) == sizeof(float) && S.tc && tc_worth(m, n, S.npw))
     return tc_inner((const double*)A, (const double*)B, m, n, S.npw, (double*)C, ldc, S.tc,
                     S.tc_bytes, dv_tc_status(S), st, pf);
@@ -340,10 +424,21 @@ static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, in
                        ldc, S.part, S.part_bytes, st, pf);
 }
 
+// C = A^+ B over the plane waves; real for vectors real in r (k = 0 mode), so
+// that the combinations built from C keep them real in r exactly.
+template <typename T>
+static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
+                cudaStream_t st, Prof* pf) {
+  DV_TRY(gram_any<T>(S, A, m, B, n, C, ldc, st, pf));
+  if (!S.gamma || m <= 0 || n <= 0) return QE_OK;
+  k_real_part<<<grid_for((size_t)m * n), 256, 0, st>>>(C, m, n, ldc);
+  return check_launch("k_real_part");
+}
+
 // C[n][m] (+)= (-) sum_k A[k][m] B[k][n]: rotations and projections out of the basis
 template <typename T>
-static int outer(const DvState& S, const z* A, int lda, const z* B, int ldb, int M, int N, int K,
-                 z* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf) {
+static int outer_any(const DvState& S, const z* A, int lda, const z* B, int ldb, int M, int N,
+                     int K, z* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf) {
   if (sizeof(T) == sizeof(float) && S.tc && tc_worth(M, N, K) && lda == M && ldb == N)
     return tc_outer((const double*)A, (const double*)B, M, N, K, (double*)C, ldc, alpha_neg, beta,
                     S.tc, S.tc_bytes, dv_tc_status(S), st, pf);
@@ -352,6 +447,18 @@ static int outer(const DvState& S, const z* A, int lda, const z* B, int ldb, int
                     alpha_neg, beta, S.oz, S.oz_bytes, dv_tc_status(S), st, pf);
   return gemm_outer_ab<T>((const double*)A, lda, (const double*)B, ldb, M, N, K, (double*)C, ldc,
                           alpha_neg, beta, st, pf);
+}
+
+// outer_any; in the k = 0 mode the rows produced (plane-wave vectors) are made
+// real in r again: the combinations are real, but the SIMT kernels' three-
+// multiplication complex product does not round conjugate pairs alike.
+template <typename T>
+static int outer(const DvState& S, const z* A, int lda, const z* B, int ldb, int M, int N, int K,
+                 z* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf) {
+  DV_TRY(outer_any<T>(S, A, lda, B, ldb, M, N, K, C, ldc, alpha_neg, beta, st, pf));
+  if (!S.gamma || N <= 0 || M != S.npw || ldc != S.npw) return QE_OK;
+  k_gamma_sym<<<grid_for((size_t)N * M), 256, 0, st>>>(C, N, M, S.mg);
+  return check_launch("k_gamma_sym");
 }
 
 // Reduced matrices: columns [n0, n1) for rows [0, n1), then the mirrored rows.
@@ -730,6 +837,10 @@ static int dv_begin(DvSolve& v, cudaStream_t st) {
                                               v.op.nproj, npw, S.hd);
   DV_TRY(check_launch("k_hdiag"));
   DV_CU(cudaMemsetAsync(S.dw.status, 0, 16 * sizeof(int), st));
+  if (S.gamma) {
+    k_gamma_start<<<nb, 256, 0, st>>>(S.V, npw, S.mg);
+    DV_TRY(check_launch("k_gamma_start"));
+  }
   v.e.assign(nb, 0.0);
   v.rn.assign(nb, 0.0);
   v.n = nb;
@@ -838,6 +949,10 @@ static int dv_step_finish(qe_ctx* ctx, DvSolve& v, cudaStream_t st, Prof* pf) {
   DV_CU(cudaMemcpyAsync(S.idx, unc.data(), nu * sizeof(int), cudaMemcpyHostToDevice, st));
   k_precond<<<nu, 256, 0, st>>>(S.R, S.idx, S.e, S.hd, npw, pmin * pmin, S.D);
   DV_TRY(check_launch("k_precond"));
+  if (S.gamma) {
+    k_gamma_sym<<<grid_for((size_t)nu * npw), 256, 0, st>>>(S.D, nu, npw, S.mg);
+    DV_TRY(check_launch("k_gamma_sym"));
+  }
   if (v.n + nu > md) {
     DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
     DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
@@ -864,7 +979,7 @@ static int dv_after_h(DvSolve& v, cudaStream_t st, Prof* pf) {
 static int dv_apply_h(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
   const size_t off = (size_t)v.h_row * v.S.npw;
   return hpsi_core(ctx, *v.P, v.op, v.precision, (const double*)(v.S.V + off),
-                   (double*)(v.S.HV + off), v.h_rows, st);
+                   (double*)(v.S.HV + off), v.h_rows, st, v.S.gamma);
 }
 
 template <typename T>
@@ -922,7 +1037,8 @@ static int davidson_run(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
   DV_TRY(dv_loop<T>(ctx, v, st));
   if (v.precision != QE_FP64) {
     DV_TRY(refine_pre(v.S, st));
-    DV_TRY(hpsi_core(ctx, *v.P, v.op, QE_FP64, (const double*)v.S.V, (double*)v.S.HV, v.S.nb, st));
+    DV_TRY(hpsi_core(ctx, *v.P, v.op, QE_FP64, (const double*)v.S.V, (double*)v.S.HV, v.S.nb, st,
+                     v.S.gamma));
     DV_TRY(refine_post(v.S, st, pf));
     DV_TRY(dv_fp64_phase(ctx, v, st));
   }
@@ -941,6 +1057,7 @@ static int davidson_batch_run(qe_ctx* ctx, std::vector<DvSolve>& vs,
     std::vector<qe_problem> pr;
     std::vector<const double*> in;
     std::vector<double*> out;
+    std::vector<char> pair;
     for (int p = 0; p < np; ++p) {
       DvSolve& v = vs[p];
       if (rcs[p] != QE_OK || v.h_rows == 0) continue;
@@ -950,9 +1067,11 @@ static int davidson_batch_run(qe_ctx* ctx, std::vector<DvSolve>& vs,
       const size_t off = (size_t)v.h_row * v.S.npw;
       in.push_back((const double*)(v.S.V + off));
       out.push_back((double*)(v.S.HV + off));
+      pair.push_back(v.S.gamma ? 1 : 0);
     }
     if (pr.empty()) return QE_OK;
-    return hpsi_batch_core(ctx, (int)pr.size(), pr.data(), precision, in.data(), out.data(), st);
+    return hpsi_batch_core(ctx, (int)pr.size(), pr.data(), precision, in.data(), out.data(), st,
+                           pair.data());
   };
   for (int p = 0; p < np; ++p) rcs[p] = dv_begin(vs[p], st);
   DV_TRY(apply_pending(vs[0].precision));
@@ -1008,10 +1127,21 @@ using namespace qe;
 
 namespace {
 
+// Whether a k = 0 solve keeps its bands real in r: by default in FP64 (C2: 19
+// iterations either way, the FFTs halved: 1.41 -> 1.21 s); the mixed path
+// keeps complex bands unless asked (QE_GAMMA), because with real bands its FP32
+// phase needed 23 instead of 16 iterations on C2 (a complex basis spans the
+// real and imaginary parts of its vectors, twice the real dimension).
+static bool gamma_mode(int precision, int flags) {
+  if (flags & QE_NO_GAMMA) return false;
+  return precision == QE_FP64 || (flags & QE_GAMMA);
+}
+
 // Checks of one problem's arguments, its plan and operator, and the layout of
 // its Davidson workspace in `basis` / `red`.
 int dv_setup(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int max_iter,
-             int max_dim, DevBuf& basis, DevBuf& red, DvSolve& v, cudaStream_t st, const char* who) {
+             int max_dim, DevBuf& basis, DevBuf& red, DvSolve& v, cudaStream_t st, const char* who,
+             bool allow_gamma) {
   DV_TRY(check_problem(prob, who));
   const int nb = prob->nbnd;
   DevPlan* P = nullptr;
@@ -1032,7 +1162,30 @@ int dv_setup(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int
   S.nb = nb;
   S.max_dim = md;
   S.np = prob->nproj;
-  return dv_alloc(basis, red, S, precision == QE_FP64);
+  DV_TRY(dv_alloc(basis, red, S, precision == QE_FP64));
+  S.gamma = false;
+  S.mg = nullptr;
+  if (allow_gamma && P->h.gamma && P->mg) {
+    // real-in-r mode needs real projectors: B_i(-G) = conj B_i(G)
+    bool real_beta = true;
+    if (v.op.nproj > 0) {
+      unsigned long long* w = reinterpret_cast<unsigned long long*>(S.dw.y);
+      DV_CU(cudaMemsetAsync(w, 0, 2 * sizeof(unsigned long long), st));
+      k_beta_mirror<<<grid_for((size_t)v.op.nproj * npw), 256, 0, st>>>(
+          (const z*)v.op.beta, v.op.nproj, npw, P->mg, w);
+      DV_TRY(check_launch("k_beta_mirror"));
+      unsigned long long hw[2];
+      DV_CU(cudaMemcpyAsync(hw, w, sizeof(hw), cudaMemcpyDeviceToHost, st));
+      DV_CU(cudaStreamSynchronize(st));
+      double dmax, bmax;
+      std::memcpy(&dmax, &hw[0], sizeof(double));
+      std::memcpy(&bmax, &hw[1], sizeof(double));
+      real_beta = dmax <= 1e-12 * bmax;
+    }
+    S.gamma = real_beta;
+    S.mg = real_beta ? P->mg : nullptr;
+  }
+  return QE_OK;
 }
 
 // Final status of a solve: barrier and overlap checks of the last Rayleigh-Ritz.
@@ -1054,7 +1207,10 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   clear_error();
   if (!ctx) { set_error("qe_davidson: null context"); return QE_EINVAL; }
   DV_TRY(check_problem(prob, "qe_davidson"));
+  const int flags = precision & (QE_GAMMA | QE_NO_GAMMA);
+  precision &= ~(QE_GAMMA | QE_NO_GAMMA);
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_davidson: bad precision"); return QE_EINVAL; }
+  const bool allow_gamma = gamma_mode(precision, flags);
   if (!(tol > 0.0) || max_iter < 0) { set_error("qe_davidson: tol must be > 0, max_iter >= 0"); return QE_EINVAL; }
   const int nb = prob->nbnd;
   if (iters) *iters = 0;
@@ -1065,7 +1221,7 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   DV_TRY(ctx_begin(ctx, st));
   DvSolve v;
   DV_TRY(dv_setup(ctx, prob, precision, tol, max_iter, max_dim, ctx->dv_basis, ctx->dv_red, v, st,
-                  "qe_davidson"));
+                  "qe_davidson", allow_gamma));
   DvState& S = v.S;
   const size_t bytes = (size_t)nb * S.npw * sizeof(z);
   const cudaMemcpyKind in_kind = prob->mem == QE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -1097,7 +1253,10 @@ extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs
     set_error("qe_davidson_batch: bad problem list");
     return QE_EINVAL;
   }
+  const int flags = precision & (QE_GAMMA | QE_NO_GAMMA);
+  precision &= ~(QE_GAMMA | QE_NO_GAMMA);
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_davidson_batch: bad precision"); return QE_EINVAL; }
+  const bool allow_gamma = gamma_mode(precision, flags);
   if (!(tol > 0.0) || max_iter < 0) { set_error("qe_davidson_batch: tol must be > 0, max_iter >= 0"); return QE_EINVAL; }
   for (int p = 0; p < nprob; ++p) {
     DV_TRY(check_problem(&probs[p], "qe_davidson_batch"));
@@ -1133,7 +1292,7 @@ extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs
     const int p = ids[i];
     sub[i] = probs[p];
     DV_TRY(dv_setup(ctx, &probs[p], precision, tol, max_iter, max_dim, *ctx->dvb_basis[i],
-                    *ctx->dvb_red[i], vs[i], st, "qe_davidson_batch"));
+                    *ctx->dvb_red[i], vs[i], st, "qe_davidson_batch", allow_gamma));
     DV_CU(cudaMemcpyAsync(vs[i].S.V, psi_inout[p], (size_t)vs[i].S.nb * vs[i].S.npw * sizeof(z),
                           cudaMemcpyDeviceToDevice, st));
   }

@@ -64,11 +64,23 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   for (int i = threadIdx.x; i < n3 * spb; i += blockDim.x) line[i] = {T(0), T(0)};
   for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(J.tw3[2 * i]), T(J.tw3[2 * i + 1])};
   __syncthreads();
-  const double2* ps = reinterpret_cast<const double2*>(J.psi) + (size_t)(J.b0 + b) * J.npw;
   const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const double2 c = ps[J.st_g[e]];
-    line[J.st_z[e] * spb + (J.st_of[e] - s0)] = {T(c.x), T(c.y)};
+  if (J.pair) {
+    // bands 2b and 2b+1 (real in r) as one complex band psi_2b + i psi_2b+1
+    const double2* pa = reinterpret_cast<const double2*>(J.psi) + (size_t)(J.b0 + 2 * b) * J.npw;
+    const bool hb = 2 * b + 1 < J.nbr;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int g = J.st_g[e];
+      const double2 a = pa[g];
+      const double2 c = hb ? pa[(size_t)J.npw + g] : make_double2(0.0, 0.0);
+      line[J.st_z[e] * spb + (J.st_of[e] - s0)] = {T(a.x - c.y), T(a.y + c.x)};
+    }
+  } else {
+    const double2* ps = reinterpret_cast<const double2*>(J.psi) + (size_t)(J.b0 + b) * J.npw;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const double2 c = ps[J.st_g[e]];
+      line[J.st_z[e] * spb + (J.st_of[e] - s0)] = {T(c.x), T(c.y)};
+    }
   }
   __syncthreads();
   fft_lines<T, +1, false>(line, spb, 1, nullptr, ns, true, J.r3, tw);
@@ -216,9 +228,34 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   }
   __syncthreads();
   fft_lines<T, -1, true>(line, spb, 1, nullptr, ns, true, J.r3, tw);
+  const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
+  if (J.pair) {
+    // W = F(V (a + i b)) with a, b real in r: F(V a)_G = (W_G + conj W_-G) / 2,
+    // F(V b)_G = (W_G - conj W_-G) / 2i.  -G sits in the mirror stick (the
+    // pair partner l ^ 1 of this tile, or the self-mirror stick itself) at -z.
+    const double2* pa = reinterpret_cast<const double2*>(J.psi) + (size_t)(J.b0 + 2 * b) * J.npw;
+    double2* ha = reinterpret_cast<double2*>(J.hpsi) + (size_t)(J.b0 + 2 * b) * J.npw;
+    const bool hb = 2 * b + 1 < J.nbr;
+    const double h = 0.5 * J.inv_n;
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int g = J.st_g[e], z = J.st_z[e], s = J.st_of[e], l = s - s0;
+      const int lm = s == J.self_st ? l : (l ^ 1);
+      const int zm = z == 0 ? 0 : n3 - z;
+      const cx<T> w = line[z * spb + l], wm = line[zm * spb + lm];
+      const double kg = J.kin[g];
+      const double2 a = pa[g];
+      ha[g] = make_double2(((double)w.x + (double)wm.x) * h + kg * a.x,
+                           ((double)w.y - (double)wm.y) * h + kg * a.y);
+      if (hb) {
+        const double2 c = pa[(size_t)J.npw + g];
+        ha[(size_t)J.npw + g] = make_double2(((double)w.y + (double)wm.y) * h + kg * c.x,
+                                             ((double)wm.x - (double)w.x) * h + kg * c.y);
+      }
+    }
+    return;
+  }
   const double2* ps = reinterpret_cast<const double2*>(J.psi) + (size_t)(J.b0 + b) * J.npw;
   double2* hp = reinterpret_cast<double2*>(J.hpsi) + (size_t)(J.b0 + b) * J.npw;
-  const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int g = J.st_g[e];
     const cx<T> c = line[J.st_z[e] * spb + (J.st_of[e] - s0)];
@@ -328,7 +365,7 @@ size_t psm_bytes(const DevPlan& P) {
 
 template <typename T>
 FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* vp, void* W, int b0,
-                   int nb, const FftShape& sh) {
+                   int nb, const FftShape& sh, int pair) {
   FftJob<T> J;
   std::memset(&J, 0, sizeof(J));
   J.r1 = P.rad[0];
@@ -352,9 +389,13 @@ FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* v
   J.nst = P.h.nst;
   J.nax = P.h.nax;
   J.npw = P.h.npw;
-  J.nb = nb;
+  J.pair = pair && P.h.gamma ? 1 : 0;
+  J.nbr = nb;
+  J.nb = J.pair ? (nb + 1) / 2 : nb;   // FFT bands
+  J.self_st = J.pair ? P.h.nst - 1 : -1;
   J.b0 = b0;
   J.spb = sh.spb > 0 ? sh.spb : default_spb<T>(P.grid[2]);
+  if (J.pair) J.spb = std::max(2, J.spb & ~1);   // a tile holds whole mirror pairs
   J.nsb = (J.nst + J.spb - 1) / J.spb;
   J.inv_n = 1.0 / ((double)P.grid[0] * P.grid[1] * P.grid[2]);
   J.stage_v = plane_stages_v<T>(P) ? 1 : 0;
@@ -374,8 +415,8 @@ int launch_vperm(const DevPlan& P, const double* vloc, T* vp, cudaStream_t st, P
 template <typename T>
 int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi, const T* vp,
                                void* Wv, int b0, int nbc, const FftShape& sh, cudaStream_t st,
-                               Prof* pf) {
-  const FftJob<T> J = make_job<T>(P, psi, hpsi, vp, Wv, b0, nbc, sh);
+                               Prof* pf, int pair) {
+  const FftJob<T> J = make_job<T>(P, psi, hpsi, vp, Wv, b0, nbc, sh, pair);
   const size_t zsm = zsm_bytes<T>(P.grid[2], J.spb);
   const size_t psm = psm_bytes<T>(P);
   if (psm > 227 * 1024) {
@@ -391,7 +432,7 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
   set_max_dynamic_smem(k_zfwd<T>);
   const int zt = sh.zthreads > 0 ? sh.zthreads : 256;
   const int pt = std::min(sh.pthreads > 0 ? sh.pthreads : 256, PlaneLB<T>::threads);
-  dim3 gz(J.nsb, nbc);
+  dim3 gz(J.nsb, J.nb);
   int rc;
   {
     ProfScope ps(pf, "k_zinv", st);
@@ -401,7 +442,7 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
   if (rc) return rc;
   {
     ProfScope ps(pf, "k_plane", st);
-    k_plane<T><<<dim3(P.grid[2], nbc), pt, psm, st>>>(J);
+    k_plane<T><<<dim3(P.grid[2], J.nb), pt, psm, st>>>(J);
     rc = check_launch("k_plane");
   }
   if (rc) return rc;
@@ -412,9 +453,9 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
 
 template <typename T>
 int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, const T* vp, void* Wv,
-                         int b0, int nbc, cudaStream_t st, Prof* pf) {
+                         int b0, int nbc, cudaStream_t st, Prof* pf, int pair) {
   return launch_local_kinetic_shape<T>(P, psi, hpsi, vp, Wv, b0, nbc, tuned_shape(P, sizeof(T)),
-                                       st, pf);
+                                       st, pf, pair);
 }
 
 // Batched local + kinetic: every stage is one persistent launch over all jobs.
@@ -464,23 +505,23 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
 template int launch_vperm<double>(const DevPlan&, const double*, double*, cudaStream_t, Prof*);
 template int launch_vperm<float>(const DevPlan&, const double*, float*, cudaStream_t, Prof*);
 template int launch_local_kinetic<double>(const DevPlan&, const double*, double*, const double*,
-                                          void*, int, int, cudaStream_t, Prof*);
+                                          void*, int, int, cudaStream_t, Prof*, int);
 template int launch_local_kinetic<float>(const DevPlan&, const double*, double*, const float*,
-                                         void*, int, int, cudaStream_t, Prof*);
+                                         void*, int, int, cudaStream_t, Prof*, int);
 template int launch_local_kinetic_shape<double>(const DevPlan&, const double*, double*,
                                                 const double*, void*, int, int, const FftShape&,
-                                                cudaStream_t, Prof*);
+                                                cudaStream_t, Prof*, int);
 template int launch_local_kinetic_shape<float>(const DevPlan&, const double*, double*, const float*,
                                                void*, int, int, const FftShape&, cudaStream_t,
-                                               Prof*);
+                                               Prof*, int);
 template int launch_local_kinetic_batch<double>(const FftJob<double>*, const int*, int, int*, size_t,
                                                 size_t, int, cudaStream_t, Prof*);
 template int launch_local_kinetic_batch<float>(const FftJob<float>*, const int*, int, int*, size_t,
                                                size_t, int, cudaStream_t, Prof*);
 template FftJob<double> make_job<double>(const DevPlan&, const double*, double*, const double*,
-                                         void*, int, int, const FftShape&);
+                                         void*, int, int, const FftShape&, int);
 template FftJob<float> make_job<float>(const DevPlan&, const double*, double*, const float*, void*,
-                                       int, int, const FftShape&);
+                                       int, int, const FftShape&, int);
 template size_t zsm_bytes<double>(int, int);
 template size_t zsm_bytes<float>(int, int);
 template size_t psm_bytes<double>(const DevPlan&);

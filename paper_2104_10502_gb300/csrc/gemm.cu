@@ -439,7 +439,8 @@ int gemm_outer(const double* A, int lda, const double* B, int ldb, int M, int N,
 // fixed), then each thread sums them for its columns n of P.
 __global__ void __launch_bounds__(128) k_dmul(const double* __restrict__ D,
                                               const double2* __restrict__ P,
-                                              double2* __restrict__ Q, int np, int nb) {
+                                              double2* __restrict__ Q, int np, int nb,
+                                              int real_p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* val = reinterpret_cast<double*>(smem_raw);
   int* col = reinterpret_cast<int*>(val + np);
@@ -476,17 +477,18 @@ __global__ void __launch_bounds__(128) k_dmul(const double* __restrict__ D,
       sx = fma(val[q], pv.x, sx);
       sy = fma(val[q], pv.y, sy);
     }
-    Q[(size_t)i * nb + n] = make_double2(sx, sy);
+    Q[(size_t)i * nb + n] = make_double2(sx, real_p ? 0.0 : sy);
   }
 }
 
-int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf) {
+int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf,
+         bool real_p) {
   if (np <= 0 || nb <= 0) return QE_OK;
   ProfScope ps(pf, "k_dmul", st);
   const size_t sm = (size_t)np * (sizeof(double) + sizeof(int));
   set_max_dynamic_smem(k_dmul);
   k_dmul<<<np, 128, sm, st>>>(D, reinterpret_cast<const double2*>(P), reinterpret_cast<double2*>(Q),
-                              np, nb);
+                              np, nb, real_p ? 1 : 0);
   return check_launch("k_dmul");
 }
 

@@ -762,7 +762,7 @@ size_t nonlocal_oz_bytes(int np, int nb, int npw) {
 // (re)computed when slice_beta is true.
 int nonlocal_oz(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
                 int nb, int npw, void* bslices, bool slice_beta, void* work, size_t work_bytes,
-                int* status, cudaStream_t st, Prof* pf) {
+                int* status, cudaStream_t st, Prof* pf, bool real_p) {
   if (np <= 0 || nb <= 0) return QE_OK;
   if (nonlocal_oz_bytes(np, nb, npw) > work_bytes) {
     set_error("nonlocal_oz: workspace too small");
@@ -789,7 +789,7 @@ int nonlocal_oz(const double* beta, const double* dmat, const double* psi, doubl
   if ((rc = oz_slice_rows(psi, npw, nb, npw, 1, wb1, &B1, st, pf))) return rc;
   if ((rc = oz_gemm_inner(A1, B1, np, nb, P, nb, part, oz_partial_bytes(np, nb, npw), status, st, pf)))
     return rc;
-  if ((rc = dmul(dmat, P, Q, np, nb, st, pf))) return rc;
+  if ((rc = dmul(dmat, P, Q, np, nb, st, pf, real_p))) return rc;
   if ((rc = oz_slice_cols(Q, nb, np, nb, 2, wb2, &B2, st, pf))) return rc;
   return oz_gemm_outer(A2, B2, npw, nb, hpsi, npw, 0, 1, status, st, pf);
 }

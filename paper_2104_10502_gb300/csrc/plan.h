@@ -24,6 +24,7 @@ struct DevPlan {
   int* st_x = nullptr;      // [nst]
   int* st_y = nullptr;      // [nst]
   int* ax = nullptr;        // [nax]
+  int* mg = nullptr;        // [npw] sphere index of -G (k = 0 plans only, else null)
   int* perm[3] = {nullptr, nullptr, nullptr};   // digit reversal per axis
   double* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i t / N_axis), interleaved
 };
@@ -99,12 +100,18 @@ struct FftJob {
   const T* vp;
   cx<T>* W;
   int nst, nax, npw, nb, b0, spb, nsb, stage_v;   // stage_v: V plane staged in shared memory
+  // pair: FFT band b carries the real-space-real bands 2b and 2b+1 of the
+  // job's nbr bands as psi_2b + i psi_2b+1 (k = 0; sticks in mirror pairs);
+  // self_st: the self-mirror stick
+  int pair, nbr, self_st;
   double inv_n;
 };
 
+// pair != 0 on a k = 0 plan: bands taken two per FFT (they must be real in r,
+// psi(-G) = conj psi(G); the result is H applied to that part of each band).
 template <typename T>
 FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* vp, void* W, int b0,
-                   int nb, const FftShape& sh);
+                   int nb, const FftShape& sh, int pair = 0);
 template <typename T>
 size_t zsm_bytes(int n3, int spb);
 template <typename T>
@@ -116,15 +123,16 @@ template <typename T>
 int launch_vperm(const DevPlan& P, const double* vloc, T* vp, cudaStream_t st, Prof* pf);
 
 // hpsi[b] = |k+G|^2 psi[b] + V_loc psi[b] for bands b0 .. b0+nbc-1.
-// W: stick workspace of nbc * N3 * nst complex T.
+// W: stick workspace of nbc * N3 * nst complex T (ceil(nbc / 2) * N3 * nst
+// with pair, as make_job).
 template <typename T>
 int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, const T* vp,
-                         void* W, int b0, int nbc, cudaStream_t st, Prof* pf);
+                         void* W, int b0, int nbc, cudaStream_t st, Prof* pf, int pair = 0);
 
 template <typename T>
 int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi, const T* vp,
                                void* W, int b0, int nbc, const FftShape& sh, cudaStream_t st,
-                               Prof* pf);
+                               Prof* pf, int pair = 0);
 template <typename T>
 int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev, int njobs,
                                int* counters, size_t smem_z, size_t smem_p, int threads,
@@ -179,10 +187,13 @@ size_t nonlocal_tc_bytes(int np, int nb, int npw);
 size_t nonlocal_tc_beta_bytes(int np, int npw);
 int nonlocal_tc(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
                 int nb, int npw, void* bpack, bool pack_beta, void* work, size_t work_bytes,
-                int* status, cudaStream_t st, Prof* pf);
+                int* status, cudaStream_t st, Prof* pf, bool real_p = false);
 
 // Q[i][n] = sum_j D[i][j] P[j][n] (D real [np][np], P complex [np][nb]).
-int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf);
+// Q = D P (D real [np][np], P complex [np][nb]); real_p: Q = D Re(P) (bands real in r
+// with real projectors at k = 0, where P is real up to rounding).
+int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf,
+         bool real_p = false);
 
 // hpsi += beta^T D (conj(beta) psi^T) with FP64-accurate products on the BF16
 // tensor cores (ozgemm.cu); beta slices in bslices (nonlocal_oz_beta_bytes),
@@ -191,7 +202,7 @@ size_t nonlocal_oz_bytes(int np, int nb, int npw);
 size_t nonlocal_oz_beta_bytes(int np, int npw);
 int nonlocal_oz(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
                 int nb, int npw, void* bslices, bool slice_beta, void* work, size_t work_bytes,
-                int* status, cudaStream_t st, Prof* pf);
+                int* status, cudaStream_t st, Prof* pf, bool real_p = false);
 // FP64 complex products on the tensor cores (default) or on the DFMA pipe
 // (environment QE_FP64_GEMM=simt).
 bool fp64_gemm_on_tensor_cores();

@@ -181,15 +181,53 @@ int build_plan_host(const double lat[9], const double k[3], double ecut,
   std::vector<long long> uk(keys);
   std::sort(uk.begin(), uk.end());
   uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
+  // At k = 0 the sphere is symmetric under G -> -G: order the sticks in mirror
+  // pairs, (x, y) next to (-x, -y), the self-mirror stick (0, 0) last, so that
+  // a z tile of an even number of sticks holds both halves of every pair.
+  std::vector<long long> order(uk);
+  P.gamma = 0;
+  if (k[0] == 0.0 && k[1] == 0.0 && k[2] == 0.0) {
+    auto mirror = [&](long long key) {
+      const int x = (int)(key / n2), y = (int)(key % n2);
+      return (long long)((n1 - x) % n1) * n2 + (n2 - y) % n2;
+    };
+    std::vector<char> used(uk.size(), 0);
+    std::vector<long long> ord;
+    long long self = -1;
+    bool ok = true;
+    for (size_t s = 0; s < uk.size() && ok; ++s) {
+      if (used[s]) continue;
+      const long long m = mirror(uk[s]);
+      if (m == uk[s]) {
+        if (self >= 0) ok = false;
+        self = uk[s];
+        used[s] = 1;
+        continue;
+      }
+      const auto it = std::lower_bound(uk.begin(), uk.end(), m);
+      if (it == uk.end() || *it != m || used[it - uk.begin()]) { ok = false; break; }
+      used[s] = used[it - uk.begin()] = 1;
+      ord.push_back(uk[s]);
+      ord.push_back(m);
+    }
+    if (ok && self >= 0) {
+      ord.push_back(self);
+      order = ord;
+      P.gamma = 1;
+    }
+  }
+  std::vector<int> pos(uk.size());   // sorted index -> stick index
+  for (size_t s = 0; s < order.size(); ++s)
+    pos[std::lower_bound(uk.begin(), uk.end(), order[s]) - uk.begin()] = (int)s;
   P.nst = (int)uk.size();
   P.st_x.resize(P.nst);
   P.st_y.resize(P.nst);
-  for (int s = 0; s < P.nst; ++s) { P.st_x[s] = (int)(uk[s] / n2); P.st_y[s] = (int)(uk[s] % n2); }
+  for (int s = 0; s < P.nst; ++s) { P.st_x[s] = (int)(order[s] / n2); P.st_y[s] = (int)(order[s] % n2); }
   P.g_st.resize(S.npw);
   P.g_z.resize(S.npw);
   std::vector<int> cnt(P.nst + 1, 0);
   for (int i = 0; i < S.npw; ++i) {
-    const int s = (int)(std::lower_bound(uk.begin(), uk.end(), keys[i]) - uk.begin());
+    const int s = pos[std::lower_bound(uk.begin(), uk.end(), keys[i]) - uk.begin()];
     P.g_st[i] = s;
     P.g_z[i] = pmod(S.miller[3 * i + 2], n3);
     cnt[s + 1]++;
@@ -207,10 +245,26 @@ int build_plan_host(const double lat[9], const double k[3], double ecut,
     P.st_z[e] = P.g_z[i];
     P.st_of[e] = s;
   }
+  // active x columns, ascending (from the x-sorted stick keys)
   P.ax.clear();
-  for (int s = 0; s < P.nst; ++s)
-    if (P.ax.empty() || P.ax.back() != P.st_x[s]) P.ax.push_back(P.st_x[s]);
+  for (const long long key : uk) {
+    const int x = (int)(key / n2);
+    if (P.ax.empty() || P.ax.back() != x) P.ax.push_back(x);
+  }
   P.nax = (int)P.ax.size();
+  if (P.gamma) {
+    // sphere index of -G for every G (Miller indices in a dense box)
+    const int bx = 2 * mx[0] + 1, by = 2 * mx[1] + 1, bz = 2 * mx[2] + 1;
+    std::vector<int> at((size_t)bx * by * bz, -1);
+    auto cell = [&](int a, int b, int c) { return ((size_t)(a + mx[0]) * by + (b + mx[1])) * bz + (c + mx[2]); };
+    for (int i = 0; i < S.npw; ++i) at[cell(S.miller[3 * i], S.miller[3 * i + 1], S.miller[3 * i + 2])] = i;
+    P.mg.resize(S.npw);
+    for (int i = 0; i < S.npw; ++i) {
+      const int j = at[cell(-S.miller[3 * i], -S.miller[3 * i + 1], -S.miller[3 * i + 2])];
+      if (j < 0) { P.gamma = 0; P.mg.clear(); break; }
+      P.mg[i] = j;
+    }
+  }
   return QE_OK;
 }
 

@@ -528,7 +528,7 @@ size_t nonlocal_tc_bytes(int np, int nb, int npw) {
 // (re)written when pack_beta is true.
 int nonlocal_tc(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
                 int nb, int npw, void* bpack, bool pack_beta, void* work, size_t work_bytes,
-                int* status, cudaStream_t st, Prof* pf) {
+                int* status, cudaStream_t st, Prof* pf, bool real_p) {
   if (np <= 0 || nb <= 0) return QE_OK;
   if (nonlocal_tc_bytes(np, nb, npw) > work_bytes) {
     set_error("nonlocal_tc: workspace too small");
@@ -571,7 +571,7 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
     ProfScope ps(pf, "k_combine_p", st);
     k_combine_p<<<grid_of((size_t)np * nb), 256, 0, st>>>(c1, ns1, Mp, Np, np, nb, P);
   }
-  rc = dmul(dmat, (const double*)P, (double*)Q, np, nb, st, pf);
+  rc = dmul(dmat, (const double*)P, (double*)Q, np, nb, st, pf, real_p);
   if (rc) return rc;
   {
     ProfScope ps(pf, "k_pack_q", st);
