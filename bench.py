@@ -246,9 +246,10 @@ def run_gpu(args, rank, world, local_rank):
     prob = ctx.problem(lat, k, ecut, grid, v, beta, dmat, nb)
     stream = torch.cuda.current_stream(dev)
 
-    def timed(precision, steps, warmup, prof=False):
+    def timed(precision, steps, warmup, prof=False, x=None):
+        x = psi if x is None else x
         for _ in range(warmup):
-            ctx.hpsi(prob, psi, hpsi, precision)
+            ctx.hpsi(prob, x, hpsi, precision)
         torch.cuda.synchronize(dev)
         if dist:
             td.barrier()
@@ -263,7 +264,7 @@ def run_gpu(args, rank, world, local_rank):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            ctx.hpsi(prob, psi, hpsi, precision)
+            ctx.hpsi(prob, x, hpsi, precision)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         if dist:
@@ -287,6 +288,18 @@ def run_gpu(args, rank, world, local_rank):
     ms_mixed, kern_mixed, _, _ = timed(q.QE_MIXED, args.steps, args.warmup, prof=True)
     value = world * nb * args.steps / (ms64 / 1e3)
     mixed_value = world * nb * args.steps / (ms_mixed / 1e3)
+    # k = 0 real-band mode (QE_GAMMA): the same bands projected on their
+    # real-in-r parts, c(-G) = conj c(G), two per FFT
+    miller = np.asarray(q.gsphere(lat, k, ecut, grid)[0])
+    where = {tuple(m): i for i, m in enumerate(miller)}
+    mg = np.array([where[tuple(-m)] for m in miller])
+    psi_r = np.ascontiguousarray(0.5 * (psi_h + np.conj(psi_h[:, mg])))
+    psi_g = torch.from_numpy(psi_r.view(np.float64).reshape(nb, npw, 2).copy()).to(dev)
+    ms_g64, _, _, _ = timed(q.QE_FP64 | q.QE_GAMMA, args.steps, args.warmup, x=psi_g)
+    ms_gmx, _, _, _ = timed(q.QE_MIXED | q.QE_GAMMA, args.steps, args.warmup, x=psi_g)
+    gamma = {"fp64": world * nb * args.steps / (ms_g64 / 1e3),
+             "mixed": world * nb * args.steps / (ms_gmx / 1e3), "unit": "bands/s",
+             "bands": "the C1 bands projected on their real-in-r parts (k = 0), two per FFT (QE_GAMMA)"}
 
     # dominant kernel of the FP64 step and its roofline (FP64 ALU-bound):
     # algorithmic FLOPs of all its launches in the timed region / their device time
@@ -372,6 +385,7 @@ def run_gpu(args, rank, world, local_rank):
                 "mixed": {"value": mixed_value, "unit": "bands/s", "ms_per_step": ms_mixed / args.steps,
                           "dtype": "fp32 FFT + TF32x3 tensor-core projector products",
                           "kernels": kernels_mixed},
+                "gamma": gamma,
                 "kernels": kernels, "peaks": pk_kind, "davidson": dav, "serve": srv, "batch": bat}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -59,9 +59,11 @@ enum { QE_FP64 = 0, QE_MIXED = 1 };   /* arithmetic of the GPU path */
  *    are real in r (B_i(-G) = conj B_i(G) within 1e-12 of max |B|) can keep
  *    every basis vector real in r: the start bands are replaced by their
  *    larger real-in-r part, H runs as with QE_GAMMA, and the returned
- *    eigenvectors are real in r (same eigenvalues).  This is the default for
- *    QE_FP64; QE_MIXED solves use it only with QE_GAMMA (their FP32 phase
- *    converges in fewer iterations on complex bands).
+ *    eigenvectors are real in r (same eigenvalues).  QE_GAMMA asks for it;
+ *    by default QE_FP64 solves on grids of at least 48^3 points use it
+ *    (smaller FFTs gain less than the mode's extra launches cost), QE_MIXED
+ *    solves do not (their FP32 phase converges in fewer iterations on complex
+ *    bands).
  *  QE_NO_GAMMA (qe_davidson, qe_davidson_batch): never. */
 enum { QE_GAMMA = 0x100, QE_NO_GAMMA = 0x200 };
 enum { QE_HOST = 0, QE_DEVICE = 1 };  /* where the caller's arrays live */

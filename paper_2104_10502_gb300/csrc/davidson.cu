@@ -411,25 +411,22 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
 // ran out); read with the other status words at every convergence test.
 static int* dv_tc_status(const DvState& S) { return S.dw.status + 12; }
 
-template <typename T>
-static int gram_any(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
-                    cudaStream_t st, Prof* pf) {
-  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(m, n, S.npw))
-    return tc_inner((const double*)A, (const double*)B, m, n, S.npw, (double*)C, ldc, S.tc,
-                    S.tc_bytes, dv_tc_status(S), st, pf);
-  if (sizeof(T) == sizeof(double) && S.oz && oz_worth(m, n, S.npw))
-    return oz_inner((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C, ldc,
-                    S.oz, S.oz_bytes, dv_tc_status(S), st, pf);
-  return gemm_inner<T>((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C,
-                       ldc, S.part, S.part_bytes, st, pf);
-}
-
 // C = A^+ B over the plane waves; real for vectors real in r (k = 0 mode), so
-// that the combinations built from C keep them real in r exactly.
+// that the combinations built from C keep them real in r exactly (the SIMT
+// path drops Im C in its split reduction, the tensor-core paths after).
 template <typename T>
 static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
                 cudaStream_t st, Prof* pf) {
-  DV_TRY(gram_any<T>(S, A, m, B, n, C, ldc, st, pf));
+  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(m, n, S.npw)) {
+    DV_TRY(tc_inner((const double*)A, (const double*)B, m, n, S.npw, (double*)C, ldc, S.tc,
+                    S.tc_bytes, dv_tc_status(S), st, pf));
+  } else if (sizeof(T) == sizeof(double) && S.oz && oz_worth(m, n, S.npw)) {
+    DV_TRY(oz_inner((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C, ldc,
+                    S.oz, S.oz_bytes, dv_tc_status(S), st, pf));
+  } else {
+    return gemm_inner<T>((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C,
+                         ldc, S.part, S.part_bytes, st, pf, S.gamma);
+  }
   if (!S.gamma || m <= 0 || n <= 0) return QE_OK;
   k_real_part<<<grid_for((size_t)m * n), 256, 0, st>>>(C, m, n, ldc);
   return check_launch("k_real_part");
@@ -1127,14 +1124,18 @@ using namespace qe;
 
 namespace {
 
-// Whether a k = 0 solve keeps its bands real in r: by default in FP64 (C2: 19
-// iterations either way, the FFTs halved: 1.41 -> 1.21 s); the mixed path
-// keeps complex bands unless asked (QE_GAMMA), because with real bands its FP32
-// phase needed 23 instead of 16 iterations on C2 (a complex basis spans the
-// real and imaginary parts of its vectors, twice the real dimension).
-static bool gamma_mode(int precision, int flags) {
+// Whether a k = 0 solve keeps its bands real in r (QE_GAMMA / QE_NO_GAMMA
+// decide when given).  By default in FP64 on grids of at least 48^3 points (C2,
+// 96^3: 19 iterations either way, the FFTs halved: 1.41 -> 1.21 s); on smaller
+// grids the FFTs are a small share and the mode's extra launches cost as much
+// as it saves (C0, 32^3: 17 -> 18 ms).  The mixed path keeps complex bands
+// unless asked, because with real bands its FP32 phase needed 23 instead of 16
+// iterations on C2 (a complex basis spans the real and imaginary parts of its
+// vectors, twice the real dimension).
+static bool gamma_mode(int precision, int flags, const int grid[3]) {
   if (flags & QE_NO_GAMMA) return false;
-  return precision == QE_FP64 || (flags & QE_GAMMA);
+  if (flags & QE_GAMMA) return true;
+  return precision == QE_FP64 && (long long)grid[0] * grid[1] * grid[2] >= 48ll * 48 * 48;
 }
 
 // Checks of one problem's arguments, its plan and operator, and the layout of
@@ -1210,8 +1211,8 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   const int flags = precision & (QE_GAMMA | QE_NO_GAMMA);
   precision &= ~(QE_GAMMA | QE_NO_GAMMA);
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_davidson: bad precision"); return QE_EINVAL; }
-  const bool allow_gamma = gamma_mode(precision, flags);
   if (!(tol > 0.0) || max_iter < 0) { set_error("qe_davidson: tol must be > 0, max_iter >= 0"); return QE_EINVAL; }
+  const bool allow_gamma = gamma_mode(precision, flags, prob->grid);
   const int nb = prob->nbnd;
   if (iters) *iters = 0;
   if (nb == 0) return QE_OK;
@@ -1256,7 +1257,6 @@ extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs
   const int flags = precision & (QE_GAMMA | QE_NO_GAMMA);
   precision &= ~(QE_GAMMA | QE_NO_GAMMA);
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_davidson_batch: bad precision"); return QE_EINVAL; }
-  const bool allow_gamma = gamma_mode(precision, flags);
   if (!(tol > 0.0) || max_iter < 0) { set_error("qe_davidson_batch: tol must be > 0, max_iter >= 0"); return QE_EINVAL; }
   for (int p = 0; p < nprob; ++p) {
     DV_TRY(check_problem(&probs[p], "qe_davidson_batch"));
@@ -1292,7 +1292,8 @@ extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs
     const int p = ids[i];
     sub[i] = probs[p];
     DV_TRY(dv_setup(ctx, &probs[p], precision, tol, max_iter, max_dim, *ctx->dvb_basis[i],
-                    *ctx->dvb_red[i], vs[i], st, "qe_davidson_batch", allow_gamma));
+                    *ctx->dvb_red[i], vs[i], st, "qe_davidson_batch",
+                    gamma_mode(precision, flags, probs[p].grid)));
     DV_CU(cudaMemcpyAsync(vs[i].S.V, psi_inout[p], (size_t)vs[i].S.nb * vs[i].S.npw * sizeof(z),
                           cudaMemcpyDeviceToDevice, st));
   }

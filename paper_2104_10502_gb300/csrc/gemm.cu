@@ -151,7 +151,7 @@ k_gemm_inner_n8(const double2* __restrict__ A, int lda, const double2* __restric
 template <typename T>
 __global__ void __launch_bounds__(256) k_reduce_split(const cx<T>* __restrict__ part, int nsplit,
                                                       int M, int N, double2* __restrict__ C,
-                                                      int ldc) {
+                                                      int ldc, int real_out) {
   const size_t total = (size_t)M * N;
   const int q = threadIdx.x & 7;
   const size_t o0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 3;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_reduce_split(const cx<T>* __restrict__ 
     }
     if (valid && q == 0) {
       const size_t m = i / N, n = i - m * N;
-      C[m * ldc + n] = make_double2(sx, sy);
+      C[m * ldc + n] = make_double2(sx, real_out ? 0.0 : sy);
     }
   }
 }
@@ -218,7 +218,7 @@ size_t gemm_inner_scratch(int M, int N, int K, size_t elem_bytes) {
 
 template <typename T>
 int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
-               int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf) {
+               int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf, bool real_out) {
   if (M <= 0 || N <= 0) return QE_OK;
   const int ns = inner_split(M, N, K);
   if ((size_t)ns * M * N * sizeof(cx<T>) > part_bytes) {
@@ -239,7 +239,8 @@ int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N,
   const size_t total = (size_t)M * N;
   const int blocks = reduce_blocks(total);
   k_reduce_split<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<T>*>(part), nsplit, M, N,
-                                            reinterpret_cast<double2*>(C), ldc);
+                                            reinterpret_cast<double2*>(C), ldc,
+                                            real_out ? 1 : 0);
   return check_launch("k_reduce_split");
 }
 
@@ -269,7 +270,7 @@ int gemm_inner_bounded(const double* A, int lda, const double* B, int ldb, int M
   const size_t total = (size_t)M * N;
   const int blocks = reduce_blocks(total);
   k_reduce_split<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<T>*>(part), nsplit, M, N,
-                                            reinterpret_cast<double2*>(C), ldc);
+                                            reinterpret_cast<double2*>(C), ldc, 0);
   return check_launch("k_reduce_split");
 }
 
@@ -493,9 +494,9 @@ int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream
 }
 
 template int gemm_inner<double>(const double*, int, const double*, int, int, int, int, double*, int,
-                                void*, size_t, cudaStream_t, Prof*);
+                                void*, size_t, cudaStream_t, Prof*, bool);
 template int gemm_inner<float>(const double*, int, const double*, int, int, int, int, double*, int,
-                               void*, size_t, cudaStream_t, Prof*);
+                               void*, size_t, cudaStream_t, Prof*, bool);
 template int gemm_outer_ab<double>(const double*, int, const double*, int, int, int, int, double*,
                                    int, int, int, cudaStream_t, Prof*);
 template int gemm_outer_ab<float>(const double*, int, const double*, int, int, int, int, double*,

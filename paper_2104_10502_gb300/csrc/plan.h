@@ -143,11 +143,12 @@ size_t stick_bytes(const DevPlan& P, int nbc, size_t elem_bytes);
 
 // ---- complex GEMMs (all matrices complex, interleaved doubles in memory) -----
 // Split-K inner products: P[m][n] = sum_k conj(A[m][k]) B[n][k]; A [M][lda],
-// B [N][ldb]; result written to C (double complex, [M][ldc]).  `part` is a
-// scratch of gemm_inner_scratch(M, N, K) bytes.
+// B [N][ldb]; result written to C (double complex, [M][ldc]; real_out: Im C = 0).
+// `part` is a scratch of gemm_inner_scratch(M, N, K) bytes.
 template <typename T>
 int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
-               double* C, int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf);
+               double* C, int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf,
+               bool real_out = false);
 size_t gemm_inner_scratch(int M, int N, int K, size_t elem_bytes);
 // As gemm_inner, with as many K splits as fit in part_bytes (>= 1).
 template <typename T>

@@ -9,7 +9,7 @@ qe_hpsi tolerances (FP64 1e-12 per band, mixed 2e-5), odd band counts, a cell
 off k = 0 where the flag must be ignored; Davidson solves with the mode (the
 default at k = 0) against the same solves without it (QE_NO_GAMMA) and the
 stored dense eigenvalues, and the returned bands real in r (the mode is the
-default for FP64 solves, on request for mixed ones).
+default for FP64 solves on grids of at least 48^3 points, else on request).
 """
 import os
 
@@ -138,7 +138,7 @@ def test_davidson_gamma_mode_matches_complex_bands(q, ctx, prec, tol, etol):
     psi0 = qeinputs.start_bands(kin, nb, c["psi_seed"])
     ref = np.loadtxt(os.path.join(GOLDEN, "c0_dense_eigs.txt"))[:nb]
     out = {}
-    on = 0 if prec == q.QE_FP64 else q.QE_GAMMA      # the k = 0 mode: FP64 default, mixed on request
+    on = q.QE_GAMMA        # C0 (32^3 grid) is below the size where FP64 solves take the mode by default
     for flag in (on, q.QE_NO_GAMMA):
         pt = _to_t(psi0)
         ev = torch.zeros(nb, dtype=torch.float64, device="cuda")
