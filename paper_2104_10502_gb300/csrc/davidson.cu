@@ -304,7 +304,7 @@ static size_t dv_bytes(size_t npw, size_t nb, size_t md) {
   const size_t big = (2 * md + 5 * nb) * npw * zb;
   const size_t smallz = (6 * md * md + 2 * md * nb + 4 * nb * nb) * zb;
   const size_t dbl = (2 * nb + npw + 1 + 3 * md + nb * md) * sizeof(double);
-  const size_t dwz = 3 * md * zb;
+  const size_t dwz = (3 * md + 8 * md + 64) * zb;   // tau, p, vbuf; compact-WY T blocks
   const size_t ints = (nb + 16) * sizeof(int);
   return big + smallz + dbl + dwz + ints + 48 * 256;
 }
@@ -344,7 +344,7 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
   // doubles: e, rn [nb]; hd [npw]; vmean; dense work: d, e, piv [md], y [nb][md]
   const size_t dbl = (2 * nb + npw + 1 + 3 * md + nb * md) * sizeof(double);
   // dense work complex: tau, p, vbuf [md]
-  const size_t dwz = 3 * md * zb;
+  const size_t dwz = (3 * md + 8 * md + 64) * zb;   // tau, p, vbuf; compact-WY T blocks
   const size_t ints = (nb + 16) * sizeof(int);
   const size_t total = big + smallz + dbl + dwz + ints + 48 * 256;   // + alignment of 31 pieces
   if (total != dv_bytes(npw, nb, md)) {
@@ -383,6 +383,7 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
   S.dw.tau = (z*)take(md * zb);
   S.dw.p = (z*)take(md * zb);
   S.dw.vbuf = (z*)take(md * zb);
+  S.dw.wyt = (z*)take((8 * md + 64) * zb);
   S.dw.refl = (z*)take(md * md * zb);
   S.idx = (int*)take(nb * sizeof(int));
   S.dw.status = (int*)take(16 * sizeof(int));
@@ -608,6 +609,7 @@ static int rayleigh_ritz_f32(DvState& S, int n, cudaStream_t st, Prof* pf) {
   w.tau = reinterpret_cast<zf*>(S.dw.tau);
   w.p = reinterpret_cast<zf*>(S.dw.p);
   w.vbuf = reinterpret_cast<zf*>(S.dw.vbuf);
+  w.wyt = reinterpret_cast<zf*>(S.dw.wyt);
   w.refl = reinterpret_cast<zf*>(S.dw.refl);
   w.d = reinterpret_cast<float*>(S.dw.d);
   w.e = reinterpret_cast<float*>(S.dw.e);
@@ -657,6 +659,7 @@ static int rr_standard_eig(DvState& S, int n, bool fp32, cudaStream_t st, Prof* 
   w.tau = reinterpret_cast<zf*>(S.dw.tau);
   w.p = reinterpret_cast<zf*>(S.dw.p);
   w.vbuf = reinterpret_cast<zf*>(S.dw.vbuf);
+  w.wyt = reinterpret_cast<zf*>(S.dw.wyt);
   w.refl = reinterpret_cast<zf*>(S.dw.refl);
   w.d = reinterpret_cast<float*>(S.dw.d);
   w.e = reinterpret_cast<float*>(S.dw.e);

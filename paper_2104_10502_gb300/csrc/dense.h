@@ -40,6 +40,7 @@ struct DenseWorkT {
   cx<R>* p = nullptr;          // [n] tridiagonalisation work vector
   cx<R>* vbuf = nullptr;       // [n] reflector of the current step, contiguous
   cx<R>* refl = nullptr;       // [n][n] reflector j in row j (coalesced back-transformation)
+  cx<R>* wyt = nullptr;        // [ceil((n-1)/8)][8][8] compact-WY T of each block of 8 reflectors
   R* d = nullptr;              // [n] diagonal of T
   R* e = nullptr;              // [n] off-diagonal of T
   R* y = nullptr;              // [nev][n] eigenvectors of T

@@ -864,30 +864,119 @@ __global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, 
   }
 }
 
-// X[:, k] = H_0 H_1 ... H_{n-2} y_k, one CTA per eigenvector; X [n][ldx].  The
-// reflectors are read from their rows in refl (contiguous, coalesced).
+// X[:, k] = H_0 H_1 ... H_{n-2} y_k by blocks of kWY reflectors in compact WY
+// form: H_j0 ... H_j0+kWY-1 = I - V T V^+ (V = [v_j0 ...] from the rows of refl,
+// v_j zero up to row j and 1 at row j+1; T upper triangular, Schreiber & Van
+// Loan 1989).  k_wy_t builds every block's T, k_backtransform applies the blocks
+// last to first with one block reduction per block instead of one per reflector.
+constexpr int kWY = 8;
+
+// T of block g (reflectors j0 = g kWY .. j0 + nr - 1): P = V^+ V over the
+// block's rows, then T_ii = tau_i, T(0:i, i) = -tau_i T(0:i, 0:i) P(0:i, i).
+// One CTA per block; T blocks of kWY x kWY complex, row-major, zero-padded.
+__global__ void __launch_bounds__(256) k_wy_t(const z* __restrict__ refl, int n,
+                                              const z* __restrict__ tau, z* __restrict__ T) {
+  __shared__ z P[kWY][kWY];
+  const int g = blockIdx.x, j0 = g * kWY, nr = min(kWY, n - 1 - j0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // P[a][b] = v_a^+ v_b for a < b: rows i >= j0 + b + 1 (v_b vanishes above)
+  for (int pq = warp; pq < kWY * kWY; pq += nw) {
+    const int a = pq / kWY, bb = pq % kWY;
+    if (!(a < bb && bb < nr)) continue;
+    const z* va = refl + (size_t)(j0 + a) * n;
+    const z* vb = refl + (size_t)(j0 + bb) * n;
+    R sr = R(0), si = R(0);
+    for (int i = j0 + bb + 1 + lane; i < n; i += 32) {
+      const z x = va[i], y = vb[i];
+      sr = fmar(x.x, y.x, fmar(x.y, y.y, sr));
+      si = fmar(x.x, y.y, fmar(-x.y, y.x, si));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) P[a][bb] = {sr, si};
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    z t[kWY][kWY];
+    for (int r = 0; r < kWY; ++r)
+      for (int c = 0; c < kWY; ++c) t[r][c] = {R(0), R(0)};
+    for (int i = 0; i < nr; ++i) {
+      const z ti = tau[j0 + i];
+      for (int r = 0; r < i; ++r) {
+        z acc = {R(0), R(0)};
+        for (int c = r; c < i; ++c) acc = cadd(acc, cmul(t[r][c], P[c][i]));
+        t[r][i] = {-(ti.x * acc.x - ti.y * acc.y), -(ti.x * acc.y + ti.y * acc.x)};
+      }
+      t[i][i] = ti;
+    }
+    z* out = T + (size_t)g * kWY * kWY;
+    for (int r = 0; r < kWY; ++r)
+      for (int c = 0; c < kWY; ++c) out[r * kWY + c] = t[r][c];
+  }
+}
+
+// One CTA per eigenvector; X [n][ldx].  Per block (last to first):
+// w = V^+ x (one block reduction), u = T w, x -= V u.
 __global__ void __launch_bounds__(256) k_backtransform(const z* __restrict__ refl, int n,
-                                                       const z* tau, const R* Y, z* X, int ldx) {
+                                                       const z* __restrict__ T, const R* Y, z* X,
+                                                       int ldx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   z* x = reinterpret_cast<z*>(smem_raw);
-  __shared__ R sh[33];
+  __shared__ z part[8][kWY];
+  __shared__ z u[kWY];
   const int k = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = {Y[(size_t)k * n + i], R(0)};
   __syncthreads();
-  for (int j = n - 2; j >= 0; --j) {
-    const z t = tau[j];
-    if (t.x == R(0) && t.y == R(0)) continue;
-    const z* v = refl + (size_t)j * n;
-    R sr = R(0), si = R(0);
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) {
-      const z vr = v[r], xr = x[r];
-      sr += vr.x * xr.x + vr.y * xr.y;
-      si += vr.x * xr.y - vr.y * xr.x;
+  const int ngroups = (n - 1 + kWY - 1) / kWY;
+  for (int g = ngroups - 1; g >= 0; --g) {
+    const int j0 = g * kWY, nr = min(kWY, n - 1 - j0);
+    z acc[kWY];
+#pragma unroll
+    for (int a = 0; a < kWY; ++a) acc[a] = {R(0), R(0)};
+    for (int i = j0 + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const z xi = x[i];
+#pragma unroll
+      for (int a = 0; a < kWY; ++a) {
+        if (a < nr && i >= j0 + a + 1) {
+          const z v = refl[(size_t)(j0 + a) * n + i];
+          acc[a].x = fmar(v.x, xi.x, fmar(v.y, xi.y, acc[a].x));
+          acc[a].y = fmar(v.x, xi.y, fmar(-v.y, xi.x, acc[a].y));
+        }
+      }
     }
-    const R a = block_sum(sr, sh);
-    const R b = block_sum(si, sh);
-    const z f = cmul(t, z{a, b});     // tau (v^+ x)
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) x[r] = csub(x[r], cmul(f, v[r]));
+#pragma unroll
+    for (int a = 0; a < kWY; ++a) {
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[a].x += __shfl_xor_sync(0xffffffffu, acc[a].x, o);
+        acc[a].y += __shfl_xor_sync(0xffffffffu, acc[a].y, o);
+      }
+      if (lane == 0) part[warp][a] = acc[a];
+    }
+    __syncthreads();
+    if (threadIdx.x < kWY) {
+      // w_c = sum over warps, then u_a = sum_{c >= a} T[a][c] w_c (c < nr)
+      __shared__ z w[kWY];
+      z s = {R(0), R(0)};
+      for (int q = 0; q < nw; ++q) s = cadd(s, part[q][threadIdx.x]);
+      w[threadIdx.x] = s;
+      __syncwarp(0xffu);
+      const z* tg = T + (size_t)g * kWY * kWY + threadIdx.x * kWY;
+      z ua = {R(0), R(0)};
+      for (int c = threadIdx.x; c < nr; ++c) ua = cadd(ua, cmul(tg[c], w[c]));
+      u[threadIdx.x] = ua;
+    }
+    __syncthreads();
+    for (int i = j0 + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      z xi = x[i];
+#pragma unroll
+      for (int a = 0; a < kWY; ++a) {
+        if (a < nr && i >= j0 + a + 1) xi = csub(xi, cmul(refl[(size_t)(j0 + a) * n + i], u[a]));
+      }
+      x[i] = xi;
+    }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)i * ldx + k] = x[i];
@@ -919,7 +1008,8 @@ static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, c
   const size_t bsm = (size_t)n * sizeof(z);
   {
     ProfScope ps(pf, "heev_backtransform", st);
-    k_backtransform<<<nev, 256, bsm, st>>>(wk.refl, n, wk.tau, wk.y, X, ldx);
+    if (n > 1) k_wy_t<<<(n - 1 + kWY - 1) / kWY, 256, 0, st>>>(wk.refl, n, wk.tau, wk.wyt);
+    k_backtransform<<<nev, 256, bsm, st>>>(wk.refl, n, wk.wyt, wk.y, X, ldx);
   }
   return check_launch("k_backtransform");
 }
