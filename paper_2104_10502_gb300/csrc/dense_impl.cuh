@@ -921,9 +921,16 @@ __global__ void __launch_bounds__(256) k_wy_t(const z* __restrict__ refl, int n,
   const int g = blockIdx.x, j0 = g * kWY, nr = min(kWY, n - 1 - j0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   // P[a][b] = v_a^+ v_b for a < b: rows i >= j0 + b + 1 (v_b vanishes above)
+  // a reflector with tau = 0 is the identity and its row of refl may be stale:
+  // it contributes zero vectors (P entries 0, T row and column 0)
   for (int pq = warp; pq < kWY * kWY; pq += nw) {
     const int a = pq / kWY, bb = pq % kWY;
     if (!(a < bb && bb < nr)) continue;
+    const z ta = tau[j0 + a], tb = tau[j0 + bb];
+    if ((ta.x == R(0) && ta.y == R(0)) || (tb.x == R(0) && tb.y == R(0))) {
+      if (lane == 0) P[a][bb] = {R(0), R(0)};
+      continue;
+    }
     const z* va = refl + (size_t)(j0 + a) * n;
     const z* vb = refl + (size_t)(j0 + bb) * n;
     R sr = R(0), si = R(0);
@@ -973,7 +980,17 @@ __global__ void __launch_bounds__(256) k_backtransform(const z* __restrict__ ref
   __syncthreads();
   const int ngroups = (n - 1 + kWY - 1) / kWY;
   for (int g = ngroups - 1; g >= 0; --g) {
-    const int j0 = g * kWY, nr = min(kWY, n - 1 - j0);
+    const int j0 = g * kWY;
+    const z* tg0 = T + (size_t)g * kWY * kWY;
+    // reflectors taking part: tau = T_aa != 0 (the others are the identity, and
+    // their rows of refl are not read)
+    unsigned act = 0;
+    const int nr = min(kWY, n - 1 - j0);
+#pragma unroll
+    for (int a = 0; a < kWY; ++a) {
+      const z d = tg0[a * kWY + a];
+      if (a < nr && (d.x != R(0) || d.y != R(0))) act |= 1u << a;
+    }
     z acc[kWY];
 #pragma unroll
     for (int a = 0; a < kWY; ++a) acc[a] = {R(0), R(0)};
@@ -981,7 +998,7 @@ __global__ void __launch_bounds__(256) k_backtransform(const z* __restrict__ ref
       const z xi = x[i];
 #pragma unroll
       for (int a = 0; a < kWY; ++a) {
-        if (a < nr && i >= j0 + a + 1) {
+        if (((act >> a) & 1u) && i >= j0 + a + 1) {
           const z v = refl[(size_t)(j0 + a) * n + i];
           acc[a].x = fmar(v.x, xi.x, fmar(v.y, xi.y, acc[a].x));
           acc[a].y = fmar(v.x, xi.y, fmar(-v.y, xi.x, acc[a].y));
@@ -1014,7 +1031,7 @@ __global__ void __launch_bounds__(256) k_backtransform(const z* __restrict__ ref
       z xi = x[i];
 #pragma unroll
       for (int a = 0; a < kWY; ++a) {
-        if (a < nr && i >= j0 + a + 1) xi = csub(xi, cmul(refl[(size_t)(j0 + a) * n + i], u[a]));
+        if (((act >> a) & 1u) && i >= j0 + a + 1) xi = csub(xi, cmul(refl[(size_t)(j0 + a) * n + i], u[a]));
       }
       x[i] = xi;
     }
@@ -1137,6 +1154,7 @@ __global__ void __launch_bounds__(512) k_rr_small(const z* __restrict__ H, const
   z* sw = sv + n;                                  // n
   R* piv = reinterpret_cast<R*>(sw + n); // n
   __shared__ R sred[4];
+  __shared__ R s_inv;
   __shared__ int s_fail;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
@@ -1153,8 +1171,11 @@ __global__ void __launch_bounds__(512) k_rr_small(const z* __restrict__ H, const
       if (tid == 0) { s_fail = 1; *status = 1 + j; }
       break;
     }
-    if (tid == 0) piv[j] = sqrt(dj);
-    const R inv = R(1) / dj;
+    // one thread divides (an FP64 division is ~10 dependent FP64 instructions,
+    // each a whole warp-instruction slot of the narrow FP64 pipe)
+    if (tid == 0) { piv[j] = sqrt(dj); s_inv = R(1) / dj; }
+    __syncthreads();
+    const R inv = s_inv;
     const int m = n - j - 1;
     for (int t = tid; t < m * m; t += nt) {
       const int r = j + 1 + t / m, c = j + 1 + t % m;
@@ -1170,25 +1191,32 @@ __global__ void __launch_bounds__(512) k_rr_small(const z* __restrict__ H, const
     for (int i = tid; i < n; i += nt) { dgl[i] = R(0); egl[i] = R(0); taug[i] = {R(0), R(0)}; }
     return;
   }
+  // reciprocal pivots, one division per thread
+  R* rpiv = reinterpret_cast<R*>(sw);
+  for (int i = tid; i < n; i += nt) rpiv[i] = R(1) / piv[i];
+  __syncthreads();
   for (int t = tid; t < n * n; t += nt) {
     const int r = t / n, c = t % n;
     const z a = L[t];
-    const z l = c > r ? z{R(0), R(0)} : (c == r ? z{piv[c], R(0)} : z{a.x / piv[c], a.y / piv[c]});
+    const z l = c > r ? z{R(0), R(0)} : (c == r ? z{piv[c], R(0)} : z{a.x * rpiv[c], a.y * rpiv[c]});
     L[t] = l;
     Lg[t] = l;
   }
   __syncthreads();
-  // 2. A = L^-1 H L^-+: two forward substitutions (rows in order, columns in parallel)
+  // 2. A = L^-1 H L^-+: two forward substitutions (rows in order, columns in
+  // parallel: for n <= 32 the lanes of one warp, whose FP64 instructions cost
+  // the same for 1 or 32 active lanes); reciprocal pivots instead of a division
+  // per row in every thread
   for (int pass = 0; pass < 2; ++pass) {
     for (int i = 0; i < n; ++i) {
       const z* li = L + (size_t)i * n;
-      const R inv = R(1) / li[i].x;
+      const R inv = rpiv[i];
       for (int c = tid; c < n; c += nt) {
         z acc = A[(size_t)i * n + c];
         for (int k = 0; k < i; ++k) {
           const z l = li[k], x = A[(size_t)k * n + c];
-          acc.x -= l.x * x.x - l.y * x.y;
-          acc.y -= l.x * x.y + l.y * x.x;
+          acc.x = fmar(-l.x, x.x, fmar(l.y, x.y, acc.x));
+          acc.y = fmar(-l.x, x.y, fmar(-l.y, x.x, acc.y));
         }
         A[(size_t)i * n + c] = {acc.x * inv, acc.y * inv};
       }
@@ -1234,8 +1262,8 @@ __global__ void __launch_bounds__(512) k_rr_small(const z* __restrict__ H, const
         const R nu = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + sg);
         const R beta = alpha.x >= R(0) ? -nu : nu;
         const z am = {alpha.x - beta, alpha.y};
-        const R den = am.x * am.x + am.y * am.y;
-        const z sc = {am.x / den, -am.y / den};
+        const R rden = R(1) / (am.x * am.x + am.y * am.y), rbeta = R(1) / beta;
+        const z sc = {am.x * rden, -am.y * rden};
         z* rrow = refl + (size_t)j * n + (j + 1);
         for (int i = 1 + lane; i < m; i += 32) {
           z* x = &A[(size_t)(j + 1 + i) * n + j];
@@ -1245,7 +1273,7 @@ __global__ void __launch_bounds__(512) k_rr_small(const z* __restrict__ H, const
           rrow[i] = v;
         }
         if (lane == 0) {
-          const z t = {(beta - alpha.x) / beta, -alpha.y / beta};
+          const z t = {(beta - alpha.x) * rbeta, -alpha.y * rbeta};
           taug[j] = t;
           egl[j] = beta;
           A[(size_t)(j + 1) * n + j] = {beta, R(0)};
