@@ -142,7 +142,7 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
   for (int c = 0; c < 3; ++c) { perm[c] = digit_reversal(P->rad[c]); tw[c] = twiddles(grid[c]); }
   // one allocation: doubles first, then ints
   size_t nd = h.npw;
-  for (int c = 0; c < 3; ++c) nd += 2 * (size_t)grid[c];
+  for (int c = 0; c < 3; ++c) nd += tw[c].size();
   size_t ni = (h.nst + 1) + 3 * (size_t)h.npw + 2 * (size_t)h.nst + h.nax + h.mg.size();
   for (int c = 0; c < 3; ++c) ni += grid[c];
   const size_t bytes = nd * sizeof(double) + ni * sizeof(int);

@@ -37,13 +37,15 @@ struct Radix {
 bool make_radix(int n, Radix& out);
 // perm[p] = natural index held at stored position p after the DIF stages.
 std::vector<int> digit_reversal(const Radix& rp);
-// table[t] = exp(-2 pi i t / n), t < n, interleaved (re, im)
+// table[t] = exp(-2 pi i t / n), t < n, interleaved (re, im), then the same
+// twiddles as (cos, tan) pairs at table[n + t] (quarter turns: (2^-60, +-2^60))
 std::vector<double> twiddles(int n);
 
 // ---- host-side plan (maps of the sphere onto sticks and planes) --------------
 struct PlanHost {
   int npw = 0, nst = 0, nax = 0;
   int n[3] = {0, 0, 0};
+  int half[3] = {0, 0, 0};        // max |Miller index| of the sphere per axis
   std::vector<double> kin;        // [npw]
   std::vector<int> st_ptr;        // [nst + 1] CSR over sticks
   std::vector<int> st_g;          // [npw] sphere index, stick-major

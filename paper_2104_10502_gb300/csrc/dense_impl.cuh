@@ -815,9 +815,16 @@ __global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, 
   __shared__ R sh[33];
   const int k0 = blockIdx.x;
   if (k0 >= nev) return;
+  // ||T|| bound (Gershgorin), a block-wide max: every thread a stride of rows
   R nrm = R(0);
-  for (int i = 0; i < n; ++i)
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
     nrm = fmax(nrm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : R(0)) + (i < n - 1 ? fabs(e[i]) : R(0)));
+  for (int o = 16; o > 0; o >>= 1) nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  nrm = R(0);
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) nrm = fmax(nrm, sh[q]);
+  __syncthreads();
   const R ctol = ctol_rel * fmax(nrm, RealT<R>::tiny);
   if (k0 > 0 && w[k0] - w[k0 - 1] <= ctol) return;   // not a cluster start
   int k1 = k0 + 1;

@@ -62,7 +62,8 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   const int s0 = sblk * spb;
   const int ns = min(spb, nst - s0);
   for (int i = threadIdx.x; i < n3 * spb; i += blockDim.x) line[i] = {T(0), T(0)};
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(J.tw3[2 * i]), T(J.tw3[2 * i + 1])};
+  const double* tw3 = J.tw3 + (ct_twiddles<T>() ? 2 * n3 : 0);
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(tw3[2 * i]), T(tw3[2 * i + 1])};
   __syncthreads();
   const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
   if (J.pair) {
@@ -83,7 +84,7 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
     }
   }
   __syncthreads();
-  fft_lines<T, +1, false>(line, spb, 1, nullptr, ns, true, J.r3, tw);
+  fft_lines<T, +1, false>(line, spb, 1, nullptr, ns, true, J.r3, tw, J.pm3, J.pr3);
   cx<T>* Wb = J.W + (size_t)b * n3 * nst;
   const FastDiv fns(ns);
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
@@ -159,8 +160,12 @@ __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* sme
     }
   }
   for (int i = threadIdx.x; i < ld * n2; i += nt) plane[i] = {T(0), T(0)};
-  for (int i = threadIdx.x; i < n1; i += nt) tw1[i] = {T(J.tw1[2 * i]), T(J.tw1[2 * i + 1])};
-  for (int i = threadIdx.x; i < n2; i += nt) tw2[i] = {T(J.tw2[2 * i]), T(J.tw2[2 * i + 1])};
+  {
+    const double* t1 = J.tw1 + (ct_twiddles<T>() ? 2 * n1 : 0);
+    const double* t2 = J.tw2 + (ct_twiddles<T>() ? 2 * n2 : 0);
+    for (int i = threadIdx.x; i < n1; i += nt) tw1[i] = {T(t1[2 * i]), T(t1[2 * i + 1])};
+    for (int i = threadIdx.x; i < n2; i += nt) tw2[i] = {T(t2[2 * i]), T(t2[2 * i + 1])};
+  }
   for (int i = threadIdx.x; i < nax; i += nt) ax[i] = J.ax[i];
   __syncthreads();
   // scatter the sticks of this plane: four loads in flight per thread
@@ -180,8 +185,8 @@ __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* sme
   __syncthreads();
   // y on the active columns, then x on every row; consecutive threads take
   // consecutive lines in both passes
-  fft_lines<T, +1, false, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2);
-  fft_lines<T, +1, false, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1);
+  fft_lines<T, +1, false, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2, J.pm2, J.pr2);
+  fft_lines<T, +1, false, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1, J.pm1, J.pr1);
   const FastDiv fn1(n1);
   if (stage) {
     cp_async_wait_all();
@@ -219,7 +224,8 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   cx<T>* tw = line + (size_t)n3 * spb;
   const int s0 = sblk * spb;
   const int ns = min(spb, nst - s0);
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(J.tw3[2 * i]), T(J.tw3[2 * i + 1])};
+  const double* tw3 = J.tw3 + (ct_twiddles<T>() ? 2 * n3 : 0);
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(tw3[2 * i]), T(tw3[2 * i + 1])};
   const cx<T>* Wb = J.W + (size_t)b * n3 * nst;
   const FastDiv fns(ns);
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
@@ -381,6 +387,12 @@ FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* v
   J.tw1 = P.tw[0];
   J.tw2 = P.tw[1];
   J.tw3 = P.tw[2];
+  J.pm1 = P.perm[0];
+  J.pm2 = P.perm[1];
+  J.pm3 = P.perm[2];
+  J.pr1 = P.rad[0].r[0] == 4 && 4 * P.h.half[0] < P.grid[0];
+  J.pr2 = P.rad[1].r[0] == 4 && 4 * P.h.half[1] < P.grid[1];
+  J.pr3 = P.rad[2].r[0] == 4 && 4 * P.h.half[2] < P.grid[2];
   J.kin = P.kin;
   J.psi = psi;
   J.hpsi = hpsi;

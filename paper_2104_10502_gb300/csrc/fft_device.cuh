@@ -103,6 +103,25 @@ __device__ __forceinline__ cx<T> twid(const cx<T>* tw, int t) {
   return SIGN < 0 ? w : cx<T>{w.x, -w.y};
 }
 
+// ---- (c, t) twiddles: w = c (1 + i t), c = cos a, t = tan a -----------------------
+// FP64 transforms keep their tables in this form, so that a twiddle applied before
+// a butterfly costs two FMAs and its factor c folds into the butterfly's own
+// additions (the FMA formulation of twiddled butterflies, Goedecker 1993): a
+// radix-2 butterfly takes 6 instead of 8 FP64 instructions, a radix-4 one 24
+// instead of 28.  The rounding error stays ~eps |v| for any t: c (v.x - t v.y)
+// rounds at |t v.y| and is then scaled by c, |c t| = |sin a| <= 1.  Quarter
+// turns (c = 0) are stored as c = 2^-60, t = +-2^60 (the product then equals
+// -+v.y to within 2^-60 |v.x| + eps |v.y|).
+template <typename T>
+__host__ __device__ constexpr bool ct_twiddles() { return sizeof(T) == 8; }
+
+// v (1 + i t)
+template <typename T>
+__device__ __forceinline__ cx<T> rot1(cx<T> v, T t) { return {fma(-t, v.y, v.x), fma(t, v.x, v.y)}; }
+// a + s u
+template <typename T>
+__device__ __forceinline__ cx<T> caxpy(cx<T> a, T s, cx<T> u) { return {fma(s, u.x, a.x), fma(s, u.y, a.y)}; }
+
 // Division by a divisor fixed for a whole stage: q = hi32(x * ceil(2^32 / d)),
 // exact for x, d < 2^16 (x d < 2^32 bounds the rounding of the multiplier
 // below the gap 1/d between x/d and the next integer).  Replaces the runtime
@@ -119,14 +138,62 @@ struct FastDiv {
   }
 };
 
+// Twiddled butterfly on (c, t) tables: y_0 = v_0, y_q = w^q v_q (w^q = tw[q i1],
+// conjugated for SIGN > 0), then the R-point DFT of y.  Radix 4 uses w^3 = w w^2:
+// y_1 + y_3 = w (v_1 + w^2 v_3) and y_1 - y_3 = w (v_1 - w^2 v_3), so only w and
+// w^2 are read, each scale c multiplying into an FMA of the butterfly.
+template <typename T, int SIGN, int R>
+__device__ __forceinline__ void bfly_ct(cx<T>* v, const cx<T>* tw, int i1) {
+  if constexpr (R == 2) {
+    const cx<T> w1 = twid<T, SIGN>(tw, i1);
+    const cx<T> u = rot1(v[1], w1.y), a = v[0];
+    v[0] = caxpy(a, w1.x, u);
+    v[1] = caxpy(a, -w1.x, u);
+  } else if constexpr (R == 4) {
+    const cx<T> w1 = twid<T, SIGN>(tw, i1), w2 = twid<T, SIGN>(tw, 2 * i1);
+    const cx<T> u2 = rot1(v[2], w2.y), u3 = rot1(v[3], w2.y);
+    const cx<T> a = caxpy(v[0], w2.x, u2), b = caxpy(v[0], -w2.x, u2);
+    const cx<T> e = rot1(caxpy(v[1], w2.x, u3), w1.y);   // (y_1 + y_3) / c_1
+    const cx<T> f = rot1(caxpy(v[1], -w2.x, u3), w1.y);  // (y_1 - y_3) / c_1
+    // X_1,3 = b +- SIGN i (y_1 - y_3)
+    const T sc = T(SIGN) * w1.x;
+    v[0] = caxpy(a, w1.x, e);
+    v[2] = caxpy(a, -w1.x, e);
+    v[1] = {fma(-sc, f.y, b.x), fma(sc, f.x, b.y)};
+    v[3] = {fma(sc, f.y, b.x), fma(-sc, f.x, b.y)};
+  } else {
+#pragma unroll
+    for (int q = 1; q < R; ++q) {
+      const cx<T> w = twid<T, SIGN>(tw, q * i1);
+      const cx<T> u = rot1(v[q], w.y);
+      v[q] = {w.x * u.x, w.x * u.y};
+    }
+    dftR<T, SIGN, R>(v);
+  }
+}
+
 // One radix-R stage over `nlines` lines of length n.  Element e of line l sits
 // at base[lofs(l) + e * es], lofs(l) = lofs_tab ? lofs_tab[l] : l * ls.
 // line_fast selects which index varies fastest across consecutive threads
 // (pick the one that makes consecutive threads touch consecutive addresses).
-template <typename T, int SIGN, bool DIT, int R>
+//
+// Without CT (tables of w itself): DIF applies the R-point DFT and then the
+// twiddles w_L^{jq} to its outputs; DIT applies w_L^{jq} to its inputs and then
+// the DFT.  With CT ((c, t) tables) both directions twiddle the inputs:
+//   * DIT as above (digit-reversed in, natural out);
+//   * the DIF traversal (natural in, digit-reversed out) becomes decimation in
+//     time with natural-order input: the butterfly of block blk and offset j
+//     combines the same elements blk L + j + q M, but first multiplies element q
+//     by w^{q k M}, k = perm[blk L] the frequency held at the block's first
+//     position (perm = the digit reversal of the stages), and leaves the same
+//     digit-reversed order.  Block 0 (the whole first stage) needs no twiddles.
+// prune (CT DIF, first stage, radix 4): the input vanishes outside
+// [0, K] + [n - K, n) with K < n / 4 (a sphere padded by at least 2x), so inputs
+// q = 1, 2 of every butterfly are zero and are neither read nor added.
+template <typename T, int SIGN, bool DIT, int R, bool CT>
 __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int* lofs_tab,
                                           int nlines, bool line_fast, int n, int L,
-                                          const cx<T>* tw) {
+                                          const cx<T>* tw, const int* perm, bool prune) {
   const int M = L / R;
   const int per_line = n / R;
   const int nit = nlines * per_line;
@@ -142,12 +209,28 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
     cx<T>* p = base + off + (blk * L + j) * es;
     const int step = M * es;
     cx<T> v[R];
+    if constexpr (CT && !DIT && R == 4) {
+      if (prune) {
+        const cx<T> a = p[0], d = p[3 * step];
+        p[0] = cadd(a, d);
+        p[2 * step] = csub(a, d);
+        p[step] = {a.x + T(SIGN) * d.y, a.y - T(SIGN) * d.x};       // a - SIGN i d
+        p[3 * step] = {a.x - T(SIGN) * d.y, a.y + T(SIGN) * d.x};   // a + SIGN i d
+        continue;
+      }
+    }
 #pragma unroll
     for (int q = 0; q < R; ++q) v[q] = p[q * step];
-    // j == 0 (every butterfly when M == 1): every twiddle is 1, skip the
-    // products; consecutive threads share j in the line-fast passes, so the
-    // branch is uniform across most warps
-    if (DIT) {
+    if constexpr (CT) {
+      // twiddle index of input 1 (0: every twiddle is 1); consecutive threads
+      // share blk and j in the line-fast passes, so the branch is warp-uniform
+      const int i1 = DIT ? j * tstep : (blk == 0 ? 0 : __ldg(perm + blk * L) * M);
+      if (i1 != 0) bfly_ct<T, SIGN, R>(v, tw, i1);
+      else dftR<T, SIGN, R>(v);
+    } else if (DIT) {
+      // j == 0 (every butterfly when M == 1): every twiddle is 1, skip the
+      // products; consecutive threads share j in the line-fast passes, so the
+      // branch is uniform across most warps
       if (j != 0) {
 #pragma unroll
         for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
@@ -165,15 +248,15 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
   }
 }
 
-template <typename T, int SIGN, bool DIT>
+template <typename T, int SIGN, bool DIT, bool CT>
 __device__ __forceinline__ void fft_stage_any(cx<T>* base, int es, int ls, const int* lofs,
                                               int nlines, bool line_fast, int n, int R, int L,
-                                              const cx<T>* tw) {
+                                              const cx<T>* tw, const int* perm, bool prune) {
   switch (R) {
-    case 2: fft_stage<T, SIGN, DIT, 2>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
-    case 3: fft_stage<T, SIGN, DIT, 3>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
-    case 4: fft_stage<T, SIGN, DIT, 4>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
-    default: fft_stage<T, SIGN, DIT, 5>(base, es, ls, lofs, nlines, line_fast, n, L, tw); break;
+    case 2: fft_stage<T, SIGN, DIT, 2, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false); break;
+    case 3: fft_stage<T, SIGN, DIT, 3, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false); break;
+    case 4: fft_stage<T, SIGN, DIT, 4, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, prune); break;
+    default: fft_stage<T, SIGN, DIT, 5, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false); break;
   }
 }
 
@@ -293,9 +376,14 @@ __device__ __forceinline__ void fft_stage2_any(cx<T>* base, int es, int ls, cons
 // Must be called by every thread of the block.  With FUSE, consecutive stages
 // are fused in pairs while the pair's register tile stays within fuse_limit
 // (same results; fewer shared-memory passes for more registers per thread).
+// FP64 (ct_twiddles) runs unfused on a (c, t) table; its DIF traversal needs
+// perm (the digit reversal of rp) and may prune the first stage (fft_stage).
 template <typename T, int SIGN, bool DIT, bool FUSE = false>
 __device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlines,
-                          bool line_fast, const Radix& rp, const cx<T>* tw) {
+                          bool line_fast, const Radix& rp, const cx<T>* tw,
+                          const int* perm = nullptr, bool prune = false) {
+  constexpr bool CT = ct_twiddles<T>();
+  static_assert(!(CT && FUSE), "fused stage pairs take tables of w");
   if (!DIT) {
     int s = 0;
     while (s < rp.nst) {
@@ -304,7 +392,8 @@ __device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlin
                                        rp.r[s + 1], rp.L[s], tw);
         s += 2;
       } else {
-        fft_stage_any<T, SIGN, false>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s], rp.L[s], tw);
+        fft_stage_any<T, SIGN, false, CT>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
+                                          rp.L[s], tw, perm, prune && s == 0);
         s += 1;
       }
       __syncthreads();
@@ -317,7 +406,8 @@ __device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlin
                                       rp.r[s], rp.L[s - 1], tw);
         s -= 2;
       } else {
-        fft_stage_any<T, SIGN, true>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s], rp.L[s], tw);
+        fft_stage_any<T, SIGN, true, CT>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
+                                         rp.L[s], tw, perm, false);
         s -= 1;
       }
       __syncthreads();

@@ -75,7 +75,7 @@ static int hpsi_noalloc_impl(const qe_problem* pr, const double* psi, double* hp
   const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
   // layout: plan image | permuted V | projections x2 | stick buffer | split-K partials
   size_t nd = h.npw;
-  for (int c = 0; c < 3; ++c) nd += 2 * (size_t)P.grid[c];
+  for (int c = 0; c < 3; ++c) nd += tw[c].size();
   size_t ni = (h.nst + 1) + 3 * (size_t)h.npw + 2 * (size_t)h.nst + h.nax;
   for (int c = 0; c < 3; ++c) ni += P.grid[c];
   const size_t plan_bytes = up256(nd * sizeof(double) + ni * sizeof(int));

@@ -26,7 +26,8 @@ struct DevPlan {
   int* ax = nullptr;        // [nax]
   int* mg = nullptr;        // [npw] sphere index of -G (k = 0 plans only, else null)
   int* perm[3] = {nullptr, nullptr, nullptr};   // digit reversal per axis
-  double* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i t / N_axis), interleaved
+  double* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i t / N_axis), interleaved,
+                                                // then as (cos, tan) (twiddles())
 };
 
 // Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum
@@ -95,6 +96,10 @@ struct FftJob {
   Radix r1, r2, r3;
   const int *st_ptr, *st_g, *st_z, *st_of, *st_x, *st_y, *ax;
   const double *tw1, *tw2, *tw3, *kin;
+  // digit reversal per axis, and whether the first inverse stage of an axis
+  // may take its input as zero outside [0, K] + [N - K, N) (radix 4 first, 4K < N)
+  const int *pm1, *pm2, *pm3;
+  int pr1, pr2, pr3;
   const double* psi;
   double* hpsi;
   const T* vp;

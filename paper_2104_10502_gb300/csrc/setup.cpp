@@ -136,12 +136,19 @@ std::vector<int> digit_reversal(const Radix& rp) {
 }
 
 std::vector<double> twiddles(int n) {
-  std::vector<double> t(2 * (size_t)n);
+  std::vector<double> t(4 * (size_t)n);
   const long double pi = 3.141592653589793238462643383279502884L;
+  const double q = 0x1p-60;
   for (int j = 0; j < n; ++j) {
     const long double a = -2.0L * pi * (long double)j / (long double)n;
-    t[2 * j] = (double)cosl(a);
-    t[2 * j + 1] = (double)sinl(a);
+    const long double c = cosl(a), s = sinl(a);
+    t[2 * j] = (double)c;
+    t[2 * j + 1] = (double)s;
+    // (cos a, tan a); a quarter turn (|c| below any other angle's 2 pi / n) as
+    // (2^-60, +-2^60)
+    const bool quarter = fabsl(c) < 1e-9L;
+    t[2 * (size_t)n + 2 * j] = quarter ? q : (double)c;
+    t[2 * (size_t)n + 2 * j + 1] = quarter ? (s > 0 ? 1.0 / q : -1.0 / q) : (double)(s / c);
   }
   return t;
 }
@@ -168,6 +175,7 @@ int build_plan_host(const double lat[9], const double k[3], double ecut,
       return QE_EINVAL;
     }
     P.n[c] = grid[c];
+    P.half[c] = mx[c];
   }
   P.npw = S.npw;
   P.kin = S.kin;
