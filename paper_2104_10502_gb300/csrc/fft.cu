@@ -202,8 +202,8 @@ __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* sme
     }
   }
   __syncthreads();
-  fft_lines<T, -1, true, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1);
-  fft_lines<T, -1, true, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2);
+  fft_lines<T, -1, true, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1, nullptr, J.pr1);
+  fft_lines<T, -1, true, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2, nullptr, J.pr2);
   for (int s0 = threadIdx.x; s0 < nst; s0 += 4 * nt) {
     int off[4];
 #pragma unroll
@@ -233,7 +233,7 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
     line[pz * spb + l] = Wb[(size_t)pz * nst + s0 + l];
   }
   __syncthreads();
-  fft_lines<T, -1, true>(line, spb, 1, nullptr, ns, true, J.r3, tw);
+  fft_lines<T, -1, true>(line, spb, 1, nullptr, ns, true, J.r3, tw, nullptr, J.pr3);
   const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
   if (J.pair) {
     // W = F(V (a + i b)) with a, b real in r: F(V a)_G = (W_G + conj W_-G) / 2,

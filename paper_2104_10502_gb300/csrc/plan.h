@@ -96,8 +96,10 @@ struct FftJob {
   Radix r1, r2, r3;
   const int *st_ptr, *st_g, *st_z, *st_of, *st_x, *st_y, *ax;
   const double *tw1, *tw2, *tw3, *kin;
-  // digit reversal per axis, and whether the first inverse stage of an axis
-  // may take its input as zero outside [0, K] + [N - K, N) (radix 4 first, 4K < N)
+  // digit reversal per axis, and whether the transforms of an axis may drop the
+  // padding outside [0, K] + [N - K, N) in their stage of span N (zero input of
+  // the first inverse stage, unread output of the last forward stage; radix 4
+  // first, 4K < N)
   const int *pm1, *pm2, *pm3;
   int pr1, pr2, pr3;
   const double* psi;
