@@ -295,6 +295,11 @@ def run_gpu(args, rank, world, local_rank):
     mg = np.array([where[tuple(-m)] for m in miller])
     psi_r = np.ascontiguousarray(0.5 * (psi_h + np.conj(psi_h[:, mg])))
     psi_g = torch.from_numpy(psi_r.view(np.float64).reshape(nb, npw, 2).copy()).to(dev)
+    # the same FP64 step with its FFT in float64 on the FP64 pipe (QE_FFT_FP64PIPE)
+    ms_pipe, _, _, _ = timed(q.QE_FP64 | q.QE_FFT_FP64PIPE, args.steps, args.warmup)
+    fp64_pipe = {"value": world * nb * args.steps / (ms_pipe / 1e3), "unit": "bands/s",
+                 "ms_per_step": ms_pipe / args.steps,
+                 "dtype": "f64 FFT on the FP64 pipe + Ozaki BF16-slice projector products"}
     ms_g64, _, _, _ = timed(q.QE_FP64 | q.QE_GAMMA, args.steps, args.warmup, x=psi_g)
     ms_gmx, _, _, _ = timed(q.QE_MIXED | q.QE_GAMMA, args.steps, args.warmup, x=psi_g)
     gamma = {"fp64": world * nb * args.steps / (ms_g64 / 1e3),
@@ -385,7 +390,7 @@ def run_gpu(args, rank, world, local_rank):
                 "mixed": {"value": mixed_value, "unit": "bands/s", "ms_per_step": ms_mixed / args.steps,
                           "dtype": "fp32 FFT + TF32x3 tensor-core projector products",
                           "kernels": kernels_mixed},
-                "gamma": gamma,
+                "gamma": gamma, "fp64_pipe": fp64_pipe,
                 "kernels": kernels, "peaks": pk_kind, "davidson": dav, "serve": srv, "batch": bat}
         print(json.dumps(line), flush=True)
     ctx.close()

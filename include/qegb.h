@@ -66,6 +66,11 @@ enum { QE_FP64 = 0, QE_MIXED = 1 };   /* arithmetic of the GPU path */
  *    bands).
  *  QE_NO_GAMMA (qe_davidson, qe_davidson_batch): never. */
 enum { QE_GAMMA = 0x100, QE_NO_GAMMA = 0x200 };
+/* QE_FFT_FP64PIPE (qe_hpsi, with QE_FP64): run the FFT in float64 on the FP64
+ * pipe instead of in float-float pairs on the FP32 pipes (the default; same
+ * 1e-12 accuracy class, several times the throughput on GB300, whose FP64
+ * rate is 1/64 of its FP32 rate).  Ignored with QE_MIXED. */
+enum { QE_FFT_FP64PIPE = 0x400 };
 enum { QE_HOST = 0, QE_DEVICE = 1 };  /* where the caller's arrays live */
 
 typedef struct qe_ctx qe_ctx;
@@ -147,9 +152,12 @@ int qe_beta_gaussian(qe_ctx* ctx, const double lat[9], const double k[3],
  *             + sum_ij B_i(G) D_ij sum_G' conj(B_j(G')) c_G',
  *   psi(r_j) = sum_G c_G e^{iG.r_j},  N = N1 N2 N3.
  * psi, hpsi: complex [nbnd][npw][2], host or device per prob->mem (hpsi is
- * overwritten).  precision: QE_FP64 (float64 throughout) or QE_MIXED (FP32
- * FFTs and FP32 projector products, float64 in and out), optionally or-ed
- * with QE_GAMMA (k = 0: bands real in r, two per FFT).
+ * overwritten).  precision: QE_FP64 (FP64-accurate, 1e-12 relative: FFT in
+ * float-float pairs, 48-bit significand, on the FP32 pipes; projector products
+ * in float64 or as Ozaki BF16 slice products on the tensor cores) or QE_MIXED
+ * (FP32 FFTs and FP32 projector products, float64 in and out), optionally
+ * or-ed with QE_GAMMA (k = 0: bands real in r, two per FFT) and, with
+ * QE_FP64, QE_FFT_FP64PIPE.
  * Errors: QE_EINVAL for bad sizes or a grid smaller than the sphere needs. */
 int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
             const double* psi, double* hpsi, void* stream);

@@ -23,6 +23,8 @@ QE_FP64, QE_MIXED = 0, 1
 # flags or-ed into precision (k = 0): QE_GAMMA for hpsi (bands real in r, two per FFT),
 # QE_NO_GAMMA for davidson (keep complex bands)
 QE_GAMMA, QE_NO_GAMMA = 0x100, 0x200
+# or-ed into QE_FP64 for hpsi: the FFT in float64 on the FP64 pipe (default: float-float pairs)
+QE_FFT_FP64PIPE = 0x400
 QE_HOST, QE_DEVICE = 0, 1
 
 SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 #include <vector>
 
 #include "plan.h"
@@ -258,7 +259,7 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(launch_local_kinetic<T>(P, psi, hpsi, (const T*)ctx->vp.p, ctx->sticks.p, b0, n, st,
                                    &ctx->prof, pair ? 1 : 0));
   }
-  if (op.nproj > 0 && sizeof(T) == sizeof(float)) {
+  if (op.nproj > 0 && std::is_same<T, float>::value) {
     // mixed precision: projector products on the tensor cores (TF32x3 split)
     const int np = op.nproj;
     QE_TRY(ctx->tc_work.ensure(nonlocal_tc_bytes(np, nb, npw)));
@@ -298,12 +299,12 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(ctx->projd.ensure((size_t)np * nb * 2 * sizeof(double)));
     const size_t sb = gemm_inner_scratch(np, nb, npw, sizeof(T));
     QE_TRY(ctx->part.ensure(sb));
-    QE_TRY(gemm_inner<T>(op.beta, npw, psi, npw, np, nb, npw, (double*)ctx->proj.p, nb,
-                         ctx->part.p, ctx->part.bytes, st, &ctx->prof));
+    QE_TRY(gemm_inner<GemmT<T>>(op.beta, npw, psi, npw, np, nb, npw, (double*)ctx->proj.p, nb,
+                                ctx->part.p, ctx->part.bytes, st, &ctx->prof));
     QE_TRY(dmul(op.dmat, (const double*)ctx->proj.p, (double*)ctx->projd.p, np, nb, st, &ctx->prof,
                 pair));
-    QE_TRY(gemm_outer<T>(op.beta, npw, (const double*)ctx->projd.p, nb, npw, nb, np, hpsi, npw, 1, st,
-                         &ctx->prof));
+    QE_TRY(gemm_outer<GemmT<T>>(op.beta, npw, (const double*)ctx->projd.p, nb, npw, nb, np, hpsi,
+                                npw, 1, st, &ctx->prof));
   }
   return QE_OK;
 }
@@ -322,9 +323,11 @@ int tc_check(qe_ctx* ctx, cudaStream_t st) {
 }
 
 int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, const double* psi,
-              double* hpsi, int nb, cudaStream_t st, bool pair) {
+              double* hpsi, int nb, cudaStream_t st, bool pair, bool fp64_pipe) {
   if (nb == 0) return QE_OK;
-  if (precision == QE_FP64) return hpsi_device<double>(ctx, P, op, psi, hpsi, nb, st, pair);
+  if (precision == QE_FP64)
+    return fp64_pipe ? hpsi_device<double>(ctx, P, op, psi, hpsi, nb, st, pair)
+                     : hpsi_device<FftF64>(ctx, P, op, psi, hpsi, nb, st, pair);
   return hpsi_device<float>(ctx, P, op, psi, hpsi, nb, st, pair);
 }
 
@@ -452,7 +455,8 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
   if (!ctx) { set_error("qe_hpsi: null context"); return QE_EINVAL; }
   QE_TRY(check_problem(prob, "qe_hpsi"));
   const bool pair = (precision & QE_GAMMA) != 0;
-  precision &= ~QE_GAMMA;
+  const bool fp64_pipe = (precision & QE_FFT_FP64PIPE) != 0;
+  precision &= ~(QE_GAMMA | QE_FFT_FP64PIPE);
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_hpsi: bad precision"); return QE_EINVAL; }
   if (prob->nbnd > 0 && (!psi || !hpsi)) { set_error("qe_hpsi: null psi/hpsi"); return QE_EINVAL; }
   QE_CU(cudaSetDevice(ctx->device));
@@ -473,7 +477,7 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
     dpsi = (const double*)ctx->h_psi.p;
     dhpsi = (double*)ctx->h_hpsi.p;
   }
-  QE_TRY(hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st, pair));
+  QE_TRY(hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st, pair, fp64_pipe));
   if (prob->mem == QE_HOST) {
     if (nb > 0)
       QE_CU(cudaMemcpyAsync(hpsi, dhpsi, nel * sizeof(double), cudaMemcpyDeviceToHost, st));

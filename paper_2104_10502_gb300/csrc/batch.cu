@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.h"
@@ -107,7 +108,7 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
     BT_TRY(W.part.ensure(L.np_max_part));
     BT_TRY(W.proj.ensure(L.np_max_proj));
     BT_TRY(W.projd.ensure(L.np_max_proj));
-    if (sizeof(T) == sizeof(float)) {
+    if (std::is_same<T, float>::value) {
       BT_TRY(W.tc_work.ensure(L.tc_work));
       BT_TRY(W.tc_beta.ensure(L.tc_beta));
     } else if (fp64_gemm_on_tensor_cores()) {
@@ -152,18 +153,18 @@ static int batch_launch(BatchWork& W, int nprob, const qe_problem* probs, const 
     const int nb = probs[p].nbnd, np = op.nproj, npw = L.plans[p]->h.npw;
     if (np <= 0 || nb <= 0) continue;
     const bool rp = L.pair[p] != 0;
-    if (sizeof(T) == sizeof(float)) {
+    if (std::is_same<T, float>::value) {
       BT_TRY(nonlocal_tc(op.beta, op.dmat, psi[p], hpsi[p], np, nb, npw, W.tc_beta.p, true,
                          W.tc_work.p, W.tc_work.bytes, (int*)W.tc_status.p, st, pf, rp));
     } else if (oz_worth(np, nb, npw)) {
       BT_TRY(nonlocal_oz(op.beta, op.dmat, psi[p], hpsi[p], np, nb, npw, W.oz_beta.p, true,
                          W.oz_work.p, W.oz_work.bytes, (int*)W.tc_status.p, st, pf, rp));
     } else {
-      BT_TRY(gemm_inner<T>(op.beta, npw, psi[p], npw, np, nb, npw, (double*)W.proj.p, nb,
-                           W.part.p, W.part.bytes, st, pf));
+      BT_TRY(gemm_inner<GemmT<T>>(op.beta, npw, psi[p], npw, np, nb, npw, (double*)W.proj.p, nb,
+                                  W.part.p, W.part.bytes, st, pf));
       BT_TRY(dmul(op.dmat, (const double*)W.proj.p, (double*)W.projd.p, np, nb, st, pf, rp));
-      BT_TRY(gemm_outer<T>(op.beta, npw, (const double*)W.projd.p, nb, npw, nb, np, hpsi[p], npw, 1,
-                           st, pf));
+      BT_TRY(gemm_outer<GemmT<T>>(op.beta, npw, (const double*)W.projd.p, nb, npw, nb, np, hpsi[p],
+                                  npw, 1, st, pf));
     }
   }
   return QE_OK;
@@ -195,7 +196,7 @@ int hpsi_batch_core(qe_ctx* ctx, int nprob, const qe_problem* probs, int precisi
                     const double* const* psi, double* const* hpsi, cudaStream_t st,
                     const char* pair) {
   BatchWork& W = ctx_batch_work(ctx);
-  if (precision == QE_FP64) return hpsi_batch_t<double>(ctx, W, nprob, probs, psi, hpsi, st, pair);
+  if (precision == QE_FP64) return hpsi_batch_t<FftF64>(ctx, W, nprob, probs, psi, hpsi, st, pair);
   return hpsi_batch_t<float>(ctx, W, nprob, probs, psi, hpsi, st, pair);
 }
 
@@ -259,13 +260,13 @@ int qe_batch_create(qe_ctx* ctx, int nprob, const qe_problem* probs, int precisi
   BatchLayout L;
   std::vector<char> tables;
   int rc = precision == QE_FP64
-               ? batch_prepare<double>(ctx, Wk, nprob, probs, psi, hpsi, L, tables, st)
+               ? batch_prepare<FftF64>(ctx, Wk, nprob, probs, psi, hpsi, L, tables, st)
                : batch_prepare<float>(ctx, Wk, nprob, probs, psi, hpsi, L, tables, st);
   if (rc) { Wk.release(); return rc; }
   char* base = static_cast<char*>(Wk.ws.p);
   BT_CU(cudaMemcpyAsync(base + L.jobs_off, tables.data(), tables.size(), cudaMemcpyHostToDevice, st));
   BT_CU(cudaStreamSynchronize(st));
-  rc = precision == QE_FP64 ? batch_launch<double>(Wk, nprob, probs, psi, hpsi, L, st, nullptr)
+  rc = precision == QE_FP64 ? batch_launch<FftF64>(Wk, nprob, probs, psi, hpsi, L, st, nullptr)
                             : batch_launch<float>(Wk, nprob, probs, psi, hpsi, L, st, nullptr);
   if (rc) { Wk.release(); return rc; }
   BT_CU(cudaStreamSynchronize(st));
@@ -277,7 +278,7 @@ int qe_batch_create(qe_ctx* ctx, int nprob, const qe_problem* probs, int precisi
     set_error("qe_batch_create: stream capture unavailable");
     return QE_ECUDA;
   }
-  rc = precision == QE_FP64 ? batch_launch<double>(Wk, nprob, probs, psi, hpsi, L, cap, nullptr)
+  rc = precision == QE_FP64 ? batch_launch<FftF64>(Wk, nprob, probs, psi, hpsi, L, cap, nullptr)
                             : batch_launch<float>(Wk, nprob, probs, psi, hpsi, L, cap, nullptr);
   const cudaError_t ec = cudaStreamEndCapture(cap, &g);
   cudaStreamDestroy(cap);
@@ -358,8 +359,8 @@ int qe_autotune(qe_ctx* ctx, const qe_problem* prob, int precision, void* stream
     for (int rep = 0; rep < 4; ++rep) {
       if (rep == 1) cudaEventRecord(e0, st);
       const int rc = el == sizeof(double)
-          ? launch_local_kinetic_shape<double>(*P, (const double*)ctx->h_psi.p, (double*)ctx->h_hpsi.p,
-                                               (const double*)ctx->vp.p, ctx->sticks.p, 0, nb, sh, st, nullptr)
+          ? launch_local_kinetic_shape<FftF64>(*P, (const double*)ctx->h_psi.p, (double*)ctx->h_hpsi.p,
+                                               (const FftF64*)ctx->vp.p, ctx->sticks.p, 0, nb, sh, st, nullptr)
           : launch_local_kinetic_shape<float>(*P, (const double*)ctx->h_psi.p, (double*)ctx->h_hpsi.p,
                                               (const float*)ctx->vp.p, ctx->sticks.p, 0, nb, sh, st, nullptr);
       if (rc) return rc;

@@ -67,9 +67,10 @@ int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView
                      cudaStream_t st);
 // H psi for nb bands already on the device.  pair (k = 0 plans): the bands are
 // real in r, psi(-G) = conj psi(G); two share each FFT and the projections are
-// taken real, so the result is H applied to that part of each band.
+// taken real, so the result is H applied to that part of each band.  fp64_pipe
+// (QE_FP64): the FFT in double on the FP64 pipe instead of in float-float pairs.
 int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, const double* psi,
-              double* hpsi, int nb, cudaStream_t st, bool pair = false);
+              double* hpsi, int nb, cudaStream_t st, bool pair = false, bool fp64_pipe = false);
 // Status word of the tensor-core kernels since the last check (synchronises on
 // `st`); QE_ETIMEOUT with a message if a bounded wait ran out, then resets it.
 int tc_check(qe_ctx* ctx, cudaStream_t st);

@@ -1,0 +1,70 @@
+// Float-float numbers: x = hi + lo, two FP32 values with |lo| <= ulp(hi) / 2,
+// together a 48-bit significand (Dekker 1971).  GB300 retires FP32 FMAs at 64x
+// the rate of FP64 ones (128 against 2 lanes per clock and SM), so an FFT kept in
+// float-float arithmetic on the FP32 pipes outruns the same FFT on the FP64 pipe
+// while staying within a few units of 2^-48 per operation.
+//
+// Error-free transformations used (Knuth's two-sum, Dekker's fast two-sum, the
+// exact product a b - fl(a b) as one FMA); sums take the "sloppy" form, whose
+// error is bounded relative to |a| + |b|, which is what a transform's norm-wise
+// error needs.  Every step is written with the _rn intrinsics so that the
+// compiler never contracts a product and a sum into one FMA: the
+// transformations rely on each rounding happening where it is written.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace qe {
+
+struct ff {
+  float hi, lo;
+  ff() = default;
+  __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
+  // nearest float, then the nearest float to the (exact) remainder
+  __host__ __device__ constexpr explicit ff(double x)
+      : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ constexpr explicit ff(int x) : hi((float)x), lo(0.0f) {}   // |x| < 2^24
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+// (s, e) -> hi + lo for |s| >= |e| (fast two-sum)
+__device__ __forceinline__ ff ff_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return ff(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+// a + b: two-sum of the high parts, low parts added into the error
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+  return ff_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+
+// a b: exact product of the high parts plus the cross terms
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_norm(p, e);
+}
+
+// a b + c with one normalisation (an overload beside the float and double fma,
+// so that code templated on the element type calls fma for all three)
+using ::fma;
+__device__ __forceinline__ ff fma(ff a, ff b, ff c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(p, c.hi);
+  const float v = __fsub_rn(s, p);
+  const float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.hi, v));
+  return ff_norm(s, __fadd_rn(t, __fadd_rn(e, c.lo)));
+}
+
+}  // namespace qe

@@ -514,29 +514,22 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
   return check_launch("batched FFT");
 }
 
-template int launch_vperm<double>(const DevPlan&, const double*, double*, cudaStream_t, Prof*);
-template int launch_vperm<float>(const DevPlan&, const double*, float*, cudaStream_t, Prof*);
-template int launch_local_kinetic<double>(const DevPlan&, const double*, double*, const double*,
-                                          void*, int, int, cudaStream_t, Prof*, int);
-template int launch_local_kinetic<float>(const DevPlan&, const double*, double*, const float*,
-                                         void*, int, int, cudaStream_t, Prof*, int);
-template int launch_local_kinetic_shape<double>(const DevPlan&, const double*, double*,
-                                                const double*, void*, int, int, const FftShape&,
-                                                cudaStream_t, Prof*, int);
-template int launch_local_kinetic_shape<float>(const DevPlan&, const double*, double*, const float*,
-                                               void*, int, int, const FftShape&, cudaStream_t,
-                                               Prof*, int);
-template int launch_local_kinetic_batch<double>(const FftJob<double>*, const int*, int, int*, size_t,
-                                                size_t, int, cudaStream_t, Prof*);
-template int launch_local_kinetic_batch<float>(const FftJob<float>*, const int*, int, int*, size_t,
-                                               size_t, int, cudaStream_t, Prof*);
-template FftJob<double> make_job<double>(const DevPlan&, const double*, double*, const double*,
-                                         void*, int, int, const FftShape&, int);
-template FftJob<float> make_job<float>(const DevPlan&, const double*, double*, const float*, void*,
-                                       int, int, const FftShape&, int);
-template size_t zsm_bytes<double>(int, int);
-template size_t zsm_bytes<float>(int, int);
-template size_t psm_bytes<double>(const DevPlan&);
-template size_t psm_bytes<float>(const DevPlan&);
+#define QE_FFT_INSTANTIATE(T)                                                                  \
+  template int launch_vperm<T>(const DevPlan&, const double*, T*, cudaStream_t, Prof*);            \
+  template int launch_local_kinetic<T>(const DevPlan&, const double*, double*, const T*, void*,    \
+                                       int, int, cudaStream_t, Prof*, int);                        \
+  template int launch_local_kinetic_shape<T>(const DevPlan&, const double*, double*, const T*,     \
+                                             void*, int, int, const FftShape&, cudaStream_t,       \
+                                             Prof*, int);                                          \
+  template int launch_local_kinetic_batch<T>(const FftJob<T>*, const int*, int, int*, size_t,      \
+                                             size_t, int, cudaStream_t, Prof*);                    \
+  template FftJob<T> make_job<T>(const DevPlan&, const double*, double*, const T*, void*, int,     \
+                                 int, const FftShape&, int);                                       \
+  template size_t zsm_bytes<T>(int, int);                                                          \
+  template size_t psm_bytes<T>(const DevPlan&);
+QE_FFT_INSTANTIATE(double)
+QE_FFT_INSTANTIATE(float)
+QE_FFT_INSTANTIATE(ff)
+#undef QE_FFT_INSTANTIATE
 
 }  // namespace qe

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "common.h"
+#include "ff.cuh"
 
 namespace qe {
 
@@ -34,6 +35,18 @@ __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.x * s, a.y * s
 // i * s * a
 template <typename T>
 __device__ __forceinline__ cx<T> cimul(cx<T> a, T s) { return {-s * a.y, s * a.x}; }
+// SIGN i a (negations only, no products)
+template <int SIGN, typename T>
+__device__ __forceinline__ cx<T> rot_i(cx<T> a) {
+  if constexpr (SIGN > 0) return {-a.y, a.x};
+  else return {a.y, -a.x};
+}
+// SIGN a for a real a
+template <int SIGN, typename T>
+__device__ __forceinline__ T sgn(T a) {
+  if constexpr (SIGN > 0) return a;
+  else return -a;
+}
 
 // ---- small DFTs: X_q = sum_r v_r exp(SIGN 2 pi i r q / R) --------------------
 template <typename T, int SIGN>
@@ -46,7 +59,7 @@ __device__ __forceinline__ void dft2(cx<T>* v) {
 template <typename T, int SIGN>
 __device__ __forceinline__ void dft3(cx<T>* v) {
   const T h = T(0.5);
-  const T s3 = T(SIGN) * T(0.866025403784438646763723170752936183);  // sin(2 pi / 3)
+  const T s3 = T(SIGN * 0.866025403784438646763723170752936183);  // SIGN sin(2 pi / 3)
   const cx<T> t1 = cadd(v[1], v[2]);
   const cx<T> t2 = {v[0].x - h * t1.x, v[0].y - h * t1.y};
   const cx<T> d = cimul(csub(v[1], v[2]), s3);
@@ -58,7 +71,7 @@ __device__ __forceinline__ void dft3(cx<T>* v) {
 template <typename T, int SIGN>
 __device__ __forceinline__ void dft4(cx<T>* v) {
   const cx<T> a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-  const cx<T> c = cadd(v[1], v[3]), d = cimul(csub(v[1], v[3]), T(SIGN));
+  const cx<T> c = cadd(v[1], v[3]), d = rot_i<SIGN>(csub(v[1], v[3]));
   v[0] = cadd(a, c);
   v[2] = csub(a, c);
   v[1] = cadd(b, d);
@@ -71,8 +84,8 @@ __device__ __forceinline__ void dft5(cx<T>* v) {
   // sin(2pi/5) = sqrt((5 + sqrt5)/8), sin(4pi/5) = sqrt((5 - sqrt5)/8)
   const T c1 = T(0.309016994374947424102293417182819059);
   const T c2 = T(-0.809016994374947424102293417182819059);
-  const T s1 = T(SIGN) * T(0.951056516295153572116439333379382143);
-  const T s2 = T(SIGN) * T(0.587785252292473129168705954639072769);
+  const T s1 = T(SIGN * 0.951056516295153572116439333379382143);
+  const T s2 = T(SIGN * 0.587785252292473129168705954639072769);
   const cx<T> a = v[0];
   const cx<T> t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
   const cx<T> t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
@@ -156,7 +169,7 @@ __device__ __forceinline__ void bfly_ct(cx<T>* v, const cx<T>* tw, int i1) {
     const cx<T> e = rot1(caxpy(v[1], w2.x, u3), w1.y);   // (y_1 + y_3) / c_1
     const cx<T> f = rot1(caxpy(v[1], -w2.x, u3), w1.y);  // (y_1 - y_3) / c_1
     // X_1,3 = b +- SIGN i (y_1 - y_3)
-    const T sc = T(SIGN) * w1.x;
+    const T sc = sgn<SIGN>(w1.x);
     v[0] = caxpy(a, w1.x, e);
     v[2] = caxpy(a, -w1.x, e);
     v[1] = {fma(-sc, f.y, b.x), fma(sc, f.x, b.y)};
@@ -182,7 +195,7 @@ __device__ __forceinline__ void bfly_ct_ends(const cx<T>* v, const cx<T>* tw, in
   const cx<T> a = caxpy(v[0], w2.x, u2), b = caxpy(v[0], -w2.x, u2);
   const cx<T> e = rot1(caxpy(v[1], w2.x, u3), w1.y);
   const cx<T> f = rot1(caxpy(v[1], -w2.x, u3), w1.y);
-  const T sc = T(SIGN) * w1.x;
+  const T sc = sgn<SIGN>(w1.x);
   x0 = caxpy(a, w1.x, e);
   x3 = {fma(sc, f.y, b.x), fma(-sc, f.x, b.y)};
 }
@@ -228,11 +241,11 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
     cx<T> v[R];
     if constexpr (CT && !DIT && R == 4) {
       if (prune) {
-        const cx<T> a = p[0], d = p[3 * step];
+        const cx<T> a = p[0], d = p[3 * step], id = rot_i<SIGN>(d);
         p[0] = cadd(a, d);
         p[2 * step] = csub(a, d);
-        p[step] = {a.x + T(SIGN) * d.y, a.y - T(SIGN) * d.x};       // a - SIGN i d
-        p[3 * step] = {a.x - T(SIGN) * d.y, a.y + T(SIGN) * d.x};   // a + SIGN i d
+        p[step] = csub(a, id);
+        p[3 * step] = cadd(a, id);
         continue;
       }
     }
@@ -247,7 +260,7 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
           bfly_ct_ends<T, SIGN>(v, tw, j * tstep, x0, x3);
         } else {
           const cx<T> a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-          const cx<T> c = cadd(v[1], v[3]), d = cimul(csub(v[1], v[3]), T(SIGN));
+          const cx<T> c = cadd(v[1], v[3]), d = rot_i<SIGN>(csub(v[1], v[3]));
           x0 = cadd(a, c);
           x3 = csub(b, d);
         }

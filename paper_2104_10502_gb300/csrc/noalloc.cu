@@ -146,12 +146,12 @@ static int hpsi_noalloc_impl(const qe_problem* pr, const double* psi, double* hp
     if (rc) return rc;
   }
   if (np > 0) {
-    rc = gemm_inner_bounded<T>(pr->beta, npw, psi, npw, np, nb, npw, proj, nb, part, part_bytes,
-                               st, nullptr);
+    rc = gemm_inner_bounded<GemmT<T>>(pr->beta, npw, psi, npw, np, nb, npw, proj, nb, part,
+                                      part_bytes, st, nullptr);
     if (rc) return rc;
     rc = dmul(pr->dmat, proj, projd, np, nb, st, nullptr);
     if (rc) return rc;
-    rc = gemm_outer<T>(pr->beta, npw, projd, nb, npw, nb, np, hpsi, npw, 1, st, nullptr);
+    rc = gemm_outer<GemmT<T>>(pr->beta, npw, projd, nb, npw, nb, np, hpsi, npw, 1, st, nullptr);
     if (rc) return rc;
   }
   return QE_OK;
@@ -188,6 +188,6 @@ extern "C" int qe_hpsi_noalloc(const qe_problem* prob, int precision, const doub
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* b = static_cast<unsigned char*>(base);
-  if (precision == QE_FP64) return qe::hpsi_noalloc_impl<double>(prob, psi, hpsi, st, b);
+  if (precision == QE_FP64) return qe::hpsi_noalloc_impl<qe::FftF64>(prob, psi, hpsi, st, b);
   return qe::hpsi_noalloc_impl<float>(prob, psi, hpsi, st, b);
 }

@@ -4,10 +4,20 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.h"
 #include "fft_device.cuh"
 
 namespace qe {
+
+// Element type of the FP64 path's FFT: float-float pairs on the FP32 pipes
+// (ff.cuh; FP64-accurate, ~2^-48 per operation); `double` runs it on the FP64
+// pipe instead (QE_FFT_FP64PIPE).
+using FftF64 = ff;
+// Type of the SIMT projector products that go with an FFT element type.
+template <typename T>
+using GemmT = std::conditional_t<std::is_same<T, float>::value, float, double>;
 
 struct DevPlan {
   double lat[9], k[3], ecut;
