@@ -81,6 +81,91 @@ def kernel_flops(name, c, npw, nst, nax, nb, nproj):
 
 TENSOR_KERNELS = {"k_oz_gemm"}
 
+# ---- FP32 operation count of the float-float FFT (the FP64 path's k_plane) ----------
+# FP32 instructions of one float-float operation (ff.cuh, results left
+# unnormalised): a sum 8 (two-sum of the high parts, two low-part additions), a
+# product 4 (exact product by one FMA, two cross FMAs), a fused a b + c 12; every
+# value a stage stores is renormalised (S: a fast two-sum per real part, 6 per
+# complex value).  As FP32 flops (an FFMA 2): 8, 7, 15, 6.
+FF_INST = {"A": 8, "M": 4, "F": 12, "S": 6}
+FF_FLOP = {"A": 8, "M": 7, "F": 15, "S": 6}
+# float-float operations per butterfly (fft_device.cuh): untwiddled DFTs, twiddled
+# butterflies on (cos, tan) twiddles (radix 2 and 4 with the twiddles folded into
+# FMAs; radix 3 and 5 as a 2-FMA rotation and a 2-product scale per input, then
+# the DFT), the padded radix-4 stages (inverse: inputs 1, 2 zero; forward: outputs
+# 0 and 3 only)
+DFT_OPS = {2: {"A": 4}, 3: {"A": 12, "M": 4}, 4: {"A": 16}, 5: {"A": 32, "M": 16}}
+
+
+def _bfly_ops(r, twiddled):
+    if not twiddled:
+        return dict(DFT_OPS[r])
+    if r == 2:
+        return {"F": 6}
+    if r == 4:
+        return {"F": 24}
+    o = dict(DFT_OPS[r])
+    o["F"] = o.get("F", 0) + 2 * (r - 1)
+    o["M"] = o.get("M", 0) + 2 * (r - 1)
+    return o
+
+
+def _radix(n):
+    r, m = [], n
+    while m % 4 == 0:
+        r.append(4)
+        m //= 4
+    for p in (2, 3, 5):
+        while m % p == 0:
+            r.append(p)
+            m //= p
+    return r
+
+
+def ff_line_ops(n, half):
+    """Float-float operations of one inverse and one forward transform of length n
+    (the plane and z kernels' stage structure); half = max |Miller index| on the axis."""
+    rs = _radix(n)
+    prune = bool(rs) and rs[0] == 4 and 4 * half < n
+    inv, fwd = {}, {}
+
+    def add(d, ops, k):
+        for key, v in ops.items():
+            d[key] = d.get(key, 0) + v * k
+
+    L = n
+    for s, r in enumerate(rs):
+        M = L // r
+        nblk = n // L
+        add(inv, {"S": 1}, n)                                # every stage stores the line
+        add(fwd, {"S": 1}, n // 2 if (s == 0 and prune) else n)
+        if s == 0 and prune:
+            add(inv, {"A": 8}, M)
+            add(fwd, {"A": 12}, 1)
+            add(fwd, {"F": 20}, M - 1)
+        else:
+            add(inv, _bfly_ops(r, False), M)                 # block 0
+            add(inv, _bfly_ops(r, True), (nblk - 1) * M)
+            add(fwd, _bfly_ops(r, False), nblk)              # offset 0 of each block
+            add(fwd, _bfly_ops(r, True), nblk * (M - 1))
+        L = M
+    return inv, fwd
+
+
+def ff_plane_launch(c, nax, nb, half):
+    """FP32 instructions and flops of one k_plane<ff> launch over nb bands."""
+    n1, n2, n3 = c["grid"]
+    i2, f2 = ff_line_ops(n2, half[1])
+    i1, f1 = ff_line_ops(n1, half[0])
+    tot = {}
+    for d, k in ((i2, nax), (f2, nax), (i1, n2), (f1, n2)):
+        for key, v in d.items():
+            tot[key] = tot.get(key, 0) + v * k
+    tot["M"] = tot.get("M", 0) + 2 * n1 * n2          # V multiply
+    inst = sum(v * FF_INST[k] for k, v in tot.items()) * n3 * nb
+    flop = sum(v * FF_FLOP[k] for k, v in tot.items()) * n3 * nb
+    return inst, flop
+
 
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled every 200 ms in the background."""
@@ -145,8 +230,8 @@ def src_hash(*names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"k_oz_gemm": ("ozgemm.cu", "tc_ptx.cuh"), "k_plane": ("fft.cu", "fft_device.cuh"), "k_zinv": ("fft.cu", "fft_device.cuh"),
-                  "k_zfwd": ("fft.cu", "fft_device.cuh"), "k_gemm_inner": ("gemm.cu",),
+KERNEL_SOURCES = {"k_oz_gemm": ("ozgemm.cu", "tc_ptx.cuh"), "k_plane": ("fft.cu", "fft_device.cuh", "ff.cuh"),
+                  "k_zinv": ("fft.cu", "fft_device.cuh", "ff.cuh"), "k_zfwd": ("fft.cu", "fft_device.cuh", "ff.cuh"), "k_gemm_inner": ("gemm.cu",),
                   "k_gemm_outer": ("gemm.cu",), "k_dmul": ("gemm.cu",)}
 
 
@@ -314,11 +399,29 @@ def run_gpu(args, rank, world, local_rank):
     calls, tot = kern[dom]
     avg_ms = tot / calls
     fl_launch = kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
+    extra = {}
     if dom in TENSOR_KERNELS:
         # per launch already; the measured BF16 burst peak of the GB300s
         fl_step = fl_launch * calls / args.steps
         bound, peak = "tensor", pk["bf16_tflops"]
         psrc = f"measured BF16 burst ({pk_kind}) of MEASURED_PEAKS.json"
+    elif dom == "k_plane":
+        # float-float FFT on the FP32 pipes: FP32 flops of its float-float
+        # operations (model above, per band) against the FP32 FMA peak of
+        # 152 SMs x 128 lanes x 2 flops x 2.07 GHz; issue_frac counts FP32
+        # instructions against the issue limit (one warp instruction per clock
+        # and sub-partition) instead
+        half = plane_halves(c)
+        inst_b, flop_b = ff_plane_launch(c, plan_nax, 1, half)
+        bands_step = nb * (1 if nb else 0)
+        fl_step = flop_b * bands_step
+        bound, peak = "alu", FP32_NOMINAL_TFLOPS
+        psrc = "nominal FP32 FMA rate of GB300 (recipe table: 152 SMs, 2.07 GHz; 128 lanes per SM)"
+        inst_step = inst_b * bands_step
+        extra = {"fp32_inst_per_band": inst_b, "fp32_flops_per_band": flop_b,
+                 "fp64_equiv_tflops": kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
+                 * args.steps / (tot / 1e3) / 1e12,
+                 "issue_frac": inst_step * args.steps / (tot / 1e3) / (FP32_NOMINAL_TFLOPS / 2 * 1e12)}
     else:
         fl_step = fl_launch
         bound, peak = "alu", FP64_NOMINAL_TFLOPS
@@ -329,7 +432,7 @@ def run_gpu(args, rank, world, local_rank):
             "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic_for(dom, "fp64"),
             "peak_source": psrc,
-            "flops_per_launch": fl, "avg_launch_ms": avg_ms}
+            "flops_per_launch": fl, "avg_launch_ms": avg_ms, **extra}
     kernels = {n: {"launches": kern[n][0], "ms": kern[n][1], "share": kern[n][1] / sum(x[1] for x in kern.values())}
                for n in kern}
     kernels_mixed = {n: {"launches": kern_mixed[n][0], "ms": kern_mixed[n][1]} for n in kern_mixed}
@@ -630,6 +733,13 @@ def run_serve_bench(q, ctx, dev, device_index):
     out["workload"] = ("24 requests: cubic a~U[10,14] bohr, ecut~U[20,30] Ry, nb~U{8..32}, "
                        "2-16 atoms, 4 projectors/atom; Poisson arrivals at 0.7 x burst capacity")
     return out
+
+
+def plane_halves(c):
+    """max |Miller index| of the sphere per axis."""
+    import paper_2104_10502_gb300 as q
+    m, _ = q.gsphere(c["lat"], c["k"], c["ecut"], c["grid"])
+    return [int(np.abs(np.asarray(m)[:, a]).max()) for a in range(3)]
 
 
 def stick_counts(c):

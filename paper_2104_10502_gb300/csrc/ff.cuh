@@ -10,6 +10,16 @@
 // error needs.  Every step is written with the _rn intrinsics so that the
 // compiler never contracts a product and a sum into one FMA: the
 // transformations rely on each rounding happening where it is written.
+//
+// The arithmetic operators leave their result unnormalised: (s, e) with s the
+// rounded sum (or product) of the high parts and e the exact error of that plus
+// the low parts, |e| a few units of 2^-24 |s| (without cancellation) instead of
+// at most half an ulp.  The two-sum of the high parts is exact for any inputs
+// and every low-part rounding stays ~2^-24 of a term already ~2^-24 of the
+// operands, so the norm-wise error is that of normalised arithmetic, while a
+// sum costs 8 instructions instead of 11, a product 4 instead of 7, a fused
+// a b + c 12 instead of 15.  ff_settle renormalises; the FFT stages settle
+// every value they store, which bounds the growth of e to one butterfly.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,12 +43,14 @@ __device__ __forceinline__ ff ff_norm(float s, float e) {
   return ff(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
 
+__device__ __forceinline__ ff ff_settle(ff a) { return ff_norm(a.hi, a.lo); }
+
 // a + b: two-sum of the high parts, low parts added into the error
 __device__ __forceinline__ ff operator+(ff a, ff b) {
   const float s = __fadd_rn(a.hi, b.hi);
   const float v = __fsub_rn(s, a.hi);
   const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
-  return ff_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+  return ff(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
 }
 
 __device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
@@ -50,10 +62,10 @@ __device__ __forceinline__ ff operator*(ff a, ff b) {
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  return ff_norm(p, e);
+  return ff(p, e);
 }
 
-// a b + c with one normalisation (an overload beside the float and double fma,
+// a b + c (an overload beside the float and double fma,
 // so that code templated on the element type calls fma for all three)
 using ::fma;
 __device__ __forceinline__ ff fma(ff a, ff b, ff c) {
@@ -64,7 +76,7 @@ __device__ __forceinline__ ff fma(ff a, ff b, ff c) {
   const float s = __fadd_rn(p, c.hi);
   const float v = __fsub_rn(s, p);
   const float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.hi, v));
-  return ff_norm(s, __fadd_rn(t, __fadd_rn(e, c.lo)));
+  return ff(s, __fadd_rn(t, __fadd_rn(e, c.lo)));
 }
 
 }  // namespace qe

@@ -102,8 +102,11 @@ constexpr bool kFusePlane = sizeof(T) == 4;
 // Launch bounds of the plane stage.  FP32: two CTAs of 256 threads per SM and
 // up to 128 registers for the fused stage pairs (capping registers for a third
 // CTA makes the fused butterflies spill).
-template <typename T> struct PlaneLB { static constexpr int threads = 512, minb = 1; };
-template <> struct PlaneLB<float> { static constexpr int threads = 256, minb = 2; };
+template <typename T> struct PlaneLB { static constexpr int threads = 512, minb = 1, dflt = 256; };
+template <> struct PlaneLB<float> { static constexpr int threads = 256, minb = 2, dflt = 256; };
+// float-float planes: 16 warps per SM (one CTA) hide the dependent FP32 chains of
+// the float-float operations better than 8
+template <> struct PlaneLB<ff> { static constexpr int threads = 512, minb = 1, dflt = 512; };
 
 // Row stride of a plane in shared memory: odd, so that the lines of one pass that
 // consecutive threads take (rows in the x pass, columns in the y pass) fall in
@@ -443,7 +446,7 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
   set_max_dynamic_smem(k_zinv<T>);
   set_max_dynamic_smem(k_zfwd<T>);
   const int zt = sh.zthreads > 0 ? sh.zthreads : 256;
-  const int pt = std::min(sh.pthreads > 0 ? sh.pthreads : 256, PlaneLB<T>::threads);
+  const int pt = std::min(sh.pthreads > 0 ? sh.pthreads : PlaneLB<T>::dflt, PlaneLB<T>::threads);
   dim3 gz(J.nsb, J.nb);
   int rc;
   {

@@ -12,6 +12,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.h"
 #include "ff.cuh"
 
@@ -40,6 +42,13 @@ template <int SIGN, typename T>
 __device__ __forceinline__ cx<T> rot_i(cx<T> a) {
   if constexpr (SIGN > 0) return {-a.y, a.x};
   else return {a.y, -a.x};
+}
+// A value about to be stored by a transform stage: float-float operations
+// leave their results unnormalised (ff.cuh), the stores renormalise.
+template <typename T>
+__device__ __forceinline__ cx<T> settle(cx<T> a) {
+  if constexpr (std::is_same<T, ff>::value) return {ff_settle(a.x), ff_settle(a.y)};
+  else return a;
 }
 // SIGN a for a real a
 template <int SIGN, typename T>
@@ -242,10 +251,10 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
     if constexpr (CT && !DIT && R == 4) {
       if (prune) {
         const cx<T> a = p[0], d = p[3 * step], id = rot_i<SIGN>(d);
-        p[0] = cadd(a, d);
-        p[2 * step] = csub(a, d);
-        p[step] = csub(a, id);
-        p[3 * step] = cadd(a, id);
+        p[0] = settle(cadd(a, d));
+        p[2 * step] = settle(csub(a, d));
+        p[step] = settle(csub(a, id));
+        p[3 * step] = settle(cadd(a, id));
         continue;
       }
     }
@@ -264,8 +273,8 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
           x0 = cadd(a, c);
           x3 = csub(b, d);
         }
-        p[0] = x0;
-        p[3 * step] = x3;
+        p[0] = settle(x0);
+        p[3 * step] = settle(x3);
         continue;
       }
     }
@@ -292,7 +301,7 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
       }
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q) p[q * step] = v[q];
+    for (int q = 0; q < R; ++q) p[q * step] = settle(v[q]);
   }
 }
 
