@@ -90,10 +90,10 @@ TENSOR_KERNELS = {"k_oz_gemm"}
 FF_INST = {"A": 8, "M": 4, "F": 12, "S": 6}
 FF_FLOP = {"A": 8, "M": 7, "F": 15, "S": 6}
 # float-float operations per butterfly (fft_device.cuh): untwiddled DFTs, twiddled
-# butterflies on (cos, tan) twiddles (radix 2 and 4 with the twiddles folded into
-# FMAs; radix 3 and 5 as a 2-FMA rotation and a 2-product scale per input, then
-# the DFT), the padded radix-4 stages (inverse: inputs 1, 2 zero; forward: outputs
-# 0 and 3 only)
+# butterflies on (cos, tan) twiddles (radix 2 and 4: rotations v (1 + i t) as two
+# fused operations, each a +- c u pair as two products and two sums; radix 3 and 5
+# as a rotation and a 2-product scale per input, then the DFT), the padded radix-4
+# stages (inverse: inputs 1, 2 zero; forward: outputs 0 and 3 only)
 DFT_OPS = {2: {"A": 4}, 3: {"A": 12, "M": 4}, 4: {"A": 16}, 5: {"A": 32, "M": 16}}
 
 
@@ -101,9 +101,9 @@ def _bfly_ops(r, twiddled):
     if not twiddled:
         return dict(DFT_OPS[r])
     if r == 2:
-        return {"F": 6}
+        return {"F": 2, "M": 2, "A": 4}
     if r == 4:
-        return {"F": 24}
+        return {"F": 8, "M": 8, "A": 16}
     o = dict(DFT_OPS[r])
     o["F"] = o.get("F", 0) + 2 * (r - 1)
     o["M"] = o.get("M", 0) + 2 * (r - 1)
@@ -142,7 +142,7 @@ def ff_line_ops(n, half):
         if s == 0 and prune:
             add(inv, {"A": 8}, M)
             add(fwd, {"A": 12}, 1)
-            add(fwd, {"F": 20}, M - 1)
+            add(fwd, {"F": 12, "M": 4, "A": 8}, M - 1)
         else:
             add(inv, _bfly_ops(r, False), M)                 # block 0
             add(inv, _bfly_ops(r, True), (nblk - 1) * M)
