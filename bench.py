@@ -84,9 +84,9 @@ TENSOR_KERNELS = {"k_oz_gemm"}
 # ---- FP32 operation count of the float-float FFT (the FP64 path's k_plane) ----------
 # FP32 instructions of one float-float operation (ff.cuh, results left
 # unnormalised): a sum 8 (two-sum of the high parts, two low-part additions), a
-# product 4 (exact product by one FMA, two cross FMAs), a fused a b + c 12; every
-# value a stage stores is renormalised (S: a fast two-sum per real part, 6 per
-# complex value).  As FP32 flops (an FFMA 2): 8, 7, 15, 6.
+# product 4 (exact product by one FMA, two cross FMAs), a fused a b + c 12; the
+# values the last stage of a transform stores are renormalised (S: a fast
+# two-sum per real part, 6 per complex value).  As FP32 flops (an FFMA 2): 8, 7, 15, 6.
 FF_INST = {"A": 8, "M": 4, "F": 12, "S": 6}
 FF_FLOP = {"A": 8, "M": 7, "F": 15, "S": 6}
 # float-float operations per butterfly (fft_device.cuh): untwiddled DFTs, twiddled
@@ -137,8 +137,10 @@ def ff_line_ops(n, half):
     for s, r in enumerate(rs):
         M = L // r
         nblk = n // L
-        add(inv, {"S": 1}, n)                                # every stage stores the line
-        add(fwd, {"S": 1}, n // 2 if (s == 0 and prune) else n)
+        if s == len(rs) - 1:
+            add(inv, {"S": 1}, n)                            # the last inverse stage
+        if s == 0:
+            add(fwd, {"S": 1}, n // 2 if prune else n)       # the last forward stage
         if s == 0 and prune:
             add(inv, {"A": 8}, M)
             add(fwd, {"A": 12}, 1)

@@ -18,8 +18,10 @@
 // and every low-part rounding stays ~2^-24 of a term already ~2^-24 of the
 // operands, so the norm-wise error is that of normalised arithmetic, while a
 // sum costs 8 instructions instead of 11, a product 4 instead of 7, a fused
-// a b + c 12 instead of 15.  ff_settle renormalises; the FFT stages settle
-// every value they store, which bounds the growth of e to one butterfly.
+// a b + c 12 instead of 15.  ff_settle renormalises; a transform settles what
+// its last stage stores, which bounds the growth of e to the few operations per
+// element of one transform (the products that drop lo x lo take a normalised
+// twiddle or potential as one factor).
 #pragma once
 
 #include <cuda_runtime.h>

@@ -43,8 +43,8 @@ __device__ __forceinline__ cx<T> rot_i(cx<T> a) {
   if constexpr (SIGN > 0) return {-a.y, a.x};
   else return {a.y, -a.x};
 }
-// A value about to be stored by a transform stage: float-float operations
-// leave their results unnormalised (ff.cuh), the stores renormalise.
+// A value about to be stored by the last stage of a transform: float-float
+// operations leave their results unnormalised (ff.cuh), these stores renormalise.
 template <typename T>
 __device__ __forceinline__ cx<T> settle(cx<T> a) {
   if constexpr (std::is_same<T, ff>::value) return {ff_settle(a.x), ff_settle(a.y)};
@@ -241,7 +241,8 @@ __device__ __forceinline__ void bfly_ct_ends(const cx<T>* v, const cx<T>* tw, in
 template <typename T, int SIGN, bool DIT, int R, bool CT>
 __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int* lofs_tab,
                                           int nlines, bool line_fast, int n, int L,
-                                          const cx<T>* tw, const int* perm, bool prune) {
+                                          const cx<T>* tw, const int* perm, bool prune,
+                                          bool fin) {
   const int M = L / R;
   const int per_line = n / R;
   const int nit = nlines * per_line;
@@ -260,10 +261,10 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
     if constexpr (CT && !DIT && R == 4) {
       if (prune) {
         const cx<T> a = p[0], d = p[3 * step], id = rot_i<SIGN>(d);
-        p[0] = settle(cadd(a, d));
-        p[2 * step] = settle(csub(a, d));
-        p[step] = settle(csub(a, id));
-        p[3 * step] = settle(cadd(a, id));
+        p[0] = cadd(a, d);
+        p[2 * step] = csub(a, d);
+        p[step] = csub(a, id);
+        p[3 * step] = cadd(a, id);
         continue;
       }
     }
@@ -310,19 +311,20 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
       }
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q) p[q * step] = settle(v[q]);
+    for (int q = 0; q < R; ++q) p[q * step] = fin ? settle(v[q]) : v[q];
   }
 }
 
 template <typename T, int SIGN, bool DIT, bool CT>
 __device__ __forceinline__ void fft_stage_any(cx<T>* base, int es, int ls, const int* lofs,
                                               int nlines, bool line_fast, int n, int R, int L,
-                                              const cx<T>* tw, const int* perm, bool prune) {
+                                              const cx<T>* tw, const int* perm, bool prune,
+                                              bool fin) {
   switch (R) {
-    case 2: fft_stage<T, SIGN, DIT, 2, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false); break;
-    case 3: fft_stage<T, SIGN, DIT, 3, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false); break;
-    case 4: fft_stage<T, SIGN, DIT, 4, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, prune); break;
-    default: fft_stage<T, SIGN, DIT, 5, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false); break;
+    case 2: fft_stage<T, SIGN, DIT, 2, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false, fin); break;
+    case 3: fft_stage<T, SIGN, DIT, 3, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false, fin); break;
+    case 4: fft_stage<T, SIGN, DIT, 4, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, prune, fin); break;
+    default: fft_stage<T, SIGN, DIT, 5, CT>(base, es, ls, lofs, nlines, line_fast, n, L, tw, perm, false, fin); break;
   }
 }
 
@@ -460,7 +462,7 @@ __device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlin
         s += 2;
       } else {
         fft_stage_any<T, SIGN, false, CT>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
-                                          rp.L[s], tw, perm, prune && s == 0);
+                                          rp.L[s], tw, perm, prune && s == 0, s == rp.nst - 1);
         s += 1;
       }
       __syncthreads();
@@ -474,7 +476,7 @@ __device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlin
         s -= 2;
       } else {
         fft_stage_any<T, SIGN, true, CT>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
-                                         rp.L[s], tw, perm, prune && s == 0);
+                                         rp.L[s], tw, perm, prune && s == 0, s == 0);
         s -= 1;
       }
       __syncthreads();
