@@ -109,6 +109,36 @@ def test_hpsi_fp64_matches_oracle(q, ctx, name, nb):
     assert _rel_band(got, want).max() <= 1e-12
 
 
+@pytest.mark.parametrize("name,grid", [("SMALL", None), ("C0", None), ("C0", (16, 16, 16))])
+def test_hpsi_fp64_both_fft_arithmetics(q, ctx, name, grid):
+    """The FP64 path's two FFT arithmetics -- float-float pairs (default) and
+    float64 on the FP64 pipe (QE_FFT_FP64PIPE) -- each within 1e-12 of the
+    oracle, on mixed-radix grids (radix 3 and 5 twiddled stages) and on a grid
+    too small for the padding skip (C0's sphere, max |m| = 7, on 16 points:
+    4 * 7 >= 16, so the first radix-4 stage takes all four inputs)."""
+    c = _cell(name) if grid is None else _cell(name, grid=grid)
+    nb = 6
+    v, beta, d = _oracle_problem(c)
+    prob, keep, kin = _gpu_problem(q, ctx, c, nb)
+    psi = qeinputs.random_vectors(nb, len(kin), seed=11)
+    want = oracle.hpsi(c["lat"], c["k"], c["ecut"], c["grid"], v, beta, d, psi)
+    pt = _to_t(psi)
+    got = {}
+    for lab, prec in (("ff", q.QE_FP64), ("pipe", q.QE_FP64 | q.QE_FFT_FP64PIPE)):
+        ht = torch.empty_like(pt)
+        ctx.hpsi(prob, pt, ht, prec)
+        torch.cuda.synchronize()
+        got[lab] = _from_t(ht)
+        assert _rel_band(got[lab], want).max() <= 1e-12, lab
+    # the flag only selects the FFT arithmetic of QE_FP64: ignored with QE_MIXED
+    hm = torch.empty_like(pt)
+    hm2 = torch.empty_like(pt)
+    ctx.hpsi(prob, pt, hm, q.QE_MIXED)
+    ctx.hpsi(prob, pt, hm2, q.QE_MIXED | q.QE_FFT_FP64PIPE)
+    torch.cuda.synchronize()
+    assert torch.equal(hm, hm2)
+
+
 def test_hpsi_c1_full_size_fp64(q, ctx):
     c = _cell("C1")
     nb = c["nbnd"]
