@@ -212,7 +212,7 @@ int check_problem(const qe_problem* pr, const char* who) {
 
 // Device views of the problem's operator arrays (copied in when they are host arrays).
 int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView& op,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool overlap) {
   const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
   const size_t nbeta = (size_t)pr->nproj * P.h.npw * 2;
   const size_t nd = (size_t)pr->nproj * pr->nproj;
@@ -228,7 +228,21 @@ int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView
   QE_TRY(ctx->h_beta.ensure(nbeta * sizeof(double)));
   QE_TRY(ctx->h_d.ensure(nd * sizeof(double)));
   QE_CU(cudaMemcpyAsync(ctx->h_v.p, pr->vloc_r, ngrid * sizeof(double), cudaMemcpyHostToDevice, st));
-  if (pr->nproj > 0) {
+  if (pr->nproj > 0 && overlap) {
+    if (!ctx->side) {
+      QE_CU(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+      QE_CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+      QE_CU(cudaEventCreateWithFlags(&ctx->ev_op, cudaEventDisableTiming));
+    }
+    // the buffers were (re)allocated in st's order: fork after that
+    QE_CU(cudaEventRecord(ctx->ev_fork, st));
+    QE_CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    QE_CU(cudaMemcpyAsync(ctx->h_beta.p, pr->beta, nbeta * sizeof(double), cudaMemcpyHostToDevice,
+                          ctx->side));
+    QE_CU(cudaMemcpyAsync(ctx->h_d.p, pr->dmat, nd * sizeof(double), cudaMemcpyHostToDevice, ctx->side));
+    QE_CU(cudaEventRecord(ctx->ev_op, ctx->side));
+    op.ready = ctx->ev_op;
+  } else if (pr->nproj > 0) {
     QE_CU(cudaMemcpyAsync(ctx->h_beta.p, pr->beta, nbeta * sizeof(double), cudaMemcpyHostToDevice, st));
     QE_CU(cudaMemcpyAsync(ctx->h_d.p, pr->dmat, nd * sizeof(double), cudaMemcpyHostToDevice, st));
   }
@@ -259,6 +273,7 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(launch_local_kinetic<T>(P, psi, hpsi, (const T*)ctx->vp.p, ctx->sticks.p, b0, n, st,
                                    &ctx->prof, pair ? 1 : 0));
   }
+  if (op.ready) QE_CU(cudaStreamWaitEvent(st, op.ready, 0));
   if (op.nproj > 0 && std::is_same<T, float>::value) {
     // mixed precision: projector products on the tensor cores (TF32x3 split)
     const int np = op.nproj;
@@ -361,6 +376,12 @@ void qe_ctx_destroy(qe_ctx* ctx) {
   if (ctx->has_cur) cudaStreamSynchronize(ctx->cur);
   ctx->prof.reset();
   ctx_trim(ctx);
+  if (ctx->side) {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamDestroy(ctx->side);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_op);
+  }
   delete ctx;
 }
 
@@ -464,8 +485,6 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
   QE_TRY(ctx_begin(ctx, st));
   DevPlan* P = nullptr;
   QE_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
-  OpView op;
-  QE_TRY(resolve_operator(ctx, prob, *P, op, st));
   const int nb = prob->nbnd;
   const size_t nel = (size_t)nb * P->h.npw * 2;
   const double* dpsi = psi;
@@ -477,7 +496,12 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
     dpsi = (const double*)ctx->h_psi.p;
     dhpsi = (double*)ctx->h_hpsi.p;
   }
-  QE_TRY(hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st, pair, fp64_pipe));
+  // host operator: V on st, beta and D on the side stream while the FFTs run
+  OpView op;
+  QE_TRY(resolve_operator(ctx, prob, *P, op, st, prob->mem == QE_HOST && nb > 0));
+  const int rc_h = hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st, pair, fp64_pipe);
+  if (op.ready) QE_CU(cudaStreamWaitEvent(st, op.ready, 0));   // join the copy stream
+  if (rc_h) return rc_h;
   if (prob->mem == QE_HOST) {
     if (nb > 0)
       QE_CU(cudaMemcpyAsync(hpsi, dhpsi, nel * sizeof(double), cudaMemcpyDeviceToHost, st));

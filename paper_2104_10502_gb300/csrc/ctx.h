@@ -30,6 +30,10 @@ struct qe_ctx {
   // the packed beta in tc_beta belongs to the operator with this tag (0: none);
   // every API call that takes an operator gets a fresh tag
   unsigned long long tc_beta_tag = 0, op_tag = 0;
+  // copy stream for the operator of a host-memory qe_hpsi (beta and D go in
+  // while the FFTs run) and its two events (created on first use)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_op = nullptr;
   // batched H|psi> workspaces (created on first use; type private to batch.cu)
   std::shared_ptr<void> batch;
   // per-solve Davidson workspaces of a batched solve (basis, reduced matrices)
@@ -52,6 +56,9 @@ struct OpView {
   const double* vloc = nullptr;
   const double* beta = nullptr;
   const double* dmat = nullptr;
+  // set when beta and D are still being copied on the context's side stream:
+  // the projector products wait for it
+  cudaEvent_t ready = nullptr;
 };
 
 // Start of an API call on stream st (see qe_ctx::cur).
@@ -63,8 +70,11 @@ int ctx_trim(qe_ctx* ctx);
 int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, const int grid[3],
              DevPlan** out);
 int check_problem(const qe_problem* pr, const char* who);
+// overlap (host-memory problems): beta and D are copied on the context's side
+// stream and op.ready is set; the caller must make st wait for it (hpsi_core
+// does before the projector products) before the call returns.
 int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView& op,
-                     cudaStream_t st);
+                     cudaStream_t st, bool overlap = false);
 // H psi for nb bands already on the device.  pair (k = 0 plans): the bands are
 // real in r, psi(-G) = conj psi(G); two share each FFT and the projections are
 // taken real, so the result is H applied to that part of each band.  fp64_pipe
