@@ -4,8 +4,10 @@
 Workload (one step): H|psi> on a block of 128 bands of the C1 cell -- cubic
 a = 20 bohr, 64 seeded random atoms (min. separation 2.5 bohr), Gaussian
 V_loc, 8 Gaussian projectors per atom (512), ecutwfc = 40 Ry (34 265 plane
-waves), FFT grid 96^3, complex128 (FP64 path).  Inputs (beta 281 MB, psi 70 MB)
-are larger than L2, so no explicit L2 flush is done between steps.
+waves), FFT grid 96^3, complex128 in and out (the FP64 path: FFT in float-float
+arithmetic, projector products as Ozaki BF16 slices; `fp64_pipe` reports the same
+step with the FFT in float64).  Inputs (beta 281 MB, psi 70 MB) are larger than
+L2, so no explicit L2 flush is done between steps.
 
 Also reported (not part of `value`): the mixed-precision H|psi> rate on the
 same cell, per-kernel device times, the roofline of the dominant kernel, an
@@ -485,7 +487,9 @@ def run_gpu(args, rank, world, local_rank):
                    "kind": "oracle", "sample": "6 band applications (3 x 2 bands) of the C1 workload"}
         line = {"metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64 / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 (FP64-accurate: FFT in float-float FP32 pairs, projector products as "
+                         "exact Ozaki BF16 slices; float64 in and out)",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "bands": nb, "npw": npw, "nproj": nproj,
                            "grid": list(grid), "l2": "inputs larger than L2 (beta 281 MB, psi 70 MB); no flush",
