@@ -84,11 +84,14 @@ def kernel_flops(name, c, npw, nst, nax, nb, nproj):
 TENSOR_KERNELS = {"k_oz_gemm"}
 
 # ---- FP32 operation count of the float-float FFT (the FP64 path's k_plane) ----------
-# FP32 instructions of one float-float operation (ff.cuh, results left
-# unnormalised): a sum 8 (two-sum of the high parts, two low-part additions), a
-# product 4 (exact product by one FMA, two cross FMAs), a fused a b + c 12; the
-# values the last stage of a transform stores are renormalised (S: a fast
-# two-sum per real part, 6 per complex value).  As FP32 flops (an FFMA 2): 8, 7, 15, 6.
+# FP32 operations of one float-float operation on a real part (ff.cuh, results
+# left unnormalised): a sum 8 (two-sum of the high parts, two low-part
+# additions), a product 4 (exact product by one FMA, two cross FMAs), a fused
+# a b + c 12; the values the last stage of a transform stores are renormalised
+# (S: a fast two-sum per real part, 6 per complex value).  As FP32 flops (an FMA
+# 2): 8, 7, 15, 6.  The kernels run the real and imaginary parts of a complex
+# value as one f32x2 instruction, so the FP32 instructions issued are half the
+# lane operations counted here (plus the lane swaps and sign flips).
 FF_INST = {"A": 8, "M": 4, "F": 12, "S": 6}
 FF_FLOP = {"A": 8, "M": 7, "F": 15, "S": 6}
 # float-float operations per butterfly (fft_device.cuh): untwiddled DFTs, twiddled

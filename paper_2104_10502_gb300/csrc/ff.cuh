@@ -82,3 +82,89 @@ __device__ __forceinline__ ff fma(ff a, ff b, ff c) {
 }
 
 }  // namespace qe
+
+// ---- two floats in one 64-bit register: the operands of the f32x2 instructions --
+// sm_100 and later execute add/sub/mul/fma.rn.f32x2 as one instruction for two
+// lanes, each lane rounded as its scalar form; a pair of float-float numbers kept
+// as (hi0, hi1), (lo0, lo1) then takes half the issue slots of two scalar ones.
+namespace qe {
+
+struct f2 {
+  unsigned long long v;
+};
+
+__device__ __forceinline__ f2 f2_of(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_split(f2 a, float& x, float& y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+// a b + c per lane
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return d;
+}
+// sign flips: both lanes, lane 0, lane 1
+__device__ __forceinline__ f2 neg2(f2 a) { return {a.v ^ 0x8000000080000000ull}; }
+__device__ __forceinline__ f2 neg2_0(f2 a) { return {a.v ^ 0x0000000080000000ull}; }
+__device__ __forceinline__ f2 neg2_1(f2 a) { return {a.v ^ 0x8000000000000000ull}; }
+// (a1, a0)
+__device__ __forceinline__ f2 swap2(f2 a) {
+  float x, y;
+  f2_split(a, x, y);
+  return f2_of(y, x);
+}
+
+// Two float-float numbers, lane by lane (the operations of ff on both lanes).
+struct ff2 {
+  f2 hi, lo;
+};
+
+__device__ __forceinline__ ff2 operator+(ff2 a, ff2 b) {
+  const f2 s = add2(a.hi, b.hi);
+  const f2 v = sub2(s, a.hi);
+  const f2 e = add2(sub2(a.hi, sub2(s, v)), sub2(b.hi, v));
+  return {s, add2(e, add2(a.lo, b.lo))};
+}
+// a - b: the two-sum of a.hi and -b.hi, written with subtractions
+__device__ __forceinline__ ff2 operator-(ff2 a, ff2 b) {
+  const f2 s = sub2(a.hi, b.hi);
+  const f2 v = sub2(s, a.hi);
+  const f2 e = sub2(sub2(a.hi, sub2(s, v)), add2(b.hi, v));
+  return {s, add2(e, sub2(a.lo, b.lo))};
+}
+__device__ __forceinline__ ff2 operator*(ff2 a, ff2 b) {
+  const f2 p = mul2(a.hi, b.hi);
+  f2 e = fma2(a.hi, b.hi, neg2(p));
+  e = fma2(a.hi, b.lo, e);
+  e = fma2(a.lo, b.hi, e);
+  return {p, e};
+}
+// a b + c
+__device__ __forceinline__ ff2 fma(ff2 a, ff2 b, ff2 c) { return a * b + c; }
+__device__ __forceinline__ ff2 ff2_settle(ff2 a) {
+  const f2 h = add2(a.hi, a.lo);
+  return {h, sub2(a.lo, sub2(h, a.hi))};
+}
+// (x, x) for a float-float x
+__device__ __forceinline__ ff2 ff2_bcast(ff x) { return {f2_of(x.hi, x.hi), f2_of(x.lo, x.lo)}; }
+
+}  // namespace qe

@@ -39,6 +39,22 @@ static int check_launch(const char* what) {
   return QE_OK;
 }
 
+// Twiddle table slots per entry in a tile's shared memory: float-float entries
+// take two elements (the (c, c) and (-t, t) pairs, fft_device.cuh), others one
+// (c, t) or w.
+template <typename T>
+__host__ __device__ constexpr int tw_slots() { return std::is_same<T, ff>::value ? 2 : 1; }
+template <typename T>
+__device__ __forceinline__ void tw_put(cx<T>* tw, int i, double a, double b) {
+  if constexpr (std::is_same<T, ff>::value) {
+    const ff c(a), t(b);
+    tw[2 * i] = {f2_of(c.hi, c.hi), f2_of(c.lo, c.lo)};
+    tw[2 * i + 1] = {f2_of(-t.hi, t.hi), f2_of(-t.lo, t.lo)};
+  } else {
+    tw[i] = {T(a), T(b)};
+  }
+}
+
 template <typename T>
 __global__ void k_vperm(const double* __restrict__ v, T* __restrict__ vp, int n1, int n2, int n3,
                         const int* __restrict__ p1, const int* __restrict__ p2,
@@ -61,9 +77,9 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   cx<T>* tw = line + (size_t)n3 * spb;
   const int s0 = sblk * spb;
   const int ns = min(spb, nst - s0);
-  for (int i = threadIdx.x; i < n3 * spb; i += blockDim.x) line[i] = {T(0), T(0)};
+  for (int i = threadIdx.x; i < n3 * spb; i += blockDim.x) line[i] = cx_zero<T>();
   const double* tw3 = J.tw3 + (ct_twiddles<T>() ? 2 * n3 : 0);
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(tw3[2 * i]), T(tw3[2 * i + 1])};
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw_put<T>(tw, i, tw3[2 * i], tw3[2 * i + 1]);
   __syncthreads();
   const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
   if (J.pair) {
@@ -74,13 +90,13 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
       const int g = J.st_g[e];
       const double2 a = pa[g];
       const double2 c = hb ? pa[(size_t)J.npw + g] : make_double2(0.0, 0.0);
-      line[J.st_z[e] * spb + (J.st_of[e] - s0)] = {T(a.x - c.y), T(a.y + c.x)};
+      line[J.st_z[e] * spb + (J.st_of[e] - s0)] = cx_from<T>(a.x - c.y, a.y + c.x);
     }
   } else {
     const double2* ps = reinterpret_cast<const double2*>(J.psi) + (size_t)(J.b0 + b) * J.npw;
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const double2 c = ps[J.st_g[e]];
-      line[J.st_z[e] * spb + (J.st_of[e] - s0)] = {T(c.x), T(c.y)};
+      line[J.st_z[e] * spb + (J.st_of[e] - s0)] = cx_from<T>(c.x, c.y);
     }
   }
   __syncthreads();
@@ -125,7 +141,8 @@ constexpr size_t kStageVMaxBytes = 113 * 1024;
 // active-column table, rounded up to 16 bytes.
 template <typename T>
 __host__ __device__ inline size_t plane_v_offset(int n1, int n2, int nax) {
-  const size_t b = ((size_t)plane_ld(n1) * n2 + n1 + n2) * sizeof(cx<T>) + (size_t)nax * sizeof(int);
+  const size_t b = ((size_t)plane_ld(n1) * n2 + (size_t)(n1 + n2) * tw_slots<T>()) * sizeof(cx<T>) +
+                   (size_t)nax * sizeof(int);
   return (b + 15) & ~(size_t)15;
 }
 
@@ -147,8 +164,8 @@ __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* sme
   const int ld = plane_ld(n1), nt = blockDim.x;
   cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
   cx<T>* tw1 = plane + (size_t)ld * n2;
-  cx<T>* tw2 = tw1 + n1;
-  int* ax = reinterpret_cast<int*>(tw2 + n2);
+  cx<T>* tw2 = tw1 + (size_t)n1 * tw_slots<T>();
+  int* ax = reinterpret_cast<int*>(tw2 + (size_t)n2 * tw_slots<T>());
   const T* v = J.vp + (size_t)pz * n1 * n2;
   T* sv = reinterpret_cast<T*>(smem + plane_v_offset<T>(n1, n2, nax));
   const bool stage = kStageV<T> && J.stage_v;
@@ -162,12 +179,12 @@ __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* sme
       for (int i = threadIdx.x; i < nv; i += nt) cp_async4(sv + i, v + i);
     }
   }
-  for (int i = threadIdx.x; i < ld * n2; i += nt) plane[i] = {T(0), T(0)};
+  for (int i = threadIdx.x; i < ld * n2; i += nt) plane[i] = cx_zero<T>();
   {
     const double* t1 = J.tw1 + (ct_twiddles<T>() ? 2 * n1 : 0);
     const double* t2 = J.tw2 + (ct_twiddles<T>() ? 2 * n2 : 0);
-    for (int i = threadIdx.x; i < n1; i += nt) tw1[i] = {T(t1[2 * i]), T(t1[2 * i + 1])};
-    for (int i = threadIdx.x; i < n2; i += nt) tw2[i] = {T(t2[2 * i]), T(t2[2 * i + 1])};
+    for (int i = threadIdx.x; i < n1; i += nt) tw_put<T>(tw1, i, t1[2 * i], t1[2 * i + 1]);
+    for (int i = threadIdx.x; i < n2; i += nt) tw_put<T>(tw2, i, t2[2 * i], t2[2 * i + 1]);
   }
   for (int i = threadIdx.x; i < nax; i += nt) ax[i] = J.ax[i];
   __syncthreads();
@@ -228,7 +245,7 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   const int s0 = sblk * spb;
   const int ns = min(spb, nst - s0);
   const double* tw3 = J.tw3 + (ct_twiddles<T>() ? 2 * n3 : 0);
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw[i] = {T(tw3[2 * i]), T(tw3[2 * i + 1])};
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw_put<T>(tw, i, tw3[2 * i], tw3[2 * i + 1]);
   const cx<T>* Wb = J.W + (size_t)b * n3 * nst;
   const FastDiv fns(ns);
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
@@ -250,15 +267,15 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
       const int g = J.st_g[e], z = J.st_z[e], s = J.st_of[e], l = s - s0;
       const int lm = s == J.self_st ? l : (l ^ 1);
       const int zm = z == 0 ? 0 : n3 - z;
-      const cx<T> w = line[z * spb + l], wm = line[zm * spb + lm];
+      double wx, wy, mx, my;
+      cx_to<T>(line[z * spb + l], wx, wy);
+      cx_to<T>(line[zm * spb + lm], mx, my);
       const double kg = J.kin[g];
       const double2 a = pa[g];
-      ha[g] = make_double2(((double)w.x + (double)wm.x) * h + kg * a.x,
-                           ((double)w.y - (double)wm.y) * h + kg * a.y);
+      ha[g] = make_double2((wx + mx) * h + kg * a.x, (wy - my) * h + kg * a.y);
       if (hb) {
         const double2 c = pa[(size_t)J.npw + g];
-        ha[(size_t)J.npw + g] = make_double2(((double)w.y + (double)wm.y) * h + kg * c.x,
-                                             ((double)wm.x - (double)w.x) * h + kg * c.y);
+        ha[(size_t)J.npw + g] = make_double2((wy + my) * h + kg * c.x, (mx - wx) * h + kg * c.y);
       }
     }
     return;
@@ -267,10 +284,11 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   double2* hp = reinterpret_cast<double2*>(J.hpsi) + (size_t)(J.b0 + b) * J.npw;
   for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const int g = J.st_g[e];
-    const cx<T> c = line[J.st_z[e] * spb + (J.st_of[e] - s0)];
+    double cr, ci;
+    cx_to<T>(line[J.st_z[e] * spb + (J.st_of[e] - s0)], cr, ci);
     const double2 p = ps[g];
     const double kg = J.kin[g];
-    hp[g] = make_double2((double)c.x * J.inv_n + kg * p.x, (double)c.y * J.inv_n + kg * p.y);
+    hp[g] = make_double2(cr * J.inv_n + kg * p.x, ci * J.inv_n + kg * p.y);
   }
 }
 
@@ -354,7 +372,7 @@ int default_spb(int n3) {
 
 template <typename T>
 size_t zsm_bytes(int n3, int spb) {
-  return ((size_t)n3 * spb + n3) * sizeof(cx<T>);
+  return ((size_t)n3 * spb + (size_t)n3 * tw_slots<T>()) * sizeof(cx<T>);
 }
 
 template <typename T>
@@ -365,7 +383,8 @@ static bool plane_stages_v(const DevPlan& P) {
 
 template <typename T>
 size_t psm_bytes(const DevPlan& P) {
-  const size_t base = ((size_t)plane_ld(P.grid[0]) * P.grid[1] + P.grid[0] + P.grid[1]) * sizeof(cx<T>) +
+  const size_t base = ((size_t)plane_ld(P.grid[0]) * P.grid[1] +
+                       (size_t)(P.grid[0] + P.grid[1]) * tw_slots<T>()) * sizeof(cx<T>) +
                       (size_t)P.h.nax * sizeof(int);
   return plane_stages_v<T>(P) ? plane_v_offset<T>(P.grid[0], P.grid[1], P.h.nax) +
                                     (size_t)P.grid[0] * P.grid[1] * sizeof(T)

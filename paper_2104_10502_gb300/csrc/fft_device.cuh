@@ -24,6 +24,50 @@ struct alignas(2 * sizeof(T)) cx {
   T x, y;
 };
 
+// A complex float-float value is kept packed: hi = (re.hi, im.hi) and lo =
+// (re.lo, im.lo), each pair one f32x2 operand, so that the operations on real
+// and imaginary parts run as one instruction for both (ff.cuh).  Same 16 bytes
+// as complex<double> in shared memory and in the stick workspace.
+template <>
+struct alignas(16) cx<ff> {
+  f2 hi, lo;
+};
+__device__ __forceinline__ ff2 as2(cx<ff> a) { return {a.hi, a.lo}; }
+__device__ __forceinline__ cx<ff> of2(ff2 a) { return {a.hi, a.lo}; }
+
+// Element construction and access that the tiles use for every element type.
+template <typename T>
+__device__ __forceinline__ cx<T> cx_zero() {
+  if constexpr (std::is_same<T, ff>::value) return {f2_of(0.f, 0.f), f2_of(0.f, 0.f)};
+  else return {T(0), T(0)};
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cx_from(double re, double im) {
+  if constexpr (std::is_same<T, ff>::value) {
+    const ff a(re), b(im);
+    return {f2_of(a.hi, b.hi), f2_of(a.lo, b.lo)};
+  } else {
+    return {T(re), T(im)};
+  }
+}
+template <typename T>
+__device__ __forceinline__ void cx_to(cx<T> a, double& re, double& im) {
+  if constexpr (std::is_same<T, ff>::value) {
+    float rh, ih, rl, il;
+    f2_split(a.hi, rh, ih);
+    f2_split(a.lo, rl, il);
+    re = (double)rh + (double)rl;
+    im = (double)ih + (double)il;
+  } else {
+    re = (double)a.x;
+    im = (double)a.y;
+  }
+}
+
+__device__ __forceinline__ cx<ff> cadd(cx<ff> a, cx<ff> b) { return of2(as2(a) + as2(b)); }
+__device__ __forceinline__ cx<ff> csub(cx<ff> a, cx<ff> b) { return of2(as2(a) - as2(b)); }
+__device__ __forceinline__ cx<ff> cscale(cx<ff> a, ff s) { return of2(as2(a) * ff2_bcast(s)); }
+
 template <typename T>
 __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T>
@@ -37,17 +81,22 @@ __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.x * s, a.y * s
 // i * s * a
 template <typename T>
 __device__ __forceinline__ cx<T> cimul(cx<T> a, T s) { return {-s * a.y, s * a.x}; }
-// SIGN i a (negations only, no products)
+// SIGN i a (negations only, no products; packed: a lane swap and a sign)
 template <int SIGN, typename T>
 __device__ __forceinline__ cx<T> rot_i(cx<T> a) {
-  if constexpr (SIGN > 0) return {-a.y, a.x};
-  else return {a.y, -a.x};
+  if constexpr (std::is_same<T, ff>::value) {
+    if constexpr (SIGN > 0) return {neg2_0(swap2(a.hi)), neg2_0(swap2(a.lo))};
+    else return {neg2_1(swap2(a.hi)), neg2_1(swap2(a.lo))};
+  } else {
+    if constexpr (SIGN > 0) return {-a.y, a.x};
+    else return {a.y, -a.x};
+  }
 }
 // A value about to be stored by the last stage of a transform: float-float
 // operations leave their results unnormalised (ff.cuh), these stores renormalise.
 template <typename T>
 __device__ __forceinline__ cx<T> settle(cx<T> a) {
-  if constexpr (std::is_same<T, ff>::value) return {ff_settle(a.x), ff_settle(a.y)};
+  if constexpr (std::is_same<T, ff>::value) return of2(ff2_settle(as2(a)));
   else return a;
 }
 
@@ -104,12 +153,55 @@ __device__ __forceinline__ void dft5(cx<T>* v) {
   v[3] = csub(r2, i2);
 }
 
+// Radix 3 and 5 on packed float-float values: the constants as broadcast pairs,
+// the products by +-i as lane swaps (rot_i); same operations as dft3 / dft5.
+template <int SIGN>
+__device__ __forceinline__ void dft3_ff(cx<ff>* v) {
+  const ff2 half = {f2_of(0.5f, 0.5f), f2_of(0.5f, 0.5f)};   // exact scaling of both parts
+  const ff2 s3 = ff2_bcast(ff(0.866025403784438646763723170752936183));   // sin(2 pi / 3)
+  const ff2 a = as2(v[0]), t1 = as2(v[1]) + as2(v[2]);
+  const ff2 t2 = a - ff2{mul2(t1.hi, half.hi), mul2(t1.lo, half.lo)};
+  const cx<ff> d = rot_i<SIGN>(of2((as2(v[1]) - as2(v[2])) * s3));
+  v[0] = of2(a + t1);
+  v[1] = of2(t2 + as2(d));
+  v[2] = of2(t2 - as2(d));
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft5_ff(cx<ff>* v) {
+  const ff2 c1 = ff2_bcast(ff(0.309016994374947424102293417182819059));
+  const ff2 c2 = ff2_bcast(ff(-0.809016994374947424102293417182819059));
+  const ff2 s1 = ff2_bcast(ff(0.951056516295153572116439333379382143));
+  const ff2 s2 = ff2_bcast(ff(0.587785252292473129168705954639072769));
+  const ff2 a = as2(v[0]);
+  const ff2 t1 = as2(v[1]) + as2(v[4]), t2 = as2(v[2]) + as2(v[3]);
+  const ff2 t3 = as2(v[1]) - as2(v[4]), t4 = as2(v[2]) - as2(v[3]);
+  const ff2 r1 = (a + c1 * t1) + c2 * t2;
+  const ff2 r2 = (a + c2 * t1) + c1 * t2;
+  // SIGN i (|s1| t3 + |s2| t4) and SIGN i (|s2| t3 - |s1| t4)
+  const ff2 i1 = as2(rot_i<SIGN>(of2(s1 * t3 + s2 * t4)));
+  const ff2 i2 = as2(rot_i<SIGN>(of2(s2 * t3 - s1 * t4)));
+  v[0] = of2(a + (t1 + t2));
+  v[1] = of2(r1 + i1);
+  v[4] = of2(r1 - i1);
+  v[2] = of2(r2 + i2);
+  v[3] = of2(r2 - i2);
+}
+
 template <typename T, int SIGN, int R>
 __device__ __forceinline__ void dftR(cx<T>* v) {
-  if constexpr (R == 2) dft2<T, SIGN>(v);
-  else if constexpr (R == 3) dft3<T, SIGN>(v);
-  else if constexpr (R == 4) dft4<T, SIGN>(v);
-  else dft5<T, SIGN>(v);
+  constexpr bool kFF = std::is_same<T, ff>::value;
+  if constexpr (R == 2) {
+    dft2<T, SIGN>(v);
+  } else if constexpr (R == 3) {
+    if constexpr (kFF) dft3_ff<SIGN>(v);
+    else dft3<T, SIGN>(v);
+  } else if constexpr (R == 4) {
+    dft4<T, SIGN>(v);
+  } else {
+    if constexpr (kFF) dft5_ff<SIGN>(v);
+    else dft5<T, SIGN>(v);
+  }
 }
 
 // Twiddle exp(SIGN 2 pi i t / n) from the table tw[t] = exp(-2 pi i t / n).
@@ -154,20 +246,82 @@ struct FastDiv {
   }
 };
 
-// x = a + s u, y = a - s u.  In float-float the product s u is formed once and
-// added and subtracted (8 + 4 + 8 instead of 2 x 12 instructions per real part;
-// the same results as two fused operations, whose two-sums are exact); in float
-// and double two FMAs.
+// x = a + s u, y = a - s u (two FMAs each part)
 template <typename T>
 __device__ __forceinline__ void axpm(cx<T> a, T s, cx<T> u, cx<T>& x, cx<T>& y) {
-  if constexpr (std::is_same<T, ff>::value) {
-    const cx<T> p = {s * u.x, s * u.y};
-    x = cadd(a, p);
-    y = csub(a, p);
+  x = caxpy(a, s, u);
+  y = caxpy(a, -s, u);
+}
+
+// ---- the same butterflies on packed float-float values ---------------------------
+// Table entry t is two values: C = (c, c) and T = (-t, t) as pairs (c and t of
+// exp(-2 pi i t / n)), so that v (1 + i t) = v + T * (v.im, v.re) is one fused
+// pair operation on the lane-swapped v, and a scale by c one pair product.  The
+// conjugate twiddle (SIGN > 0) negates T.  a +- c u share the product c u (the
+// same results as two fused operations: their two-sums are exact).
+template <int SIGN>
+__device__ __forceinline__ ff2 tw_t(const cx<ff>* tw, int t) {
+  const ff2 x = as2(tw[2 * t + 1]);
+  if constexpr (SIGN < 0) return x;
+  else return {neg2(x.hi), neg2(x.lo)};
+}
+__device__ __forceinline__ ff2 tw_c(const cx<ff>* tw, int t) { return as2(tw[2 * t]); }
+// v (1 + i t) with tt = (-t, t)
+__device__ __forceinline__ ff2 rot1_ff(ff2 v, ff2 tt) {
+  return tt * ff2{swap2(v.hi), swap2(v.lo)} + v;
+}
+__device__ __forceinline__ void axpm_ff(ff2 a, ff2 c, ff2 u, ff2& x, ff2& y) {
+  const ff2 p = c * u;
+  x = a + p;
+  y = a - p;
+}
+template <int SIGN>
+__device__ __forceinline__ ff2 rot_i_ff(ff2 a) { return as2(rot_i<SIGN>(of2(a))); }
+
+template <int SIGN, int R>
+__device__ __forceinline__ void bfly_ct_ff(cx<ff>* v, const cx<ff>* tw, int i1) {
+  if constexpr (R == 2) {
+    const ff2 u = rot1_ff(as2(v[1]), tw_t<SIGN>(tw, i1));
+    ff2 x, y;
+    axpm_ff(as2(v[0]), tw_c(tw, i1), u, x, y);
+    v[0] = of2(x);
+    v[1] = of2(y);
+  } else if constexpr (R == 4) {
+    const ff2 t1 = tw_t<SIGN>(tw, i1), t2 = tw_t<SIGN>(tw, 2 * i1);
+    const ff2 c1 = tw_c(tw, i1), c2 = tw_c(tw, 2 * i1);
+    const ff2 u2 = rot1_ff(as2(v[2]), t2), u3 = rot1_ff(as2(v[3]), t2);
+    ff2 a, b, e, f, x0, x1, x2, x3;
+    axpm_ff(as2(v[0]), c2, u2, a, b);
+    axpm_ff(as2(v[1]), c2, u3, e, f);
+    e = rot1_ff(e, t1);
+    f = rot1_ff(f, t1);
+    axpm_ff(a, c1, e, x0, x2);
+    axpm_ff(b, c1, rot_i_ff<SIGN>(f), x1, x3);
+    v[0] = of2(x0);
+    v[1] = of2(x1);
+    v[2] = of2(x2);
+    v[3] = of2(x3);
   } else {
-    x = caxpy(a, s, u);
-    y = caxpy(a, -s, u);
+#pragma unroll
+    for (int q = 1; q < R; ++q)
+      v[q] = of2(tw_c(tw, q * i1) * rot1_ff(as2(v[q]), tw_t<SIGN>(tw, q * i1)));
+    dftR<ff, SIGN, R>(v);
   }
+}
+
+template <int SIGN>
+__device__ __forceinline__ void bfly_ct_ends_ff(const cx<ff>* v, const cx<ff>* tw, int i1,
+                                                cx<ff>& x0, cx<ff>& x3) {
+  const ff2 t1 = tw_t<SIGN>(tw, i1), t2 = tw_t<SIGN>(tw, 2 * i1);
+  const ff2 c1 = tw_c(tw, i1), c2 = tw_c(tw, 2 * i1);
+  const ff2 u2 = rot1_ff(as2(v[2]), t2), u3 = rot1_ff(as2(v[3]), t2);
+  ff2 a, b, e, f;
+  axpm_ff(as2(v[0]), c2, u2, a, b);
+  axpm_ff(as2(v[1]), c2, u3, e, f);
+  e = rot1_ff(e, t1);
+  f = rot1_ff(f, t1);
+  x0 = of2(c1 * e + a);
+  x3 = of2(b - c1 * rot_i_ff<SIGN>(f));
 }
 
 // Twiddled butterfly on (c, t) tables: y_0 = v_0, y_q = w^q v_q (w^q = tw[q i1],
@@ -176,7 +330,9 @@ __device__ __forceinline__ void axpm(cx<T> a, T s, cx<T> u, cx<T>& x, cx<T>& y) 
 // w^2 are read, each scale c multiplying into an FMA of the butterfly.
 template <typename T, int SIGN, int R>
 __device__ __forceinline__ void bfly_ct(cx<T>* v, const cx<T>* tw, int i1) {
-  if constexpr (R == 2) {
+  if constexpr (std::is_same<T, ff>::value) {
+    bfly_ct_ff<SIGN, R>(v, tw, i1);
+  } else if constexpr (R == 2) {
     const cx<T> w1 = twid<T, SIGN>(tw, i1);
     const cx<T> u = rot1(v[1], w1.y), a = v[0];
     axpm(a, w1.x, u, v[0], v[1]);
@@ -207,6 +363,10 @@ __device__ __forceinline__ void bfly_ct(cx<T>* v, const cx<T>* tw, int i1) {
 template <typename T, int SIGN>
 __device__ __forceinline__ void bfly_ct_ends(const cx<T>* v, const cx<T>* tw, int i1, cx<T>& x0,
                                              cx<T>& x3) {
+  if constexpr (std::is_same<T, ff>::value) {
+    bfly_ct_ends_ff<SIGN>(v, tw, i1, x0, x3);
+    return;
+  } else {
   const cx<T> w1 = twid<T, SIGN>(tw, i1), w2 = twid<T, SIGN>(tw, 2 * i1);
   const cx<T> u2 = rot1(v[2], w2.y), u3 = rot1(v[3], w2.y);
   cx<T> a, b, e, f;
@@ -216,6 +376,7 @@ __device__ __forceinline__ void bfly_ct_ends(const cx<T>* v, const cx<T>* tw, in
   f = rot1(f, w1.y);
   x0 = caxpy(a, w1.x, e);
   x3 = caxpy(b, -w1.x, rot_i<SIGN>(f));
+  }
 }
 
 // One radix-R stage over `nlines` lines of length n.  Element e of line l sits
@@ -294,7 +455,7 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
       const int i1 = DIT ? j * tstep : (blk == 0 ? 0 : __ldg(perm + blk * L) * M);
       if (i1 != 0) bfly_ct<T, SIGN, R>(v, tw, i1);
       else dftR<T, SIGN, R>(v);
-    } else if (DIT) {
+    } else if constexpr (DIT) {
       // j == 0 (every butterfly when M == 1): every twiddle is 1, skip the
       // products; consecutive threads share j in the line-fast passes, so the
       // branch is uniform across most warps
@@ -310,8 +471,13 @@ __device__ __forceinline__ void fft_stage(cx<T>* base, int es, int ls, const int
         for (int q = 1; q < R; ++q) v[q] = cmul(v[q], twid<T, SIGN>(tw, j * q * tstep));
       }
     }
+    if (fin) {   // uniform across the block: one branch per stage, no per-value select
 #pragma unroll
-    for (int q = 0; q < R; ++q) p[q * step] = fin ? settle(v[q]) : v[q];
+      for (int q = 0; q < R; ++q) p[q * step] = settle(v[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) p[q * step] = v[q];
+    }
   }
 }
 
@@ -456,11 +622,16 @@ __device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlin
   if (!DIT) {
     int s = 0;
     while (s < rp.nst) {
-      if (FUSE && s + 1 < rp.nst && rp.r[s] * rp.r[s + 1] <= fuse_limit<T>()) {
-        fft_stage2_any<T, SIGN, false>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
-                                       rp.r[s + 1], rp.L[s], tw);
-        s += 2;
-      } else {
+      bool fused = false;
+      if constexpr (FUSE) {
+        if (s + 1 < rp.nst && rp.r[s] * rp.r[s + 1] <= fuse_limit<T>()) {
+          fft_stage2_any<T, SIGN, false>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
+                                         rp.r[s + 1], rp.L[s], tw);
+          s += 2;
+          fused = true;
+        }
+      }
+      if (!fused) {
         fft_stage_any<T, SIGN, false, CT>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
                                           rp.L[s], tw, perm, prune && s == 0, s == rp.nst - 1);
         s += 1;
@@ -470,11 +641,16 @@ __device__ void fft_lines(cx<T>* base, int es, int ls, const int* lofs, int nlin
   } else {
     int s = rp.nst - 1;
     while (s >= 0) {
-      if (FUSE && s >= 1 && rp.r[s - 1] * rp.r[s] <= fuse_limit<T>()) {
-        fft_stage2_any<T, SIGN, true>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s - 1],
-                                      rp.r[s], rp.L[s - 1], tw);
-        s -= 2;
-      } else {
+      bool fused = false;
+      if constexpr (FUSE) {
+        if (s >= 1 && rp.r[s - 1] * rp.r[s] <= fuse_limit<T>()) {
+          fft_stage2_any<T, SIGN, true>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s - 1],
+                                        rp.r[s], rp.L[s - 1], tw);
+          s -= 2;
+          fused = true;
+        }
+      }
+      if (!fused) {
         fft_stage_any<T, SIGN, true, CT>(base, es, ls, lofs, nlines, line_fast, rp.n, rp.r[s],
                                          rp.L[s], tw, perm, prune && s == 0, s == 0);
         s -= 1;
