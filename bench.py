@@ -415,17 +415,19 @@ def run_gpu(args, rank, world, local_rank):
     elif dom == "k_plane":
         # float-float FFT on the FP32 pipes: FP32 flops of its float-float
         # operations (model above, per band) against the FP32 FMA peak of
-        # 152 SMs x 128 lanes x 2 flops x 2.07 GHz; issue_frac counts FP32
-        # instructions against the issue limit (one warp instruction per clock
-        # and sub-partition) instead
+        # 152 SMs x 128 lanes x 2 flops x 2.07 GHz; issue_frac counts its f32x2
+        # instructions (two lane operations each; ncu counts 219 M per C1 band
+        # against the model's 223 M) against the issue limit of one warp
+        # instruction per clock and sub-partition
         half = plane_halves(c)
-        inst_b, flop_b = ff_plane_launch(c, plan_nax, 1, half)
+        ops_b, flop_b = ff_plane_launch(c, plan_nax, 1, half)
+        inst_b = ops_b / 2          # f32x2: one instruction per two lane operations
         bands_step = nb * (1 if nb else 0)
         fl_step = flop_b * bands_step
         bound, peak = "alu", FP32_NOMINAL_TFLOPS
         psrc = "nominal FP32 FMA rate of GB300 (recipe table: 152 SMs, 2.07 GHz; 128 lanes per SM)"
         inst_step = inst_b * bands_step
-        extra = {"fp32_inst_per_band": inst_b, "fp32_flops_per_band": flop_b,
+        extra = {"fp32_ops_per_band": ops_b, "fp32x2_inst_per_band": inst_b, "fp32_flops_per_band": flop_b,
                  "fp64_equiv_tflops": kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
                  * args.steps / (tot / 1e3) / 1e12,
                  "issue_frac": inst_step * args.steps / (tot / 1e3) / (FP32_NOMINAL_TFLOPS / 2 * 1e12)}
