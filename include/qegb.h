@@ -157,7 +157,10 @@ int qe_beta_gaussian(qe_ctx* ctx, const double lat[9], const double k[3],
  * in float64 or as Ozaki BF16 slice products on the tensor cores) or QE_MIXED
  * (FP32 FFTs and FP32 projector products, float64 in and out), optionally
  * or-ed with QE_GAMMA (k = 0: bands real in r, two per FFT) and, with
- * QE_FP64, QE_FFT_FP64PIPE.
+ * QE_FP64, QE_FFT_FP64PIPE.  The float-float FFT has the exponent range of
+ * float: it keeps the 1e-12 accuracy for coefficients and potential values of
+ * magnitude within about 1e-25 .. 1e25 (wavefunctions of any normalisation in
+ * practice); outside that range use QE_FFT_FP64PIPE.
  * Errors: QE_EINVAL for bad sizes or a grid smaller than the sphere needs. */
 int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
             const double* psi, double* hpsi, void* stream);
