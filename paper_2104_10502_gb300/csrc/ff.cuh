@@ -4,24 +4,30 @@
 // float-float arithmetic on the FP32 pipes outruns the same FFT on the FP64 pipe
 // while staying within a few units of 2^-48 per operation.
 //
+// `ff` is the storage and constant type (one value); the arithmetic runs on
+// `ff2`, two values at once, each pair of parts one 64-bit operand of the f32x2
+// instructions (sm_100 and later: add/sub/mul/fma.rn.f32x2, one instruction for
+// two lanes, each lane rounded as its scalar form), which halves the issue slots.
+// The FFT packs the real and imaginary parts of a complex value into the lanes.
+//
 // Error-free transformations used (Knuth's two-sum, Dekker's fast two-sum, the
 // exact product a b - fl(a b) as one FMA); sums take the "sloppy" form, whose
 // error is bounded relative to |a| + |b|, which is what a transform's norm-wise
-// error needs.  Every step is written with the _rn intrinsics so that the
-// compiler never contracts a product and a sum into one FMA: the
-// transformations rely on each rounding happening where it is written.
+// error needs.  Every step is one inline-PTX .rn instruction, so the compiler
+// never contracts a product and a sum into one FMA: the transformations rely on
+// each rounding happening where it is written.
 //
-// The arithmetic operators leave their result unnormalised: (s, e) with s the
-// rounded sum (or product) of the high parts and e the exact error of that plus
-// the low parts, |e| a few units of 2^-24 |s| (without cancellation) instead of
-// at most half an ulp.  The two-sum of the high parts is exact for any inputs
-// and every low-part rounding stays ~2^-24 of a term already ~2^-24 of the
-// operands, so the norm-wise error is that of normalised arithmetic, while a
-// sum costs 8 instructions instead of 11, a product 4 instead of 7, a fused
-// a b + c 12 instead of 15.  ff_settle renormalises; a transform settles what
-// its last stage stores, which bounds the growth of e to the few operations per
-// element of one transform (the products that drop lo x lo take a normalised
-// twiddle or potential as one factor).
+// The operators leave their result unnormalised: (s, e) with s the rounded sum
+// (or product) of the high parts and e the exact error of that plus the low
+// parts, |e| a few units of 2^-24 |s| (without cancellation) instead of at most
+// half an ulp.  The two-sum of the high parts is exact for any inputs and every
+// low-part rounding stays ~2^-24 of a term already ~2^-24 of the operands, so
+// the norm-wise error is that of normalised arithmetic, while a sum costs 8
+// instructions instead of 11, a product 4 (+1 sign flip) instead of 7, a fused
+// a b + c 12 instead of 15 (per lane pair).  ff2_settle renormalises; a
+// transform settles what its last stage stores, which bounds the growth of e to
+// the few operations per element of one transform (the products that drop
+// lo x lo take a normalised twiddle or potential as one factor).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,55 +45,8 @@ struct ff {
   __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
-// (s, e) -> hi + lo for |s| >= |e| (fast two-sum)
-__device__ __forceinline__ ff ff_norm(float s, float e) {
-  const float h = __fadd_rn(s, e);
-  return ff(h, __fsub_rn(e, __fsub_rn(h, s)));
-}
-
-__device__ __forceinline__ ff ff_settle(ff a) { return ff_norm(a.hi, a.lo); }
-
-// a + b: two-sum of the high parts, low parts added into the error
-__device__ __forceinline__ ff operator+(ff a, ff b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float v = __fsub_rn(s, a.hi);
-  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
-  return ff(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
-}
-
-__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
-__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
-
-// a b: exact product of the high parts plus the cross terms
-__device__ __forceinline__ ff operator*(ff a, ff b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return ff(p, e);
-}
-
-// a b + c (an overload beside the float and double fma,
-// so that code templated on the element type calls fma for all three)
-using ::fma;
-__device__ __forceinline__ ff fma(ff a, ff b, ff c) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  const float s = __fadd_rn(p, c.hi);
-  const float v = __fsub_rn(s, p);
-  const float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, v)), __fsub_rn(c.hi, v));
-  return ff(s, __fadd_rn(t, __fadd_rn(e, c.lo)));
-}
-
-}  // namespace qe
 
 // ---- two floats in one 64-bit register: the operands of the f32x2 instructions --
-// sm_100 and later execute add/sub/mul/fma.rn.f32x2 as one instruction for two
-// lanes, each lane rounded as its scalar form; a pair of float-float numbers kept
-// as (hi0, hi1), (lo0, lo1) then takes half the issue slots of two scalar ones.
-namespace qe {
 
 struct f2 {
   unsigned long long v;
@@ -133,7 +92,7 @@ __device__ __forceinline__ f2 swap2(f2 a) {
   return f2_of(y, x);
 }
 
-// Two float-float numbers, lane by lane (the operations of ff on both lanes).
+// Two float-float numbers, lane by lane.
 struct ff2 {
   f2 hi, lo;
 };
@@ -158,7 +117,9 @@ __device__ __forceinline__ ff2 operator*(ff2 a, ff2 b) {
   e = fma2(a.lo, b.hi, e);
   return {p, e};
 }
-// a b + c
+// a b + c (an overload beside the float and double fma, so that code templated
+// on the element type calls fma for all of them)
+using ::fma;
 __device__ __forceinline__ ff2 fma(ff2 a, ff2 b, ff2 c) { return a * b + c; }
 __device__ __forceinline__ ff2 ff2_settle(ff2 a) {
   const f2 h = add2(a.hi, a.lo);
