@@ -84,7 +84,9 @@ def _oracle_h(c, psi):
     return oracle.hpsi(lat, k, ecut, grid, v, beta, d, psi)
 
 
-@pytest.mark.parametrize("nb,prec,tol", [(8, 0, 1e-12), (7, 0, 1e-12), (1, 0, 1e-12), (9, 1, 2e-5)])
+# prec: 0 = QE_FP64 (float-float FFT), 1 = QE_MIXED, 0x400 = QE_FP64 | QE_FFT_FP64PIPE
+@pytest.mark.parametrize("nb,prec,tol", [(8, 0, 1e-12), (7, 0, 1e-12), (1, 0, 1e-12), (9, 1, 2e-5),
+                                         (7, 0x400, 1e-12)])
 def test_gamma_hpsi_matches_oracle(q, ctx, nb, prec, tol):
     c = qeinputs.config("C0")
     prob, keep, miller, kin = _problem(q, ctx, c, nb)
