@@ -724,12 +724,70 @@ __device__ void multisect(const F* d, const F* e2, int n, int k, F tiny, F& lo, 
   }
 }
 
+// ---- float-float Sturm counts (the FP64 bisection's final rounds) ---------------------
+// GB300 runs FP64 at 1/64 of its FP32 rate and the Sturm recurrence is a chain of
+// dependent divisions, so its FP64 rounds are latency-bound at the FP64 pipe's
+// pace.  Float-float (ff.cuh: hi + lo floats, 48-bit significand, normalised
+// here) counts with a backward error of a few units of 2^-47 ||T||, resolving
+// eigenvalues to ~1e-14 ||T||; the division takes an approximate quotient of the
+// high parts and one correction from the exact remainder (~2^-44 relative).
+__device__ __forceinline__ ff ffs_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return ff(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+// a - b (Knuth's two-sum of a.hi and -b.hi, then the low parts)
+__device__ __forceinline__ ff ffs_sub(ff a, ff b) {
+  const float s = __fsub_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fsub_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fadd_rn(b.hi, v));
+  return ffs_norm(s, __fadd_rn(e, __fsub_rn(a.lo, b.lo)));
+}
+// a / b
+__device__ __forceinline__ ff ffs_div(ff a, ff b) {
+  const float r = __fdividef(a.hi, b.hi);
+  const float p = __fmul_rn(r, b.hi);
+  const float pe = __fmaf_rn(r, b.lo, __fmaf_rn(r, b.hi, -p));   // r b = p + pe
+  const ff d = ffs_sub(a, ff(p, pe));                              // the remainder a - r b
+  return ffs_norm(r, __fdividef(d.hi, b.hi));
+}
+__device__ int sturm_count_ff(const ff* d, const ff* e2, int n, ff x, float tiny) {
+  int cnt = 0;
+  ff q = ffs_sub(d[0], x);
+  if (q.hi == 0.f) q = ff(-tiny, 0.f);
+  if (q.hi < 0.f) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = ffs_sub(ffs_sub(d[i], x), ffs_div(e2[i - 1], q));
+    if (q.hi == 0.f) q = ff(-tiny, 0.f);
+    if (q.hi < 0.f) ++cnt;
+  }
+  return cnt;
+}
+// multisect with float-float counts on a double bracket, down to `width`
+__device__ void multisect_ff(const ff* d, const ff* e2, int n, int k, float tiny, double& lo,
+                             double& hi, double width) {
+  const int lane = threadIdx.x & 31;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= width) break;
+    const double step = (hi - lo) / 33.0;
+    const double x = lo + step * (lane + 1);
+    const int c = (x > lo && x < hi) ? sturm_count_ff(d, e2, n, ff(x), tiny) : (x <= lo ? 0 : n);
+    const unsigned above = __ballot_sync(0xffffffffu, c > k);
+    const int first = above ? __ffs(above) - 1 : 32;
+    const double nlo = first == 0 ? lo : lo + step * first;
+    const double nhi = first == 32 ? hi : lo + step * (first + 1);
+    if (!(nhi < hi || nlo > lo)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+}
+
 // One warp per eigenvalue, two per CTA; d and e^2 staged in shared memory.
 // FP64: the bracket is first narrowed in FP32 (d, e^2 rounded to float, ~60x the
 // FP64 rate on GB300) to 64 float ulps of ||T||, widened by 16 ulps (the
 // rounding of T and the Sturm count's backward error are a few ulps of ||T||),
-// and finished in FP64: about 4 of the ~11 FP64 rounds are saved.
-// Dynamic shared memory: n (d) + n (e^2) R, and 2 n floats in FP64.
+// then in float-float to 2^-42 ||T|| (the counts' resolution, ~1e-13 ||T||),
+// and finished by at most a few FP64 rounds to the FP64 resolution.
+// Dynamic shared memory: n (d) + n (e^2) R, and in FP64 2 n floats + 2 n ff.
 __global__ void __launch_bounds__(64) k_bisect(const R* d, const R* e, int n, int nev,
                                                 R* w) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -741,10 +799,14 @@ __global__ void __launch_bounds__(64) k_bisect(const R* d, const R* e, int n, in
   }
   float* fd = reinterpret_cast<float*>(se2 + n);
   float* fe2 = fd + n;
+  ff* xd = reinterpret_cast<ff*>(fe2 + n);
+  ff* xe2 = xd + n;
   if constexpr (sizeof(R) == 8) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       fd[i] = (float)d[i];
       fe2[i] = i < n - 1 ? (float)(e[i] * e[i]) : 0.f;
+      xd[i] = ff((double)d[i]);
+      xe2[i] = i < n - 1 ? ff((double)(e[i] * e[i])) : ff(0.0);
     }
   }
   __syncthreads();
@@ -778,6 +840,13 @@ __global__ void __launch_bounds__(64) k_bisect(const R* d, const R* e, int n, in
     const R pad = R(16) * R(fe) * nrm + RealT<R>::tiny;
     lo = fmax(lo, R(flo) - pad);
     hi = fmin(hi, R(fhi) + pad);
+    // float-float rounds down to 2^-42 ||T||, widened by 2^-44 ||T|| (their
+    // counts' backward error is a few units of 2^-47 ||T||)
+    double xlo = lo, xhi = hi;
+    multisect_ff(xd, xe2, n, k, (float)fmax(1e-30 * nrm, 1e-30), xlo, xhi, 0x1p-42 * nrm);
+    const R xpad = 0x1p-44 * nrm + RealT<R>::tiny;
+    lo = fmax(lo, R(xlo) - xpad);
+    hi = fmin(hi, R(xhi) + xpad);
   }
   multisect<R>(sd, se2, n, k, tiny, lo, hi, RealT<R>::eps, R(0));
   if (lane == 0) w[k] = R(0.5) * (lo + hi);
@@ -1055,7 +1124,7 @@ static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, c
   {
     ProfScope ps(pf, "heev_bisect", st);
     // two warps per block: the Sturm counts are FP64-bound, so spread them over the SMs
-    const size_t bsm_b = (size_t)n * (2 * sizeof(R) + (sizeof(R) == 8 ? 2 * sizeof(float) : 0));
+    const size_t bsm_b = (size_t)n * (2 * sizeof(R) + (sizeof(R) == 8 ? 2 * sizeof(float) + 2 * sizeof(ff) : 0));
     set_max_dynamic_smem(k_bisect);
     k_bisect<<<(nev * 32 + 63) / 64, 64, bsm_b, st>>>(wk.d, wk.e, n, nev, w);
   }
