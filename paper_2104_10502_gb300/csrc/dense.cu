@@ -17,4 +17,5 @@
 // The multi-CTA kernels are cooperative launches with a bounded grid barrier.
 #define QE_DENSE_R double
 #define QE_DENSE_NS qe
+#define QE_DENSE_FP64 1
 #include "dense_impl.cuh"

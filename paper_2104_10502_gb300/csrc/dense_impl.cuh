@@ -553,6 +553,7 @@ __global__ void __launch_bounds__(256) k_tridiag_coop(z* A, int n, int lda, z* t
 // kTridRows rows per CTA.  Dynamic shared memory: (ceil(n / G) + 3) n complex.
 constexpr int kTridRows = 8;
 
+#if !defined(QE_DENSE_FP64)   // FP64: k_tridiag_rows_ff below
 __global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* tau, R* e, R* dg,
                                                       z* refl, GridBar bar) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -682,6 +683,8 @@ __global__ void __launch_bounds__(256) k_tridiag_rows(z* A, int n, int lda, z* t
     __syncthreads();   // the next reflector reads all of sx
   }
 }
+#endif
+
 
 // ---- tridiagonal eigenvalues: Sturm bisection, one thread per eigenvalue --------
 // Number of eigenvalues of T below x (Sturm sequence in the ratio form, e2 the
@@ -780,6 +783,235 @@ __device__ void multisect_ff(const ff* d, const ff* e2, int n, int k, float tiny
     hi = nhi;
   }
 }
+
+#if defined(QE_DENSE_FP64)
+// ---- the FP64 tridiagonalisation in float-float arithmetic ---------------------------
+// k_tridiag_rows with every value a packed float-float complex number (ff.cuh:
+// lanes (re, im), hi and lo pairs; 48-bit significands) instead of complex
+// double: the same rows, exchange vectors, barriers and reflectors, with the
+// FP64 pipe's work (12 FMAs per element and step) moved to the FP32 pipes.  The
+// reduction's backward error is a few units of 2^-46 ||A|| instead of 2^-53,
+// ~1e-14 ||A||, far below the 1e-10 eigenvalue tolerance of the FP64 solves;
+// d, e, tau and the reflectors leave in double.
+// exchange vectors written by other CTAs: read through L2 (as ldz)
+__device__ __forceinline__ ff2 pk_load(const z* p) {
+  const ulonglong2 u = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+  return {{u.x}, {u.y}};
+}
+__device__ __forceinline__ void pk_store(z* p, ff2 a) { *reinterpret_cast<cx<ff>*>(p) = of2(a); }
+__device__ __forceinline__ ff2 pk_re(ff2 a) {   // (re, re)
+  float rh, ih, rl, il;
+  f2_split(a.hi, rh, ih);
+  f2_split(a.lo, rl, il);
+  return {f2_of(rh, rh), f2_of(rl, rl)};
+}
+__device__ __forceinline__ ff2 pk_im(ff2 a) {   // (im, im)
+  float rh, ih, rl, il;
+  f2_split(a.hi, rh, ih);
+  f2_split(a.lo, rl, il);
+  return {f2_of(ih, ih), f2_of(il, il)};
+}
+__device__ __forceinline__ ff2 pk_i(ff2 a) { return {neg2_0(swap2(a.hi)), neg2_0(swap2(a.lo))}; }   // i a
+__device__ __forceinline__ ff2 pk_conj(ff2 a) { return {neg2_1(a.hi), neg2_1(a.lo)}; }
+__device__ __forceinline__ ff2 pk_neg(ff2 a) { return {neg2(a.hi), neg2(a.lo)}; }
+__device__ __forceinline__ ff2 pk_zero() { return {f2_of(0.f, 0.f), f2_of(0.f, 0.f)}; }
+// acc + a b (complex): re(a) b + im(a) (i b) + acc
+__device__ __forceinline__ ff2 pk_fma(ff2 a, ff2 b, ff2 acc) {
+  return fma(pk_im(a), pk_i(b), fma(pk_re(a), b, acc));
+}
+__device__ __forceinline__ ff2 pk_mul(ff2 a, ff2 b) { return fma(pk_im(a), pk_i(b), pk_re(a) * b); }
+__device__ __forceinline__ ff2 pk_shfl_xor(ff2 a, int o) {
+  return {{__shfl_xor_sync(0xffffffffu, a.hi.v, o)}, {__shfl_xor_sync(0xffffffffu, a.lo.v, o)}};
+}
+// block sum (all threads get it; fixed order, so every CTA forms the same value)
+__device__ __forceinline__ ff2 pk_block_sum(ff2 a, cx<ff> (*buf)[8], int par) {
+  for (int o = 16; o > 0; o >>= 1) a = a + pk_shfl_xor(a, o);   // two-sums exact: same in every lane
+  if ((threadIdx.x & 31) == 0) buf[par][threadIdx.x >> 5] = of2(ff2_settle(a));
+  __syncthreads();
+  ff2 t = as2(buf[par][0]);
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = t + as2(buf[par][w]);
+  return ff2_settle(t);
+}
+// scalar parts and float-float scalar arithmetic (normalised)
+__device__ __forceinline__ ff pk_get_re(ff2 a) {
+  float rh, ih, rl, il;
+  f2_split(a.hi, rh, ih);
+  f2_split(a.lo, rl, il);
+  return ff(rh, rl);
+}
+__device__ __forceinline__ ff pk_get_im(ff2 a) {
+  float rh, ih, rl, il;
+  f2_split(a.hi, rh, ih);
+  f2_split(a.lo, rl, il);
+  return ff(ih, il);
+}
+__device__ __forceinline__ ff2 pk_make(ff re, ff im) { return {f2_of(re.hi, im.hi), f2_of(re.lo, im.lo)}; }
+__device__ __forceinline__ ff ffs_neg(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff ffs_add(ff a, ff b) { return ffs_sub(a, ffs_neg(b)); }
+__device__ __forceinline__ ff ffs_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ffs_norm(p, e);
+}
+// sqrt(a), a >= 0: float root and one correction from the exact remainder
+__device__ __forceinline__ ff ffs_sqrt(ff a) {
+  if (!(a.hi > 0.f)) return ff(0.f, 0.f);
+  const float r = sqrtf(a.hi);
+  const float p = __fmul_rn(r, r);
+  const float pe = __fmaf_rn(r, r, -p);
+  const ff d = ffs_sub(a, ff(p, pe));
+  return ffs_norm(r, __fdividef(d.hi, __fmul_rn(2.f, r)));
+}
+__device__ __forceinline__ double ffs_to_d(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ z pk_to_z(ff2 a) {
+  const ff r = pk_get_re(a), i = pk_get_im(a);
+  return {ffs_to_d(r), ffs_to_d(i)};
+}
+
+__global__ void __launch_bounds__(256) k_tridiag_rows_ff(z* A, int n, int lda, z* tau, R* e,
+                                                         R* dg, z* refl, GridBar bar) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  const int nrmax = (n + G - 1) / G;
+  const int nr = c < n ? (n - 1 - c) / G + 1 : 0;   // rows owned: c + q G, q < nr
+  cx<ff>* rows = reinterpret_cast<cx<ff>*>(smem_raw);   // nrmax x n
+  cx<ff>* sv = rows + (size_t)nrmax * n;               // reflector v (index i <-> row j+1+i)
+  cx<ff>* sw = sv + n;                                 // p, then w
+  cx<ff>* sx = sw + n;                                 // column to reduce
+  __shared__ cx<ff> rb[2][8];
+  __shared__ cx<ff> spart[8][kTridRows];
+  for (int q = 0; q < nr; ++q) {
+    const z* src = A + (size_t)(c + q * G) * lda;
+    for (int k = tid; k < n; k += nt) {
+      const z a = ldz(src + k);
+      rows[(size_t)q * n + k] = cx_from<ff>(a.x, a.y);
+    }
+  }
+  for (int i = tid; i < n - 1; i += nt) {
+    const z a = ldz(&A[(size_t)(1 + i) * lda]);
+    sx[i] = cx_from<ff>(a.x, a.y);
+  }
+  if (c == 0 && tid == 0) dg[0] = ldz(&A[0]).x;
+  // every CTA has read A: its rows 0..3 become the exchange vectors
+  if (!grid_sync_mono(bar, 1)) return;
+  const ff2 one = {f2_of(1.f, 0.f), f2_of(0.f, 0.f)};
+  for (int j = 0; j < n - 1; ++j) {
+    const int m = n - 1 - j, par = j & 1;
+    z* xp = A + (size_t)(2 * par) * lda;       // p_r at [r]
+    z* xc = A + (size_t)(2 * par + 1) * lda;   // A[r][j+1] at [r], r >= j+2
+    // reflector of step j from sx[0..m)
+    const ff2 alpha = as2(sx[0]);
+    ff2 ss = pk_zero();
+    for (int i = 1 + tid; i < m; i += nt) {
+      const ff2 x = as2(sx[i]);
+      ss = x * x + ss;
+    }
+    const ff2 s2 = pk_block_sum(ss, rb, 0);
+    const ff sigma = ffs_add(pk_get_re(s2), pk_get_im(s2));
+    const ff ar = pk_get_re(alpha), ai = pk_get_im(alpha);
+    ff2 t;
+    ff beta;
+    if (sigma.hi == 0.f && ai.hi == 0.f) {
+      t = pk_zero();
+      beta = ar;
+      for (int i = tid; i < m; i += nt) sv[i] = of2(i == 0 ? one : pk_zero());
+    } else {
+      const ff nu = ffs_sqrt(ffs_add(ffs_add(ffs_mul(ar, ar), ffs_mul(ai, ai)), sigma));
+      beta = ar.hi >= 0.f ? ffs_neg(nu) : nu;
+      const ff amr = ffs_sub(ar, beta);
+      const ff rden = ffs_div(ff(1.f, 0.f), ffs_add(ffs_mul(amr, amr), ffs_mul(ai, ai)));
+      const ff2 sc = pk_make(ffs_mul(amr, rden), ffs_neg(ffs_mul(ai, rden)));
+      t = pk_make(ffs_div(ffs_sub(beta, ar), beta), ffs_neg(ffs_div(ai, beta)));
+      for (int i = tid; i < m; i += nt) sv[i] = of2(i == 0 ? one : ff2_settle(pk_mul(as2(sx[i]), sc)));
+    }
+    __syncthreads();
+    if (c == 0) {
+      z* rrow = refl + (size_t)j * n + (j + 1);
+      for (int i = tid; i < m; i += nt) rrow[i] = pk_to_z(as2(sv[i]));
+      if (tid == 0) { tau[j] = pk_to_z(t); e[j] = ffs_to_d(beta); }
+    }
+    // p = tau A v on the owned rows of the trailing block (r >= j+1)
+    const int q0 = c >= j + 1 ? 0 : (j + 1 - c + G - 1) / G;
+    const int nq = nr - q0;
+    if (nq > 0) {
+      ff2 acc[kTridRows];
+#pragma unroll
+      for (int q = 0; q < kTridRows; ++q) acc[q] = pk_zero();
+      for (int k = warp * 32 + lane; k < m; k += nwarp * 32) {
+        const ff2 vk = as2(sv[k]), ivk = pk_i(vk);
+        const cx<ff>* base = rows + (size_t)q0 * n + (j + 1) + k;
+#pragma unroll
+        for (int q = 0; q < kTridRows; ++q)
+          if (q < nq) {
+            const ff2 a = as2(base[(size_t)q * n]);
+            acc[q] = fma(pk_im(a), ivk, fma(pk_re(a), vk, acc[q]));
+          }
+      }
+#pragma unroll
+      for (int q = 0; q < kTridRows; ++q) {
+        if (q < nq) {
+          ff2 a = ff2_settle(acc[q]);
+          for (int o = 16; o > 0; o >>= 1) a = a + pk_shfl_xor(a, o);
+          if (lane == 0) spart[warp][q] = of2(ff2_settle(a));
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < nq) {
+      ff2 a = as2(spart[0][tid]);
+      for (int w = 1; w < nwarp; ++w) a = a + as2(spart[w][tid]);
+      const int q = q0 + tid, r = c + q * G;
+      pk_store(&xp[r], ff2_settle(pk_mul(t, ff2_settle(a))));
+      if (r >= j + 2) pk_store(&xc[r], as2(rows[(size_t)q * n + (j + 1)]));
+    }
+    if (!grid_sync_mono(bar, (unsigned)j + 2)) return;
+    // w = p - (1/2) conj(tau) (v^+ p) v; the next column (rows j+2 ..)
+    ff2 sp = pk_zero();
+    for (int i = tid; i < m; i += nt) {
+      const ff2 v = as2(sv[i]), pr = pk_load(&xp[j + 1 + i]);
+      sw[i] = of2(pr);
+      sp = pk_fma(pk_conj(v), pr, sp);
+    }
+    for (int i = tid; i < m - 1; i += nt) sx[i] = of2(pk_load(&xc[j + 2 + i]));
+    const ff2 vp = pk_block_sum(ff2_settle(sp), rb, 1);
+    const ff2 half = {f2_of(0.5f, 0.5f), f2_of(0.5f, 0.5f)};
+    const ff2 cf = ff2_settle(pk_mul(pk_conj(t), vp));
+    const ff2 ncoef = pk_neg(ff2{mul2(cf.hi, half.hi), mul2(cf.lo, half.lo)});
+    for (int i = tid; i < m; i += nt) sw[i] = of2(ff2_settle(pk_fma(ncoef, as2(sv[i]), as2(sw[i]))));
+    __syncthreads();
+    // A -= v w^+ + w v^+ on the owned rows, and on the next column
+    for (int q = q0; q < nr; ++q) {
+      const int kr = c + q * G - (j + 1);
+      const ff2 nvr = pk_neg(as2(sv[kr])), nwr = pk_neg(as2(sw[kr]));
+      const ff2 nvr_re = pk_re(nvr), nvr_im = pk_im(nvr), nwr_re = pk_re(nwr), nwr_im = pk_im(nwr);
+      cx<ff>* arow = rows + (size_t)q * n + (j + 1);
+      for (int k = tid; k < m; k += nt) {
+        const ff2 cw = pk_conj(as2(sw[k])), cv = pk_conj(as2(sv[k]));
+        ff2 a = as2(arow[k]);
+        a = fma(nvr_re, cw, a);
+        a = fma(nvr_im, pk_i(cw), a);
+        a = fma(nwr_re, cv, a);
+        a = fma(nwr_im, pk_i(cv), a);
+        a = ff2_settle(a);
+        arow[k] = of2(a);
+        if (kr == 0 && k == 0) dg[j + 1] = ffs_to_d(pk_get_re(a));
+      }
+    }
+    {
+      // v_0 = 1: x_i - v_{i+1} conj(w_0) - w_{i+1}
+      const ff2 cw0 = pk_conj(as2(sw[0]));
+      for (int i = tid; i < m - 1; i += nt) {
+        const ff2 x = as2(sx[i]) - as2(sw[i + 1]);
+        sx[i] = of2(ff2_settle(pk_fma(pk_neg(as2(sv[i + 1])), cw0, x)));
+      }
+    }
+    __syncthreads();   // the next reflector reads all of sx
+  }
+}
+#endif
 
 // One warp per eigenvalue, two per CTA; d and e^2 staged in shared memory.
 // FP64: the bracket is first narrowed in FP32 (d, e^2 rounded to float, ~60x the
@@ -1152,6 +1384,13 @@ static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, c
 
 // Grid of k_tridiag_rows for an n x n matrix (0: use k_tridiag_coop): one CTA per
 // SM (at most n), provided every CTA's rows and vectors fit in shared memory.
+// The FP64 instantiation runs the float-float kernel (k_tridiag_rows_ff, the same
+// layout and launch shape).
+#if defined(QE_DENSE_FP64)
+#define QE_TRIDIAG_ROWS k_tridiag_rows_ff
+#else
+#define QE_TRIDIAG_ROWS k_tridiag_rows
+#endif
 static int tridiag_rows_grid(int n, size_t* smem) {
   if (n < 16) return 0;
   int dev = 0, nsm = 0, optin = 0;
@@ -1160,15 +1399,15 @@ static int tridiag_rows_grid(int n, size_t* smem) {
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return 0;
   cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, (const void*)k_tridiag_rows) != cudaSuccess) return 0;
+  if (cudaFuncGetAttributes(&fa, (const void*)QE_TRIDIAG_ROWS) != cudaSuccess) return 0;
   const int g = std::min(nsm, n);
   const int nrmax = (n + g - 1) / g;
   if (nrmax > kTridRows) return 0;
   const size_t sm = (size_t)(nrmax + 3) * n * sizeof(z);
   if (sm + fa.sharedSizeBytes > (size_t)optin) return 0;
-  set_max_dynamic_smem(k_tridiag_rows);
+  set_max_dynamic_smem(QE_TRIDIAG_ROWS);
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_rows, 256, sm) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, QE_TRIDIAG_ROWS, 256, sm) != cudaSuccess ||
       occ < 1)
     return 0;
   *smem = sm;
@@ -1192,7 +1431,7 @@ int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R
   if (g > 0) {
     void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.d, &wk.refl, &bar};
     ProfScope ps(pf, "heev_tridiag", st);
-    int rc0 = launch_coop((const void*)k_tridiag_rows, g, args, st, "k_tridiag_rows", rsm);
+    int rc0 = launch_coop((const void*)QE_TRIDIAG_ROWS, g, args, st, "k_tridiag_rows", rsm);
     if (rc0) return rc0;
   } else {
     void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.p, &wk.d, &wk.vbuf, &wk.refl, &bar};
