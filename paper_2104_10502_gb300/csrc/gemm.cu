@@ -9,9 +9,13 @@
 //   gemm_outer  C[n][m] (+)= sum_k A[k][m] B[k][n]    (beta (D P), rotations V X);
 //   dmul        Q = D P with a real D.
 // These are SIMT kernels: FP64 has no tcgen05 kind on sm_103a (and DMMA runs
-// no faster than DFMA on GB300), so the FP64 path is ALU-bound and uses the
-// three-multiplication complex product to cut its FMAs by a quarter.
+// no faster than DFMA on GB300), so they use the three-multiplication complex
+// product to cut the multiply-adds by a quarter, and the FP64 instantiation
+// computes in float-float arithmetic on the FP32 pipes (ff.cuh: 48-bit
+// significands, ~1e-14 relative, the FP64 rate being 1/64 of the FP32 one on
+// GB300); operands arrive and results leave in double.
 #include <algorithm>
+#include <type_traits>
 
 #include "fft_device.cuh"
 #include "plan.h"
@@ -27,6 +31,13 @@ static int check_launch(const char* what) {
   return QE_OK;
 }
 
+// Arithmetic of the kernels behind an instantiation (float-float for double) and
+// the type of their split-K partials (double for float-float).
+template <typename T>
+using CompT = std::conditional_t<std::is_same<T, double>::value, ff, T>;
+template <typename C>
+using PartT = std::conditional_t<std::is_same<C, ff>::value, double, C>;
+
 constexpr int IBM = 32, IBN = 32, IBK = 16;
 
 // grid: (ceil(N/32), ceil(M/32), nsplit); block 256 = 16 x 16, 2 x 2 outputs each.
@@ -36,7 +47,8 @@ constexpr int IBM = 32, IBN = 32, IBK = 16;
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gemm_inner(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
-             int M, int N, int K, int kchunk, cx<T>* __restrict__ part) {
+             int M, int N, int K, int kchunk, cx<PartT<T>>* __restrict__ part) {
+  using P = PartT<T>;
   __shared__ T Ar[IBK][IBM + 1], Ai[IBK][IBM + 1], As[IBK][IBM + 1];
   __shared__ T Br[IBK][IBN + 1], Bi[IBK][IBN + 1], Bs[IBK][IBN + 1];
   const int tid = threadIdx.x;
@@ -83,13 +95,14 @@ k_gemm_inner(const double2* __restrict__ A, int lda, const double2* __restrict__
     }
     __syncthreads();
   }
-  cx<T>* out = part + (size_t)blockIdx.z * M * N;
+  cx<P>* out = part + (size_t)blockIdx.z * M * N;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int m = m0 + ty * 2 + i, n = n0 + tx * 2 + j;
-      if (m < M && n < N) out[(size_t)m * N + n] = {t1[i][j] + t2[i][j], t3[i][j] - t1[i][j] + t2[i][j]};
+      if (m < M && n < N)
+        out[(size_t)m * N + n] = {P(t1[i][j] + t2[i][j]), P(t3[i][j] - t1[i][j] + t2[i][j])};
     }
 }
 
@@ -100,7 +113,8 @@ k_gemm_inner(const double2* __restrict__ A, int lda, const double2* __restrict__
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_gemm_inner_n8(const double2* __restrict__ A, int lda, const double2* __restrict__ B, int ldb,
-                int M, int N, int K, int kchunk, cx<T>* __restrict__ part) {
+                int M, int N, int K, int kchunk, cx<PartT<T>>* __restrict__ part) {
+  using P = PartT<T>;
   __shared__ T Ar[IBK][IBM + 1], Ai[IBK][IBM + 1], As[IBK][IBM + 1];
   __shared__ T Br[IBK][9], Bi[IBK][9], Bs[IBK][9];
   const int tid = threadIdx.x;
@@ -141,7 +155,7 @@ k_gemm_inner_n8(const double2* __restrict__ A, int lda, const double2* __restric
   }
   const int m = m0 + tm, n = tn;
   if (m < M && n < N)
-    part[(size_t)blockIdx.z * M * N + (size_t)m * N + n] = {t1 + t2, t3 - t1 + t2};
+    part[(size_t)blockIdx.z * M * N + (size_t)m * N + n] = {P(t1 + t2), P(t3 - t1 + t2)};
 }
 
 // C = sum over splits of the partials, in split order.  Eight threads per
@@ -198,16 +212,17 @@ static int inner_split(int M, int N, int K) {
 template <typename T>
 static void launch_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
                          int kchunk, int nsplit, void* part, cudaStream_t st) {
+  using C = CompT<T>;
   if (N <= 8) {
     dim3 g(1, (M + IBM - 1) / IBM, nsplit);
-    k_gemm_inner_n8<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+    k_gemm_inner_n8<C><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
                                            reinterpret_cast<const double2*>(B), ldb, M, N, K, kchunk,
-                                           reinterpret_cast<cx<T>*>(part));
+                                           reinterpret_cast<cx<PartT<C>>*>(part));
   } else {
     dim3 g((N + IBN - 1) / IBN, (M + IBM - 1) / IBM, nsplit);
-    k_gemm_inner<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+    k_gemm_inner<C><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
                                         reinterpret_cast<const double2*>(B), ldb, M, N, K, kchunk,
-                                        reinterpret_cast<cx<T>*>(part));
+                                        reinterpret_cast<cx<PartT<C>>*>(part));
   }
 }
 
@@ -221,7 +236,7 @@ int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N,
                int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf, bool real_out) {
   if (M <= 0 || N <= 0) return QE_OK;
   const int ns = inner_split(M, N, K);
-  if ((size_t)ns * M * N * sizeof(cx<T>) > part_bytes) {
+  if ((size_t)ns * M * N * sizeof(cx<PartT<CompT<T>>>) > part_bytes) {
     set_error("gemm_inner: scratch too small");
     return QE_EINVAL;
   }
@@ -238,7 +253,8 @@ int gemm_inner(const double* A, int lda, const double* B, int ldb, int M, int N,
   ProfScope ps(pf, "k_reduce_split", st);
   const size_t total = (size_t)M * N;
   const int blocks = reduce_blocks(total);
-  k_reduce_split<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<T>*>(part), nsplit, M, N,
+  using P = PartT<CompT<T>>;
+  k_reduce_split<P><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<P>*>(part), nsplit, M, N,
                                             reinterpret_cast<double2*>(C), ldc,
                                             real_out ? 1 : 0);
   return check_launch("k_reduce_split");
@@ -250,7 +266,7 @@ template <typename T>
 int gemm_inner_bounded(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
                        double* C, int ldc, void* part, size_t part_bytes, cudaStream_t st, Prof* pf) {
   if (M <= 0 || N <= 0) return QE_OK;
-  const size_t one = (size_t)M * N * sizeof(cx<T>);
+  const size_t one = (size_t)M * N * sizeof(cx<PartT<CompT<T>>>);
   if (one > part_bytes) {
     set_error("gemm_inner_bounded: scratch holds no split");
     return QE_EINVAL;
@@ -269,7 +285,8 @@ int gemm_inner_bounded(const double* A, int lda, const double* B, int ldb, int M
   ProfScope ps(pf, "k_reduce_split", st);
   const size_t total = (size_t)M * N;
   const int blocks = reduce_blocks(total);
-  k_reduce_split<T><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<T>*>(part), nsplit, M, N,
+  using P = PartT<CompT<T>>;
+  k_reduce_split<P><<<blocks, 256, 0, st>>>(reinterpret_cast<const cx<P>*>(part), nsplit, M, N,
                                             reinterpret_cast<double2*>(C), ldc, 0);
   return check_launch("k_reduce_split");
 }
@@ -416,14 +433,14 @@ int gemm_outer_ab(const double* A, int lda, const double* B, int ldb, int M, int
   }
   ProfScope ps(pf, "k_gemm_outer", st);
   if (N <= 8) {
-    k_gemm_outer_n8<T><<<(M + 31) / 32, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+    k_gemm_outer_n8<CompT<T>><<<(M + 31) / 32, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
                                                        reinterpret_cast<const double2*>(B), ldb, M, N,
                                                        K, reinterpret_cast<double2*>(C), ldc,
                                                        alpha_neg, beta);
     return check_launch("k_gemm_outer");
   }
   dim3 g((M + OBM - 1) / OBM, (N + OBN - 1) / OBN);
-  k_gemm_outer<T><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
+  k_gemm_outer<CompT<T>><<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(A), lda,
                                       reinterpret_cast<const double2*>(B), ldb, M, N, K,
                                       reinterpret_cast<double2*>(C), ldc, alpha_neg, beta);
   return check_launch("k_gemm_outer");
