@@ -792,7 +792,9 @@ __device__ void multisect_ff(const ff* d, const ff* e2, int n, int k, float tiny
 // FP64 pipe's work (12 FMAs per element and step) moved to the FP32 pipes.  The
 // reduction's backward error is a few units of 2^-46 ||A|| instead of 2^-53,
 // ~1e-14 ||A||, far below the 1e-10 eigenvalue tolerance of the FP64 solves;
-// d, e, tau and the reflectors leave in double.
+// d, e and tau leave in double, the reflector rows packed float-float (for
+// k_wy_t_ff and k_backtransform_ff, the back-transformation in the same
+// arithmetic).
 // exchange vectors written by other CTAs: read through L2 (as ldz)
 __device__ __forceinline__ ff2 pk_load(const z* p) {
   const ulonglong2 u = __ldcg(reinterpret_cast<const ulonglong2*>(p));
@@ -930,7 +932,8 @@ __global__ void __launch_bounds__(256) k_tridiag_rows_ff(z* A, int n, int lda, z
     __syncthreads();
     if (c == 0) {
       z* rrow = refl + (size_t)j * n + (j + 1);
-      for (int i = tid; i < m; i += nt) rrow[i] = pk_to_z(as2(sv[i]));
+      // reflector rows stay packed float-float (k_wy_t_ff, k_backtransform_ff read them)
+      for (int i = tid; i < m; i += nt) *reinterpret_cast<cx<ff>*>(&rrow[i]) = sv[i];
       if (tid == 0) { tau[j] = pk_to_z(t); e[j] = ffs_to_d(beta); }
     }
     // p = tau A v on the owned rows of the trailing block (r >= j+1)
@@ -1348,10 +1351,125 @@ __global__ void __launch_bounds__(256) k_backtransform(const z* __restrict__ ref
   for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)i * ldx + k] = x[i];
 }
 
+#if defined(QE_DENSE_FP64)
+// k_wy_t and k_backtransform on the packed float-float reflector rows that
+// k_tridiag_rows_ff leaves (the FP64 path): the dot products and the updates of
+// the eigenvectors in float-float on the FP32 pipes, T and the results in double.
+__device__ __forceinline__ ff2 pk_of_z(z a) { return as2(cx_from<ff>(a.x, a.y)); }
+
+__global__ void __launch_bounds__(256) k_wy_t_ff(const z* __restrict__ refl, int n,
+                                                 const z* __restrict__ tau, z* __restrict__ T) {
+  __shared__ z P[kWY][kWY];
+  const int g = blockIdx.x, j0 = g * kWY, nr = min(kWY, n - 1 - j0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const cx<ff>* rf = reinterpret_cast<const cx<ff>*>(refl);
+  for (int pq = warp; pq < kWY * kWY; pq += nw) {
+    const int a = pq / kWY, bb = pq % kWY;
+    if (!(a < bb && bb < nr)) continue;
+    const z ta = tau[j0 + a], tb = tau[j0 + bb];
+    if ((ta.x == R(0) && ta.y == R(0)) || (tb.x == R(0) && tb.y == R(0))) {
+      if (lane == 0) P[a][bb] = {R(0), R(0)};
+      continue;
+    }
+    const cx<ff>* va = rf + (size_t)(j0 + a) * n;
+    const cx<ff>* vb = rf + (size_t)(j0 + bb) * n;
+    ff2 acc = pk_zero();
+    for (int i = j0 + bb + 1 + lane; i < n; i += 32) acc = pk_fma(pk_conj(as2(va[i])), as2(vb[i]), acc);
+    acc = ff2_settle(acc);
+    for (int o = 16; o > 0; o >>= 1) acc = acc + pk_shfl_xor(acc, o);
+    if (lane == 0) P[a][bb] = pk_to_z(ff2_settle(acc));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    z t[kWY][kWY];
+    for (int r = 0; r < kWY; ++r)
+      for (int c = 0; c < kWY; ++c) t[r][c] = {R(0), R(0)};
+    for (int i = 0; i < nr; ++i) {
+      const z ti = tau[j0 + i];
+      for (int r = 0; r < i; ++r) {
+        z acc = {R(0), R(0)};
+        for (int c = r; c < i; ++c) acc = cadd(acc, cmul(t[r][c], P[c][i]));
+        t[r][i] = {-(ti.x * acc.x - ti.y * acc.y), -(ti.x * acc.y + ti.y * acc.x)};
+      }
+      t[i][i] = ti;
+    }
+    z* out = T + (size_t)g * kWY * kWY;
+    for (int r = 0; r < kWY; ++r)
+      for (int c = 0; c < kWY; ++c) out[r * kWY + c] = t[r][c];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_backtransform_ff(const z* __restrict__ refl, int n,
+                                                          const z* __restrict__ T, const R* Y,
+                                                          z* X, int ldx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<ff>* x = reinterpret_cast<cx<ff>*>(smem_raw);
+  __shared__ cx<ff> part[8][kWY];
+  __shared__ cx<ff> u[kWY];
+  __shared__ cx<ff> w[kWY];
+  const cx<ff>* rf = reinterpret_cast<const cx<ff>*>(refl);
+  const int k = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = cx_from<ff>(Y[(size_t)k * n + i], 0.0);
+  __syncthreads();
+  const int ngroups = (n - 1 + kWY - 1) / kWY;
+  for (int g = ngroups - 1; g >= 0; --g) {
+    const int j0 = g * kWY;
+    const z* tg0 = T + (size_t)g * kWY * kWY;
+    unsigned act = 0;
+    const int nr = min(kWY, n - 1 - j0);
+#pragma unroll
+    for (int a = 0; a < kWY; ++a) {
+      const z d = tg0[a * kWY + a];
+      if (a < nr && (d.x != R(0) || d.y != R(0))) act |= 1u << a;
+    }
+    ff2 acc[kWY];
+#pragma unroll
+    for (int a = 0; a < kWY; ++a) acc[a] = pk_zero();
+    for (int i = j0 + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const ff2 xi = as2(x[i]);
+#pragma unroll
+      for (int a = 0; a < kWY; ++a)
+        if (((act >> a) & 1u) && i >= j0 + a + 1)
+          acc[a] = pk_fma(pk_conj(as2(rf[(size_t)(j0 + a) * n + i])), xi, acc[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < kWY; ++a) {
+      ff2 s = ff2_settle(acc[a]);
+      for (int o = 16; o > 0; o >>= 1) s = s + pk_shfl_xor(s, o);
+      if (lane == 0) part[warp][a] = of2(ff2_settle(s));
+    }
+    __syncthreads();
+    if (threadIdx.x < kWY) {
+      // w_c = sum over warps, then u_a = sum_{c >= a} T[a][c] w_c (c < nr)
+      ff2 s = as2(part[0][threadIdx.x]);
+      for (int q = 1; q < nw; ++q) s = s + as2(part[q][threadIdx.x]);
+      w[threadIdx.x] = of2(ff2_settle(s));
+      __syncwarp(0xffu);
+      const z* tg = T + (size_t)g * kWY * kWY + threadIdx.x * kWY;
+      ff2 ua = pk_zero();
+      for (int c = threadIdx.x; c < nr; ++c) ua = pk_fma(pk_of_z(tg[c]), as2(w[c]), ua);
+      u[threadIdx.x] = of2(ff2_settle(ua));
+    }
+    __syncthreads();
+    for (int i = j0 + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      ff2 xi = as2(x[i]);
+#pragma unroll
+      for (int a = 0; a < kWY; ++a)
+        if (((act >> a) & 1u) && i >= j0 + a + 1)
+          xi = pk_fma(pk_neg(as2(rf[(size_t)(j0 + a) * n + i])), as2(u[a]), xi);
+      x[i] = of2(ff2_settle(xi));
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)i * ldx + k] = pk_to_z(as2(x[i]));
+}
+#endif
+
 // Eigenvalues and eigenvectors of the tridiagonal T (wk.d, wk.e) and the
 // back-transformation through the reflectors (wk.tau, wk.refl) into X.
 static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, cudaStream_t st,
-                       Prof* pf) {
+                       Prof* pf, bool ff_refl = false) {
   int rc = QE_OK;
   {
     ProfScope ps(pf, "heev_bisect", st);
@@ -1376,8 +1494,17 @@ static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, c
   const size_t bsm = (size_t)n * sizeof(z);
   {
     ProfScope ps(pf, "heev_backtransform", st);
-    if (n > 1) k_wy_t<<<(n - 1 + kWY - 1) / kWY, 256, 0, st>>>(wk.refl, n, wk.tau, wk.wyt);
-    k_backtransform<<<nev, 256, bsm, st>>>(wk.refl, n, wk.wyt, wk.y, X, ldx);
+#if defined(QE_DENSE_FP64)
+    if (ff_refl) {
+      set_max_dynamic_smem(k_backtransform_ff);
+      if (n > 1) k_wy_t_ff<<<(n - 1 + kWY - 1) / kWY, 256, 0, st>>>(wk.refl, n, wk.tau, wk.wyt);
+      k_backtransform_ff<<<nev, 256, bsm, st>>>(wk.refl, n, wk.wyt, wk.y, X, ldx);
+    } else
+#endif
+    {
+      if (n > 1) k_wy_t<<<(n - 1 + kWY - 1) / kWY, 256, 0, st>>>(wk.refl, n, wk.tau, wk.wyt);
+      k_backtransform<<<nev, 256, bsm, st>>>(wk.refl, n, wk.wyt, wk.y, X, ldx);
+    }
   }
   return check_launch("k_backtransform");
 }
@@ -1443,7 +1570,11 @@ int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R
     int rc0 = launch_coop((const void*)k_tridiag_coop, blocks, args, st, "k_tridiag_coop", tsm);
     if (rc0) return rc0;
   }
+#if defined(QE_DENSE_FP64)
+  return heev_finish(n, nev, w, X, ldx, wk, st, pf, g > 0);   // rows kernel: packed reflectors
+#else
   return heev_finish(n, nev, w, X, ldx, wk, st, pf);
+#endif
 }
 
 // ---- small generalised problems in one CTA ---------------------------------------------
