@@ -1590,6 +1590,7 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
+#if !defined(QE_DENSE_FP64)   // FP64: k_rr_small_ff below
 __global__ void __launch_bounds__(512) k_rr_small(const z* __restrict__ H, const z* __restrict__ S,
                                                   int ld, int n, z* Lg, R* dgl, R* egl,
                                                   z* taug, z* refl, int* status) {
@@ -1777,6 +1778,205 @@ __global__ void __launch_bounds__(512) k_rr_small(const z* __restrict__ H, const
   }
   for (int i = tid; i < n; i += nt) dgl[i] = A[(size_t)i * n + i].x;
 }
+#endif
+
+#if defined(QE_DENSE_FP64)
+// k_rr_small in float-float arithmetic (the FP64 path): the same steps, order
+// and layout on packed float-float complex values, whose dependent chains
+// (the substitutions, the reductions, the pivots' square roots and divisions)
+// are far shorter on the FP32 pipes than on GB300's FP64 pipe.  Lg, d, e and tau
+// leave in double, the reflector rows packed float-float (k_backtransform_ff).
+__device__ __forceinline__ ff2 pk_warp_sum(ff2 a) {
+  for (int o = 16; o > 0; o >>= 1) a = a + pk_shfl_xor(a, o);
+  return ff2_settle(a);
+}
+__global__ void __launch_bounds__(512) k_rr_small_ff(const z* __restrict__ H,
+                                                     const z* __restrict__ S, int ld, int n,
+                                                     z* Lg, R* dgl, R* egl, z* taug, z* refl,
+                                                     int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<ff>* A = reinterpret_cast<cx<ff>*>(smem_raw);   // n x n: H, then the reduced matrix
+  cx<ff>* L = A + (size_t)n * n;                     // n x n: S, then its Cholesky factor
+  cx<ff>* sv = L + (size_t)n * n;                    // n
+  cx<ff>* sw = sv + n;                               // n
+  ff* piv = reinterpret_cast<ff*>(sw + n);           // n
+  ff* rpiv = piv + n;                                // n
+  __shared__ cx<ff> sred[2];                          // tau, coefficient of w
+  __shared__ ff s_inv;
+  __shared__ int s_fail;
+  cx<ff>* rf = reinterpret_cast<cx<ff>*>(refl);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  if (tid == 0) s_fail = 0;
+  // 1. Cholesky of S in place (right-looking, lower triangle)
+  for (int t = tid; t < n * n; t += nt) {
+    const z sv0 = S[(size_t)(t / n) * ld + t % n], hv0 = H[(size_t)(t / n) * ld + t % n];
+    L[t] = cx_from<ff>(sv0.x, sv0.y);
+    A[t] = cx_from<ff>(hv0.x, hv0.y);
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const ff dj = pk_get_re(as2(L[(size_t)j * n + j]));
+    if (!(dj.hi > 0.f)) {
+      if (tid == 0) { s_fail = 1; *status = 1 + j; }
+      break;
+    }
+    if (tid == 0) { piv[j] = ffs_sqrt(dj); s_inv = ffs_div(ff(1.f, 0.f), dj); }
+    __syncthreads();
+    const ff2 inv = ff2_bcast(s_inv);
+    const int m = n - j - 1;
+    for (int t = tid; t < m * m; t += nt) {
+      const int r = j + 1 + t / m, c = j + 1 + t % m;
+      if (c > r) continue;
+      const ff2 p = pk_mul(as2(L[(size_t)r * n + j]), pk_conj(as2(L[(size_t)c * n + j])));
+      cx<ff>& a = L[(size_t)r * n + c];
+      a = of2(ff2_settle(as2(a) - p * inv));
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (s_fail) {
+    for (int i = tid; i < n; i += nt) { dgl[i] = R(0); egl[i] = R(0); taug[i] = {R(0), R(0)}; }
+    return;
+  }
+  for (int i = tid; i < n; i += nt) rpiv[i] = ffs_div(ff(1.f, 0.f), piv[i]);
+  __syncthreads();
+  for (int t = tid; t < n * n; t += nt) {
+    const int r = t / n, c = t % n;
+    ff2 l;
+    if (c > r) l = pk_zero();
+    else if (c == r) l = pk_make(piv[c], ff(0.f, 0.f));
+    else l = ff2_settle(as2(L[t]) * ff2_bcast(rpiv[c]));
+    L[t] = of2(l);
+    Lg[t] = pk_to_z(l);
+  }
+  __syncthreads();
+  // 2. A = L^-1 H L^-+: two forward substitutions, columns in parallel
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i < n; ++i) {
+      const cx<ff>* li = L + (size_t)i * n;
+      const ff2 inv = ff2_bcast(rpiv[i]);
+      for (int c = tid; c < n; c += nt) {
+        ff2 acc = as2(A[(size_t)i * n + c]);
+        for (int k = 0; k < i; ++k) acc = pk_fma(pk_neg(as2(li[k])), as2(A[(size_t)k * n + c]), acc);
+        A[(size_t)i * n + c] = of2(ff2_settle(ff2_settle(acc) * inv));
+      }
+      __syncthreads();
+    }
+    if (pass == 0) {
+      for (int t = tid; t < n * n; t += nt) {
+        const int r = t / n, c = t % n;
+        if (c < r) continue;
+        const ff2 a = as2(A[t]), b = as2(A[(size_t)c * n + r]);
+        A[t] = of2(pk_conj(b));
+        A[(size_t)c * n + r] = of2(pk_conj(a));
+      }
+      __syncthreads();
+    }
+  }
+  // Hermitian part
+  {
+    const ff2 half = {f2_of(0.5f, 0.5f), f2_of(0.5f, 0.5f)};
+    for (int t = tid; t < n * n; t += nt) {
+      const int r = t / n, c = t % n;
+      if (c < r) continue;
+      const ff2 hs = as2(A[t]) + pk_conj(as2(A[(size_t)c * n + r]));
+      const ff2 h = ff2_settle({mul2(hs.hi, half.hi), mul2(hs.lo, half.lo)});
+      A[t] = of2(h);
+      A[(size_t)c * n + r] = of2(pk_conj(h));
+    }
+  }
+  __syncthreads();
+  // 3. Householder tridiagonalisation in place
+  const ff2 one = {f2_of(1.f, 0.f), f2_of(0.f, 0.f)};
+  for (int j = 0; j < n - 1; ++j) {
+    const int m = n - j - 1;
+    if (warp == 0) {
+      const ff2 alpha = as2(A[(size_t)(j + 1) * n + j]);
+      ff2 ss = pk_zero();
+      for (int i = 1 + lane; i < m; i += 32) {
+        const ff2 x = as2(A[(size_t)(j + 1 + i) * n + j]);
+        ss = x * x + ss;
+      }
+      ss = pk_warp_sum(ff2_settle(ss));
+      const ff sg = ffs_add(pk_get_re(ss), pk_get_im(ss));
+      const ff ar = pk_get_re(alpha), ai = pk_get_im(alpha);
+      if (sg.hi == 0.f && ai.hi == 0.f) {
+        if (lane == 0) { taug[j] = {R(0), R(0)}; egl[j] = ffs_to_d(ar); sred[0] = of2(pk_zero()); }
+      } else {
+        const ff nu = ffs_sqrt(ffs_add(ffs_add(ffs_mul(ar, ar), ffs_mul(ai, ai)), sg));
+        const ff beta = ar.hi >= 0.f ? ffs_neg(nu) : nu;
+        const ff amr = ffs_sub(ar, beta);
+        const ff rden = ffs_div(ff(1.f, 0.f), ffs_add(ffs_mul(amr, amr), ffs_mul(ai, ai)));
+        const ff rbeta = ffs_div(ff(1.f, 0.f), beta);
+        const ff2 sc = pk_make(ffs_mul(amr, rden), ffs_neg(ffs_mul(ai, rden)));
+        cx<ff>* rrow = rf + (size_t)j * n + (j + 1);
+        for (int i = 1 + lane; i < m; i += 32) {
+          cx<ff>* x = &A[(size_t)(j + 1 + i) * n + j];
+          const cx<ff> v = of2(ff2_settle(pk_mul(as2(*x), sc)));
+          *x = v;
+          sv[i] = v;
+          rrow[i] = v;
+        }
+        if (lane == 0) {
+          const ff2 t = pk_make(ffs_mul(ffs_sub(beta, ar), rbeta), ffs_neg(ffs_mul(ai, rbeta)));
+          taug[j] = pk_to_z(t);
+          egl[j] = ffs_to_d(beta);
+          A[(size_t)(j + 1) * n + j] = of2(pk_make(beta, ff(0.f, 0.f)));
+          sv[0] = of2(one);
+          rrow[0] = of2(one);
+          sred[0] = of2(t);
+        }
+      }
+    }
+    __syncthreads();
+    const ff2 t = as2(sred[0]);
+    {
+      float th, tih, tl, til;
+      f2_split(t.hi, th, tih);
+      f2_split(t.lo, tl, til);
+      if (th == 0.f && tih == 0.f && tl == 0.f && til == 0.f) {   // uniform
+        __syncthreads();
+        continue;
+      }
+    }
+    // p = tau A_trail v (one warp per row)
+    for (int r = warp; r < m; r += nwarps) {
+      const cx<ff>* row = A + (size_t)(j + 1 + r) * n + (j + 1);
+      ff2 acc = pk_zero();
+      for (int c = lane; c < m; c += 32) acc = pk_fma(as2(row[c]), as2(sv[c]), acc);
+      acc = pk_warp_sum(ff2_settle(acc));
+      if (lane == 0) sw[r] = of2(ff2_settle(pk_mul(t, acc)));
+    }
+    __syncthreads();
+    // w = p - (1/2) conj(tau) (v^+ p) v
+    if (warp == 0) {
+      ff2 acc = pk_zero();
+      for (int i = lane; i < m; i += 32) acc = pk_fma(pk_conj(as2(sv[i])), as2(sw[i]), acc);
+      acc = pk_warp_sum(ff2_settle(acc));
+      if (lane == 0) {
+        const ff2 cf = ff2_settle(pk_mul(pk_conj(t), acc));
+        const ff2 half = {f2_of(0.5f, 0.5f), f2_of(0.5f, 0.5f)};
+        sred[1] = of2(ff2{mul2(cf.hi, half.hi), mul2(cf.lo, half.lo)});
+      }
+    }
+    __syncthreads();
+    const ff2 ncoef = pk_neg(as2(sred[1]));
+    for (int i = tid; i < m; i += nt) sw[i] = of2(ff2_settle(pk_fma(ncoef, as2(sv[i]), as2(sw[i]))));
+    __syncthreads();
+    // A_trail -= v w^+ + w v^+
+    for (int q = tid; q < m * m; q += nt) {
+      const int r = q / m, c = q % m;
+      cx<ff>& a = A[(size_t)(j + 1 + r) * n + (j + 1 + c)];
+      ff2 x = pk_fma(pk_neg(as2(sv[r])), pk_conj(as2(sw[c])), as2(a));
+      x = pk_fma(pk_neg(as2(sw[r])), pk_conj(as2(sv[c])), x);
+      a = of2(ff2_settle(x));
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) dgl[i] = ffs_to_d(pk_get_re(as2(A[(size_t)i * n + i])));
+}
+#endif
 
 int rr_small_fits(int n) { return n > 0 && n <= kSmallDense; }
 
@@ -1786,6 +1986,17 @@ int rr_small(const z* H, const z* S, int ld, int n, int nev, z* L, R* w, z* X, i
     set_error("rr_small: n = %d, nev = %d", n, nev);
     return QE_EINVAL;
   }
+#if defined(QE_DENSE_FP64)
+  const size_t smem = 2 * (size_t)n * n * sizeof(z) + 2 * (size_t)n * sizeof(z) + 2 * (size_t)n * sizeof(ff);
+  set_max_dynamic_smem(k_rr_small_ff);
+  {
+    ProfScope ps(pf, "rr_small", st);
+    k_rr_small_ff<<<1, 512, smem, st>>>(H, S, ld, n, L, wk.d, wk.e, wk.tau, wk.refl, wk.status);
+  }
+  const int rc = check_launch("k_rr_small");
+  if (rc) return rc;
+  return heev_finish(n, nev, w, X, ldx, wk, st, pf, true);
+#else
   const size_t smem = 2 * (size_t)n * n * sizeof(z) + 2 * (size_t)n * sizeof(z) + (size_t)n * sizeof(R);
   set_max_dynamic_smem(k_rr_small);
   {
@@ -1795,6 +2006,7 @@ int rr_small(const z* H, const z* S, int ld, int n, int nev, z* L, R* w, z* X, i
   const int rc = check_launch("k_rr_small");
   if (rc) return rc;
   return heev_finish(n, nev, w, X, ldx, wk, st, pf);
+#endif
 }
 
 
