@@ -565,6 +565,12 @@ def run_davidson_bench(q, ctx, dev):
                                          c["widths"], c["nbnd"], c["psi_seed"], dev)
         ev = torch.zeros(c["nbnd"], dtype=torch.float64, device=dev)
         times, iters = [], []
+        if reps == 1:
+            # one untimed solve first: first-use costs (module loading of kernels
+            # not launched yet, workspace growth) stay out of the single timed one
+            pt = pt0.clone()
+            ctx.davidson(prob, pt, ev, None, precision=prec, tol=tol, max_iter=200)
+            torch.cuda.synchronize(dev)
         for _ in range(reps):
             pt = pt0.clone()
             torch.cuda.synchronize(dev)
