@@ -1107,6 +1107,7 @@ constexpr int kInvIters = sizeof(R) == 8 ? 3 : 4;
 // One CTA per cluster of consecutive eigenvalues closer than ctol; the CTA whose
 // index starts a cluster handles all of it, the others return.  Vectors are rows
 // Y[k][0..n).  Shared memory: 6 arrays of n doubles (+ ints) for the factorisation.
+#if !defined(QE_DENSE_FP64)   // FP64: k_inviter_ff below
 __global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, int nev,
                                                  const R* w, R ctol_rel, R* Y) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1215,6 +1216,138 @@ __global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, 
     __syncthreads();
   }
 }
+#endif
+
+#if defined(QE_DENSE_FP64)
+// k_inviter in float-float arithmetic (the FP64 path): the LU of T - lambda I and
+// the solves are one thread's dependent chains, whose FP64 divisions and
+// multiply-adds cost ~64 cycles per instruction on GB300; in float-float on the
+// FP32 pipes the chain is several times shorter.  The eigenvalue shift, the
+// cluster test and the output stay double; eigenvectors to ~1e-14.
+__device__ __forceinline__ ff ffi_abs(ff a) { return a.hi < 0.f ? ffs_neg(a) : a; }
+__device__ ff ffi_block_sum(ff v, ff* sh) {
+  for (int o = 16; o > 0; o >>= 1)
+    v = ffs_add(v, ff(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)));
+  const int wv = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[wv] = v;
+  __syncthreads();
+  ff t = sh[0];
+  for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = ffs_add(t, sh[q]);
+  __syncthreads();
+  return t;
+}
+__global__ void __launch_bounds__(256) k_inviter_ff(const R* d, const R* e, int n, int nev,
+                                                    const R* w, R ctol_rel, R* Y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ff* u0 = reinterpret_cast<ff*>(smem_raw);
+  ff* u1 = u0 + n;
+  ff* u2 = u1 + n;
+  ff* ml = u2 + n;
+  ff* y = ml + n;
+  ff* xd = y + n;
+  ff* xe = xd + n;
+  int* sw = reinterpret_cast<int*>(xe + n);
+  __shared__ R sh[33];
+  __shared__ ff shf[33];
+  const int k0 = blockIdx.x;
+  if (k0 >= nev) return;
+  R nrm = R(0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    nrm = fmax(nrm, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : R(0)) + (i < n - 1 ? fabs(e[i]) : R(0)));
+  for (int o = 16; o > 0; o >>= 1) nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  nrm = R(0);
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) nrm = fmax(nrm, sh[q]);
+  __syncthreads();
+  const R ctol = ctol_rel * fmax(nrm, RealT<R>::tiny);
+  if (k0 > 0 && w[k0] - w[k0 - 1] <= ctol) return;   // not a cluster start
+  int k1 = k0 + 1;
+  while (k1 < nev && w[k1] - w[k1 - 1] <= ctol) ++k1;
+  const ff tiny((double)fmax(RealT<R>::eps * nrm, 1e-30));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    xd[i] = ff((double)d[i]);
+    xe[i] = i < n - 1 ? ff((double)e[i]) : ff(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int k = k0; k < k1; ++k) {
+    const ff lam((double)w[k]);
+    if (threadIdx.x == 0) {
+      ff c0 = ffs_sub(xd[0], lam), c1 = n > 1 ? xe[0] : ff(0.f, 0.f), c2(0.f, 0.f);
+      for (int i = 0; i < n - 1; ++i) {
+        ff n0 = xe[i], n1 = ffs_sub(xd[i + 1], lam), n2 = (i + 2 < n) ? xe[i + 1] : ff(0.f, 0.f);
+        int sp = 0;
+        if (fabsf(n0.hi) > fabsf(c0.hi)) {
+          ff t;
+          t = c0; c0 = n0; n0 = t;
+          t = c1; c1 = n1; n1 = t;
+          t = c2; c2 = n2; n2 = t;
+          sp = 1;
+        }
+        if (fabsf(c0.hi) < tiny.hi) c0 = c0.hi < 0.f ? ffs_neg(tiny) : tiny;
+        const ff rc = ffs_div(ff(1.f, 0.f), c0);
+        const ff mlt = ffs_mul(n0, rc);
+        u0[i] = rc; u1[i] = c1; u2[i] = c2; ml[i] = mlt; sw[i] = sp;
+        c0 = ffs_sub(n1, ffs_mul(mlt, c1));
+        c1 = ffs_sub(n2, ffs_mul(mlt, c2));
+        c2 = ff(0.f, 0.f);
+      }
+      if (fabsf(c0.hi) < tiny.hi) c0 = c0.hi < 0.f ? ffs_neg(tiny) : tiny;
+      u0[n - 1] = ffs_div(ff(1.f, 0.f), c0); u1[n - 1] = ff(0.f, 0.f); u2[n - 1] = ff(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = ff(start_component(k, i));
+    __syncthreads();
+    for (int it = 0; it < kInvIters; ++it) {
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < n - 1; ++i) {
+          if (sw[i]) { const ff t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
+          y[i + 1] = ffs_sub(y[i + 1], ffs_mul(ml[i], y[i]));
+        }
+        for (int i = n - 1; i >= 0; --i) {
+          ff sacc = y[i];
+          if (i + 1 < n) sacc = ffs_sub(sacc, ffs_mul(u1[i], y[i + 1]));
+          if (i + 2 < n) sacc = ffs_sub(sacc, ffs_mul(u2[i], y[i + 2]));
+          y[i] = ffs_mul(sacc, u0[i]);
+        }
+      }
+      __syncthreads();
+      // scale down first (the solve grows the vector by up to 1/tiny)
+      float mx = 0.f;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmaxf(mx, fabsf(y[i].hi));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((threadIdx.x & 31) == 0) shf[threadIdx.x >> 5] = ff(mx, 0.f);
+      __syncthreads();
+      float m2 = 0.f;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m2 = fmaxf(m2, shf[q].hi);
+      __syncthreads();
+      const ff inv_mx = ffs_div(ff(1.f, 0.f), ff(m2 > 0.f ? m2 : 1.f, 0.f));
+      for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = ffs_mul(y[i], inv_mx);
+      __syncthreads();
+      // orthogonalise against the finished vectors of this cluster (twice)
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int q = k0; q < k; ++q) {
+          const R* yq = Y + (size_t)q * n;
+          ff sacc(0.f, 0.f);
+          for (int i = threadIdx.x; i < n; i += blockDim.x) sacc = ffs_add(sacc, ffs_mul(ff((double)yq[i]), y[i]));
+          const ff sdot = ffi_block_sum(sacc, shf);
+          for (int i = threadIdx.x; i < n; i += blockDim.x)
+            y[i] = ffs_sub(y[i], ffs_mul(sdot, ff((double)yq[i])));
+          __syncthreads();
+        }
+      }
+      ff sacc(0.f, 0.f);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sacc = ffs_add(sacc, ffs_mul(y[i], y[i]));
+      const ff ss = ffi_block_sum(sacc, shf);
+      const ff inv = ss.hi > 0.f ? ffs_div(ff(1.f, 0.f), ffs_sqrt(ss)) : ff(0.f, 0.f);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = ffs_mul(y[i], inv);
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Y[(size_t)k * n + i] = ffs_to_d(y[i]);
+    __syncthreads();
+  }
+}
+#endif
 
 // X[:, k] = H_0 H_1 ... H_{n-2} y_k by blocks of kWY reflectors in compact WY
 // form: H_j0 ... H_j0+kWY-1 = I - V T V^+ (V = [v_j0 ...] from the rows of refl,
@@ -1480,15 +1613,24 @@ static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, c
   }
   rc = check_launch("k_bisect");
   if (rc) return rc;
-  const size_t ism = (size_t)n * (5 * sizeof(R) + sizeof(int));
   // same (largest) cap for every caller: the attribute is shared process-wide
-  set_max_dynamic_smem(k_inviter);
   set_max_dynamic_smem(k_backtransform);
   // eigenvalues within 1e-10 of each other (relative to the spread of T) share a cluster
+#if defined(QE_DENSE_FP64)
   {
+    const size_t ism = (size_t)n * (7 * sizeof(ff) + sizeof(int));
+    set_max_dynamic_smem(k_inviter_ff);
+    ProfScope ps(pf, "heev_inviter", st);
+    k_inviter_ff<<<nev, 256, ism, st>>>(wk.d, wk.e, n, nev, w, wk.ctol_rel, wk.y);
+  }
+#else
+  {
+    const size_t ism = (size_t)n * (5 * sizeof(R) + sizeof(int));
+    set_max_dynamic_smem(k_inviter);
     ProfScope ps(pf, "heev_inviter", st);
     k_inviter<<<nev, 256, ism, st>>>(wk.d, wk.e, n, nev, w, wk.ctol_rel, wk.y);
   }
+#endif
   rc = check_launch("k_inviter");
   if (rc) return rc;
   const size_t bsm = (size_t)n * sizeof(z);
