@@ -1020,8 +1020,8 @@ __global__ void __launch_bounds__(256) k_tridiag_rows_ff(z* A, int n, int lda, z
 // FP64: the bracket is first narrowed in FP32 (d, e^2 rounded to float, ~60x the
 // FP64 rate on GB300) to 64 float ulps of ||T||, widened by 16 ulps (the
 // rounding of T and the Sturm count's backward error are a few ulps of ||T||),
-// then in float-float to 2^-42 ||T|| (the counts' resolution, ~1e-13 ||T||),
-// and finished by at most a few FP64 rounds to the FP64 resolution.
+// then in float-float to 2^-45 ||T|| (the counts' resolution, ~1e-14 ||T||,
+// that of T itself after the float-float reduction; no FP64 rounds).
 // Dynamic shared memory: n (d) + n (e^2) R, and in FP64 2 n floats + 2 n ff.
 __global__ void __launch_bounds__(64) k_bisect(const R* d, const R* e, int n, int nev,
                                                 R* w) {
@@ -1075,13 +1075,13 @@ __global__ void __launch_bounds__(64) k_bisect(const R* d, const R* e, int n, in
     const R pad = R(16) * R(fe) * nrm + RealT<R>::tiny;
     lo = fmax(lo, R(flo) - pad);
     hi = fmin(hi, R(fhi) + pad);
-    // float-float rounds down to 2^-42 ||T||, widened by 2^-44 ||T|| (their
-    // counts' backward error is a few units of 2^-47 ||T||)
+    // float-float rounds down to 2^-45 ||T|| (their counts' backward error is a
+    // few units of 2^-47 ||T||): the eigenvalue to ~1e-14 ||T||, the accuracy
+    // that T itself carries when the FP64 path's float-float reduction formed it
     double xlo = lo, xhi = hi;
-    multisect_ff(xd, xe2, n, k, (float)fmax(1e-30 * nrm, 1e-30), xlo, xhi, 0x1p-42 * nrm);
-    const R xpad = 0x1p-44 * nrm + RealT<R>::tiny;
-    lo = fmax(lo, R(xlo) - xpad);
-    hi = fmin(hi, R(xhi) + xpad);
+    multisect_ff(xd, xe2, n, k, (float)fmax(1e-30 * nrm, 1e-30), xlo, xhi, 0x1p-45 * nrm);
+    if (lane == 0) w[k] = 0.5 * (xlo + xhi);
+    return;
   }
   multisect<R>(sd, se2, n, k, tiny, lo, hi, RealT<R>::eps, R(0));
   if (lane == 0) w[k] = R(0.5) * (lo + hi);
