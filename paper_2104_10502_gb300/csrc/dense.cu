@@ -15,6 +15,9 @@
 //                 of (nearly) equal eigenvalues, back-transformation.
 //   rr_small      the whole generalised reduction for n <= 64 in one CTA.
 // The multi-CTA kernels are cooperative launches with a bounded grid barrier.
+// In this instantiation (QE_DENSE_FP64) the tridiagonalisation, the last
+// bisection rounds, inverse iteration, back-transformation and rr_small run in
+// float-float arithmetic on the FP32 pipes (the *_ff kernels of dense_impl.cuh).
 #define QE_DENSE_R double
 #define QE_DENSE_NS qe
 #define QE_DENSE_FP64 1
