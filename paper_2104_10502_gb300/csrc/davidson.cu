@@ -414,7 +414,8 @@ static int* dv_tc_status(const DvState& S) { return S.dw.status + 12; }
 
 // C = A^+ B over the plane waves; real for vectors real in r (k = 0 mode), so
 // that the combinations built from C keep them real in r exactly (the SIMT
-// path drops Im C in its split reduction, the tensor-core paths after).
+// path drops Im C in its split reduction, the FP64 tensor-core path computes
+// only Re C, the FP32 one drops Im C after).
 template <typename T>
 static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
                 cudaStream_t st, Prof* pf) {
@@ -422,8 +423,8 @@ static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, in
     DV_TRY(tc_inner((const double*)A, (const double*)B, m, n, S.npw, (double*)C, ldc, S.tc,
                     S.tc_bytes, dv_tc_status(S), st, pf));
   } else if (sizeof(T) == sizeof(double) && S.oz && oz_worth(m, n, S.npw)) {
-    DV_TRY(oz_inner((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C, ldc,
-                    S.oz, S.oz_bytes, dv_tc_status(S), st, pf));
+    return oz_inner((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C, ldc,
+                    S.oz, S.oz_bytes, dv_tc_status(S), st, pf, S.gamma);
   } else {
     return gemm_inner<T>((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C,
                          ldc, S.part, S.part_bytes, st, pf, S.gamma);

@@ -381,9 +381,10 @@ constexpr int OZ_ROW_CHUNK = 2048;   // complex elements of a row per CTA
 
 // Row exponents of a complex [rows][K] matrix: grid (rows, ceil(K / 2048)); the
 // CTAs of a row merge their exponent bounds with atomicMax (monotonic in the
-// maximum) into e, which holds 0x80808080 beforehand (kept by all-zero rows).
+// maximum) into e[r >> shift] (shift 1: one exponent for the rows 2p and 2p+1),
+// which holds 0x80808080 beforehand (kept by all-zero rows).
 __global__ void __launch_bounds__(256) k_oz_rowmax(const double2* __restrict__ src, int ld, int K,
-                                                   int* __restrict__ e) {
+                                                   int shift, int* __restrict__ e) {
   __shared__ unsigned long long sh[33];
   const int r = blockIdx.x;
   const double2* row = src + (size_t)r * ld;
@@ -396,12 +397,13 @@ __global__ void __launch_bounds__(256) k_oz_rowmax(const double2* __restrict__ s
     mx = h > mx ? h : mx;
   }
   mx = block_max_u64(mx, sh);
-  if (threadIdx.x == 0 && mx != 0) atomicMax(&e[r], exp_bound_bits(mx));
+  if (threadIdx.x == 0 && mx != 0) atomicMax(&e[r >> shift], exp_bound_bits(mx));
 }
 
 // Row slicing: input row r of a complex [rows][K] matrix (leading dimension ld,
 // complex units).  form 0: output row r = (x, y)_k; form 1: rows 2r = (x, y)_k
-// and 2r+1 = (y, -x)_k.  Q is [S][rows_out_p][Kp] BF16 (padding zeroed), e the
+// and 2r+1 = (y, -x)_k; form 3: as form 0 with the exponent e[r >> 1] shared by
+// the rows 2p and 2p+1.  Q is [S][rows_out_p][Kp] BF16 (padding zeroed), e the
 // row exponents (k_oz_rowmax).  grid (input rows incl. padding, ceil(Kp/2 / 2048)).
 __global__ void __launch_bounds__(256) k_oz_slice_rows(const double2* __restrict__ src, int ld,
                                                        int rows, int K, int form, int rows_out_p,
@@ -410,9 +412,9 @@ __global__ void __launch_bounds__(256) k_oz_slice_rows(const double2* __restrict
   const int r = blockIdx.x;
   const double2* row = src + (size_t)r * ld;
   const bool valid = r < rows;
-  const int ex = valid ? oz_exp(e[r]) : 0;
+  const int ex = valid ? oz_exp(e[form == 3 ? r >> 1 : r]) : 0;
   const size_t slice2 = (size_t)rows_out_p * Kp / 2;     // one slice, in BF16 pairs
-  const int orow = form == 0 ? r : 2 * r;
+  const int orow = form == 1 ? 2 * r : r;
   unsigned* base0 = reinterpret_cast<unsigned*>(Q + (size_t)orow * Kp);
   unsigned* base1 = reinterpret_cast<unsigned*>(Q + (size_t)(orow + 1) * Kp);
   const int k0 = blockIdx.y * OZ_ROW_CHUNK, k1 = min(Kp / 2, k0 + OZ_ROW_CHUNK);
@@ -506,6 +508,26 @@ __global__ void k_oz_reduce(const double2* __restrict__ part, int nsplit, long l
   }
 }
 
+// The real-output form: part[z][p][m] holds (Re C[m][2p], Re C[m][2p+1]);
+// C[m][n] = (sum_z, 0) for n < N, fixed order.
+__global__ void k_oz_reduce_real(const double2* __restrict__ part, int nsplit, long long zstride,
+                                 int Mp, int M, int N, double2* __restrict__ C, int ldc) {
+  const int np = (N + 1) / 2;
+  const size_t total = (size_t)M * np;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i / np), p = (int)(i % np);
+    double sx = 0.0, sy = 0.0;
+    for (int z = 0; z < nsplit; ++z) {
+      const double2 v = part[(size_t)z * zstride + (size_t)p * Mp + m];
+      sx += v.x;
+      sy += v.y;
+    }
+    C[(size_t)m * ldc + 2 * p] = make_double2(sx, 0.0);
+    if (2 * p + 1 < N) C[(size_t)m * ldc + 2 * p + 1] = make_double2(sy, 0.0);
+  }
+}
+
 // ---- host side ----------------------------------------------------------------
 static inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
 static inline size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -561,24 +583,28 @@ static OzOperand oz_carve(void* mem, int rows_out, int K) {
 }
 
 // Slices of the rows of a complex [rows][K] matrix (form 0: one output row per
-// input row; form 1: the inner product's B pair).  Returns the carved operand.
+// input row; form 1: the inner product's B pair; form 3: form 0 with one
+// exponent per row pair, e[p] for the rows 2p and 2p+1, the B operand of the
+// real-output inner product).  Returns the carved operand.
 int oz_slice_rows(const double* src, int ld, int rows, int K, int form, void* mem, OzOperand* out,
                   cudaStream_t st, Prof* pf) {
-  const int rows_out = form == 0 ? rows : 2 * rows;
+  const int rows_out = form == 1 ? 2 * rows : rows;
+  const int shift = form == 3 ? 1 : 0;
   *out = oz_carve(mem, rows_out, K);
   if (rows > 0) {
     ProfScope ps(pf, "k_oz_rowmax", st);
-    if (cudaMemsetAsync(out->e, 0x80, (size_t)rows * sizeof(int), st) != cudaSuccess) {
+    const int ne = (rows + shift) >> shift;
+    if (cudaMemsetAsync(out->e, 0x80, (size_t)ne * sizeof(int), st) != cudaSuccess) {
       set_error("oz_slice_rows: memset failed");
       return QE_ECUDA;
     }
     dim3 gm(rows, (K + OZ_ROW_CHUNK - 1) / OZ_ROW_CHUNK);
-    k_oz_rowmax<<<gm, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, out->e);
+    k_oz_rowmax<<<gm, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, shift, out->e);
     int rc = oz_check("k_oz_rowmax");
     if (rc) return rc;
   }
   ProfScope ps(pf, "k_oz_slice_rows", st);
-  const int in_rows_p = form == 0 ? out->rows_p : out->rows_p / 2;
+  const int in_rows_p = form == 1 ? out->rows_p / 2 : out->rows_p;
   dim3 g(in_rows_p, (out->Kp / 2 + OZ_ROW_CHUNK - 1) / OZ_ROW_CHUNK);
   k_oz_slice_rows<<<g, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, rows, K, form,
                                      out->rows_p, out->Kp, out->e, out->q);
@@ -619,11 +645,18 @@ static int oz_splits(int tiles, int nks) {
   return (nks + per - 1) / per;
 }
 
+// Partials of the complex inner product (2N GEMM columns) or of its real-output
+// form (N columns, fewer tiles, so possibly more K splits): the larger of the two.
 size_t oz_partial_bytes(int M, int N, int K) {
-  const int Mp = pad_to(std::max(M, 1), OZ_BM), Np = pad_to(2 * std::max(N, 1), OZ_BM);
+  const int Mp = pad_to(std::max(M, 1), OZ_BM);
   const int nks = pad_to(2 * std::max(K, 1), OZ_BK) / OZ_BK;
-  const int ns = oz_splits((Mp / OZ_BM) * (Np / OZ_BN), nks);
-  return up256((size_t)ns * (Np / 2) * Mp * 16);
+  size_t b = 0;
+  for (int cols : {2 * std::max(N, 1), std::max(N, 1)}) {
+    const int Np = pad_to(cols, OZ_BM);
+    const int ns = oz_splits((Mp / OZ_BM) * (Np / OZ_BN), nks);
+    b = std::max(b, (size_t)ns * (Np / 2) * Mp * 16);
+  }
+  return up256(b);
 }
 
 static int oz_launch(const OzOperand& A, const OzOperand& B, int M, int N, double2* out, int ldo,
@@ -649,16 +682,27 @@ static int oz_launch(const OzOperand& A, const OzOperand& B, int M, int N, doubl
 }
 
 // C[m][n] = sum_k conj(A[m][k]) B[n][k] with A sliced by oz_slice_rows (form 0)
-// and B by oz_slice_rows (form 1); split K, fixed-order reduction.
+// and B by oz_slice_rows (form 1); split K, fixed-order reduction.  real: C[m][n]
+// = (Re sum_k conj(A[m][k]) B[n][k], 0) with B sliced in form 3, so that the
+// GEMM's column pair (2p, 2p+1) holds the real parts of the complex columns 2p
+// and 2p+1 (one exponent per pair): half the columns of the complex form.
 int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* C, int ldc,
-                  void* part, size_t part_bytes, int* status, cudaStream_t st, Prof* pf) {
+                  void* part, size_t part_bytes, int* status, cudaStream_t st, Prof* pf,
+                  bool real = false) {
   if (M <= 0 || N <= 0) return QE_OK;
+  const int Nc = N;
+  if (real) N = (N + 1) / 2;   // GEMM column pairs
   const int nks = A.Kp / OZ_BK;
-  const int ns = oz_splits((A.rows_p / OZ_BM) * (B.rows_p / OZ_BN), nks);
+  int ns = oz_splits((A.rows_p / OZ_BM) * (B.rows_p / OZ_BN), nks);
   const long long zstride = (long long)(B.rows_p / 2) * A.rows_p;
-  if ((size_t)ns * zstride * 16 > part_bytes) {
+  const size_t cap = part_bytes / ((size_t)zstride * 16);   // splits the buffer holds
+  if (cap < 1) {
     set_error("oz_gemm_inner: partial buffer too small");
     return QE_EINVAL;
+  }
+  if ((size_t)ns > cap) {   // fewer, longer K ranges (none empty)
+    const int per = (nks + (int)cap - 1) / (int)cap;
+    ns = (nks + per - 1) / per;
   }
   int rc = oz_launch(A, B, M, N, reinterpret_cast<double2*>(part), A.rows_p, zstride, ns, 0, 0,
                      status, st, pf);
@@ -668,8 +712,13 @@ int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* 
   ProfScope ps(pf, "k_oz_reduce", st);
   const size_t total = (size_t)M * N;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
-  k_oz_reduce<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(part), nsplit, zstride,
-                                      A.rows_p, M, N, reinterpret_cast<double2*>(C), ldc);
+  if (real)
+    k_oz_reduce_real<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(part), nsplit,
+                                             zstride, A.rows_p, M, Nc,
+                                             reinterpret_cast<double2*>(C), ldc);
+  else
+    k_oz_reduce<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(part), nsplit, zstride,
+                                        A.rows_p, M, N, reinterpret_cast<double2*>(C), ldc);
   return oz_check("k_oz_reduce");
 }
 
@@ -709,9 +758,11 @@ size_t oz_outer_scratch(int M, int N, int K) {
 }
 
 // C[m][n] = sum_k conj(A[m][k]) B[n][k] (rows of A and B contiguous in k,
-// leading dimensions in complex units), FP64-accurate on the tensor cores.
+// leading dimensions in complex units), FP64-accurate on the tensor cores;
+// real: C[m][n] = (Re of it, 0) at half the tensor-core work.
 int oz_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
-             int ldc, void* scratch, size_t scratch_bytes, int* status, cudaStream_t st, Prof* pf) {
+             int ldc, void* scratch, size_t scratch_bytes, int* status, cudaStream_t st, Prof* pf,
+             bool real) {
   if (M <= 0 || N <= 0) return QE_OK;
   if (oz_inner_scratch(M, N, K) > scratch_bytes) {
     set_error("oz_inner: scratch too small");
@@ -722,9 +773,9 @@ int oz_inner(const double* A, int lda, const double* B, int ldb, int M, int N, i
   int rc;
   if ((rc = oz_slice_rows(A, lda, M, K, 0, p, &a, st, pf))) return rc;
   p += oz_operand_bytes(M, K);
-  if ((rc = oz_slice_rows(B, ldb, N, K, 1, p, &b, st, pf))) return rc;
+  if ((rc = oz_slice_rows(B, ldb, N, K, real ? 3 : 1, p, &b, st, pf))) return rc;
   p += oz_operand_bytes(2 * N, K);
-  return oz_gemm_inner(a, b, M, N, C, ldc, p, oz_partial_bytes(M, N, K), status, st, pf);
+  return oz_gemm_inner(a, b, M, N, C, ldc, p, oz_partial_bytes(M, N, K), status, st, pf, real);
 }
 
 // C[n][m] (+)= (-) sum_k A[k][m] B[k][n] (rows of A and B indexed by k),
@@ -786,8 +837,10 @@ int nonlocal_oz(const double* beta, const double* dmat, const double* psi, doubl
   double* P = reinterpret_cast<double*>(wb2 + oz_operand_bytes(2 * nb, np));
   P = reinterpret_cast<double*>(((uintptr_t)P + 255) & ~(uintptr_t)255);
   double* Q = reinterpret_cast<double*>(reinterpret_cast<char*>(P) + up256((size_t)np * nb * 16));
-  if ((rc = oz_slice_rows(psi, npw, nb, npw, 1, wb1, &B1, st, pf))) return rc;
-  if ((rc = oz_gemm_inner(A1, B1, np, nb, P, nb, part, oz_partial_bytes(np, nb, npw), status, st, pf)))
+  // real_p: only Re P is used, so the real-output product (half the work)
+  if ((rc = oz_slice_rows(psi, npw, nb, npw, real_p ? 3 : 1, wb1, &B1, st, pf))) return rc;
+  if ((rc = oz_gemm_inner(A1, B1, np, nb, P, nb, part, oz_partial_bytes(np, nb, npw), status, st, pf,
+                          real_p)))
     return rc;
   if ((rc = dmul(dmat, P, Q, np, nb, st, pf, real_p))) return rc;
   if ((rc = oz_slice_cols(Q, nb, np, nb, 2, wb2, &B2, st, pf))) return rc;

@@ -231,8 +231,10 @@ bool oz_worth(long long M, long long N, long long K);
 // a bounded wait that ran out writes a non-zero code to *status.
 size_t oz_inner_scratch(int M, int N, int K);
 size_t oz_outer_scratch(int M, int N, int K);
+// real: C = (Re of the inner product, 0), half the tensor-core work.
 int oz_inner(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
-             int ldc, void* scratch, size_t scratch_bytes, int* status, cudaStream_t st, Prof* pf);
+             int ldc, void* scratch, size_t scratch_bytes, int* status, cudaStream_t st, Prof* pf,
+             bool real = false);
 int oz_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
              int ldc, int alpha_neg, int beta, void* scratch, size_t scratch_bytes, int* status,
              cudaStream_t st, Prof* pf);
