@@ -103,9 +103,11 @@ def test_gamma_hpsi_matches_oracle(q, ctx, nb, prec, tol):
     assert np.abs(got - np.conj(got[:, mg])).max() <= 10 * tol * np.abs(got).max()
 
 
-def test_gamma_hpsi_c1_sampled(q, ctx):
+# nb = 7: an odd band count at C1 size, where the FP64 projections take the
+# real-output tensor-core product with a ragged last column pair
+@pytest.mark.parametrize("nb", [128, 7])
+def test_gamma_hpsi_c1_sampled(q, ctx, nb):
     c = qeinputs.config("C1")
-    nb = c["nbnd"]
     prob, keep, miller, kin = _problem(q, ctx, c, nb)
     psi = _real_in_r(qeinputs.start_bands(kin, nb, c["psi_seed"]), _mirror(miller))
     pt = _to_t(psi)
@@ -113,7 +115,8 @@ def test_gamma_hpsi_c1_sampled(q, ctx):
     ctx.hpsi(prob, pt, ht, q.QE_FP64 | q.QE_GAMMA)
     torch.cuda.synchronize()
     got = _from_t(ht)
-    sel = np.array([0, 1, 62, 63, 126, 127])       # both halves of three band pairs
+    # both halves of three band pairs; all of the odd block
+    sel = np.array([0, 1, 62, 63, 126, 127]) if nb == 128 else np.arange(nb)
     want = _oracle_h(c, psi[sel])
     assert _rel_band(got[sel], want).max() <= 1e-12
 
