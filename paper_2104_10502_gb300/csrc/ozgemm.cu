@@ -22,6 +22,8 @@
 //   inner  P = conj(A) B^T:  A'[m] = (ar, ai)_k,  B'[2n] = (br, bi)_k,  B'[2n+1] = (bi, -br)_k
 //   outer  C = A^T B:        A'[m] = (ar, ai)_k,  B'[2n] = (br, -bi)_k, B'[2n+1] = (bi, br)_k
 // so that column 2n of the real product is Re and 2n+1 is Im of complex column n.
+// Where only Re P is wanted (bands real in r, k = 0): B'[n] = (br, bi)_k, so that
+// columns 2p and 2p+1 are Re P of complex columns 2p and 2p+1 (half the work).
 #include <cuda_bf16.h>
 
 #include <algorithm>
