@@ -56,6 +56,36 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def measure_fp32_peak(dev):
+    """FP32 FMA rate of this GPU measured live: a cuBLAS SGEMM (8192^3, TF32
+    off, 2 N^3 flops), best of 5 after one warm-up.  MEASURED_PEAKS.json holds
+    HBM and BF16 peaks only; this is the FP32-pipe denominator of the FFT
+    kernels' rooflines."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn(n, n, device=dev, dtype=torch.float32)
+        b = torch.randn(n, n, device=dev, dtype=torch.float32)
+        c = a @ b
+        torch.cuda.synchronize(dev)
+        best = None
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = a @ b
+            e1.record()
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        del a, b, c
+        return 2.0 * n ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def fft_flops(n):
     return 5.0 * n * math.log2(n) if n > 1 else 0.0
 
@@ -82,6 +112,29 @@ def kernel_flops(name, c, npw, nst, nax, nb, nproj):
 
 
 TENSOR_KERNELS = {"k_oz_gemm"}
+
+
+def plane_bytes(c, nst, nb, nchunks, s):
+    """Algorithmic DRAM bytes of the plane stage (a4-a6) over nb bands: the
+    sticks read in and written out once (2 nst N3 s per band) and the
+    potential once per band chunk (N s / 2); s = bytes of a complex element."""
+    n1, n2, n3 = c["grid"]
+    return nb * 2.0 * nst * n3 * s + nchunks * n1 * n2 * n3 * s / 2.0
+
+
+def fft_path_bytes(c, npw, nst, nb, nchunks, s):
+    """Algorithmic bytes of the whole FFT path a2-a7 over nb bands:
+    read c and write Hc (2 npw s), the sticks written and read on the way in
+    and on the way out (4 nst N3 s), V once per band chunk (N s / 2)."""
+    n1, n2, n3 = c["grid"]
+    return nb * (2.0 * npw + 4.0 * nst * n3) * s + nchunks * n1 * n2 * n3 * s / 2.0
+
+
+def fft_path_flops(c, nst, nax, nb):
+    """5 N log2 N flops of the pruned transforms a3, a4, a6, a7 and the V
+    multiply, per nb bands."""
+    return (kernel_flops("k_zinv", c, 0, nst, nax, nb, 0) * 2
+            + kernel_flops("k_plane", c, 0, nst, nax, nb, 0))
 
 # ---- FP32 operation count of the float-float FFT (the FP64 path's k_plane) ----------
 # FP32 operations of one float-float operation on a real part (ff.cuh, results
@@ -270,6 +323,26 @@ def c1_cpu_inputs(c):
     return v, beta, d, kin
 
 
+def sampled_oracle_error(q, ctx, prob, psi, psi_h, c, inputs, sel=(0, 63, 127)):
+    """Largest per-band relative error ||Hpsi_gpu - Hpsi_oracle|| / ||Hpsi_oracle||
+    of the FP64 and mixed H|psi> of the timed block, on sampled bands."""
+    import oracle
+    import torch
+    v, beta, d, kin = inputs
+    sel = list(sel)
+    want = oracle.hpsi(c["lat"], c["k"], c["ecut"], c["grid"], v, beta, d, psi_h[sel])
+    out = {"bands": sel}
+    for tag, prec in (("fp64", q.QE_FP64), ("mixed", q.QE_MIXED)):
+        h = torch.empty_like(psi)
+        ctx.hpsi(prob, psi, h, prec)
+        torch.cuda.synchronize()
+        g = h.cpu().numpy()
+        g = g[..., 0] + 1j * g[..., 1]
+        out[tag] = float(max(np.linalg.norm(g[b] - want[i]) / np.linalg.norm(want[i])
+                             for i, b in enumerate(sel)))
+    return out
+
+
 def cpu_oracle_rate(c, inputs, nb_sample, reps):
     """Oracle H|psi> on `nb_sample` bands, `reps` times; returns bands/s."""
     import oracle
@@ -398,50 +471,72 @@ def run_gpu(args, rank, world, local_rank):
              "mixed": world * nb * args.steps / (ms_gmx / 1e3), "unit": "bands/s",
              "bands": "the C1 bands projected on their real-in-r parts (k = 0), two per FFT (QE_GAMMA)"}
 
-    # dominant kernel of the FP64 step and its roofline (FP64 ALU-bound):
-    # algorithmic FLOPs of all its launches in the timed region / their device time
+    # dominant kernel of the FP64 step and its roofline.  SURVEY 8(d): the FFT
+    # kernels are counted in the method's own work (5 N log2 N flops of the
+    # pruned transforms, the sticks and V as bytes), against the pipe they run
+    # on (FP32: the float-float FFT executes on the FP32 pipes; peak = an SGEMM
+    # measured live in this run) and against HBM (MEASURED_PEAKS.json).
     pk, pk_kind = peaks()
+    fp32_peak = measure_fp32_peak(dev)
     plan_nst, plan_nax = stick_counts(c)
     dom = max(kern, key=lambda n: kern[n][1])
     calls, tot = kern[dom]
     avg_ms = tot / calls
-    fl_launch = kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
+    bands_per_launch = nb * args.steps / calls
     extra = {}
     if dom in TENSOR_KERNELS:
-        # per launch already; the measured BF16 burst peak of the GB300s
-        fl_step = fl_launch * calls / args.steps
-        bound, peak = "tensor", pk["bf16_tflops"]
-        psrc = f"measured BF16 burst ({pk_kind}) of MEASURED_PEAKS.json"
+        fl = kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
+        bound, peak, unit = "tensor", pk["bf16_tflops"], "TFLOP/s"
+        psrc = f"BF16 burst of MEASURED_PEAKS.json ({pk_kind})"
+        achieved = fl / (avg_ms / 1e3) / 1e12
     elif dom == "k_plane":
-        # float-float FFT on the FP32 pipes: FP32 flops of its float-float
-        # operations (model above, per band) against the FP32 FMA peak of
-        # 152 SMs x 128 lanes x 2 flops x 2.07 GHz; issue_frac counts its f32x2
-        # instructions (two lane operations each; ncu counts 219 M per C1 band
-        # against the model's 223 M) against the issue limit of one warp
-        # instruction per clock and sub-partition
+        # the method's flops per launch (5 N log2 N, pruned) over the launch time
+        fl = kernel_flops(dom, c, npw, plan_nst, plan_nax, 1, nproj) * bands_per_launch
+        bound, peak, unit = "alu", fp32_peak, "TFLOP/s"
+        psrc = "FP32 FMA rate measured in this run (cuBLAS SGEMM 8192^3, TF32 off)"
+        achieved = fl / (avg_ms / 1e3) / 1e12
+        # float-float instruction count (model of the FP32 operations it executes)
         half = plane_halves(c)
         ops_b, flop_b = ff_plane_launch(c, plan_nax, 1, half)
         inst_b = ops_b / 2          # f32x2: one instruction per two lane operations
-        bands_step = nb * (1 if nb else 0)
-        fl_step = flop_b * bands_step
-        bound, peak = "alu", FP32_NOMINAL_TFLOPS
-        psrc = "nominal FP32 FMA rate of GB300 (recipe table: 152 SMs, 2.07 GHz; 128 lanes per SM)"
-        inst_step = inst_b * bands_step
-        extra = {"fp32_ops_per_band": ops_b, "fp32x2_inst_per_band": inst_b, "fp32_flops_per_band": flop_b,
-                 "fp64_equiv_tflops": kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
-                 * args.steps / (tot / 1e3) / 1e12,
-                 "issue_frac": inst_step * args.steps / (tot / 1e3) / (FP32_NOMINAL_TFLOPS / 2 * 1e12)}
+        nchunks_ff = max(1, round(nb / bands_per_launch))
+        byts = plane_bytes(c, plan_nst, bands_per_launch, 1, 16)
+        extra = {"bands_per_launch": bands_per_launch,
+                 "hbm_algorithmic_gbs": byts / (avg_ms / 1e3) / 1e9,
+                 "hbm_peak_gbs": pk["hbm_gbs"],
+                 "hbm_frac": byts / (avg_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                 "algorithmic_bytes_per_launch": byts,
+                 "fp32_nominal_tflops": FP32_NOMINAL_TFLOPS,
+                 "frac_of_nominal": achieved / FP32_NOMINAL_TFLOPS,
+                 "ff_fp32_flops_per_band": flop_b, "ff_fp32x2_inst_per_band": inst_b,
+                 "ff_emulation_tflops": flop_b * bands_per_launch / (avg_ms / 1e3) / 1e12,
+                 "issue_frac": inst_b * bands_per_launch / (avg_ms / 1e3) / (FP32_NOMINAL_TFLOPS / 2 * 1e12)}
     else:
-        fl_step = fl_launch
-        bound, peak = "alu", FP64_NOMINAL_TFLOPS
-        psrc = "nominal FP64 of GB300 (recipe table); measured DFMA loop 1.17-1.19"
-    fl = fl_step * args.steps / calls
-    achieved = fl_step * args.steps / (tot / 1e3) / 1e12
+        fl = kernel_flops(dom, c, npw, plan_nst, plan_nax, nb, nproj)
+        bound, peak, unit = "alu", FP64_NOMINAL_TFLOPS, "TFLOP/s"
+        psrc = "nominal FP64 of GB300 (recipe table)"
+        achieved = fl / (avg_ms / 1e3) / 1e12
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak,
+            "unit": unit, "frac": achieved / peak,
             "traffic": traffic_for(dom, "fp64"),
             "peak_source": psrc,
             "flops_per_launch": fl, "avg_launch_ms": avg_ms, **extra}
+
+    # the FFT path a2-a7 as a whole (FP64 and mixed): algorithmic bytes rate
+    # against HBM and the method's flops against the FP32 pipe
+    def fft_path(kd, s_bytes):
+        names = ("k_zinv", "k_plane", "k_zfwd", "k_vperm")
+        ms = sum(kd[n][1] for n in names if n in kd) / args.steps
+        nch = max(1, kd.get("k_plane", (1, 0))[0] // max(1, args.steps))
+        byts = fft_path_bytes(c, npw, plan_nst, nb, nch, s_bytes)
+        fl = fft_path_flops(c, plan_nst, plan_nax, nb)
+        return {"ms_per_step": ms, "algorithmic_bytes": byts, "flops": fl,
+                "gbs": byts / (ms / 1e3) / 1e9, "hbm_frac": byts / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                "tflops": fl / (ms / 1e3) / 1e12, "fp32_frac": fl / (ms / 1e3) / 1e12 / fp32_peak}
+    fftp = {"fp64": fft_path(kern, 16), "mixed": fft_path(kern_mixed, 8),
+            "fp32_peak_tflops": fp32_peak, "hbm_peak_gbs": pk["hbm_gbs"],
+            "note": "5 N log2 N flops of the pruned transforms; bytes: c in, Hc out, sticks "
+                    "written and read twice, V once per band chunk"}
     kernels = {n: {"launches": kern[n][0], "ms": kern[n][1], "share": kern[n][1] / sum(x[1] for x in kern.values())}
                for n in kern}
     kernels_mixed = {n: {"launches": kern_mixed[n][0], "ms": kern_mixed[n][1]} for n in kern_mixed}
@@ -483,9 +578,10 @@ def run_gpu(args, rank, world, local_rank):
 
     line = None
     if rank == 0:
+        cinp = c1_cpu_inputs(c)
+        oracle_err = sampled_oracle_error(q, ctx, prob, psi, psi_h, c, cinp)
         cpu = None
         if not args.no_cpu_baseline:
-            cinp = c1_cpu_inputs(c)
             cpu_oracle_rate(c, cinp, 1, 1)
             rate = cpu_oracle_rate(c, cinp, 2, 3)
             cpu = {"value": rate, "unit": "bands/s", "cores": len(os.sched_getaffinity(0)),
@@ -504,7 +600,8 @@ def run_gpu(args, rank, world, local_rank):
                 "mixed": {"value": mixed_value, "unit": "bands/s", "ms_per_step": ms_mixed / args.steps,
                           "dtype": "fp32 FFT + TF32x3 tensor-core projector products",
                           "kernels": kernels_mixed},
-                "gamma": gamma, "fp64_pipe": fp64_pipe,
+                "gamma": gamma, "fp64_pipe": fp64_pipe, "fft_path": fftp,
+                "max_rel_err_vs_oracle": oracle_err,
                 "kernels": kernels, "peaks": pk_kind, "davidson": dav, "serve": srv, "batch": bat}
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -552,46 +649,71 @@ def golden(name):
         return None
 
 
+DAV_LADDER = (3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6)
+DAV_TARGET_RY = 1e-6
+
+
 def run_davidson_bench(q, ctx, dev):
-    """Davidson solves/s: C0 (FP64 tol 1e-8, mixed tol 1e-5) and C2 (FP64 tol 1e-6,
-    mixed tol 1e-4), eigenvalue errors against the oracle's stored references."""
+    """Davidson solves/s at matched accuracy (the metric: mixed vs FP64 at 1e-6
+    Ry).  Every arm -- FP64; mixed (TF32x3 products, FP64 Rayleigh-Ritz, the
+    default); mixed with FP32 reduced eigenproblems (QE_RR_FP32) -- runs at the
+    loosest residual tolerance of DAV_LADDER whose eigenvalues all lie within
+    1e-6 Ry of the oracle's stored values (C0: dense diagonalisation; C2: the
+    oracle's Davidson), found by solving down the ladder; then timed solves at
+    that tolerance (C0: 5, C2: 3): median, min, max.  The FP64 arm is also
+    reported at the strict tolerance of the parity tests (C0 1e-8, C2 1e-6)."""
     import torch
-    out = {}
-    specs = [("C0", q.QE_FP64, 1e-8, 5, "c0_dense_eigs.txt"), ("C0", q.QE_MIXED, 1e-5, 5, "c0_dense_eigs.txt"),
-             ("C2", q.QE_FP64, 1e-6, 1, "c2_davidson_eigs.txt"), ("C2", q.QE_MIXED, 1e-4, 1, "c2_davidson_eigs.txt")]
-    for name, prec, tol, reps, gold in specs:
+    out = {"target_ry": DAV_TARGET_RY, "ladder": list(DAV_LADDER)}
+    arms = (("fp64", q.QE_FP64), ("mixed", q.QE_MIXED), ("mixed_rr32", q.QE_MIXED | q.QE_RR_FP32))
+
+    def solve(prob, pt0, nb, prec, tol):
+        pt = pt0.clone()
+        ev = torch.zeros(nb, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, it = ctx.davidson(prob, pt, ev, None, precision=prec, tol=tol, max_iter=300)
+        torch.cuda.synchronize(dev)
+        return rc, it, ev.cpu().numpy(), time.perf_counter() - t0
+
+    for name, reps, gold, strict in (("C0", 5, "c0_dense_eigs.txt", 1e-8),
+                                     ("C2", 3, "c2_davidson_eigs.txt", 1e-6)):
         c = qeinputs.config(name)
+        nb = c["nbnd"]
         prob, pt0, keep = device_problem(q, ctx, c["lat"], c["k"], c["ecut"], c["grid"], c["tau"],
-                                         c["widths"], c["nbnd"], c["psi_seed"], dev)
-        ev = torch.zeros(c["nbnd"], dtype=torch.float64, device=dev)
-        times, iters = [], []
-        if reps == 1:
-            # one untimed solve first: first-use costs (module loading of kernels
-            # not launched yet, workspace growth) stay out of the single timed one
-            pt = pt0.clone()
-            ctx.davidson(prob, pt, ev, None, precision=prec, tol=tol, max_iter=200)
-            torch.cuda.synchronize(dev)
-        for _ in range(reps):
-            pt = pt0.clone()
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            rc, it = ctx.davidson(prob, pt, ev, None, precision=prec, tol=tol, max_iter=200)
-            torch.cuda.synchronize(dev)
-            times.append(time.perf_counter() - t0)
-            iters.append(it)
-        ref = golden(gold)
-        err = None
-        if ref is not None and len(ref) >= c["nbnd"]:
-            err = float(np.abs(ev.cpu().numpy() - ref[:c["nbnd"]]).max())
-        key = f"{name}_{'fp64' if prec == q.QE_FP64 else 'mixed'}"
-        out[key] = {"solves_per_s": 1.0 / float(np.median(times)), "seconds": float(np.median(times)),
-                    "iters": int(np.median(iters)), "tol": tol, "status": int(rc),
-                    "max_abs_eig_err_ry": err, "nbnd": c["nbnd"]}
-        del prob, pt0, keep
-    for name in ("C0", "C2"):
-        f, m = out.get(f"{name}_fp64"), out.get(f"{name}_mixed")
-        if f and m:
+                                         c["widths"], nb, c["psi_seed"], dev)
+        ref = golden(gold)[:nb]
+        for tag, prec in arms:
+            chosen = None
+            for tol in DAV_LADDER:
+                rc, it, ev, _ = solve(prob, pt0, nb, prec, tol)
+                err = float(np.abs(ev - ref).max())
+                if rc == q.QE_OK and err <= DAV_TARGET_RY:
+                    chosen = (tol, err)
+                    break
+            if chosen is None:
+                out[f"{name}_{tag}"] = {"status": "no tolerance of the ladder met the target"}
+                continue
+            tol = chosen[0]
+            times, iters, errs = [], [], []
+            for _ in range(reps):
+                rc, it, ev, dt = solve(prob, pt0, nb, prec, tol)
+                times.append(dt)
+                iters.append(it)
+                errs.append(float(np.abs(ev - ref).max()))
+            out[f"{name}_{tag}"] = {
+                "solves_per_s": 1.0 / float(np.median(times)), "seconds": float(np.median(times)),
+                "seconds_min": float(min(times)), "seconds_max": float(max(times)), "reps": reps,
+                "iters": int(np.median(iters)), "tol": tol, "status": int(rc),
+                "max_abs_eig_err_ry": max(errs), "nbnd": nb}
+        rc, it, ev, dt = solve(prob, pt0, nb, q.QE_FP64, strict)
+        out[f"{name}_fp64_strict"] = {"tol": strict, "seconds": dt, "iters": int(it), "status": int(rc),
+                                      "max_abs_eig_err_ry": float(np.abs(ev - ref).max())}
+        f, m, m32 = (out.get(f"{name}_{t}") for t in ("fp64", "mixed", "mixed_rr32"))
+        if f and m and "solves_per_s" in f and "solves_per_s" in m:
             out[f"{name}_mixed_speedup"] = m["solves_per_s"] / f["solves_per_s"]
+        if f and m32 and "solves_per_s" in f and "solves_per_s" in m32:
+            out[f"{name}_mixed_rr32_speedup"] = m32["solves_per_s"] / f["solves_per_s"]
+        del prob, pt0, keep
     return out
 
 

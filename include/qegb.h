@@ -71,6 +71,12 @@ enum { QE_GAMMA = 0x100, QE_NO_GAMMA = 0x200 };
  * 1e-12 accuracy class, several times the throughput on GB300, whose FP64
  * rate is 1/64 of its FP32 rate).  Ignored with QE_MIXED. */
 enum { QE_FFT_FP64PIPE = 0x400 };
+/* QE_RR_FP32 (qe_davidson, qe_davidson_batch, with QE_MIXED): solve the
+ * reduced eigenproblems of the mixed iterations (Cholesky of the overlap
+ * matrix, tridiagonal eigensolver) in FP32.  By default QE_MIXED keeps the
+ * Rayleigh-Ritz step in FP64 (on reduced matrices from its TF32x3 products).
+ * Ignored with QE_FP64. */
+enum { QE_RR_FP32 = 0x800 };
 enum { QE_HOST = 0, QE_DEVICE = 1 };  /* where the caller's arrays live */
 
 typedef struct qe_ctx qe_ctx;
@@ -111,6 +117,16 @@ int qe_profile(qe_ctx* ctx, int enable);
  * only reports `launches`.  QE_EINVAL past the last entry. */
 int qe_profile_read(qe_ctx* ctx, int index, char* name, int name_len,
                     long long* calls, double* ms, long long* launches);
+
+/* Test hook for the bounded device waits (failure handling of the timing and
+ * error utilities, Sec. 3.1): with wait_ns > 0, every grid-wide barrier of
+ * the cooperative dense-eigensolver kernels launched by this context's
+ * Davidson solves waits for one arrival more than its grid supplies, for at
+ * most wait_ns nanoseconds, so that each barrier runs out: the kernel sets
+ * the error word and returns, and the solve returns QE_ETIMEOUT with the
+ * context still usable.  wait_ns = 0 restores normal barriers (2 s limit).
+ * Affects solves started after the call. */
+int qe_test_grid_wait(qe_ctx* ctx, long long wait_ns);
 
 /* Plane-wave sphere (Sec. 3.2.2 item (vi): generation of plane waves and their
  * mapping to FFT grids).  S_k = { m : |k + sum_i m_i b_i|^2 <= ecut (1 + 1e-12) },
@@ -165,8 +181,9 @@ int qe_beta_gaussian(qe_ctx* ctx, const double lat[9], const double k[3],
 int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
             const double* psi, double* hpsi, void* stream);
 
-/* H|psi> exactly as qe_hpsi, for callers that cannot allocate device memory
- * (no counterpart in the paper).  Such callers include code running inside a
+/* The same H|psi> as qe_hpsi, to the FP64 parity tolerance (1e-12 per band;
+ * 2e-5 with QE_MIXED), for callers that cannot allocate device memory (no
+ * counterpart in the paper).  Such callers include code running inside a
  * memory pool or arena that another component owns, under an allocator that
  * must see every allocation, or at points where a cudaMalloc would synchronise
  * the device or fail because other work holds the free memory.  qe_hpsi takes
@@ -174,6 +191,10 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
  * entry point takes all of it from one fixed 64 MiB device array inside the
  * library (present on every GPU that loads the library, until process exit)
  * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - precision: QE_FP64 or QE_MIXED only (no QE_GAMMA, no QE_FFT_FP64PIPE:
+ *    QE_EINVAL).  The FP64 projector products run on the SIMT kernels (the
+ *    tensor-core slices of qe_hpsi would not fit in the array), so results
+ *    differ from qe_hpsi by rounding, not bit for bit.
  *  - No context: it runs on the calling thread's current CUDA device, which
  *    must hold every array; prob->mem must be QE_DEVICE (else QE_EINVAL).
  *  - The caller passes inputs (psi, vloc_r, beta, dmat) and the output hpsi.
@@ -183,6 +204,10 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
  *    needed size in qe_last_error() (use qe_hpsi for those).
  *  - The first call on each device looks up the array's device address; make
  *    that first call before any stream capture.
+ *  - A call whose cell, k, cut-off or grid differs from the previous call's on
+ *    the device copies a new plan (the sphere's maps) from host memory into
+ *    the array; that pageable copy can synchronise the calling stream.  Calls
+ *    that repeat the previous problem's plan copy nothing from the host.
  *  - Every call uses the same array and leaves its contents behind; the
  *    kernels overwrite all of it that they read.  Calls whose work overlaps on
  *    the GPU (different streams, or different host threads) race on the

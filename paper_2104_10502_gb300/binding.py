@@ -25,6 +25,9 @@ QE_FP64, QE_MIXED = 0, 1
 QE_GAMMA, QE_NO_GAMMA = 0x100, 0x200
 # or-ed into QE_FP64 for hpsi: the FFT in float64 on the FP64 pipe (default: float-float pairs)
 QE_FFT_FP64PIPE = 0x400
+# or-ed into QE_MIXED for davidson: reduced eigenproblems of the mixed iterations in FP32
+# (default: FP64 Rayleigh-Ritz)
+QE_RR_FP32 = 0x800
 QE_HOST, QE_DEVICE = 0, 1
 
 SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
@@ -32,7 +35,7 @@ SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
            "qe_profile_read", "qe_hpsi_noalloc", "qe_serve_create", "qe_serve_submit",
            "qe_serve_poll", "qe_serve_cancel", "qe_serve_stats", "qe_serve_destroy",
            "qe_hpsi_batch", "qe_batch_create", "qe_batch_run", "qe_batch_destroy", "qe_autotune",
-           "qe_davidson_batch"]
+           "qe_davidson_batch", "qe_test_grid_wait"]
 QE_SERVE_FAKE_SOLVER = 1
 
 
@@ -72,6 +75,7 @@ _lib.qe_vloc_gaussian.argtypes = [_P, _D, _I, ctypes.c_int, _D, ctypes.c_double,
 _lib.qe_beta_gaussian.argtypes = [_P, _D, _D, ctypes.c_double, ctypes.c_int, _D, ctypes.c_int, _D,
                                   _P, ctypes.c_int, _P]
 _lib.qe_profile.argtypes = [_P, ctypes.c_int]
+_lib.qe_test_grid_wait.argtypes = [_P, ctypes.c_longlong]
 _lib.qe_profile_read.argtypes = [_P, ctypes.c_int, ctypes.c_char_p, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_longlong), _D,
                                  ctypes.POINTER(ctypes.c_longlong)]
@@ -228,6 +232,11 @@ class Context:
             i += 1
         return out, launches.value
 
+    def test_grid_wait(self, wait_ns: int):
+        """Test hook: make every grid barrier of later Davidson solves run out
+        after wait_ns nanoseconds (0 restores normal barriers)."""
+        _check(_lib.qe_test_grid_wait(self._h, int(wait_ns)))
+
     # ---- builders ---------------------------------------------------------
     def vloc_gaussian(self, lat, grid, tau, out, amp=-2.0, sigma=1.0, stream=None):
         lat = _f64(lat, 9)
@@ -335,35 +344,6 @@ class Context:
                                            int(max_iter), int(max_dim), pp, pe, pr_, its, sts,
                                            _stream(stream, *psis)), allow=(QE_ENOCONV,))
         return rc, list(sts)[:n], list(its)[:n]
-
-
-class Batch:
-    """A batched H|psi> captured in a CUDA graph (qe_batch_*).  Keeps references
-    to the problems and arrays: replay with run() after updating psi in place."""
-
-    def __init__(self, ctx, probs, psis, hpsis, precision, stream):
-        self._keep = (list(probs), list(psis), list(hpsis))
-        n, arr, pp, hp = Context._batch_args(probs, psis, hpsis)
-        self._keep += (arr, pp, hp)
-        h = _P()
-        self._stream = _stream(stream, *psis)
-        _check(_lib.qe_batch_create(ctx._h, n, arr, int(precision), pp, hp, self._stream,
-                                    ctypes.byref(h)))
-        self._h = h
-
-    def run(self, stream=None):
-        _check(_lib.qe_batch_run(self._h, self._stream if stream is None else _stream(stream)))
-
-    def close(self):
-        if getattr(self, "_h", None):
-            _lib.qe_batch_destroy(self._h)
-            self._h = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
 
 
 class Batch:

@@ -394,6 +394,13 @@ int qe_profile(qe_ctx* ctx, int enable) {
   return QE_OK;
 }
 
+int qe_test_grid_wait(qe_ctx* ctx, long long wait_ns) {
+  clear_error();
+  if (!ctx || wait_ns < 0) { set_error("qe_test_grid_wait: invalid argument"); return QE_EINVAL; }
+  ctx->test_wait_ns = (unsigned long long)wait_ns;
+  return QE_OK;
+}
+
 int qe_profile_read(qe_ctx* ctx, int index, char* name, int name_len, long long* calls,
                     double* ms, long long* launches) {
   clear_error();

@@ -38,6 +38,10 @@ struct qe_ctx {
   std::shared_ptr<void> batch;
   // per-solve Davidson workspaces of a batched solve (basis, reduced matrices)
   std::vector<std::unique_ptr<qe::DevBuf>> dvb_basis, dvb_red;
+  // test hook (qe_test_grid_wait): when non-zero, the grid barriers of this
+  // context's Davidson solves wait for an arrival that never comes, bounded by
+  // this many nanoseconds, so that every one of them runs out
+  unsigned long long test_wait_ns = 0;
   qe_ctx() {
     for (qe::DevBuf* b : bufs()) b->sp = &cur;
   }

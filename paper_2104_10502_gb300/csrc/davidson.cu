@@ -816,6 +816,9 @@ struct DvSolve {
   // mixed path: best largest residual so far and iterations without a 20 % gain
   double best_rmax = HUGE_VAL;
   int stall = 0;
+  // mixed path: solve the reduced eigenproblems of its iterations in FP32
+  // (QE_RR_FP32) instead of FP64
+  bool mixed_rr32 = false;
 };
 
 // The FP64 path solves small reduced problems (n <= 64, the single-CTA path) in
@@ -823,8 +826,11 @@ struct DvSolve {
 // then only steer the next corrections, and FP32 is ~60x faster on GB300.
 // Convergence is accepted only after an FP64 Rayleigh-Ritz.  (On C2, n up to
 // 1024, FP32 Ritz vectors doubled the iteration count, 19 -> 38.)
+// The mixed path keeps its Rayleigh-Ritz (Cholesky of S_r, the reduced
+// eigenproblem) in FP64 by default, on reduced matrices from its TF32x3
+// products; with QE_RR_FP32 it solves them in FP32 like the small FP64 ones.
 static bool rr_in_fp32(const DvSolve& v) {
-  if (v.precision != QE_FP64) return true;
+  if (v.precision != QE_FP64) return v.mixed_rr32;
   return v.n <= kSmallDense && v.rmax > std::max(1e-3, 1e3 * v.tol);
 }
 
@@ -1168,6 +1174,10 @@ int dv_setup(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int
   S.max_dim = md;
   S.np = prob->nproj;
   DV_TRY(dv_alloc(basis, red, S, precision == QE_FP64));
+  if (ctx->test_wait_ns) {
+    S.dw.bar.wait_ns = ctx->test_wait_ns;
+    S.dw.bar.stall = 1;
+  }
   S.gamma = false;
   S.mg = nullptr;
   if (allow_gamma && P->h.gamma && P->mg) {
@@ -1212,8 +1222,8 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   clear_error();
   if (!ctx) { set_error("qe_davidson: null context"); return QE_EINVAL; }
   DV_TRY(check_problem(prob, "qe_davidson"));
-  const int flags = precision & (QE_GAMMA | QE_NO_GAMMA);
-  precision &= ~(QE_GAMMA | QE_NO_GAMMA);
+  const int flags = precision & (QE_GAMMA | QE_NO_GAMMA | QE_RR_FP32);
+  precision &= ~(QE_GAMMA | QE_NO_GAMMA | QE_RR_FP32);
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_davidson: bad precision"); return QE_EINVAL; }
   if (!(tol > 0.0) || max_iter < 0) { set_error("qe_davidson: tol must be > 0, max_iter >= 0"); return QE_EINVAL; }
   const bool allow_gamma = gamma_mode(precision, flags, prob->grid);
@@ -1227,6 +1237,7 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   DvSolve v;
   DV_TRY(dv_setup(ctx, prob, precision, tol, max_iter, max_dim, ctx->dv_basis, ctx->dv_red, v, st,
                   "qe_davidson", allow_gamma));
+  v.mixed_rr32 = (flags & QE_RR_FP32) != 0;
   DvState& S = v.S;
   const size_t bytes = (size_t)nb * S.npw * sizeof(z);
   const cudaMemcpyKind in_kind = prob->mem == QE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -1258,8 +1269,8 @@ extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs
     set_error("qe_davidson_batch: bad problem list");
     return QE_EINVAL;
   }
-  const int flags = precision & (QE_GAMMA | QE_NO_GAMMA);
-  precision &= ~(QE_GAMMA | QE_NO_GAMMA);
+  const int flags = precision & (QE_GAMMA | QE_NO_GAMMA | QE_RR_FP32);
+  precision &= ~(QE_GAMMA | QE_NO_GAMMA | QE_RR_FP32);
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_davidson_batch: bad precision"); return QE_EINVAL; }
   if (!(tol > 0.0) || max_iter < 0) { set_error("qe_davidson_batch: tol must be > 0, max_iter >= 0"); return QE_EINVAL; }
   for (int p = 0; p < nprob; ++p) {
@@ -1298,6 +1309,7 @@ extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs
     DV_TRY(dv_setup(ctx, &probs[p], precision, tol, max_iter, max_dim, *ctx->dvb_basis[i],
                     *ctx->dvb_red[i], vs[i], st, "qe_davidson_batch",
                     gamma_mode(precision, flags, probs[p].grid)));
+    vs[i].mixed_rr32 = (flags & QE_RR_FP32) != 0;
     DV_CU(cudaMemcpyAsync(vs[i].S.V, psi_inout[p], (size_t)vs[i].S.nb * vs[i].S.npw * sizeof(z),
                           cudaMemcpyDeviceToDevice, st));
   }

@@ -13,10 +13,15 @@ constexpr int kSmallDense = 64;   // largest one solved by the single-CTA shared
 
 // State of the grid-wide barrier of the cooperative kernels (zeroed by the host
 // before each launch); err is the shared error word (1 = a barrier timed out).
+// wait_ns bounds every wait (2 s); stall (0 normally) is the number of extra
+// arrivals a barrier waits for: a count that no CTA supplies, so that every
+// barrier runs out (the test hook qe_test_grid_wait).
 struct GridBar {
   unsigned int* count = nullptr;   // count[0] arrivals, count[1] generation
   unsigned int* gen = nullptr;     // == count + 1
   int* err = nullptr;
+  unsigned long long wait_ns = 2000000000ull;
+  unsigned int stall = 0;
 };
 
 // Precision-dependent constants of the dense kernels (machine epsilon, the

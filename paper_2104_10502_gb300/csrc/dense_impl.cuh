@@ -91,8 +91,8 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every wait
-// is bounded (2 s); on time-out the error word is set, the waiting CTAs see it
-// within 1024 polls, return false and leave the kernel.
+// is bounded (b.wait_ns, 2 s); on time-out the error word is set, the waiting
+// CTAs see it within 1024 polls, return false and leave the kernel.
 __device__ bool grid_sync(const GridBar& b) {
   __shared__ int s_ok;
   __syncthreads();
@@ -103,7 +103,7 @@ __device__ bool grid_sync(const GridBar& b) {
     const unsigned int g = ld_acquire_gpu(b.gen);
     __threadfence();
     const unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
-    if (arrived == gridDim.x) {
+    if (arrived == gridDim.x + b.stall) {
       atomicExch(b.count, 0u);
       __threadfence();
       atomicAdd(b.gen, 1u);
@@ -116,7 +116,7 @@ __device__ bool grid_sync(const GridBar& b) {
         if ((it & 1023) == 1023) {
           const unsigned long long t = gtime_ns();
           if (t0 == 0) t0 = t;
-          else if (t - t0 > 2000000000ull) { atomicExch(b.err, 1); ok = 0; break; }
+          else if (t - t0 > b.wait_ns) { atomicExch(b.err, 1); ok = 0; break; }
           if (*(volatile int*)b.err) { ok = 0; break; }
         }
       }
@@ -132,7 +132,7 @@ __device__ bool grid_sync(const GridBar& b) {
 // of the launch returns once count reaches k * gridDim.x.  Arrival is one
 // fence and one reduction without a return value, the wait one acquire poll
 // of the same word: fewer L2 round trips than the generation barrier.  Bounded
-// (2 s) like grid_sync.
+// (b.wait_ns) like grid_sync.
 __device__ bool grid_sync_mono(const GridBar& b, unsigned k) {
   __shared__ int s_ok;
   __syncthreads();
@@ -141,14 +141,14 @@ __device__ bool grid_sync_mono(const GridBar& b, unsigned k) {
     int ok = 1;
     __threadfence();
     atomicAdd(b.count, 1u);
-    const unsigned target = k * gridDim.x;
+    const unsigned target = k * gridDim.x + b.stall;
     unsigned long long t0 = 0;
     for (int it = 0;; ++it) {
       if (ld_acquire_gpu(b.count) >= target) break;
       if ((it & 1023) == 1023) {
         const unsigned long long t = gtime_ns();
         if (t0 == 0) t0 = t;
-        else if (t - t0 > 2000000000ull) { atomicExch(b.err, 1); ok = 0; break; }
+        else if (t - t0 > b.wait_ns) { atomicExch(b.err, 1); ok = 0; break; }
         if (*(volatile int*)b.err) { ok = 0; break; }
       }
     }

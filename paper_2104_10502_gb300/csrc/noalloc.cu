@@ -33,6 +33,21 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 static std::mutex g_noalloc_mu;
 static std::vector<void*> g_noalloc_addr;   // device address of the array, per device
 
+// The plan (sphere maps, twiddles, digit reversals) that the array holds on
+// each device: a call with the same cell, k, cut-off and grid finds it there
+// and copies nothing from the host.
+struct NoallocPlanKey {
+  bool valid = false;
+  double lat[9], k[3], ecut;
+  int grid[3];
+  bool same(const qe_problem* pr) const {
+    return valid && std::memcmp(lat, pr->lat, sizeof(lat)) == 0 &&
+           std::memcmp(k, pr->k, sizeof(k)) == 0 && ecut == pr->ecutwfc &&
+           std::memcmp(grid, pr->grid, sizeof(grid)) == 0;
+  }
+};
+static std::vector<NoallocPlanKey> g_noalloc_plan;   // per device
+
 // Once per device, with that device current: the array's device address.  The
 // host-side symbol is only a stand-in and must never be handed to a kernel.
 static int noalloc_scratch(int dev, void** out) {
@@ -55,7 +70,7 @@ static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 template <typename T>
 static int hpsi_noalloc_impl(const qe_problem* pr, const double* psi, double* hpsi,
-                             cudaStream_t st, unsigned char* base) {
+                             cudaStream_t st, unsigned char* base, int dev) {
   DevPlan P;   // device pointers below point into the fixed array; P.block stays null
   std::memcpy(P.lat, pr->lat, sizeof(P.lat));
   std::memcpy(P.k, pr->k, sizeof(P.k));
@@ -122,10 +137,23 @@ static int hpsi_noalloc_impl(const qe_problem* pr, const double* psi, double* hp
   const size_t o_ax = put_i(h.ax.data(), h.nax);
   size_t o_perm[3];
   for (int c = 0; c < 3; ++c) o_perm[c] = put_i(perm[c].data(), perm[c].size());
-  cudaError_t e = cudaMemcpyAsync(p_plan, img.data(), plan_bytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) {
-    set_error("qe_hpsi_noalloc: plan upload: %s", cudaGetErrorString(e));
-    return QE_ECUDA;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if ((int)g_noalloc_plan.size() <= dev) g_noalloc_plan.resize(dev + 1);
+    NoallocPlanKey& key = g_noalloc_plan[dev];
+    if (!key.same(pr)) {
+      key.valid = false;
+      cudaError_t e = cudaMemcpyAsync(p_plan, img.data(), plan_bytes, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) {
+        set_error("qe_hpsi_noalloc: plan upload: %s", cudaGetErrorString(e));
+        return QE_ECUDA;
+      }
+      std::memcpy(key.lat, pr->lat, sizeof(key.lat));
+      std::memcpy(key.k, pr->k, sizeof(key.k));
+      key.ecut = pr->ecutwfc;
+      std::memcpy(key.grid, pr->grid, sizeof(key.grid));
+      key.valid = true;
+    }
   }
   double* dd = reinterpret_cast<double*>(p_plan);
   int* di = reinterpret_cast<int*>(p_plan + nd * sizeof(double));
@@ -188,6 +216,6 @@ extern "C" int qe_hpsi_noalloc(const qe_problem* prob, int precision, const doub
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   unsigned char* b = static_cast<unsigned char*>(base);
-  if (precision == QE_FP64) return qe::hpsi_noalloc_impl<qe::FftF64>(prob, psi, hpsi, st, b);
-  return qe::hpsi_noalloc_impl<float>(prob, psi, hpsi, st, b);
+  if (precision == QE_FP64) return qe::hpsi_noalloc_impl<qe::FftF64>(prob, psi, hpsi, st, b, dev);
+  return qe::hpsi_noalloc_impl<float>(prob, psi, hpsi, st, b, dev);
 }

@@ -74,7 +74,7 @@ def test_single_plane_wave_gives_analytic_gaussian_coefficients():
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
 
 
-def test_vtilde_matches_analytic_on_skewed_cell():
+def test_vtilde_matches_analytic_on_orthorhombic_cell():
     lat = np.array([[9.0, 0.0, 0.0], [0.0, 10.0, 0.0], [0.0, 0.0, 11.0]])
     tau = np.array([[1.0, 2.0, 3.0], [6.0, 5.5, 8.0]])
     grid = (30, 32, 36)
@@ -82,6 +82,31 @@ def test_vtilde_matches_analytic_on_skewed_cell():
     vt = oracle.vtilde(v)
     b = oracle.reciprocal(lat)
     for g in [(0, 0, 0), (1, 0, 0), (2, -3, 1), (-4, 4, 5), (3, 3, -3)]:
+        gc = np.array(g) @ b
+        want = _vc_analytic(lat, tau, gc[None, :])[0]
+        got = vt[g[2] % grid[2], g[1] % grid[1], g[0] % grid[0]]
+        assert abs(got - want) < 1e-15
+
+
+@pytest.mark.parametrize("lat", [
+    np.array([[10.0, 0.0, 0.0], [2.0, 10.0, 0.0], [1.0, -1.5, 11.0]]),
+    np.array([[10.5, 0.7, -0.4], [-1.2, 9.8, 0.9], [0.6, 2.1, 10.2]]),
+])
+def test_vtilde_matches_analytic_on_skewed_cell(lat):
+    """The general (27-image) branch of vloc_gaussian on skewed cells: its
+    discrete Fourier coefficients equal the closed-form transform of the
+    periodic Gaussian, (amp / Omega) (2 pi sigma^2)^{3/2} e^{-sigma^2 g^2 / 2}
+    sum_I e^{-i g.R_I}, at Cartesian g = sum_i m_i b_i.  A lattice used by
+    columns instead of rows (r or the images built from lat^T) moves the
+    Gaussians and fails here.  Truncation of the image sum (next images at
+    >= 9 bohr: e^{-40}) and grid aliasing (e^{-60}) are far below the bound."""
+    tau = np.array([[1.0, 2.0, 3.0], [6.0, 5.5, 8.0], [8.5, 0.4, 1.2]])
+    grid = (40, 40, 45)
+    v = oracle.vloc_gaussian(lat, grid, tau)
+    vt = oracle.vtilde(v)
+    b = oracle.reciprocal(lat)
+    for g in [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, -3, 1), (-4, 4, 5), (3, 3, -3),
+              (1, -1, 2), (-2, 0, -3)]:
         gc = np.array(g) @ b
         want = _vc_analytic(lat, tau, gc[None, :])[0]
         got = vt[g[2] % grid[2], g[1] % grid[1], g[0] % grid[0]]
