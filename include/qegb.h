@@ -229,6 +229,44 @@ int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
                 int max_iter, int max_dim, double* psi_inout, double* evals,
                 double* resid, int* iters, void* stream);
 
+/* Band-by-band conjugate-gradient eigensolver (Sec. 3.3: iterative solution of
+ * the Kohn-Sham Hamiltonian with the conjugate-gradient method, beside
+ * Davidson) for the nbnd lowest eigenpairs, on the same H|psi> as qe_hpsi.
+ * The start bands are rotated by a Rayleigh-Ritz step; then, in a sweep, each
+ * band in turn minimises its Rayleigh quotient orthogonally to the bands below
+ * it along preconditioned Polak-Ribiere directions with an exact line
+ * minimisation (at most max_iter iterations per band and sweep), and the sweep
+ * ends with a Rayleigh-Ritz rotation of the block.  Converged when every
+ * ||H psi_n - e_n psi_n|| <= tol after a rotation; QE_ENOCONV (best bands
+ * filled in) after max_sweeps sweeps.  QE_MIXED sweeps with FP32 products and
+ * H while residuals are above max(tol, 1e-4), then in FP64.  psi_inout, evals,
+ * resid (may be NULL) as qe_davidson; iters (may be NULL): CG iterations (H
+ * applications to search directions) summed over bands and sweeps.  Arrays
+ * per prob->mem; device work is ordered on `stream` and the call returns after
+ * it ends. */
+int qe_cg(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int max_iter,
+          int max_sweeps, double* psi_inout, double* evals, double* resid, int* iters,
+          void* stream);
+
+/* Charge density (Sec. 3.3: charge-density generation, on the bands of the
+ * iterative solvers) of a set of bands over k points of one cell:
+ *   rho(r_j) = (1 / Omega) sum_k sum_n w_nk |psi_nk(r_j)|^2,
+ *   psi_nk(r_j) = sum_G c_nk(G) e^{iG.r_j},
+ * on the grid [N3][N2][N1] (x fastest), Omega = |det lat|; for bands with
+ * sum_G |c|^2 = 1, (Omega / N) sum_j rho(r_j) = sum_nk w_nk.
+ * kpts [nk][3] (Cartesian, host); nbnd [nk] (host); psi[i]: the bands of k
+ * point i, complex [nbnd[i]][npw_i][2] in that k point's qe_gsphere order;
+ * weights[i]: [nbnd[i]] doubles w_nk (occupation times k weight), host arrays.
+ * psi[i] and rho live per `mem` (QE_HOST / QE_DEVICE).  precision: QE_FP64
+ * (FP64-accurate: the float-float FFT of qe_hpsi, sums in float64) or
+ * QE_MIXED (FP32 FFT), optionally or-ed with QE_GAMMA (k = 0 points: bands
+ * real in r, two per FFT).  The sum over bands and k points runs in a fixed
+ * order: results are deterministic.  Device work is ordered on `stream`; with
+ * QE_HOST the call returns after it ends. */
+int qe_density(qe_ctx* ctx, const double lat[9], double ecut, const int grid[3], int nk,
+               const double* kpts, const int* nbnd, const double* const* psi,
+               const double* const* weights, int precision, double* rho, int mem, void* stream);
+
 /* ---- Batches: many problems per launch --------------------------------------
  * The paper's benchmarks parallelise over k points (pools, Sec. 3.3) and note
  * that several small runs sharing one GPU pay off.  A batch applies H to the

@@ -19,10 +19,12 @@ from .pw import (reciprocal, volume, gsphere, grid_slots, vloc_gaussian,
 from .hamiltonian import (apply_local, apply_nonlocal, apply_kinetic, hpsi,
                           dense_h, h_diag, vtilde)
 from .eigen import rayleigh_ritz, davidson
+from .density import band_in_r, density
+from .cg import cg
 
 __all__ = [
     "reciprocal", "volume", "gsphere", "grid_slots", "vloc_gaussian",
     "beta_gaussian", "check_grid", "apply_local", "apply_nonlocal",
     "apply_kinetic", "hpsi", "dense_h", "h_diag", "vtilde", "rayleigh_ritz",
-    "davidson",
+    "davidson", "band_in_r", "density", "cg",
 ]

@@ -35,7 +35,7 @@ SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
            "qe_profile_read", "qe_hpsi_noalloc", "qe_serve_create", "qe_serve_submit",
            "qe_serve_poll", "qe_serve_cancel", "qe_serve_stats", "qe_serve_destroy",
            "qe_hpsi_batch", "qe_batch_create", "qe_batch_run", "qe_batch_destroy", "qe_autotune",
-           "qe_davidson_batch", "qe_test_grid_wait"]
+           "qe_davidson_batch", "qe_test_grid_wait", "qe_cg", "qe_density"]
 QE_SERVE_FAKE_SOLVER = 1
 
 
@@ -102,6 +102,10 @@ _lib.qe_hpsi_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, _P, _P, 
 _lib.qe_hpsi.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_davidson.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
                              ctypes.c_int, ctypes.c_int, _P, _P, _P, _I, _P]
+_lib.qe_density.argtypes = [_P, _D, ctypes.c_double, _I, ctypes.c_int, _D, _I, ctypes.POINTER(_P),
+                            ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int, _P]
+_lib.qe_cg.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                       ctypes.c_int, _P, _P, _P, _I, _P]
 _lib.qe_davidson_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P),
                                    ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I, _P]
@@ -328,6 +332,48 @@ class Context:
                                      int(max_iter), int(max_dim), pp, pe, pr_, ctypes.byref(it),
                                      _stream(stream, psi)), allow=(QE_ENOCONV,))
         return rc, it.value
+
+    def cg(self, prob: Problem, psi, evals, resid=None, precision=QE_FP64, tol=1e-8,
+           max_iter=100, max_sweeps=20, stream=None):
+        """Band-by-band CG.  Returns (status, iters); status QE_OK or QE_ENOCONV."""
+        pp, mp = _ptr(psi)
+        pe, me = _ptr(evals)
+        pr_, mr = _ptr(resid)
+        if mp != prob.mem or me != prob.mem or (resid is not None and mr != prob.mem):
+            raise ValueError("psi/evals/resid must live where the problem's arrays live")
+        it = ctypes.c_int(0)
+        rc = _check(_lib.qe_cg(self._h, ctypes.byref(prob), int(precision), float(tol), int(max_iter),
+                               int(max_sweeps), pp, pe, pr_, ctypes.byref(it), _stream(stream, psi)),
+                    allow=(QE_ENOCONV,))
+        return rc, it.value
+
+    def density(self, lat, ecut, grid, kpts, psis, weights, rho, precision=QE_FP64, stream=None):
+        """rho = (1/Omega) sum_k sum_n w_nk |psi_nk(r)|^2 on the grid.  psis: per k
+        point, host complex128 (nb, npw) arrays or CUDA tensors (nb, npw, 2);
+        weights: per k point, host float64 (nb,); rho: host float64 or CUDA
+        tensor (N3, N2, N1), where the bands live."""
+        lat = _f64(lat, 9)
+        g = np.ascontiguousarray(grid, dtype=np.int32)
+        kp = _f64(kpts).reshape(-1, 3)
+        nk = kp.shape[0]
+        if len(psis) != nk or len(weights) != nk:
+            raise ValueError("one band block and one weight vector per k point")
+        nb = np.ascontiguousarray([int(p.shape[0]) for p in psis], dtype=np.int32)
+        ws = [_f64(w) for w in weights]
+        pr, mr = _ptr(rho)
+        ptrs, mems = [], set()
+        for p in psis:
+            pp, mp = _ptr(p)
+            ptrs.append(pp)
+            mems.add(mp)
+        if mems and mems != {mr}:
+            raise ValueError("bands and rho must live in the same memory")
+        parr = (_P * max(nk, 1))(*ptrs)
+        warr = (_P * max(nk, 1))(*[ctypes.c_void_p(w.ctypes.data) for w in ws])
+        _check(_lib.qe_density(self._h, _dptr(lat), float(ecut), g.ctypes.data_as(_I), nk,
+                               _dptr(kp), nb.ctypes.data_as(_I), parr, warr, int(precision), pr, mr,
+                               _stream(stream, rho)))
+        return rho
 
     def davidson_batch(self, probs, psis, evals, resids=None, precision=QE_FP64, tol=1e-8,
                        max_iter=100, max_dim=0, stream=None):

@@ -21,6 +21,8 @@ struct qe_ctx {
   qe::DevBuf h_v, h_beta, h_d, h_psi, h_hpsi;
   // Davidson workspaces
   qe::DevBuf dv_basis, dv_red;
+  // charge density: per-group accumulators and the band weights
+  qe::DevBuf dens_acc, dens_w;
   // tensor-core path: packed operands and the kernel's status word (a bounded
   // wait that ran out writes a non-zero code; read at the next synchronising point)
   qe::DevBuf tc_work, tc_status, tc_beta;
@@ -48,7 +50,7 @@ struct qe_ctx {
   std::vector<qe::DevBuf*> bufs() {
     return {&sticks, &vp,       &part,     &proj,   &projd,   &h_v,     &h_beta,
             &h_d,    &h_psi,    &h_hpsi,   &dv_basis, &dv_red, &tc_work, &tc_status, &tc_beta,
-            &oz_beta, &oz_work};
+            &oz_beta, &oz_work, &dens_acc, &dens_w};
   }
 };
 

@@ -1214,6 +1214,242 @@ int dv_final_status(DvSolve& v, cudaStream_t st, const char* who) {
   return QE_OK;
 }
 
+// ---- band-by-band conjugate gradient ------------------------------------------------
+// Sec. 3.3 names the conjugate-gradient method beside Davidson.  Each band
+// minimises the Rayleigh quotient in the complement of the bands below it, along
+// preconditioned Polak-Ribiere directions, with an exact line minimisation on
+// the unit sphere (Teter, Payne and Allan 1989); a sweep over the bands ends with
+// a Rayleigh-Ritz rotation of the block.  The vector operations of one band run
+// in single-CTA kernels (one fixed-order reduction each); the projections on the
+// lower bands and H are the library's products.
+
+// e = Re<p|hp>; g = hp - e p; ||g||; z = g / sqrt((h_G - e)^2 + pmin^2)
+__global__ void __launch_bounds__(1024) k_cg_grad(const z* __restrict__ p, const z* __restrict__ hp,
+                                                  const double* __restrict__ hd, int npw, double pmin2,
+                                                  z* __restrict__ g, z* __restrict__ zz, double* sc) {
+  __shared__ double sh[33];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) s += p[i].x * hp[i].x + p[i].y * hp[i].y;
+  const double e = dv_block_sum(s, sh);
+  double gg = 0.0;
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) {
+    const z a = hp[i], b = p[i];
+    const z v = {a.x - e * b.x, a.y - e * b.y};
+    g[i] = v;
+    gg += v.x * v.x + v.y * v.y;
+    const double x = hd[i] - e;
+    const double inv = rsqrt(x * x + pmin2);
+    zz[i] = {v.x * inv, v.y * inv};
+  }
+  gg = dv_block_sum(gg, sh);
+  if (threadIdx.x == 0) { sc[0] = e; sc[1] = sqrt(gg); }
+}
+
+// d = z (first) or z + max(0, Re<z, g - g_prev> / gz_prev) d_prev; sc[3] = Re<z, g>
+__global__ void __launch_bounds__(1024) k_cg_dir(const z* __restrict__ zz, const z* __restrict__ g,
+                                                 const z* __restrict__ gp, const z* __restrict__ dp,
+                                                 z* __restrict__ d, int npw, int first, double* sc) {
+  __shared__ double sh[33];
+  double num = 0.0, gz = 0.0;
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) {
+    const z a = zz[i], b = g[i];
+    gz += a.x * b.x + a.y * b.y;
+    if (!first) {
+      const z c = gp[i];
+      num += a.x * (b.x - c.x) + a.y * (b.y - c.y);
+    }
+  }
+  gz = dv_block_sum(gz, sh);
+  num = dv_block_sum(num, sh);
+  const double beta = first ? 0.0 : fmax(0.0, num / sc[2]);
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) {
+    const z a = zz[i];
+    if (first) d[i] = a;
+    else d[i] = {a.x + beta * dp[i].x, a.y + beta * dp[i].y};
+  }
+  if (threadIdx.x == 0) sc[3] = gz;
+}
+
+// dn = d / ||d||
+__global__ void __launch_bounds__(1024) k_cg_unit(const z* __restrict__ d, z* __restrict__ dn, int npw) {
+  __shared__ double sh[33];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) s += d[i].x * d[i].x + d[i].y * d[i].y;
+  s = dv_block_sum(s, sh);
+  const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) dn[i] = {d[i].x * inv, d[i].y * inv};
+}
+
+// exact line minimum on p(t) = cos t p + sin t dn: b = Re<p|H dn>, c = <dn|H dn>,
+// t = atan2(-2b, c - e) / 2; p, hp move there; gz_prev <- gz
+__global__ void __launch_bounds__(1024) k_cg_step(z* __restrict__ p, z* __restrict__ hp,
+                                                  const z* __restrict__ dn, const z* __restrict__ hdn,
+                                                  int npw, double* sc) {
+  __shared__ double sh[33];
+  double b = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) {
+    const z h = hdn[i];
+    b += p[i].x * h.x + p[i].y * h.y;
+    c += dn[i].x * h.x + dn[i].y * h.y;
+  }
+  b = dv_block_sum(b, sh);
+  c = dv_block_sum(c, sh);
+  const double t = 0.5 * atan2(-2.0 * b, c - sc[0]);
+  double sn, cs;
+  sincos(t, &sn, &cs);
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) {
+    const z a = p[i], u = dn[i], ha = hp[i], hu = hdn[i];
+    p[i] = {cs * a.x + sn * u.x, cs * a.y + sn * u.y};
+    hp[i] = {cs * ha.x + sn * hu.x, cs * ha.y + sn * hu.y};
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sc[2] = sc[3];
+}
+
+// p, hp <- p / ||p||, hp / ||p||
+__global__ void __launch_bounds__(1024) k_cg_renorm(z* __restrict__ p, z* __restrict__ hp, int npw) {
+  __shared__ double sh[33];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) s += p[i].x * p[i].x + p[i].y * p[i].y;
+  s = dv_block_sum(s, sh);
+  const double inv = 1.0 / sqrt(s);
+  for (int i = threadIdx.x; i < npw; i += blockDim.x) {
+    p[i] = {p[i].x * inv, p[i].y * inv};
+    hp[i] = {hp[i].x * inv, hp[i].y * inv};
+  }
+}
+
+// x -= A^T (A^+ x) over the rows [0, m) of A (projection on orthonormal rows);
+// with hx, also hx -= HA^T (A^+ x) (the same combination of the H products).
+template <typename T>
+static int cg_project(const DvState& S, const z* A, const z* HA, int m, z* x, z* hx,
+                      cudaStream_t st, Prof* pf) {
+  if (m <= 0) return QE_OK;
+  const int npw = S.npw;
+  DV_TRY(gemm_inner<T>((const double*)A, npw, (const double*)x, npw, m, 1, npw, (double*)S.G, 1,
+                       S.part, S.part_bytes, st, pf));
+  if (hx)
+    DV_TRY(gemm_outer_ab<T>((const double*)HA, npw, (const double*)S.G, 1, npw, 1, m, (double*)hx,
+                            npw, 1, 1, st, pf));
+  return gemm_outer_ab<T>((const double*)A, npw, (const double*)S.G, 1, npw, 1, m, (double*)x, npw,
+                          1, 1, st, pf);
+}
+
+struct CgRun {
+  int iters = 0, sweeps = 0;
+  bool conv = false;
+};
+
+// Rayleigh-Ritz of span(Psi) (FP64 reduced problem, products in T), the
+// rotated bands and their residual norms; returns the largest residual norm.
+template <typename T>
+static int cg_rotate(qe_ctx* ctx, DvSolve& v, cudaStream_t st, double* rmax) {
+  DvState& S = v.S;
+  Prof* pf = &ctx->prof;
+  const int nb = S.nb, npw = S.npw;
+  const size_t bytes = (size_t)nb * npw * sizeof(z);
+  DV_CU(cudaMemcpyAsync(S.V, S.Psi, bytes, cudaMemcpyDeviceToDevice, st));
+  DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, bytes, cudaMemcpyDeviceToDevice, st));
+  DV_TRY(update_reduced<T>(S, 0, nb, true, st, pf));
+  DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
+  DV_TRY(rayleigh_ritz(S, nb, true, st, pf));
+  DV_TRY(outer<T>(S, S.V, npw, S.X, nb, npw, nb, nb, S.Psi, npw, 0, 0, st, pf));
+  DV_TRY(outer<T>(S, S.HV, npw, S.X, nb, npw, nb, nb, S.HPsi, npw, 0, 0, st, pf));
+  k_resid<<<nb, 256, 0, st>>>(S.Psi, S.HPsi, S.e, npw, S.R, S.rn);
+  DV_TRY(check_launch("k_resid"));
+  DV_CU(cudaMemcpyAsync(v.rn.data(), S.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DV_CU(cudaStreamSynchronize(st));
+  DV_TRY(tc_check(ctx, st));
+  double r = 0.0;
+  for (int b = 0; b < nb; ++b) r = std::max(r, std::isfinite(v.rn[b]) ? v.rn[b] : HUGE_VAL);
+  *rmax = r;
+  return QE_OK;
+}
+
+// One sweep: every band in turn, at most max_iter CG iterations each.
+template <typename T>
+static int cg_sweep(qe_ctx* ctx, DvSolve& v, int precision, double tol, int max_iter, CgRun& run,
+                    cudaStream_t st) {
+  DvState& S = v.S;
+  Prof* pf = &ctx->prof;
+  const int nb = S.nb, npw = S.npw;
+  const double pmin2 = 0.1 * 0.1;
+  // scratch rows past the bands: V[nb..nb+3], HV[nb..nb+3] (max_dim >= nb + 4)
+  z* g = S.V + (size_t)nb * npw;
+  z* gp = g + npw;
+  z* zz = gp + npw;
+  z* zp = zz + npw;
+  z* d = S.HV + (size_t)(nb + 2) * npw;
+  z* dp = d + npw;
+  z* dn = S.HV + (size_t)nb * npw;
+  z* hdn = dn + npw;
+  double* sc = reinterpret_cast<double*>(S.C);
+  for (int n = 0; n < nb; ++n) {
+    z* p = S.Psi + (size_t)n * npw;
+    z* hp = S.HPsi + (size_t)n * npw;
+    if (n > 0) {
+      DV_TRY(cg_project<T>(S, S.Psi, S.HPsi, n, p, hp, st, pf));
+      k_cg_renorm<<<1, 1024, 0, st>>>(p, hp, npw);
+      DV_TRY(check_launch("k_cg_renorm"));
+    }
+    for (int it = 0; it < max_iter; ++it) {
+      k_cg_grad<<<1, 1024, 0, st>>>(p, hp, S.hd, npw, pmin2, g, zz, sc);
+      DV_TRY(check_launch("k_cg_grad"));
+      double gn = 0.0;
+      DV_CU(cudaMemcpyAsync(&gn, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      DV_CU(cudaStreamSynchronize(st));
+      if (!(gn > tol)) break;
+      DV_TRY(cg_project<T>(S, S.Psi, nullptr, n + 1, zz, nullptr, st, pf));
+      k_cg_dir<<<1, 1024, 0, st>>>(zz, g, gp, dp, d, npw, it == 0 ? 1 : 0, sc);
+      DV_TRY(check_launch("k_cg_dir"));
+      DV_TRY(cg_project<T>(S, S.Psi, nullptr, n + 1, d, nullptr, st, pf));
+      k_cg_unit<<<1, 1024, 0, st>>>(d, dn, npw);
+      DV_TRY(check_launch("k_cg_unit"));
+      DV_TRY(hpsi_core(ctx, *v.P, v.op, precision, (const double*)dn, (double*)hdn, 1, st));
+      k_cg_step<<<1, 1024, 0, st>>>(p, hp, dn, hdn, npw, sc);
+      DV_TRY(check_launch("k_cg_step"));
+      std::swap(g, gp);
+      std::swap(zz, zp);
+      std::swap(d, dp);
+      ++run.iters;
+    }
+  }
+  ++run.sweeps;
+  return QE_OK;
+}
+
+// The whole solve: start block rotated, sweeps until every residual <= tol.
+// The mixed path sweeps with FP32 products and H while its residuals are above
+// max(tol, 1e-4) (the FP32 rounding floor), then recomputes H Psi in FP64 and
+// goes on in FP64.
+static int cg_run(qe_ctx* ctx, DvSolve& v, double tol, int max_iter, int max_sweeps, CgRun& run,
+                  cudaStream_t st) {
+  DvState& S = v.S;
+  const int nb = S.nb, npw = S.npw;
+  const size_t bytes = (size_t)nb * npw * sizeof(z);
+  DV_TRY(dv_begin(v, st));
+  int prec = v.precision;
+  DV_TRY(hpsi_core(ctx, *v.P, v.op, prec, (const double*)S.V, (double*)S.HV, nb, st));
+  DV_CU(cudaMemcpyAsync(S.Psi, S.V, bytes, cudaMemcpyDeviceToDevice, st));
+  DV_CU(cudaMemcpyAsync(S.HPsi, S.HV, bytes, cudaMemcpyDeviceToDevice, st));
+  double rmax = HUGE_VAL;
+  DV_TRY(prec == QE_FP64 ? cg_rotate<double>(ctx, v, st, &rmax) : cg_rotate<float>(ctx, v, st, &rmax));
+  while (true) {
+    if (prec != QE_FP64 && (rmax <= std::max(tol, 1e-4) || run.sweeps >= max_sweeps)) {
+      prec = QE_FP64;
+      DV_TRY(hpsi_core(ctx, *v.P, v.op, prec, (const double*)S.Psi, (double*)S.HPsi, nb, st));
+      DV_TRY(cg_rotate<double>(ctx, v, st, &rmax));
+    }
+    if (rmax <= tol || run.sweeps >= max_sweeps) break;
+    DV_TRY(prec == QE_FP64 ? cg_sweep<double>(ctx, v, prec, tol, max_iter, run, st)
+                           : cg_sweep<float>(ctx, v, prec, std::max(tol, 1e-4), max_iter, run, st));
+    DV_TRY(prec == QE_FP64 ? cg_rotate<double>(ctx, v, st, &rmax) : cg_rotate<float>(ctx, v, st, &rmax));
+  }
+  run.conv = prec == QE_FP64 && rmax <= tol;
+  (void)npw;
+  return QE_OK;
+}
+
 }  // namespace
 
 extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
@@ -1339,4 +1575,48 @@ extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs
   DV_TRY(tc_check(ctx, st));
   if (worst == QE_ENOCONV) set_error("qe_davidson_batch: some problems did not converge");
   return worst;
+}
+
+extern "C" int qe_cg(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int max_iter,
+                     int max_sweeps, double* psi_inout, double* evals, double* resid, int* iters,
+                     void* stream) {
+  clear_error();
+  if (!ctx) { set_error("qe_cg: null context"); return QE_EINVAL; }
+  DV_TRY(check_problem(prob, "qe_cg"));
+  if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_cg: bad precision"); return QE_EINVAL; }
+  if (!(tol > 0.0) || max_iter < 1 || max_sweeps < 0) {
+    set_error("qe_cg: tol must be > 0, max_iter >= 1, max_sweeps >= 0");
+    return QE_EINVAL;
+  }
+  const int nb = prob->nbnd;
+  if (iters) *iters = 0;
+  if (nb == 0) return QE_OK;
+  if (!psi_inout || !evals) { set_error("qe_cg: null psi/evals"); return QE_EINVAL; }
+  DV_CU(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  DV_TRY(ctx_begin(ctx, st));
+  DvSolve v;
+  // four scratch vectors past the bands in V and in HV
+  DV_TRY(dv_setup(ctx, prob, precision, tol, max_iter, std::max(default_max_dim(nb), nb + 4),
+                  ctx->dv_basis, ctx->dv_red, v, st, "qe_cg", false));
+  DvState& S = v.S;
+  if (S.max_dim < nb + 4) { set_error("qe_cg: %d bands need more plane waves", nb); return QE_EINVAL; }
+  const size_t bytes = (size_t)nb * S.npw * sizeof(z);
+  const cudaMemcpyKind in_kind = prob->mem == QE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind out_kind = prob->mem == QE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  DV_CU(cudaMemcpyAsync(S.V, psi_inout, bytes, in_kind, st));
+  CgRun run;
+  const int rc = cg_run(ctx, v, tol, max_iter, max_sweeps, run, st);
+  if (iters) *iters = run.iters;
+  if (rc) return rc;
+  DV_CU(cudaMemcpyAsync(psi_inout, S.Psi, bytes, out_kind, st));
+  DV_CU(cudaMemcpyAsync(evals, S.e, nb * sizeof(double), out_kind, st));
+  if (resid) DV_CU(cudaMemcpyAsync(resid, S.rn, nb * sizeof(double), out_kind, st));
+  DV_TRY(dv_final_status(v, st, "qe_cg"));
+  DV_TRY(tc_check(ctx, st));
+  if (!run.conv) {
+    set_error("qe_cg: not converged after %d sweeps", run.sweeps);
+    return QE_ENOCONV;
+  }
+  return QE_OK;
 }

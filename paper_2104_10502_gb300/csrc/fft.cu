@@ -357,6 +357,115 @@ __global__ void __launch_bounds__(BatchLB<T, STAGE>::threads, BatchLB<T, STAGE>:
   }
 }
 
+// ---- charge density: inverse transforms only, w |psi(r)|^2 summed over bands ----------
+// rho(r) = (1 / Omega) sum_nk w_nk |psi_nk(r)|^2 (Sec. 3.3, charge-density
+// generation).  After the z stage (zinv_tile), CTA (plane pz, group grp) runs
+// the inverse y and x transforms of each FFT band of its group in turn and adds
+// w |psi|^2 of its plane into per-thread registers (elements t, t + nt, ...;
+// every band in the same order), then adds the sum into acc[grp][pz][...]
+// (digit-reversed positions in all three axes, like the permuted potential).
+// One CTA owns each (group, plane) slice in a launch, so the sums are
+// deterministic; launches for more bands or k points accumulate in turn.
+// Pair mode (k = 0): FFT band b carries the real-in-r bands 2b and 2b+1 as
+// a + i b, so |a|^2 = Re^2 and |b|^2 = Im^2 with their own weights.
+constexpr int kDensRegs = 24;
+constexpr int kDensThreads = 512;
+
+template <typename T>
+__device__ void dens_plane_tile(const FftJob<T>& J, int grp, int ngrp, int pz,
+                                const double* __restrict__ w, double* __restrict__ acc,
+                                unsigned char* smem) {
+  const int n1 = J.r1.n, n2 = J.r2.n, n3 = J.r3.n, nst = J.nst, nax = J.nax;
+  const int ld = plane_ld(n1), nt = blockDim.x, n12 = n1 * n2;
+  cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
+  cx<T>* tw1 = plane + (size_t)ld * n2;
+  cx<T>* tw2 = tw1 + (size_t)n1 * tw_slots<T>();
+  int* ax = reinterpret_cast<int*>(tw2 + (size_t)n2 * tw_slots<T>());
+  {
+    const double* t1 = J.tw1 + (ct_twiddles<T>() ? 2 * n1 : 0);
+    const double* t2 = J.tw2 + (ct_twiddles<T>() ? 2 * n2 : 0);
+    for (int i = threadIdx.x; i < n1; i += nt) tw_put<T>(tw1, i, t1[2 * i], t1[2 * i + 1]);
+    for (int i = threadIdx.x; i < n2; i += nt) tw_put<T>(tw2, i, t2[2 * i], t2[2 * i + 1]);
+  }
+  for (int i = threadIdx.x; i < nax; i += nt) ax[i] = J.ax[i];
+  const int bpg = (J.nb + ngrp - 1) / ngrp;
+  const int b0 = grp * bpg, b1 = min(J.nb, b0 + bpg);
+  const bool in_regs = n12 <= kDensRegs * nt;
+  double racc[kDensRegs];
+#pragma unroll
+  for (int k = 0; k < kDensRegs; ++k) racc[k] = 0.0;
+  double* accp = acc + ((size_t)grp * n3 + pz) * n12;
+  const FastDiv fn1(n1);
+  for (int b = b0; b < b1; ++b) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < ld * n2; i += nt) plane[i] = cx_zero<T>();
+    __syncthreads();
+    const cx<T>* Wp = J.W + ((size_t)b * n3 + pz) * nst;
+    for (int s = threadIdx.x; s < nst; s += nt) plane[J.st_y[s] * ld + J.st_x[s]] = Wp[s];
+    __syncthreads();
+    fft_lines<T, +1, false, kFusePlane<T>>(plane, ld, 0, ax, nax, true, J.r2, tw2, J.pm2, J.pr2);
+    fft_lines<T, +1, false, kFusePlane<T>>(plane, 1, ld, nullptr, n2, true, J.r1, tw1, J.pm1, J.pr1);
+    // weights of this FFT band's real bands (pair) or of the band itself
+    double wa, wb = 0.0;
+    if (J.pair) {
+      wa = w[J.b0 + 2 * b];
+      if (2 * b + 1 < J.nbr) wb = w[J.b0 + 2 * b + 1];
+    } else {
+      wa = w[J.b0 + b];
+    }
+    if (in_regs) {
+#pragma unroll
+      for (int k = 0; k < kDensRegs; ++k) {
+        const int i = threadIdx.x + k * nt;
+        if (i < n12) {
+          const int y = fn1.div(i), x = i - y * n1;
+          double re, im;
+          cx_to<T>(plane[y * ld + x], re, im);
+          racc[k] += J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im);
+        }
+      }
+    } else {
+      for (int i = threadIdx.x; i < n12; i += nt) {
+        const int y = fn1.div(i), x = i - y * n1;
+        double re, im;
+        cx_to<T>(plane[y * ld + x], re, im);
+        accp[i] += J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im);
+      }
+    }
+  }
+  if (in_regs) {
+#pragma unroll
+    for (int k = 0; k < kDensRegs; ++k) {
+      const int i = threadIdx.x + k * nt;
+      if (i < n12) accp[i] += racc[k];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDensThreads) k_dens_plane(const FftJob<T> J, int ngrp,
+                                                            const double* __restrict__ w,
+                                                            double* __restrict__ acc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dens_plane_tile<T>(J, blockIdx.y, ngrp, blockIdx.x, w, acc, smem_raw);
+}
+
+// rho[perm3[pz]][perm2[py]][perm1[px]] = scale * sum_g acc[g][pz][py][px]
+__global__ void k_dens_finish(const double* __restrict__ acc, int ngrp, int n1, int n2, int n3,
+                              const int* __restrict__ p1, const int* __restrict__ p2,
+                              const int* __restrict__ p3, double scale, double* __restrict__ rho) {
+  const size_t total = (size_t)n1 * n2 * n3;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int px = (int)(i % n1);
+    const int py = (int)((i / n1) % n2);
+    const int pz = (int)(i / ((size_t)n1 * n2));
+    double s = 0.0;
+    for (int g = 0; g < ngrp; ++g) s += acc[(size_t)g * total + i];
+    rho[((size_t)p3[pz] * n2 + p2[py]) * n1 + p1[px]] = scale * s;
+  }
+}
+
 // ---- host side ---------------------------------------------------------------------
 size_t stick_bytes(const DevPlan& P, int nbc, size_t elem_bytes) {
   return (size_t)nbc * P.grid[2] * P.h.nst * elem_bytes;
@@ -536,6 +645,48 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
   return check_launch("batched FFT");
 }
 
+// Density of bands b0 .. b0+nbc-1 of psi (weights w, device, indexed by band)
+// into the group accumulators acc [ngrp][N3][N2][N1]: z stage into W, then the
+// inverse planes.  pair: k = 0 bands real in r, two per FFT.
+template <typename T>
+int launch_density(const DevPlan& P, const double* psi, const double* w, void* Wv, int b0, int nbc,
+                   int ngrp, double* acc, cudaStream_t st, Prof* pf, int pair) {
+  const FftShape sh = tuned_shape(P, sizeof(T));
+  const FftJob<T> J = make_job<T>(P, psi, nullptr, nullptr, Wv, b0, nbc, sh, pair);
+  const size_t zsm = zsm_bytes<T>(P.grid[2], J.spb);
+  const size_t psm = ((size_t)plane_ld(P.grid[0]) * P.grid[1] +
+                      (size_t)(P.grid[0] + P.grid[1]) * tw_slots<T>()) * sizeof(cx<T>) +
+                     (size_t)P.h.nax * sizeof(int);
+  if (psm > 227 * 1024) {
+    set_error("FFT plane %d x %d does not fit in shared memory at this precision", P.grid[0],
+              P.grid[1]);
+    return QE_EINVAL;
+  }
+  set_max_dynamic_smem(k_zinv<T>);
+  set_max_dynamic_smem(k_dens_plane<T>);
+  const int zt = sh.zthreads > 0 ? sh.zthreads : 256;
+  int rc;
+  {
+    ProfScope ps(pf, "k_zinv", st);
+    k_zinv<T><<<dim3(J.nsb, J.nb), zt, zsm, st>>>(J);
+    rc = check_launch("k_zinv");
+  }
+  if (rc) return rc;
+  ProfScope ps(pf, "k_dens_plane", st);
+  k_dens_plane<T><<<dim3(P.grid[2], ngrp), kDensThreads, psm, st>>>(J, ngrp, w, acc);
+  return check_launch("k_dens_plane");
+}
+
+int launch_density_finish(const DevPlan& P, const double* acc, int ngrp, double scale, double* rho,
+                          cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, "k_dens_finish", st);
+  const size_t total = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
+  k_dens_finish<<<blocks, 256, 0, st>>>(acc, ngrp, P.grid[0], P.grid[1], P.grid[2], P.perm[0],
+                                        P.perm[1], P.perm[2], scale, rho);
+  return check_launch("k_dens_finish");
+}
+
 #define QE_FFT_INSTANTIATE(T)                                                                  \
   template int launch_vperm<T>(const DevPlan&, const double*, T*, cudaStream_t, Prof*);            \
   template int launch_local_kinetic<T>(const DevPlan&, const double*, double*, const T*, void*,    \
@@ -548,7 +699,9 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
   template FftJob<T> make_job<T>(const DevPlan&, const double*, double*, const T*, void*, int,     \
                                  int, const FftShape&, int);                                       \
   template size_t zsm_bytes<T>(int, int);                                                          \
-  template size_t psm_bytes<T>(const DevPlan&);
+  template size_t psm_bytes<T>(const DevPlan&);                                                    \
+  template int launch_density<T>(const DevPlan&, const double*, const double*, void*, int, int,    \
+                                 int, double*, cudaStream_t, Prof*, int);
 QE_FFT_INSTANTIATE(double)
 QE_FFT_INSTANTIATE(float)
 QE_FFT_INSTANTIATE(ff)

@@ -155,6 +155,17 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
                                int* counters, size_t smem_z, size_t smem_p, int threads,
                                cudaStream_t st, Prof* pf);
 
+// Charge density (sum of w |psi(r)|^2): bands b0 .. b0+nbc-1 of psi with device
+// weights w[b] into the group accumulators acc [ngrp][N3][N2][N1] (digit-reversed
+// positions; zeroed by the caller before the first launch); W as for
+// launch_local_kinetic.  launch_density_finish writes rho [N3][N2][N1] (natural
+// order) = scale * the sum of the groups.
+template <typename T>
+int launch_density(const DevPlan& P, const double* psi, const double* w, void* W, int b0, int nbc,
+                   int ngrp, double* acc, cudaStream_t st, Prof* pf, int pair = 0);
+int launch_density_finish(const DevPlan& P, const double* acc, int ngrp, double scale, double* rho,
+                          cudaStream_t st, Prof* pf);
+
 // Size in bytes of the stick workspace for nbc bands.
 size_t stick_bytes(const DevPlan& P, int nbc, size_t elem_bytes);
 
