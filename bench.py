@@ -573,6 +573,7 @@ def run_gpu(args, rank, world, local_rank):
                "d2h_bytes_per_step": int(oh.nbytes), "steps": esteps}
 
     dav = run_davidson_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
+    cgd = run_cg_density_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
     srv = run_serve_bench(q, ctx, dev, local_rank) if (rank == 0 and not args.no_solvers) else None
     bat = run_batch_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
 
@@ -602,7 +603,7 @@ def run_gpu(args, rank, world, local_rank):
                           "kernels": kernels_mixed},
                 "gamma": gamma, "fp64_pipe": fp64_pipe, "fft_path": fftp,
                 "max_rel_err_vs_oracle": oracle_err,
-                "kernels": kernels, "peaks": pk_kind, "davidson": dav, "serve": srv, "batch": bat}
+                "kernels": kernels, "peaks": pk_kind, "davidson": dav, "cg_density": cgd, "serve": srv, "batch": bat}
         print(json.dumps(line), flush=True)
     ctx.close()
     return line
@@ -714,6 +715,81 @@ def run_davidson_bench(q, ctx, dev):
         if f and m32 and "solves_per_s" in f and "solves_per_s" in m32:
             out[f"{name}_mixed_rr32_speedup"] = m32["solves_per_s"] / f["solves_per_s"]
         del prob, pt0, keep
+    return out
+
+
+def run_cg_density_bench(q, ctx, dev):
+    """The band-by-band CG eigensolver on C0 (FP64 and mixed, each at the
+    loosest tolerance of DAV_LADDER whose eigenvalues are within 1e-6 Ry of the
+    dense diagonalisation, 5 timed solves) and the charge density of the 128
+    C1 bands (FP64 and mixed, bands/s over 10 calls after 3 warm-ups, the error
+    of 8 bands' density against the oracle)."""
+    import torch
+    import oracle
+    out = {}
+    c = qeinputs.config("C0")
+    nb = c["nbnd"]
+    prob, pt0, keep = device_problem(q, ctx, c["lat"], c["k"], c["ecut"], c["grid"], c["tau"],
+                                     c["widths"], nb, c["psi_seed"], dev)
+    ref = golden("c0_dense_eigs.txt")[:nb]
+
+    def solve(prec, tol):
+        pt = pt0.clone()
+        ev = torch.zeros(nb, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, it = ctx.cg(prob, pt, ev, None, precision=prec, tol=tol)
+        torch.cuda.synchronize(dev)
+        return rc, it, ev.cpu().numpy(), time.perf_counter() - t0
+
+    for tag, prec in (("fp64", q.QE_FP64), ("mixed", q.QE_MIXED)):
+        chosen = None
+        for tol in DAV_LADDER:
+            rc, it, ev, _ = solve(prec, tol)
+            if rc == q.QE_OK and np.abs(ev - ref).max() <= DAV_TARGET_RY:
+                chosen = tol
+                break
+        if chosen is None:
+            out[f"C0_{tag}"] = {"status": "no tolerance of the ladder met the target"}
+            continue
+        runs = [solve(prec, chosen) for _ in range(5)]
+        ts = [r[3] for r in runs]
+        out[f"C0_{tag}"] = {"solves_per_s": 1.0 / float(np.median(ts)), "seconds": float(np.median(ts)),
+                            "seconds_min": float(min(ts)), "seconds_max": float(max(ts)),
+                            "tol": chosen, "cg_iters": int(runs[-1][1]),
+                            "max_abs_eig_err_ry": float(max(np.abs(r[2] - ref).max() for r in runs))}
+    del prob, pt0, keep
+    c = qeinputs.config("C1")
+    nb = c["nbnd"]
+    lat, k, ecut, grid = c["lat"], c["k"], c["ecut"], c["grid"]
+    _, kin = q.gsphere(lat, k, ecut, grid)
+    psi_h = qeinputs.start_bands(kin, nb, c["psi_seed"])
+    psi_h /= np.linalg.norm(psi_h, axis=1)[:, None]
+    psi = torch.from_numpy(psi_h.view(np.float64).reshape(nb, len(kin), 2).copy()).to(dev)
+    w = np.full(nb, 2.0)
+    rho = torch.empty((grid[2], grid[1], grid[0]), dtype=torch.float64, device=dev)
+    want8 = oracle.density(lat, ecut, grid, [k], [psi_h[:8]], [w[:8]])
+    dens = {"workload": "C1: 128 bands, grid 96^3, weights 2", "bands": nb}
+    stream = torch.cuda.current_stream(dev)
+    for tag, prec in (("fp64", q.QE_FP64), ("mixed", q.QE_MIXED)):
+        for _ in range(3):
+            ctx.density(lat, ecut, grid, np.array([k]), [psi], [w], rho, prec)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 10
+        for _ in range(reps):
+            ctx.density(lat, ecut, grid, np.array([k]), [psi], [w], rho, prec)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        r8 = torch.empty_like(rho)
+        ctx.density(lat, ecut, grid, np.array([k]), [psi[:8].contiguous()], [w[:8]], r8, prec)
+        torch.cuda.synchronize(dev)
+        err = float(np.abs(r8.cpu().numpy() - want8).max() / np.abs(want8).max())
+        dens[tag] = {"bands_per_s": nb / (ms / 1e3), "ms_per_call": ms,
+                     "max_rel_err_vs_oracle_8_bands": err}
+    out["density"] = dens
     return out
 
 

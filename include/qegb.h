@@ -77,6 +77,16 @@ enum { QE_FFT_FP64PIPE = 0x400 };
  * Rayleigh-Ritz step in FP64 (on reduced matrices from its TF32x3 products).
  * Ignored with QE_FP64. */
 enum { QE_RR_FP32 = 0x800 };
+/* QE_SAME_OPERATOR (qe_hpsi, device memory): the operator -- vloc_r, beta and
+ * dmat -- is the same (same pointers, same contents, same cell, k, cut-off
+ * and grid) as in this context's previous qe_hpsi call at the same precision,
+ * so the forms prepared from it then (the potential in the FFT's order, the
+ * tensor-core slices or packs of beta) are used as they are instead of being
+ * rebuilt; the caller promises that nothing changed in between (results are
+ * undefined otherwise).  Quantum ESPRESSO likewise builds these once per k
+ * point and applies H many times.  Without a matching previous call the flag
+ * has no effect; other entry points on the context in between may clear it. */
+enum { QE_SAME_OPERATOR = 0x1000 };
 enum { QE_HOST = 0, QE_DEVICE = 1 };  /* where the caller's arrays live */
 
 typedef struct qe_ctx qe_ctx;

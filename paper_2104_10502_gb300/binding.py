@@ -28,6 +28,9 @@ QE_FFT_FP64PIPE = 0x400
 # or-ed into QE_MIXED for davidson: reduced eigenproblems of the mixed iterations in FP32
 # (default: FP64 Rayleigh-Ritz)
 QE_RR_FP32 = 0x800
+# or-ed into precision for hpsi (device arrays): the operator is unchanged since the
+# previous hpsi call on the context; its prepared forms are reused
+QE_SAME_OPERATOR = 0x1000
 QE_HOST, QE_DEVICE = 0, 1
 
 SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",

@@ -108,6 +108,7 @@ int ctx_trim(qe_ctx* ctx) {
   ctx_batch_release(ctx);
   ctx->tc_beta_tag = 0;
   ctx->oz_beta_tag = 0;
+  ctx->last_op = qe_ctx::LastOp{};
   for (auto& p : ctx->plans)
     if (p->block) cudaFreeAsync(p->block, ctx->cur);
   ctx->plans.clear();
@@ -141,6 +142,9 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
   std::vector<int> perm[3];
   std::vector<double> tw[3];
   for (int c = 0; c < 3; ++c) { perm[c] = digit_reversal(P->rad[c]); tw[c] = twiddles(grid[c]); }
+  // square planes with the register-resident transform keep x and y in its order
+  P->sq = sq_plane_size(grid);
+  if (P->sq) perm[0] = perm[1] = sq_order(P->sq);
   // one allocation: doubles first, then ints
   size_t nd = h.npw;
   for (int c = 0; c < 3; ++c) nd += tw[c].size();
@@ -256,12 +260,16 @@ int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView
 // projections are taken real.
 template <typename T>
 static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const double* psi,
-                       double* hpsi, int nb, cudaStream_t st, bool pair) {
+                       double* hpsi, int nb, cudaStream_t st, bool pair, bool vp_ready = false) {
   const int npw = P.h.npw;
   pair = pair && P.h.gamma;
   const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
-  QE_TRY(ctx->vp.ensure(ngrid * sizeof(T)));
-  QE_TRY(launch_vperm<T>(P, op.vloc, (T*)ctx->vp.p, st, &ctx->prof));
+  if (!vp_ready || !ctx->vp.p || ctx->vp.bytes < ngrid * sizeof(T)) {
+    // the permuted potential no longer belongs to the last qe_hpsi operator
+    ctx->last_op = qe_ctx::LastOp{};
+    QE_TRY(ctx->vp.ensure(ngrid * sizeof(T)));
+    QE_TRY(launch_vperm<T>(P, op.vloc, (T*)ctx->vp.p, st, &ctx->prof));
+  }
   const size_t per_band = stick_bytes(P, 1, 2 * sizeof(T));
   const int per_fft = pair ? 2 : 1;   // bands per FFT
   int nfb = (int)std::max<size_t>(1, ctx->stick_budget / std::max<size_t>(per_band, 1));
@@ -338,12 +346,12 @@ int tc_check(qe_ctx* ctx, cudaStream_t st) {
 }
 
 int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, const double* psi,
-              double* hpsi, int nb, cudaStream_t st, bool pair, bool fp64_pipe) {
+              double* hpsi, int nb, cudaStream_t st, bool pair, bool fp64_pipe, bool vp_ready) {
   if (nb == 0) return QE_OK;
   if (precision == QE_FP64)
-    return fp64_pipe ? hpsi_device<double>(ctx, P, op, psi, hpsi, nb, st, pair)
-                     : hpsi_device<FftF64>(ctx, P, op, psi, hpsi, nb, st, pair);
-  return hpsi_device<float>(ctx, P, op, psi, hpsi, nb, st, pair);
+    return fp64_pipe ? hpsi_device<double>(ctx, P, op, psi, hpsi, nb, st, pair, vp_ready)
+                     : hpsi_device<FftF64>(ctx, P, op, psi, hpsi, nb, st, pair, vp_ready);
+  return hpsi_device<float>(ctx, P, op, psi, hpsi, nb, st, pair, vp_ready);
 }
 
 }  // namespace qe
@@ -484,7 +492,8 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
   QE_TRY(check_problem(prob, "qe_hpsi"));
   const bool pair = (precision & QE_GAMMA) != 0;
   const bool fp64_pipe = (precision & QE_FFT_FP64PIPE) != 0;
-  precision &= ~(QE_GAMMA | QE_FFT_FP64PIPE);
+  const bool same_op = (precision & QE_SAME_OPERATOR) != 0;
+  precision &= ~(QE_GAMMA | QE_FFT_FP64PIPE | QE_SAME_OPERATOR);
   if (precision != QE_FP64 && precision != QE_MIXED) { set_error("qe_hpsi: bad precision"); return QE_EINVAL; }
   if (prob->nbnd > 0 && (!psi || !hpsi)) { set_error("qe_hpsi: null psi/hpsi"); return QE_EINVAL; }
   QE_CU(cudaSetDevice(ctx->device));
@@ -506,7 +515,22 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
   // host operator: V on st, beta and D on the side stream while the FFTs run
   OpView op;
   QE_TRY(resolve_operator(ctx, prob, *P, op, st, prob->mem == QE_HOST && nb > 0));
-  const int rc_h = hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st, pair, fp64_pipe);
+  // QE_SAME_OPERATOR: a device operator identical to the previous call's keeps
+  // its prepared forms (the tag selects the kept slices or packs of beta)
+  const int fft_type = precision == QE_MIXED ? 0 : (fp64_pipe ? 2 : 1);
+  const qe_ctx::LastOp lo = ctx->last_op;
+  bool vp_ready = false;
+  if (prob->mem == QE_DEVICE && same_op && nb > 0 && lo.tag != 0 && lo.plan == P &&
+      lo.vloc == op.vloc && lo.beta == op.beta && lo.dmat == op.dmat && lo.nproj == op.nproj &&
+      lo.fft_type == fft_type) {
+    op.tag = lo.tag;
+    vp_ready = true;
+  }
+  const int rc_h = hpsi_core(ctx, *P, op, precision, dpsi, dhpsi, nb, st, pair, fp64_pipe, vp_ready);
+  if (rc_h == QE_OK && prob->mem == QE_DEVICE && nb > 0)
+    ctx->last_op = {P, op.vloc, op.beta, op.dmat, op.nproj, fft_type, op.tag};
+  else
+    ctx->last_op = qe_ctx::LastOp{};
   if (op.ready) QE_CU(cudaStreamWaitEvent(st, op.ready, 0));   // join the copy stream
   if (rc_h) return rc_h;
   if (prob->mem == QE_HOST) {

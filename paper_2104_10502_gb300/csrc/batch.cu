@@ -350,6 +350,7 @@ int qe_autotune(qe_ctx* ctx, const qe_problem* prob, int precision, void* stream
   BT_TRY(ctx->h_hpsi.ensure(nel * sizeof(double)));
   BT_CU(cudaMemsetAsync(ctx->h_psi.p, 0, nel * sizeof(double), st));
   const size_t ngrid = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
+  ctx->last_op = qe_ctx::LastOp{};   // the permuted potential is overwritten below
   BT_TRY(ctx->vp.ensure(ngrid * el));
   BT_TRY(ctx->sticks.ensure(stick_bytes(*P, nb, 2 * el)));
   cudaEvent_t e0, e1;

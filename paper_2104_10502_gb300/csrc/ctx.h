@@ -32,6 +32,14 @@ struct qe_ctx {
   // the packed beta in tc_beta belongs to the operator with this tag (0: none);
   // every API call that takes an operator gets a fresh tag
   unsigned long long tc_beta_tag = 0, op_tag = 0;
+  // the operator of the last device-memory qe_hpsi (QE_SAME_OPERATOR reuses
+  // its prepared forms: permuted potential, tensor-core slices or packs of beta)
+  struct LastOp {
+    const void* plan = nullptr;
+    const double *vloc = nullptr, *beta = nullptr, *dmat = nullptr;
+    int nproj = 0, fft_type = -1;
+    unsigned long long tag = 0;
+  } last_op;
   // copy stream for the operator of a host-memory qe_hpsi (beta and D go in
   // while the FFTs run) and its two events (created on first use)
   cudaStream_t side = nullptr;
@@ -85,8 +93,11 @@ int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView
 // real in r, psi(-G) = conj psi(G); two share each FFT and the projections are
 // taken real, so the result is H applied to that part of each band.  fp64_pipe
 // (QE_FP64): the FFT in double on the FP64 pipe instead of in float-float pairs.
+// vp_ready: the context's permuted potential already holds op.vloc for this
+// plan and element type (QE_SAME_OPERATOR).
 int hpsi_core(qe_ctx* ctx, const DevPlan& P, const OpView& op, int precision, const double* psi,
-              double* hpsi, int nb, cudaStream_t st, bool pair = false, bool fp64_pipe = false);
+              double* hpsi, int nb, cudaStream_t st, bool pair = false, bool fp64_pipe = false,
+              bool vp_ready = false);
 // Status word of the tensor-core kernels since the last check (synchronises on
 // `st`); QE_ETIMEOUT with a message if a bounded wait ran out, then resets it.
 int tc_check(qe_ctx* ctx, cudaStream_t st);

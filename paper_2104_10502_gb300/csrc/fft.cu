@@ -27,6 +27,7 @@
 
 #include "fft_device.cuh"
 #include "plan.h"
+#include "plane2.cuh"
 
 namespace qe {
 
@@ -158,8 +159,142 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// ---- square planes with the register-resident two-pass transform (plane2.cuh) ----------
+// Shared memory: the plane (row stride N | 1), the twiddle table of length N,
+// the active-column table.
+template <typename T, int N>
+__device__ __forceinline__ void sq_setup(const FftJob<T>& J, cx<T>* plane, cx<T>* tab, int* ax) {
+  constexpr int ld = N | 1;
+  for (int i = threadIdx.x; i < ld * N; i += blockDim.x) plane[i] = cx_zero<T>();
+  for (int t = threadIdx.x; t < N; t += blockDim.x) sq_tw_put<T>(tab, t, J.tw1[2 * t], J.tw1[2 * t + 1]);
+  for (int i = threadIdx.x; i < J.nax; i += blockDim.x) ax[i] = J.ax[i];
+}
+
+// Inverse y transforms of the active columns (sticks scattered beforehand),
+// then the inverse x pass 1 of every row; ends with a barrier.
+template <typename T, int N>
+__device__ __forceinline__ void sq_inverse_yx1(const FftJob<T>& J, cx<T>* plane, const cx<T>* tab,
+                                               const int* ax) {
+  constexpr int A = SqSplit<N>::A, B = SqSplit<N>::B, ld = N | 1;
+  const int nax = J.nax, nt = blockDim.x;
+  const FastDiv fax(nax), fn(N);
+  for (int it = threadIdx.x; it < nax * B; it += nt) {
+    const int n2 = fax.div(it), l = it - n2 * nax;
+    if (J.pr2) sq_inv1<T, N, true>(plane + ax[l], ld, n2, tab);
+    else sq_inv1<T, N, false>(plane + ax[l], ld, n2, tab);
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nax * A; it += nt) {
+    const int k1 = fax.div(it), l = it - k1 * nax;
+    cx<T>* p = plane + ax[l];
+    cx<T> o[B];
+    sq_inv2_regs<T, N>(p, ld, k1, tab, o);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) p[(B * k1 + k2) * ld] = o[k2];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < N * B; it += nt) {
+    const int n2 = fn.div(it), y = it - n2 * N;
+    if (J.pr1) sq_inv1<T, N, true>(plane + y * ld, 1, n2, tab);
+    else sq_inv1<T, N, false>(plane + y * ld, 1, n2, tab);
+  }
+  __syncthreads();
+}
+
+template <typename T, int N>
+__device__ void plane_tile_sq(const FftJob<T>& J, int b, int pz, unsigned char* smem) {
+  constexpr int A = SqSplit<N>::A, B = SqSplit<N>::B, ld = N | 1;
+  const int n3 = J.r3.n, nst = J.nst, nax = J.nax, nt = blockDim.x;
+  cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
+  cx<T>* tab = plane + ld * N;
+  int* ax = reinterpret_cast<int*>(tab + N * sq_tw_slots<T>());
+  sq_setup<T, N>(J, plane, tab, ax);
+  __syncthreads();
+  cx<T>* Wp = J.W + ((size_t)b * n3 + pz) * nst;
+  for (int s0 = threadIdx.x; s0 < nst; s0 += 4 * nt) {
+    int off[4];
+    cx<T> val[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = s0 + u * nt;
+      if (s < nst) { off[u] = J.st_y[s] * ld + J.st_x[s]; val[u] = Wp[s]; }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (s0 + u * nt < nst) plane[off[u]] = val[u];
+  }
+  __syncthreads();
+  sq_inverse_yx1<T, N>(J, plane, tab, ax);
+  // x: inverse pass 2, times V, forward pass 1 on the same B values of a row
+  const FastDiv fax(nax), fn(N);
+  const T* vz = J.vp + (size_t)pz * N * N;
+  for (int it = threadIdx.x; it < N * A; it += nt) {
+    const int k1 = fn.div(it), y = it - k1 * N;
+    cx<T>* p = plane + y * ld;
+    const T* vr = vz + (size_t)y * N + B * k1;
+    T vv[B];
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) vv[k2] = vr[k2];
+    cx<T> o[B], f[B];
+    sq_inv2_regs<T, N>(p, 1, k1, tab, o);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) o[k2] = cscale(o[k2], vv[k2]);
+    sq_fwd1_regs<T, N>(o, k1, tab, f);
+#pragma unroll
+    for (int m2 = 0; m2 < B; ++m2) p[B * k1 + m2] = f[m2];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < N * B; it += nt) {
+    const int m2 = fn.div(it), y = it - m2 * N;
+    if (J.pr1) sq_fwd2<T, N, true>(plane + y * ld, 1, m2, tab);
+    else sq_fwd2<T, N, false>(plane + y * ld, 1, m2, tab);
+  }
+  __syncthreads();
+  // y forward on the active columns
+  for (int it = threadIdx.x; it < nax * A; it += nt) {
+    const int k1 = fax.div(it), l = it - k1 * nax;
+    cx<T>* p = plane + ax[l];
+    cx<T> in[B], f[B];
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) in[k2] = p[(B * k1 + k2) * ld];
+    sq_fwd1_regs<T, N>(in, k1, tab, f);
+#pragma unroll
+    for (int m2 = 0; m2 < B; ++m2) p[(B * k1 + m2) * ld] = f[m2];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < nax * B; it += nt) {
+    const int m2 = fax.div(it), l = it - m2 * nax;
+    if (J.pr2) sq_fwd2<T, N, true>(plane + ax[l], ld, m2, tab);
+    else sq_fwd2<T, N, false>(plane + ax[l], ld, m2, tab);
+  }
+  __syncthreads();
+  for (int s0 = threadIdx.x; s0 < nst; s0 += 4 * nt) {
+    int off[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int s = s0 + u * nt;
+      if (s < nst) off[u] = J.st_y[s] * ld + J.st_x[s];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (s0 + u * nt < nst) Wp[s0 + u * nt] = plane[off[u]];
+  }
+}
+
+// Sizes with a register-resident plane transform (plane2.cuh SqSplit).
+#define QE_SQ_DISPATCH(CALL)                                  \
+  switch (J.sq) {                                             \
+    case 96: CALL(96); return;                                \
+    case 48: CALL(48); return;                                \
+    case 32: CALL(32); return;                                \
+    default: break;                                           \
+  }
+
 template <typename T>
 __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* smem) {
+#define QE_SQ_PLANE(n) plane_tile_sq<T, n>(J, b, pz, smem)
+  QE_SQ_DISPATCH(QE_SQ_PLANE)
+#undef QE_SQ_PLANE
   const int n1 = J.r1.n, n2 = J.r2.n, n3 = J.r3.n, nst = J.nst, nax = J.nax;
   const int ld = plane_ld(n1), nt = blockDim.x;
   cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
@@ -371,10 +506,88 @@ __global__ void __launch_bounds__(BatchLB<T, STAGE>::threads, BatchLB<T, STAGE>:
 constexpr int kDensRegs = 24;
 constexpr int kDensThreads = 512;
 
+// The density tile on a square plane with the register-resident transform:
+// the same band loop and sums as dens_plane_tile, the inverse transforms of
+// plane2.cuh (its x and y order is the plan's).
+template <typename T, int N>
+__device__ void dens_plane_tile_sq(const FftJob<T>& J, int grp, int ngrp, int pz,
+                                   const double* __restrict__ w, double* __restrict__ acc,
+                                   unsigned char* smem) {
+  constexpr int A = SqSplit<N>::A, B = SqSplit<N>::B, ld = N | 1, n12 = N * N;
+  const int n3 = J.r3.n, nst = J.nst, nt = blockDim.x;
+  cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
+  cx<T>* tab = plane + ld * N;
+  int* ax = reinterpret_cast<int*>(tab + N * sq_tw_slots<T>());
+  sq_setup<T, N>(J, plane, tab, ax);
+  const int bpg = (J.nb + ngrp - 1) / ngrp;
+  const int b0 = grp * bpg, b1 = min(J.nb, b0 + bpg);
+  const bool in_regs = n12 <= kDensRegs * nt;
+  double racc[kDensRegs];
+#pragma unroll
+  for (int k = 0; k < kDensRegs; ++k) racc[k] = 0.0;
+  double* accp = acc + ((size_t)grp * n3 + pz) * n12;
+  const FastDiv fn(N);
+  for (int b = b0; b < b1; ++b) {
+    __syncthreads();
+    if (b > b0)
+      for (int i = threadIdx.x; i < ld * N; i += nt) plane[i] = cx_zero<T>();
+    __syncthreads();
+    const cx<T>* Wp = J.W + ((size_t)b * n3 + pz) * nst;
+    for (int s = threadIdx.x; s < nst; s += nt) plane[J.st_y[s] * ld + J.st_x[s]] = Wp[s];
+    __syncthreads();
+    sq_inverse_yx1<T, N>(J, plane, tab, ax);
+    for (int it = threadIdx.x; it < N * A; it += nt) {
+      const int k1 = fn.div(it), y = it - k1 * N;
+      cx<T>* p = plane + y * ld;
+      cx<T> o[B];
+      sq_inv2_regs<T, N>(p, 1, k1, tab, o);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) p[B * k1 + k2] = o[k2];
+    }
+    __syncthreads();
+    double wa, wb = 0.0;
+    if (J.pair) {
+      wa = w[J.b0 + 2 * b];
+      if (2 * b + 1 < J.nbr) wb = w[J.b0 + 2 * b + 1];
+    } else {
+      wa = w[J.b0 + b];
+    }
+    if (in_regs) {
+#pragma unroll
+      for (int k = 0; k < kDensRegs; ++k) {
+        const int i = threadIdx.x + k * nt;
+        if (i < n12) {
+          const int y = fn.div(i), x = i - y * N;
+          double re, im;
+          cx_to<T>(plane[y * ld + x], re, im);
+          racc[k] += J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im);
+        }
+      }
+    } else {
+      for (int i = threadIdx.x; i < n12; i += nt) {
+        const int y = fn.div(i), x = i - y * N;
+        double re, im;
+        cx_to<T>(plane[y * ld + x], re, im);
+        accp[i] += J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im);
+      }
+    }
+  }
+  if (in_regs) {
+#pragma unroll
+    for (int k = 0; k < kDensRegs; ++k) {
+      const int i = threadIdx.x + k * nt;
+      if (i < n12) accp[i] += racc[k];
+    }
+  }
+}
+
 template <typename T>
 __device__ void dens_plane_tile(const FftJob<T>& J, int grp, int ngrp, int pz,
                                 const double* __restrict__ w, double* __restrict__ acc,
                                 unsigned char* smem) {
+#define QE_SQ_DENS(n) dens_plane_tile_sq<T, n>(J, grp, ngrp, pz, w, acc, smem)
+  QE_SQ_DISPATCH(QE_SQ_DENS)
+#undef QE_SQ_DENS
   const int n1 = J.r1.n, n2 = J.r2.n, n3 = J.r3.n, nst = J.nst, nax = J.nax;
   const int ld = plane_ld(n1), nt = blockDim.x, n12 = n1 * n2;
   cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
@@ -467,6 +680,27 @@ __global__ void k_dens_finish(const double* __restrict__ acc, int ngrp, int n1, 
 }
 
 // ---- host side ---------------------------------------------------------------------
+int sq_plane_size(const int grid[3]) {
+  if (grid[0] != grid[1]) return 0;
+  switch (grid[0]) {
+    case 96: case 48: case 32: return grid[0];
+    default: return 0;
+  }
+}
+
+std::vector<int> sq_order(int n) {
+  int A = 0, B = 0;
+  switch (n) {
+    case 96: A = SqSplit<96>::A; B = SqSplit<96>::B; break;
+    case 48: A = SqSplit<48>::A; B = SqSplit<48>::B; break;
+    case 32: A = SqSplit<32>::A; B = SqSplit<32>::B; break;
+    default: return {};
+  }
+  std::vector<int> perm(n);
+  for (int p = 0; p < n; ++p) perm[p] = p / B + A * (p % B);   // position B k1 + k2 holds k1 + A k2
+  return perm;
+}
+
 size_t stick_bytes(const DevPlan& P, int nbc, size_t elem_bytes) {
   return (size_t)nbc * P.grid[2] * P.h.nst * elem_bytes;
 }
@@ -542,6 +776,7 @@ FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* v
   J.nsb = (J.nst + J.spb - 1) / J.spb;
   J.inv_n = 1.0 / ((double)P.grid[0] * P.grid[1] * P.grid[2]);
   J.stage_v = plane_stages_v<T>(P) ? 1 : 0;
+  J.sq = P.sq;
   return J;
 }
 

@@ -86,6 +86,8 @@ static int hpsi_noalloc_impl(const qe_problem* pr, const double* psi, double* hp
     perm[c] = digit_reversal(P.rad[c]);
     tw[c] = twiddles(P.grid[c]);
   }
+  P.sq = sq_plane_size(P.grid);
+  if (P.sq) perm[0] = perm[1] = sq_order(P.sq);
   const int nb = pr->nbnd, np = pr->nproj, npw = h.npw;
   const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
   // layout: plan image | permuted V | projections x2 | stick buffer | split-K partials

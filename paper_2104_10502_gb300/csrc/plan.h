@@ -19,9 +19,15 @@ using FftF64 = ff;
 template <typename T>
 using GemmT = std::conditional_t<std::is_same<T, float>::value, float, double>;
 
+// Plane size with a register-resident two-pass transform (plane2.cuh), or 0.
+int sq_plane_size(const int grid[3]);
+// perm[p] = natural index held at line position p of that transform of length n.
+std::vector<int> sq_order(int n);
+
 struct DevPlan {
   double lat[9], k[3], ecut;
   int grid[3];
+  int sq = 0;   // sq_plane_size(grid): x and y perms are sq_order(n) when non-zero
   PlanHost h;
   Radix rad[3];
   // device arrays (one allocation)
@@ -121,6 +127,10 @@ struct FftJob {
   // job's nbr bands as psi_2b + i psi_2b+1 (k = 0; sticks in mirror pairs);
   // self_st: the self-mirror stick
   int pair, nbr, self_st;
+  // sq: N when the planes are N x N with a register-resident two-pass plane
+  // transform (plane2.cuh; x and y in its order, the plan's perm[0], perm[1]),
+  // 0 for the stage-by-stage transform
+  int sq;
   double inv_n;
 };
 

@@ -223,3 +223,32 @@ def test_hpsi_rejects_bad_grids(q, ctx):
     with pytest.raises(q.QEError) as e:
         ctx.hpsi(prob, pt, torch.empty_like(pt))
     assert e.value.code == q.QE_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_same_operator_flag_reuses_and_invalidates(q, ctx, prec):
+    """QE_SAME_OPERATOR reuses the prepared operator of the previous call (bit
+    for bit the same result); another operator prepared in between (a second
+    cell, a Davidson solve) makes the flag fall back to rebuilding it."""
+    c0 = _cell("C0")
+    sm = _cell("SMALL")
+    p0, keep0, kin0 = _gpu_problem(q, ctx, c0, 6)
+    p1, keep1, kin1 = _gpu_problem(q, ctx, sm, 5)
+    x0 = _to_t(qeinputs.random_vectors(6, len(kin0), seed=31))
+    x1 = _to_t(qeinputs.random_vectors(5, len(kin1), seed=32))
+    ref0, ref1 = torch.empty_like(x0), torch.empty_like(x1)
+    ctx.hpsi(p0, x0, ref0, prec)
+    ctx.hpsi(p1, x1, ref1, prec)
+    out = torch.empty_like(x1)
+    ctx.hpsi(p1, x1, out, prec | q.QE_SAME_OPERATOR)          # same as the previous call
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref1)
+    out0 = torch.empty_like(x0)
+    ctx.hpsi(p0, x0, out0, prec | q.QE_SAME_OPERATOR)         # another operator: rebuilt
+    torch.cuda.synchronize()
+    assert torch.equal(out0, ref0)
+    ev = torch.zeros(5, dtype=torch.float64, device="cuda")
+    ctx.davidson(p1, x1.clone(), ev, None, precision=prec, tol=1e-5)
+    ctx.hpsi(p0, x0, out0, prec | q.QE_SAME_OPERATOR)         # after a solve in between
+    torch.cuda.synchronize()
+    assert torch.equal(out0, ref0)
