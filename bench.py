@@ -574,7 +574,8 @@ def run_gpu(args, rank, world, local_rank):
 
     dav = run_davidson_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
     cgd = run_cg_density_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
-    srv = run_serve_bench(q, ctx, dev, local_rank) if (rank == 0 and not args.no_solvers) else None
+    srv = (run_serve_bench(q, ctx, dev, local_rank, args.serve_requests)
+           if (rank == 0 and not args.no_solvers and args.serve_requests > 0) else None)
     bat = run_batch_bench(q, ctx, dev) if (rank == 0 and not args.no_solvers) else None
 
     line = None
@@ -886,67 +887,96 @@ def profile_davidson(name):
                       "seconds": times[-1]}))
 
 
+SERVE_RATES = (0.25, 0.5, 1.0, 2.0, 4.0, 8.0)
+SERVE_TOL = 1e-3        # the loosest residual of DAV_LADDER that meets 1e-6 Ry on C0 and C2
+
+
 def serve_requests(q, ctx, n, seed, dev):
-    """Requests drawn like the serving workload, shrunk so that a stream ends in
-    seconds: cubic a in U[10,14] bohr, ecut in U[20,30] Ry, nb in U{8..32},
-    2..16 random atoms, one projector width (4 projectors/atom), minimum
-    2,3,5-smooth grid."""
+    """The serving workload: cubic a ~ U[10,24] bohr, ecut ~
+    U[20,50] Ry, nb ~ U{8..256} (at most npw / 2), atoms ~ U{2..96} placed at
+    random (at most a^3/24, so that rejection sampling at 2.5 bohr stays quick
+    in the small cells), the C0 potentials (Gaussian V_loc, 4 projectors per
+    atom of width 1 bohr), k = 0, grid the smallest 2,3,5-smooth N >= 2 floor(2
+    sqrt(ecut) a / 2 pi) + 1; draws from default_rng(seed), start bands seeded by
+    index.  Host arrays (the server copies them at submit)."""
     rng = np.random.default_rng(seed)
     reqs = []
     for i in range(n):
-        a = float(rng.uniform(10.0, 14.0))
-        ecut = float(rng.uniform(20.0, 30.0))
-        nb = int(rng.integers(8, 33))
-        natom = int(rng.integers(2, 17))
+        a = float(rng.uniform(10.0, 24.0))
+        ecut = float(rng.uniform(20.0, 50.0))
+        nb = int(rng.integers(8, 257))
+        natom = int(rng.integers(2, 97))
+        natom = max(2, min(natom, int(a ** 3 / 24)))
         lat = qeinputs.cubic(a)
-        tau = qeinputs.random_atoms(lat, natom, 2.0, seed=1000 + seed * 100 + i)
+        tau = qeinputs.random_atoms(lat, natom, 2.5, seed=1000 + seed * 1000 + i)
         g = min_grid(a, ecut)
         grid = (g, g, g)
+        _, kin = q.gsphere(lat, np.zeros(3), ecut, grid)
+        nb = max(1, min(nb, len(kin) // 2))
         prob_d, pt, keep = device_problem(q, ctx, lat, np.zeros(3), ecut, grid, tau, (1.0,), nb, i, dev)
         v, beta, d = keep
         vh, bh, dh = v.cpu().numpy().copy(), beta.cpu().numpy().copy(), d.cpu().numpy().copy()
-        ph = pt.cpu().numpy().copy()
-        psi0 = ph[..., 0] + 1j * ph[..., 1]
+        ph = pt.cpu().numpy()
+        psi0 = np.ascontiguousarray(ph[..., 0] + 1j * ph[..., 1])
         prob = q.problem(lat, np.zeros(3), ecut, grid, vh, bh, dh, nb)
-        reqs.append((prob, psi0, (vh, bh, dh)))
+        reqs.append((prob, psi0, (vh, bh, dh), dict(a=a, ecut=ecut, nb=nb, natom=natom, npw=len(kin),
+                                                    grid=g)))
+        del prob_d, pt, keep
     return reqs
 
 
-def run_serve_bench(q, ctx, dev, device_index):
-    """Serving: the same request list as a burst (capacity) and as a Poisson
-    stream at 70 % of capacity; latency = submit -> completion."""
-    out = {}
-    reqs = serve_requests(q, ctx, 24, 6, dev)
-    for prec, tol, tag in ((q.QE_FP64, 1e-8, "fp64"), (q.QE_MIXED, 1e-5, "mixed")):
-        with q.Server(device=device_index, budget_bytes=32 << 30, max_slots=4) as s:
+def run_serve_bench(q, ctx, dev, device_index, nreq):
+    """Serving (continuous batching, lockstep rounds) on the C4 stream, FP64 and
+    mixed at the residual tolerance that meets 1e-6 Ry: the capacity (all
+    requests submitted at once), then Poisson arrivals at SERVE_RATES x capacity,
+    each rate with all `nreq` requests in a shuffled order; latency = submit ->
+    completion as the server measures it; p50 / p99 per rate."""
+    import torch
+    reqs = serve_requests(q, ctx, nreq, 6, dev)
+    torch.cuda.synchronize(dev)
+    meta = [r[3] for r in reqs]
+    out = {"workload": "C4: cubic a~U[10,24] bohr, ecut~U[20,50] Ry, nb~U{8..256}, 2-96 atoms "
+                       "(<= a^3/24), 4 projectors/atom, k = 0; Poisson arrivals at "
+                       f"{list(SERVE_RATES)} x capacity",
+           "requests_per_rate": nreq, "tol": SERVE_TOL, "budget_gib": 96, "max_slots": 32,
+           "npw_range": [min(m["npw"] for m in meta), max(m["npw"] for m in meta)],
+           "nb_range": [min(m["nb"] for m in meta), max(m["nb"] for m in meta)]}
+    rng = np.random.default_rng(7)
+    for prec, tag in ((q.QE_FP64, "fp64"), (q.QE_MIXED, "mixed")):
+        with q.Server(device=device_index, budget_bytes=96 << 30, max_slots=32,
+                      max_queue=4 * nreq) as s:
             t0 = time.perf_counter()
-            ts = [s.submit(p, x, precision=prec, tol=tol) for p, x, _ in reqs]
+            ts = [s.submit(p, x, precision=prec, tol=SERVE_TOL, max_iter=300) for p, x, _, _ in reqs]
             res = [s.poll(t) for t in ts]
             burst = time.perf_counter() - t0
         cap = len(reqs) / burst
-        rate = 0.7 * cap
-        rng = np.random.default_rng(7)
-        gaps = rng.exponential(1.0 / rate, len(reqs))
-        lat = []
-        with q.Server(device=device_index, budget_bytes=32 << 30, max_slots=4) as s:
-            t0 = time.perf_counter()
-            tickets = []
-            t_next = 0.0
-            for (p, x, _), gap in zip(reqs, gaps):
-                t_next += gap
-                while time.perf_counter() - t0 < t_next:
-                    time.sleep(0.0005)
-                tickets.append(s.submit(p, x, precision=prec, tol=tol))
-            res2 = [s.poll(t) for t in tickets]
-            wall = time.perf_counter() - t0
-        lat = np.array([r["latency_s"] for r in res2]) * 1e3
-        ok = sum(r["status"] == q.QE_OK for r in res2)
-        out[tag] = {"burst_solves_per_s": cap, "stream_rate_per_s": rate,
-                    "stream_solves_per_s": len(reqs) / wall, "p50_ms": float(np.percentile(lat, 50)),
-                    "p99_ms": float(np.percentile(lat, 99)), "converged": ok, "requests": len(reqs),
-                    "slots": 4}
-    out["workload"] = ("24 requests: cubic a~U[10,14] bohr, ecut~U[20,30] Ry, nb~U{8..32}, "
-                       "2-16 atoms, 4 projectors/atom; Poisson arrivals at 0.7 x burst capacity")
+        block = {"capacity_solves_per_s": cap, "burst_seconds": burst,
+                 "converged": int(sum(r["status"] == q.QE_OK for r in res)), "rates": []}
+        for f in SERVE_RATES:
+            lam = f * cap
+            order = rng.permutation(len(reqs))
+            gaps = rng.exponential(1.0 / lam, len(reqs))
+            with q.Server(device=device_index, budget_bytes=96 << 30, max_slots=32,
+                          max_queue=4 * nreq) as s:
+                tickets = []
+                t0 = time.perf_counter()
+                t_next = 0.0
+                for i, gap in zip(order, gaps):
+                    t_next += gap
+                    while time.perf_counter() - t0 < t_next:
+                        time.sleep(0.0002)
+                    p, x, _, _ = reqs[i]
+                    tickets.append(s.submit(p, x, precision=prec, tol=SERVE_TOL, max_iter=300))
+                t_sub = time.perf_counter() - t0
+                rr = [s.poll(t) for t in tickets]
+                wall = time.perf_counter() - t0
+            lat = np.array([r["latency_s"] for r in rr]) * 1e3
+            block["rates"].append({
+                "rate_factor": f, "offered_per_s": lam, "achieved_arrivals_per_s": len(reqs) / t_sub,
+                "solves_per_s": len(reqs) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "samples": len(rr),
+                "converged": int(sum(r["status"] == q.QE_OK for r in rr))})
+        out[tag] = block
     return out
 
 
@@ -975,6 +1005,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solvers", action="store_true",
                     help="skip the Davidson and serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=100,
+                    help="requests of the serving stream per arrival rate (0: no serving run)")
     ap.add_argument("--profile-davidson", default=None, metavar="CONFIG",
                     help="profiling driver: one FP64 Davidson solve of C0, SMALL or C2 after one "
                          "warm-up solve, a one-line JSON with its time, nothing else")

@@ -23,6 +23,7 @@
 
 #include "ctx.h"
 #include "dense.h"
+#include "dvtask.h"
 #include "fft_device.cuh"
 
 namespace qe {
@@ -1008,9 +1009,12 @@ static int dv_loop(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
 // on as an FP64 Davidson from them (they are an orthonormal basis to FP64
 // rounding) until tol or max_iter.  The mixed path thus meets the same
 // residual criterion as the FP64 one, with most iterations in FP32.
-static int dv_fp64_phase(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
+// First half: the decision and the FP64 basis; *more = true when FP64
+// iterations follow (dv_loop<double>, or a lockstep driver's rounds).
+static int dv_fp64_begin(qe_ctx* ctx, DvSolve& v, cudaStream_t st, bool* more) {
   DvState& S = v.S;
   const int nb = S.nb, npw = S.npw;
+  *more = false;
   DV_CU(cudaMemcpyAsync(v.rn.data(), S.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   DV_CU(cudaStreamSynchronize(st));
   double rmax = 0.0;
@@ -1032,7 +1036,14 @@ static int dv_fp64_phase(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
   v.conv = false;
   v.rmax = rmax;
   v.h_rows = 0;
-  return dv_loop<double>(ctx, v, st);
+  *more = true;
+  return QE_OK;
+}
+
+static int dv_fp64_phase(qe_ctx* ctx, DvSolve& v, cudaStream_t st) {
+  bool more = false;
+  DV_TRY(dv_fp64_begin(ctx, v, st, &more));
+  return more ? dv_loop<double>(ctx, v, st) : QE_OK;
 }
 
 template <typename T>
@@ -1451,6 +1462,205 @@ static int cg_run(qe_ctx* ctx, DvSolve& v, double tol, int max_iter, int max_swe
 }
 
 }  // namespace
+
+// ---- lockstep rounds of independent solves (serving) --------------------------------
+namespace qe {
+
+enum { DV_FIRST_H = 0, DV_STEP = 1, DV_H = 2, DV_REFINE_H = 3, DV_DONE = 4 };
+
+struct DvTask {
+  cudaStream_t cur = nullptr;   // stream of the task's buffers (the driver's)
+  DevBuf basis, red, opbuf;     // Davidson workspace; device copies of V, beta, D
+  qe_problem prob{};            // device pointers into opbuf
+  DvSolve v;
+  int phase = DV_FIRST_H;
+  int h_prec = QE_FP64;         // arithmetic of the pending H product
+  int rc = QE_OK;
+  DvTask() {
+    basis.sp = &cur;
+    red.sp = &cur;
+    opbuf.sp = &cur;
+  }
+};
+
+int dv_task_create(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int max_iter,
+                   const double* psi0, void* stream, DvTask** out) {
+  *out = nullptr;
+  DV_TRY(check_problem(prob, "qe_serve"));
+  if (prob->mem != QE_HOST || !psi0) { set_error("qe_serve: host arrays expected"); return QE_EINVAL; }
+  const int flags = precision & (QE_GAMMA | QE_NO_GAMMA | QE_RR_FP32);
+  precision &= ~(QE_GAMMA | QE_NO_GAMMA | QE_RR_FP32);
+  cudaStream_t st = (cudaStream_t)stream;
+  DevPlan* P = nullptr;
+  DV_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
+  auto t = std::make_unique<DvTask>();
+  t->cur = st;
+  const size_t ngrid = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
+  const size_t nbeta = (size_t)prob->nproj * P->h.npw * 2, nd = (size_t)prob->nproj * prob->nproj;
+  const size_t ov = (ngrid * sizeof(double) + 255) & ~(size_t)255;
+  const size_t ob = (nbeta * sizeof(double) + 255) & ~(size_t)255;
+  DV_TRY(t->opbuf.ensure(ov + ob + nd * sizeof(double) + 256));
+  char* base = static_cast<char*>(t->opbuf.p);
+  DV_CU(cudaMemcpyAsync(base, prob->vloc_r, ngrid * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (prob->nproj > 0) {
+    DV_CU(cudaMemcpyAsync(base + ov, prob->beta, nbeta * sizeof(double), cudaMemcpyHostToDevice, st));
+    DV_CU(cudaMemcpyAsync(base + ov + ob, prob->dmat, nd * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  t->prob = *prob;
+  t->prob.vloc_r = reinterpret_cast<const double*>(base);
+  t->prob.beta = prob->nproj > 0 ? reinterpret_cast<const double*>(base + ov) : nullptr;
+  t->prob.dmat = prob->nproj > 0 ? reinterpret_cast<const double*>(base + ov + ob) : nullptr;
+  t->prob.mem = QE_DEVICE;
+  DV_TRY(dv_setup(ctx, &t->prob, precision, tol, max_iter, 0, t->basis, t->red, t->v, st, "qe_serve",
+                  gamma_mode(precision, flags, prob->grid)));
+  t->v.mixed_rr32 = (flags & QE_RR_FP32) != 0;
+  DvState& S = t->v.S;
+  DV_CU(cudaMemcpyAsync(S.V, psi0, (size_t)S.nb * S.npw * sizeof(z), cudaMemcpyHostToDevice, st));
+  DV_TRY(dv_begin(t->v, st));
+  t->phase = DV_FIRST_H;
+  t->h_prec = precision;
+  *out = t.release();
+  return QE_OK;
+}
+
+bool dv_task_done(const DvTask* t) { return t->phase == DV_DONE || t->rc != QE_OK; }
+
+// After the FP64 Rayleigh-Ritz that ends the mixed path's FP32 phase.
+static int dv_task_after_refine(qe_ctx* ctx, DvTask& t, cudaStream_t st) {
+  bool more = false;
+  DV_TRY(dv_fp64_begin(ctx, t.v, st, &more));
+  t.phase = more ? DV_STEP : DV_DONE;
+  return QE_OK;
+}
+
+int dv_round(qe_ctx* ctx, DvTask* const* tasks, int n, void* stream, void* const* side, int nside,
+             void* const* events) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Prof* pf = &ctx->prof;
+  auto live = [&](const DvTask* t) { return t->rc == QE_OK && t->phase != DV_DONE; };
+  // 1. the pending H products, one batched call per arithmetic
+  for (int prec : {QE_FP64, QE_MIXED}) {
+    std::vector<DvTask*> ts;
+    std::vector<qe_problem> pr;
+    std::vector<const double*> in;
+    std::vector<double*> outp;
+    std::vector<char> pair;
+    for (int i = 0; i < n; ++i) {
+      DvTask* t = tasks[i];
+      const bool wants = t->phase == DV_FIRST_H || t->phase == DV_H || t->phase == DV_REFINE_H;
+      if (!live(t) || !wants || t->h_prec != prec || t->v.h_rows <= 0) continue;
+      qe_problem q = t->prob;
+      q.nbnd = t->v.h_rows;
+      const size_t off = (size_t)t->v.h_row * t->v.S.npw;
+      ts.push_back(t);
+      pr.push_back(q);
+      in.push_back(reinterpret_cast<const double*>(t->v.S.V + off));
+      outp.push_back(reinterpret_cast<double*>(t->v.S.HV + off));
+      pair.push_back(t->v.S.gamma ? 1 : 0);
+    }
+    if (pr.empty()) continue;
+    const int rc = hpsi_batch_core(ctx, (int)pr.size(), pr.data(), prec, in.data(), outp.data(), st,
+                                   pair.data());
+    if (rc) {
+      for (DvTask* t : ts) t->rc = rc;
+      continue;
+    }
+    // 2. what follows each H product
+    for (DvTask* t : ts) {
+      DvSolve& v = t->v;
+      const bool f64 = v.precision == QE_FP64;
+      if (t->phase == DV_FIRST_H) {
+        t->rc = f64 ? dv_after_first_h<double>(v, st, pf) : dv_after_first_h<float>(v, st, pf);
+        t->phase = DV_STEP;
+      } else if (t->phase == DV_H) {
+        t->rc = f64 ? dv_after_h<double>(v, st, pf) : dv_after_h<float>(v, st, pf);
+        t->phase = DV_STEP;
+      } else {
+        v.h_rows = 0;
+        t->rc = refine_post(v.S, st, pf);
+        if (t->rc == QE_OK) t->rc = dv_task_after_refine(ctx, *t, st);
+      }
+    }
+  }
+  // 3. one Rayleigh-Ritz step of every task at that stage, task i on a side
+  //    stream (forked after the H products): all launched, then the
+  //    convergence tests in turn (each waits for its own stream only)
+  std::vector<DvTask*> step;
+  for (int i = 0; i < n; ++i)
+    if (live(tasks[i]) && tasks[i]->phase == DV_STEP) step.push_back(tasks[i]);
+  const int ns = std::max(1, nside);
+  auto sst = [&](size_t i) { return nside > 0 ? (cudaStream_t)side[i % ns] : st; };
+  if (nside > 0 && !step.empty()) {
+    DV_CU(cudaEventRecord((cudaEvent_t)events[0], st));
+    for (int k = 0; k < ns; ++k) DV_CU(cudaStreamWaitEvent((cudaStream_t)side[k], (cudaEvent_t)events[0], 0));
+  }
+  for (size_t i = 0; i < step.size(); ++i) {
+    DvTask* t = step[i];
+    t->rc = t->v.precision == QE_FP64 ? dv_step_launch<double>(t->v, sst(i), pf)
+                                      : dv_step_launch<float>(t->v, sst(i), pf);
+  }
+  for (size_t i = 0; i < step.size(); ++i) {
+    DvTask* t = step[i];
+    if (t->rc != QE_OK) continue;
+    DvSolve& v = t->v;
+    t->rc = v.precision == QE_FP64 ? dv_step_finish<double>(ctx, v, sst(i), pf)
+                                   : dv_step_finish<float>(ctx, v, sst(i), pf);
+    if (t->rc != QE_OK) continue;
+    if (v.done) {
+      if (v.precision != QE_FP64) {
+        // the FP32 phase ended: FP64 H of the Ritz vectors, FP64 Rayleigh-Ritz
+        t->rc = refine_pre(v.S, sst(i));
+        v.h_row = 0;
+        v.h_rows = v.S.nb;
+        t->h_prec = QE_FP64;
+        t->phase = DV_REFINE_H;
+      } else {
+        t->phase = DV_DONE;
+      }
+    } else if (v.h_rows > 0) {
+      t->h_prec = v.precision;
+      t->phase = DV_H;
+    }
+  }
+  if (nside > 0 && !step.empty()) {
+    // join: the next round's H products follow every task's step
+    for (int k = 0; k < ns; ++k) {
+      DV_CU(cudaEventRecord((cudaEvent_t)events[1 + k], (cudaStream_t)side[k]));
+      DV_CU(cudaStreamWaitEvent(st, (cudaEvent_t)events[1 + k], 0));
+    }
+  }
+  return QE_OK;
+}
+
+int dv_task_result(qe_ctx* ctx, DvTask* t, double* psi, double* evals, double* resid, int* iters,
+                   void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  DvSolve& v = t->v;
+  DvState& S = v.S;
+  if (iters) *iters = v.it;
+  if (t->rc != QE_OK && t->rc != QE_ENOCONV) return t->rc;
+  if (psi) DV_CU(cudaMemcpyAsync(psi, S.Psi, (size_t)S.nb * S.npw * sizeof(z), cudaMemcpyDeviceToHost, st));
+  if (evals) DV_CU(cudaMemcpyAsync(evals, S.e, S.nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (resid) DV_CU(cudaMemcpyAsync(resid, S.rn, S.nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DV_TRY(dv_final_status(v, st, "qe_serve"));
+  if (t->rc == QE_ENOCONV) return QE_ENOCONV;
+  if (!v.conv) {
+    set_error("qe_serve: not converged after %d iterations", v.it);
+    return QE_ENOCONV;
+  }
+  return QE_OK;
+}
+
+void dv_task_destroy(DvTask* t, void* stream) {
+  if (!t) return;
+  t->cur = (cudaStream_t)stream;
+  t->basis.release();
+  t->red.release();
+  t->opbuf.release();
+  delete t;
+}
+
+}  // namespace qe
 
 extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, double tol,
                            int max_iter, int max_dim, double* psi_inout, double* evals,

@@ -222,9 +222,23 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   if (warp < 8) {
     // epilogue warp: TMEM lanes of quarter (warp % 4), columns [c0, c0 + 32)
     const int quarter = warp & 3, c0 = (warp >> 2) * OZ_ECOLS;
-    double acc[OZ_ECOLS];
+    // Integer accumulation in units of 2^-unit of the scaled product (no FP64
+    // instruction per chunk: GB300's FP64 pipe would bound the drain).  A
+    // chunk's exact diagonal sums combine, four at a time, into
+    //   T0 = ((S_0 128 + S_1) 128 + S_2) 128 + S_3   (units 2^-35),
+    //   T1 = ((S_4 128 + S_5) 128 + S_6) 128 + S_7   (units 2^-63),
+    // added as T0 2^(unit-35) + round(T1 2^(unit-63)).  The CTA's whole value
+    // is below its K range K_cta (|a|, |b| < 1 after scaling), so unit =
+    // min(52, 62 - bits(K_cta)) keeps the sum below 2^62; the rounding adds at
+    // most 2^-(unit+1) per chunk of 384 terms, below 2^-53 per term of the K
+    // sum when unit >= 45 (K_cta < 2^17), the order of the dropped slice pairs.
+    const int kbits = 64 - __clzll((long long)nk * OZ_BK);
+    const int unit = max(36, min(52, 62 - kbits));
+    const int sh0 = unit - 35, sh1 = 63 - unit;
+    const long long half1 = 1ll << (sh1 - 1);
+    long long acc[OZ_ECOLS];
 #pragma unroll
-    for (int q = 0; q < OZ_ECOLS; ++q) acc[q] = 0.0;
+    for (int q = 0; q < OZ_ECOLS; ++q) acc[q] = 0;
     bool ok = true;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
     for (int c = 0; c < nchunks; ++c) {
@@ -234,12 +248,9 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // Combine the exact integer sums of four diagonals in int64,
-      //   T = ((S_d0 128 + S_d0+1) 128 + S_d0+2) 128 + S_d0+3  (|T| < 2^46),
-      // so that each column costs 2 conversions and 2 FP64 FMAs per chunk
-      // instead of 8 each (GB300's FP64 pipe also runs the conversions).
 #pragma unroll
       for (int cb = 0; cb < OZ_ECOLS / 8; ++cb) {
+        long long t0[8];
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
           uint32_t r[4][8];
@@ -247,13 +258,13 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           for (int dd = 0; dd < 4; ++dd)
             tmem_ld8_nowait(lane_base + (uint32_t)((4 * g + dd) * OZ_BN + cb * 8), r[dd]);
           tmem_wait_ld();
-          const double w = pow2(-7 * (4 * g + 3 + 2));
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             long long T = __float2int_rn(__uint_as_float(r[0][q]));
 #pragma unroll
             for (int dd = 1; dd < 4; ++dd) T = T * 128 + __float2int_rn(__uint_as_float(r[dd][q]));
-            acc[cb * 8 + q] = fma(__ll2double_rn(T), w, acc[cb * 8 + q]);
+            if (g == 0) t0[q] = T;
+            else acc[cb * 8 + q] += (t0[q] << sh0) + ((T + half1) >> sh1);
           }
         }
       }
@@ -269,8 +280,8 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       for (int q = 0; q < OZ_ECOLS / 2; ++q) {
         const int n = ((n0 + c0) >> 1) + q;
         if (n >= N) break;
-        const double f = pow2(ea + oz_exp(eB[n]));
-        double2 v = make_double2(acc[2 * q] * f, acc[2 * q + 1] * f);
+        const double f = pow2(ea + oz_exp(eB[n]) - unit);
+        double2 v = make_double2(__ll2double_rn(acc[2 * q]) * f, __ll2double_rn(acc[2 * q + 1]) * f);
         if (alpha_neg) { v.x = -v.x; v.y = -v.y; }
         double2* p = o + (size_t)n * ldo;
         if (beta) { const double2 old = *p; v.x += old.x; v.y += old.y; }

@@ -6,12 +6,17 @@
 // The paper's outlook (Sec. 4) observes that memory per card bounds the system
 // size and that ensembles of many independent runs are the way to fill an
 // exascale machine; Sec. 3.3 notes that over-subscribing one GPU with several
-// small runs pays off.  Here every admitted request gets a slot: a worker thread
-// with its own context and CUDA stream, so the kernels of concurrent solves
-// overlap on the GPU.  A request is admitted, in arrival order, when a slot is
-// idle and its estimated device footprint fits in what the budget has left;
-// when a solve finishes its workspace goes back to the stream-ordered pool and
-// the next request is admitted.
+// small runs pays off.  Here one engine thread owns a context and a stream and
+// advances every admitted solve in lockstep rounds (dvtask.h): a round applies
+// H to the new basis vectors of ALL running solves in one batched call (one
+// persistent launch per FFT stage over every cell's bands), then takes one
+// Rayleigh-Ritz step of each.  Between rounds, requests are admitted in arrival
+// order while the number of running solves is below max_slots and the
+// estimated device footprint fits in what the budget has left, so a new
+// arrival joins at the next iteration boundary; a finished solve returns its
+// results and its workspace.  A solve's arithmetic is the same whatever else
+// runs (deterministic kernels, its own buffers): results are bit for bit those
+// of the solve alone.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -27,8 +32,10 @@
 #include <cuda_runtime.h>
 
 #include "common.h"
+#include "dvtask.h"
 
 namespace qe {
+int ctx_begin(qe_ctx* ctx, cudaStream_t st);
 int ctx_trim_public(qe_ctx* ctx);
 size_t davidson_footprint(int npw, int nb, int max_dim, int nproj, const int grid[3], int nst);
 int default_max_dim(int nb);
@@ -55,10 +62,12 @@ struct Request {
   std::string err;
 };
 
-struct Worker {
-  std::thread th;
-  qe_ctx* ctx = nullptr;
-  cudaStream_t st = nullptr;
+// One running solve of the engine.
+struct Active {
+  std::shared_ptr<Request> r;
+  qe::DvTask* task = nullptr;   // GPU solve
+  int fake_left = 0;            // QE_SERVE_FAKE_SOLVER: rounds left
+  bool failed = false;
 };
 
 }  // namespace
@@ -75,68 +84,147 @@ struct qe_srv {
   uint64_t next_id = 1;
   bool stop = false;
   int running = 0;
-  long long submitted = 0, completed = 0;
-  std::vector<std::unique_ptr<Worker>> workers;
+  long long submitted = 0, completed = 0, rounds = 0;
+  std::thread engine;
+  qe_ctx* ctx = nullptr;
+  cudaStream_t st = nullptr;
+  // side streams of the per-solve Rayleigh-Ritz steps and the fork/join events
+  std::vector<void*> side, events;
 };
+
+// Side streams of the engine: the dense eigensolvers of that many running
+// solves overlap within a round.
+constexpr int kServeSideStreams = 8;
 
 namespace {
 
-// Test hook (QE_SERVE_FAKE_SOLVER): no GPU work; a "solve" sleeps max_iter
-// milliseconds, copies psi through, returns evals = 0 and QE_OK, or QE_ENOCONV
-// when tol > 1.  Exercises admission, queueing, cancellation and timeouts on
-// machines without a GPU.
-void fake_solve(Request& r) {
-  std::this_thread::sleep_for(std::chrono::milliseconds(r.max_iter));
+// Test hook (QE_SERVE_FAKE_SOLVER): no GPU work; a "solve" takes max_iter
+// rounds of 1 ms, copies psi through, returns evals = 0 and QE_OK, or
+// QE_ENOCONV when tol > 1.  Exercises admission, queueing, cancellation and
+// timeouts on machines without a GPU.
+void fake_finish(Request& r) {
   std::fill(r.evals.begin(), r.evals.end(), 0.0);
   std::fill(r.resid.begin(), r.resid.end(), 0.0);
   r.iters = r.max_iter;
   r.status = r.tol > 1.0 ? QE_ENOCONV : QE_OK;
 }
 
-void worker_loop(qe_srv* s, Worker* w) {
+// Set up the device side of an admitted request; false (status set) on failure.
+bool start_solve(qe_srv* s, Active& a) {
+  Request& r = *a.r;
+  if (s->flags & QE_SERVE_FAKE_SOLVER) {
+    a.fake_left = r.max_iter;
+    return true;
+  }
+  r.prob.vloc_r = r.vloc.data();
+  r.prob.beta = r.beta.empty() ? nullptr : r.beta.data();
+  r.prob.dmat = r.dmat.empty() ? nullptr : r.dmat.data();
+  r.prob.mem = QE_HOST;
+  const int rc = qe::dv_task_create(s->ctx, &r.prob, r.precision, r.tol, r.max_iter, r.psi.data(),
+                                    s->st, &a.task);
+  if (rc) {
+    r.status = rc;
+    r.err = qe_last_error();
+    return false;
+  }
+  return true;
+}
+
+// Results of a finished solve into the request; frees its device state.
+void finish_solve(qe_srv* s, Active& a) {
+  Request& r = *a.r;
+  if (s->flags & QE_SERVE_FAKE_SOLVER) {
+    fake_finish(r);
+    return;
+  }
+  if (a.task) {
+    int it = 0;
+    r.status = qe::dv_task_result(s->ctx, a.task, r.psi.data(), r.evals.data(), r.resid.data(), &it,
+                                  s->st);
+    r.iters = it;
+    if (r.status != QE_OK) r.err = qe_last_error();
+    qe::dv_task_destroy(a.task, s->st);
+    a.task = nullptr;
+    cudaStreamSynchronize(s->st);
+  }
+}
+
+void engine_loop(qe_srv* s) {
   const bool fake = (s->flags & QE_SERVE_FAKE_SOLVER) != 0;
-  if (!fake) cudaSetDevice(s->device);
+  if (!fake) {
+    cudaSetDevice(s->device);
+    qe::ctx_begin(s->ctx, s->st);   // the context's buffers and plans follow the engine stream
+  }
+  std::vector<Active> act;
   while (true) {
-    std::shared_ptr<Request> r;
+    std::vector<std::shared_ptr<Request>> admit;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv_work.wait(lk, [&] {
-        return s->stop || (!s->pending.empty() && s->used + s->pending.front()->bytes <= s->budget);
-      });
-      if (s->stop) return;
-      r = s->pending.front();
-      s->pending.pop_front();
-      s->used += r->bytes;
-      s->running++;
-      r->running = true;
+      auto can_admit = [&] {
+        return !s->stop && !s->pending.empty() && (int)act.size() + (int)admit.size() < s->max_slots &&
+               s->used + s->pending.front()->bytes <= s->budget;
+      };
+      if (act.empty()) s->cv_work.wait(lk, [&] { return s->stop || can_admit(); });
+      if (s->stop && act.empty()) return;
+      while (can_admit()) {
+        auto r = s->pending.front();
+        s->pending.pop_front();
+        s->used += r->bytes;
+        s->running++;
+        r->running = true;
+        admit.push_back(r);
+      }
     }
+    for (auto& r : admit) {
+      Active a;
+      a.r = r;
+      a.failed = !start_solve(s, a);
+      act.push_back(a);
+    }
+    // one lockstep round of every running solve
     if (fake) {
-      fake_solve(*r);
+      bool any = false;
+      for (auto& a : act) any = any || (!a.failed && a.fake_left > 0);
+      if (any) std::this_thread::sleep_for(std::chrono::milliseconds(1));
+      for (auto& a : act)
+        if (a.fake_left > 0) --a.fake_left;
     } else {
-      r->prob.vloc_r = r->vloc.data();
-      r->prob.beta = r->beta.empty() ? nullptr : r->beta.data();
-      r->prob.dmat = r->dmat.empty() ? nullptr : r->dmat.data();
-      r->prob.mem = QE_HOST;
-      int it = 0;
-      r->status = qe_davidson(w->ctx, &r->prob, r->precision, r->tol, r->max_iter, 0, r->psi.data(),
-                              r->evals.data(), r->resid.data(), &it, w->st);
-      r->iters = it;
-      if (r->status != QE_OK) r->err = qe_last_error();
-      // give the workspace back so that the budget accounting stays true
-      qe::ctx_trim_public(w->ctx);
+      std::vector<qe::DvTask*> ts;
+      for (auto& a : act)
+        if (!a.failed && a.task && !qe::dv_task_done(a.task)) ts.push_back(a.task);
+      if (!ts.empty())
+        qe::dv_round(s->ctx, ts.data(), (int)ts.size(), s->st, s->side.data(), (int)s->side.size(),
+                     s->events.data());
     }
-    {
+    // completions
+    std::vector<Active> keep;
+    std::vector<Active> fin;
+    for (auto& a : act) {
+      const bool done = a.failed || (fake ? a.fake_left <= 0 : qe::dv_task_done(a.task));
+      (done ? fin : keep).push_back(a);
+    }
+    act.swap(keep);
+    for (auto& a : fin) {
+      if (!a.failed) finish_solve(s, a);
       std::lock_guard<std::mutex> lk(s->mu);
-      r->t_done = Clock::now();
-      r->running = false;
-      r->done = true;
-      if (r->canceled) r->status = QE_ECANCELED;
-      s->used -= r->bytes;
+      a.r->t_done = Clock::now();
+      a.r->running = false;
+      a.r->done = true;
+      if (a.r->canceled) a.r->status = QE_ECANCELED;
+      s->used -= a.r->bytes;
       s->running--;
       s->completed++;
     }
-    s->cv_done.notify_all();
-    s->cv_work.notify_all();
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->rounds++;
+    }
+    if (!fin.empty()) {
+      // keep the plan cache and the shared workspaces from growing without
+      // bound over a long stream of different cells
+      if (!fake && act.empty()) qe::ctx_trim_public(s->ctx);
+      s->cv_done.notify_all();
+    }
   }
 }
 
@@ -158,33 +246,32 @@ int qe_serve_create(int device, size_t hbm_budget_bytes, int max_slots, int max_
   s->max_slots = max_slots;
   s->max_queue = max_queue;
   s->flags = flags;
-  const bool fake = (flags & QE_SERVE_FAKE_SOLVER) != 0;
-  for (int i = 0; i < max_slots; ++i) {
-    auto w = std::make_unique<Worker>();
-    if (!fake) {
-      int rc = qe_ctx_create(device, &w->ctx);
-      if (rc) {
-        for (auto& x : s->workers) {
-          if (x->ctx) qe_ctx_destroy(x->ctx);
-          if (x->st) cudaStreamDestroy(x->st);
-        }
-        return rc;
-      }
-      if (cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        qe_ctx_destroy(w->ctx);
-        for (auto& x : s->workers) {
-          if (x->ctx) qe_ctx_destroy(x->ctx);
-          if (x->st) cudaStreamDestroy(x->st);
-        }
-        qe::set_error("qe_serve_create: cudaStreamCreate failed");
-        return QE_ECUDA;
-      }
+  if (!(flags & QE_SERVE_FAKE_SOLVER)) {
+    int rc = qe_ctx_create(device, &s->ctx);
+    if (rc) return rc;
+    bool ok = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < kServeSideStreams; ++i) {
+      cudaStream_t x = nullptr;
+      ok = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) s->side.push_back(x);
     }
-    s->workers.push_back(std::move(w));
+    for (int i = 0; ok && i <= kServeSideStreams; ++i) {
+      cudaEvent_t e = nullptr;
+      ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) s->events.push_back(e);
+    }
+    if (!ok) {
+      cudaGetLastError();
+      for (void* x : s->side) cudaStreamDestroy((cudaStream_t)x);
+      for (void* e : s->events) cudaEventDestroy((cudaEvent_t)e);
+      if (s->st) cudaStreamDestroy(s->st);
+      qe_ctx_destroy(s->ctx);
+      qe::set_error("qe_serve_create: stream or event creation failed");
+      return QE_ECUDA;
+    }
   }
   qe_srv* raw = s.release();
-  for (auto& w : raw->workers) w->th = std::thread(worker_loop, raw, w.get());
+  raw->engine = std::thread(engine_loop, raw);
   *out = raw;
   return QE_OK;
 }
@@ -315,12 +402,11 @@ void qe_serve_destroy(qe_srv* s) {
   }
   s->cv_work.notify_all();
   s->cv_done.notify_all();
-  for (auto& w : s->workers)
-    if (w->th.joinable()) w->th.join();
-  for (auto& w : s->workers) {
-    if (w->ctx) qe_ctx_destroy(w->ctx);
-    if (w->st) cudaStreamDestroy(w->st);
-  }
+  if (s->engine.joinable()) s->engine.join();
+  if (s->ctx) qe_ctx_destroy(s->ctx);
+  for (void* x : s->side) cudaStreamDestroy((cudaStream_t)x);
+  for (void* e : s->events) cudaEventDestroy((cudaEvent_t)e);
+  if (s->st) cudaStreamDestroy(s->st);
   delete s;
 }
 
