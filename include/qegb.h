@@ -226,6 +226,36 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
 int qe_hpsi_noalloc(const qe_problem* prob, int precision, const double* psi,
                     double* hpsi, void* stream);
 
+/* Projectors defined instead of stored (Sec. 3.2.2 item (viii), calculation of
+ * pseudopotential terms; Sec. 4 names memory per card as the bound on system
+ * size).  For atom I at R_I (tau, Cartesian bohr, host) and radial function n
+ * with angular momentum l[n] (0 or 1, host) and radial table
+ * radial[n][G] = F_n(|k+G|) (qe_gsphere order, host or device per prob->mem):
+ *   beta_{I,n,c}(G) = e^{-i (k+G).R_I} (-i)^{l_n} Y_{l_n c}(k+G) F_n(G),
+ *   Y_00 = 1 / (2 sqrt(pi)),  Y_1c(q) = sqrt(3 / (4 pi)) q_c  (c = x, y, z),
+ * ordered atom-major, per atom per radial function its 2 l_n + 1 components.
+ * (The Gaussian projectors of qe_beta_gaussian are radial functions of each
+ * width with l = 0 and l = 1 and F = Omega^-1/2 N (2 pi)^{3/2} w^{2l+3}
+ * e^{-w^2 q^2 / 2}.)  At most 8 radial functions. */
+typedef struct {
+  int natom;
+  const double* tau;      /* [natom][3] */
+  int nrad;
+  const int* l;           /* [nrad] */
+  const double* radial;   /* [nrad][npw] */
+} qe_projectors;
+
+/* qe_hpsi with the projectors of `pj` generated on the fly: prob->beta is not
+ * read (may be NULL), prob->nproj must equal natom * sum_n (2 l_n + 1) and
+ * prob->dmat is D over those projectors.  The FP64 path forms beta straight
+ * into the tensor-core slices of its products from per-atom phase tables (no
+ * beta array is stored or copied; with host arrays none crosses the bus); the
+ * other paths form the values into a work array first.  Same arguments,
+ * precisions and results (to the tolerances of qe_hpsi: 1e-12 FP64, 2e-5
+ * mixed) as qe_hpsi with the equivalent stored beta. */
+int qe_hpsi_gen(qe_ctx* ctx, const qe_problem* prob, const qe_projectors* pj, int precision,
+                const double* psi, double* hpsi, void* stream);
+
 /* Block Davidson (Sec. 3.3, iterative solution of the Kohn-Sham Hamiltonian;
  * Sec. 3.2.1, KS_Solvers and the dense eigensolver of LAXlib) for the nbnd
  * lowest eigenpairs.  psi_inout: start bands in, Ritz vectors out
@@ -276,6 +306,23 @@ int qe_cg(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int ma
 int qe_density(qe_ctx* ctx, const double lat[9], double ecut, const int grid[3], int nk,
                const double* kpts, const int* nbnd, const double* const* psi,
                const double* const* weights, int precision, double* rho, int mem, void* stream);
+
+/* One self-consistency step of the local potential (Sec. 3.3: electronic
+ * self-consistency and charge-density generation on the GPU): from the bands
+ * (arguments as qe_density) the density rho, then, in Rydberg units,
+ *   V_H(r)  = sum_{0 < |G|^2 <= 4 ecut} 8 pi rho~(G) / |G|^2 e^{iG.r},
+ *             rho~(G) = (1/N) sum_j rho(r_j) e^{-iG.r_j}  (the density sphere),
+ *   v_x(r)  = -2 (3 rho(r) / pi)^{1/3}                    (Slater exchange, LDA),
+ *   V_new   = (1 - alpha) V_in + alpha (V_ext + V_H + v_x).
+ * vext, vin, vnew and rho_out (optional) are [N3][N2][N1] doubles, with psi per
+ * `mem`; weights are host arrays.  QE_EINVAL when the grid cannot hold the
+ * density sphere (N_i < 2 max|m_i| + 1 for |G|^2 <= 4 ecut).  precision as
+ * qe_density (the transforms of V_H in that arithmetic).  Device work is ordered
+ * on `stream`; with QE_HOST the call returns after it ends. */
+int qe_scf_step(qe_ctx* ctx, const double lat[9], double ecut, const int grid[3], int nk,
+                const double* kpts, const int* nbnd, const double* const* psi,
+                const double* const* weights, const double* vext, const double* vin, double alpha,
+                int precision, double* vnew, double* rho_out, int mem, void* stream);
 
 /* ---- Batches: many problems per launch --------------------------------------
  * The paper's benchmarks parallelise over k points (pools, Sec. 3.3) and note

@@ -21,10 +21,11 @@ from .hamiltonian import (apply_local, apply_nonlocal, apply_kinetic, hpsi,
 from .eigen import rayleigh_ritz, davidson
 from .density import band_in_r, density
 from .cg import cg
+from .scf import hartree, exchange, scf_step
 
 __all__ = [
     "reciprocal", "volume", "gsphere", "grid_slots", "vloc_gaussian",
     "beta_gaussian", "check_grid", "apply_local", "apply_nonlocal",
     "apply_kinetic", "hpsi", "dense_h", "h_diag", "vtilde", "rayleigh_ritz",
-    "davidson", "band_in_r", "density", "cg",
+    "davidson", "band_in_r", "density", "cg", "hartree", "exchange", "scf_step",
 ]

@@ -38,7 +38,7 @@ SYMBOLS = ["qe_last_error", "qe_ctx_create", "qe_ctx_destroy", "qe_gsphere",
            "qe_profile_read", "qe_hpsi_noalloc", "qe_serve_create", "qe_serve_submit",
            "qe_serve_poll", "qe_serve_cancel", "qe_serve_stats", "qe_serve_destroy",
            "qe_hpsi_batch", "qe_batch_create", "qe_batch_run", "qe_batch_destroy", "qe_autotune",
-           "qe_davidson_batch", "qe_test_grid_wait", "qe_cg", "qe_density"]
+           "qe_davidson_batch", "qe_test_grid_wait", "qe_cg", "qe_density", "qe_hpsi_gen", "qe_scf_step"]
 QE_SERVE_FAKE_SOLVER = 1
 
 
@@ -59,6 +59,11 @@ _lib = _load()
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
+
+
+class Projectors(ctypes.Structure):
+    _fields_ = [("natom", ctypes.c_int), ("tau", _P), ("nrad", ctypes.c_int), ("l", _P),
+                ("radial", _P)]
 
 
 class Problem(ctypes.Structure):
@@ -103,10 +108,15 @@ _lib.qe_batch_destroy.restype = None
 _lib.qe_autotune.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P]
 _lib.qe_hpsi_noalloc.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
 _lib.qe_hpsi.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, _P, _P, _P]
+_lib.qe_hpsi_gen.argtypes = [_P, ctypes.POINTER(Problem), ctypes.POINTER(Projectors), ctypes.c_int,
+                             _P, _P, _P]
 _lib.qe_davidson.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double,
                              ctypes.c_int, ctypes.c_int, _P, _P, _P, _I, _P]
 _lib.qe_density.argtypes = [_P, _D, ctypes.c_double, _I, ctypes.c_int, _D, _I, ctypes.POINTER(_P),
                             ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.c_int, _P]
+_lib.qe_scf_step.argtypes = [_P, _D, ctypes.c_double, _I, ctypes.c_int, _D, _I, ctypes.POINTER(_P),
+                             ctypes.POINTER(_P), _P, _P, ctypes.c_double, ctypes.c_int, _P, _P,
+                             ctypes.c_int, _P]
 _lib.qe_cg.argtypes = [_P, ctypes.POINTER(Problem), ctypes.c_int, ctypes.c_double, ctypes.c_int,
                        ctypes.c_int, _P, _P, _P, _I, _P]
 _lib.qe_davidson_batch.argtypes = [_P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
@@ -289,6 +299,19 @@ class Context:
         pr._keep = (vloc, beta, dmat)
         return pr
 
+    @staticmethod
+    def problem_gen(lat, k, ecut, grid, vloc, dmat, nproj, nbnd) -> Problem:
+        """Problem descriptor for hpsi_gen: no stored beta, nproj projectors
+        generated from their definition, D over them."""
+        pr = Context.problem(lat, k, ecut, grid, vloc, None, None, nbnd)
+        pd, md = _ptr(dmat)
+        if nproj and md != pr.mem:
+            raise ValueError("vloc and dmat must live in the same memory")
+        pr.nproj = int(nproj)
+        pr.dmat = pd if nproj else None
+        pr._keep = (vloc, None, dmat)
+        return pr
+
     def hpsi(self, prob: Problem, psi, hpsi, precision=QE_FP64, stream=None):
         pp, mp = _ptr(psi)
         ph, mh = _ptr(hpsi)
@@ -296,6 +319,27 @@ class Context:
             raise ValueError("psi/hpsi must live where the problem's arrays live")
         _check(_lib.qe_hpsi(self._h, ctypes.byref(prob), int(precision), pp, ph,
                             _stream(stream, psi)))
+        return hpsi
+
+    def hpsi_gen(self, prob: Problem, tau, lrad, radial, psi, hpsi, precision=QE_FP64,
+                 stream=None):
+        """H|psi> with projectors generated on the fly from atom positions tau
+        (natom, 3), angular momenta lrad (nrad,) and the radial table radial
+        (nrad, npw) (host float64 or a CUDA tensor, where the problem lives);
+        prob.beta is not read."""
+        tau = _f64(tau)
+        lr = np.ascontiguousarray(lrad, dtype=np.int32)
+        pr_, mr = _ptr(radial)
+        if lr.size and mr != prob.mem:
+            raise ValueError("the radial table must live where the problem's arrays live")
+        pj = Projectors(int(tau.size // 3), ctypes.c_void_p(tau.ctypes.data), int(lr.size),
+                        ctypes.c_void_p(lr.ctypes.data), pr_)
+        pp, mp = _ptr(psi)
+        ph, mh = _ptr(hpsi)
+        if prob.nbnd > 0 and (mp != prob.mem or mh != prob.mem):
+            raise ValueError("psi/hpsi must live where the problem's arrays live")
+        _check(_lib.qe_hpsi_gen(self._h, ctypes.byref(prob), ctypes.byref(pj), int(precision), pp, ph,
+                                _stream(stream, psi)))
         return hpsi
 
     # ---- batches ------------------------------------------------------------------
@@ -377,6 +421,35 @@ class Context:
                                _dptr(kp), nb.ctypes.data_as(_I), parr, warr, int(precision), pr, mr,
                                _stream(stream, rho)))
         return rho
+
+    def scf_step(self, lat, ecut, grid, kpts, psis, weights, vext, vin, alpha, vnew, rho=None,
+                 precision=QE_FP64, stream=None):
+        """One self-consistency step: V_new = (1 - alpha) V_in + alpha (V_ext + V_H[rho] +
+        v_x[rho]) with rho from the bands (arrays as density(); vext, vin, vnew, rho
+        where the bands live)."""
+        lat = _f64(lat, 9)
+        g = np.ascontiguousarray(grid, dtype=np.int32)
+        kp = _f64(kpts).reshape(-1, 3)
+        nk = kp.shape[0]
+        nb = np.ascontiguousarray([int(p.shape[0]) for p in psis], dtype=np.int32)
+        ws = [_f64(w) for w in weights]
+        ptrs, mems = [], set()
+        for p in psis:
+            pp, mp = _ptr(p)
+            ptrs.append(pp)
+            mems.add(mp)
+        pe, me = _ptr(vext)
+        pi_, mi = _ptr(vin)
+        pn, mn = _ptr(vnew)
+        pr_, mr = _ptr(rho)
+        if len({me, mi, mn} | mems | ({mr} if rho is not None else set())) != 1:
+            raise ValueError("bands, potentials and rho must live in the same memory")
+        parr = (_P * max(nk, 1))(*ptrs)
+        warr = (_P * max(nk, 1))(*[ctypes.c_void_p(w.ctypes.data) for w in ws])
+        _check(_lib.qe_scf_step(self._h, _dptr(lat), float(ecut), g.ctypes.data_as(_I), nk, _dptr(kp),
+                                nb.ctypes.data_as(_I), parr, warr, pe, pi_, float(alpha),
+                                int(precision), pn, pr_, mn, _stream(stream, vnew)))
+        return vnew
 
     def davidson_batch(self, probs, psis, evals, resids=None, precision=QE_FP64, tol=1e-8,
                        max_iter=100, max_dim=0, stream=None):

@@ -256,6 +256,10 @@ int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView
   return QE_OK;
 }
 
+template <typename T>
+static int hpsi_device_nonlocal(qe_ctx* ctx, const DevPlan& P, const OpView& op, const double* psi,
+                                double* hpsi, int nb, cudaStream_t st, bool pair);
+
 // pair: the bands are real in r (k = 0 plan); two share each FFT and the
 // projections are taken real.
 template <typename T>
@@ -282,6 +286,25 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
                                    &ctx->prof, pair ? 1 : 0));
   }
   if (op.ready) QE_CU(cudaStreamWaitEvent(st, op.ready, 0));
+  const bool use_oz = op.nproj > 0 && !std::is_same<T, float>::value && oz_worth(op.nproj, nb, npw);
+  if (op.gen && op.nproj > 0 && !use_oz) {
+    // generated projectors on the paths that read beta values: generate them here
+    QE_TRY(ctx->gen_beta.ensure((size_t)op.nproj * npw * 2 * sizeof(double)));
+    QE_TRY(gen_beta_values(*op.gen, (double*)ctx->gen_beta.p, st, &ctx->prof));
+    OpView o2 = op;
+    o2.gen = nullptr;
+    o2.beta = (const double*)ctx->gen_beta.p;
+    o2.tag = ++ctx->op_tag;
+    return hpsi_device_nonlocal<T>(ctx, P, o2, psi, hpsi, nb, st, pair);
+  }
+  return hpsi_device_nonlocal<T>(ctx, P, op, psi, hpsi, nb, st, pair);
+}
+
+// The nonlocal term of hpsi_device.
+template <typename T>
+static int hpsi_device_nonlocal(qe_ctx* ctx, const DevPlan& P, const OpView& op, const double* psi,
+                                double* hpsi, int nb, cudaStream_t st, bool pair) {
+  const int npw = P.h.npw;
   if (op.nproj > 0 && std::is_same<T, float>::value) {
     // mixed precision: projector products on the tensor cores (TF32x3 split)
     const int np = op.nproj;
@@ -312,7 +335,12 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
     QE_TRY(ctx->oz_beta.ensure(nonlocal_oz_beta_bytes(np, npw)));
     if (ctx->oz_beta.p != before || ctx->oz_beta.bytes != before_bytes) ctx->oz_beta_tag = 0;
     const bool slice = ctx->oz_beta_tag == 0 || ctx->oz_beta_tag != op.tag;
-    QE_TRY(nonlocal_oz(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->oz_beta.p, slice,
+    if (op.gen && slice) {
+      // projectors generated on the fly straight into the slices: no beta array
+      QE_TRY(ctx->gen_scr.ensure(oz_gen_scratch_bytes(*op.gen)));
+      QE_TRY(oz_gen_beta(*op.gen, ctx->oz_beta.p, ctx->gen_scr.p, st, &ctx->prof));
+    }
+    QE_TRY(nonlocal_oz(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->oz_beta.p, slice && !op.gen,
                        ctx->oz_work.p, ctx->oz_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof,
                        pair));
     ctx->oz_beta_tag = op.tag;
@@ -390,6 +418,11 @@ void qe_ctx_destroy(qe_ctx* ctx) {
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_op);
   }
+  for (void* x : ctx->round_side) {
+    cudaStreamSynchronize((cudaStream_t)x);
+    cudaStreamDestroy((cudaStream_t)x);
+  }
+  for (void* e : ctx->round_events) cudaEventDestroy((cudaEvent_t)e);
   delete ctx;
 }
 

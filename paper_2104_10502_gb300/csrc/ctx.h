@@ -21,8 +21,13 @@ struct qe_ctx {
   qe::DevBuf h_v, h_beta, h_d, h_psi, h_hpsi;
   // Davidson workspaces
   qe::DevBuf dv_basis, dv_red;
-  // charge density: per-group accumulators and the band weights
-  qe::DevBuf dens_acc, dens_w;
+  // charge density: per-group accumulators and the band weights; the
+  // self-consistency step's work
+  qe::DevBuf dens_acc, dens_w, scf_work;
+  // generated projectors: Miller indices of a plan's sphere, phase tables,
+  // radial table copy, exponent scratch, beta values for the non-sliced paths
+  qe::DevBuf gen_mill, gen_tab, gen_rad, gen_scr, gen_beta;
+  const void* gen_mill_plan = nullptr;
   // tensor-core path: packed operands and the kernel's status word (a bounded
   // wait that ran out writes a non-zero code; read at the next synchronising point)
   qe::DevBuf tc_work, tc_status, tc_beta;
@@ -48,6 +53,9 @@ struct qe_ctx {
   std::shared_ptr<void> batch;
   // per-solve Davidson workspaces of a batched solve (basis, reduced matrices)
   std::vector<std::unique_ptr<qe::DevBuf>> dvb_basis, dvb_red;
+  // side streams and fork/join events of lockstep Davidson rounds (created on
+  // first use; cudaStream_t / cudaEvent_t values)
+  std::vector<void*> round_side, round_events;
   // test hook (qe_test_grid_wait): when non-zero, the grid barriers of this
   // context's Davidson solves wait for an arrival that never comes, bounded by
   // this many nanoseconds, so that every one of them runs out
@@ -58,7 +66,8 @@ struct qe_ctx {
   std::vector<qe::DevBuf*> bufs() {
     return {&sticks, &vp,       &part,     &proj,   &projd,   &h_v,     &h_beta,
             &h_d,    &h_psi,    &h_hpsi,   &dv_basis, &dv_red, &tc_work, &tc_status, &tc_beta,
-            &oz_beta, &oz_work, &dens_acc, &dens_w};
+            &oz_beta, &oz_work, &dens_acc, &dens_w, &scf_work, &gen_mill, &gen_tab, &gen_rad,
+            &gen_scr, &gen_beta};
   }
 };
 
@@ -73,6 +82,8 @@ struct OpView {
   // set when beta and D are still being copied on the context's side stream:
   // the projector products wait for it
   cudaEvent_t ready = nullptr;
+  // projectors generated on the fly (qe_hpsi_gen): beta is not stored
+  const GenProj* gen = nullptr;
 };
 
 // Start of an API call on stream st (see qe_ctx::cur).

@@ -1484,10 +1484,11 @@ struct DvTask {
 };
 
 int dv_task_create(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int max_iter,
-                   const double* psi0, void* stream, DvTask** out) {
+                   int max_dim, const double* psi0, void* stream, DvTask** out) {
   *out = nullptr;
-  DV_TRY(check_problem(prob, "qe_serve"));
-  if (prob->mem != QE_HOST || !psi0) { set_error("qe_serve: host arrays expected"); return QE_EINVAL; }
+  DV_TRY(check_problem(prob, "dv_task"));
+  if (!psi0) { set_error("dv_task: null start bands"); return QE_EINVAL; }
+  const bool dev_in = prob->mem == QE_DEVICE;
   const int flags = precision & (QE_GAMMA | QE_NO_GAMMA | QE_RR_FP32);
   precision &= ~(QE_GAMMA | QE_NO_GAMMA | QE_RR_FP32);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1495,27 +1496,31 @@ int dv_task_create(qe_ctx* ctx, const qe_problem* prob, int precision, double to
   DV_TRY(get_plan(ctx, prob->lat, prob->k, prob->ecutwfc, prob->grid, &P));
   auto t = std::make_unique<DvTask>();
   t->cur = st;
-  const size_t ngrid = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
-  const size_t nbeta = (size_t)prob->nproj * P->h.npw * 2, nd = (size_t)prob->nproj * prob->nproj;
-  const size_t ov = (ngrid * sizeof(double) + 255) & ~(size_t)255;
-  const size_t ob = (nbeta * sizeof(double) + 255) & ~(size_t)255;
-  DV_TRY(t->opbuf.ensure(ov + ob + nd * sizeof(double) + 256));
-  char* base = static_cast<char*>(t->opbuf.p);
-  DV_CU(cudaMemcpyAsync(base, prob->vloc_r, ngrid * sizeof(double), cudaMemcpyHostToDevice, st));
-  if (prob->nproj > 0) {
-    DV_CU(cudaMemcpyAsync(base + ov, prob->beta, nbeta * sizeof(double), cudaMemcpyHostToDevice, st));
-    DV_CU(cudaMemcpyAsync(base + ov + ob, prob->dmat, nd * sizeof(double), cudaMemcpyHostToDevice, st));
-  }
   t->prob = *prob;
-  t->prob.vloc_r = reinterpret_cast<const double*>(base);
-  t->prob.beta = prob->nproj > 0 ? reinterpret_cast<const double*>(base + ov) : nullptr;
-  t->prob.dmat = prob->nproj > 0 ? reinterpret_cast<const double*>(base + ov + ob) : nullptr;
-  t->prob.mem = QE_DEVICE;
-  DV_TRY(dv_setup(ctx, &t->prob, precision, tol, max_iter, 0, t->basis, t->red, t->v, st, "qe_serve",
-                  gamma_mode(precision, flags, prob->grid)));
+  if (!dev_in) {
+    // host operator: device copies owned by the task
+    const size_t ngrid = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
+    const size_t nbeta = (size_t)prob->nproj * P->h.npw * 2, nd = (size_t)prob->nproj * prob->nproj;
+    const size_t ov = (ngrid * sizeof(double) + 255) & ~(size_t)255;
+    const size_t ob = (nbeta * sizeof(double) + 255) & ~(size_t)255;
+    DV_TRY(t->opbuf.ensure(ov + ob + nd * sizeof(double) + 256));
+    char* base = static_cast<char*>(t->opbuf.p);
+    DV_CU(cudaMemcpyAsync(base, prob->vloc_r, ngrid * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (prob->nproj > 0) {
+      DV_CU(cudaMemcpyAsync(base + ov, prob->beta, nbeta * sizeof(double), cudaMemcpyHostToDevice, st));
+      DV_CU(cudaMemcpyAsync(base + ov + ob, prob->dmat, nd * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    t->prob.vloc_r = reinterpret_cast<const double*>(base);
+    t->prob.beta = prob->nproj > 0 ? reinterpret_cast<const double*>(base + ov) : nullptr;
+    t->prob.dmat = prob->nproj > 0 ? reinterpret_cast<const double*>(base + ov + ob) : nullptr;
+    t->prob.mem = QE_DEVICE;
+  }
+  DV_TRY(dv_setup(ctx, &t->prob, precision, tol, max_iter, max_dim, t->basis, t->red, t->v, st,
+                  "dv_task", gamma_mode(precision, flags, prob->grid)));
   t->v.mixed_rr32 = (flags & QE_RR_FP32) != 0;
   DvState& S = t->v.S;
-  DV_CU(cudaMemcpyAsync(S.V, psi0, (size_t)S.nb * S.npw * sizeof(z), cudaMemcpyHostToDevice, st));
+  DV_CU(cudaMemcpyAsync(S.V, psi0, (size_t)S.nb * S.npw * sizeof(z),
+                        dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   DV_TRY(dv_begin(t->v, st));
   t->phase = DV_FIRST_H;
   t->h_prec = precision;
@@ -1633,19 +1638,20 @@ int dv_round(qe_ctx* ctx, DvTask* const* tasks, int n, void* stream, void* const
 }
 
 int dv_task_result(qe_ctx* ctx, DvTask* t, double* psi, double* evals, double* resid, int* iters,
-                   void* stream) {
+                   bool device_out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   DvSolve& v = t->v;
   DvState& S = v.S;
+  const cudaMemcpyKind kind = device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (iters) *iters = v.it;
   if (t->rc != QE_OK && t->rc != QE_ENOCONV) return t->rc;
-  if (psi) DV_CU(cudaMemcpyAsync(psi, S.Psi, (size_t)S.nb * S.npw * sizeof(z), cudaMemcpyDeviceToHost, st));
-  if (evals) DV_CU(cudaMemcpyAsync(evals, S.e, S.nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (resid) DV_CU(cudaMemcpyAsync(resid, S.rn, S.nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-  DV_TRY(dv_final_status(v, st, "qe_serve"));
+  if (psi) DV_CU(cudaMemcpyAsync(psi, S.Psi, (size_t)S.nb * S.npw * sizeof(z), kind, st));
+  if (evals) DV_CU(cudaMemcpyAsync(evals, S.e, S.nb * sizeof(double), kind, st));
+  if (resid) DV_CU(cudaMemcpyAsync(resid, S.rn, S.nb * sizeof(double), kind, st));
+  DV_TRY(dv_final_status(v, st, "davidson"));
   if (t->rc == QE_ENOCONV) return QE_ENOCONV;
   if (!v.conv) {
-    set_error("qe_serve: not converged after %d iterations", v.it);
+    set_error("davidson: not converged after %d iterations", v.it);
     return QE_ENOCONV;
   }
   return QE_OK;
@@ -1736,52 +1742,57 @@ extern "C" int qe_davidson_batch(qe_ctx* ctx, int nprob, const qe_problem* probs
   DV_CU(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   DV_TRY(ctx_begin(ctx, st));
-  // the solves with bands, each with its own workspace
-  std::vector<int> ids;
-  for (int p = 0; p < nprob; ++p)
-    if (probs[p].nbnd > 0) ids.push_back(p);
-  const int ns = (int)ids.size();
-  while ((int)ctx->dvb_basis.size() < ns) {
-    ctx->dvb_basis.push_back(std::make_unique<DevBuf>());
-    ctx->dvb_red.push_back(std::make_unique<DevBuf>());
-    ctx->dvb_basis.back()->sp = &ctx->cur;
-    ctx->dvb_red.back()->sp = &ctx->cur;
-  }
-  std::vector<DvSolve> vs(ns);
-  std::vector<qe_problem> sub(ns);
-  for (int i = 0; i < ns; ++i) {
-    const int p = ids[i];
-    sub[i] = probs[p];
-    DV_TRY(dv_setup(ctx, &probs[p], precision, tol, max_iter, max_dim, *ctx->dvb_basis[i],
-                    *ctx->dvb_red[i], vs[i], st, "qe_davidson_batch",
-                    gamma_mode(precision, flags, probs[p].grid)));
-    vs[i].mixed_rr32 = (flags & QE_RR_FP32) != 0;
-    DV_CU(cudaMemcpyAsync(vs[i].S.V, psi_inout[p], (size_t)vs[i].S.nb * vs[i].S.npw * sizeof(z),
-                          cudaMemcpyDeviceToDevice, st));
-  }
-  std::vector<int> rcs(ns, QE_OK);
-  DV_TRY(precision == QE_FP64 ? davidson_batch_run<double>(ctx, vs, sub, st, rcs)
-                              : davidson_batch_run<float>(ctx, vs, sub, st, rcs));
-  int worst = QE_OK;
-  for (int i = 0; i < ns; ++i) {
-    const int p = ids[i];
-    DvSolve& v = vs[i];
-    int rc = rcs[i];
-    if (iters) iters[p] = v.it;
-    if (rc == QE_OK || rc == QE_ENOCONV) {
-      const int nb = v.S.nb;
-      DV_CU(cudaMemcpyAsync(psi_inout[p], v.S.Psi, (size_t)nb * v.S.npw * sizeof(z),
-                            cudaMemcpyDeviceToDevice, st));
-      DV_CU(cudaMemcpyAsync(evals[p], v.S.e, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      if (resid && resid[p])
-        DV_CU(cudaMemcpyAsync(resid[p], v.S.rn, nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      const int frc = dv_final_status(v, st, "qe_davidson_batch");
-      if (frc) rc = frc;
-      else if (rc == QE_OK && !v.conv) rc = QE_ENOCONV;
+  // one lockstep task per solve with bands; the Rayleigh-Ritz steps of a round
+  // run on the context's side streams, so that the dense eigensolvers of
+  // different solves overlap
+  constexpr int kSide = 8;
+  if (ctx->round_side.empty()) {
+    for (int i = 0; i < kSide; ++i) {
+      cudaStream_t x = nullptr;
+      DV_CU(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+      ctx->round_side.push_back(x);
     }
+    for (int i = 0; i <= kSide; ++i) {
+      cudaEvent_t e = nullptr;
+      DV_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      ctx->round_events.push_back(e);
+    }
+  }
+  std::vector<int> ids;
+  std::vector<DvTask*> tasks;
+  auto cleanup = [&] {
+    for (DvTask* t : tasks) dv_task_destroy(t, st);
+    tasks.clear();
+  };
+  int worst = QE_OK;
+  for (int p = 0; p < nprob; ++p) {
+    if (probs[p].nbnd <= 0) continue;
+    DvTask* t = nullptr;
+    const int rc = dv_task_create(ctx, &probs[p], precision | flags, tol, max_iter, max_dim,
+                                  psi_inout[p], st, &t);
+    if (rc) { cleanup(); return rc; }
+    ids.push_back(p);
+    tasks.push_back(t);
+  }
+  while (true) {
+    std::vector<DvTask*> live;
+    for (DvTask* t : tasks)
+      if (!dv_task_done(t)) live.push_back(t);
+    if (live.empty()) break;
+    const int rc = dv_round(ctx, live.data(), (int)live.size(), st, ctx->round_side.data(),
+                            (int)ctx->round_side.size(), ctx->round_events.data());
+    if (rc) { cleanup(); return rc; }
+  }
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    const int p = ids[i];
+    int it = 0;
+    const int rc = dv_task_result(ctx, tasks[i], psi_inout[p], evals[p], resid ? resid[p] : nullptr,
+                                  &it, true, st);
+    if (iters) iters[p] = it;
     if (status) status[p] = rc;
     if (rc != QE_OK && (worst == QE_OK || worst == QE_ENOCONV)) worst = rc;
   }
+  cleanup();
   DV_TRY(tc_check(ctx, st));
   if (worst == QE_ENOCONV) set_error("qe_davidson_batch: some problems did not converge");
   return worst;

@@ -11,12 +11,14 @@ namespace qe {
 
 struct DvTask;
 
-// A solve of the problem described by host arrays (prob->mem = QE_HOST; copied
-// to device buffers the task owns, ordered on `stream`), psi0 [nbnd][npw][2]
-// host.  precision: QE_FP64 or QE_MIXED with the qe_davidson flags.  The task
-// starts with its first H product pending.
+// A solve of prob: host arrays (prob->mem = QE_HOST) are copied to device
+// buffers the task owns, device arrays are used in place (they must outlive
+// the task); psi0 [nbnd][npw][2] lives where prob's arrays do.  precision:
+// QE_FP64 or QE_MIXED with the qe_davidson flags; max_dim as qe_davidson's
+// (0: default).  Ordered on `stream`; the task starts with its first H
+// product pending.
 int dv_task_create(qe_ctx* ctx, const qe_problem* prob, int precision, double tol, int max_iter,
-                   const double* psi0, void* stream, DvTask** out);
+                   int max_dim, const double* psi0, void* stream, DvTask** out);
 // One round for every unfinished task: the pending H products of all of them
 // in one batched call per precision on `stream`, then one Rayleigh-Ritz step
 // each, task i on side[i % nside] (cudaStream_t values; ordered after the H
@@ -27,10 +29,11 @@ int dv_task_create(qe_ctx* ctx, const qe_problem* prob, int precision, double to
 int dv_round(qe_ctx* ctx, DvTask* const* tasks, int n, void* stream, void* const* side, int nside,
              void* const* events);
 bool dv_task_done(const DvTask* t);
-// Results of a finished task into host arrays (any may be NULL); returns its
+// Results of a finished task into host arrays, or device arrays with
+// device_out (any may be NULL); returns its
 // status (QE_OK, QE_ENOCONV or the error that ended it; the message is set).
 int dv_task_result(qe_ctx* ctx, DvTask* t, double* psi, double* evals, double* resid, int* iters,
-                   void* stream);
+                   bool device_out, void* stream);
 // Frees the task's device buffers (stream-ordered on `stream`).
 void dv_task_destroy(DvTask* t, void* stream);
 

@@ -515,7 +515,7 @@ constexpr int kDensThreads = 512;
 template <typename T, int N>
 __device__ void dens_plane_tile_sq(const FftJob<T>& J, int grp, int ngrp, int pz,
                                    const double* __restrict__ w, double* __restrict__ acc,
-                                   unsigned char* smem) {
+                                   int mode, unsigned char* smem) {
   constexpr int A = SqSplit<N>::A, B = SqSplit<N>::B, ld = N | 1, n12 = N * N;
   const int n3 = J.r3.n, nst = J.nst, nt = blockDim.x;
   cx<T>* plane = reinterpret_cast<cx<T>*>(smem);
@@ -563,7 +563,7 @@ __device__ void dens_plane_tile_sq(const FftJob<T>& J, int grp, int ngrp, int pz
           const int y = fn.div(i), x = i - y * N;
           double re, im;
           cx_to<T>(plane[y * ld + x], re, im);
-          racc[k] += J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im);
+          racc[k] += mode ? wa * re : (J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im));
         }
       }
     } else {
@@ -571,7 +571,7 @@ __device__ void dens_plane_tile_sq(const FftJob<T>& J, int grp, int ngrp, int pz
         const int y = fn.div(i), x = i - y * N;
         double re, im;
         cx_to<T>(plane[y * ld + x], re, im);
-        accp[i] += J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im);
+        accp[i] += mode ? wa * re : (J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im));
       }
     }
   }
@@ -587,8 +587,8 @@ __device__ void dens_plane_tile_sq(const FftJob<T>& J, int grp, int ngrp, int pz
 template <typename T>
 __device__ void dens_plane_tile(const FftJob<T>& J, int grp, int ngrp, int pz,
                                 const double* __restrict__ w, double* __restrict__ acc,
-                                unsigned char* smem) {
-#define QE_SQ_DENS(n) dens_plane_tile_sq<T, n>(J, grp, ngrp, pz, w, acc, smem)
+                                int mode, unsigned char* smem) {
+#define QE_SQ_DENS(n) dens_plane_tile_sq<T, n>(J, grp, ngrp, pz, w, acc, mode, smem)
   QE_SQ_DISPATCH(QE_SQ_DENS)
 #undef QE_SQ_DENS
   const int n1 = J.r1.n, n2 = J.r2.n, n3 = J.r3.n, nst = J.nst, nax = J.nax;
@@ -637,7 +637,7 @@ __device__ void dens_plane_tile(const FftJob<T>& J, int grp, int ngrp, int pz,
           const int y = fn1.div(i), x = i - y * n1;
           double re, im;
           cx_to<T>(plane[y * ld + x], re, im);
-          racc[k] += J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im);
+          racc[k] += mode ? wa * re : (J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im));
         }
       }
     } else {
@@ -645,7 +645,7 @@ __device__ void dens_plane_tile(const FftJob<T>& J, int grp, int ngrp, int pz,
         const int y = fn1.div(i), x = i - y * n1;
         double re, im;
         cx_to<T>(plane[y * ld + x], re, im);
-        accp[i] += J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im);
+        accp[i] += mode ? wa * re : (J.pair ? wa * re * re + wb * im * im : wa * (re * re + im * im));
       }
     }
   }
@@ -658,12 +658,14 @@ __device__ void dens_plane_tile(const FftJob<T>& J, int grp, int ngrp, int pz,
   }
 }
 
+// mode 0: acc += w |psi(r)|^2 (the density); mode 1: acc += w Re psi(r) (the
+// inverse transform of one band to the grid)
 template <typename T>
 __global__ void __launch_bounds__(kDensThreads) k_dens_plane(const FftJob<T> J, int ngrp,
                                                             const double* __restrict__ w,
-                                                            double* __restrict__ acc) {
+                                                            double* __restrict__ acc, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  dens_plane_tile<T>(J, blockIdx.y, ngrp, blockIdx.x, w, acc, smem_raw);
+  dens_plane_tile<T>(J, blockIdx.y, ngrp, blockIdx.x, w, acc, mode, smem_raw);
 }
 
 // rho[perm3[pz]][perm2[py]][perm1[px]] = scale * sum_g acc[g][pz][py][px]
@@ -888,7 +890,7 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
 // inverse planes.  pair: k = 0 bands real in r, two per FFT.
 template <typename T>
 int launch_density(const DevPlan& P, const double* psi, const double* w, void* Wv, int b0, int nbc,
-                   int ngrp, double* acc, cudaStream_t st, Prof* pf, int pair) {
+                   int ngrp, double* acc, cudaStream_t st, Prof* pf, int pair, int mode) {
   const FftShape sh = tuned_shape(P, sizeof(T));
   const FftJob<T> J = make_job<T>(P, psi, nullptr, nullptr, Wv, b0, nbc, sh, pair);
   const size_t zsm = zsm_bytes<T>(P.grid[2], J.spb);
@@ -911,7 +913,7 @@ int launch_density(const DevPlan& P, const double* psi, const double* w, void* W
   }
   if (rc) return rc;
   ProfScope ps(pf, "k_dens_plane", st);
-  k_dens_plane<T><<<dim3(P.grid[2], ngrp), kDensThreads, psm, st>>>(J, ngrp, w, acc);
+  k_dens_plane<T><<<dim3(P.grid[2], ngrp), kDensThreads, psm, st>>>(J, ngrp, w, acc, mode);
   return check_launch("k_dens_plane");
 }
 
@@ -939,7 +941,7 @@ int launch_density_finish(const DevPlan& P, const double* acc, int ngrp, double 
   template size_t zsm_bytes<T>(int, int);                                                          \
   template size_t psm_bytes<T>(const DevPlan&);                                                    \
   template int launch_density<T>(const DevPlan&, const double*, const double*, void*, int, int,    \
-                                 int, double*, cudaStream_t, Prof*, int);
+                                 int, double*, cudaStream_t, Prof*, int, int);
 QE_FFT_INSTANTIATE(double)
 QE_FFT_INSTANTIATE(float)
 QE_FFT_INSTANTIATE(ff)

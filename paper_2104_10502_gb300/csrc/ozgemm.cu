@@ -649,6 +649,178 @@ int oz_slice_cols(const double* src, int ld, int K, int cols, int form, void* me
   return oz_check("k_oz_slice_cols");
 }
 
+// ---- projectors generated on the fly, straight into the slices -------------------
+// One thread per (atom, plane wave) forms the atom's structure factor once,
+//   S = e^{-i k.R} T_x[m_x] T_y[m_y] T_z[m_z],   T_c[m] = e^{-i 2 pi m f_c},
+// and from it every projector of the atom, beta = S (-i)^l Y_lc(q) F_n(G),
+// which it cuts into the row slices (inner product: row = projector) and the
+// column slices (outer product: row = plane wave) at once.  No beta array is
+// read or written.  The exponents come from bounds that do not depend on the
+// atom (|S| = 1): per projector component, max over G of |Y_lc(q) F_n(G)|; per
+// plane wave, the max over the components; each times (1 + 2^-40), which covers
+// the rounding of S, so that every sliced value is below 2^e.
+__device__ __forceinline__ void gen_q(const GenProj& g, int G, double q[3]) {
+  const int m0 = g.mill[3 * G], m1 = g.mill[3 * G + 1], m2 = g.mill[3 * G + 2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) q[c] = ((g.k[c] + m0 * g.b[c]) + m1 * g.b[3 + c]) + m2 * g.b[6 + c];
+}
+
+// |Y_lc(q)| F_n(G) (the magnitude of every projector component at G)
+__device__ __forceinline__ double gen_amp(const GenProj& g, int n, int c, int G, const double q[3]) {
+  const double f = fabs(g.radial[(size_t)n * g.npw + G]);
+  if (g.l[n] == 0) return 0.28209479177387814347 * f;           // 1 / (2 sqrt(pi))
+  return 0.48860251190291992159 * fabs(q[c]) * f;                // sqrt(3 / (4 pi)) |q_c|
+}
+
+// Exponent bounds.  grid (ceil(npw / 256), 1): per-G column exponents, and the
+// per-component maxima merged with atomicMax (as ordered bit patterns) into cmax.
+__global__ void k_gen_exps(GenProj g, unsigned long long* __restrict__ cmax, int* __restrict__ ecol) {
+  const int G = blockIdx.x * blockDim.x + threadIdx.x;
+  if (G >= g.npw) return;
+  double q[3];
+  gen_q(g, G, q);
+  double mx = 0.0;
+  int j = 0;
+  for (int n = 0; n < g.nrad; ++n)
+    for (int c = 0; c < 2 * g.l[n] + 1; ++c, ++j) {
+      const double a = gen_amp(g, n, c, G, q);
+      mx = fmax(mx, a);
+      atomicMax(&cmax[j], mag_bits(a));
+    }
+  ecol[G] = mx > 0.0 ? exp_bound(mx * (1.0 + 0x1p-40)) : (int)0x80808080;
+}
+
+// Row exponents of every projector from the component maxima.
+__global__ void k_gen_erow(GenProj g, const unsigned long long* __restrict__ cmax, int* __restrict__ erow) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.np) return;
+  const double a = __longlong_as_double((long long)cmax[i % g.nper]);
+  erow[i] = a > 0.0 ? exp_bound(a * (1.0 + 0x1p-40)) : (int)0x80808080;
+}
+
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// beta of atom I at plane wave G for every projector of the atom, handed to f(i, beta)
+template <typename F>
+__device__ __forceinline__ void gen_atom(const GenProj& g, int I, int G, F&& f) {
+  double q[3];
+  gen_q(g, G, q);
+  const double2* tab = reinterpret_cast<const double2*>(g.tab) + (size_t)I * g.tstride;
+  const int m0 = g.mill[3 * G], m1 = g.mill[3 * G + 1], m2 = g.mill[3 * G + 2];
+  double2 S = reinterpret_cast<const double2*>(g.ekr)[I];
+  S = cmul2(S, tab[g.toff[0] + m0 + g.half[0]]);
+  S = cmul2(S, tab[g.toff[1] + m1 + g.half[1]]);
+  S = cmul2(S, tab[g.toff[2] + m2 + g.half[2]]);
+  for (int n = 0; n < g.nrad; ++n) {
+    const double F = g.radial[(size_t)n * g.npw + G];
+    if (g.l[n] == 0) {
+      const double a = 0.28209479177387814347 * F;
+      f(I * g.nper + g.off[n], make_double2(S.x * a, S.y * a));
+    } else {
+      for (int c = 0; c < 3; ++c) {
+        const double a = 0.48860251190291992159 * q[c] * F;
+        f(I * g.nper + g.off[n] + c, make_double2(S.y * a, -S.x * a));   // (-i) S a
+      }
+    }
+  }
+}
+
+// Both slicings.  grid (ceil(npw / 128), natom); A1: [S][rows_p1][Kp1] (row i,
+// K pair (2G, 2G+1)); A2: [S][rows_p2][Kp2] (row G, K pair (2i, 2i+1)).
+__global__ void __launch_bounds__(128) k_gen_slices(GenProj g, const int* __restrict__ erow,
+                                                    const int* __restrict__ ecol, int rows_p1, int Kp1,
+                                                    unsigned* __restrict__ Q1, int rows_p2, int Kp2,
+                                                    unsigned* __restrict__ Q2) {
+  const int G = blockIdx.x * blockDim.x + threadIdx.x, I = blockIdx.y;
+  if (G >= g.npw) return;
+  const size_t s1 = (size_t)rows_p1 * Kp1 / 2, s2 = (size_t)rows_p2 * Kp2 / 2;
+  const int ec = oz_exp(ecol[G]);
+  gen_atom(g, I, G, [&](int i, double2 v) {
+    unsigned short qx[OZ_S], qy[OZ_S];
+    const int er = oz_exp(erow[i]);
+    slices_of(v.x, er, qx);
+    slices_of(v.y, er, qy);
+    unsigned* p1 = Q1 + (size_t)i * (Kp1 / 2) + G;
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) p1[t * s1] = pack2(qx[t], qy[t]);
+    slices_of(v.x, ec, qx);
+    slices_of(v.y, ec, qy);
+    unsigned* p2 = Q2 + (size_t)G * (Kp2 / 2) + i;
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) p2[t * s2] = pack2(qx[t], qy[t]);
+  });
+}
+
+// Zero the rectangle [r0, r1) x [c0, c1) (uint32 units) of every slice.
+__global__ void k_zero_rect(unsigned* __restrict__ Q, size_t slice, int ld, int r0, int r1, int c0,
+                            int c1) {
+  const size_t w = (size_t)(c1 - c0), total = (size_t)(r1 - r0) * w * OZ_S;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = t / ((size_t)(r1 - r0) * w), rem = t % ((size_t)(r1 - r0) * w);
+    const int r = r0 + (int)(rem / w), c = c0 + (int)(rem % w);
+    Q[s * slice + (size_t)r * ld + c] = 0u;
+  }
+}
+
+static int zero_rect(unsigned* Q, size_t slice, int ld, int r0, int r1, int c0, int c1, cudaStream_t st) {
+  if (r1 <= r0 || c1 <= c0) return QE_OK;
+  const size_t total = (size_t)(r1 - r0) * (c1 - c0) * OZ_S;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
+  k_zero_rect<<<blocks, 256, 0, st>>>(Q, slice, ld, r0, r1, c0, c1);
+  return oz_check("k_zero_rect");
+}
+
+size_t oz_gen_scratch_bytes(const GenProj& g) {
+  return up256((size_t)g.nper * sizeof(unsigned long long)) + 256;
+}
+
+int oz_gen_beta(const GenProj& g, void* bslices, void* scratch, cudaStream_t st, Prof* pf) {
+  if (g.np <= 0 || g.npw <= 0) return QE_OK;
+  char* bs = static_cast<char*>(bslices);
+  const OzOperand A1 = oz_carve(bs, g.np, g.npw);
+  const OzOperand A2 = oz_carve(bs + oz_operand_bytes(g.np, g.npw), g.npw, g.np);
+  unsigned long long* cmax = static_cast<unsigned long long*>(scratch);
+  ProfScope ps(pf, "k_gen_slices", st);
+  if (cudaMemsetAsync(cmax, 0, (size_t)g.nper * sizeof(unsigned long long), st) != cudaSuccess) {
+    set_error("oz_gen_beta: memset failed");
+    return QE_ECUDA;
+  }
+  k_gen_exps<<<(g.npw + 255) / 256, 256, 0, st>>>(g, cmax, A2.e);
+  k_gen_erow<<<(g.np + 255) / 256, 256, 0, st>>>(g, cmax, A1.e);
+  int rc = oz_check("k_gen_exps");
+  if (rc) return rc;
+  unsigned* Q1 = reinterpret_cast<unsigned*>(A1.q);
+  unsigned* Q2 = reinterpret_cast<unsigned*>(A2.q);
+  const size_t s1 = (size_t)A1.rows_p * A1.Kp / 2, s2 = (size_t)A2.rows_p * A2.Kp / 2;
+  // the padding of both slicings, then the values
+  if ((rc = zero_rect(Q1, s1, A1.Kp / 2, g.np, A1.rows_p, 0, A1.Kp / 2, st)) ||
+      (rc = zero_rect(Q1, s1, A1.Kp / 2, 0, g.np, g.npw, A1.Kp / 2, st)) ||
+      (rc = zero_rect(Q2, s2, A2.Kp / 2, g.npw, A2.rows_p, 0, A2.Kp / 2, st)) ||
+      (rc = zero_rect(Q2, s2, A2.Kp / 2, 0, g.npw, g.np, A2.Kp / 2, st)))
+    return rc;
+  k_gen_slices<<<dim3((g.npw + 127) / 128, g.natom), 128, 0, st>>>(g, A1.e, A2.e, A1.rows_p, A1.Kp,
+                                                                    Q1, A2.rows_p, A2.Kp, Q2);
+  if (pf) pf->launches += 6;
+  return oz_check("k_gen_slices");
+}
+
+// The generated beta as values (row i = projector, complex [np][npw]).
+__global__ void __launch_bounds__(128) k_gen_values(GenProj g, double2* __restrict__ beta) {
+  const int G = blockIdx.x * blockDim.x + threadIdx.x, I = blockIdx.y;
+  if (G >= g.npw) return;
+  gen_atom(g, I, G, [&](int i, double2 v) { beta[(size_t)i * g.npw + G] = v; });
+}
+
+int gen_beta_values(const GenProj& g, double* beta, cudaStream_t st, Prof* pf) {
+  if (g.np <= 0 || g.npw <= 0) return QE_OK;
+  ProfScope ps(pf, "k_gen_values", st);
+  k_gen_values<<<dim3((g.npw + 127) / 128, g.natom), 128, 0, st>>>(g, reinterpret_cast<double2*>(beta));
+  return oz_check("k_gen_values");
+}
+
 // K splits: as many CTAs as fit in ONE wave (one CTA per SM: the kernel holds
 // all of TMEM and ~195 KB of shared memory), at least one chunk each.
 static int oz_splits(int tiles, int nks) {

@@ -170,9 +170,10 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
 // positions; zeroed by the caller before the first launch); W as for
 // launch_local_kinetic.  launch_density_finish writes rho [N3][N2][N1] (natural
 // order) = scale * the sum of the groups.
+// mode 1: acc += w Re psi(r) instead (the inverse transform of the bands to the grid).
 template <typename T>
 int launch_density(const DevPlan& P, const double* psi, const double* w, void* W, int b0, int nbc,
-                   int ngrp, double* acc, cudaStream_t st, Prof* pf, int pair = 0);
+                   int ngrp, double* acc, cudaStream_t st, Prof* pf, int pair = 0, int mode = 0);
 int launch_density_finish(const DevPlan& P, const double* acc, int ngrp, double scale, double* rho,
                           cudaStream_t st, Prof* pf);
 
@@ -233,6 +234,33 @@ int nonlocal_tc(const double* beta, const double* dmat, const double* psi, doubl
 // with real projectors at k = 0, where P is real up to rounding).
 int dmul(const double* D, const double* P, double* Q, int np, int nb, cudaStream_t st, Prof* pf,
          bool real_p = false);
+
+// ---- projectors generated on the fly (betagen.cu) ------------------------------
+// beta_{I,n,c}(G) = e^{-i q.R_I} (-i)^{l_n} Y_{l_n c}(q) F_n(G), q = k + G, with
+// the structure factor from per-atom, per-axis phase tables (the separable
+// e^{-iG.R_I} = prod_c e^{-i 2 pi m_c f_Ic}) times e^{-i k.R_I}, the real solid
+// harmonic Y_00 = 1/(2 sqrt pi), Y_1c = sqrt(3/4pi) q_c, and the caller's radial
+// table F_n(G).  Projector order: atom-major; per atom, per radial function n
+// its 2 l_n + 1 components.
+constexpr int kGenMaxRad = 8;
+struct GenProj {
+  int natom = 0, nper = 0, nrad = 0, npw = 0, np = 0;
+  const int* mill = nullptr;        // [npw][3] signed Miller indices of the sphere
+  const double* tab = nullptr;      // phase tables, complex: atom I, axis c, m in [-half_c, half_c]
+  int toff[3] = {0, 0, 0}, half[3] = {0, 0, 0}, tstride = 0;
+  const double* ekr = nullptr;      // [natom] complex e^{-i k.R_I}
+  const double* radial = nullptr;   // [nrad][npw] F_n(G)
+  int l[kGenMaxRad] = {}, off[kGenMaxRad] = {};
+  double b[9] = {}, k[3] = {};
+};
+// The two Ozaki slicings of the generated beta (rows for the inner product,
+// columns for the outer one) into bslices (nonlocal_oz_beta_bytes), as
+// nonlocal_oz's own slicing of a stored beta would lay them out.
+int oz_gen_beta(const GenProj& g, void* bslices, void* scratch, cudaStream_t st, Prof* pf);
+// Bytes of oz_gen_beta's scratch (the exponent bounds).
+size_t oz_gen_scratch_bytes(const GenProj& g);
+// The generated beta as values, complex [np][npw] (the SIMT and TF32 paths).
+int gen_beta_values(const GenProj& g, double* beta, cudaStream_t st, Prof* pf);
 
 // hpsi += beta^T D (conj(beta) psi^T) with FP64-accurate products on the BF16
 // tensor cores (ozgemm.cu); beta slices in bslices (nonlocal_oz_beta_bytes),

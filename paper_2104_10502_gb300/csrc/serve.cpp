@@ -120,7 +120,7 @@ bool start_solve(qe_srv* s, Active& a) {
   r.prob.beta = r.beta.empty() ? nullptr : r.beta.data();
   r.prob.dmat = r.dmat.empty() ? nullptr : r.dmat.data();
   r.prob.mem = QE_HOST;
-  const int rc = qe::dv_task_create(s->ctx, &r.prob, r.precision, r.tol, r.max_iter, r.psi.data(),
+  const int rc = qe::dv_task_create(s->ctx, &r.prob, r.precision, r.tol, r.max_iter, 0, r.psi.data(),
                                     s->st, &a.task);
   if (rc) {
     r.status = rc;
@@ -140,7 +140,7 @@ void finish_solve(qe_srv* s, Active& a) {
   if (a.task) {
     int it = 0;
     r.status = qe::dv_task_result(s->ctx, a.task, r.psi.data(), r.evals.data(), r.resid.data(), &it,
-                                  s->st);
+                                  false, s->st);
     r.iters = it;
     if (r.status != QE_OK) r.err = qe_last_error();
     qe::dv_task_destroy(a.task, s->st);
