@@ -791,6 +791,48 @@ def run_cg_density_bench(q, ctx, dev):
         dens[tag] = {"bands_per_s": nb / (ms / 1e3), "ms_per_call": ms,
                      "max_rel_err_vs_oracle_8_bands": err}
     out["density"] = dens
+    # one self-consistency step from the same bands (alpha 0.3, V_in = V_ext)
+    v = torch.empty((grid[2], grid[1], grid[0]), dtype=torch.float64, device=dev)
+    ctx.vloc_gaussian(lat, grid, c["tau"], v)
+    vnew = torch.empty_like(v)
+    for _ in range(2):
+        ctx.scf_step(lat, ecut, grid, np.array([k]), [psi], [w], v, v, 0.3, vnew, None, q.QE_FP64)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        ctx.scf_step(lat, ecut, grid, np.array([k]), [psi], [w], v, v, 0.3, vnew, None, q.QE_FP64)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    out["scf_step"] = {"workload": "C1: 128 bands, density + Hartree (|G|^2 <= 160 Ry) + Slater exchange + "
+                                   "mixing, FP64", "ms_per_step": e0.elapsed_time(e1) / 5}
+    # H|psi> with the projectors generated on the fly (no stored beta), FP64
+    widths = c["widths"]
+    omega = abs(np.linalg.det(lat))
+    cf = (2 * math.pi) ** 1.5 / math.sqrt(omega)
+    rows, ls = [], []
+    for wd in widths:
+        gq = np.exp(-0.5 * wd * wd * kin)
+        rows += [cf * math.sqrt(4.0 / (math.sqrt(math.pi) * wd ** 3)) * wd ** 3 * gq,
+                 cf * math.sqrt(8.0 / (3.0 * math.sqrt(math.pi) * wd ** 5)) * wd ** 5 * gq]
+        ls += [0, 1]
+    rad = torch.from_numpy(np.ascontiguousarray(rows)).to(dev)
+    dm = torch.from_numpy(qeinputs.d_matrix(len(c["tau"]), len(widths))).to(dev)
+    pg = ctx.problem_gen(lat, k, ecut, grid, v, dm, dm.shape[0], nb)
+    hg = torch.empty_like(psi)
+    for _ in range(3):
+        ctx.hpsi_gen(pg, c["tau"], ls, rad, psi, hg, q.QE_FP64)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(10):
+        ctx.hpsi_gen(pg, c["tau"], ls, rad, psi, hg, q.QE_FP64)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / 10
+    out["hpsi_generated_projectors"] = {"bands_per_s": nb / (ms / 1e3), "ms_per_call": ms,
+                                        "note": "C1 FP64, beta formed from atoms, radial tables and "
+                                                "phase tables straight into the tensor-core slices"}
     return out
 
 
