@@ -355,6 +355,22 @@ def cpu_oracle_rate(c, inputs, nb_sample, reps):
     return nb_sample * reps / dt
 
 
+def cpu_oracle_davidson_c0(tol):
+    """Seconds of one oracle block-Davidson solve of C0 on the host cores."""
+    import oracle
+    c = qeinputs.config("C0")
+    lat, k, ecut, grid = c["lat"], c["k"], c["ecut"], c["grid"]
+    v = oracle.vloc_gaussian(lat, grid, c["tau"])
+    beta = oracle.beta_gaussian(lat, k, ecut, c["tau"], c["widths"])
+    d = qeinputs.d_matrix(len(c["tau"]), len(c["widths"]))
+    _, kin, _ = oracle.gsphere(lat, k, ecut)
+    psi0 = qeinputs.start_bands(kin, c["nbnd"], c["psi_seed"])
+    t0 = time.perf_counter()
+    r = oracle.davidson(lambda x: oracle.hpsi(lat, k, ecut, grid, v, beta, d, x),
+                        oracle.h_diag(kin, v, beta, d), psi0, tol)
+    return time.perf_counter() - t0, int(r["iters"]), bool(r["converged"])
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -588,6 +604,9 @@ def run_gpu(args, rank, world, local_rank):
             rate = cpu_oracle_rate(c, cinp, 2, 3)
             cpu = {"value": rate, "unit": "bands/s", "cores": len(os.sched_getaffinity(0)),
                    "kind": "oracle", "sample": "6 band applications (3 x 2 bands) of the C1 workload"}
+            secs, its, conv = cpu_oracle_davidson_c0(1e-8)
+            cpu["davidson_C0"] = {"solves_per_s": 1.0 / secs, "seconds": secs, "iters": its,
+                                  "converged": conv, "tol": 1e-8}
         line = {"metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -212,8 +212,9 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision,
  *    projections, one band's stick buffer and one split of the projector
  *    product must fit in 64 MiB; larger problems return QE_EINVAL with the
  *    needed size in qe_last_error() (use qe_hpsi for those).
- *  - The first call on each device looks up the array's device address; make
- *    that first call before any stream capture.
+ *  - Not callable while `stream` is being captured into a CUDA graph
+ *    (QE_EINVAL): which plan the array holds is host-side state that a
+ *    replayed graph would not consult.
  *  - A call whose cell, k, cut-off or grid differs from the previous call's on
  *    the device copies a new plan (the sphere's maps) from host memory into
  *    the array; that pageable copy can synchronise the calling stream.  Calls

@@ -213,10 +213,22 @@ extern "C" int qe_hpsi_noalloc(const qe_problem* prob, int precision, const doub
     qe::set_error("qe_hpsi_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
     return QE_ECUDA;
   }
+  cudaStream_t st = (cudaStream_t)stream;
+  // Under capture the plan check below would run once, at capture time, while
+  // the graph may be replayed after other calls replaced the array's plan.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) {
+    qe::set_error("qe_hpsi_noalloc: cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    return QE_ECUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) {
+    qe::set_error("qe_hpsi_noalloc: not callable while the stream is being captured");
+    return QE_EINVAL;
+  }
   void* base = nullptr;
   rc = qe::noalloc_scratch(dev, &base);
   if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   unsigned char* b = static_cast<unsigned char*>(base);
   if (precision == QE_FP64) return qe::hpsi_noalloc_impl<qe::FftF64>(prob, psi, hpsi, st, b, dev);
   return qe::hpsi_noalloc_impl<float>(prob, psi, hpsi, st, b, dev);

@@ -80,13 +80,14 @@ __device__ __forceinline__ int oz_exp(int e) { return e == (int)0x80808080 ? 0 :
 // A slices: rows t * Mp + m of mapA; B slices: rows t * Np + j of mapB.
 // Output: complex pairs (C'[m][2n], C'[m][2n+1]) to out[z * zstride + n * ldo + m]
 // for m < M, n < N (n = j / 2), negated if alpha_neg, added to the old value if
-// beta.  grid (Np / 64, Mp / 128, nsplit); CTA z takes K steps
+// beta; scaled by 2^(eA[m] + eB[n]) (one exponent per column pair), or, with
+// ecol, column j by 2^(eA[m] + eB[j]).  grid (Np / 64, Mp / 128, nsplit); CTA z takes K steps
 // [z * ks_per_split, min(nks, (z + 1) * ks_per_split)).
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           int Mp, int Np, int nks, int ks_per_split, const int* __restrict__ eA,
           const int* __restrict__ eB, double2* __restrict__ out, int ldo, long long zstride, int M,
-          int N, int alpha_neg, int beta, int* status) {
+          int N, int alpha_neg, int beta, int ecol, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -280,8 +281,10 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       for (int q = 0; q < OZ_ECOLS / 2; ++q) {
         const int n = ((n0 + c0) >> 1) + q;
         if (n >= N) break;
-        const double f = pow2(ea + oz_exp(eB[n]) - unit);
-        double2 v = make_double2(__ll2double_rn(acc[2 * q]) * f, __ll2double_rn(acc[2 * q + 1]) * f);
+        const int eb0 = oz_exp(eB[ecol ? 2 * n : n]);
+        const int eb1 = ecol ? oz_exp(eB[2 * n + 1]) : eb0;
+        double2 v = make_double2(__ll2double_rn(acc[2 * q]) * pow2(ea + eb0 - unit),
+                                 __ll2double_rn(acc[2 * q + 1]) * pow2(ea + eb1 - unit));
         if (alpha_neg) { v.x = -v.x; v.y = -v.y; }
         double2* p = o + (size_t)n * ldo;
         if (beta) { const double2 old = *p; v.x += old.x; v.y += old.y; }
@@ -394,10 +397,9 @@ constexpr int OZ_ROW_CHUNK = 2048;   // complex elements of a row per CTA
 
 // Row exponents of a complex [rows][K] matrix: grid (rows, ceil(K / 2048)); the
 // CTAs of a row merge their exponent bounds with atomicMax (monotonic in the
-// maximum) into e[r >> shift] (shift 1: one exponent for the rows 2p and 2p+1),
-// which holds 0x80808080 beforehand (kept by all-zero rows).
+// maximum) into e[r], which holds 0x80808080 beforehand (kept by all-zero rows).
 __global__ void __launch_bounds__(256) k_oz_rowmax(const double2* __restrict__ src, int ld, int K,
-                                                   int shift, int* __restrict__ e) {
+                                                   int* __restrict__ e) {
   __shared__ unsigned long long sh[33];
   const int r = blockIdx.x;
   const double2* row = src + (size_t)r * ld;
@@ -410,13 +412,12 @@ __global__ void __launch_bounds__(256) k_oz_rowmax(const double2* __restrict__ s
     mx = h > mx ? h : mx;
   }
   mx = block_max_u64(mx, sh);
-  if (threadIdx.x == 0 && mx != 0) atomicMax(&e[r >> shift], exp_bound_bits(mx));
+  if (threadIdx.x == 0 && mx != 0) atomicMax(&e[r], exp_bound_bits(mx));
 }
 
 // Row slicing: input row r of a complex [rows][K] matrix (leading dimension ld,
 // complex units).  form 0: output row r = (x, y)_k; form 1: rows 2r = (x, y)_k
-// and 2r+1 = (y, -x)_k; form 3: as form 0 with the exponent e[r >> 1] shared by
-// the rows 2p and 2p+1.  Q is [S][rows_out_p][Kp] BF16 (padding zeroed), e the
+// and 2r+1 = (y, -x)_k.  Q is [S][rows_out_p][Kp] BF16 (padding zeroed), e the
 // row exponents (k_oz_rowmax).  grid (input rows incl. padding, ceil(Kp/2 / 2048)).
 __global__ void __launch_bounds__(256) k_oz_slice_rows(const double2* __restrict__ src, int ld,
                                                        int rows, int K, int form, int rows_out_p,
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_rows(const double2* __restrict
   const int r = blockIdx.x;
   const double2* row = src + (size_t)r * ld;
   const bool valid = r < rows;
-  const int ex = valid ? oz_exp(e[form == 3 ? r >> 1 : r]) : 0;
+  const int ex = valid ? oz_exp(e[r]) : 0;
   const size_t slice2 = (size_t)rows_out_p * Kp / 2;     // one slice, in BF16 pairs
   const int orow = form == 1 ? 2 * r : r;
   unsigned* base0 = reinterpret_cast<unsigned*>(Q + (size_t)orow * Kp);
@@ -596,23 +597,22 @@ static OzOperand oz_carve(void* mem, int rows_out, int K) {
 }
 
 // Slices of the rows of a complex [rows][K] matrix (form 0: one output row per
-// input row; form 1: the inner product's B pair; form 3: form 0 with one
-// exponent per row pair, e[p] for the rows 2p and 2p+1, the B operand of the
-// real-output inner product).  Returns the carved operand.
+// input row, also the B operand of the real-output inner product; form 1: the
+// inner product's B pair).  Returns the carved operand.
 int oz_slice_rows(const double* src, int ld, int rows, int K, int form, void* mem, OzOperand* out,
                   cudaStream_t st, Prof* pf) {
   const int rows_out = form == 1 ? 2 * rows : rows;
-  const int shift = form == 3 ? 1 : 0;
   *out = oz_carve(mem, rows_out, K);
   if (rows > 0) {
     ProfScope ps(pf, "k_oz_rowmax", st);
-    const int ne = (rows + shift) >> shift;
-    if (cudaMemsetAsync(out->e, 0x80, (size_t)ne * sizeof(int), st) != cudaSuccess) {
+    // padding rows too: the real-output product reads the exponent of the
+    // ragged last column pair's empty half
+    if (cudaMemsetAsync(out->e, 0x80, (size_t)out->rows_p * sizeof(int), st) != cudaSuccess) {
       set_error("oz_slice_rows: memset failed");
       return QE_ECUDA;
     }
     dim3 gm(rows, (K + OZ_ROW_CHUNK - 1) / OZ_ROW_CHUNK);
-    k_oz_rowmax<<<gm, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, shift, out->e);
+    k_oz_rowmax<<<gm, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, out->e);
     int rc = oz_check("k_oz_rowmax");
     if (rc) return rc;
   }
@@ -845,8 +845,8 @@ size_t oz_partial_bytes(int M, int N, int K) {
 }
 
 static int oz_launch(const OzOperand& A, const OzOperand& B, int M, int N, double2* out, int ldo,
-                     long long zstride, int nsplit, int alpha_neg, int beta, int* status,
-                     cudaStream_t st, Prof* pf) {
+                     long long zstride, int nsplit, int alpha_neg, int beta, int ecol,
+                     int* status, cudaStream_t st, Prof* pf) {
   if (A.Kp != B.Kp) {
     set_error("oz_gemm: K padding mismatch");
     return QE_EINVAL;
@@ -862,15 +862,17 @@ static int oz_launch(const OzOperand& A, const OzOperand& B, int M, int N, doubl
   ProfScope ps(pf, "k_oz_gemm", st);
   dim3 g(B.rows_p / OZ_BN, A.rows_p / OZ_BM, nsplit);
   k_oz_gemm<<<g, OZ_THREADS, OZ_SMEM_BYTES, st>>>(mA, mB, A.rows_p, B.rows_p, nks, per, A.e, B.e,
-                                                   out, ldo, zstride, M, N, alpha_neg, beta, status);
+                                                   out, ldo, zstride, M, N, alpha_neg, beta, ecol,
+                                                   status);
   return oz_check("k_oz_gemm");
 }
 
 // C[m][n] = sum_k conj(A[m][k]) B[n][k] with A sliced by oz_slice_rows (form 0)
 // and B by oz_slice_rows (form 1); split K, fixed-order reduction.  real: C[m][n]
-// = (Re sum_k conj(A[m][k]) B[n][k], 0) with B sliced in form 3, so that the
+// = (Re sum_k conj(A[m][k]) B[n][k], 0) with B sliced in form 0, so that the
 // GEMM's column pair (2p, 2p+1) holds the real parts of the complex columns 2p
-// and 2p+1 (one exponent per pair): half the columns of the complex form.
+// and 2p+1, each scaled by its own row's exponent: half the columns of the
+// complex form.
 int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* C, int ldc,
                   void* part, size_t part_bytes, int* status, cudaStream_t st, Prof* pf,
                   bool real = false) {
@@ -890,7 +892,7 @@ int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* 
     ns = (nks + per - 1) / per;
   }
   int rc = oz_launch(A, B, M, N, reinterpret_cast<double2*>(part), A.rows_p, zstride, ns, 0, 0,
-                     status, st, pf);
+                     real ? 1 : 0, status, st, pf);
   if (rc) return rc;
   const int per = (nks + ns - 1) / ns;
   const int nsplit = (nks + per - 1) / per;
@@ -912,8 +914,8 @@ int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* 
 int oz_gemm_outer(const OzOperand& A, const OzOperand& B, int M, int N, double* C, int ldc,
                   int alpha_neg, int beta, int* status, cudaStream_t st, Prof* pf) {
   if (M <= 0 || N <= 0) return QE_OK;
-  return oz_launch(A, B, M, N, reinterpret_cast<double2*>(C), ldc, 0, 1, alpha_neg, beta, status,
-                   st, pf);
+  return oz_launch(A, B, M, N, reinterpret_cast<double2*>(C), ldc, 0, 1, alpha_neg, beta, 0,
+                   status, st, pf);
 }
 
 bool fp64_gemm_on_tensor_cores() {
@@ -958,7 +960,7 @@ int oz_inner(const double* A, int lda, const double* B, int ldb, int M, int N, i
   int rc;
   if ((rc = oz_slice_rows(A, lda, M, K, 0, p, &a, st, pf))) return rc;
   p += oz_operand_bytes(M, K);
-  if ((rc = oz_slice_rows(B, ldb, N, K, real ? 3 : 1, p, &b, st, pf))) return rc;
+  if ((rc = oz_slice_rows(B, ldb, N, K, real ? 0 : 1, p, &b, st, pf))) return rc;
   p += oz_operand_bytes(2 * N, K);
   return oz_gemm_inner(a, b, M, N, C, ldc, p, oz_partial_bytes(M, N, K), status, st, pf, real);
 }
@@ -1023,7 +1025,7 @@ int nonlocal_oz(const double* beta, const double* dmat, const double* psi, doubl
   P = reinterpret_cast<double*>(((uintptr_t)P + 255) & ~(uintptr_t)255);
   double* Q = reinterpret_cast<double*>(reinterpret_cast<char*>(P) + up256((size_t)np * nb * 16));
   // real_p: only Re P is used, so the real-output product (half the work)
-  if ((rc = oz_slice_rows(psi, npw, nb, npw, real_p ? 3 : 1, wb1, &B1, st, pf))) return rc;
+  if ((rc = oz_slice_rows(psi, npw, nb, npw, real_p ? 0 : 1, wb1, &B1, st, pf))) return rc;
   if ((rc = oz_gemm_inner(A1, B1, np, nb, P, nb, part, oz_partial_bytes(np, nb, npw), status, st, pf,
                           real_p)))
     return rc;

@@ -121,6 +121,32 @@ def test_gamma_hpsi_c1_sampled(q, ctx, nb):
     assert _rel_band(got[sel], want).max() <= 1e-12
 
 
+def test_gamma_hpsi_c1_unlike_norms(q, ctx):
+    """Neighbouring bands of very different norm (1 and 1e-6, as the projected
+    corrections of an orthonormalisation pass can be): the real-output
+    projection product gives each band its own exponent, so the weak bands
+    keep the FP64 tolerance relative to their own norm.  V_loc = 0, because
+    bands 2b and 2b+1 also share one FFT, whose rounding is relative to the
+    pair (V = 0 makes the local term exactly zero, isolating the kinetic and
+    nonlocal terms)."""
+    c = qeinputs.config("C1")
+    nb = 16
+    prob, keep, miller, kin = _problem(q, ctx, c, nb)
+    keep[0].zero_()
+    psi = _real_in_r(qeinputs.start_bands(kin, nb, c["psi_seed"]), _mirror(miller))
+    psi[1::2] *= 1e-6
+    pt = _to_t(psi)
+    ht = torch.empty_like(pt)
+    ctx.hpsi(prob, pt, ht, q.QE_FP64 | q.QE_GAMMA)
+    torch.cuda.synchronize()
+    got = _from_t(ht)
+    lat, k, ecut, grid = c["lat"], c["k"], c["ecut"], c["grid"]
+    beta = oracle.beta_gaussian(lat, k, ecut, c["tau"], c["widths"])
+    d = qeinputs.d_matrix(len(c["tau"]), len(c["widths"]))
+    want = oracle.hpsi(lat, k, ecut, grid, np.zeros((grid[2], grid[1], grid[0])), beta, d, psi)
+    assert _rel_band(got, want).max() <= 1e-12
+
+
 def test_gamma_flag_is_ignored_off_gamma(q, ctx):
     c = qeinputs.config("SMALL")
     assert np.any(np.asarray(c["k"]) != 0.0)

@@ -85,3 +85,28 @@ def test_noalloc_refuses_problems_beyond_its_array():
         q.hpsi_noalloc(prob, pt, torch.empty_like(pt), q.QE_FP64)
     assert e.value.code == q.QE_EINVAL
     assert "64" in str(e.value) or "holds" in str(e.value)
+
+
+def test_noalloc_refuses_calls_under_stream_capture():
+    import paper_2104_10502_gb300 as q
+    torch.cuda.set_device(0)
+    with q.Context(0) as ctx:
+        prob, pt, keep = _setup(q, ctx, "C0", 2, 23)
+        out = torch.empty_like(pt)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        caught = []
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                try:
+                    q.hpsi_noalloc(prob, pt, out, q.QE_FP64, stream=s.cuda_stream)
+                except q.QEError as e:      # refused before queueing anything
+                    caught.append(e)
+        torch.cuda.synchronize()
+        assert caught and caught[0].code == q.QE_EINVAL
+        assert "captur" in str(caught[0])
+        # the stream is usable again afterwards
+        q.hpsi_noalloc(prob, pt, out, q.QE_FP64)
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all()
