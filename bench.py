@@ -290,7 +290,8 @@ def src_hash(*names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"k_oz_gemm": ("ozgemm.cu", "tc_ptx.cuh"), "k_plane": ("fft.cu", "fft_device.cuh", "ff.cuh"),
+KERNEL_SOURCES = {"k_oz_gemm": ("ozgemm.cu", "tc_ptx.cuh"),
+                  "k_plane": ("fft.cu", "fft_device.cuh", "ff.cuh", "plane2.cuh"),
                   "k_zinv": ("fft.cu", "fft_device.cuh", "ff.cuh"), "k_zfwd": ("fft.cu", "fft_device.cuh", "ff.cuh"), "k_gemm_inner": ("gemm.cu",),
                   "k_gemm_outer": ("gemm.cu",), "k_dmul": ("gemm.cu",)}
 

@@ -162,22 +162,34 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // ---- square planes with the register-resident two-pass transform (plane2.cuh) ----------
 // Shared memory: the plane (row stride N | 1), the twiddle table of length N,
 // the active-column table.
+// With the padding skipped along both axes (pr1 and pr2), the inverse passes
+// read only the columns and rows outside [N/4, 3N/4) before anything writes
+// there: the y pass reads the outer rows of the active columns, the x pass the
+// outer columns of every row after the y pass has filled the active columns --
+// so only the outer columns of every row need zeros (half the plane).
 template <typename T, int N>
 __device__ __forceinline__ void sq_setup(const FftJob<T>& J, cx<T>* plane, cx<T>* tab, int* ax) {
-  constexpr int ld = N | 1;
-  for (int i = threadIdx.x; i < ld * N; i += blockDim.x) plane[i] = cx_zero<T>();
+  constexpr int ld = N | 1, Q = N / 4, W = N - 2 * Q;   // outer columns: [0, Q) and [N - Q, N)
+  if (J.pr1 && J.pr2) {
+    for (int i = threadIdx.x; i < 2 * Q * N; i += blockDim.x) {
+      const int y = i / (2 * Q), c = i - y * (2 * Q);
+      plane[y * ld + (c < Q ? c : c + W)] = cx_zero<T>();
+    }
+  } else {
+    for (int i = threadIdx.x; i < ld * N; i += blockDim.x) plane[i] = cx_zero<T>();
+  }
   for (int t = threadIdx.x; t < N; t += blockDim.x) sq_tw_put<T>(tab, t, J.tw1[2 * t], J.tw1[2 * t + 1]);
   for (int i = threadIdx.x; i < J.nax; i += blockDim.x) ax[i] = J.ax[i];
 }
 
-// Inverse y transforms of the active columns (sticks scattered beforehand),
-// then the inverse x pass 1 of every row; ends with a barrier.
+// Inverse y transforms of the active columns (sticks scattered beforehand);
+// ends with a barrier.
 template <typename T, int N>
-__device__ __forceinline__ void sq_inverse_yx1(const FftJob<T>& J, cx<T>* plane, const cx<T>* tab,
-                                               const int* ax) {
+__device__ __forceinline__ void sq_inverse_y(const FftJob<T>& J, cx<T>* plane, const cx<T>* tab,
+                                             const int* ax) {
   constexpr int A = SqSplit<N>::A, B = SqSplit<N>::B, ld = N | 1;
   const int nax = J.nax, nt = blockDim.x;
-  const FastDiv fax(nax), fn(N);
+  const FastDiv fax(nax);
   for (int it = threadIdx.x; it < nax * B; it += nt) {
     const int n2 = fax.div(it), l = it - n2 * nax;
     if (J.pr2) sq_inv1<T, N, true>(plane + ax[l], ld, n2, tab);
@@ -193,10 +205,61 @@ __device__ __forceinline__ void sq_inverse_yx1(const FftJob<T>& J, cx<T>* plane,
     for (int k2 = 0; k2 < B; ++k2) p[(B * k1 + k2) * ld] = o[k2];
   }
   __syncthreads();
+}
+
+// The above, then the inverse x pass 1 of every row; ends with a barrier.
+template <typename T, int N>
+__device__ __forceinline__ void sq_inverse_yx1(const FftJob<T>& J, cx<T>* plane, const cx<T>* tab,
+                                               const int* ax) {
+  constexpr int B = SqSplit<N>::B, ld = N | 1;
+  const int nt = blockDim.x;
+  sq_inverse_y<T, N>(J, plane, tab, ax);
+  const FastDiv fn(N);
   for (int it = threadIdx.x; it < N * B; it += nt) {
     const int n2 = fn.div(it), y = it - n2 * N;
     if (J.pr1) sq_inv1<T, N, true>(plane + y * ld, 1, n2, tab);
     else sq_inv1<T, N, false>(plane + y * ld, 1, n2, tab);
+  }
+  __syncthreads();
+}
+
+// The x step of a plane pair with rows owned by warps: inverse pass 1, then
+// inverse pass 2 x V x forward pass 1, then forward pass 2, each row's three
+// phases in one warp, so that only __syncwarp separates them (no block barrier,
+// no warp waiting for the slowest row of the plane).  Lane j of a round takes
+// row y0 + j mod R: with 16-byte elements and the odd row stride the lanes of
+// one access spread over all banks.  R = N / warps rows per warp.
+template <typename T, int N>
+__device__ __forceinline__ void sq_x_step_warp_rows(const FftJob<T>& J, cx<T>* plane, const cx<T>* tab,
+                                                    const T* vz, int R, const FastDiv& fR) {
+  constexpr int A = SqSplit<N>::A, B = SqSplit<N>::B, ld = N | 1;
+  const int lane = threadIdx.x & 31, y0 = (threadIdx.x >> 5) * R;
+  for (int it = lane; it < R * B; it += 32) {
+    const int n2 = fR.div(it), y = y0 + (it - n2 * R);
+    if (J.pr1) sq_inv1<T, N, true>(plane + y * ld, 1, n2, tab);
+    else sq_inv1<T, N, false>(plane + y * ld, 1, n2, tab);
+  }
+  __syncwarp();
+  for (int it = lane; it < R * A; it += 32) {
+    const int k1 = fR.div(it), y = y0 + (it - k1 * R);
+    cx<T>* p = plane + y * ld;
+    const T* vr = vz + (size_t)y * N + B * k1;
+    T vv[B];
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) vv[k2] = vr[k2];
+    cx<T> o[B], f[B];
+    sq_inv2_regs<T, N>(p, 1, k1, tab, o);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) o[k2] = cscale(o[k2], vv[k2]);
+    sq_fwd1_regs<T, N>(o, k1, tab, f);
+#pragma unroll
+    for (int m2 = 0; m2 < B; ++m2) p[B * k1 + m2] = f[m2];
+  }
+  __syncwarp();
+  for (int it = lane; it < R * B; it += 32) {
+    const int m2 = fR.div(it), y = y0 + (it - m2 * R);
+    if (J.pr1) sq_fwd2<T, N, true>(plane + y * ld, 1, m2, tab);
+    else sq_fwd2<T, N, false>(plane + y * ld, 1, m2, tab);
   }
   __syncthreads();
 }
@@ -228,9 +291,16 @@ __device__ void plane_tile_sq(const FftJob<T>& J, int b, int pz, unsigned char* 
       if (s0 + u * nt < nst) plane[off[u]] = val[u];
   }
   __syncthreads();
+  const FastDiv fax(nax), fn(N);
+  const int nw = nt >> 5;
+  if (sizeof(cx<T>) == 16 && N % nw == 0) {
+    // 16-byte elements (float-float, float64): x rows owned by warps
+    sq_inverse_y<T, N>(J, plane, tab, ax);
+    const FastDiv fR(N / nw);
+    sq_x_step_warp_rows<T, N>(J, plane, tab, vz, N / nw, fR);
+  } else {
   sq_inverse_yx1<T, N>(J, plane, tab, ax);
   // x: inverse pass 2, times V, forward pass 1 on the same B values of a row
-  const FastDiv fax(nax), fn(N);
   for (int it = threadIdx.x; it < N * A; it += nt) {
     const int k1 = fn.div(it), y = it - k1 * N;
     cx<T>* p = plane + y * ld;
@@ -253,6 +323,7 @@ __device__ void plane_tile_sq(const FftJob<T>& J, int b, int pz, unsigned char* 
     else sq_fwd2<T, N, false>(plane + y * ld, 1, m2, tab);
   }
   __syncthreads();
+  }
   // y forward on the active columns
   for (int it = threadIdx.x; it < nax * A; it += nt) {
     const int k1 = fax.div(it), l = it - k1 * nax;
@@ -292,6 +363,24 @@ __device__ void plane_tile_sq(const FftJob<T>& J, int b, int pz, unsigned char* 
     case 32: CALL(32); return;                                \
     default: break;                                           \
   }
+
+// Launch bounds of the square-plane kernel.  FP32: at most 85 registers a
+// thread (72 used: the register-resident passes hold one line's 8 or 12
+// values), so that three CTAs of 256 threads (76 KB of shared memory each)
+// share an SM -- 24 warps where the general plane kernel, at 123 registers,
+// fits 16.  C1 mixed: 0.413 -> 0.381 ms per 68-band launch (384 threads:
+// 0.393).
+// Float-float and float64 planes: 384 threads (12 warps, 8 rows of the x step
+// each: whole rounds of every pass; 0.644 -> 0.590 ms per 32-band C1 launch
+// against 512 threads with block barriers between the x passes).
+template <typename T> struct SqLB { static constexpr int threads = 512, minb = 1, dflt = 384; };
+template <> struct SqLB<float> { static constexpr int threads = 384, minb = 2, dflt = 256; };
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SqLB<T>::threads, SqLB<T>::minb) k_plane_sq(const FftJob<T> J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  plane_tile_sq<T, N>(J, blockIdx.y, blockIdx.x, smem_raw);
+}
 
 template <typename T>
 __device__ void plane_tile(const FftJob<T>& J, int b, int pz, unsigned char* smem) {
@@ -725,7 +814,7 @@ size_t zsm_bytes(int n3, int spb) {
 
 template <typename T>
 static bool plane_stages_v(const DevPlan& P) {
-  return kStageV<T> && plane_v_offset<T>(P.grid[0], P.grid[1], P.h.nax) +
+  return kStageV<T> && P.sq == 0 && plane_v_offset<T>(P.grid[0], P.grid[1], P.h.nax) +
                                (size_t)P.grid[0] * P.grid[1] * sizeof(T) <= kStageVMaxBytes;
 }
 
@@ -811,10 +900,14 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
   // process: always set the same (largest) value so that concurrent callers
   // with different plane sizes cannot lower it under each other's launch.
   set_max_dynamic_smem(k_plane<T>);
+  set_max_dynamic_smem(k_plane_sq<T, 96>);
+  set_max_dynamic_smem(k_plane_sq<T, 48>);
+  set_max_dynamic_smem(k_plane_sq<T, 32>);
   set_max_dynamic_smem(k_zinv<T>);
   set_max_dynamic_smem(k_zfwd<T>);
   const int zt = sh.zthreads > 0 ? sh.zthreads : 256;
   const int pt = std::min(sh.pthreads > 0 ? sh.pthreads : PlaneLB<T>::dflt, PlaneLB<T>::threads);
+  const int pts = std::min(sh.pthreads > 0 ? sh.pthreads : SqLB<T>::dflt, SqLB<T>::threads);
   dim3 gz(J.nsb, J.nb);
   int rc;
   {
@@ -825,7 +918,13 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
   if (rc) return rc;
   {
     ProfScope ps(pf, "k_plane", st);
-    k_plane<T><<<dim3(P.grid[2], J.nb), pt, psm, st>>>(J);
+    const dim3 gp(P.grid[2], J.nb);
+    switch (J.sq) {
+      case 96: k_plane_sq<T, 96><<<gp, pts, psm, st>>>(J); break;
+      case 48: k_plane_sq<T, 48><<<gp, pts, psm, st>>>(J); break;
+      case 32: k_plane_sq<T, 32><<<gp, pts, psm, st>>>(J); break;
+      default: k_plane<T><<<gp, pt, psm, st>>>(J); break;
+    }
     rc = check_launch("k_plane");
   }
   if (rc) return rc;

@@ -728,29 +728,46 @@ __device__ __forceinline__ void gen_atom(const GenProj& g, int I, int G, F&& f) 
 }
 
 // Both slicings.  grid (ceil(npw / 128), natom); A1: [S][rows_p1][Kp1] (row i,
-// K pair (2G, 2G+1)); A2: [S][rows_p2][Kp2] (row G, K pair (2i, 2i+1)).
+// K pair (2G, 2G+1)); A2: [S][rows_p2][Kp2] (row G, K pair (2i, 2i+1)).  The A1
+// words of a projector are consecutive in G, so consecutive threads store them
+// together; the A2 words of one G are the atom's nper consecutive columns, which
+// one thread produces one projector at a time -- they are staged in shared
+// memory (sQ[t][g][j], 8 x 128 x nper words) and stored row by row, a warp
+// writing whole 32-byte sectors instead of 4-byte pieces.
 __global__ void __launch_bounds__(128) k_gen_slices(GenProj g, const int* __restrict__ erow,
                                                     const int* __restrict__ ecol, int rows_p1, int Kp1,
                                                     unsigned* __restrict__ Q1, int rows_p2, int Kp2,
                                                     unsigned* __restrict__ Q2) {
-  const int G = blockIdx.x * blockDim.x + threadIdx.x, I = blockIdx.y;
-  if (G >= g.npw) return;
+  extern __shared__ unsigned sQ[];
+  const int G0 = blockIdx.x * blockDim.x, G = G0 + threadIdx.x, I = blockIdx.y;
+  const int nper = g.nper, nt = blockDim.x;
   const size_t s1 = (size_t)rows_p1 * Kp1 / 2, s2 = (size_t)rows_p2 * Kp2 / 2;
-  const int ec = oz_exp(ecol[G]);
-  gen_atom(g, I, G, [&](int i, double2 v) {
-    unsigned short qx[OZ_S], qy[OZ_S];
-    const int er = oz_exp(erow[i]);
-    slices_of(v.x, er, qx);
-    slices_of(v.y, er, qy);
-    unsigned* p1 = Q1 + (size_t)i * (Kp1 / 2) + G;
+  if (G < g.npw) {
+    const int ec = oz_exp(ecol[G]);
+    gen_atom(g, I, G, [&](int i, double2 v) {
+      unsigned short qx[OZ_S], qy[OZ_S];
+      const int er = oz_exp(erow[i]);
+      slices_of(v.x, er, qx);
+      slices_of(v.y, er, qy);
+      unsigned* p1 = Q1 + (size_t)i * (Kp1 / 2) + G;
 #pragma unroll
-    for (int t = 0; t < OZ_S; ++t) p1[t * s1] = pack2(qx[t], qy[t]);
-    slices_of(v.x, ec, qx);
-    slices_of(v.y, ec, qy);
-    unsigned* p2 = Q2 + (size_t)G * (Kp2 / 2) + i;
+      for (int t = 0; t < OZ_S; ++t) p1[t * s1] = pack2(qx[t], qy[t]);
+      slices_of(v.x, ec, qx);
+      slices_of(v.y, ec, qy);
+      const int j = i - I * nper;
 #pragma unroll
-    for (int t = 0; t < OZ_S; ++t) p2[t * s2] = pack2(qx[t], qy[t]);
-  });
+      for (int t = 0; t < OZ_S; ++t) sQ[((size_t)t * nt + threadIdx.x) * nper + j] = pack2(qx[t], qy[t]);
+    });
+  }
+  __syncthreads();
+  const int rows = min(nt, g.npw - G0);
+  const int per_t = rows * nper;
+  for (int w = threadIdx.x; w < OZ_S * per_t; w += nt) {
+    const int t = w / per_t, r = w - t * per_t;
+    const int gg = r / nper, j = r - gg * nper;
+    Q2[t * s2 + (size_t)(G0 + gg) * (Kp2 / 2) + (size_t)I * nper + j] =
+        sQ[((size_t)t * nt + gg) * nper + j];
+  }
 }
 
 // Zero the rectangle [r0, r1) x [c0, c1) (uint32 units) of every slice.
@@ -801,8 +818,10 @@ int oz_gen_beta(const GenProj& g, void* bslices, void* scratch, cudaStream_t st,
       (rc = zero_rect(Q2, s2, A2.Kp / 2, g.npw, A2.rows_p, 0, A2.Kp / 2, st)) ||
       (rc = zero_rect(Q2, s2, A2.Kp / 2, 0, g.npw, g.np, A2.Kp / 2, st)))
     return rc;
-  k_gen_slices<<<dim3((g.npw + 127) / 128, g.natom), 128, 0, st>>>(g, A1.e, A2.e, A1.rows_p, A1.Kp,
-                                                                    Q1, A2.rows_p, A2.Kp, Q2);
+  const size_t gsm = (size_t)OZ_S * 128 * g.nper * sizeof(unsigned);   // <= 96 KB (nper <= 24)
+  set_max_dynamic_smem(k_gen_slices);
+  k_gen_slices<<<dim3((g.npw + 127) / 128, g.natom), 128, gsm, st>>>(g, A1.e, A2.e, A1.rows_p, A1.Kp,
+                                                                      Q1, A2.rows_p, A2.Kp, Q2);
   if (pf) pf->launches += 6;
   return oz_check("k_gen_slices");
 }
