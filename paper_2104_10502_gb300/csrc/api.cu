@@ -29,11 +29,13 @@ void Prof::end(const char* name, cudaStream_t st, cudaEvent_t ev) {
   cudaEvent_t b;
   if (cudaEventCreate(&b) != cudaSuccess) { cudaGetLastError(); cudaEventDestroy(ev); return; }
   cudaEventRecord(b, st);
+  std::lock_guard<std::mutex> lk(mu);
   recs.push_back({name, ev, b});
 }
 
 int Prof::fold() {
   int rc = QE_OK;
+  std::lock_guard<std::mutex> lk(mu);
   for (auto& r : recs) {
     float t = 0.f;
     if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {

@@ -20,6 +20,8 @@
 #include <cmath>
 #include <cstring>
 #include <vector>
+#include <string>
+#include <thread>
 
 #include "ctx.h"
 #include "dense.h"
@@ -1476,6 +1478,7 @@ struct DvTask {
   int phase = DV_FIRST_H;
   int h_prec = QE_FP64;         // arithmetic of the pending H product
   int rc = QE_OK;
+  std::string err;              // message of the error that ended it
   DvTask() {
     basis.sp = &cur;
     red.sp = &cur;
@@ -1543,9 +1546,14 @@ int dv_round(qe_ctx* ctx, DvTask* const* tasks, int n, void* stream, void* const
   cudaStream_t st = (cudaStream_t)stream;
   Prof* pf = &ctx->prof;
   auto live = [&](const DvTask* t) { return t->rc == QE_OK && t->phase != DV_DONE; };
-  // 1. the pending H products, one batched call per arithmetic
+  // task i runs its own work on side stream i % nside (the same stream in every
+  // round, so a task's work stays in order)
+  const int ns = std::max(1, nside);
+  auto sst = [&](int i) { return nside > 0 ? (cudaStream_t)side[i % ns] : st; };
+  // 1. the pending H products, one batched call per arithmetic on `stream`
+  std::vector<int> after;   // tasks whose H product ran in this round
   for (int prec : {QE_FP64, QE_MIXED}) {
-    std::vector<DvTask*> ts;
+    std::vector<int> ts;
     std::vector<qe_problem> pr;
     std::vector<const double*> in;
     std::vector<double*> outp;
@@ -1557,7 +1565,7 @@ int dv_round(qe_ctx* ctx, DvTask* const* tasks, int n, void* stream, void* const
       qe_problem q = t->prob;
       q.nbnd = t->v.h_rows;
       const size_t off = (size_t)t->v.h_row * t->v.S.npw;
-      ts.push_back(t);
+      ts.push_back(i);
       pr.push_back(q);
       in.push_back(reinterpret_cast<const double*>(t->v.S.V + off));
       outp.push_back(reinterpret_cast<double*>(t->v.S.HV + off));
@@ -1567,54 +1575,67 @@ int dv_round(qe_ctx* ctx, DvTask* const* tasks, int n, void* stream, void* const
     const int rc = hpsi_batch_core(ctx, (int)pr.size(), pr.data(), prec, in.data(), outp.data(), st,
                                    pair.data());
     if (rc) {
-      for (DvTask* t : ts) t->rc = rc;
+      for (int i : ts) tasks[i]->rc = rc;
       continue;
     }
-    // 2. what follows each H product
-    for (DvTask* t : ts) {
-      DvSolve& v = t->v;
-      const bool f64 = v.precision == QE_FP64;
-      if (t->phase == DV_FIRST_H) {
-        t->rc = f64 ? dv_after_first_h<double>(v, st, pf) : dv_after_first_h<float>(v, st, pf);
-        t->phase = DV_STEP;
-      } else if (t->phase == DV_H) {
-        t->rc = f64 ? dv_after_h<double>(v, st, pf) : dv_after_h<float>(v, st, pf);
-        t->phase = DV_STEP;
-      } else {
-        v.h_rows = 0;
-        t->rc = refine_post(v.S, st, pf);
-        if (t->rc == QE_OK) t->rc = dv_task_after_refine(ctx, *t, st);
-      }
-    }
+    after.insert(after.end(), ts.begin(), ts.end());
   }
-  // 3. one Rayleigh-Ritz step of every task at that stage, task i on a side
-  //    stream (forked after the H products): all launched, then the
-  //    convergence tests in turn (each waits for its own stream only)
-  std::vector<DvTask*> step;
-  for (int i = 0; i < n; ++i)
-    if (live(tasks[i]) && tasks[i]->phase == DV_STEP) step.push_back(tasks[i]);
-  const int ns = std::max(1, nside);
-  auto sst = [&](size_t i) { return nside > 0 ? (cudaStream_t)side[i % ns] : st; };
-  if (nside > 0 && !step.empty()) {
+  // fork: every side stream follows the H products
+  bool forked = false;
+  auto fork = [&]() -> int {
+    if (forked || nside <= 0) return QE_OK;
+    forked = true;
     DV_CU(cudaEventRecord((cudaEvent_t)events[0], st));
     for (int k = 0; k < ns; ++k) DV_CU(cudaStreamWaitEvent((cudaStream_t)side[k], (cudaEvent_t)events[0], 0));
+    return QE_OK;
+  };
+  // 2. what follows each H product (the new reduced-matrix blocks), each task
+  //    on its side stream
+  if (!after.empty()) DV_TRY(fork());
+  for (int i : after) {
+    DvTask* t = tasks[i];
+    DvSolve& v = t->v;
+    const bool f64 = v.precision == QE_FP64;
+    const cudaStream_t s = sst(i);
+    if (t->phase == DV_FIRST_H) {
+      t->rc = f64 ? dv_after_first_h<double>(v, s, pf) : dv_after_first_h<float>(v, s, pf);
+      t->phase = DV_STEP;
+    } else if (t->phase == DV_H) {
+      t->rc = f64 ? dv_after_h<double>(v, s, pf) : dv_after_h<float>(v, s, pf);
+      t->phase = DV_STEP;
+    } else {
+      v.h_rows = 0;
+      t->rc = refine_post(v.S, s, pf);
+      if (t->rc == QE_OK) t->rc = dv_task_after_refine(ctx, *t, s);
+    }
   }
-  for (size_t i = 0; i < step.size(); ++i) {
-    DvTask* t = step[i];
+  // 3. one Rayleigh-Ritz step of every task at that stage: all launched, then
+  //    the convergence tests in turn (each waits for its own stream only)
+  std::vector<int> step;
+  for (int i = 0; i < n; ++i)
+    if (live(tasks[i]) && tasks[i]->phase == DV_STEP) step.push_back(i);
+  if (!step.empty()) DV_TRY(fork());
+  for (int i : step) {
+    DvTask* t = tasks[i];
     t->rc = t->v.precision == QE_FP64 ? dv_step_launch<double>(t->v, sst(i), pf)
                                       : dv_step_launch<float>(t->v, sst(i), pf);
   }
-  for (size_t i = 0; i < step.size(); ++i) {
-    DvTask* t = step[i];
-    if (t->rc != QE_OK) continue;
+  // The convergence test and the orthonormalisation of the corrections wait on
+  // the host for their task's stream (residual norms, dropped columns): one
+  // host thread per side stream takes that stream's tasks in order, so that
+  // one task's waits do not hold back the launches of the others.
+  auto finish = [&](int i) {
+    DvTask* t = tasks[i];
+    if (t->rc != QE_OK) return;
     DvSolve& v = t->v;
     t->rc = v.precision == QE_FP64 ? dv_step_finish<double>(ctx, v, sst(i), pf)
                                    : dv_step_finish<float>(ctx, v, sst(i), pf);
-    if (t->rc != QE_OK) continue;
+    if (t->rc != QE_OK) { t->err = qe_last_error(); return; }
     if (v.done) {
       if (v.precision != QE_FP64) {
         // the FP32 phase ended: FP64 H of the Ritz vectors, FP64 Rayleigh-Ritz
         t->rc = refine_pre(v.S, sst(i));
+        if (t->rc != QE_OK) t->err = qe_last_error();
         v.h_row = 0;
         v.h_rows = v.S.nb;
         t->h_prec = QE_FP64;
@@ -1626,9 +1647,25 @@ int dv_round(qe_ctx* ctx, DvTask* const* tasks, int n, void* stream, void* const
       t->h_prec = v.precision;
       t->phase = DV_H;
     }
+  };
+  const int nworkers = std::min(ns, (int)step.size());
+  if (nside > 1 && nworkers > 1) {
+    std::vector<std::thread> workers;
+    workers.reserve(nworkers);
+    for (int k = 0; k < nworkers; ++k)
+      workers.emplace_back([&, k]() {
+        cudaSetDevice(ctx->device);
+        for (int i : step)
+          if (i % ns == k) finish(i);
+      });
+    for (auto& w : workers) w.join();
+  } else {
+    for (int i : step) finish(i);
   }
-  if (nside > 0 && !step.empty()) {
-    // join: the next round's H products follow every task's step
+  for (int i : step)
+    if (tasks[i]->rc != QE_OK && !tasks[i]->err.empty()) set_error("%s", tasks[i]->err.c_str());
+  if (forked) {
+    // join: the next round's H products follow every task's work
     for (int k = 0; k < ns; ++k) {
       DV_CU(cudaEventRecord((cudaEvent_t)events[1 + k], (cudaStream_t)side[k]));
       DV_CU(cudaStreamWaitEvent(st, (cudaEvent_t)events[1 + k], 0));
@@ -1644,7 +1681,10 @@ int dv_task_result(qe_ctx* ctx, DvTask* t, double* psi, double* evals, double* r
   DvState& S = v.S;
   const cudaMemcpyKind kind = device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (iters) *iters = v.it;
-  if (t->rc != QE_OK && t->rc != QE_ENOCONV) return t->rc;
+  if (t->rc != QE_OK && t->rc != QE_ENOCONV) {
+    if (!t->err.empty()) set_error("%s", t->err.c_str());
+    return t->rc;
+  }
   if (psi) DV_CU(cudaMemcpyAsync(psi, S.Psi, (size_t)S.nb * S.npw * sizeof(z), kind, st));
   if (evals) DV_CU(cudaMemcpyAsync(evals, S.e, S.nb * sizeof(double), kind, st));
   if (resid) DV_CU(cudaMemcpyAsync(resid, S.rn, S.nb * sizeof(double), kind, st));

@@ -4,6 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
+
 #include <type_traits>
 
 #include "common.h"
@@ -66,7 +69,8 @@ inline void set_max_dynamic_smem(F* f) {
 // launches (always, even when timing is off).
 struct Prof {
   bool on = false;
-  long long launches = 0;
+  std::atomic<long long> launches{0};
+  std::mutex mu;   // recs: the lockstep rounds record from several host threads
   struct Rec { const char* name; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<std::string> names;
