@@ -444,9 +444,14 @@ static int outer_any(const DvState& S, const z* A, int lda, const z* B, int ldb,
   if (sizeof(T) == sizeof(float) && S.tc && tc_worth(M, N, K) && lda == M && ldb == N)
     return tc_outer((const double*)A, (const double*)B, M, N, K, (double*)C, ldc, alpha_neg, beta,
                     S.tc, S.tc_bytes, dv_tc_status(S), st, pf);
-  if (sizeof(T) == sizeof(double) && S.oz && oz_worth(M, N, K))
+  if (sizeof(T) == sizeof(double) && S.oz && oz_worth(M, N, K)) {
+    // k = 0 mode: the right-hand matrices (Ritz vectors, Gram blocks) are real
+    if (S.gamma && oz_outer_real_scratch(M, N, K) <= S.oz_bytes)
+      return oz_outer_real((const double*)A, lda, (const double*)B, ldb, M, N, K, (double*)C, ldc,
+                           alpha_neg, beta, S.oz, S.oz_bytes, dv_tc_status(S), st, pf);
     return oz_outer((const double*)A, lda, (const double*)B, ldb, M, N, K, (double*)C, ldc,
                     alpha_neg, beta, S.oz, S.oz_bytes, dv_tc_status(S), st, pf);
+  }
   return gemm_outer_ab<T>((const double*)A, lda, (const double*)B, ldb, M, N, K, (double*)C, ldc,
                           alpha_neg, beta, st, pf);
 }

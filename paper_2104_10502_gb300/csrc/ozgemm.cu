@@ -80,14 +80,16 @@ __device__ __forceinline__ int oz_exp(int e) { return e == (int)0x80808080 ? 0 :
 // A slices: rows t * Mp + m of mapA; B slices: rows t * Np + j of mapB.
 // Output: complex pairs (C'[m][2n], C'[m][2n+1]) to out[z * zstride + n * ldo + m]
 // for m < M, n < N (n = j / 2), negated if alpha_neg, added to the old value if
-// beta; scaled by 2^(eA[m] + eB[n]) (one exponent per column pair), or, with
-// ecol, column j by 2^(eA[m] + eB[j]).  grid (Np / 64, Mp / 128, nsplit); CTA z takes K steps
+// beta; scaled by 2^(eA[m] + eB[n]) (emode 0: one exponent per column pair), or
+// column j by 2^(eA[m] + eB[j]) (emode 1).  emode 2: real outputs, C'[m][j] x
+// 2^(eA[m] + eB[j]) to the real (m even) or imaginary (m odd) part of
+// out[z * zstride + j * ldo + m / 2], for m < M, j < N.  grid (Np / 64, Mp / 128, nsplit); CTA z takes K steps
 // [z * ks_per_split, min(nks, (z + 1) * ks_per_split)).
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
           int Mp, int Np, int nks, int ks_per_split, const int* __restrict__ eA,
           const int* __restrict__ eB, double2* __restrict__ out, int ldo, long long zstride, int M,
-          int N, int alpha_neg, int beta, int ecol, int* status) {
+          int N, int alpha_neg, int beta, int emode, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -274,7 +276,23 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       if (lane == 0) mbar_arrive(accempty);
     }
     const int m = m0 + quarter * 32 + lane;
-    if (ok && m < M) {
+    if (ok && m < M && emode == 2) {
+      // real outputs: GEMM row m is the real (m even) or imaginary (m odd) part
+      // of complex output row m / 2, GEMM column j a real column
+      const int ea = oz_exp(eA[m]);
+      double* o = reinterpret_cast<double*>(out + (size_t)blockIdx.z * zstride) + (m & 1);
+#pragma unroll
+      for (int c = 0; c < OZ_ECOLS; ++c) {
+        const int j = n0 + c0 + c;
+        if (j >= N) break;
+        double v = __ll2double_rn(acc[c]) * pow2(ea + oz_exp(eB[j]) - unit);
+        if (alpha_neg) v = -v;
+        double* p = o + 2 * ((size_t)j * ldo + (m >> 1));
+        if (beta) v += *p;
+        *p = v;
+      }
+    } else if (ok && m < M) {
+      const int ecol = emode;
       const int ea = oz_exp(eA[m]);
       double2* o = out + (size_t)blockIdx.z * zstride + m;
 #pragma unroll
@@ -452,25 +470,38 @@ __global__ void __launch_bounds__(256) k_oz_slice_rows(const double2* __restrict
 // its exponent bound with atomicMax (the bound is monotonic in the maximum);
 // e must hold 0x80808080 (below every exponent) beforehand, and an all-zero
 // column keeps it.
-__global__ void k_oz_colmax(const double2* __restrict__ src, int ld, int K, int M, int* __restrict__ e) {
+// split: the real and imaginary parts of column m get their own exponents,
+// e[2m] and e[2m+1] (the real-K slicing, form 4).
+__global__ void k_oz_colmax(const double2* __restrict__ src, int ld, int K, int M, int split,
+                            int* __restrict__ e) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
   const int k0 = blockIdx.y * 64, k1 = min(K, k0 + 64);
-  unsigned long long mx = 0;
+  unsigned long long mx = 0, my = 0;
 #pragma unroll 8
   for (int k = k0; k < k1; ++k) {
     const double2 v = src[(size_t)k * ld + m];
     const unsigned long long a = mag_bits(v.x), c = mag_bits(v.y);
-    const unsigned long long h = a > c ? a : c;
-    mx = h > mx ? h : mx;
+    mx = a > mx ? a : mx;
+    my = c > my ? c : my;
   }
-  if (mx != 0) atomicMax(&e[m], exp_bound_bits(mx));
+  if (split) {
+    if (mx != 0) atomicMax(&e[2 * m], exp_bound_bits(mx));
+    if (my != 0) atomicMax(&e[2 * m + 1], exp_bound_bits(my));
+  } else {
+    const unsigned long long h = mx > my ? mx : my;
+    if (h != 0) atomicMax(&e[m], exp_bound_bits(h));
+  }
 }
 
 // Transposed slicing of a complex [K][M] matrix: output rows from its columns.
-// form 0: row m = (x, y)_k; form 2: rows 2m = (x, -y)_k and 2m+1 = (y, x)_k.
+// form 0: row m = (x, y)_k; form 2: rows 2m = (x, -y)_k and 2m+1 = (y, x)_k
+// (K axis of 2K interleaved entries).  Real K axis (K entries, the products
+// with a real right-hand matrix): form 4: rows 2m = (x)_k and 2m+1 = (y)_k with
+// the exponents e[2m], e[2m+1]; form 5: row m = (x)_k (the real matrix itself).
 // 32 x 32 tiles through shared memory (reads coalesced along m, writes along k).
-// grid (ceil(cols_p / 32), Kp / 64) with cols_p = the padded column count.
+// grid (ceil(cols_p / 32), Kp / 64) with cols_p = the padded column count
+// (Kp / 32 for the real forms).
 __global__ void k_oz_slice_cols(const double2* __restrict__ src, int ld, int K, int M, int form,
                                 const int* __restrict__ e, int rows_out_p, int Kp,
                                 __nv_bfloat16* __restrict__ Q) {
@@ -482,6 +513,25 @@ __global__ void k_oz_slice_cols(const double2* __restrict__ src, int ld, int K, 
   }
   __syncthreads();
   const size_t slice = (size_t)rows_out_p * Kp;
+  if (form >= 4) {
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int m = m0 + r, k = k0 + threadIdx.x;
+      const int orow = form == 4 ? 2 * m : m;
+      if (orow >= rows_out_p || k >= Kp) continue;
+      const double2 v = tile[threadIdx.x][r];
+      unsigned short qx[OZ_S], qy[OZ_S];
+      slices_of(v.x, m < M ? oz_exp(e[orow]) : 0, qx);
+      unsigned short* p0 = reinterpret_cast<unsigned short*>(Q) + (size_t)orow * Kp + k;
+#pragma unroll
+      for (int t = 0; t < OZ_S; ++t) p0[t * slice] = qx[t];
+      if (form == 4) {
+        slices_of(v.y, m < M ? oz_exp(e[orow + 1]) : 0, qy);
+#pragma unroll
+        for (int t = 0; t < OZ_S; ++t) p0[t * slice + Kp] = qy[t];
+      }
+    }
+    return;
+  }
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int m = m0 + r, k = k0 + threadIdx.x;
     const int orow = form == 0 ? m : 2 * m;
@@ -628,22 +678,24 @@ int oz_slice_rows(const double* src, int ld, int rows, int K, int form, void* me
 // per column; form 2: the outer product's B pair).
 int oz_slice_cols(const double* src, int ld, int K, int cols, int form, void* mem, OzOperand* out,
                   cudaStream_t st, Prof* pf) {
-  const int rows_out = form == 0 ? cols : 2 * cols;
-  *out = oz_carve(mem, rows_out, K);
+  const bool real_k = form >= 4;
+  const int rows_out = (form == 0 || form == 5) ? cols : 2 * cols;
+  *out = oz_carve(mem, rows_out, real_k ? (K + 1) / 2 : K);
   {
     ProfScope ps(pf, "k_oz_colmax", st);
-    if (cudaMemsetAsync(out->e, 0x80, (size_t)cols * sizeof(int), st) != cudaSuccess) {
+    if (cudaMemsetAsync(out->e, 0x80, (size_t)out->rows_p * sizeof(int), st) != cudaSuccess) {
       set_error("oz_slice_cols: memset failed");
       return QE_ECUDA;
     }
     dim3 gm((cols + 255) / 256, (K + 63) / 64);
-    k_oz_colmax<<<gm, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols, out->e);
+    k_oz_colmax<<<gm, 256, 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols,
+                                    form == 4 ? 1 : 0, out->e);
     int rc = oz_check("k_oz_colmax");
     if (rc) return rc;
   }
   ProfScope ps(pf, "k_oz_slice_cols", st);
-  const int cols_p = form == 0 ? out->rows_p : out->rows_p / 2;
-  dim3 g((cols_p + 31) / 32, out->Kp / 64);
+  const int cols_p = rows_out == cols ? out->rows_p : out->rows_p / 2;
+  dim3 g((cols_p + 31) / 32, real_k ? out->Kp / 32 : out->Kp / 64);
   k_oz_slice_cols<<<g, dim3(32, 8), 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols,
                                              form, out->e, out->rows_p, out->Kp, out->q);
   return oz_check("k_oz_slice_cols");
@@ -1001,6 +1053,35 @@ int oz_outer(const double* A, int lda, const double* B, int ldb, int M, int N, i
   p += oz_operand_bytes(M, K);
   if ((rc = oz_slice_cols(B, ldb, K, N, 2, p, &b, st, pf))) return rc;
   return oz_gemm_outer(a, b, M, N, C, ldc, alpha_neg, beta, status, st, pf);
+}
+
+// C[n][m] (+)= (-) sum_k A[k][m] Re B[k][n] (B real, its imaginary parts not
+// read): A's columns sliced as separate real and imaginary rows over a real K
+// axis (form 4), B's columns as real rows (form 5), so the GEMM has 2M rows, N
+// columns and depth K -- half the tensor-core work of the complex form, whose
+// B pair rows would carry the zero imaginary parts.
+size_t oz_outer_real_scratch(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 0;
+  const int kc = (K + 1) / 2;
+  return oz_operand_bytes(2 * M, kc) + oz_operand_bytes(N, kc);
+}
+
+int oz_outer_real(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+                  double* C, int ldc, int alpha_neg, int beta, void* scratch, size_t scratch_bytes,
+                  int* status, cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  if (oz_outer_real_scratch(M, N, K) > scratch_bytes) {
+    set_error("oz_outer_real: scratch too small");
+    return QE_EINVAL;
+  }
+  char* p = static_cast<char*>(scratch);
+  OzOperand a, b;
+  int rc;
+  if ((rc = oz_slice_cols(A, lda, K, M, 4, p, &a, st, pf))) return rc;
+  p += oz_operand_bytes(2 * M, (K + 1) / 2);
+  if ((rc = oz_slice_cols(B, ldb, K, N, 5, p, &b, st, pf))) return rc;
+  return oz_launch(a, b, 2 * M, N, reinterpret_cast<double2*>(C), ldc, 0, 1, alpha_neg, beta, 2,
+                   status, st, pf);
 }
 
 // ---- the nonlocal term -----------------------------------------------------------

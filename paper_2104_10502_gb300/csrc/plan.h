@@ -291,5 +291,10 @@ int oz_inner(const double* A, int lda, const double* B, int ldb, int M, int N, i
 int oz_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
              int ldc, int alpha_neg, int beta, void* scratch, size_t scratch_bytes, int* status,
              cudaStream_t st, Prof* pf);
+// oz_outer with a real B (imaginary parts ignored): half the tensor-core work.
+size_t oz_outer_real_scratch(int M, int N, int K);
+int oz_outer_real(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+                  double* C, int ldc, int alpha_neg, int beta, void* scratch, size_t scratch_bytes,
+                  int* status, cudaStream_t st, Prof* pf);
 
 }  // namespace qe
