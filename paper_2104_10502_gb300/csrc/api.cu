@@ -336,16 +336,19 @@ static int hpsi_device_nonlocal(qe_ctx* ctx, const DevPlan& P, const OpView& op,
     const size_t before_bytes = ctx->oz_beta.bytes;
     QE_TRY(ctx->oz_beta.ensure(nonlocal_oz_beta_bytes(np, npw)));
     if (ctx->oz_beta.p != before || ctx->oz_beta.bytes != before_bytes) ctx->oz_beta_tag = 0;
-    const bool slice = ctx->oz_beta_tag == 0 || ctx->oz_beta_tag != op.tag;
+    // the kept column slices have one of two forms (complex or real-K)
+    const int form = nonlocal_oz_real_outer(pair, np) ? 4 : 0;
+    const bool slice = ctx->oz_beta_tag == 0 || ctx->oz_beta_tag != op.tag || ctx->oz_beta_form != form;
     if (op.gen && slice) {
       // projectors generated on the fly straight into the slices: no beta array
       QE_TRY(ctx->gen_scr.ensure(oz_gen_scratch_bytes(*op.gen)));
-      QE_TRY(oz_gen_beta(*op.gen, ctx->oz_beta.p, ctx->gen_scr.p, st, &ctx->prof));
+      QE_TRY(oz_gen_beta(*op.gen, ctx->oz_beta.p, ctx->gen_scr.p, st, &ctx->prof, form == 4));
     }
     QE_TRY(nonlocal_oz(op.beta, op.dmat, psi, hpsi, np, nb, npw, ctx->oz_beta.p, slice && !op.gen,
                        ctx->oz_work.p, ctx->oz_work.bytes, (int*)ctx->tc_status.p, st, &ctx->prof,
                        pair));
     ctx->oz_beta_tag = op.tag;
+    ctx->oz_beta_form = form;
   } else if (op.nproj > 0) {
     const int np = op.nproj;
     QE_TRY(ctx->proj.ensure((size_t)np * nb * 2 * sizeof(double)));

@@ -34,6 +34,7 @@ struct qe_ctx {
   // FP64 path on the tensor cores: beta slices (tagged like tc_beta) and work
   qe::DevBuf oz_beta, oz_work;
   unsigned long long oz_beta_tag = 0;
+  int oz_beta_form = 0;        // form of the kept column slices (0 complex, 4 real-K)
   // the packed beta in tc_beta belongs to the operator with this tag (0: none);
   // every API call that takes an operator gets a fresh tag
   unsigned long long tc_beta_tag = 0, op_tag = 0;

@@ -268,6 +268,11 @@ struct DvState {
   // FP64 subspace products on the tensor cores: operand slices + partials
   void* oz = nullptr;
   size_t oz_bytes = 0;
+  // the row slices of V[0:vrows), kept across products (oz_cache_rows): the
+  // basis only grows by appended rows between the points that rewrite it
+  // (restart, collapse, refinement), which set vrows = 0
+  void* vcache = nullptr;
+  int vrows = 0;
   // the mixed path's subspace products on the tensor cores (TF32 x3)
   void* tc = nullptr;
   size_t tc_bytes = 0;
@@ -302,6 +307,13 @@ static size_t dv_oz_bytes(size_t npw, size_t nb, size_t md, bool fp64) {
                   oz_outer_scratch((int)npw, (int)nb, (int)n)) + 256;
 }
 
+// The kept row slices of the basis, where its inner products run on the tensor
+// cores.
+static size_t dv_vcache_bytes(size_t npw, size_t nb, size_t md) {
+  if (!fp64_gemm_on_tensor_cores() || !oz_worth((long long)md, (long long)nb, (long long)npw)) return 0;
+  return oz_cache_bytes((int)md, (int)npw) + 256;
+}
+
 static size_t dv_bytes(size_t npw, size_t nb, size_t md) {
   const size_t zb = sizeof(z);
   const size_t big = (2 * md + 5 * nb) * npw * zb;
@@ -325,7 +337,8 @@ size_t davidson_footprint(int npw, int nb, int max_dim, int nproj, const int gri
   const size_t ngrid = (size_t)grid[0] * grid[1] * grid[2];
   const size_t per_band = (size_t)grid[2] * nst * sizeof(z);
   const size_t nbc = std::max<size_t>(1, std::min<size_t>(nb, ((size_t)64 << 20) / std::max<size_t>(per_band, 1)));
-  size_t b = dv_bytes(npw, nb, md) + dv_red_bytes(md) + dv_oz_bytes(npw, nb, md, true);
+  size_t b = dv_bytes(npw, nb, md) + dv_red_bytes(md) + dv_oz_bytes(npw, nb, md, true) +
+             dv_vcache_bytes(npw, nb, md);
   b += ngrid * sizeof(double) * 2;                                  // V copy + permuted V
   b += nbc * per_band;                                              // stick buffer
   b += gemm_inner_scratch(nproj, nb, npw, sizeof(double));          // split-K partials
@@ -401,13 +414,16 @@ static int dv_alloc(DevBuf& basis, DevBuf& red, DvState& S, bool fp64) {
   const size_t sb = dv_red_bytes(md);
   const size_t ob = dv_oz_bytes(npw, nb, md, fp64);
   const size_t tb = dv_tc_bytes(npw, nb, md, fp64);
-  DV_TRY(red.ensure(sb + ob + tb));
+  const size_t vb = dv_vcache_bytes(npw, nb, md);
+  DV_TRY(red.ensure(sb + ob + tb + vb));
   S.part = red.p;
   S.part_bytes = sb;
   S.oz = ob ? static_cast<char*>(red.p) + sb : nullptr;
   S.oz_bytes = ob;
   S.tc = tb ? static_cast<char*>(red.p) + sb + ob : nullptr;
   S.tc_bytes = tb;
+  S.vcache = vb ? static_cast<char*>(red.p) + sb + ob + tb : nullptr;
+  S.vrows = 0;
   return QE_OK;
 }
 
@@ -420,8 +436,18 @@ static int* dv_tc_status(const DvState& S) { return S.dw.status + 12; }
 // path drops Im C in its split reduction, the FP64 tensor-core path computes
 // only Re C, the FP32 one drops Im C after).
 template <typename T>
-static int gram(const DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
+static int gram(DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
                 cudaStream_t st, Prof* pf) {
+  if (sizeof(T) == sizeof(double) && A == S.V && S.vcache && S.oz && oz_worth(m, n, S.npw) &&
+      oz_inner_cached_scratch(m, n, S.npw) <= S.oz_bytes) {
+    // the basis: slice only the rows added since the last product with it
+    if (S.vrows < m) {
+      DV_TRY(oz_cache_rows((const double*)S.V, S.npw, S.vrows, m, S.npw, S.max_dim, S.vcache, st, pf));
+      S.vrows = m;
+    }
+    return oz_inner_cached(S.vcache, S.max_dim, m, (const double*)B, S.npw, n, S.npw, (double*)C, ldc,
+                           S.oz, S.oz_bytes, dv_tc_status(S), st, pf, S.gamma);
+  }
   if (sizeof(T) == sizeof(float) && S.tc && tc_worth(m, n, S.npw)) {
     DV_TRY(tc_inner((const double*)A, (const double*)B, m, n, S.npw, (double*)C, ldc, S.tc,
                     S.tc_bytes, dv_tc_status(S), st, pf));
@@ -471,7 +497,7 @@ static int outer(const DvState& S, const z* A, int lda, const z* B, int ldb, int
 // Reduced matrices: columns [n0, n1) for rows [0, n1), then the mirrored rows.
 // The overlap S_r only when the Rayleigh-Ritz that follows is a generalised one.
 template <typename T>
-static int update_reduced(const DvState& S, int n0, int n1, bool with_s, cudaStream_t st, Prof* pf) {
+static int update_reduced(DvState& S, int n0, int n1, bool with_s, cudaStream_t st, Prof* pf) {
   const int md = S.max_dim;
   DV_TRY(gram<T>(S, S.V, n1, S.HV + (size_t)n0 * S.npw, n1 - n0, S.Hr + n0, md, st, pf));
   if (with_s) DV_TRY(gram<T>(S, S.V, n1, S.V + (size_t)n0 * S.npw, n1 - n0, S.Sr + n0, md, st, pf));
@@ -788,6 +814,7 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
 // applies FP64 H to them into HV[0:nb], refine_post does the Rayleigh-Ritz.
 static int refine_pre(DvState& S, cudaStream_t st) {
   DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)S.nb * S.npw * sizeof(z), cudaMemcpyDeviceToDevice, st));
+  S.vrows = 0;   // V rewritten: its kept slices are stale
   return QE_OK;
 }
 
@@ -854,6 +881,7 @@ static int dv_begin(DvSolve& v, cudaStream_t st) {
   DV_CU(cudaMemsetAsync(S.dw.status, 0, 16 * sizeof(int), st));
   if (S.gamma) {
     k_gamma_start<<<nb, 256, 0, st>>>(S.V, npw, S.mg);
+    S.vrows = 0;   // V rewritten: its kept slices are stale
     DV_TRY(check_launch("k_gamma_start"));
   }
   v.e.assign(nb, 0.0);
@@ -894,6 +922,7 @@ static int dv_step_launch(DvSolve& v, cudaStream_t st, Prof* pf) {
   if (v.first) {
     // the Ritz vectors of the start block become the (orthonormal) basis
     DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+    S.vrows = 0;   // V rewritten: its kept slices are stale
     DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
     v.n = nb;
     DV_TRY(update_reduced<T>(S, 0, v.n, true, st, pf));
@@ -970,6 +999,7 @@ static int dv_step_finish(qe_ctx* ctx, DvSolve& v, cudaStream_t st, Prof* pf) {
   }
   if (v.n + nu > md) {
     DV_CU(cudaMemcpyAsync(S.V, S.Psi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
+    S.vrows = 0;   // V rewritten: its kept slices are stale
     DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, (size_t)nb * npw * zb, cudaMemcpyDeviceToDevice, st));
     v.n = nb;
     DV_TRY(update_reduced<T>(S, 0, v.n, true, st, pf));
@@ -1034,6 +1064,7 @@ static int dv_fp64_begin(qe_ctx* ctx, DvSolve& v, cudaStream_t st, bool* more) {
   if (all || v.it >= v.max_iter) return QE_OK;
   const size_t bytes = (size_t)nb * npw * sizeof(z);
   DV_CU(cudaMemcpyAsync(S.V, S.Psi, bytes, cudaMemcpyDeviceToDevice, st));
+  S.vrows = 0;   // V rewritten: its kept slices are stale
   DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, bytes, cudaMemcpyDeviceToDevice, st));
   v.n = nb;
   DV_TRY(update_reduced<double>(S, 0, nb, true, st, &ctx->prof));
@@ -1367,6 +1398,7 @@ static int cg_rotate(qe_ctx* ctx, DvSolve& v, cudaStream_t st, double* rmax) {
   const int nb = S.nb, npw = S.npw;
   const size_t bytes = (size_t)nb * npw * sizeof(z);
   DV_CU(cudaMemcpyAsync(S.V, S.Psi, bytes, cudaMemcpyDeviceToDevice, st));
+  S.vrows = 0;   // V rewritten: its kept slices are stale
   DV_CU(cudaMemcpyAsync(S.HV, S.HPsi, bytes, cudaMemcpyDeviceToDevice, st));
   DV_TRY(update_reduced<T>(S, 0, nb, true, st, pf));
   DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
@@ -1529,6 +1561,7 @@ int dv_task_create(qe_ctx* ctx, const qe_problem* prob, int precision, double to
   DvState& S = t->v.S;
   DV_CU(cudaMemcpyAsync(S.V, psi0, (size_t)S.nb * S.npw * sizeof(z),
                         dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  S.vrows = 0;
   DV_TRY(dv_begin(t->v, st));
   t->phase = DV_FIRST_H;
   t->h_prec = precision;
@@ -1740,6 +1773,7 @@ extern "C" int qe_davidson(qe_ctx* ctx, const qe_problem* prob, int precision, d
   const cudaMemcpyKind in_kind = prob->mem == QE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const cudaMemcpyKind out_kind = prob->mem == QE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   DV_CU(cudaMemcpyAsync(S.V, psi_inout, bytes, in_kind, st));
+  S.vrows = 0;   // V rewritten: its kept slices are stale
   int rc = precision == QE_FP64 ? davidson_run<double>(ctx, v, st) : davidson_run<float>(ctx, v, st);
   if (iters) *iters = v.it;
   if (rc && rc != QE_ENOCONV) return rc;
@@ -1866,11 +1900,13 @@ extern "C" int qe_cg(qe_ctx* ctx, const qe_problem* prob, int precision, double 
   DV_TRY(dv_setup(ctx, prob, precision, tol, max_iter, std::max(default_max_dim(nb), nb + 4),
                   ctx->dv_basis, ctx->dv_red, v, st, "qe_cg", false));
   DvState& S = v.S;
+  S.vcache = nullptr;   // the CG keeps scratch rows in V past the bands: no kept slices
   if (S.max_dim < nb + 4) { set_error("qe_cg: %d bands need more plane waves", nb); return QE_EINVAL; }
   const size_t bytes = (size_t)nb * S.npw * sizeof(z);
   const cudaMemcpyKind in_kind = prob->mem == QE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   const cudaMemcpyKind out_kind = prob->mem == QE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   DV_CU(cudaMemcpyAsync(S.V, psi_inout, bytes, in_kind, st));
+  S.vrows = 0;   // V rewritten: its kept slices are stale
   CgRun run;
   const int rc = cg_run(ctx, v, tol, max_iter, max_sweeps, run, st);
   if (iters) *iters = run.iters;

@@ -628,7 +628,8 @@ static int oz_map(CUtensorMap* m, const __nv_bfloat16* ptr, int rows, int Kp, in
 struct OzOperand {
   __nv_bfloat16* q = nullptr;
   int* e = nullptr;
-  int rows_p = 0, Kp = 0;
+  int rows_p = 0, Kp = 0;   // the allocation: [S][rows_p][Kp]
+  int rows_used = 0;        // rows the products tile (<= rows_p, a multiple of 128)
 };
 
 size_t oz_operand_bytes(int rows_out, int K) {
@@ -639,6 +640,7 @@ size_t oz_operand_bytes(int rows_out, int K) {
 static OzOperand oz_carve(void* mem, int rows_out, int K) {
   OzOperand o;
   o.rows_p = pad_to(std::max(rows_out, 1), OZ_BM);
+  o.rows_used = o.rows_p;
   o.Kp = pad_to(2 * std::max(K, 1), OZ_BK);
   char* p = reinterpret_cast<char*>(((uintptr_t)mem + 255) & ~(uintptr_t)255);
   o.q = reinterpret_cast<__nv_bfloat16*>(p);
@@ -726,7 +728,8 @@ __device__ __forceinline__ double gen_amp(const GenProj& g, int n, int c, int G,
 
 // Exponent bounds.  grid (ceil(npw / 256), 1): per-G column exponents, and the
 // per-component maxima merged with atomicMax (as ordered bit patterns) into cmax.
-__global__ void k_gen_exps(GenProj g, unsigned long long* __restrict__ cmax, int* __restrict__ ecol) {
+__global__ void k_gen_exps(GenProj g, unsigned long long* __restrict__ cmax, int* __restrict__ ecol,
+                           int form4) {
   const int G = blockIdx.x * blockDim.x + threadIdx.x;
   if (G >= g.npw) return;
   double q[3];
@@ -739,7 +742,13 @@ __global__ void k_gen_exps(GenProj g, unsigned long long* __restrict__ cmax, int
       mx = fmax(mx, a);
       atomicMax(&cmax[j], mag_bits(a));
     }
-  ecol[G] = mx > 0.0 ? exp_bound(mx * (1.0 + 0x1p-40)) : (int)0x80808080;
+  const int ex = mx > 0.0 ? exp_bound(mx * (1.0 + 0x1p-40)) : (int)0x80808080;
+  if (form4) {   // |Re beta|, |Im beta| <= |beta|: the bound of both rows of G
+    ecol[2 * G] = ex;
+    ecol[2 * G + 1] = ex;
+  } else {
+    ecol[G] = ex;
+  }
 }
 
 // Row exponents of every projector from the component maxima.
@@ -789,13 +798,13 @@ __device__ __forceinline__ void gen_atom(const GenProj& g, int I, int G, F&& f) 
 __global__ void __launch_bounds__(128) k_gen_slices(GenProj g, const int* __restrict__ erow,
                                                     const int* __restrict__ ecol, int rows_p1, int Kp1,
                                                     unsigned* __restrict__ Q1, int rows_p2, int Kp2,
-                                                    unsigned* __restrict__ Q2) {
+                                                    unsigned* __restrict__ Q2, int form4) {
   extern __shared__ unsigned sQ[];
   const int G0 = blockIdx.x * blockDim.x, G = G0 + threadIdx.x, I = blockIdx.y;
   const int nper = g.nper, nt = blockDim.x;
   const size_t s1 = (size_t)rows_p1 * Kp1 / 2, s2 = (size_t)rows_p2 * Kp2 / 2;
   if (G < g.npw) {
-    const int ec = oz_exp(ecol[G]);
+    const int ec = oz_exp(ecol[form4 ? 2 * G : G]);
     gen_atom(g, I, G, [&](int i, double2 v) {
       unsigned short qx[OZ_S], qy[OZ_S];
       const int er = oz_exp(erow[i]);
@@ -814,6 +823,20 @@ __global__ void __launch_bounds__(128) k_gen_slices(GenProj g, const int* __rest
   __syncthreads();
   const int rows = min(nt, g.npw - G0);
   const int per_t = rows * nper;
+  if (form4) {
+    // real K axis: row 2G the real parts, row 2G+1 the imaginary parts (BF16 each)
+    unsigned short* Qu = reinterpret_cast<unsigned short*>(Q2);
+    const size_t su = (size_t)rows_p2 * Kp2;
+    for (int w = threadIdx.x; w < OZ_S * per_t; w += nt) {
+      const int t = w / per_t, r = w - t * per_t;
+      const int gg = r / nper, j = r - gg * nper;
+      const unsigned v = sQ[((size_t)t * nt + gg) * nper + j];
+      unsigned short* q = Qu + t * su + (size_t)(2 * (G0 + gg)) * Kp2 + (size_t)I * nper + j;
+      q[0] = (unsigned short)(v & 0xFFFFu);
+      q[Kp2] = (unsigned short)(v >> 16);
+    }
+    return;
+  }
   for (int w = threadIdx.x; w < OZ_S * per_t; w += nt) {
     const int t = w / per_t, r = w - t * per_t;
     const int gg = r / nper, j = r - gg * nper;
@@ -846,34 +869,41 @@ size_t oz_gen_scratch_bytes(const GenProj& g) {
   return up256((size_t)g.nper * sizeof(unsigned long long)) + 256;
 }
 
-int oz_gen_beta(const GenProj& g, void* bslices, void* scratch, cudaStream_t st, Prof* pf) {
+int oz_gen_beta(const GenProj& g, void* bslices, void* scratch, cudaStream_t st, Prof* pf, bool form4) {
   if (g.np <= 0 || g.npw <= 0) return QE_OK;
+  if (form4 && g.np % 2 != 0) {
+    set_error("oz_gen_beta: the real-K column form needs an even projector count");
+    return QE_EINVAL;
+  }
   char* bs = static_cast<char*>(bslices);
   const OzOperand A1 = oz_carve(bs, g.np, g.npw);
-  const OzOperand A2 = oz_carve(bs + oz_operand_bytes(g.np, g.npw), g.npw, g.np);
+  const OzOperand A2 = form4 ? oz_carve(bs + oz_operand_bytes(g.np, g.npw), 2 * g.npw, g.np / 2)
+                             : oz_carve(bs + oz_operand_bytes(g.np, g.npw), g.npw, g.np);
   unsigned long long* cmax = static_cast<unsigned long long*>(scratch);
   ProfScope ps(pf, "k_gen_slices", st);
   if (cudaMemsetAsync(cmax, 0, (size_t)g.nper * sizeof(unsigned long long), st) != cudaSuccess) {
     set_error("oz_gen_beta: memset failed");
     return QE_ECUDA;
   }
-  k_gen_exps<<<(g.npw + 255) / 256, 256, 0, st>>>(g, cmax, A2.e);
+  k_gen_exps<<<(g.npw + 255) / 256, 256, 0, st>>>(g, cmax, A2.e, form4 ? 1 : 0);
   k_gen_erow<<<(g.np + 255) / 256, 256, 0, st>>>(g, cmax, A1.e);
   int rc = oz_check("k_gen_exps");
   if (rc) return rc;
   unsigned* Q1 = reinterpret_cast<unsigned*>(A1.q);
   unsigned* Q2 = reinterpret_cast<unsigned*>(A2.q);
   const size_t s1 = (size_t)A1.rows_p * A1.Kp / 2, s2 = (size_t)A2.rows_p * A2.Kp / 2;
-  // the padding of both slicings, then the values
+  // the padding of both slicings (uint32 words: pairs of BF16), then the values
+  const int rows2 = form4 ? 2 * g.npw : g.npw, cols2 = form4 ? g.np / 2 : g.np;
   if ((rc = zero_rect(Q1, s1, A1.Kp / 2, g.np, A1.rows_p, 0, A1.Kp / 2, st)) ||
       (rc = zero_rect(Q1, s1, A1.Kp / 2, 0, g.np, g.npw, A1.Kp / 2, st)) ||
-      (rc = zero_rect(Q2, s2, A2.Kp / 2, g.npw, A2.rows_p, 0, A2.Kp / 2, st)) ||
-      (rc = zero_rect(Q2, s2, A2.Kp / 2, 0, g.npw, g.np, A2.Kp / 2, st)))
+      (rc = zero_rect(Q2, s2, A2.Kp / 2, rows2, A2.rows_p, 0, A2.Kp / 2, st)) ||
+      (rc = zero_rect(Q2, s2, A2.Kp / 2, 0, rows2, cols2, A2.Kp / 2, st)))
     return rc;
   const size_t gsm = (size_t)OZ_S * 128 * g.nper * sizeof(unsigned);   // <= 96 KB (nper <= 24)
   set_max_dynamic_smem(k_gen_slices);
   k_gen_slices<<<dim3((g.npw + 127) / 128, g.natom), 128, gsm, st>>>(g, A1.e, A2.e, A1.rows_p, A1.Kp,
-                                                                      Q1, A2.rows_p, A2.Kp, Q2);
+                                                                      Q1, A2.rows_p, A2.Kp, Q2,
+                                                                      form4 ? 1 : 0);
   if (pf) pf->launches += 6;
   return oz_check("k_gen_slices");
 }
@@ -931,7 +961,7 @@ static int oz_launch(const OzOperand& A, const OzOperand& B, int M, int N, doubl
   const int per = (nks + nsplit - 1) / nsplit;
   set_max_dynamic_smem(k_oz_gemm);
   ProfScope ps(pf, "k_oz_gemm", st);
-  dim3 g(B.rows_p / OZ_BN, A.rows_p / OZ_BM, nsplit);
+  dim3 g(B.rows_p / OZ_BN, A.rows_used / OZ_BM, nsplit);
   k_oz_gemm<<<g, OZ_THREADS, OZ_SMEM_BYTES, st>>>(mA, mB, A.rows_p, B.rows_p, nks, per, A.e, B.e,
                                                    out, ldo, zstride, M, N, alpha_neg, beta, ecol,
                                                    status);
@@ -951,8 +981,8 @@ int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* 
   const int Nc = N;
   if (real) N = (N + 1) / 2;   // GEMM column pairs
   const int nks = A.Kp / OZ_BK;
-  int ns = oz_splits((A.rows_p / OZ_BM) * (B.rows_p / OZ_BN), nks);
-  const long long zstride = (long long)(B.rows_p / 2) * A.rows_p;
+  int ns = oz_splits((A.rows_used / OZ_BM) * (B.rows_p / OZ_BN), nks);
+  const long long zstride = (long long)(B.rows_p / 2) * A.rows_used;
   const size_t cap = part_bytes / ((size_t)zstride * 16);   // splits the buffer holds
   if (cap < 1) {
     set_error("oz_gemm_inner: partial buffer too small");
@@ -962,7 +992,7 @@ int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* 
     const int per = (nks + (int)cap - 1) / (int)cap;
     ns = (nks + per - 1) / per;
   }
-  int rc = oz_launch(A, B, M, N, reinterpret_cast<double2*>(part), A.rows_p, zstride, ns, 0, 0,
+  int rc = oz_launch(A, B, M, N, reinterpret_cast<double2*>(part), A.rows_used, zstride, ns, 0, 0,
                      real ? 1 : 0, status, st, pf);
   if (rc) return rc;
   const int per = (nks + ns - 1) / ns;
@@ -972,11 +1002,11 @@ int oz_gemm_inner(const OzOperand& A, const OzOperand& B, int M, int N, double* 
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 8);
   if (real)
     k_oz_reduce_real<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(part), nsplit,
-                                             zstride, A.rows_p, M, Nc,
+                                             zstride, A.rows_used, M, Nc,
                                              reinterpret_cast<double2*>(C), ldc);
   else
     k_oz_reduce<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(part), nsplit, zstride,
-                                        A.rows_p, M, N, reinterpret_cast<double2*>(C), ldc);
+                                        A.rows_used, M, N, reinterpret_cast<double2*>(C), ldc);
   return oz_check("k_oz_reduce");
 }
 
@@ -1084,9 +1114,70 @@ int oz_outer_real(const double* A, int lda, const double* B, int ldb, int M, int
                    status, st, pf);
 }
 
+// ---- row slices kept across products -------------------------------------------
+// A matrix whose rows are only ever appended (the Davidson basis) keeps its row
+// slices in `mem` ([S][pad(rows_cap)][Kp], per-row exponents): rows are sliced
+// once, when they are added, and the inner products with its first M rows tile
+// only pad(M) of them.  Rows past M in the last tile may hold older slices; a
+// product row depends on its own A row only, and rows past M are never written.
+size_t oz_cache_bytes(int rows_cap, int K) { return oz_operand_bytes(rows_cap, K); }
+
+int oz_cache_rows(const double* src, int ld, int r0, int r1, int K, int rows_cap, void* mem,
+                  cudaStream_t st, Prof* pf) {
+  if (r1 <= r0) return QE_OK;
+  if (r0 < 0 || r1 > rows_cap) {
+    set_error("oz_cache_rows: rows [%d, %d) outside the cache of %d", r0, r1, rows_cap);
+    return QE_EINVAL;
+  }
+  const OzOperand o = oz_carve(mem, rows_cap, K);
+  const int n = r1 - r0;
+  const double2* s2 = reinterpret_cast<const double2*>(src) + (size_t)r0 * ld;
+  {
+    ProfScope ps(pf, "k_oz_rowmax", st);
+    if (cudaMemsetAsync(o.e + r0, 0x80, (size_t)n * sizeof(int), st) != cudaSuccess) {
+      set_error("oz_cache_rows: memset failed");
+      return QE_ECUDA;
+    }
+    k_oz_rowmax<<<dim3(n, (K + OZ_ROW_CHUNK - 1) / OZ_ROW_CHUNK), 256, 0, st>>>(s2, ld, K, o.e + r0);
+    int rc = oz_check("k_oz_rowmax");
+    if (rc) return rc;
+  }
+  ProfScope ps(pf, "k_oz_slice_rows", st);
+  k_oz_slice_rows<<<dim3(n, (o.Kp / 2 + OZ_ROW_CHUNK - 1) / OZ_ROW_CHUNK), 256, 0, st>>>(
+      s2, ld, n, K, 0, o.rows_p, o.Kp, o.e + r0, o.q + (size_t)r0 * o.Kp);
+  return oz_check("k_oz_slice_rows");
+}
+
+size_t oz_inner_cached_scratch(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 0;
+  return oz_operand_bytes(2 * N, K) + oz_partial_bytes(M, N, K);
+}
+
+// oz_inner with A = the first M rows kept in `mem` (oz_cache_rows).
+int oz_inner_cached(const void* mem, int rows_cap, int M, const double* B, int ldb, int N, int K,
+                    double* C, int ldc, void* scratch, size_t scratch_bytes, int* status,
+                    cudaStream_t st, Prof* pf, bool real) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  if (M > rows_cap || oz_inner_cached_scratch(M, N, K) > scratch_bytes) {
+    set_error("oz_inner_cached: %d rows of %d, or scratch too small", M, rows_cap);
+    return QE_EINVAL;
+  }
+  OzOperand a = oz_carve(const_cast<void*>(mem), rows_cap, K);
+  a.rows_used = pad_to(M, OZ_BM);
+  char* p = static_cast<char*>(scratch);
+  OzOperand b;
+  int rc;
+  if ((rc = oz_slice_rows(B, ldb, N, K, real ? 0 : 1, p, &b, st, pf))) return rc;
+  p += oz_operand_bytes(2 * N, K);
+  return oz_gemm_inner(a, b, M, N, C, ldc, p, oz_partial_bytes(M, N, K), status, st, pf, real);
+}
+
 // ---- the nonlocal term -----------------------------------------------------------
+bool nonlocal_oz_real_outer(bool real_p, int np) { return real_p && np % 2 == 0; }
+
 size_t nonlocal_oz_beta_bytes(int np, int npw) {
-  return oz_operand_bytes(np, npw) + oz_operand_bytes(npw, np);
+  return oz_operand_bytes(np, npw) +
+         std::max(oz_operand_bytes(npw, np), oz_operand_bytes(2 * npw, (np + 1) / 2));
 }
 
 size_t nonlocal_oz_bytes(int np, int nb, int npw) {
@@ -1109,13 +1200,18 @@ int nonlocal_oz(const double* beta, const double* dmat, const double* psi, doubl
   char* bs = static_cast<char*>(bslices);
   OzOperand A1, A2, B1, B2;
   int rc;
+  // real_p: Q = D Re P is real, so the outer product takes beta's columns as
+  // separate real and imaginary rows over a real K axis (half the work)
+  const bool r4 = nonlocal_oz_real_outer(real_p, np);
   if (slice_beta) {
     if ((rc = oz_slice_rows(beta, npw, np, npw, 0, bs, &A1, st, pf))) return rc;
-    if ((rc = oz_slice_cols(beta, npw, np, npw, 0, bs + oz_operand_bytes(np, npw), &A2, st, pf)))
+    if ((rc = oz_slice_cols(beta, npw, np, npw, r4 ? 4 : 0, bs + oz_operand_bytes(np, npw), &A2, st,
+                            pf)))
       return rc;
   } else {
     A1 = oz_carve(bs, np, npw);
-    A2 = oz_carve(bs + oz_operand_bytes(np, npw), npw, np);
+    A2 = r4 ? oz_carve(bs + oz_operand_bytes(np, npw), 2 * npw, (np + 1) / 2)
+            : oz_carve(bs + oz_operand_bytes(np, npw), npw, np);
   }
   char* w = static_cast<char*>(work);
   char* wb1 = w;
@@ -1130,6 +1226,11 @@ int nonlocal_oz(const double* beta, const double* dmat, const double* psi, doubl
                           real_p)))
     return rc;
   if ((rc = dmul(dmat, P, Q, np, nb, st, pf, real_p))) return rc;
+  if (r4) {
+    if ((rc = oz_slice_cols(Q, nb, np, nb, 5, wb2, &B2, st, pf))) return rc;
+    return oz_launch(A2, B2, 2 * npw, nb, reinterpret_cast<double2*>(hpsi), npw, 0, 1, 0, 1, 2,
+                     status, st, pf);
+  }
   if ((rc = oz_slice_cols(Q, nb, np, nb, 2, wb2, &B2, st, pf))) return rc;
   return oz_gemm_outer(A2, B2, npw, nb, hpsi, npw, 0, 1, status, st, pf);
 }

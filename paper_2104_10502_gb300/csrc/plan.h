@@ -259,8 +259,11 @@ struct GenProj {
 };
 // The two Ozaki slicings of the generated beta (rows for the inner product,
 // columns for the outer one) into bslices (nonlocal_oz_beta_bytes), as
-// nonlocal_oz's own slicing of a stored beta would lay them out.
-int oz_gen_beta(const GenProj& g, void* bslices, void* scratch, cudaStream_t st, Prof* pf);
+// nonlocal_oz's own slicing of a stored beta would lay them out; form4: the
+// columns as separate real and imaginary rows (the k = 0 band-pair products,
+// nonlocal_oz_real_outer).
+int oz_gen_beta(const GenProj& g, void* bslices, void* scratch, cudaStream_t st, Prof* pf,
+                bool form4 = false);
 // Bytes of oz_gen_beta's scratch (the exponent bounds).
 size_t oz_gen_scratch_bytes(const GenProj& g);
 // The generated beta as values, complex [np][npw] (the SIMT and TF32 paths).
@@ -271,6 +274,10 @@ int gen_beta_values(const GenProj& g, double* beta, cudaStream_t st, Prof* pf);
 // work of nonlocal_oz_bytes().
 size_t nonlocal_oz_bytes(int np, int nb, int npw);
 size_t nonlocal_oz_beta_bytes(int np, int npw);
+// Whether nonlocal_oz with real_p keeps beta's column slices in the real-K form
+// (a real Q = D Re P: half the outer product's work); the kept slices of one
+// form do not serve the other.
+bool nonlocal_oz_real_outer(bool real_p, int np);
 int nonlocal_oz(const double* beta, const double* dmat, const double* psi, double* hpsi, int np,
                 int nb, int npw, void* bslices, bool slice_beta, void* work, size_t work_bytes,
                 int* status, cudaStream_t st, Prof* pf, bool real_p = false);
@@ -291,6 +298,16 @@ int oz_inner(const double* A, int lda, const double* B, int ldb, int M, int N, i
 int oz_outer(const double* A, int lda, const double* B, int ldb, int M, int N, int K, double* C,
              int ldc, int alpha_neg, int beta, void* scratch, size_t scratch_bytes, int* status,
              cudaStream_t st, Prof* pf);
+// Row slices of an append-only matrix kept across products (the Davidson
+// basis): oz_cache_rows slices rows [r0, r1) into `mem` (oz_cache_bytes);
+// oz_inner_cached is oz_inner with A = the first M kept rows.
+size_t oz_cache_bytes(int rows_cap, int K);
+int oz_cache_rows(const double* src, int ld, int r0, int r1, int K, int rows_cap, void* mem,
+                  cudaStream_t st, Prof* pf);
+size_t oz_inner_cached_scratch(int M, int N, int K);
+int oz_inner_cached(const void* mem, int rows_cap, int M, const double* B, int ldb, int N, int K,
+                    double* C, int ldc, void* scratch, size_t scratch_bytes, int* status,
+                    cudaStream_t st, Prof* pf, bool real = false);
 // oz_outer with a real B (imaginary parts ignored): half the tensor-core work.
 size_t oz_outer_real_scratch(int M, int N, int K);
 int oz_outer_real(const double* A, int lda, const double* B, int ldb, int M, int N, int K,
