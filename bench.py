@@ -951,6 +951,7 @@ def profile_davidson(name):
 
 SERVE_RATES = (0.25, 0.5, 1.0, 2.0, 4.0, 8.0)
 SERVE_TOL = 1e-3        # the loosest residual of DAV_LADDER that meets 1e-6 Ry on C0 and C2
+SERVE_NREF = 16         # served requests re-solved to residual 1e-9 for the accuracy check
 
 
 def serve_requests(q, ctx, n, seed, dev):
@@ -1004,6 +1005,7 @@ def run_serve_bench(q, ctx, dev, device_index, nreq):
            "npw_range": [min(m["npw"] for m in meta), max(m["npw"] for m in meta)],
            "nb_range": [min(m["nb"] for m in meta), max(m["nb"] for m in meta)]}
     rng = np.random.default_rng(7)
+    burst_res = {}
     for prec, tag in ((q.QE_FP64, "fp64"), (q.QE_MIXED, "mixed")):
         with q.Server(device=device_index, budget_bytes=96 << 30, max_slots=32,
                       max_queue=4 * nreq) as s:
@@ -1012,6 +1014,7 @@ def run_serve_bench(q, ctx, dev, device_index, nreq):
             res = [s.poll(t) for t in ts]
             burst = time.perf_counter() - t0
         cap = len(reqs) / burst
+        burst_res[tag] = res
         block = {"capacity_solves_per_s": cap, "burst_seconds": burst,
                  "converged": int(sum(r["status"] == q.QE_OK for r in res)), "rates": []}
         for f in SERVE_RATES:
@@ -1039,6 +1042,22 @@ def run_serve_bench(q, ctx, dev, device_index, nreq):
                 "p99_ms": float(np.percentile(lat, 99)), "samples": len(rr),
                 "converged": int(sum(r["status"] == q.QE_OK for r in rr))})
         out[tag] = block
+    # accuracy of the served results: the first SERVE_NREF requests solved again
+    # by the FP64 path to residual 1e-9 (the FP64 path is held within 1e-10 Ry
+    # of the oracle by the parity tests), against the burst results of each arm
+    with q.Server(device=device_index, budget_bytes=96 << 30, max_slots=32,
+                  max_queue=4 * nreq) as s:
+        ts = [s.submit(p, x, precision=q.QE_FP64, tol=1e-9, max_iter=600)
+              for p, x, _, _ in reqs[:SERVE_NREF]]
+        ref = [s.poll(t) for t in ts]
+    acc = {"reference": f"FP64 solves of the first {SERVE_NREF} requests to residual 1e-9",
+           "reference_converged": int(sum(r["status"] == q.QE_OK for r in ref))}
+    for tag in ("fp64", "mixed"):
+        errs = [float(np.abs(b["evals"] - r["evals"]).max())
+                for b, r in zip(burst_res[tag][:SERVE_NREF], ref)]
+        acc[tag] = {"max_abs_eig_err_ry": max(errs), "per_request_ry": errs,
+                    "max_resid_all_requests": float(max(r["resid"].max() for r in burst_res[tag]))}
+    out["accuracy"] = acc
     return out
 
 
