@@ -171,9 +171,16 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
   } else if (warp == 9 && lane == 0 && nk > 0) {
     // MMA issuer: for every K step and A slice t, the pairs (t, u), u <= S-1-t,
-    // into the accumulator of diagonal d = t + u
+    // into the accumulator of diagonal d = t + u.  Fully unrolled over (t, u,
+    // kk): the A stage, its phase and every descriptor offset are constants
+    // (the K step's S slices fill S / ASTAGES whole turns of the A ring), so an
+    // MMA costs one add and one OR of the issuing thread, not a descriptor build.
+    static_assert(OZ_S % OZ_ASTAGES == 0 && (OZ_S / OZ_ASTAGES) % 2 == 0,
+                  "a K step must take an even number of turns of the A ring");
     const uint32_t idesc = oz_idesc();
-    int j = 0, c = 0;
+    const uint64_t dhi = sw128_desc(0);
+    const uint32_t a_lo0 = (smem_u32(sA) & 0x3FFFF) >> 4, b_lo0 = (smem_u32(sB) & 0x3FFFF) >> 4;
+    int c = 0;
     bool ok = true;
     for (int i = 0; i < nk && ok; ++i) {
       const bool cstart = (i % OZ_KPC) == 0;
@@ -188,22 +195,24 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         ok = false;
         break;
       }
-      const uint32_t bbase = smem_u32(sB + sb * OZ_BSTAGE_BYTES);
-      for (int t = 0; t < OZ_S; ++t, ++j) {
-        const int sa = j % OZ_ASTAGES;
-        if (!mbar_wait(&afull[sa], (uint32_t)(j / OZ_ASTAGES) & 1u, limit)) {
+      const uint32_t b_lo = b_lo0 + (uint32_t)sb * (OZ_BSTAGE_BYTES >> 4);
+#pragma unroll
+      for (int t = 0; t < OZ_S; ++t) {
+        const int sa = t % OZ_ASTAGES;
+        if (!mbar_wait(&afull[sa], (uint32_t)(t / OZ_ASTAGES) & 1u, limit)) {
           atomicExch(&s_err, OZ_TIMEOUT);
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t abase = smem_u32(sA + sa * OZ_A_BYTES);
+        const uint32_t a_lo = a_lo0 + (uint32_t)sa * (OZ_A_BYTES >> 4);
+#pragma unroll
         for (int u = 0; u < OZ_S - t; ++u) {
           const uint32_t dt = tmem + (uint32_t)((t + u) * OZ_BN);
 #pragma unroll
           for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-            const uint64_t ad = sw128_desc(abase + kk * 32);
-            const uint64_t bd = sw128_desc(bbase + u * OZ_B_BYTES + kk * 32);
+            const uint64_t ad = dhi | (uint64_t)(a_lo + kk * 2);
+            const uint64_t bd = dhi | (uint64_t)(b_lo + u * (OZ_B_BYTES >> 4) + kk * 2);
             mma_bf16(dt, ad, bd, idesc, (cstart && t == 0 && kk == 0) ? 0u : 1u);
           }
         }
