@@ -105,7 +105,10 @@ k_tc_gemm_tf32x3(const __grid_constant__ CUtensorMap mAhi, const __grid_constant
     }
   } else if (nkb > 0 && warp == 1 && lane == 0) {
     // MMA issuer: three split products per K step of 8
+    // descriptors: constant fields once, the start address (16-byte units) per MMA
     const uint32_t idesc = tf32_idesc();
+    const uint64_t dhi = sw128_desc(0);
+    const uint32_t lo0 = (smem_u32(tiles) & 0x3FFFF) >> 4;
     bool ok = true;
     for (int i = 0; i < nkb; ++i) {
       const int s = i % TC_STAGES;
@@ -116,14 +119,14 @@ k_tc_gemm_tf32x3(const __grid_constant__ CUtensorMap mAhi, const __grid_constant
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(tiles + s * TC_STAGE_BYTES);
+      const uint32_t sa = lo0 + (uint32_t)s * (TC_STAGE_BYTES >> 4);
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 8; ++kk) {
-        const uint32_t off = kk * 32;
-        const uint64_t ahi = sw128_desc(sa + off);
-        const uint64_t alo = sw128_desc(sa + TC_TILE_BYTES + off);
-        const uint64_t bhi = sw128_desc(sa + 2 * TC_TILE_BYTES + off);
-        const uint64_t blo = sw128_desc(sa + 3 * TC_TILE_BYTES + off);
+        const uint32_t off = kk * 2;
+        const uint64_t ahi = dhi | (uint64_t)(sa + off);
+        const uint64_t alo = dhi | (uint64_t)(sa + (TC_TILE_BYTES >> 4) + off);
+        const uint64_t bhi = dhi | (uint64_t)(sa + 2 * (TC_TILE_BYTES >> 4) + off);
+        const uint64_t blo = dhi | (uint64_t)(sa + 3 * (TC_TILE_BYTES >> 4) + off);
         mma_tf32(tmem, ahi, bhi, idesc, (i | kk) != 0 ? 1u : 0u);
         mma_tf32(tmem, ahi, blo, idesc, 1u);
         mma_tf32(tmem, alo, bhi, idesc, 1u);
