@@ -147,6 +147,8 @@ int get_plan(qe_ctx* ctx, const double lat[9], const double k[3], double ecut, c
   // square planes with the register-resident transform keep x and y in its order
   P->sq = sq_plane_size(grid);
   if (P->sq) perm[0] = perm[1] = sq_order(P->sq);
+  P->sqz = sq_line_size(grid[2]);
+  if (P->sqz) perm[2] = sq_order(P->sqz);
   // one allocation: doubles first, then ints
   size_t nd = h.npw;
   for (int c = 0; c < 3; ++c) nd += tw[c].size();

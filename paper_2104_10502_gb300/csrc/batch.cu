@@ -50,7 +50,18 @@ struct BatchLayout {
   size_t tc_work = 0, tc_beta = 0;
   size_t oz_work = 0, oz_beta = 0;
   std::vector<char> pair;   // per problem: bands taken two per FFT (real in r, k = 0)
+  bool all_sqz = true;      // every problem's z lines take the two-pass transform
 };
+
+// A problem's launch shape inside a batch: its tuned shape, except that when
+// the batch's z stages run 256 threads (not every problem has two-pass z lines)
+// the two-pass z lines take the 32-stick tiles that suit that thread count.
+template <typename T>
+static FftShape batch_shape(const DevPlan& P, bool all_sqz) {
+  FftShape sh = tuned_shape(P, sizeof(T));
+  if (!all_sqz && P.sqz && sh.spb == 0) sh.spb = default_spb<T>(P.grid[2]);
+  return sh;
+}
 
 template <typename T>
 static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem* probs,
@@ -76,6 +87,7 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
     OpView op;
     BT_TRY(resolve_operator(ctx, pr, *P, op, st));
     L.plans.push_back(P);
+    L.all_sqz = L.all_sqz && P->sqz != 0;   // z stages: 128 threads suit the two-pass z lines
     L.ops.push_back(op);
     L.pair.push_back(pair && pair[p] && P->h.gamma ? 1 : 0);
     const size_t ngrid = (size_t)P->grid[0] * P->grid[1] * P->grid[2];
@@ -83,9 +95,6 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
     off += up256(ngrid * sizeof(T));
     L.w_off.push_back(off);
     off += up256(stick_bytes(*P, std::max(1, pr->nbnd), 2 * sizeof(T)));
-    const FftShape sh = tuned_shape(*P, sizeof(T));
-    const int spb = make_job<T>(*P, nullptr, nullptr, nullptr, nullptr, 0, 1, sh).spb;
-    L.smem_z = std::max(L.smem_z, zsm_bytes<T>(P->grid[2], spb));
     L.smem_p = std::max(L.smem_p, psm_bytes<T>(*P));
     if (op.nproj > 0) {
       L.np_max_part = std::max(L.np_max_part, gemm_inner_scratch(op.nproj, pr->nbnd, P->h.npw, sizeof(T)));
@@ -95,6 +104,11 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
       L.oz_work = std::max(L.oz_work, nonlocal_oz_bytes(op.nproj, pr->nbnd, P->h.npw));
       L.oz_beta = std::max(L.oz_beta, nonlocal_oz_beta_bytes(op.nproj, P->h.npw));
     }
+  }
+  for (int p = 0; p < nprob; ++p) {
+    const int spb = make_job<T>(*L.plans[p], nullptr, nullptr, nullptr, nullptr, 0, 1,
+                                batch_shape<T>(*L.plans[p], L.all_sqz)).spb;
+    L.smem_z = std::max(L.smem_z, zsm_bytes<T>(L.plans[p]->grid[2], spb));
   }
   L.jobs_off = off;
   off += up256((size_t)nprob * sizeof(FftJob<T>));
@@ -129,7 +143,7 @@ static int batch_prepare(qe_ctx* ctx, BatchWork& W, int nprob, const qe_problem*
   pre[nprob + 1] = 0;
   for (int p = 0; p < nprob; ++p) {
     const DevPlan& P = *L.plans[p];
-    const FftShape sh = tuned_shape(P, sizeof(T));
+    const FftShape sh = batch_shape<T>(P, L.all_sqz);
     jobs[p] = make_job<T>(P, psi[p], hpsi[p], reinterpret_cast<const T*>(base + L.vp_off[p]),
                           base + L.w_off[p], 0, probs[p].nbnd, sh, L.pair[p]);
     pre[p + 1] = pre[p] + jobs[p].nb * jobs[p].nsb;   // FFT bands (band pairs with pair)
@@ -147,7 +161,7 @@ static int batch_launch(BatchWork& W, int nprob, const qe_problem* probs, const 
   BT_TRY(launch_local_kinetic_batch<T>(reinterpret_cast<const FftJob<T>*>(base + L.jobs_off),
                                        reinterpret_cast<const int*>(base + L.prefix_off), nprob,
                                        reinterpret_cast<int*>(base + L.counters_off), L.smem_z,
-                                       L.smem_p, 256, st, pf));
+                                       L.smem_p, 256, L.all_sqz ? 128 : 256, st, pf));
   for (int p = 0; p < nprob; ++p) {
     const OpView& op = L.ops[p];
     const int nb = probs[p].nbnd, np = op.nproj, npw = L.plans[p]->h.npw;

@@ -71,6 +71,63 @@ __global__ void k_vperm(const double* __restrict__ v, T* __restrict__ vp, int n1
 }
 
 // ---- tiles ----------------------------------------------------------------------
+// z lines with the register-resident two-pass transform (plane2.cuh): stick l
+// of the tile is the line at line + l with element stride spb; consecutive
+// threads take consecutive sticks.  Each ends with a barrier.
+template <typename T, int N>
+__device__ __forceinline__ void sq_z_inverse(const FftJob<T>& J, cx<T>* line, int spb, int ns,
+                                             const cx<T>* tab) {
+  constexpr int A = SqSplit<N>::A, B = SqSplit<N>::B;
+  const FastDiv fns(ns);
+  for (int it = threadIdx.x; it < ns * B; it += blockDim.x) {
+    const int n2 = fns.div(it), l = it - n2 * ns;
+    if (J.pr3) sq_inv1<T, N, true>(line + l, spb, n2, tab);
+    else sq_inv1<T, N, false>(line + l, spb, n2, tab);
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < ns * A; it += blockDim.x) {
+    const int k1 = fns.div(it), l = it - k1 * ns;
+    cx<T>* p = line + l;
+    cx<T> o[B];
+    sq_inv2_regs<T, N>(p, spb, k1, tab, o);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) p[(B * k1 + k2) * spb] = o[k2];
+  }
+  __syncthreads();
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void sq_z_forward(const FftJob<T>& J, cx<T>* line, int spb, int ns,
+                                             const cx<T>* tab) {
+  constexpr int A = SqSplit<N>::A, B = SqSplit<N>::B;
+  const FastDiv fns(ns);
+  for (int it = threadIdx.x; it < ns * A; it += blockDim.x) {
+    const int k1 = fns.div(it), l = it - k1 * ns;
+    cx<T>* p = line + l;
+    cx<T> in[B], f[B];
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) in[k2] = p[(B * k1 + k2) * spb];
+    sq_fwd1_regs<T, N>(in, k1, tab, f);
+#pragma unroll
+    for (int m2 = 0; m2 < B; ++m2) p[(B * k1 + m2) * spb] = f[m2];
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < ns * B; it += blockDim.x) {
+    const int m2 = fns.div(it), l = it - m2 * ns;
+    if (J.pr3) sq_fwd2<T, N, true>(line + l, spb, m2, tab);
+    else sq_fwd2<T, N, false>(line + l, spb, m2, tab);
+  }
+  __syncthreads();
+}
+
+#define QE_SQZ_DISPATCH(CALL) \
+  switch (J.sqz) {            \
+    case 96: CALL(96); break; \
+    case 48: CALL(48); break; \
+    case 32: CALL(32); break; \
+    default: break;           \
+  }
+
 template <typename T>
 __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* smem) {
   cx<T>* line = reinterpret_cast<cx<T>*>(smem);
@@ -79,8 +136,12 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   const int s0 = sblk * spb;
   const int ns = min(spb, nst - s0);
   for (int i = threadIdx.x; i < n3 * spb; i += blockDim.x) line[i] = cx_zero<T>();
-  const double* tw3 = J.tw3 + (ct_twiddles<T>() ? 2 * n3 : 0);
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw_put<T>(tw, i, tw3[2 * i], tw3[2 * i + 1]);
+  if (J.sqz) {
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) sq_tw_put<T>(tw, i, J.tw3[2 * i], J.tw3[2 * i + 1]);
+  } else {
+    const double* tw3 = J.tw3 + (ct_twiddles<T>() ? 2 * n3 : 0);
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) tw_put<T>(tw, i, tw3[2 * i], tw3[2 * i + 1]);
+  }
   __syncthreads();
   const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
   if (J.pair) {
@@ -101,7 +162,13 @@ __device__ void zinv_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
     }
   }
   __syncthreads();
-  fft_lines<T, +1, false>(line, spb, 1, nullptr, ns, true, J.r3, tw, J.pm3, J.pr3);
+  if (J.sqz) {
+#define QE_SQZ_INV(n) sq_z_inverse<T, n>(J, line, spb, ns, tw)
+    QE_SQZ_DISPATCH(QE_SQZ_INV)
+#undef QE_SQZ_INV
+  } else {
+    fft_lines<T, +1, false>(line, spb, 1, nullptr, ns, true, J.r3, tw, J.pm3, J.pr3);
+  }
   cx<T>* Wb = J.W + (size_t)b * n3 * nst;
   const FastDiv fns(ns);
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
@@ -471,8 +538,12 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
   cx<T>* tw = line + (size_t)n3 * spb;
   const int s0 = sblk * spb;
   const int ns = min(spb, nst - s0);
-  const double* tw3 = J.tw3 + (ct_twiddles<T>() ? 2 * n3 : 0);
-  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw_put<T>(tw, i, tw3[2 * i], tw3[2 * i + 1]);
+  if (J.sqz) {
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) sq_tw_put<T>(tw, i, J.tw3[2 * i], J.tw3[2 * i + 1]);
+  } else {
+    const double* tw3 = J.tw3 + (ct_twiddles<T>() ? 2 * n3 : 0);
+    for (int i = threadIdx.x; i < n3; i += blockDim.x) tw_put<T>(tw, i, tw3[2 * i], tw3[2 * i + 1]);
+  }
   const cx<T>* Wb = J.W + (size_t)b * n3 * nst;
   const FastDiv fns(ns);
   for (int i = threadIdx.x; i < n3 * ns; i += blockDim.x) {
@@ -480,7 +551,13 @@ __device__ void zfwd_tile(const FftJob<T>& J, int b, int sblk, unsigned char* sm
     line[pz * spb + l] = Wb[(size_t)pz * nst + s0 + l];
   }
   __syncthreads();
-  fft_lines<T, -1, true>(line, spb, 1, nullptr, ns, true, J.r3, tw, nullptr, J.pr3);
+  if (J.sqz) {
+#define QE_SQZ_FWD(n) sq_z_forward<T, n>(J, line, spb, ns, tw)
+    QE_SQZ_DISPATCH(QE_SQZ_FWD)
+#undef QE_SQZ_FWD
+  } else {
+    fft_lines<T, -1, true>(line, spb, 1, nullptr, ns, true, J.r3, tw, nullptr, J.pr3);
+  }
   const int e0 = J.st_ptr[s0], e1 = J.st_ptr[s0 + ns];
   if (J.pair) {
     // W = F(V (a + i b)) with a, b real in r: F(V a)_G = (W_G + conj W_-G) / 2,
@@ -774,12 +851,16 @@ __global__ void k_dens_finish(const double* __restrict__ acc, int ngrp, int n1, 
 }
 
 // ---- host side ---------------------------------------------------------------------
-int sq_plane_size(const int grid[3]) {
-  if (grid[0] != grid[1]) return 0;
-  switch (grid[0]) {
-    case 96: case 48: case 32: return grid[0];
+int sq_line_size(int n) {
+  switch (n) {
+    case 96: case 48: case 32: return n;
     default: return 0;
   }
+}
+
+int sq_plane_size(const int grid[3]) {
+  if (grid[0] != grid[1]) return 0;
+  return sq_line_size(grid[0]);
 }
 
 std::vector<int> sq_order(int n) {
@@ -798,6 +879,11 @@ std::vector<int> sq_order(int n) {
 size_t stick_bytes(const DevPlan& P, int nbc, size_t elem_bytes) {
   return (size_t)nbc * P.grid[2] * P.h.nst * elem_bytes;
 }
+
+// z lines with the two-pass transform: 16 sticks and 128 threads per CTA (C1,
+// float-float: z stage 0.124 -> 0.113 ms per 32 bands; 32 sticks or 256
+// threads leave a third of the threads idle in one pass of the two)
+constexpr int kSqzSticks = 16, kSqzThreads = 128;
 
 template <typename T>
 int default_spb(int n3) {
@@ -865,12 +951,13 @@ FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* v
   J.nb = J.pair ? (nb + 1) / 2 : nb;   // FFT bands
   J.self_st = J.pair ? P.h.nst - 1 : -1;
   J.b0 = b0;
-  J.spb = sh.spb > 0 ? sh.spb : default_spb<T>(P.grid[2]);
+  J.spb = sh.spb > 0 ? sh.spb : (P.sqz ? kSqzSticks : default_spb<T>(P.grid[2]));
   if (J.pair) J.spb = std::max(2, J.spb & ~1);   // a tile holds whole mirror pairs
   J.nsb = (J.nst + J.spb - 1) / J.spb;
   J.inv_n = 1.0 / ((double)P.grid[0] * P.grid[1] * P.grid[2]);
   J.stage_v = plane_stages_v<T>(P) ? 1 : 0;
   J.sq = P.sq;
+  J.sqz = P.sqz;
   return J;
 }
 
@@ -905,7 +992,7 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
   set_max_dynamic_smem(k_plane_sq<T, 32>);
   set_max_dynamic_smem(k_zinv<T>);
   set_max_dynamic_smem(k_zfwd<T>);
-  const int zt = sh.zthreads > 0 ? sh.zthreads : 256;
+  const int zt = sh.zthreads > 0 ? sh.zthreads : (J.sqz ? kSqzThreads : 256);
   const int pt = std::min(sh.pthreads > 0 ? sh.pthreads : PlaneLB<T>::dflt, PlaneLB<T>::threads);
   const int pts = std::min(sh.pthreads > 0 ? sh.pthreads : SqLB<T>::dflt, SqLB<T>::threads);
   dim3 gz(J.nsb, J.nb);
@@ -946,7 +1033,7 @@ int launch_local_kinetic(const DevPlan& P, const double* psi, double* hpsi, cons
 // per-item needs over the jobs.
 template <typename T>
 int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev, int njobs,
-                               int* counters, size_t smem_z, size_t smem_p, int threads,
+                               int* counters, size_t smem_z, size_t smem_p, int threads, int zthreads,
                                cudaStream_t st, Prof* pf) {
   if (smem_p > 227 * 1024) {
     set_error("batched FFT: a plane does not fit in shared memory at this precision");
@@ -963,10 +1050,10 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
     return QE_ECUDA;
   }
   int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_batch<T, 0>, threads, smem_z);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_batch<T, 0>, zthreads, smem_z);
   {
     ProfScope ps(pf, "k_zinv_batch", st);
-    k_fft_batch<T, 0><<<nsm * std::max(1, occ), threads, smem_z, st>>>(jobs_dev, prefix_dev, njobs,
+    k_fft_batch<T, 0><<<nsm * std::max(1, occ), zthreads, smem_z, st>>>(jobs_dev, prefix_dev, njobs,
                                                                        counters);
   }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_batch<T, 1>, threads, smem_p);
@@ -975,10 +1062,10 @@ int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev,
     k_fft_batch<T, 1><<<nsm * std::max(1, occ), threads, smem_p, st>>>(
         jobs_dev, prefix_dev + (njobs + 1), njobs, counters + 1);
   }
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_batch<T, 2>, threads, smem_z);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fft_batch<T, 2>, zthreads, smem_z);
   {
     ProfScope ps(pf, "k_zfwd_batch", st);
-    k_fft_batch<T, 2><<<nsm * std::max(1, occ), threads, smem_z, st>>>(jobs_dev, prefix_dev, njobs,
+    k_fft_batch<T, 2><<<nsm * std::max(1, occ), zthreads, smem_z, st>>>(jobs_dev, prefix_dev, njobs,
                                                                        counters + 2);
   }
   return check_launch("batched FFT");
@@ -1003,7 +1090,7 @@ int launch_density(const DevPlan& P, const double* psi, const double* w, void* W
   }
   set_max_dynamic_smem(k_zinv<T>);
   set_max_dynamic_smem(k_dens_plane<T>);
-  const int zt = sh.zthreads > 0 ? sh.zthreads : 256;
+  const int zt = sh.zthreads > 0 ? sh.zthreads : (J.sqz ? kSqzThreads : 256);
   int rc;
   {
     ProfScope ps(pf, "k_zinv", st);
@@ -1034,10 +1121,11 @@ int launch_density_finish(const DevPlan& P, const double* acc, int ngrp, double 
                                              void*, int, int, const FftShape&, cudaStream_t,       \
                                              Prof*, int);                                          \
   template int launch_local_kinetic_batch<T>(const FftJob<T>*, const int*, int, int*, size_t,      \
-                                             size_t, int, cudaStream_t, Prof*);                    \
+                                             size_t, int, int, cudaStream_t, Prof*);               \
   template FftJob<T> make_job<T>(const DevPlan&, const double*, double*, const T*, void*, int,     \
                                  int, const FftShape&, int);                                       \
   template size_t zsm_bytes<T>(int, int);                                                          \
+  template int default_spb<T>(int);                                                                \
   template size_t psm_bytes<T>(const DevPlan&);                                                    \
   template int launch_density<T>(const DevPlan&, const double*, const double*, void*, int, int,    \
                                  int, double*, cudaStream_t, Prof*, int, int);

@@ -88,6 +88,8 @@ static int hpsi_noalloc_impl(const qe_problem* pr, const double* psi, double* hp
   }
   P.sq = sq_plane_size(P.grid);
   if (P.sq) perm[0] = perm[1] = sq_order(P.sq);
+  P.sqz = sq_line_size(P.grid[2]);
+  if (P.sqz) perm[2] = sq_order(P.sqz);
   const int nb = pr->nbnd, np = pr->nproj, npw = h.npw;
   const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
   // layout: plan image | permuted V | projections x2 | stick buffer | split-K partials

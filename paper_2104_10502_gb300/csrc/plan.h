@@ -24,6 +24,8 @@ using GemmT = std::conditional_t<std::is_same<T, float>::value, float, double>;
 
 // Plane size with a register-resident two-pass transform (plane2.cuh), or 0.
 int sq_plane_size(const int grid[3]);
+// n when lines of n points have the register-resident two-pass transform, else 0
+int sq_line_size(int n);
 // perm[p] = natural index held at line position p of that transform of length n.
 std::vector<int> sq_order(int n);
 
@@ -31,6 +33,7 @@ struct DevPlan {
   double lat[9], k[3], ecut;
   int grid[3];
   int sq = 0;   // sq_plane_size(grid): x and y perms are sq_order(n) when non-zero
+  int sqz = 0;  // sq_line_size(grid[2]): the z perm is sq_order(n) when non-zero
   PlanHost h;
   Radix rad[3];
   // device arrays (one allocation)
@@ -133,8 +136,9 @@ struct FftJob {
   int pair, nbr, self_st;
   // sq: N when the planes are N x N with a register-resident two-pass plane
   // transform (plane2.cuh; x and y in its order, the plan's perm[0], perm[1]),
-  // 0 for the stage-by-stage transform
-  int sq;
+  // 0 for the stage-by-stage transform; sqz: the same for the z lines of the
+  // sticks (z in its order, the plan's perm[2])
+  int sq, sqz;
   double inv_n;
 };
 
@@ -143,6 +147,8 @@ struct FftJob {
 template <typename T>
 FftJob<T> make_job(const DevPlan& P, const double* psi, double* hpsi, const T* vp, void* W, int b0,
                    int nb, const FftShape& sh, int pair = 0);
+template <typename T>
+int default_spb(int n3);   // sticks per z tile of the stage-by-stage z lines
 template <typename T>
 size_t zsm_bytes(int n3, int spb);
 template <typename T>
@@ -167,7 +173,7 @@ int launch_local_kinetic_shape(const DevPlan& P, const double* psi, double* hpsi
 template <typename T>
 int launch_local_kinetic_batch(const FftJob<T>* jobs_dev, const int* prefix_dev, int njobs,
                                int* counters, size_t smem_z, size_t smem_p, int threads,
-                               cudaStream_t st, Prof* pf);
+                               int zthreads, cudaStream_t st, Prof* pf);
 
 // Charge density (sum of w |psi(r)|^2): bands b0 .. b0+nbc-1 of psi with device
 // weights w[b] into the group accumulators acc [ngrp][N3][N2][N1] (digit-reversed
