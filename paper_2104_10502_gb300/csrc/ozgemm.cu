@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "common.h"
 #include "plan.h"
@@ -64,6 +65,47 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1.
+template <int I, int N, typename F>
+__device__ __forceinline__ void oz_sfor_from(F& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    oz_sfor_from<I + 1, N>(f);
+  }
+}
+template <int N, typename F>
+__device__ __forceinline__ void oz_sfor(F&& f) {
+  oz_sfor_from<0, N>(f);
+}
+
+// The same with the A operand kept in the tensor core's collector buffer across
+// consecutive MMAs of one A tile: C = 1 fills it (read from shared memory), 2
+// uses it, 3 uses it for the last time.
+template <int C>
+__device__ __forceinline__ void mma_bf16_coll(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accum) {
+  if constexpr (C == 1)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  else if constexpr (C == 2)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  else if constexpr (C == 3)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  else
+    mma_bf16(dtmem, adesc, bdesc, idesc, accum);
 }
 
 // 2^e as a double for the exponent range of normal numbers.
@@ -173,8 +215,9 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     // MMA issuer: for every K step and A slice t, the pairs (t, u), u <= S-1-t,
     // into the accumulator of diagonal d = t + u.  Fully unrolled over (t, u,
     // kk): the A stage, its phase and every descriptor offset are constants
-    // (the K step's S slices fill S / ASTAGES whole turns of the A ring), so an
-    // MMA costs one add and one OR of the issuing thread, not a descriptor build.
+    // (the K step's S slices fill S / ASTAGES whole turns of the A ring; six
+    // stages with runtime indices measured 0.675 -> 0.689 ms), so an MMA costs
+    // one add and one OR of the issuing thread, not a descriptor build.
     static_assert(OZ_S % OZ_ASTAGES == 0 && (OZ_S / OZ_ASTAGES) % 2 == 0,
                   "a K step must take an even number of turns of the A ring");
     const uint32_t idesc = oz_idesc();
@@ -196,28 +239,33 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         break;
       }
       const uint32_t b_lo = b_lo0 + (uint32_t)sb * (OZ_BSTAGE_BYTES >> 4);
-#pragma unroll
-      for (int t = 0; t < OZ_S; ++t) {
-        const int sa = t % OZ_ASTAGES;
+      oz_sfor<OZ_S>([&](auto T) {
+        constexpr int t = decltype(T)::value;
+        if (!ok) return;
+        constexpr int sa = t % OZ_ASTAGES;
         if (!mbar_wait(&afull[sa], (uint32_t)(t / OZ_ASTAGES) & 1u, limit)) {
           atomicExch(&s_err, OZ_TIMEOUT);
           ok = false;
-          break;
+          return;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a_lo = a_lo0 + (uint32_t)sa * (OZ_A_BYTES >> 4);
+        // per 16-deep k slab, the pairs (t, u) one after the other on the same A
+        // slab: it enters the collector buffer once instead of once per pair
 #pragma unroll
-        for (int u = 0; u < OZ_S - t; ++u) {
-          const uint32_t dt = tmem + (uint32_t)((t + u) * OZ_BN);
-#pragma unroll
-          for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-            const uint64_t ad = dhi | (uint64_t)(a_lo + kk * 2);
+        for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+          const uint64_t ad = dhi | (uint64_t)(a_lo + kk * 2);
+          const uint32_t acc = (cstart && t == 0 && kk == 0) ? 0u : 1u;
+          oz_sfor<OZ_S - t>([&](auto U) {
+            constexpr int u = decltype(U)::value, nu = OZ_S - t;
+            constexpr int coll = nu == 1 ? 0 : (u == 0 ? 1 : (u == nu - 1 ? 3 : 2));
+            const uint32_t dt = tmem + (uint32_t)((t + u) * OZ_BN);
             const uint64_t bd = dhi | (uint64_t)(b_lo + u * (OZ_B_BYTES >> 4) + kk * 2);
-            mma_bf16(dt, ad, bd, idesc, (cstart && t == 0 && kk == 0) ? 0u : 1u);
-          }
+            mma_bf16_coll<coll>(dt, ad, bd, idesc, acc);
+          });
         }
         mma_commit(&aempty[sa]);
-      }
+      });
       if (!ok) break;
       mma_commit(&bempty[sb]);
       if ((i % OZ_KPC) == OZ_KPC - 1 || i == nk - 1) {
