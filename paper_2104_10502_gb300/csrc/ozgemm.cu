@@ -57,6 +57,11 @@ __host__ __device__ constexpr uint32_t oz_idesc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(OZ_BN >> 3) << 17) |
          ((uint32_t)(OZ_BM >> 4) << 24);
 }
+// ... with N = n columns (a multiple of 16, at most 256)
+__host__ __device__ constexpr uint32_t oz_idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(OZ_BM >> 4) << 24);
+}
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accum) {
@@ -213,14 +218,17 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
   } else if (warp == 9 && lane == 0 && nk > 0) {
     // MMA issuer: for every K step and A slice t, the pairs (t, u), u <= S-1-t,
-    // into the accumulator of diagonal d = t + u.  Fully unrolled over (t, u,
-    // kk): the A stage, its phase and every descriptor offset are constants
-    // (the K step's S slices fill S / ASTAGES whole turns of the A ring; six
-    // stages with runtime indices measured 0.675 -> 0.689 ms), so an MMA costs
-    // one add and one OR of the issuing thread, not a descriptor build.
+    // into the accumulator of diagonal d = t + u.  The accumulators of the
+    // diagonals t .. S-1 are consecutive in TMEM (64 columns each) and the B
+    // slices u = 0 .. S-1-t consecutive in shared memory (64 rows each), so one
+    // MMA of N = 64 (S - t) columns -- in pieces of at most 256 -- computes all
+    // pairs of slice t: 12 MMAs per 16-deep k slab instead of 36 (one thread
+    // issues them, ~57 cycles each, which had bounded the 128 x 64 x 16 form at
+    // 47 % of the tensor pipe).  The loops are unrolled: the A stage, its phase
+    // and every descriptor are constants (a K step's S slices fill S / ASTAGES
+    // whole turns of the A ring).
     static_assert(OZ_S % OZ_ASTAGES == 0 && (OZ_S / OZ_ASTAGES) % 2 == 0,
                   "a K step must take an even number of turns of the A ring");
-    const uint32_t idesc = oz_idesc();
     const uint64_t dhi = sw128_desc(0);
     const uint32_t a_lo0 = (smem_u32(sA) & 0x3FFFF) >> 4, b_lo0 = (smem_u32(sB) & 0x3FFFF) >> 4;
     int c = 0;
@@ -250,18 +258,20 @@ k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a_lo = a_lo0 + (uint32_t)sa * (OZ_A_BYTES >> 4);
-        // per 16-deep k slab, the pairs (t, u) one after the other on the same A
-        // slab: it enters the collector buffer once instead of once per pair
 #pragma unroll
         for (int kk = 0; kk < OZ_BK / 16; ++kk) {
           const uint64_t ad = dhi | (uint64_t)(a_lo + kk * 2);
           const uint32_t acc = (cstart && t == 0 && kk == 0) ? 0u : 1u;
-          oz_sfor<OZ_S - t>([&](auto U) {
-            constexpr int u = decltype(U)::value, nu = OZ_S - t;
-            constexpr int coll = nu == 1 ? 0 : (u == 0 ? 1 : (u == nu - 1 ? 3 : 2));
-            const uint32_t dt = tmem + (uint32_t)((t + u) * OZ_BN);
-            const uint64_t bd = dhi | (uint64_t)(b_lo + u * (OZ_B_BYTES >> 4) + kk * 2);
-            mma_bf16_coll<coll>(dt, ad, bd, idesc, acc);
+          constexpr int npiece = (OZ_S - t + 3) / 4;
+          oz_sfor<npiece>([&](auto Pc) {
+            constexpr int pc = decltype(Pc)::value, u0 = 4 * pc;
+            constexpr int nu = (OZ_S - t - u0) < 4 ? (OZ_S - t - u0) : 4;
+            constexpr uint32_t idn = oz_idesc_n(nu * OZ_BN);
+            // two pieces on one A slab: it enters the collector buffer once
+            constexpr int coll = npiece == 1 ? 0 : (pc == 0 ? 1 : 3);
+            const uint32_t dt = tmem + (uint32_t)((t + u0) * OZ_BN);
+            const uint64_t bd = dhi | (uint64_t)(b_lo + u0 * (OZ_B_BYTES >> 4) + kk * 2);
+            mma_bf16_coll<coll>(dt, ad, bd, idn, acc);
           });
         }
         mma_commit(&aempty[sa]);
@@ -832,13 +842,13 @@ __device__ __forceinline__ void gen_atom(const GenProj& g, int I, int G, F&& f) 
   S = cmul2(S, tab[g.toff[1] + m1 + g.half[1]]);
   S = cmul2(S, tab[g.toff[2] + m2 + g.half[2]]);
   for (int n = 0; n < g.nrad; ++n) {
-    const double F = g.radial[(size_t)n * g.npw + G];
+    const double rad = g.radial[(size_t)n * g.npw + G];
     if (g.l[n] == 0) {
-      const double a = 0.28209479177387814347 * F;
+      const double a = 0.28209479177387814347 * rad;
       f(I * g.nper + g.off[n], make_double2(S.x * a, S.y * a));
     } else {
       for (int c = 0; c < 3; ++c) {
-        const double a = 0.48860251190291992159 * q[c] * F;
+        const double a = 0.48860251190291992159 * q[c] * rad;
         f(I * g.nper + g.off[n] + c, make_double2(S.y * a, -S.x * a));   // (-i) S a
       }
     }
