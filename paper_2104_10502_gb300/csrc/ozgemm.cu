@@ -663,6 +663,86 @@ __global__ void k_oz_slice_cols(const double2* __restrict__ src, int ld, int K, 
   }
 }
 
+// Both exponent sets of a complex [R][C] matrix in one read: row r's bound into
+// er[r], column c's into ec[c] (both hold 0x80808080 beforehand).  grid
+// (ceil(C / 256), ceil(R / 8)), 256 threads: each thread scans 8 rows of one
+// column; the row maxima meet through shared memory.
+__global__ void __launch_bounds__(256) k_oz_bothmax(const double2* __restrict__ src, int R, int C,
+                                                    int* __restrict__ er, int* __restrict__ ec) {
+  __shared__ unsigned long long rmax[8][8];   // [row][warp]
+  const int cidx = blockIdx.x * 256 + threadIdx.x, r0 = blockIdx.y * 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long cm = 0;
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = r0 + rr;
+    unsigned long long h = 0;
+    if (r < R && cidx < C) {
+      const double2 v = src[(size_t)r * C + cidx];
+      const unsigned long long a = mag_bits(v.x), b = mag_bits(v.y);
+      h = a > b ? a : b;
+    }
+    cm = h > cm ? h : cm;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, h, o);
+      h = w > h ? w : h;
+    }
+    if (lane == 0) rmax[rr][warp] = h;
+  }
+  if (cidx < C && cm != 0) atomicMax(&ec[cidx], exp_bound_bits(cm));
+  __syncthreads();
+  if (threadIdx.x < 8 && r0 + threadIdx.x < R) {
+    unsigned long long h = 0;
+    for (int w = 0; w < 8; ++w) h = rmax[threadIdx.x][w] > h ? rmax[threadIdx.x][w] : h;
+    if (h != 0) atomicMax(&er[r0 + threadIdx.x], exp_bound_bits(h));
+  }
+}
+
+// Both slicings of a complex [R][C] matrix in one read, through 32 x 32 tiles in
+// shared memory: Q1 (form 0 of oz_slice_rows: row r = (x, y) over c, exponent
+// er[r], [S][rows1][Kp1]) and Q2 (form 0 of oz_slice_cols: row c = (x, y) over
+// r, exponent ec[c], [S][rows2][Kp2]), padding zeroed.  grid (ceil(max(C,
+// rows2, Kp1/2) / 32), ceil(max(R, rows1, Kp2/2) / 32)), block (32, 8).
+__global__ void __launch_bounds__(256) k_oz_slice_both(const double2* __restrict__ src, int R, int C,
+                                                       const int* __restrict__ er,
+                                                       const int* __restrict__ ec, int rows1, int Kp1,
+                                                       unsigned* __restrict__ Q1, int rows2, int Kp2,
+                                                       unsigned* __restrict__ Q2) {
+  __shared__ double2 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    const int r = r0 + rr, c = c0 + threadIdx.x;
+    tile[rr][threadIdx.x] = (r < R && c < C) ? src[(size_t)r * C + c] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const size_t s1 = (size_t)rows1 * Kp1 / 2, s2 = (size_t)rows2 * Kp2 / 2;
+  unsigned short qx[OZ_S], qy[OZ_S];
+  // row form: thread (x = c, y) writes rows r0 + y + 8 i, consecutive c along a row
+  for (int rr = threadIdx.y; rr < 32; rr += blockDim.y) {
+    const int r = r0 + rr, c = c0 + threadIdx.x;
+    if (r >= rows1 || 2 * c >= Kp1) continue;
+    const double2 v = tile[rr][threadIdx.x];
+    const int ex = r < R ? oz_exp(er[r]) : 0;
+    slices_of(v.x, ex, qx);
+    slices_of(v.y, ex, qy);
+    unsigned* p = Q1 + (size_t)r * (Kp1 / 2) + c;
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) p[t * s1] = pack2(qx[t], qy[t]);
+  }
+  // column form: thread (x = r, y) writes rows c0 + y + 8 i, consecutive r along a row
+  for (int cc = threadIdx.y; cc < 32; cc += blockDim.y) {
+    const int c = c0 + cc, r = r0 + threadIdx.x;
+    if (c >= rows2 || 2 * r >= Kp2) continue;
+    const double2 v = tile[threadIdx.x][cc];
+    const int ex = c < C ? oz_exp(ec[c]) : 0;
+    slices_of(v.x, ex, qx);
+    slices_of(v.y, ex, qy);
+    unsigned* p = Q2 + (size_t)c * (Kp2 / 2) + r;
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) p[t * s2] = pack2(qx[t], qy[t]);
+  }
+}
+
 // P[m][n] = sum_z part[z][n][m] (fixed order), into C with leading dimension ldc.
 __global__ void k_oz_reduce(const double2* __restrict__ part, int nsplit, long long zstride,
                             int Mp, int M, int N, double2* __restrict__ C, int ldc) {
@@ -809,6 +889,34 @@ int oz_slice_cols(const double* src, int ld, int K, int cols, int form, void* me
   k_oz_slice_cols<<<g, dim3(32, 8), 0, st>>>(reinterpret_cast<const double2*>(src), ld, K, cols,
                                              form, out->e, out->rows_p, out->Kp, out->q);
   return oz_check("k_oz_slice_cols");
+}
+
+// Both slicings of a complex [R][C] matrix (ld = C) from one max pass and one
+// slicing pass: *rows = oz_slice_rows(form 0) into mem1, *cols =
+// oz_slice_cols(form 0) into mem2 -- the same operands, bit for bit.
+int oz_slice_both(const double* src, int R, int C, void* mem1, void* mem2, OzOperand* rows,
+                  OzOperand* cols, cudaStream_t st, Prof* pf) {
+  *rows = oz_carve(mem1, R, C);
+  *cols = oz_carve(mem2, C, R);
+  {
+    ProfScope ps(pf, "k_oz_bothmax", st);
+    if (cudaMemsetAsync(rows->e, 0x80, (size_t)rows->rows_p * sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(cols->e, 0x80, (size_t)cols->rows_p * sizeof(int), st) != cudaSuccess) {
+      set_error("oz_slice_both: memset failed");
+      return QE_ECUDA;
+    }
+    k_oz_bothmax<<<dim3((C + 255) / 256, (R + 7) / 8), 256, 0, st>>>(
+        reinterpret_cast<const double2*>(src), R, C, rows->e, cols->e);
+    int rc = oz_check("k_oz_bothmax");
+    if (rc) return rc;
+  }
+  ProfScope ps(pf, "k_oz_slice_both", st);
+  const int cx = std::max(C, std::max(cols->rows_p, rows->Kp / 2));
+  const int ry = std::max(R, std::max(rows->rows_p, cols->Kp / 2));
+  k_oz_slice_both<<<dim3((cx + 31) / 32, (ry + 31) / 32), dim3(32, 8), 0, st>>>(
+      reinterpret_cast<const double2*>(src), R, C, rows->e, cols->e, rows->rows_p, rows->Kp,
+      reinterpret_cast<unsigned*>(rows->q), cols->rows_p, cols->Kp, reinterpret_cast<unsigned*>(cols->q));
+  return oz_check("k_oz_slice_both");
 }
 
 // ---- projectors generated on the fly, straight into the slices -------------------
@@ -1311,7 +1419,11 @@ int nonlocal_oz(const double* beta, const double* dmat, const double* psi, doubl
   // real_p: Q = D Re P is real, so the outer product takes beta's columns as
   // separate real and imaginary rows over a real K axis (half the work)
   const bool r4 = nonlocal_oz_real_outer(real_p, np);
-  if (slice_beta) {
+  if (slice_beta && !r4) {
+    // both forms from one max pass and one slicing pass over beta
+    if ((rc = oz_slice_both(beta, np, npw, bs, bs + oz_operand_bytes(np, npw), &A1, &A2, st, pf)))
+      return rc;
+  } else if (slice_beta) {
     if ((rc = oz_slice_rows(beta, npw, np, npw, 0, bs, &A1, st, pf))) return rc;
     if ((rc = oz_slice_cols(beta, npw, np, npw, r4 ? 4 : 0, bs + oz_operand_bytes(np, npw), &A2, st,
                             pf)))
