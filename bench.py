@@ -123,7 +123,7 @@ def plane_bytes(c, nst, nb, nchunks, s):
 
 
 def fft_path_bytes(c, npw, nst, nb, nchunks, s):
-    """Algorithmic bytes of the whole FFT path a2-a7 over nb bands (SURVEY 8(d)):
+    """Algorithmic bytes of the whole FFT path a2-a7 over nb bands:
     read c and write Hc (2 npw s), the sticks written and read on the way in
     and on the way out (4 nst N3 s), V once per band chunk (N s / 2)."""
     n1, n2, n3 = c["grid"]
@@ -488,7 +488,7 @@ def run_gpu(args, rank, world, local_rank):
              "mixed": world * nb * args.steps / (ms_gmx / 1e3), "unit": "bands/s",
              "bands": "the C1 bands projected on their real-in-r parts (k = 0), two per FFT (QE_GAMMA)"}
 
-    # dominant kernel of the FP64 step and its roofline.  SURVEY 8(d): the FFT
+    # dominant kernel of the FP64 step and its roofline.  The FFT
     # kernels are counted in the method's own work (5 N log2 N flops of the
     # pruned transforms, the sticks and V as bytes), against the pipe they run
     # on (FP32: the float-float FFT executes on the FP32 pipes; peak = an SGEMM
@@ -955,7 +955,7 @@ SERVE_NREF = 16         # served requests re-solved to residual 1e-9 for the acc
 
 
 def serve_requests(q, ctx, n, seed, dev):
-    """The serving workload: cubic a ~ U[10,24] bohr, ecut ~
+    """The serving workload (C4): cubic a ~ U[10,24] bohr, ecut ~
     U[20,50] Ry, nb ~ U{8..256} (at most npw / 2), atoms ~ U{2..96} placed at
     random (at most a^3/24, so that rejection sampling at 2.5 bohr stays quick
     in the small cells), the C0 potentials (Gaussian V_loc, 4 projectors per
