@@ -685,7 +685,7 @@ static int rayleigh_ritz_f32(DvState& S, int n, cudaStream_t st, Prof* pf) {
 // into S.e, S.X (ld nb), in FP32 or FP64.
 static int rr_standard_eig(DvState& S, int n, bool fp32, cudaStream_t st, Prof* pf) {
   const int nb = S.nb;
-  if (!fp32) return heev_lowest(S.Lw, n, n, nb, S.e, S.X, nb, S.dw, st, pf);
+  if (!fp32) return heev_lowest(S.Lw, n, n, nb, S.e, S.X, nb, S.dw, st, pf, S.gamma);
   using zf = cx<float>;
   zf* A32 = reinterpret_cast<zf*>(S.Zw);
   zf* X32 = reinterpret_cast<zf*>(S.C);
@@ -723,7 +723,7 @@ static int rayleigh_ritz(DvState& S, int n, bool generalised, cudaStream_t st, P
   if (!generalised) {
     DV_CU(cudaMemcpy2DAsync(S.Aw, n * zb, S.Hr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
     DV_TRY(hermitize(S.Aw, n, n, st));
-    return heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf);
+    return heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf, S.gamma);
   }
   if (rr_small_fits(n)) {
     // one CTA in shared memory: Cholesky, reduction, tridiagonalisation
@@ -747,7 +747,7 @@ static int rayleigh_ritz(DvState& S, int n, bool generalised, cudaStream_t st, P
     DV_TRY(hermitize(S.Aw, n, n, st));
     pf->launches += 4;
   }
-  DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf));
+  DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf, S.gamma));
   {
     ProfScope ps(pf, "rr_backsub", st);
     DV_TRY(trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st));            // X = L^-+ Y

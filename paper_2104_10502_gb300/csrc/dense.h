@@ -74,9 +74,10 @@ int conj_transpose(const cx<double>* src, int lds, cx<double>* dst, int ldd, int
                    cudaStream_t st);
 int hermitize(cx<double>* A, int n, int lda, cudaStream_t st);
 // Lowest nev eigenpairs of Hermitian A (destroyed): w[nev] ascending, X [n][ldx]
-// with eigenvector k in column k.
+// with eigenvector k in column k.  real_sym: A is real (zero imaginary parts;
+// the k = 0 reduced problems), reduced by the real form of the kernel.
 int heev_lowest(cx<double>* A, int n, int lda, int nev, double* w, cx<double>* X, int ldx,
-                DenseWork& wk, cudaStream_t st, Prof* pf);
+                DenseWork& wk, cudaStream_t st, Prof* pf, bool real_sym = false);
 // Generalised lowest eigenpairs for n <= kSmallDense in one CTA: S = L L^+
 // (L -> L, n x n; a non-positive pivot sets wk.status[0] = 1 + column), then
 // the standard problem of L^-1 H L^-+ -> w[nev], Y in X (ld ldx); the caller
@@ -109,7 +110,7 @@ int hermitize(cx<float>* A, int n, int lda, cudaStream_t st);
 // Lowest nev eigenpairs of Hermitian A (destroyed): w[nev] ascending, X [n][ldx]
 // with eigenvector k in column k.
 int heev_lowest(cx<float>* A, int n, int lda, int nev, float* w, cx<float>* X, int ldx,
-                DenseWorkT<float>& wk, cudaStream_t st, Prof* pf);
+                DenseWorkT<float>& wk, cudaStream_t st, Prof* pf, bool real_sym = false);
 // Generalised lowest eigenpairs for n <= kSmallDense in one CTA: S = L L^+
 // (L -> L, n x n; a non-positive pivot sets wk.status[0] = 1 + column), then
 // the standard problem of L^-1 H L^-+ -> w[nev], Y in X (ld ldx); the caller

@@ -1278,6 +1278,252 @@ __global__ void __launch_bounds__(kTridFusedThreads) k_tridiag_fused_ff(z* A, in
     dg[n - 1] = ffs_to_d(pk_get_re(a));
   }
 }
+
+// ---- the real symmetric form (k = 0 reduced problems) ------------------------------
+// The reduced matrices of the k = 0 (real-in-r) Davidson are real symmetric;
+// this is k_tridiag_fused_ff on real values: the f32x2 lanes carry two adjacent
+// columns instead of (re, im), so a row pair costs three float-float FMAs where
+// a complex element costs six, and the rows take half the shared memory.  Rows
+// and vectors are pair-packed by absolute index (pair P = columns 2P and 2P+1,
+// as one cx<ff>: hi parts, then lo parts); vectors are zero outside their range
+// (v_j and w_j below index j+1, the column below j+2), so the pass and the
+// updates run over whole pairs and the lanes outside the trailing block add
+// exact zeros.  The exchange vectors hold p and the next column pair-packed as
+// floats.  tau and the reflector rows leave in the complex formats (zero
+// imaginary parts) that heev_finish reads.  256 threads; n <= 2 * 2 * 256.
+constexpr int kTridRealThreads = 256;
+constexpr int kTridRealU = 2;
+
+// keep lane 0 and/or lane 1 of a packed pair (the other becomes +0)
+__device__ __forceinline__ ff2 pk_lanes(ff2 a, bool keep0, bool keep1) {
+  const unsigned long long m = (keep0 ? 0xffffffffull : 0ull) | (keep1 ? 0xffffffff00000000ull : 0ull);
+  return {{a.hi.v & m}, {a.lo.v & m}};
+}
+__device__ __forceinline__ ff pk_lane(ff2 a, int l) { return l ? pk_get_im(a) : pk_get_re(a); }
+// element i of a pair-packed vector
+__device__ __forceinline__ ff pk_elem(const cx<ff>* v, int i) { return pk_lane(as2(v[i >> 1]), i & 1); }
+__device__ __forceinline__ void pk_put_elem(float* base, int i, ff x) {
+  base[4 * (i >> 1) + (i & 1)] = x.hi;
+  base[4 * (i >> 1) + 2 + (i & 1)] = x.lo;
+}
+
+__global__ void __launch_bounds__(kTridRealThreads) k_tridiag_real_ff(z* A, int n, int lda,
+                                                                    z* tau, R* e, R* dg,
+                                                                    z* refl, GridBar bar) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int U = kTridRealU;
+  const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  const int NP = (n + 1) >> 1;                     // pairs per row
+  const int nrmax = (n + G - 1) / G;
+  const int nr = c < n ? (n - 1 - c) / G + 1 : 0;   // rows owned: c + q G, q < nr
+  cx<ff>* rows = reinterpret_cast<cx<ff>*>(smem_raw);   // nrmax x NP
+  // rows + (nrmax + (j & 1)) NP: v_j; the other one v_{j-1}
+  cx<ff>* sw = rows + (size_t)(nrmax + 2) * NP;   // w_{j-1} (pending), then w_j
+  cx<ff>* sx = rows + (size_t)(nrmax + 3) * NP;   // column to reduce (absolute index)
+  __shared__ cx<ff> rb[2][32];
+  __shared__ ff scal[2];   // the scale of v (x_i -> v_i) and tau
+  __shared__ cx<ff> spart[kTridRealThreads / 32][kTridRows];
+  for (int q = 0; q < nr; ++q) {
+    const z* src = A + (size_t)(c + q * G) * lda;
+    for (int P = tid; P < NP; P += nt) {
+      const ff a0 = ff(ldz(src + 2 * P).x);
+      const ff a1 = 2 * P + 1 < n ? ff(ldz(src + 2 * P + 1).x) : ff(0.f, 0.f);
+      rows[(size_t)q * NP + P] = of2(pk_make(a0, a1));
+    }
+  }
+  ff2 ss = pk_zero();   // squared norm of the column below its first entry
+  for (int P = tid; P < NP; P += nt) {
+    const int i0 = 2 * P, i1 = 2 * P + 1;
+    const ff a0 = i0 >= 1 ? ff(ldz(&A[(size_t)i0 * lda]).x) : ff(0.f, 0.f);
+    const ff a1 = i1 < n ? ff(ldz(&A[(size_t)i1 * lda]).x) : ff(0.f, 0.f);
+    const ff2 x = pk_make(a0, a1);
+    sx[P] = of2(x);
+    const ff2 xm = pk_lanes(x, i0 >= 2, i1 >= 2);
+    ss = xm * xm + ss;
+  }
+  if (c == 0 && tid == 0) dg[0] = ldz(&A[0]).x;
+  // every CTA has read A: its rows 0..3 become the exchange vectors
+  if (!grid_sync_mono(bar, 1)) return;
+  const ff one = ff(1.f, 0.f);
+  for (int j = 0; j < n - 1; ++j) {
+    const int par = j & 1;
+    const bool pend = j >= 1;
+    float* xpf = reinterpret_cast<float*>(A + (size_t)(2 * par) * lda);       // p, pair-packed
+    float* xcf = reinterpret_cast<float*>(A + (size_t)(2 * par + 1) * lda);   // next column
+    cx<ff>* sv = rows + (size_t)(nrmax + par) * NP;
+    const cx<ff>* svp = rows + (size_t)(nrmax + (par ^ 1)) * NP;
+    // reflector of step j from x (indices j+1 ..): one warp forms its scalars
+    for (int o = 16; o > 0; o >>= 1) ss = ss + pk_shfl_xor(ss, o);
+    if (lane == 0) rb[0][warp] = of2(ff2_settle(ss));
+    __syncthreads();
+    if (warp == 0) {
+      const ff2 s2 = pk_fold_partials(rb[0], nwarp);
+      if (lane == 0) {
+        const ff sigma = ffs_add(pk_get_re(s2), pk_get_im(s2));
+        const ff alpha = pk_elem(sx, j + 1);
+        ff t, sc, beta;
+        if (sigma.hi == 0.f) {   // v = e_{j+1}, tau = 0
+          t = ff(0.f, 0.f);
+          sc = ff(0.f, 0.f);
+          beta = alpha;
+        } else {
+          const ff nu = ffs_sqrt(ffs_add(ffs_mul(alpha, alpha), sigma));
+          beta = alpha.hi >= 0.f ? ffs_neg(nu) : nu;
+          sc = ffs_div(one, ffs_sub(alpha, beta));
+          t = ffs_div(ffs_sub(beta, alpha), beta);
+        }
+        scal[0] = sc;
+        scal[1] = t;
+        if (c == 0) { tau[j] = {ffs_to_d(t), R(0)}; e[j] = ffs_to_d(beta); }
+      }
+    } else if (pend && tid == 32 && c == j % G) {
+      // row j: the diagonal share of the pending update of step j - 1 (v_j = 1 there)
+      const int P = j >> 1;
+      const ff2 nv = ff2_bcast(ffs_neg(pk_elem(svp, j))), nw = ff2_bcast(ffs_neg(pk_elem(sw, j)));
+      ff2 a = as2(rows[(size_t)(j / G) * NP + P]);
+      a = fma(nv, as2(sw[P]), a);
+      a = fma(nw, as2(svp[P]), a);
+      dg[j] = ffs_to_d(pk_lane(ff2_settle(a), j & 1));
+    }
+    __syncthreads();
+    const ff2 sc = ff2_bcast(scal[0]), t2 = ff2_bcast(scal[1]);
+    // v_j on the owned pairs P = tid + u nt: 0 below index j+1, 1 at j+1
+    ff2 vk[U], cwk[U], cvk[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int P = tid + u * nt;
+      vk[u] = cwk[u] = cvk[u] = pk_zero();
+      if (P < NP) {
+        const int i0 = 2 * P;
+        ff2 v = pk_lanes(ff2_settle(as2(sx[P]) * sc), i0 >= j + 2, i0 + 1 >= j + 2);
+        if (i0 == j + 1) v = pk_make(one, pk_get_im(v));
+        if (i0 + 1 == j + 1) v = pk_make(pk_get_re(v), one);
+        vk[u] = v;
+        sv[P] = of2(v);
+        if (c == 0) {
+          // reflector row j, indices j+1 .. n-1, as complex float-float (zero imaginary)
+          for (int l = 0; l < 2; ++l) {
+            const int i = i0 + l;
+            if (i >= j + 1 && i < n) {
+              const ff x = pk_lane(v, l);
+              cx<ff> o;
+              o.hi = f2_of(x.hi, 0.f);
+              o.lo = f2_of(x.lo, 0.f);
+              *reinterpret_cast<cx<ff>*>(&refl[(size_t)j * n + i]) = o;
+            }
+          }
+        }
+        if (pend) {
+          cwk[u] = as2(sw[P]);
+          cvk[u] = as2(svp[P]);
+        }
+      }
+    }
+    // owned rows of the trailing block (r >= j+1): the pending update of step
+    // j - 1, and (A v)_r, over the pairs that hold columns j+1 ..
+    const int P0 = (j + 1) >> 1;
+    const int q0 = c >= j + 1 ? 0 : (j + 1 - c + G - 1) / G;
+    const int nq = nr - q0;
+    if (nq > 0) {
+      ff2 acc[kTridRows];
+#pragma unroll
+      for (int q = 0; q < kTridRows; ++q) {
+        acc[q] = pk_zero();
+        if (q < nq) {
+          const int r = c + (q0 + q) * G;
+          cx<ff>* base = rows + (size_t)(q0 + q) * NP;
+          ff2 nv = pk_zero(), nw = pk_zero();
+          if (pend) {
+            nv = ff2_bcast(ffs_neg(pk_elem(svp, r)));
+            nw = ff2_bcast(ffs_neg(pk_elem(sw, r)));
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int P = tid + u * nt;
+            if (P >= P0 && P < NP) {
+              ff2 a = as2(base[P]);
+              if (pend) {
+                a = ff2_settle(fma(nw, cvk[u], fma(nv, cwk[u], a)));
+                base[P] = of2(a);
+              }
+              acc[q] = fma(a, vk[u], acc[q]);
+            }
+          }
+          acc[q] = ff2_settle(acc[q]);
+        }
+      }
+      const ff2 s8 = pk_warp_rows8(acc);
+      if ((lane & 3) == 0) spart[warp][lane >> 2] = of2(ff2_settle(s8));
+    }
+    __syncthreads();
+    if (warp < nq) {
+      ff2 a = lane < nwarp ? as2(spart[lane][warp]) : pk_zero();
+      for (int o = nwarp >> 1; o > 0; o >>= 1) a = a + pk_shfl_xor(a, o);
+      if (lane == 0) {
+        const int q = q0 + warp, r = c + q * G;
+        a = ff2_settle(a);
+        pk_put_elem(xpf, r, ffs_mul(scal[1], ffs_add(pk_get_re(a), pk_get_im(a))));
+        if (r >= j + 2) pk_put_elem(xcf, r, pk_elem(rows + (size_t)q * NP, j + 1));
+      }
+    }
+    if (!grid_sync_mono(bar, (unsigned)j + 2)) return;
+    // loads of the published vectors: p (indices j+1 ..), the column (j+2 ..), p_{j+1}
+    ff2 pi[U], xi[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int P = tid + u * nt, i0 = 2 * P;
+      pi[u] = xi[u] = pk_zero();
+      // (the padding lane of an odd n is never written: masked like the stale entries)
+      if (P < NP && i0 + 1 >= j + 1) {
+        pi[u] = pk_lanes(pk_load(reinterpret_cast<const z*>(xpf + 4 * P)), i0 >= j + 1, i0 + 1 < n);
+        if (i0 + 1 >= j + 2)
+          xi[u] = pk_lanes(pk_load(reinterpret_cast<const z*>(xcf + 4 * P)), i0 >= j + 2,
+                           i0 + 1 < n);
+      }
+    }
+    const int Pj = (j + 1) >> 1;
+    const ff2 pjp = pk_load(reinterpret_cast<const z*>(xpf + 4 * Pj));
+    const ff pj1 = pk_lane(pjp, (j + 1) & 1);
+    ff2 sp = pk_zero();
+#pragma unroll
+    for (int u = 0; u < U; ++u) sp = fma(vk[u], pi[u], sp);
+    for (int o = 16; o > 0; o >>= 1) sp = sp + pk_shfl_xor(sp, o);
+    if (lane == 0) rb[1][warp] = of2(ff2_settle(sp));
+    __syncthreads();
+    // w = p - (1/2) tau (v . p) v; the next column: x_i - w_i - v_i w_{j+1}
+    // (indices j+2 ..), and its squared norm below its first entry
+    const ff2 vpp = pk_fold_partials(rb[1], nwarp);
+    const ff vp = ffs_add(pk_get_re(vpp), pk_get_im(vpp));
+    const ff2 ncoef = ff2_bcast(ffs_neg(ffs_mul(ff(0.5f, 0.f), ffs_mul(scal[1], vp))));
+    const ff2 wj1 = ff2_settle(fma(ncoef, ff2_bcast(one), ff2_bcast(pj1)));
+    ss = pk_zero();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int P = tid + u * nt, i0 = 2 * P;
+      if (P < NP) {
+        const ff2 w = ff2_settle(fma(ncoef, vk[u], pi[u]));
+        sw[P] = of2(w);
+        const ff2 x = pk_lanes(ff2_settle(fma(pk_neg(vk[u]), wj1, xi[u] - w)), i0 >= j + 2,
+                               i0 + 1 >= j + 2);
+        sx[P] = of2(x);
+        const ff2 xm = pk_lanes(x, i0 >= j + 3, i0 + 1 >= j + 3);
+        ss = xm * xm + ss;
+      }
+    }
+  }
+  // row n - 1: the diagonal share of the last step's update
+  __syncthreads();
+  if (n >= 2 && tid == 0 && c == (n - 1) % G) {
+    const cx<ff>* vl = rows + (size_t)(nrmax + ((n - 2) & 1)) * NP;
+    const int P = (n - 1) >> 1;
+    const ff2 nv = ff2_bcast(ffs_neg(pk_elem(vl, n - 1))), nw = ff2_bcast(ffs_neg(pk_elem(sw, n - 1)));
+    ff2 a = as2(rows[(size_t)((n - 1) / G) * NP + P]);
+    a = fma(nv, as2(sw[P]), a);
+    a = fma(nw, as2(vl[P]), a);
+    dg[n - 1] = ffs_to_d(pk_lane(ff2_settle(a), (n - 1) & 1));
+  }
+}
 #endif
 
 // One warp per eigenvalue, two per CTA; d and e^2 staged in shared memory.
@@ -1953,6 +2199,32 @@ static int tridiag_rows_grid(int n, size_t* smem) {
 }
 
 #if defined(QE_DENSE_FP64)
+// Grid of k_tridiag_real_ff (0: it does not fit): as k_tridiag_fused_ff, with
+// (ceil(n / G) + 4) ceil(n / 2) pairs of shared memory.
+static int tridiag_real_grid(int n, size_t* smem) {
+  if (n < 16 || n > 2 * kTridRealU * kTridRealThreads) return 0;
+  int dev = 0, nsm = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, (const void*)k_tridiag_real_ff) != cudaSuccess) return 0;
+  const int g = std::min(nsm, (n + 3) / 4);
+  const int nrmax = (n + g - 1) / g;
+  if (nrmax > kTridRows) return 0;
+  const size_t sm = (size_t)(nrmax + 4) * ((n + 1) / 2) * sizeof(cx<ff>);
+  if (sm + fa.sharedSizeBytes > (size_t)optin) return 0;
+  set_max_dynamic_smem(k_tridiag_real_ff);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_real_ff, kTridRealThreads,
+                                                    sm) != cudaSuccess ||
+      occ < 1)
+    return 0;
+  *smem = sm;
+  return g;
+}
+
 // Grid of k_tridiag_fused_ff (0: it does not fit, use tridiag_rows_grid): the
 // CTA count of k_tridiag_rows_ff, (ceil(n / G) + 4) n complex of shared memory.
 static int tridiag_fused_grid(int n, size_t* smem) {
@@ -1981,7 +2253,8 @@ static int tridiag_fused_grid(int n, size_t* smem) {
 #endif
 
 int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk,
-                cudaStream_t st, Prof* pf) {
+                cudaStream_t st, Prof* pf, bool real_sym) {
+  (void)real_sym;   // the FP32 instantiation reduces every matrix in complex form
   if (n <= 0 || nev <= 0) return QE_OK;
   if (nev > n || n > kMaxDense) {
     set_error("heev_lowest: n = %d, nev = %d (max n %d)", n, nev, kMaxDense);
@@ -1994,6 +2267,19 @@ int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R
   GridBar bar = wk.bar;
   size_t rsm = 0;
 #if defined(QE_DENSE_FP64)
+  if (real_sym) {
+    const int gr = tridiag_real_grid(n, &rsm);
+    if (gr > 0) {
+      void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.d, &wk.refl, &bar};
+      {
+        ProfScope ps(pf, "heev_tridiag", st);
+        int rc0 = launch_coop((const void*)k_tridiag_real_ff, gr, args, st, "k_tridiag_real_ff",
+                              rsm, kTridRealThreads);
+        if (rc0) return rc0;
+      }
+      return heev_finish(n, nev, w, X, ldx, wk, st, pf, true);   // packed reflectors
+    }
+  }
   const int gf = tridiag_fused_grid(n, &rsm);
   if (gf > 0) {
     void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.d, &wk.refl, &bar};
