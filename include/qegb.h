@@ -60,10 +60,10 @@ enum { QE_FP64 = 0, QE_MIXED = 1 };   /* arithmetic of the GPU path */
  *    every basis vector real in r: the start bands are replaced by their
  *    larger real-in-r part, H runs as with QE_GAMMA, and the returned
  *    eigenvectors are real in r (same eigenvalues).  QE_GAMMA asks for it;
- *    by default QE_FP64 solves on grids of at least 48^3 points use it
- *    (smaller FFTs gain less than the mode's extra launches cost), QE_MIXED
- *    solves do not (their FP32 phase converges in fewer iterations on complex
- *    bands).
+ *    by default solves on grids of at least 48^3 points use it (smaller FFTs
+ *    gain less than the mode's extra launches cost), except QE_MIXED solves
+ *    with QE_RR_FP32 (whose FP32 phase converges in fewer iterations on
+ *    complex bands).
  *  QE_NO_GAMMA (qe_davidson, qe_davidson_batch): never. */
 enum { QE_GAMMA = 0x100, QE_NO_GAMMA = 0x200 };
 /* QE_FFT_FP64PIPE (qe_hpsi, with QE_FP64): run the FFT in float64 on the FP64

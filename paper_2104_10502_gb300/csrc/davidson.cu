@@ -222,14 +222,6 @@ __global__ void k_gamma_sym(z* X, int rows, int npw, const int* __restrict__ mg)
   }
 }
 
-// Im C = 0 on a rows x cols block (inner products of vectors real in r are real).
-__global__ void k_real_part(z* C, int rows, int cols, int ldc) {
-  const size_t total = (size_t)rows * cols;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x)
-    C[(t / cols) * ldc + t % cols].y = 0.0;
-}
-
 // Largest |beta_i(-G) - conj beta_i(G)| and largest |beta_i(G)|, as the bit
 // patterns of non-negative doubles (ordered like the values) in out[0], out[1].
 __global__ void k_beta_mirror(const z* __restrict__ beta, int np, int npw, const int* __restrict__ mg,
@@ -433,8 +425,8 @@ static int* dv_tc_status(const DvState& S) { return S.dw.status + 12; }
 
 // C = A^+ B over the plane waves; real for vectors real in r (k = 0 mode), so
 // that the combinations built from C keep them real in r exactly (the SIMT
-// path drops Im C in its split reduction, the FP64 tensor-core path computes
-// only Re C, the FP32 one drops Im C after).
+// path drops Im C in its split reduction, the tensor-core paths compute only
+// Re C).
 template <typename T>
 static int gram(DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
                 cudaStream_t st, Prof* pf) {
@@ -448,28 +440,28 @@ static int gram(DvState& S, const z* A, int m, const z* B, int n, z* C, int ldc,
     return oz_inner_cached(S.vcache, S.max_dim, m, (const double*)B, S.npw, n, S.npw, (double*)C, ldc,
                            S.oz, S.oz_bytes, dv_tc_status(S), st, pf, S.gamma);
   }
-  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(m, n, S.npw)) {
-    DV_TRY(tc_inner((const double*)A, (const double*)B, m, n, S.npw, (double*)C, ldc, S.tc,
-                    S.tc_bytes, dv_tc_status(S), st, pf));
-  } else if (sizeof(T) == sizeof(double) && S.oz && oz_worth(m, n, S.npw)) {
+  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(m, n, S.npw))
+    return tc_inner((const double*)A, (const double*)B, m, n, S.npw, (double*)C, ldc, S.tc,
+                    S.tc_bytes, dv_tc_status(S), st, pf, S.gamma);
+  if (sizeof(T) == sizeof(double) && S.oz && oz_worth(m, n, S.npw))
     return oz_inner((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C, ldc,
                     S.oz, S.oz_bytes, dv_tc_status(S), st, pf, S.gamma);
-  } else {
-    return gemm_inner<T>((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C,
-                         ldc, S.part, S.part_bytes, st, pf, S.gamma);
-  }
-  if (!S.gamma || m <= 0 || n <= 0) return QE_OK;
-  k_real_part<<<grid_for((size_t)m * n), 256, 0, st>>>(C, m, n, ldc);
-  return check_launch("k_real_part");
+  return gemm_inner<T>((const double*)A, S.npw, (const double*)B, S.npw, m, n, S.npw, (double*)C,
+                       ldc, S.part, S.part_bytes, st, pf, S.gamma);
 }
 
 // C[n][m] (+)= (-) sum_k A[k][m] B[k][n]: rotations and projections out of the basis
 template <typename T>
 static int outer_any(const DvState& S, const z* A, int lda, const z* B, int ldb, int M, int N,
                      int K, z* C, int ldc, int alpha_neg, int beta, cudaStream_t st, Prof* pf) {
-  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(M, N, K) && lda == M && ldb == N)
+  if (sizeof(T) == sizeof(float) && S.tc && tc_worth(M, N, K) && lda == M && ldb == N) {
+    // k = 0 mode: the right-hand matrices (Ritz vectors, Gram blocks) are real
+    if (S.gamma && tc_outer_real_bytes(M, N, K) <= S.tc_bytes)
+      return tc_outer_real((const double*)A, (const double*)B, M, N, K, (double*)C, ldc, alpha_neg,
+                           beta, S.tc, S.tc_bytes, dv_tc_status(S), st, pf);
     return tc_outer((const double*)A, (const double*)B, M, N, K, (double*)C, ldc, alpha_neg, beta,
                     S.tc, S.tc_bytes, dv_tc_status(S), st, pf);
+  }
   if (sizeof(T) == sizeof(double) && S.oz && oz_worth(M, N, K)) {
     // k = 0 mode: the right-hand matrices (Ritz vectors, Gram blocks) are real
     if (S.gamma && oz_outer_real_scratch(M, N, K) <= S.oz_bytes)
@@ -563,7 +555,7 @@ static int dense_inner(const DvState& S, const z* A, int M, const z* B, int N, i
                        cudaStream_t st, Prof* pf) {
   if (sizeof(T) == sizeof(float) && S.tc && tc_worth(M, N, K) && tc_inner_bytes(M, N, K) <= S.tc_bytes)
     return tc_inner((const double*)A, (const double*)B, M, N, K, (double*)C, ldc, S.tc, S.tc_bytes,
-                    dv_tc_status(S), st, pf);
+                    dv_tc_status(S), st, pf, S.gamma);
   if (sizeof(T) == sizeof(double) && S.oz && oz_worth(M, N, K) && oz_inner_scratch(M, N, K) <= S.oz_bytes)
     return oz_inner((const double*)A, K, (const double*)B, K, M, N, K, (double*)C, ldc, S.oz,
                     S.oz_bytes, dv_tc_status(S), st, pf);
@@ -1184,17 +1176,20 @@ using namespace qe;
 namespace {
 
 // Whether a k = 0 solve keeps its bands real in r (QE_GAMMA / QE_NO_GAMMA
-// decide when given).  By default in FP64 on grids of at least 48^3 points (C2,
-// 96^3: 19 iterations either way, the FFTs halved: 1.41 -> 1.21 s); on smaller
-// grids the FFTs are a small share and the mode's extra launches cost as much
-// as it saves (C0, 32^3: 17 -> 18 ms).  The mixed path keeps complex bands
-// unless asked, because with real bands its FP32 phase needed 23 instead of 16
-// iterations on C2 (a complex basis spans the real and imaginary parts of its
-// vectors, twice the real dimension).
+// decide when given).  By default on grids of at least 48^3 points: C2 (96^3)
+// at the matched tolerance takes 12 iterations either way, FP64 0.31 -> 0.23 s
+// and mixed 0.21 -> 0.17 s (FFTs halved, real products and real reduced
+// problems); on smaller grids the FFTs are a small share and the mode's extra
+// launches cost as much as it saves (C0, 32^3: 17 -> 18 ms).  A mixed solve
+// with FP32 reduced problems (QE_RR_FP32) keeps complex bands unless asked:
+// with real bands its FP32 phase needed 23 instead of 16 iterations on C2 (a
+// complex basis spans the real and imaginary parts of its vectors, twice the
+// real dimension).
 static bool gamma_mode(int precision, int flags, const int grid[3]) {
   if (flags & QE_NO_GAMMA) return false;
   if (flags & QE_GAMMA) return true;
-  return precision == QE_FP64 && (long long)grid[0] * grid[1] * grid[2] >= 48ll * 48 * 48;
+  if (precision == QE_MIXED && (flags & QE_RR_FP32)) return false;
+  return (long long)grid[0] * grid[1] * grid[2] >= 48ll * 48 * 48;
 }
 
 // Checks of one problem's arguments, its plan and operator, and the layout of

@@ -1289,8 +1289,9 @@ __global__ void __launch_bounds__(kTridFusedThreads) k_tridiag_fused_ff(z* A, in
 // (v_j and w_j below index j+1, the column below j+2), so the pass and the
 // updates run over whole pairs and the lanes outside the trailing block add
 // exact zeros.  The exchange vectors hold p and the next column pair-packed as
-// floats.  tau and the reflector rows leave in the complex formats (zero
-// imaginary parts) that heev_finish reads.  256 threads; n <= 2 * 2 * 256.
+// floats.  tau leaves in the complex format (zero imaginary parts), the
+// reflector rows pair-packed; heev_finish reads both with its real kernels.
+// 256 threads; n <= 2 * 2 * 256.
 constexpr int kTridRealThreads = 256;
 constexpr int kTridRealU = 2;
 
@@ -1401,19 +1402,8 @@ __global__ void __launch_bounds__(kTridRealThreads) k_tridiag_real_ff(z* A, int 
         if (i0 + 1 == j + 1) v = pk_make(pk_get_re(v), one);
         vk[u] = v;
         sv[P] = of2(v);
-        if (c == 0) {
-          // reflector row j, indices j+1 .. n-1, as complex float-float (zero imaginary)
-          for (int l = 0; l < 2; ++l) {
-            const int i = i0 + l;
-            if (i >= j + 1 && i < n) {
-              const ff x = pk_lane(v, l);
-              cx<ff> o;
-              o.hi = f2_of(x.hi, 0.f);
-              o.lo = f2_of(x.lo, 0.f);
-              *reinterpret_cast<cx<ff>*>(&refl[(size_t)j * n + i]) = o;
-            }
-          }
-        }
+        // reflector row j pair-packed, every pair (k_wy_t_real_ff, k_backtransform_real_ff)
+        if (c == 0) reinterpret_cast<cx<ff>*>(refl + (size_t)j * n)[P] = of2(v);
         if (pend) {
           cwk[u] = as2(sw[P]);
           cvk[u] = as2(svp[P]);
@@ -2107,12 +2097,145 @@ __global__ void __launch_bounds__(256) k_backtransform_ff(const z* __restrict__ 
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) X[(size_t)i * ldx + k] = pk_to_z(as2(x[i]));
 }
+
+// ---- the back-transformation of the real symmetric form ----------------------------
+// k_tridiag_real_ff leaves reflector row j pair-packed (pair P = entries 2P and
+// 2P+1, zero below j+1, every pair of the row written); these are k_wy_t_ff and
+// k_backtransform_ff on real pairs: each f32x2 lane pair carries two entries of
+// a real vector, the dot products of a group leave the warp in the transposing
+// butterfly, and T (real) is kept in the complex format with zero imaginary parts.
+// n <= 2 * 2 * 256.
+__device__ __forceinline__ const cx<ff>* refl_pairs(const z* refl, int n, int j) {
+  return reinterpret_cast<const cx<ff>*>(refl + (size_t)j * n);
+}
+
+__global__ void __launch_bounds__(256) k_wy_t_real_ff(const z* __restrict__ refl, int n,
+                                                      const z* __restrict__ tau, z* __restrict__ T) {
+  __shared__ z P[kWY][kWY];
+  const int g = blockIdx.x, j0 = g * kWY, nr = min(kWY, n - 1 - j0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int NP = (n + 1) >> 1;
+  for (int pq = warp; pq < kWY * kWY; pq += nw) {
+    const int a = pq / kWY, bb = pq % kWY;
+    if (!(a < bb && bb < nr)) continue;
+    const z ta = tau[j0 + a], tb = tau[j0 + bb];
+    if (ta.x == R(0) || tb.x == R(0)) {
+      if (lane == 0) P[a][bb] = {R(0), R(0)};
+      continue;
+    }
+    const cx<ff>* va = refl_pairs(refl, n, j0 + a);
+    const cx<ff>* vb = refl_pairs(refl, n, j0 + bb);
+    ff2 acc = pk_zero();
+    for (int p = ((j0 + bb + 1) >> 1) + lane; p < NP; p += 32) acc = fma(as2(va[p]), as2(vb[p]), acc);
+    acc = ff2_settle(acc);
+    for (int o = 16; o > 0; o >>= 1) acc = acc + pk_shfl_xor(acc, o);
+    if (lane == 0) P[a][bb] = {ffs_to_d(ffs_add(pk_get_re(acc), pk_get_im(acc))), R(0)};
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    z t[kWY][kWY];
+    for (int r = 0; r < kWY; ++r)
+      for (int c = 0; c < kWY; ++c) t[r][c] = {R(0), R(0)};
+    for (int i = 0; i < nr; ++i) {
+      const z ti = tau[j0 + i];
+      for (int r = 0; r < i; ++r) {
+        z acc = {R(0), R(0)};
+        for (int c = r; c < i; ++c) acc = cadd(acc, cmul(t[r][c], P[c][i]));
+        t[r][i] = {-(ti.x * acc.x - ti.y * acc.y), -(ti.x * acc.y + ti.y * acc.x)};
+      }
+      t[i][i] = ti;
+    }
+    z* out = T + (size_t)g * kWY * kWY;
+    for (int r = 0; r < kWY; ++r)
+      for (int c = 0; c < kWY; ++c) out[r * kWY + c] = t[r][c];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_backtransform_real_ff(const z* __restrict__ refl, int n,
+                                                               const z* __restrict__ T,
+                                                               const R* Y, z* X, int ldx) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int U = 2;
+  cx<ff>* x = reinterpret_cast<cx<ff>*>(smem_raw);   // pair-packed eigenvector
+  __shared__ cx<ff> part[8][kWY];
+  __shared__ ff wv[kWY], uv[kWY];
+  const int k = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  const int NP = (n + 1) >> 1;
+  for (int p = tid; p < NP; p += nt) {
+    const ff a0 = ff(Y[(size_t)k * n + 2 * p]);
+    const ff a1 = 2 * p + 1 < n ? ff(Y[(size_t)k * n + 2 * p + 1]) : ff(0.f, 0.f);
+    x[p] = of2(pk_make(a0, a1));
+  }
+  __syncthreads();
+  const int ngroups = (n - 1 + kWY - 1) / kWY;
+  for (int g = ngroups - 1; g >= 0; --g) {
+    const int j0 = g * kWY, p0 = (j0 + 1) >> 1;
+    const int nr = min(kWY, n - 1 - j0);
+    const z* tg0 = T + (size_t)g * kWY * kWY;
+    unsigned act = 0;
+#pragma unroll
+    for (int a = 0; a < kWY; ++a)
+      if (a < nr && tg0[a * kWY + a].x != R(0)) act |= 1u << a;
+    // w_a = v_a . x over the pairs from p0 (v_a is zero below its own start)
+    ff2 acc[kWY];
+#pragma unroll
+    for (int a = 0; a < kWY; ++a) acc[a] = pk_zero();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + tid + u * nt;
+      if (p < NP) {
+        const ff2 xp = as2(x[p]);
+#pragma unroll
+        for (int a = 0; a < kWY; ++a)
+          if ((act >> a) & 1u) acc[a] = fma(as2(refl_pairs(refl, n, j0 + a)[p]), xp, acc[a]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < kWY; ++a) acc[a] = ff2_settle(acc[a]);
+    const ff2 s8 = pk_warp_rows8(acc);
+    if ((lane & 3) == 0) part[warp][lane >> 2] = of2(ff2_settle(s8));
+    __syncthreads();
+    if (warp == 0) {
+      if (lane < kWY) {
+        ff2 s = as2(part[0][lane]);
+        for (int q = 1; q < nw; ++q) s = s + as2(part[q][lane]);
+        s = ff2_settle(s);
+        wv[lane] = ffs_add(pk_get_re(s), pk_get_im(s));
+      }
+      __syncwarp();
+      if (lane < kWY) {
+        // u_a = sum_{c >= a} T[a][c] w_c (c < nr)
+        const z* tg = tg0 + lane * kWY;
+        ff ua = ff(0.f, 0.f);
+        for (int c = lane; c < nr; ++c) ua = ffs_add(ua, ffs_mul(ff(tg[c].x), wv[c]));
+        uv[lane] = ua;
+      }
+    }
+    __syncthreads();
+    // x -= sum_a v_a u_a
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = p0 + tid + u * nt;
+      if (p < NP) {
+        ff2 xp = as2(x[p]);
+#pragma unroll
+        for (int a = 0; a < kWY; ++a)
+          if ((act >> a) & 1u)
+            xp = fma(pk_neg(as2(refl_pairs(refl, n, j0 + a)[p])), ff2_bcast(uv[a]), xp);
+        x[p] = of2(ff2_settle(xp));
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) X[(size_t)i * ldx + k] = {ffs_to_d(pk_elem(x, i)), R(0)};
+}
 #endif
 
 // Eigenvalues and eigenvectors of the tridiagonal T (wk.d, wk.e) and the
 // back-transformation through the reflectors (wk.tau, wk.refl) into X.
 static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, cudaStream_t st,
-                       Prof* pf, bool ff_refl = false) {
+                       Prof* pf, bool ff_refl = false, bool real_refl = false) {
   int rc = QE_OK;
   {
     ProfScope ps(pf, "heev_bisect", st);
@@ -2147,7 +2270,12 @@ static int heev_finish(int n, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk, c
   {
     ProfScope ps(pf, "heev_backtransform", st);
 #if defined(QE_DENSE_FP64)
-    if (ff_refl) {
+    if (real_refl) {
+      set_max_dynamic_smem(k_backtransform_real_ff);
+      if (n > 1) k_wy_t_real_ff<<<(n - 1 + kWY - 1) / kWY, 256, 0, st>>>(wk.refl, n, wk.tau, wk.wyt);
+      k_backtransform_real_ff<<<nev, 256, ((n + 1) / 2) * sizeof(cx<ff>), st>>>(wk.refl, n, wk.wyt,
+                                                                              wk.y, X, ldx);
+    } else if (ff_refl) {
       set_max_dynamic_smem(k_backtransform_ff);
       if (n > 1) k_wy_t_ff<<<(n - 1 + kWY - 1) / kWY, 256, 0, st>>>(wk.refl, n, wk.tau, wk.wyt);
       k_backtransform_ff<<<nev, 256, bsm, st>>>(wk.refl, n, wk.wyt, wk.y, X, ldx);
@@ -2277,7 +2405,7 @@ int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R
                               rsm, kTridRealThreads);
         if (rc0) return rc0;
       }
-      return heev_finish(n, nev, w, X, ldx, wk, st, pf, true);   // packed reflectors
+      return heev_finish(n, nev, w, X, ldx, wk, st, pf, true, true);   // real pair-packed reflectors
     }
   }
   const int gf = tridiag_fused_grid(n, &rsm);

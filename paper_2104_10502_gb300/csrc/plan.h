@@ -227,11 +227,19 @@ int tc_gemm_splits(int Mp, int Np, int Kp);
 // non-zero code to *status.
 size_t tc_inner_bytes(int M, int N, int K);
 size_t tc_outer_bytes(int M, int N, int K);
+// real_out: only Re C, written as (Re C, 0) (the k = 0 real-in-r products), with
+// half the GEMM columns.
 int tc_inner(const double* A, const double* B, int M, int N, int K, double* C, int ldc, void* work,
-             size_t work_bytes, int* status, cudaStream_t st, Prof* pf);
+             size_t work_bytes, int* status, cudaStream_t st, Prof* pf, bool real_out = false);
 int tc_outer(const double* A, const double* B, int M, int N, int K, double* C, int ldc,
              int alpha_neg, int beta, void* work, size_t work_bytes, int* status, cudaStream_t st,
              Prof* pf);
+// tc_outer for a real-valued B (zero imaginary parts; the k = 0 mode's Ritz
+// vectors and Gram blocks): half the tensor-core work; work of tc_outer_real_bytes().
+size_t tc_outer_real_bytes(int M, int N, int K);
+int tc_outer_real(const double* A, const double* B, int M, int N, int K, double* C, int ldc,
+                  int alpha_neg, int beta, void* work, size_t work_bytes, int* status,
+                  cudaStream_t st, Prof* pf);
 // hpsi += beta^T D (conj(beta) psi^T) on the tensor cores; work of nonlocal_tc_bytes().
 size_t nonlocal_tc_bytes(int np, int nb, int npw);
 size_t nonlocal_tc_beta_bytes(int np, int npw);

@@ -370,6 +370,38 @@ __global__ void k_pack_beta_t(const double2* __restrict__ beta, int np, int npw,
   }
 }
 
+// Transposed complex operand as real rows (outer products with a real right-hand
+// matrix): A'[2m][k] = Re A[k][m], A'[2m+1][k] = Im A[k][m], A [K][M]; tiles
+// through shared memory.
+__global__ void k_pack_t_reim(const double2* __restrict__ A, int K, int M, int Kp,
+                              float* __restrict__ hi, float* __restrict__ lo) {
+  __shared__ double2 tile[32][33];
+  const int m0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, m = m0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < K && m < M) ? A[(size_t)k * M + m] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int m = m0 + r, k = k0 + threadIdx.x;
+    if (m >= M || k >= K) continue;
+    const double2 v = tile[threadIdx.x][r];
+    split_store((float)v.x, hi, lo, (size_t)(2 * m) * Kp + k);
+    split_store((float)v.y, hi, lo, (size_t)(2 * m + 1) * Kp + k);
+  }
+}
+
+// B rows n < N: Re Q[k][n] over k < K (Q [K][N] real-valued); zero elsewhere
+__global__ void k_pack_q_real(const double2* __restrict__ Q, int K, int N, int Np, int Kp,
+                              float* __restrict__ hi, float* __restrict__ lo) {
+  const size_t total = (size_t)Np * Kp;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / Kp), k = (int)(t % Kp);
+    split_store(r < N && k < K ? (float)Q[(size_t)k * N + r].x : 0.f, hi, lo, t);
+  }
+}
+
 // zero the padding of a transposed-operand matrix: rows >= rows, and columns
 // k >= kvalid of the first rows
 __global__ void k_pack_pad(int Mp, int Kp, int rows, int kvalid, float* __restrict__ hi,
@@ -471,6 +503,19 @@ __global__ void k_combine_inner(const float* __restrict__ C32, int ns, int Mp, i
   }
 }
 
+// C[m][n] = (sum_s C32[s][m][n], 0): the real-output inner products
+__global__ void k_combine_inner_real(const float* __restrict__ C32, int ns, int Mp, int Np, int M,
+                                     int N, double2* __restrict__ C, int ldc) {
+  const size_t total = (size_t)M * N;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(t / N), n = (int)(t % N);
+    double re = 0.0;
+    for (int s = 0; s < ns; ++s) re += (double)C32[(size_t)s * Mp * Np + (size_t)m * Np + n];
+    C[(size_t)m * ldc + n] = make_double2(re, 0.0);
+  }
+}
+
 // C[n][m] (+)= (-) (sum_s C32[s][m][n], sum_s C32[s][m][N + n]) (outer products)
 __global__ void k_combine_outer(const float* __restrict__ C32, int ns, int Mp, int Np, int M, int N,
                                 double2* __restrict__ C, int ldc, int alpha_neg, int beta) {
@@ -483,6 +528,28 @@ __global__ void k_combine_outer(const float* __restrict__ C32, int ns, int Mp, i
       const float* c = C32 + (size_t)s * Mp * Np + (size_t)m * Np;
       re += (double)c[n];
       im += (double)c[N + n];
+    }
+    if (alpha_neg) { re = -re; im = -im; }
+    double2* p = C + (size_t)n * ldc + m;
+    if (beta) { const double2 o = *p; re += o.x; im += o.y; }
+    *p = make_double2(re, im);
+  }
+}
+
+// C[n][m] (+)= (-) (sum_s C32[s][2m][n], sum_s C32[s][2m+1][n]) (outer products
+// with a real right-hand matrix)
+__global__ void k_combine_outer_reim(const float* __restrict__ C32, int ns, int Mp, int Np, int M,
+                                     int N, double2* __restrict__ C, int ldc, int alpha_neg,
+                                     int beta) {
+  const size_t total = (size_t)N * M;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int n = (int)(t / M), m = (int)(t % M);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      const float* c = C32 + (size_t)s * Mp * Np + (size_t)(2 * m) * Np + n;
+      re += (double)c[0];
+      im += (double)c[Np];
     }
     if (alpha_neg) { re = -re; im = -im; }
     double2* p = C + (size_t)n * ldc + m;
@@ -614,13 +681,16 @@ size_t tc_outer_bytes(int M, int N, int K) {
 }
 
 int tc_inner(const double* A, const double* B, int M, int N, int K, double* C, int ldc, void* work,
-             size_t work_bytes, int* status, cudaStream_t st, Prof* pf) {
+             size_t work_bytes, int* status, cudaStream_t st, Prof* pf, bool real_out) {
   if (M <= 0 || N <= 0) return QE_OK;
   if (tc_inner_bytes(M, N, K) > work_bytes) {
     set_error("tc_inner: workspace too small");
     return QE_EINVAL;
   }
-  const int Mp = pad_to(M, TC_BM), Kp = kcat(K), Np = pad_to(2 * N, TC_BN), kh = kh_of(K);
+  // real output: Re(a^+ b) is the real dot product of the [Re | Im] rows, so B
+  // needs only its [Re | Im] rows (half the GEMM's columns)
+  const int Mp = pad_to(M, TC_BM), Kp = kcat(K), Np = pad_to(real_out ? N : 2 * N, TC_BN);
+  const int kh = kh_of(K);
   const int ns = tc_gemm_splits(Mp, Np, Kp);
   char* p = static_cast<char*>(work);
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
@@ -632,15 +702,67 @@ int tc_inner(const double* A, const double* B, int M, int N, int K, double* C, i
   {
     ProfScope ps(pf, "k_tc_pack", st);
     k_pack_rows<<<pack_grid(Kp, kh, Mp), 256, 0, st>>>((const double2*)A, M, K, kh, Kp, ahi, alo);
-    k_pack_psi<<<pack_grid(Kp, kh, Np - N), 256, 0, st>>>((const double2*)B, N, K, kh, Kp, bhi, blo);
+    if (real_out)
+      k_pack_rows<<<pack_grid(Kp, kh, Np), 256, 0, st>>>((const double2*)B, N, K, kh, Kp, bhi, blo);
+    else
+      k_pack_psi<<<pack_grid(Kp, kh, Np - N), 256, 0, st>>>((const double2*)B, N, K, kh, Kp, bhi, blo);
     if (pf) pf->launches += 1;
   }
   int rc = tc_gemm_tf32x3(ahi, alo, bhi, blo, Mp, Np, Kp, ns, c, status, st, pf);
   if (rc) return rc;
   ProfScope ps(pf, "k_tc_combine", st);
-  k_combine_inner<<<grid_of((size_t)M * N), 256, 0, st>>>(c, ns, Mp, Np, M, N, (double2*)C, ldc);
+  if (real_out)
+    k_combine_inner_real<<<grid_of((size_t)M * N), 256, 0, st>>>(c, ns, Mp, Np, M, N, (double2*)C, ldc);
+  else
+    k_combine_inner<<<grid_of((size_t)M * N), 256, 0, st>>>(c, ns, Mp, Np, M, N, (double2*)C, ldc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_error("tc_inner: %s", cudaGetErrorString(e)); return QE_ECUDA; }
+  return QE_OK;
+}
+
+size_t tc_outer_real_bytes(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 0;
+  const size_t Mp = pad_to(2 * M, TC_BM), Kp = pad_to(K, TC_BK), Np = pad_to(N, TC_BN);
+  const size_t ns = tc_gemm_splits((int)Mp, (int)Np, (int)Kp);
+  return 2 * Mp * Kp * 4 + 2 * Np * Kp * 4 + ns * Mp * Np * 4 + 8 * 256;
+}
+
+// The outer product with a real right-hand matrix B: the real and imaginary parts
+// of A's columns are separate GEMM rows over a real K axis, 2M x N x K instead of
+// M x 2N x 2K (half the tensor-core work).
+int tc_outer_real(const double* A, const double* B, int M, int N, int K, double* C, int ldc,
+                  int alpha_neg, int beta, void* work, size_t work_bytes, int* status,
+                  cudaStream_t st, Prof* pf) {
+  if (M <= 0 || N <= 0) return QE_OK;
+  if (tc_outer_real_bytes(M, N, K) > work_bytes) {
+    set_error("tc_outer_real: workspace too small");
+    return QE_EINVAL;
+  }
+  const int Mp = pad_to(2 * M, TC_BM), Kp = pad_to(K, TC_BK), Np = pad_to(N, TC_BN);
+  const int ns = tc_gemm_splits(Mp, Np, Kp);
+  char* p = static_cast<char*>(work);
+  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return q; };
+  float* ahi = (float*)take((size_t)Mp * Kp * 4);
+  float* alo = (float*)take((size_t)Mp * Kp * 4);
+  float* bhi = (float*)take((size_t)Np * Kp * 4);
+  float* blo = (float*)take((size_t)Np * Kp * 4);
+  float* c = (float*)take((size_t)ns * Mp * Np * 4);
+  {
+    ProfScope ps(pf, "k_tc_pack", st);
+    k_pack_pad<<<grid_of((size_t)(Mp - 2 * M) * Kp + (size_t)2 * M * (Kp - K)), 256, 0, st>>>(
+        Mp, Kp, 2 * M, K, ahi, alo);
+    dim3 gt((M + 31) / 32, (K + 31) / 32);
+    k_pack_t_reim<<<gt, dim3(32, 8), 0, st>>>((const double2*)A, K, M, Kp, ahi, alo);
+    k_pack_q_real<<<grid_of((size_t)Np * Kp), 256, 0, st>>>((const double2*)B, K, N, Np, Kp, bhi, blo);
+    if (pf) pf->launches += 2;
+  }
+  int rc = tc_gemm_tf32x3(ahi, alo, bhi, blo, Mp, Np, Kp, ns, c, status, st, pf);
+  if (rc) return rc;
+  ProfScope ps(pf, "k_tc_combine", st);
+  k_combine_outer_reim<<<grid_of((size_t)M * N), 256, 0, st>>>(c, ns, Mp, Np, M, N, (double2*)C,
+                                                             ldc, alpha_neg, beta);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error("tc_outer_real: %s", cudaGetErrorString(e)); return QE_ECUDA; }
   return QE_OK;
 }
 

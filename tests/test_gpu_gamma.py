@@ -9,7 +9,8 @@ qe_hpsi tolerances (FP64 1e-12 per band, mixed 2e-5), odd band counts, a cell
 off k = 0 where the flag must be ignored; Davidson solves with the mode (the
 default at k = 0) against the same solves without it (QE_NO_GAMMA) and the
 stored dense eigenvalues, and the returned bands real in r (the mode is the
-default for FP64 solves on grids of at least 48^3 points, else on request).
+default for solves on grids of at least 48^3 points, mixed ones with
+QE_RR_FP32 excepted, else on request).
 """
 import os
 
@@ -169,7 +170,7 @@ def test_davidson_gamma_mode_matches_complex_bands(q, ctx, prec, tol, etol):
     psi0 = qeinputs.start_bands(kin, nb, c["psi_seed"])
     ref = np.loadtxt(os.path.join(GOLDEN, "c0_dense_eigs.txt"))[:nb]
     out = {}
-    on = q.QE_GAMMA        # C0 (32^3 grid) is below the size where FP64 solves take the mode by default
+    on = q.QE_GAMMA        # C0 (32^3 grid) is below the size where solves take the mode by default
     for flag in (on, q.QE_NO_GAMMA):
         pt = _to_t(psi0)
         ev = torch.zeros(nb, dtype=torch.float64, device="cuda")
