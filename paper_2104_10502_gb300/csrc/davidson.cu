@@ -652,7 +652,7 @@ static int rayleigh_ritz_f32(DvState& S, int n, cudaStream_t st, Prof* pf) {
   } else {
     {
       ProfScope ps(pf, "rr_cholesky", st);
-      DV_TRY(f32::cholesky(L32, n, n, 0.f, false, w.piv, w.status, w.bar, w.p, w.vbuf, st));
+      DV_TRY(f32::cholesky(L32, n, n, 0.f, false, w.piv, w.status, w.bar, st, S.gamma));
     }
     {
       ProfScope ps(pf, "rr_reduce", st);
@@ -667,7 +667,7 @@ static int rayleigh_ritz_f32(DvState& S, int n, cudaStream_t st, Prof* pf) {
   }
   {
     ProfScope ps(pf, "rr_backsub", st);
-    DV_TRY(f32::trsm_upper_h(L32, n, n, X32, nb, nb, st));
+    DV_TRY(f32::trsm_upper_h(L32, n, n, X32, nb, nb, st, S.gamma));
   }
   k_c_to_z<<<grid_for((size_t)n * nb), 256, 0, st>>>(X32, nb, S.X, nb, n, nb, e32, S.e, nb);
   return check_launch("k_c_to_z");
@@ -721,13 +721,13 @@ static int rayleigh_ritz(DvState& S, int n, bool generalised, cudaStream_t st, P
     // one CTA in shared memory: Cholesky, reduction, tridiagonalisation
     DV_TRY(rr_small(S.Hr, S.Sr, md, n, nb, S.Lw, S.e, S.X, nb, S.dw, st, pf));
     ProfScope ps(pf, "rr_backsub", st);
-    return trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st);            // X = L^-+ Y
+    return trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st, S.gamma);   // X = L^-+ Y
   }
   DV_CU(cudaMemcpy2DAsync(S.Lw, n * zb, S.Sr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
   DV_CU(cudaMemcpy2DAsync(S.Zw, n * zb, S.Hr, md * zb, n * zb, n, cudaMemcpyDeviceToDevice, st));
   {
     ProfScope ps(pf, "rr_cholesky", st);
-    DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, S.dw.bar, S.dw.p, S.dw.vbuf, st));
+    DV_TRY(cholesky(S.Lw, n, n, 0.0, false, S.dw.piv, S.dw.status, S.dw.bar, st, S.gamma));
   }
   {
     // L^T in the reflector buffer (free until the eigensolver) for coalesced solves
@@ -742,7 +742,7 @@ static int rayleigh_ritz(DvState& S, int n, bool generalised, cudaStream_t st, P
   DV_TRY(heev_lowest(S.Aw, n, n, nb, S.e, S.X, nb, S.dw, st, pf, S.gamma));
   {
     ProfScope ps(pf, "rr_backsub", st);
-    DV_TRY(trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st));            // X = L^-+ Y
+    DV_TRY(trsm_upper_h(S.Lw, n, n, S.X, nb, nb, st, S.gamma));   // X = L^-+ Y
   }
   return QE_OK;
 }
@@ -763,8 +763,8 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
     DV_TRY(gram<T>(S, cur, ncur, cur, ncur, S.G, ncur, st, pf));
     DV_TRY(hermitize(S.G, ncur, ncur, st));
     DV_CU(cudaMemsetAsync(S.dw.status, 0, sizeof(int), st));
-    DV_TRY(cholesky(S.G, ncur, ncur, drop * drop, true, S.dw.piv, S.dw.status, S.dw.bar, S.dw.p,
-                    S.dw.vbuf, st));
+    DV_TRY(cholesky(S.G, ncur, ncur, drop * drop, true, S.dw.piv, S.dw.status, S.dw.bar, st,
+                    S.gamma));
     std::vector<double> piv(ncur);
     DV_CU(cudaMemcpyAsync(piv.data(), S.dw.piv, ncur * sizeof(double), cudaMemcpyDeviceToHost, st));
     DV_CU(cudaStreamSynchronize(st));
@@ -782,7 +782,7 @@ static int orthonormalise(DvState& S, int n, z* in, int nd, z* out, int* nk_out,
     k_gather_sub<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.G, ncur, S.idx, nk, S.Lk, nk);
     k_identity<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.Mk, nk, nk);
     DV_TRY(check_launch("orthonormalise"));
-    DV_TRY(trsm_upper_h(S.Lk, nk, nk, S.Mk, nk, nk, st));
+    DV_TRY(trsm_upper_h(S.Lk, nk, nk, S.Mk, nk, nk, st, S.gamma));
     DV_CU(cudaMemsetAsync(S.Mf, 0, (size_t)ncur * nk * sizeof(z), st));
     k_place_rows<<<grid_for((size_t)nk * nk), 256, 0, st>>>(S.Mk, nk, S.idx, nk, S.Mf);
     DV_TRY(check_launch("k_place_rows"));

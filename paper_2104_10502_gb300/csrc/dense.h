@@ -59,17 +59,18 @@ using DenseWork = DenseWorkT<double>;
 // Lower Cholesky in place (upper part zeroed).  allow_drop: a column whose
 // remaining pivot^2 is <= drop2 is dropped (zero column, piv = 0); otherwise a
 // non-positive pivot sets *status = 1 + column.
-// c0, c1: n complex each (contiguous copies of the pivot column).
+// real_sym: A real (zero imaginary parts), factored in real arithmetic.
 int cholesky(cx<double>* A, int n, int lda, double drop2, bool allow_drop, double* piv,
-             int* status, GridBar bar, cx<double>* c0, cx<double>* c1, cudaStream_t st);
+             int* status, GridBar bar, cudaStream_t st, bool real_sym = false);
 // L X = B with L given as its transpose LT (LT[i][r] = L[r][i]).
 int trsm_lower_t(const cx<double>* LT, int n, int ldt, cx<double>* B, int ldb, int ncols,
                  cudaStream_t st);
 // dst = src^T (rows x cols -> cols x rows)
 int transpose(const cx<double>* src, int lds, cx<double>* dst, int ldd, int rows, int cols,
               cudaStream_t st);
+// L^+ X = B (L lower with real positive diagonal); real_sym: L and B real.
 int trsm_upper_h(const cx<double>* L, int n, int ldl, cx<double>* B, int ldb, int ncols,
-                 cudaStream_t st);
+                 cudaStream_t st, bool real_sym = false);
 int conj_transpose(const cx<double>* src, int lds, cx<double>* dst, int ldd, int rows, int cols,
                    cudaStream_t st);
 int hermitize(cx<double>* A, int n, int lda, cudaStream_t st);
@@ -93,17 +94,18 @@ namespace qe::f32 {
 // Lower Cholesky in place (upper part zeroed).  allow_drop: a column whose
 // remaining pivot^2 is <= drop2 is dropped (zero column, piv = 0); otherwise a
 // non-positive pivot sets *status = 1 + column.
-// c0, c1: n complex each (contiguous copies of the pivot column).
+// real_sym: A real (zero imaginary parts), factored in real arithmetic.
 int cholesky(cx<float>* A, int n, int lda, float drop2, bool allow_drop, float* piv,
-             int* status, GridBar bar, cx<float>* c0, cx<float>* c1, cudaStream_t st);
+             int* status, GridBar bar, cudaStream_t st, bool real_sym = false);
 // L X = B with L given as its transpose LT (LT[i][r] = L[r][i]).
 int trsm_lower_t(const cx<float>* LT, int n, int ldt, cx<float>* B, int ldb, int ncols,
                  cudaStream_t st);
 // dst = src^T (rows x cols -> cols x rows)
 int transpose(const cx<float>* src, int lds, cx<float>* dst, int ldd, int rows, int cols,
               cudaStream_t st);
+// L^+ X = B (L lower with real positive diagonal); real_sym: L and B real.
 int trsm_upper_h(const cx<float>* L, int n, int ldl, cx<float>* B, int ldb, int ncols,
-                 cudaStream_t st);
+                 cudaStream_t st, bool real_sym = false);
 int conj_transpose(const cx<float>* src, int lds, cx<float>* dst, int ldd, int rows, int cols,
                    cudaStream_t st);
 int hermitize(cx<float>* A, int n, int lda, cudaStream_t st);

@@ -175,57 +175,134 @@ __device__ __forceinline__ void block_sum2_1b(R& a, R& b, R (*rb)[2][8], int par
   for (int w = 0; w < nw; ++w) { a += rb[par][0][w]; b += rb[par][1][w]; }
 }
 
-// Cholesky of the lower triangle, all columns in one launch (one barrier per
-// column).  The pivot column of step j is read from a contiguous copy (c0/c1,
-// n complex each, alternating): the warp that updates row r writes the new
-// A[r][j+1] there for step j+1, so no step reads a column of A with stride lda.
-__global__ void __launch_bounds__(256) k_chol_coop(z* A, int n, int lda, R drop2, int allow_drop,
-                                                   R* piv, int* status, GridBar bar, z* c0,
-                                                   z* c1) {
-  const size_t nthr = (size_t)gridDim.x * blockDim.x;
-  const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (size_t i = gtid; i < (size_t)n; i += nthr) c0[i] = ldz(&A[i * lda]);
-  if (!grid_sync(bar)) return;
-  for (int j = 0; j < n; ++j) {
-    z* cur = (j & 1) ? c1 : c0;
-    z* nxt = (j & 1) ? c0 : c1;
-    const R d = ldz(&cur[j]).x;
-    const bool keep = allow_drop ? (d > drop2) : (d > R(0));
-    if (gtid == 0) {
-      piv[j] = keep ? sqrt(d) : R(0);
-      if (!keep && !allow_drop) *status = 1 + j;
+// Cholesky of the lower triangle with dropping: a pivot above drop2 (above 0
+// without dropping) is kept, else its column is dropped (zero in L, pivot 0; a
+// zero pivot without dropping sets *status = 1 + column), which is Gram-Schmidt
+// with dropping expressed on the Gram matrix.  Blocked: panels of kCholB columns
+// with two grid barriers each instead of one per column.  Per panel every CTA
+// loads the diagonal block and one warp factors it in shared memory
+// (right-looking); the rows below are solved against it one row per warp
+// (L21 = A21 L11^-+, forward substitution across the lanes); after the barrier
+// CTA 0 writes L11 and the pivots, and every warp takes (row, 32 columns) units
+// of the trailing update A22 -= L21 L21^+; a second barrier closes the panel.
+// The arithmetic is FP64 (R), spread over the grid for the trailing update,
+// whose FP64 work dominates; REAL: zero imaginary parts (the k = 0 Gram
+// matrices), a quarter of it.  The upper triangle is zeroed at the end.
+constexpr int kCholB = 32;
+
+template <bool REAL>
+__global__ void __launch_bounds__(256) k_chol_blocked(z* A, int n, int lda, R drop2, int allow_drop,
+                                                      R* piv, int* status, GridBar bar) {
+  __shared__ z D[kCholB][kCholB + 1];   // diagonal block -> L11 (lower)
+  __shared__ R sd[kCholB];               // its pivots (0: dropped)
+  const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+  const int gw = c * nwarp + warp, nw = G * nwarp;
+  unsigned nbar = 0;
+  for (int j0 = 0; j0 < n; j0 += kCholB) {
+    const int b = min(kCholB, n - j0), j1 = j0 + b, m = n - j1;
+    for (int t = tid; t < b * b; t += nt) {
+      const int r = t / b, q = t % b;
+      D[r][q] = q <= r ? ldz(&A[(size_t)(j0 + r) * lda + j0 + q]) : z{R(0), R(0)};
     }
-    if (keep) {
-      // lower trailing block, consecutive threads on consecutive columns of a row
-      const R inv = R(1) / d;
-      const int m = n - j - 1;
-      const size_t total = (size_t)m * m;
-      for (size_t t = gtid; t < total; t += nthr) {
-        const int r = j + 1 + (int)(t / m), c = j + 1 + (int)(t % m);
-        if (c > r) continue;
-        const z arj = ldz(&cur[r]), acj = ldz(&cur[c]);
-        z* a = &A[(size_t)r * lda + c];
-        const z av = ldz(a);
-        const z nv = {av.x - (arj.x * acj.x + arj.y * acj.y) * inv,
-                      av.y - (arj.y * acj.x - arj.x * acj.y) * inv};
-        *a = nv;
-        if (c == j + 1) nxt[r] = nv;
+    __syncthreads();
+    if (warp == 0) {
+      for (int j = 0; j < b; ++j) {
+        const R d = D[j][j].x;
+        const bool keep = allow_drop ? (d > drop2) : (d > R(0));
+        const R p = keep ? sqrt(d) : R(0);
+        __syncwarp();
+        if (lane == j) { D[j][j] = {p, R(0)}; sd[j] = p; }
+        if (lane > j && lane < b) {
+          const z a = D[lane][j];
+          D[lane][j] = keep ? z{a.x / p, REAL ? R(0) : a.y / p} : z{R(0), R(0)};
+        }
+        __syncwarp();
+        if (keep && lane > j && lane < b) {
+          const z lj = D[lane][j];
+          for (int k = j + 1; k <= lane; ++k) {
+            const z lk = D[k][j];
+            z& a = D[lane][k];
+            if (REAL) {
+              a.x = fmar(-lj.x, lk.x, a.x);
+            } else {   // a -= lj conj(lk)
+              a.x = fmar(-lj.x, lk.x, fmar(-lj.y, lk.y, a.x));
+              a.y = fmar(-lj.y, lk.x, fmar(lj.x, lk.y, a.y));
+            }
+          }
+        }
+        __syncwarp();
       }
-    } else {
-      // a dropped column changes nothing: the next pivot column as it stands
-      for (size_t r = j + 1 + gtid; r < (size_t)n; r += nthr) nxt[r] = ldz(&A[r * lda + j + 1]);
     }
-    if (!grid_sync(bar)) return;
+    __syncthreads();
+    // L21: row r solves l_r L11^+ = a_r; lane q carries column j0 + q
+    for (int r = j1 + gw; r < n; r += nw) {
+      z a = lane < b ? ldz(&A[(size_t)r * lda + j0 + lane]) : z{R(0), R(0)};
+      for (int j = 0; j < b; ++j) {
+        const R p = sd[j];
+        const z aj = {__shfl_sync(0xffffffffu, a.x, j), REAL ? R(0) : __shfl_sync(0xffffffffu, a.y, j)};
+        const z lj = p > R(0) ? z{aj.x / p, REAL ? R(0) : aj.y / p} : z{R(0), R(0)};
+        if (lane == j) a = lj;
+        if (lane > j && lane < b && p > R(0)) {   // a_q -= l_j conj(L11[q][j])
+          const z lq = D[lane][j];
+          if (REAL) {
+            a.x = fmar(-lj.x, lq.x, a.x);
+          } else {
+            a.x = fmar(-lj.x, lq.x, fmar(-lj.y, lq.y, a.x));
+            a.y = fmar(-lj.y, lq.x, fmar(lj.x, lq.y, a.y));
+          }
+        }
+      }
+      if (lane < b) A[(size_t)r * lda + j0 + lane] = a;
+    }
+    if (!grid_sync_mono(bar, ++nbar)) return;
+    if (c == 0) {
+      for (int t = tid; t < b * b; t += nt) {
+        const int r = t / b, q = t % b;
+        if (q <= r) A[(size_t)(j0 + r) * lda + j0 + q] = D[r][q];
+      }
+      for (int j = tid; j < b; j += nt) {
+        piv[j0 + j] = sd[j];
+        const bool keep = sd[j] > R(0);
+        if (!keep && !allow_drop) *status = 1 + j0 + j;
+      }
+    }
+    // trailing update: unit (row r, columns q0 .. q0 + 31) of the lower triangle
+    const int nch = (m + 31) / 32;
+    for (int u = gw; u < m * nch; u += nw) {   // uniform per warp
+      const int r = j1 + u / nch, q0 = j1 + 32 * (u % nch);
+      if (q0 > r) continue;
+      const int q = q0 + lane;
+      const bool act = q <= r;
+      const z lr = lane < b ? ldz(&A[(size_t)r * lda + j0 + lane]) : z{R(0), R(0)};
+      const z* lq = A + (size_t)(act ? q : r) * lda + j0;
+      z acc = {R(0), R(0)};
+      for (int k = 0; k < b; ++k) {   // acc = sum_k l_rk conj(l_qk)
+        const R rx = __shfl_sync(0xffffffffu, lr.x, k);
+        const R ry = REAL ? R(0) : __shfl_sync(0xffffffffu, lr.y, k);
+        if (act) {
+          const z lk = ldz(lq + k);
+          if (REAL) {
+            acc.x = fmar(rx, lk.x, acc.x);
+          } else {
+            acc.x = fmar(rx, lk.x, fmar(ry, lk.y, acc.x));
+            acc.y = fmar(ry, lk.x, fmar(-rx, lk.y, acc.y));
+          }
+        }
+      }
+      if (act) {
+        z* a = &A[(size_t)r * lda + q];
+        const z av = ldz(a);
+        *a = {av.x - acc.x, REAL ? R(0) : av.y - acc.y};
+      }
+    }
+    if (!grid_sync_mono(bar, ++nbar)) return;
   }
   const size_t total = (size_t)n * n;
+  const size_t nthr = (size_t)G * nt, gtid = (size_t)c * nt + tid;
   for (size_t t = gtid; t < total; t += nthr) {
     const int i = (int)(t / n), j = (int)(t % n);
-    z& a = A[(size_t)i * lda + j];
-    const R pj = ldd(&piv[j]);
-    if (j > i || pj == R(0)) { a = {R(0), R(0)}; continue; }
-    if (i == j) { a = {pj, R(0)}; continue; }
-    const z av = ldz(&a);
-    a = {av.x / pj, av.y / pj};
+    if (j > i) A[(size_t)i * lda + j] = {R(0), R(0)};
   }
 }
 
@@ -252,16 +329,22 @@ static int launch_coop(const void* f, int blocks, void** args, cudaStream_t st, 
 }
 
 int cholesky(z* A, int n, int lda, R drop2, bool allow_drop, R* piv, int* status,
-             GridBar bar, z* c0, z* c1, cudaStream_t st) {
+             GridBar bar, cudaStream_t st, bool real_sym) {
   if (n <= 0) return QE_OK;
   if (cudaMemsetAsync(bar.count, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) {
     set_error("cholesky: memset failed");
     return QE_ECUDA;
   }
   int allow = allow_drop ? 1 : 0;
-  void* args[] = {&A, &n, &lda, &drop2, &allow, &piv, &status, &bar, &c0, &c1};
-  const int blocks = coop_blocks((const void*)k_chol_coop, (size_t)n * n / 2);
-  return launch_coop((const void*)k_chol_coop, blocks, args, st, "k_chol_coop");
+  void* args[] = {&A, &n, &lda, &drop2, &allow, &piv, &status, &bar};
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // one CTA per SM at most; ~256 elements of the lower triangle per CTA, so that
+  // the FP64 work of the trailing updates spreads over the SMs
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>(nsm, ((size_t)n * n / 2 + 255) / 256));
+  const void* f = real_sym ? (const void*)k_chol_blocked<true> : (const void*)k_chol_blocked<false>;
+  return launch_coop(f, blocks, args, st, "k_chol_blocked");
 }
 
 // ---- triangular solves ---------------------------------------------------------
@@ -318,14 +401,78 @@ __global__ void __launch_bounds__(256) k_trsm_upper_h(const z* L, int n, int ldl
   }
 }
 
+// L^+ X = B for one column of B per CTA (n <= kTrsmRows * 256): the column lives
+// in registers (row r in thread r mod 256), x_i goes through shared memory, and
+// each thread prefetches its entries of the next row of L during a step, so a
+// step is one block barrier, not an L2 round trip.  REAL: zero imaginary parts.
+constexpr int kTrsmRows = 4;
+
+template <bool REAL>
+__global__ void __launch_bounds__(256) k_trsm_upper_h_col(const z* L, int n, int ldl, z* B, int ldb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  z* sx = reinterpret_cast<z*>(smem_raw);   // x_i, n
+  const int col = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  z b[kTrsmRows], lcur[kTrsmRows];
+#pragma unroll
+  for (int k = 0; k < kTrsmRows; ++k) {
+    const int r = tid + k * nt;
+    b[k] = r < n ? B[(size_t)r * ldb + col] : z{R(0), R(0)};
+    lcur[k] = r < n ? ldz(&L[(size_t)(n - 1) * ldl + r]) : z{R(0), R(0)};
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    z lnx[kTrsmRows];
+#pragma unroll
+    for (int k = 0; k < kTrsmRows; ++k) {   // L[i-1][r], r <= i - 1
+      const int r = tid + k * nt;
+      lnx[k] = (i > 0 && r < i) ? ldz(&L[(size_t)(i - 1) * ldl + r]) : z{R(0), R(0)};
+    }
+#pragma unroll
+    for (int k = 0; k < kTrsmRows; ++k)
+      if (tid + k * nt == i) {   // the owner of row i: x_i = b_i / L_ii
+        const R inv = R(1) / lcur[k].x;
+        b[k] = {b[k].x * inv, REAL ? R(0) : b[k].y * inv};
+        sx[i] = b[k];
+      }
+    __syncthreads();
+    const z x = sx[i];
+#pragma unroll
+    for (int k = 0; k < kTrsmRows; ++k) {
+      if (tid + k * nt < i) {   // b_r -= conj(L[i][r]) x_i
+        const z l = lcur[k];
+        if (REAL) {
+          b[k].x = fmar(-l.x, x.x, b[k].x);
+        } else {
+          b[k].x = fmar(-l.x, x.x, fmar(-l.y, x.y, b[k].x));
+          b[k].y = fmar(-l.x, x.y, fmar(l.y, x.x, b[k].y));
+        }
+      }
+      lcur[k] = lnx[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kTrsmRows; ++k) {
+    const int r = tid + k * nt;
+    if (r < n) B[(size_t)r * ldb + col] = b[k];
+  }
+}
+
 int trsm_lower_t(const z* LT, int n, int ldt, z* B, int ldb, int ncols, cudaStream_t st) {
   if (n <= 0 || ncols <= 0) return QE_OK;
   k_trsm_lower_t<<<(ncols + TCOLS - 1) / TCOLS, 256, 0, st>>>(LT, n, ldt, B, ldb, ncols);
   return check_launch("k_trsm_lower_t");
 }
 
-int trsm_upper_h(const z* L, int n, int ldl, z* B, int ldb, int ncols, cudaStream_t st) {
+int trsm_upper_h(const z* L, int n, int ldl, z* B, int ldb, int ncols, cudaStream_t st,
+                 bool real_sym) {
   if (n <= 0 || ncols <= 0) return QE_OK;
+  if (n <= kTrsmRows * 256) {
+    const size_t sm = (size_t)n * sizeof(z);
+    if (real_sym)
+      k_trsm_upper_h_col<true><<<ncols, 256, sm, st>>>(L, n, ldl, B, ldb);
+    else
+      k_trsm_upper_h_col<false><<<ncols, 256, sm, st>>>(L, n, ldl, B, ldb);
+    return check_launch("k_trsm_upper_h_col");
+  }
   k_trsm_upper_h<<<(ncols + TCOLS - 1) / TCOLS, 256, 0, st>>>(L, n, ldl, B, ldb, ncols);
   return check_launch("k_trsm_upper_h");
 }
