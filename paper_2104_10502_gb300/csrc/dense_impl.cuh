@@ -194,7 +194,7 @@ template <bool REAL>
 __global__ void __launch_bounds__(256) k_chol_blocked(z* A, int n, int lda, R drop2, int allow_drop,
                                                       R* piv, int* status, GridBar bar) {
   __shared__ z D[kCholB][kCholB + 1];   // diagonal block -> L11 (lower)
-  __shared__ R sd[kCholB];               // its pivots (0: dropped)
+  __shared__ R sd[kCholB], sdi[kCholB];  // its pivots (0: dropped) and their reciprocals
   const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   const int gw = c * nwarp + warp, nw = G * nwarp;
@@ -208,14 +208,24 @@ __global__ void __launch_bounds__(256) k_chol_blocked(z* A, int n, int lda, R dr
     __syncthreads();
     if (warp == 0) {
       for (int j = 0; j < b; ++j) {
-        const R d = D[j][j].x;
-        const bool keep = allow_drop ? (d > drop2) : (d > R(0));
-        const R p = keep ? sqrt(d) : R(0);
-        __syncwarp();
-        if (lane == j) { D[j][j] = {p, R(0)}; sd[j] = p; }
+        // lane j forms the pivot and its reciprocal (one square root and one
+        // division per column), the others scale by the reciprocal
+        R p = R(0), inv = R(0);
+        if (lane == j) {
+          const R d = D[j][j].x;
+          const bool keep = allow_drop ? (d > drop2) : (d > R(0));
+          p = keep ? sqrt(d) : R(0);
+          inv = keep ? R(1) / p : R(0);
+          D[j][j] = {p, R(0)};
+          sd[j] = p;
+          sdi[j] = inv;
+        }
+        p = __shfl_sync(0xffffffffu, p, j);
+        inv = __shfl_sync(0xffffffffu, inv, j);
+        const bool keep = p > R(0);
         if (lane > j && lane < b) {
           const z a = D[lane][j];
-          D[lane][j] = keep ? z{a.x / p, REAL ? R(0) : a.y / p} : z{R(0), R(0)};
+          D[lane][j] = keep ? z{a.x * inv, REAL ? R(0) : a.y * inv} : z{R(0), R(0)};
         }
         __syncwarp();
         if (keep && lane > j && lane < b) {
@@ -239,9 +249,9 @@ __global__ void __launch_bounds__(256) k_chol_blocked(z* A, int n, int lda, R dr
     for (int r = j1 + gw; r < n; r += nw) {
       z a = lane < b ? ldz(&A[(size_t)r * lda + j0 + lane]) : z{R(0), R(0)};
       for (int j = 0; j < b; ++j) {
-        const R p = sd[j];
+        const R p = sd[j], inv = sdi[j];
         const z aj = {__shfl_sync(0xffffffffu, a.x, j), REAL ? R(0) : __shfl_sync(0xffffffffu, a.y, j)};
-        const z lj = p > R(0) ? z{aj.x / p, REAL ? R(0) : aj.y / p} : z{R(0), R(0)};
+        const z lj = p > R(0) ? z{aj.x * inv, REAL ? R(0) : aj.y * inv} : z{R(0), R(0)};
         if (lane == j) a = lj;
         if (lane > j && lane < b && p > R(0)) {   // a_q -= l_j conj(L11[q][j])
           const z lq = D[lane][j];
@@ -275,19 +285,21 @@ __global__ void __launch_bounds__(256) k_chol_blocked(z* A, int n, int lda, R dr
       const int q = q0 + lane;
       const bool act = q <= r;
       const z lr = lane < b ? ldz(&A[(size_t)r * lda + j0 + lane]) : z{R(0), R(0)};
-      const z* lq = A + (size_t)(act ? q : r) * lda + j0;
+      const z* lqp = A + (size_t)(act ? q : r) * lda + j0;
+      // the lane's row of L21, all loads issued before the first use
+      z lq[kCholB];
+#pragma unroll
+      for (int k = 0; k < kCholB; ++k) lq[k] = (act && k < b) ? ldz(lqp + k) : z{R(0), R(0)};
       z acc = {R(0), R(0)};
-      for (int k = 0; k < b; ++k) {   // acc = sum_k l_rk conj(l_qk)
+#pragma unroll
+      for (int k = 0; k < kCholB; ++k) {   // acc = sum_k l_rk conj(l_qk)
         const R rx = __shfl_sync(0xffffffffu, lr.x, k);
         const R ry = REAL ? R(0) : __shfl_sync(0xffffffffu, lr.y, k);
-        if (act) {
-          const z lk = ldz(lq + k);
-          if (REAL) {
-            acc.x = fmar(rx, lk.x, acc.x);
-          } else {
-            acc.x = fmar(rx, lk.x, fmar(ry, lk.y, acc.x));
-            acc.y = fmar(ry, lk.x, fmar(-rx, lk.y, acc.y));
-          }
+        if (REAL) {
+          acc.x = fmar(rx, lq[k].x, acc.x);
+        } else {
+          acc.x = fmar(rx, lq[k].x, fmar(ry, lq[k].y, acc.x));
+          acc.y = fmar(ry, lq[k].x, fmar(-rx, lq[k].y, acc.y));
         }
       }
       if (act) {
@@ -2555,7 +2567,10 @@ int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R
       return heev_finish(n, nev, w, X, ldx, wk, st, pf, true, true);   // real pair-packed reflectors
     }
   }
-  const int gf = tridiag_fused_grid(n, &rsm);
+  // the fused kernel holds a whole SM's registers (512 threads x 128): beside
+  // other solves' kernels (C3 lockstep rounds: batched FP64 Davidson 44.5 ->
+  // 41.6 solves/s with it) the rows kernel, which shares an SM, is the better one
+  const int gf = wk.shared ? 0 : tridiag_fused_grid(n, &rsm);
   if (gf > 0) {
     void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.d, &wk.refl, &bar};
     {
