@@ -1579,9 +1579,6 @@ int dv_round(qe_ctx* ctx, DvTask* const* tasks, int n, void* stream, void* const
   cudaStream_t st = (cudaStream_t)stream;
   Prof* pf = &ctx->prof;
   auto live = [&](const DvTask* t) { return t->rc == QE_OK && t->phase != DV_DONE; };
-  int nlive = 0;
-  for (int i = 0; i < n; ++i) nlive += live(tasks[i]) ? 1 : 0;
-  for (int i = 0; i < n; ++i) tasks[i]->v.S.dw.shared = nlive > 1;
   // task i runs its own work on side stream i % nside (the same stream in every
   // round, so a task's work stays in order)
   const int ns = std::max(1, nside);

@@ -53,8 +53,6 @@ struct DenseWorkT {
   int* status = nullptr;       // device status word (0 = ok)
   GridBar bar;                 // barrier state (3 words, next to status)
   R ctol_rel = RealT<R>::ctol; // cluster width relative to the spread of T
-  bool shared = false;         // other solves' kernels run beside this one's (lockstep
-                               // rounds): keep to the kernels that share an SM
 };
 using DenseWork = DenseWorkT<double>;
 

@@ -1174,28 +1174,7 @@ __global__ void __launch_bounds__(256) k_tridiag_rows_ff(z* A, int n, int lda, z
   }
 }
 
-// ---- the same reduction with one pass over the rows per step --------------------------
-// In k_tridiag_rows_ff most of a step is CTA-local latency, not the grid barrier
-// (phase clocks over a C2 solve: 1.6 of 8.0 us per column at the barrier, 3.2 in
-// the two passes over the rows, 1.2 in the block sums).  This form (512 threads)
-// defers the rank-2 update of step j - 1 on the owned rows into the pass of step
-// j that forms p = tau A v, so each element is read, updated, written back and
-// multiplied by v_j in one visit.  The rows' pending pair (v_{j-1}, w_{j-1})
-// therefore lives beside v_j (two v buffers alternate; w overwrites its
-// predecessor once the pass is done), and row j, which no later pass visits,
-// takes its diagonal share of the pending update from its owner.  One warp forms
-// the reflector's scalars (norm, beta, tau and the scale of v) and the others
-// read them from shared memory; v itself is formed inside the pass by the thread
-// that owns its index.  After the grid barrier each thread loads the published
-// p and next-column entries it needs (p_0, p_i, p_{i+1}, x_i), so w and the
-// updated column follow from one block sum (v^+ p) without another barrier.  The
-// p sums of the (at most 8) rows leave a warp in one transposing butterfly (each
-// level halves the rows a lane carries).  Reflectors are those of
-// k_tridiag_rows_ff up to rounding order.  Dynamic shared memory:
-// (ceil(n / G) + 4) n complex; n <= kTridFusedU * 512.
-constexpr int kTridFusedThreads = 512;
-constexpr int kTridFusedU = 2;
-
+// ---- helpers of the one-pass real tridiagonalisation and back-transformation ---------
 __device__ __forceinline__ ff2 pk_shfl_idx(ff2 a, int src) {
   return {{__shfl_sync(0xffffffffu, a.hi.v, src)}, {__shfl_sync(0xffffffffu, a.lo.v, src)}};
 }
@@ -1228,224 +1207,31 @@ __device__ __forceinline__ ff2 pk_warp_rows8(const ff2 (&a)[8]) {
   s = s + pk_shfl_xor(s, 2);
   return s + pk_shfl_xor(s, 1);
 }
-// a - v conj(w_k) - w conj(v_k), given the row's (re, re) and (im, im) parts of
-// -v and -w and cw = conj(w_k), cv = conj(v_k)
-struct PkRank2Row {
-  ff2 nvr, nvi, nwr, nwi;
-};
-__device__ __forceinline__ PkRank2Row pk_rank2_row(ff2 v, ff2 w) {
-  const ff2 nv = pk_neg(v), nw = pk_neg(w);
-  return {pk_re(nv), pk_im(nv), pk_re(nw), pk_im(nw)};
-}
-__device__ __forceinline__ ff2 pk_rank2(ff2 a, const PkRank2Row& r, ff2 cw, ff2 cv) {
-  a = fma(r.nvr, cw, a);
-  a = fma(r.nvi, pk_i(cw), a);
-  a = fma(r.nwr, cv, a);
-  a = fma(r.nwi, pk_i(cv), a);
-  return ff2_settle(a);
-}
-
-__global__ void __launch_bounds__(kTridFusedThreads) k_tridiag_fused_ff(z* A, int n, int lda,
-                                                                      z* tau, R* e, R* dg,
-                                                                      z* refl, GridBar bar) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int U = kTridFusedU;
-  const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
-  const int nrmax = (n + G - 1) / G;
-  const int nr = c < n ? (n - 1 - c) / G + 1 : 0;   // rows owned: c + q G, q < nr
-  cx<ff>* rows = reinterpret_cast<cx<ff>*>(smem_raw);   // nrmax x n
-  // rows + (nrmax + (j & 1)) n: v_j; the other one v_{j-1}
-  cx<ff>* sw = rows + (size_t)(nrmax + 2) * n;   // w_{j-1} (pending), then w_j
-  cx<ff>* sx = rows + (size_t)(nrmax + 3) * n;   // column to reduce (index i <-> row j+1+i)
-  __shared__ cx<ff> rb[2][32];
-  __shared__ cx<ff> scal[2];   // the scale of v (x_i -> v_i) and tau
-  __shared__ cx<ff> spart[kTridFusedThreads / 32][kTridRows];
-  for (int q = 0; q < nr; ++q) {
-    const z* src = A + (size_t)(c + q * G) * lda;
-    for (int k = tid; k < n; k += nt) {
-      const z a = ldz(src + k);
-      rows[(size_t)q * n + k] = cx_from<ff>(a.x, a.y);
-    }
-  }
-  ff2 ss = pk_zero();   // squared norm of the column below its first entry
-  for (int i = tid; i < n - 1; i += nt) {
-    const z a = ldz(&A[(size_t)(1 + i) * lda]);
-    const cx<ff> x = cx_from<ff>(a.x, a.y);
-    sx[i] = x;
-    if (i >= 1) ss = as2(x) * as2(x) + ss;
-  }
-  if (c == 0 && tid == 0) dg[0] = ldz(&A[0]).x;
-  // every CTA has read A: its rows 0..3 become the exchange vectors
-  if (!grid_sync_mono(bar, 1)) return;
-  const ff2 one = {f2_of(1.f, 0.f), f2_of(0.f, 0.f)};
-  for (int j = 0; j < n - 1; ++j) {
-    const int m = n - 1 - j, par = j & 1;
-    const bool pend = j >= 1;
-    z* xp = A + (size_t)(2 * par) * lda;       // p_r at [r]
-    z* xc = A + (size_t)(2 * par + 1) * lda;   // A[r][j+1] at [r], r >= j+2
-    cx<ff>* sv = rows + (size_t)(nrmax + par) * n;
-    const cx<ff>* svp = rows + (size_t)(nrmax + (par ^ 1)) * n;
-    // reflector of step j from sx[0..m): one warp forms its scalars
-    for (int o = 16; o > 0; o >>= 1) ss = ss + pk_shfl_xor(ss, o);
-    if (lane == 0) rb[0][warp] = of2(ff2_settle(ss));
-    __syncthreads();
-    if (warp == 0) {
-      const ff2 s2 = pk_fold_partials(rb[0], nwarp);
-      if (lane == 0) {
-        const ff sigma = ffs_add(pk_get_re(s2), pk_get_im(s2));
-        const ff2 alpha = as2(sx[0]);
-        const ff ar = pk_get_re(alpha), ai = pk_get_im(alpha);
-        ff2 t, sc;
-        ff beta;
-        if (sigma.hi == 0.f && ai.hi == 0.f) {   // v = e_0, tau = 0
-          t = pk_zero();
-          sc = pk_zero();
-          beta = ar;
-        } else {
-          const ff nu = ffs_sqrt(ffs_add(ffs_add(ffs_mul(ar, ar), ffs_mul(ai, ai)), sigma));
-          beta = ar.hi >= 0.f ? ffs_neg(nu) : nu;
-          const ff amr = ffs_sub(ar, beta);
-          const ff rden = ffs_div(ff(1.f, 0.f), ffs_add(ffs_mul(amr, amr), ffs_mul(ai, ai)));
-          sc = pk_make(ffs_mul(amr, rden), ffs_neg(ffs_mul(ai, rden)));
-          t = pk_make(ffs_div(ffs_sub(beta, ar), beta), ffs_neg(ffs_div(ai, beta)));
-        }
-        scal[0] = of2(sc);
-        scal[1] = of2(t);
-        if (c == 0) { tau[j] = pk_to_z(t); e[j] = ffs_to_d(beta); }
-      }
-    } else if (pend && tid == 32 && c == j % G) {
-      // row j: the diagonal share of the pending update of step j - 1 (v_0 = 1)
-      const ff2 v0 = as2(svp[0]), w0 = as2(sw[0]);
-      const ff2 a = pk_rank2(as2(rows[(size_t)(j / G) * n + j]), pk_rank2_row(v0, w0),
-                             pk_conj(w0), pk_conj(v0));
-      dg[j] = ffs_to_d(pk_get_re(a));
-    }
-    __syncthreads();
-    const ff2 sc = as2(scal[0]), t = as2(scal[1]);
-    // v_k for the owned indices k = tid + u nt; the pending pair's column entries
-    ff2 vk[U], cwk[U], cvk[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = tid + u * nt;
-      vk[u] = cwk[u] = cvk[u] = pk_zero();
-      if (k < m) {
-        vk[u] = k == 0 ? one : ff2_settle(pk_mul(as2(sx[k]), sc));
-        sv[k] = of2(vk[u]);
-        // reflector rows stay packed float-float (k_wy_t_ff, k_backtransform_ff read them)
-        if (c == 0) *reinterpret_cast<cx<ff>*>(&refl[(size_t)j * n + (j + 1) + k]) = of2(vk[u]);
-        if (pend) {
-          cwk[u] = pk_conj(as2(sw[k + 1]));
-          cvk[u] = pk_conj(as2(svp[k + 1]));
-        }
-      }
-    }
-    // owned rows of the trailing block (r >= j+1): apply the pending update of
-    // step j - 1 to columns j+1.., and accumulate (A v)_r
-    const int q0 = c >= j + 1 ? 0 : (j + 1 - c + G - 1) / G;
-    const int nq = nr - q0;
-    if (nq > 0) {
-      ff2 acc[kTridRows];
-#pragma unroll
-      for (int q = 0; q < kTridRows; ++q) {
-        acc[q] = pk_zero();
-        if (q < nq) {
-          cx<ff>* base = rows + (size_t)(q0 + q) * n + (j + 1);
-          PkRank2Row rc{};
-          if (pend) {
-            const int kr = c + (q0 + q) * G - j;
-            rc = pk_rank2_row(as2(svp[kr]), as2(sw[kr]));
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int k = tid + u * nt;
-            if (k < m) {
-              ff2 a = as2(base[k]);
-              if (pend) {
-                a = pk_rank2(a, rc, cwk[u], cvk[u]);
-                base[k] = of2(a);
-              }
-              acc[q] = fma(pk_im(a), pk_i(vk[u]), fma(pk_re(a), vk[u], acc[q]));
-            }
-          }
-          acc[q] = ff2_settle(acc[q]);
-        }
-      }
-      const ff2 s8 = pk_warp_rows8(acc);
-      if ((lane & 3) == 0) spart[warp][lane >> 2] = of2(ff2_settle(s8));
-    }
-    __syncthreads();
-    if (warp < nq) {
-      ff2 a = lane < nwarp ? as2(spart[lane][warp]) : pk_zero();
-      for (int o = nwarp >> 1; o > 0; o >>= 1) a = a + pk_shfl_xor(a, o);
-      if (lane == 0) {
-        const int q = q0 + warp, r = c + q * G;
-        pk_store(&xp[r], ff2_settle(pk_mul(t, ff2_settle(a))));
-        if (r >= j + 2) pk_store(&xc[r], as2(rows[(size_t)q * n + (j + 1)]));
-      }
-    }
-    if (!grid_sync_mono(bar, (unsigned)j + 2)) return;
-    // all loads of the published vectors first: p_0, and per owned index i p_i,
-    // p_{i+1} and the next column's x_i
-    const ff2 p0 = pk_load(&xp[j + 1]);
-    ff2 pi[U], pn[U], xi[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = tid + u * nt;
-      pi[u] = pn[u] = xi[u] = pk_zero();
-      if (i < m) pi[u] = pk_load(&xp[j + 1 + i]);
-      if (i < m - 1) {
-        pn[u] = pk_load(&xp[j + 2 + i]);
-        xi[u] = pk_load(&xc[j + 2 + i]);
-      }
-    }
-    ff2 sp = pk_zero();
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (tid + u * nt < m) sp = pk_fma(pk_conj(vk[u]), pi[u], sp);
-    for (int o = 16; o > 0; o >>= 1) sp = sp + pk_shfl_xor(sp, o);
-    if (lane == 0) rb[1][warp] = of2(ff2_settle(sp));
-    __syncthreads();   // also publishes v_j (sv) to every thread
-    // w = p - (1/2) conj(tau) (v^+ p) v; the next column (rows j+2 ..):
-    // x_i - v_{i+1} conj(w_0) - w_{i+1} (v_0 = 1), and its squared norm below its
-    // first entry
-    const ff2 vp = pk_fold_partials(rb[1], nwarp);
-    const ff2 half = {f2_of(0.5f, 0.5f), f2_of(0.5f, 0.5f)};
-    const ff2 cf = ff2_settle(pk_mul(pk_conj(t), vp));
-    const ff2 ncoef = pk_neg(ff2{mul2(cf.hi, half.hi), mul2(cf.lo, half.lo)});
-    const ff2 cw0 = pk_conj(ff2_settle(pk_fma(ncoef, one, p0)));
-    ss = pk_zero();
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = tid + u * nt;
-      if (i < m) sw[i] = of2(ff2_settle(pk_fma(ncoef, vk[u], pi[u])));
-      if (i < m - 1) {
-        const ff2 v1 = as2(sv[i + 1]);
-        const ff2 w1 = ff2_settle(pk_fma(ncoef, v1, pn[u]));
-        const ff2 x = ff2_settle(pk_fma(pk_neg(v1), cw0, xi[u] - w1));
-        sx[i] = of2(x);
-        if (i >= 1) ss = x * x + ss;
-      }
-    }
-  }
-  // row n - 1: the diagonal share of the last step's update
-  __syncthreads();
-  if (n >= 2 && tid == 0 && c == (n - 1) % G) {
-    const ff2 v0 = as2(rows[(size_t)(nrmax + ((n - 2) & 1)) * n]), w0 = as2(sw[0]);
-    const ff2 a = pk_rank2(as2(rows[(size_t)((n - 1) / G) * n + (n - 1)]), pk_rank2_row(v0, w0),
-                           pk_conj(w0), pk_conj(v0));
-    dg[n - 1] = ffs_to_d(pk_get_re(a));
-  }
-}
-
 // ---- the real symmetric form (k = 0 reduced problems) ------------------------------
-// The reduced matrices of the k = 0 (real-in-r) Davidson are real symmetric;
-// this is k_tridiag_fused_ff on real values: the f32x2 lanes carry two adjacent
-// columns instead of (re, im), so a row pair costs three float-float FMAs where
-// a complex element costs six, and the rows take half the shared memory.  Rows
-// and vectors are pair-packed by absolute index (pair P = columns 2P and 2P+1,
-// as one cx<ff>: hi parts, then lo parts); vectors are zero outside their range
-// (v_j and w_j below index j+1, the column below j+2), so the pass and the
+// The reduced matrices of the k = 0 (real-in-r) Davidson are real symmetric
+// (the real-output products write exact zeros).  This reduction keeps the row
+// ownership, exchange vectors and single grid barrier per column of
+// k_tridiag_rows_ff, with its CTA-local latency cut (phase clocks in
+// k_tridiag_rows_ff over a C2 solve: 1.6 of 8.0 us per column at the grid
+// barrier, 3.2 in the two passes over the rows, 1.2 in the block sums):
+//  - the rank-2 update of step j - 1 on the owned rows is deferred into the pass
+//    of step j that forms p = tau A v, so each element is read, updated,
+//    written back and multiplied by v_j in one visit; the rows' pending pair
+//    (v_{j-1}, w_{j-1}) lives beside v_j (two v buffers alternate; w overwrites
+//    its predecessor once the pass is done), and row j, which no later pass
+//    visits, takes its diagonal share of the pending update from its owner;
+//  - one warp forms the reflector's scalars (norm, beta, tau, the scale of v),
+//    the others read them from shared memory, and v is formed inside the pass;
+//  - after the barrier each thread loads the published p and next-column
+//    entries it needs, so w and the next column follow from one block sum;
+//  - the p sums of the (at most 8) rows leave a warp in one transposing
+//    butterfly (each level halves the rows a lane carries);
+//  - the f32x2 lanes carry two adjacent columns instead of (re, im): a row pair
+//    costs three float-float FMAs where a complex element costs six, and the
+//    rows take half the shared memory.
+// Rows and vectors are pair-packed by absolute index (pair P = columns 2P and
+// 2P+1, as one cx<ff>: hi parts, then lo parts); vectors are zero outside their
+// range (v_j and w_j below index j+1, the column below j+2), so the pass and the
 // updates run over whole pairs and the lanes outside the trailing block add
 // exact zeros.  The exchange vectors hold p and the next column pair-packed as
 // floats.  tau leaves in the complex format (zero imaginary parts), the
@@ -2486,8 +2272,8 @@ static int tridiag_rows_grid(int n, size_t* smem) {
 }
 
 #if defined(QE_DENSE_FP64)
-// Grid of k_tridiag_real_ff (0: it does not fit): as k_tridiag_fused_ff, with
-// (ceil(n / G) + 4) ceil(n / 2) pairs of shared memory.
+// Grid of k_tridiag_real_ff (0: it does not fit): the CTA count of
+// k_tridiag_rows_ff, with (ceil(n / G) + 4) ceil(n / 2) pairs of shared memory.
 static int tridiag_real_grid(int n, size_t* smem) {
   if (n < 16 || n > 2 * kTridRealU * kTridRealThreads) return 0;
   int dev = 0, nsm = 0, optin = 0;
@@ -2512,31 +2298,6 @@ static int tridiag_real_grid(int n, size_t* smem) {
   return g;
 }
 
-// Grid of k_tridiag_fused_ff (0: it does not fit, use tridiag_rows_grid): the
-// CTA count of k_tridiag_rows_ff, (ceil(n / G) + 4) n complex of shared memory.
-static int tridiag_fused_grid(int n, size_t* smem) {
-  if (n < 16 || n > kTridFusedU * kTridFusedThreads) return 0;
-  int dev = 0, nsm = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
-    return 0;
-  cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, (const void*)k_tridiag_fused_ff) != cudaSuccess) return 0;
-  const int g = std::min(nsm, (n + 3) / 4);
-  const int nrmax = (n + g - 1) / g;
-  if (nrmax > kTridRows) return 0;
-  const size_t sm = (size_t)(nrmax + 4) * n * sizeof(z);
-  if (sm + fa.sharedSizeBytes > (size_t)optin) return 0;
-  set_max_dynamic_smem(k_tridiag_fused_ff);
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tridiag_fused_ff, kTridFusedThreads,
-                                                    sm) != cudaSuccess ||
-      occ < 1)
-    return 0;
-  *smem = sm;
-  return g;
-}
 #endif
 
 int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R>& wk,
@@ -2566,20 +2327,6 @@ int heev_lowest(z* A, int n, int lda, int nev, R* w, z* X, int ldx, DenseWorkT<R
       }
       return heev_finish(n, nev, w, X, ldx, wk, st, pf, true, true);   // real pair-packed reflectors
     }
-  }
-  // the fused kernel holds a whole SM's registers (512 threads x 128): beside
-  // other solves' kernels (C3 lockstep rounds: batched FP64 Davidson 44.5 ->
-  // 41.6 solves/s with it) the rows kernel, which shares an SM, is the better one
-  const int gf = wk.shared ? 0 : tridiag_fused_grid(n, &rsm);
-  if (gf > 0) {
-    void* args[] = {&A, &n, &lda, &wk.tau, &wk.e, &wk.d, &wk.refl, &bar};
-    {
-      ProfScope ps(pf, "heev_tridiag", st);
-      int rc0 = launch_coop((const void*)k_tridiag_fused_ff, gf, args, st, "k_tridiag_fused_ff",
-                            rsm, kTridFusedThreads);
-      if (rc0) return rc0;
-    }
-    return heev_finish(n, nev, w, X, ldx, wk, st, pf, true);   // packed reflectors
   }
 #endif
   const int g = tridiag_rows_grid(n, &rsm);

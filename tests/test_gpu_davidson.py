@@ -169,3 +169,22 @@ def test_c2_full_size_fp64_and_mixed_against_oracle(q, ctx):
     rc, it, ev, rs = _solve(q, ctx, prob, pt, 1e-6, max_iter=200)
     assert rc == q.QE_OK
     assert np.abs(ev - ref).max() <= 1e-10
+
+
+def test_c2_full_size_complex_bands_against_oracle(q, ctx):
+    """C2 with complex bands (QE_NO_GAMMA; the default on this grid keeps them
+    real in r): the complex reduced problems, their float-float
+    tridiagonalisation and the complex Cholesky of the orthonormalisation, FP64
+    within 1e-10 Ry and mixed within 1e-6 Ry of the oracle's Davidson."""
+    c, prob, pt0, keep = _setup(q, ctx, "C2")
+    ref = _golden("c2_davidson_eigs.txt")
+    pt = pt0.clone()
+    rc, it, ev, rs = _solve(q, ctx, prob, pt, 1e-4, precision=q.QE_MIXED | q.QE_NO_GAMMA,
+                            max_iter=200)
+    assert rc == q.QE_OK
+    assert np.abs(ev - ref).max() <= 1e-6
+    pt = pt0.clone()
+    rc, it, ev, rs = _solve(q, ctx, prob, pt, 1e-6, precision=q.QE_FP64 | q.QE_NO_GAMMA,
+                            max_iter=200)
+    assert rc == q.QE_OK
+    assert np.abs(ev - ref).max() <= 1e-10
