@@ -180,11 +180,12 @@ __device__ __forceinline__ void block_sum2_1b(R& a, R& b, R (*rb)[2][8], int par
 // zero pivot without dropping sets *status = 1 + column), which is Gram-Schmidt
 // with dropping expressed on the Gram matrix.  Blocked: panels of kCholB columns
 // with two grid barriers each instead of one per column.  Per panel every CTA
-// loads the diagonal block and one warp factors it in shared memory
-// (right-looking); the rows below are solved against it one row per warp
-// (L21 = A21 L11^-+, forward substitution across the lanes); after the barrier
-// CTA 0 writes L11 and the pivots, and every warp takes (row, 32 columns) units
-// of the trailing update A22 -= L21 L21^+; a second barrier closes the panel.
+// loads the diagonal block and factors it in shared memory (right-looking, the
+// update of each step spread over the CTA); the rows below are solved against
+// it one row per warp (L21 = A21 L11^-+, forward substitution across the
+// lanes); after the barrier CTA 0 writes L11 and the pivots, and every warp
+// takes (row, 32 columns) units of the trailing update A22 -= L21 L21^+; a
+// second barrier closes the panel.
 // The arithmetic is FP64 (R), spread over the grid for the trailing update,
 // whose FP64 work dominates; REAL: zero imaginary parts (the k = 0 Gram
 // matrices), a quarter of it.  The upper triangle is zeroed at the end.
@@ -206,42 +207,41 @@ __global__ void __launch_bounds__(256) k_chol_blocked(z* A, int n, int lda, R dr
       D[r][q] = q <= r ? ldz(&A[(size_t)(j0 + r) * lda + j0 + q]) : z{R(0), R(0)};
     }
     __syncthreads();
-    if (warp == 0) {
-      for (int j = 0; j < b; ++j) {
-        // lane j forms the pivot and its reciprocal (one square root and one
-        // division per column), the others scale by the reciprocal
-        R p = R(0), inv = R(0);
-        if (lane == j) {
-          const R d = D[j][j].x;
-          const bool keep = allow_drop ? (d > drop2) : (d > R(0));
-          p = keep ? sqrt(d) : R(0);
-          inv = keep ? R(1) / p : R(0);
-          D[j][j] = {p, R(0)};
-          sd[j] = p;
-          sdi[j] = inv;
-        }
-        p = __shfl_sync(0xffffffffu, p, j);
-        inv = __shfl_sync(0xffffffffu, inv, j);
-        const bool keep = p > R(0);
-        if (lane > j && lane < b) {
-          const z a = D[lane][j];
-          D[lane][j] = keep ? z{a.x * inv, REAL ? R(0) : a.y * inv} : z{R(0), R(0)};
-        }
-        __syncwarp();
-        if (keep && lane > j && lane < b) {
-          const z lj = D[lane][j];
-          for (int k = j + 1; k <= lane; ++k) {
-            const z lk = D[k][j];
-            z& a = D[lane][k];
-            if (REAL) {
-              a.x = fmar(-lj.x, lk.x, a.x);
-            } else {   // a -= lj conj(lk)
-              a.x = fmar(-lj.x, lk.x, fmar(-lj.y, lk.y, a.x));
-              a.y = fmar(-lj.y, lk.x, fmar(lj.x, lk.y, a.y));
-            }
+    // the diagonal block, right-looking: one thread forms the pivot and its
+    // reciprocal, the CTA updates the rest of the block from the unscaled column
+    // (l_q l_k^+ = a_qj conj(a_kj) / d), then scales the column
+    for (int j = 0; j < b; ++j) {
+      if (tid == 0) {
+        const R d = D[j][j].x;
+        const bool keep = allow_drop ? (d > drop2) : (d > R(0));
+        const R p = keep ? sqrt(d) : R(0);
+        D[j][j] = {p, R(0)};
+        sd[j] = p;
+        sdi[j] = keep ? R(1) / p : R(0);
+      }
+      __syncthreads();
+      const R inv = sdi[j];
+      const int m = b - j - 1;
+      if (inv > R(0)) {
+        for (int t = tid; t < m * m; t += nt) {
+          const int q = j + 1 + t / m, k = j + 1 + t % m;
+          if (k > q) continue;
+          const z aq = D[q][j], ak = D[k][j];
+          const R i2 = inv * inv;
+          z& a = D[q][k];
+          if (REAL) {
+            a.x = fmar(-aq.x * i2, ak.x, a.x);
+          } else {   // a -= aq conj(ak) / d
+            const z lq = {aq.x * i2, aq.y * i2};
+            a.x = fmar(-lq.x, ak.x, fmar(-lq.y, ak.y, a.x));
+            a.y = fmar(-lq.y, ak.x, fmar(lq.x, ak.y, a.y));
           }
         }
-        __syncwarp();
+      }
+      __syncthreads();
+      for (int q = j + 1 + tid; q < b; q += nt) {
+        const z a = D[q][j];
+        D[q][j] = inv > R(0) ? z{a.x * inv, REAL ? R(0) : a.y * inv} : z{R(0), R(0)};
       }
     }
     __syncthreads();
