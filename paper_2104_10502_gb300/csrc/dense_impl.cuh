@@ -1611,15 +1611,24 @@ __global__ void __launch_bounds__(256) k_inviter(const R* d, const R* e, int n, 
     __syncthreads();
     for (int it = 0; it < kInvIters; ++it) {
       if (threadIdx.x == 0) {
+        // running entries in registers (as k_inviter_ff)
+        R cur = y[0];
         for (int i = 0; i < n - 1; ++i) {
-          if (sw[i]) { const R t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
-          y[i + 1] -= ml[i] * y[i];
+          R nxt = y[i + 1];
+          if (sw[i]) { const R t = cur; cur = nxt; nxt = t; }
+          y[i] = cur;
+          cur = nxt - ml[i] * cur;
         }
+        y[n - 1] = cur;
+        R y1 = R(0), y2 = R(0);
         for (int i = n - 1; i >= 0; --i) {
           R s = y[i];
-          if (i + 1 < n) s -= u1[i] * y[i + 1];
-          if (i + 2 < n) s -= u2[i] * y[i + 2];
-          y[i] = s * u0[i];
+          if (i + 1 < n) s -= u1[i] * y1;
+          if (i + 2 < n) s -= u2[i] * y2;
+          const R yi = s * u0[i];
+          y[i] = yi;
+          y2 = y1;
+          y1 = yi;
         }
       }
       __syncthreads();
@@ -1745,15 +1754,25 @@ __global__ void __launch_bounds__(256) k_inviter_ff(const R* d, const R* e, int 
     __syncthreads();
     for (int it = 0; it < kInvIters; ++it) {
       if (threadIdx.x == 0) {
+        // the sweeps carry their running entries in registers: the recurrence
+        // does not wait on a shared-memory store and reload per step
+        ff cur = y[0];
         for (int i = 0; i < n - 1; ++i) {
-          if (sw[i]) { const ff t = y[i]; y[i] = y[i + 1]; y[i + 1] = t; }
-          y[i + 1] = ffs_sub(y[i + 1], ffs_mul(ml[i], y[i]));
+          ff nxt = y[i + 1];
+          if (sw[i]) { const ff t = cur; cur = nxt; nxt = t; }
+          y[i] = cur;
+          cur = ffs_sub(nxt, ffs_mul(ml[i], cur));
         }
+        y[n - 1] = cur;
+        ff y1(0.f, 0.f), y2(0.f, 0.f);   // y[i + 1], y[i + 2] of the backward sweep
         for (int i = n - 1; i >= 0; --i) {
           ff sacc = y[i];
-          if (i + 1 < n) sacc = ffs_sub(sacc, ffs_mul(u1[i], y[i + 1]));
-          if (i + 2 < n) sacc = ffs_sub(sacc, ffs_mul(u2[i], y[i + 2]));
-          y[i] = ffs_mul(sacc, u0[i]);
+          if (i + 1 < n) sacc = ffs_sub(sacc, ffs_mul(u1[i], y1));
+          if (i + 2 < n) sacc = ffs_sub(sacc, ffs_mul(u2[i], y2));
+          const ff yi = ffs_mul(sacc, u0[i]);
+          y[i] = yi;
+          y2 = y1;
+          y1 = yi;
         }
       }
       __syncthreads();
