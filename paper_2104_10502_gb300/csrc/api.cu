@@ -219,6 +219,35 @@ int check_problem(const qe_problem* pr, const char* who) {
 #define QE_CU(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_error("%s: %s", #x, cudaGetErrorString(e_)); return QE_ECUDA; } } while (0)
 
 // Device views of the problem's operator arrays (copied in when they are host arrays).
+// psi of a host-memory call into dst in up to 8 band chunks on the copy stream,
+// one event per chunk (after the buffers' stream-ordered allocation on st).
+static int upload_psi_chunks(qe_ctx* ctx, const double* psi, double* dst, int nb, int npw,
+                             cudaStream_t st) {
+  if (!ctx->side) {
+    QE_CU(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    QE_CU(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    QE_CU(cudaEventCreateWithFlags(&ctx->ev_op, cudaEventDisableTiming));
+  }
+  const int chunk = (nb + 7) / 8, nch = (nb + chunk - 1) / chunk;
+  while ((int)ctx->psi_ev.size() < nch) {
+    cudaEvent_t e;
+    QE_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->psi_ev.push_back(e);
+  }
+  QE_CU(cudaEventRecord(ctx->ev_fork, st));
+  QE_CU(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  const size_t band = (size_t)npw * 2;
+  for (int c = 0; c < nch; ++c) {
+    const int b0 = c * chunk, n = std::min(chunk, nb - b0);
+    QE_CU(cudaMemcpyAsync(dst + (size_t)b0 * band, psi + (size_t)b0 * band, (size_t)n * band * sizeof(double),
+                          cudaMemcpyHostToDevice, ctx->side));
+    QE_CU(cudaEventRecord(ctx->psi_ev[c], ctx->side));
+  }
+  ctx->psi_ev_n = nch;
+  ctx->psi_ev_bands = chunk;
+  return QE_OK;
+}
+
 int resolve_operator(qe_ctx* ctx, const qe_problem* pr, const DevPlan& P, OpView& op,
                      cudaStream_t st, bool overlap) {
   const size_t ngrid = (size_t)P.grid[0] * P.grid[1] * P.grid[2];
@@ -284,11 +313,17 @@ static int hpsi_device(qe_ctx* ctx, const DevPlan& P, const OpView& op, const do
   nfb = std::min(nfb, (nb + per_fft - 1) / per_fft);
   const int nbc = nfb * per_fft;
   QE_TRY(ctx->sticks.ensure(stick_bytes(P, nfb, 2 * sizeof(T))));
+  int waited = 0;   // psi chunks of a host-memory call already joined
   for (int b0 = 0; b0 < nb; b0 += nbc) {
     const int n = std::min(nbc, nb - b0);
+    if (ctx->psi_ev_n > 0) {
+      const int need = std::min(ctx->psi_ev_n, (b0 + n + ctx->psi_ev_bands - 1) / ctx->psi_ev_bands);
+      for (; waited < need; ++waited) QE_CU(cudaStreamWaitEvent(st, ctx->psi_ev[waited], 0));
+    }
     QE_TRY(launch_local_kinetic<T>(P, psi, hpsi, (const T*)ctx->vp.p, ctx->sticks.p, b0, n, st,
                                    &ctx->prof, pair ? 1 : 0));
   }
+  for (; waited < ctx->psi_ev_n; ++waited) QE_CU(cudaStreamWaitEvent(st, ctx->psi_ev[waited], 0));
   if (op.ready) QE_CU(cudaStreamWaitEvent(st, op.ready, 0));
   const bool use_oz = op.nproj > 0 && !std::is_same<T, float>::value && oz_worth(op.nproj, nb, npw);
   if (op.gen && op.nproj > 0 && !use_oz) {
@@ -425,6 +460,7 @@ void qe_ctx_destroy(qe_ctx* ctx) {
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_op);
   }
+  for (cudaEvent_t e : ctx->psi_ev) cudaEventDestroy(e);
   for (void* x : ctx->round_side) {
     cudaStreamSynchronize((cudaStream_t)x);
     cudaStreamDestroy((cudaStream_t)x);
@@ -545,12 +581,20 @@ int qe_hpsi(qe_ctx* ctx, const qe_problem* prob, int precision, const double* ps
   const size_t nel = (size_t)nb * P->h.npw * 2;
   const double* dpsi = psi;
   double* dhpsi = hpsi;
+  // the pending upload belongs to this call only, whatever path it leaves by
+  struct PsiUploadReset {
+    qe_ctx* c;
+    ~PsiUploadReset() { c->psi_ev_n = 0; }
+  } psi_upload_reset{ctx};
+  ctx->psi_ev_n = 0;
   if (prob->mem == QE_HOST && nb > 0) {
     QE_TRY(ctx->h_psi.ensure(nel * sizeof(double)));
     QE_TRY(ctx->h_hpsi.ensure(nel * sizeof(double)));
-    QE_CU(cudaMemcpyAsync(ctx->h_psi.p, psi, nel * sizeof(double), cudaMemcpyHostToDevice, st));
     dpsi = (const double*)ctx->h_psi.p;
     dhpsi = (double*)ctx->h_hpsi.p;
+    // psi in band chunks on the copy stream, ahead of beta: the FFTs of the
+    // first chunks run while the rest arrives
+    QE_TRY(upload_psi_chunks(ctx, psi, (double*)ctx->h_psi.p, nb, P->h.npw, st));
   }
   // host operator: V on st, beta and D on the side stream while the FFTs run
   OpView op;

@@ -50,6 +50,11 @@ struct qe_ctx {
   // while the FFTs run) and its two events (created on first use)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_op = nullptr;
+  // host-memory qe_hpsi: psi goes in on `side` in chunks of psi_ev_bands bands,
+  // psi_ev[c] recorded after chunk c; the FFT of a band chunk waits only for
+  // the copies it reads (psi_ev_n = 0: no pending upload)
+  std::vector<cudaEvent_t> psi_ev;
+  int psi_ev_n = 0, psi_ev_bands = 0;
   // batched H|psi> workspaces (created on first use; type private to batch.cu)
   std::shared_ptr<void> batch;
   // per-solve Davidson workspaces of a batched solve (basis, reduced matrices)

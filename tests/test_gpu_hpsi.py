@@ -172,21 +172,24 @@ def test_hpsi_mixed_matches_oracle(q, ctx):
     assert _rel_band(_from_t(ht), want).max() <= 2e-5
 
 
-def test_hpsi_host_memory_matches_device(q, ctx):
+@pytest.mark.parametrize("prec_name,nb", [("QE_FP64", 5), ("QE_FP64", 19), ("QE_MIXED", 11)])
+def test_hpsi_host_memory_matches_device(q, ctx, prec_name, nb):
+    """Host buffers (psi uploaded in band chunks beside the FFTs, beta beside
+    them too) give bit for bit the device-buffer result."""
+    prec = getattr(q, prec_name)
     c = _cell("SMALL")
-    nb = 5
     prob_d, (vg, bg, dg), kin = _gpu_problem(q, ctx, c, nb)
     psi = qeinputs.random_vectors(nb, len(kin), seed=3)
     pt = _to_t(psi)
     ht = torch.empty_like(pt)
-    ctx.hpsi(prob_d, pt, ht, q.QE_FP64)
+    ctx.hpsi(prob_d, pt, ht, prec)
     torch.cuda.synchronize()
     vh = vg.cpu().numpy().copy()
     bh = bg.cpu().numpy().copy()
     dh = dg.cpu().numpy().copy()
     prob_h = ctx.problem(c["lat"], c["k"], c["ecut"], c["grid"], vh, bh, dh, nb)
     out = np.zeros_like(psi)
-    ctx.hpsi(prob_h, np.ascontiguousarray(psi), out, q.QE_FP64)
+    ctx.hpsi(prob_h, np.ascontiguousarray(psi), out, prec)
     assert np.array_equal(out, _from_t(ht))
 
 
