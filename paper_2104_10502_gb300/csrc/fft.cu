@@ -360,8 +360,8 @@ __device__ void plane_tile_sq(const FftJob<T>& J, int b, int pz, unsigned char* 
   __syncthreads();
   const FastDiv fax(nax), fn(N);
   const int nw = nt >> 5;
-  if (sizeof(cx<T>) == 16 && N % nw == 0) {
-    // 16-byte elements (float-float, float64): x rows owned by warps
+  if (N % nw == 0) {
+    // x rows owned by warps
     sq_inverse_y<T, N>(J, plane, tab, ax);
     const FastDiv fR(N / nw);
     sq_x_step_warp_rows<T, N>(J, plane, tab, vz, N / nw, fR);
